@@ -1,0 +1,165 @@
+"""Closed-form deflection and deformation tensor per component (oracle, FP64).
+
+TEST INFRASTRUCTURE ONLY.
+
+Conventions (Sec. 2.1): angles in arcsec (theta_0 = 1"), the potential psi is
+defined without a_dis, so every strength here is the a_dis = 1 value; the
+position angle is counter-clockwise from +x; ellipticity eps = (1-q)/(1+q).
+Each function takes offsets (dx, dy) = theta - theta_c as float64 tensors (any
+broadcastable shape, e.g. (S, 1) parameters against (1, N) positions) and
+returns (alpha_x, alpha_y, psi_xx, psi_yy, psi_xy).
+
+The paper lists no profile formulas; it follows Keeton (2001) for the PJE
+(Sec. 3.4) and names an "isothermal ellipsoid with a finite core radius"
+(SIELens, Sec. 5).  The forms below are that catalogue's softened isothermal
+ellipsoid, its dPIE difference, the spherical NFW (Bartelmann 1996) and the
+external shear, written from their definitions.  Pins: tests/test_oracle_profiles.py.
+"""
+import torch
+
+
+def _rotate_back(c, s, au, av, puu, pvv, puv):
+    """(u, v) = M (dx, dy) with M = [[c, s], [-s, c]]: alpha = M^T alpha_uv,
+    Psi = M^T Psi_uv M."""
+    ax = c * au - s * av
+    ay = s * au + c * av
+    pxx = c * c * puu - 2.0 * c * s * puv + s * s * pvv
+    pyy = s * s * puu + 2.0 * c * s * puv + c * c * pvv
+    pxy = c * s * (puu - pvv) + (c * c - s * s) * puv
+    return ax, ay, pxx, pyy, pxy
+
+
+def sie(dx, dy, b, q, pa, s):
+    """Cored (softened) isothermal ellipsoid.
+
+    kappa = (b/2) / sqrt(s^2 + u^2 + v^2/q^2) with (u, v) the frame rotated by
+    the position angle (major axis along u).  With psi~ = sqrt(q^2 (s^2 + u^2) + v^2)
+    and e = sqrt(1 - q^2):
+      alpha_u = (b q / e) atan(e u / (psi~ + s)),
+      alpha_v = (b q / e) atanh(e v / (psi~ + q^2 s)),
+      psi_uu = (b q / psi~) (q^2 s^2 + v^2 + s psi~) / D,
+      psi_vv = (b q / psi~) (s^2 + u^2 + s psi~) / D,
+      psi_uv = -(b q / psi~) u v / D,    D = (1 + q^2) s^2 + 2 psi~ s + u^2 + v^2.
+    q = 1 takes the limit alpha = b (u, v) / (psi~ + s).
+    """
+    dx, dy, b, q, pa, s = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64)
+                                                     for t in (dx, dy, b, q, pa, s)])
+    c, sn = torch.cos(pa), torch.sin(pa)
+    u = c * dx + sn * dy
+    v = -sn * dx + c * dy
+    q2 = q * q
+    psi = torch.sqrt(q2 * (s * s + u * u) + v * v)
+    e = torch.sqrt((1.0 - q) * (1.0 + q))
+    round_ = e == 0
+    e_safe = torch.where(round_, torch.ones_like(e), e)
+    au_ell = b * q / e_safe * torch.atan(e_safe * u / (psi + s))
+    av_ell = b * q / e_safe * torch.atanh(e_safe * v / (psi + q2 * s))
+    au = torch.where(round_, b * u / (psi + s), au_ell)
+    av = torch.where(round_, b * v / (psi + s), av_ell)
+    D = (1.0 + q2) * s * s + 2.0 * psi * s + u * u + v * v
+    f = b * q / (psi * D)
+    puu = f * (q2 * s * s + v * v + s * psi)
+    pvv = f * (s * s + u * u + s * psi)
+    puv = -f * u * v
+    return _rotate_back(c, sn, au, av, puu, pvv, puv)
+
+
+def dpie(dx, dy, b, q, pa, core, cut):
+    """Pseudo-Jaffe ellipsoid / dPIE: the cored ellipsoid of core radius `core`
+    minus the same ellipsoid of core radius `cut` (Keeton 2001), i.e.
+    kappa = (b/2) [1/sqrt(core^2 + xi^2) - 1/sqrt(cut^2 + xi^2)], xi^2 = u^2 + v^2/q^2."""
+    a1 = sie(dx, dy, b, q, pa, core)
+    a2 = sie(dx, dy, b, q, pa, cut)
+    return tuple(p - m for p, m in zip(a1, a2))
+
+
+def _axisym(dx, dy, kbar, kappa, r2):
+    """Axially symmetric lens: alpha = kbar (dx, dy) with kbar the mean convergence
+    inside r, Psi_ij = kbar delta_ij + 2 (kappa - kbar) x_i x_j / r^2."""
+    pos = r2 > 0
+    r2s = torch.where(pos, r2, torch.ones_like(r2))
+    t = torch.where(pos, 2.0 * (kappa - kbar) / r2s, torch.zeros_like(r2))
+    return kbar * dx, kbar * dy, kbar + t * dx * dx, kbar + t * dy * dy, t * dx * dy
+
+
+def pje_sph(dx, dy, b, core, cut):
+    """Spherical pseudo-Jaffe (dPIE with q = 1), used for cluster members under axial
+    symmetry (Sec. 4.1, 4.2).  With S = sqrt(core^2 + r^2), R = sqrt(cut^2 + r^2):
+    kappa = (b/2)(1/S - 1/R), kbar = b/(S + core) - b/(R + cut)."""
+    dx, dy, b, core, cut = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64)
+                                                     for t in (dx, dy, b, core, cut)])
+    r2 = dx * dx + dy * dy
+    S = torch.sqrt(core * core + r2)
+    R = torch.sqrt(cut * cut + r2)
+    kbar = b / (S + core) - b / (R + cut)
+    kappa = 0.5 * b * (1.0 / S - 1.0 / R)
+    return _axisym(dx, dy, kbar, kappa, r2)
+
+
+def _series(w, n_terms=12):
+    """sum_{n>=0} w^n / (2n + 1)  (= atanh(sqrt w)/sqrt w for w > 0, atan(sqrt -w)/sqrt -w for w < 0)."""
+    out = torch.zeros_like(w)
+    p = torch.ones_like(w)
+    for n in range(n_terms):
+        out = out + p / (2 * n + 1)
+        p = p * w
+    return out
+
+
+def nfw_sph(dx, dy, ks, rs):
+    """Spherical NFW (Bartelmann 1996) with x = r / rs:
+    F(x) = atanh(sqrt(1-x^2))/sqrt(1-x^2) (x<1), atan(sqrt(x^2-1))/sqrt(x^2-1) (x>1);
+    kappa = 2 ks (1 - F)/(x^2 - 1);  h(x) = ln(x/2) + 2 atanh(sqrt((1-x)/(1+x)))/sqrt(1-x^2)
+    (atan form for x > 1);  kbar = 4 ks h / x^2.  Near x = 1 both use the power series
+    in w = 1 - x^2 and u = (1-x)/(1+x) of the same functions."""
+    dx, dy, ks, rs = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64)
+                                               for t in (dx, dy, ks, rs)])
+    r2 = dx * dx + dy * dy
+    x2 = r2 / (rs * rs)
+    x = torch.sqrt(x2)
+    w = (1.0 - x) * (1.0 + x)
+    near = w.abs() < 1e-3
+    lt = (w > 0) & ~near
+    gt = (w < 0) & ~near
+    wl = torch.where(lt, w, torch.full_like(w, 0.5))
+    wg = torch.where(gt, -w, torch.full_like(w, 0.5))
+    Flt = torch.atanh(torch.sqrt(wl)) / torch.sqrt(wl)
+    Fgt = torch.atan(torch.sqrt(wg)) / torch.sqrt(wg)
+    # (1 - F)/(x^2 - 1) = (F - 1)/w ; near x = 1 the series sum_{n>=1} w^{n-1}/(2n+1)
+    g_near = _tail(torch.where(near, w, torch.zeros_like(w)))
+    F = torch.where(lt, Flt, torch.where(gt, Fgt, torch.ones_like(w)))
+    wsafe = torch.where(near, torch.ones_like(w), w)
+    kappa = 2.0 * ks * torch.where(near, g_near, (F - 1.0) / wsafe)
+    # h(x) = ln(x/2) + (2/(1+x)) sum_n u^n/(2n+1), u = (1-x)/(1+x)
+    u = (1.0 - x) / (1.0 + x)
+    nu = u.abs() < 1e-3
+    ul = torch.where((u > 0) & ~nu, u, torch.full_like(u, 0.5))
+    ug = torch.where((u < 0) & ~nu, -u, torch.full_like(u, 0.5))
+    Hl = torch.atanh(torch.sqrt(ul)) / torch.sqrt(ul)
+    Hg = torch.atan(torch.sqrt(ug)) / torch.sqrt(ug)
+    Hs = _series(torch.where(nu, u, torch.zeros_like(u)))
+    Hsum = torch.where(nu, Hs, torch.where(u > 0, Hl, Hg))
+    h = torch.log(x / 2.0) + 2.0 / (1.0 + x) * Hsum
+    kbar = 4.0 * ks * h / x2
+    return _axisym(dx, dy, kbar, kappa, r2)
+
+
+def _tail(w, n_terms=12):
+    """sum_{n>=1} w^{n-1} / (2n + 1) = (F - 1)/w for the series F above."""
+    out = torch.zeros_like(w)
+    p = torch.ones_like(w)
+    for n in range(1, n_terms + 1):
+        out = out + p / (2 * n + 1)
+        p = p * w
+    return out
+
+
+def shear(dx, dy, gamma, pa):
+    """External shear psi = (gamma/2) r^2 cos 2(phi - pa):
+    (gamma1, gamma2) = gamma (cos 2pa, sin 2pa), alpha = (g1 dx + g2 dy, g2 dx - g1 dy),
+    kappa = 0."""
+    dx, dy, gamma, pa = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64)
+                                                  for t in (dx, dy, gamma, pa)])
+    g1 = gamma * torch.cos(2.0 * pa)
+    g2 = gamma * torch.sin(2.0 * pa)
+    return g1 * dx + g2 * dy, g2 * dx - g1 * dy, g1, -g1, g2
