@@ -1,0 +1,243 @@
+/*
+ * lf.h -- C ABI of the B300 (sm_103a) batched lens-equation / source-plane chi^2 library.
+ *
+ * The library evaluates the paper's strong-lensing forward model on the GPU:
+ *   - deflection alpha and deformation tensor psi_ij summed over analytic components
+ *     (cored isothermal ellipsoid, dPIE / pseudo-Jaffe ellipsoid, spherical NFW, external
+ *     shear) and over cluster members on the luminosity scaling relations
+ *     (Sec. 2.1; Sec. 3.4, Eq. scaling);
+ *   - the lens map beta = theta - a_dis alpha (Eq. lens_eq), the Jacobian
+ *     A = I - a_dis psi_ij (Eq. jac), kappa, gamma and mu = 1/det A (Sec. 2.1);
+ *   - multi-plane ray tracing with the Jacobian product (Sec. 2.2);
+ *   - the source-plane chi^2 with the analytic best-fit source (Eq. chi2_src, Sec. 3.1)
+ *     for thousands of parameter samples per launch, and its gradient with respect to the
+ *     parameters (the paper has no gradient; it is the hand-written adjoint of that chi^2).
+ *
+ * Conventions (Sec. 2.1): angles in arcsec; the potential carries no a_dis, so every
+ * strength is its a_dis = 1 value; position angles are radians counter-clockwise from +x;
+ * ellipticity eps = (1 - q)/(1 + q).  kappa and gamma returned by the grid calls are the
+ * paper's a_dis-free values; mu includes a_dis.
+ *
+ * Memory: arrays documented "device" are caller-owned device memory, read or written
+ * stream-ordered on `stream` (a cudaStream_t passed as void*; NULL = legacy default
+ * stream).  Arrays documented "host" are read during the call only.  No call allocates
+ * device memory except lf_plan_create, which owns everything it allocates until
+ * lf_plan_destroy.  Every call is asynchronous with respect to the host.
+ *
+ * Errors: every call validates its arguments before launching anything and returns
+ * LF_EINVAL (with a message in lf_last_error()) on a bad argument; LF_ECUDA when a CUDA
+ * call fails (including an earlier asynchronous fault that surfaces at launch);
+ * LF_EUNSUPPORTED for a valid request outside what the kernels implement.  Kernels never
+ * trap: a bounded wait that runs out sets a device error word that lf_device_error()
+ * reads and clears (LF_ETIMEOUT).  Nothing aborts the process.
+ */
+#ifndef LF_H_
+#define LF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LF_OK = 0,
+  LF_EINVAL = 1,
+  LF_ECUDA = 2,
+  LF_ENOMEM = 3,
+  LF_ETIMEOUT = 4,
+  LF_EUNSUPPORTED = 5
+} lf_status;
+
+/* Component kinds (Sec. 2.1 profile library; closed forms after Keeton 2001). */
+typedef enum {
+  LF_SIE = 1,    /* cored isothermal ellipsoid: b, eps, pa, core (= s)                 */
+  LF_DPIE = 2,   /* dPIE / pseudo-Jaffe ellipsoid: b, eps, pa, core, cut; eps = 0 is round */
+  LF_NFW = 3,    /* spherical NFW: b = kappa_s, core = theta_s (scale radius, arcsec)  */
+  LF_SHEAR = 4   /* external shear: b = gamma, pa = shear angle; x, y = reference point */
+} lf_kind;
+
+/* LF_FP64: every operation in FP64, one thread per position (the plain comparator).
+ * LF_MIXED: per-component closed forms in FP32 on offsets taken in float-float, FP32 sums
+ * per component chunk folded into float-float accumulators, then FP64 for det A, mu, the
+ * multi-plane Jacobian product and the chi^2 reduction. */
+typedef enum { LF_FP64 = 0, LF_MIXED = 1 } lf_precision;
+
+/* One explicit component, 64 bytes (device arrays of these are staged into shared
+ * memory by bulk copy, so the array must be 16-byte aligned). */
+typedef struct {
+  double x, y;     /* centre, arcsec */
+  double b;        /* strength at a_dis = 1 (arcsec; kappa_s for NFW; gamma for shear) */
+  double eps;      /* ellipticity (1-q)/(1+q), 0 <= eps < 1 */
+  double pa;       /* position angle, radians CCW from +x */
+  double core;     /* core radius s (arcsec); NFW scale radius theta_s */
+  double cut;      /* dPIE truncation radius (arcsec), cut > core */
+  int32_t kind;    /* lf_kind */
+  int32_t pad;
+} lf_comp;
+
+/* One cluster member, 32 bytes: a round pseudo-Jaffe galaxy whose strength, core and
+ * cut follow the scaling relations of Eq. scaling from its luminosity. */
+typedef struct {
+  double x, y;     /* centre, arcsec */
+  double log_l;    /* log10(L / L*) */
+  double pad;
+} lf_member;
+
+/* Eq. scaling in lensing units: v = v* (L/L*)^lam, so b = b* (L/L*)^(2 lam);
+ * core = core* (L/L*)^beta; cut = cut* (L/L*)^alpha. */
+typedef struct {
+  double b_star;     /* arcsec, = 4 pi (v_star / c)^2 */
+  double core_star;  /* arcsec */
+  double cut_star;   /* arcsec */
+  double lam, beta, alpha;
+} lf_scaling;
+
+/* One lens plane. */
+typedef struct {
+  int32_t n_comp;            /* >= 0 */
+  int32_t n_mem;             /* >= 0 */
+  const lf_comp* comp;       /* device [n_comp], 16-byte aligned (NULL if n_comp == 0) */
+  const lf_member* mem;      /* device [n_mem], 16-byte aligned (NULL if n_mem == 0) */
+  lf_scaling scaling;        /* host values, used when n_mem > 0 */
+} lf_plane;
+
+/* Pixel-centre grid: pixel (i, j) sits at (x0 + i dx, y0 + j dy); outputs are row-major
+ * with y the slow index, element j * nx + i. */
+typedef struct {
+  double x0, y0, dx, dy;
+  int32_t nx, ny;
+} lf_grid;
+
+/* ---------------------------------------------------------------- grid maps ------ */
+
+/* alpha on a grid (Sec. 2.1, alpha = grad psi).  ax, ay: device [ny * nx] FP64. */
+lf_status lf_deflect_grid(const lf_plane* plane, const lf_grid* grid, int32_t precision,
+                          double* ax, double* ay, void* stream);
+
+/* alpha, kappa, gamma1, gamma2 and mu = 1/det A with det A = (1 - a kappa)^2 - a^2 |gamma|^2
+ * evaluated in FP64 (Eq. jac and the magnification below it).  Any output pointer may be
+ * NULL to skip it.  ax, ay, mu: device FP64 [ny * nx]; kappa, g1, g2: device FP32.
+ * a_dis in (0, 1]. */
+lf_status lf_jacobian_grid(const lf_plane* plane, const lf_grid* grid, double a_dis,
+                           int32_t precision, double* ax, double* ay, float* kappa,
+                           float* g1, float* g2, double* mu, void* stream);
+
+/* Same quantities at arbitrary positions: theta device [n * 2] FP64 (x, y interleaved). */
+lf_status lf_jacobian_points(const lf_plane* plane, const double* theta, int32_t n,
+                             double a_dis, int32_t precision, double* ax, double* ay,
+                             float* kappa, float* g1, float* g2, double* mu, void* stream);
+
+/* ------------------------------------------------------------- multi-plane ------- */
+
+/* Multi-plane lens equation and Jacobian (Sec. 2.2):
+ *   theta_j = theta_1 - sum_{i<j} r[i][j] alpha_i(theta_i),
+ *   A_j = I - sum_{i<j} r[i][j] psi_i(theta_i) A_i,
+ *   beta = theta_1 - sum_j rs[j] alpha_j(theta_j),  A = I - sum_j rs[j] psi_j A_j,
+ * with r[i][j] = D_ij / D_j and rs[j] = D_js / D_s.
+ * planes: host [n_planes] (1 <= n_planes <= 8), ordered by redshift.
+ * ratios: host [(n_planes + 1) * n_planes]: row i < n_planes holds r[i][0..n_planes-1]
+ *   (only j > i is read), the last row holds rs[0..n_planes-1].
+ * Positions: theta device [n * 2] FP64, or theta == NULL and `grid` (n ignored).
+ * beta: device [n * 2] FP64; A: device [n * 4] FP64 row-major (A00, A01, A10, A11);
+ * either may be NULL. */
+lf_status lf_trace_multiplane(const lf_plane* planes, int32_t n_planes, const double* ratios,
+                              const double* theta, int32_t n, const lf_grid* grid,
+                              int32_t precision, double* beta, double* A, void* stream);
+
+/* ------------------------------------------------------------ chi^2 plans ------- */
+
+/* Field codes a sampled parameter can target, and the transform applied first. */
+typedef enum { LF_F_X = 0, LF_F_Y, LF_F_B, LF_F_EPS, LF_F_PA, LF_F_CORE, LF_F_CUT } lf_field;
+typedef enum { LF_S_BSTAR = 0, LF_S_CORESTAR, LF_S_CUTSTAR, LF_S_LAM, LF_S_BETA, LF_S_ALPHA } lf_scaling_slot;
+typedef enum {
+  LF_XF_IDENT = 0,   /* value used as is                                  */
+  LF_XF_VDISP = 1,   /* km/s -> b = 4 pi (v/c)^2 arcsec                   */
+  LF_XF_DEG = 2,     /* degrees -> radians                                */
+  LF_XF_KPC = 3      /* kpc -> arcsec with the plane's arcsec_per_kpc     */
+} lf_xform;
+
+/* Observed multiple images, grouped into families (CSR).  All host arrays. */
+typedef struct {
+  int32_t n_img, n_fam;
+  const double* theta_obs;   /* [n_img * 2] observed positions, arcsec               */
+  const double* sinv;        /* [n_img * 3] S_i^-1 as (xx, xy, yy) (Eq. chi2_img)    */
+  const int32_t* fam_off;    /* [n_fam + 1] image offsets, fam_off[0] = 0            */
+  const double* fam_ratio;   /* single plane: [n_fam] a_dis of each family;
+                                multi-plane: [n_fam * n_planes] D_js/D_s per family  */
+} lf_images;
+
+/* One cluster of a plan: its base model, images and parameter map.  The sampled
+ * parameter vector of length P overwrites P fields of the base model per sample. */
+typedef struct {
+  int32_t n_planes;                 /* 1..8 */
+  const lf_plane* planes;           /* host [n_planes]; comp/mem device pointers */
+  const double* ratios;             /* host, multi-plane only: r[i][j] as in
+                                       lf_trace_multiplane (rows 0..n_planes-1)   */
+  const double* arcsec_per_kpc;     /* host [n_planes] for LF_XF_KPC             */
+  lf_images images;
+  int32_t P;                        /* parameters per sample, 1..64 */
+  const int32_t* p_comp;            /* host [P]: component index counted over all planes
+                                       in order, or -1 for a scaling slot of the first
+                                       plane that has members                     */
+  const int32_t* p_field;           /* host [P]: lf_field, or lf_scaling_slot if -1 */
+  const int32_t* p_xform;           /* host [P]: lf_xform                            */
+} lf_cluster;
+
+typedef struct lf_plan lf_plan;
+
+/* Builds a plan for n_clusters clusters that share P.  Copies everything it needs to the
+ * device (the caller may free its arrays afterwards) and records the launch shape.
+ * flags: bit 0 = capture the chi^2 launch in a CUDA graph; bit 1 = autotune the tile
+ * shape on first use.  max_samples bounds S of later calls. */
+lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, int32_t n_clusters,
+                         int32_t max_samples, int32_t precision, int32_t flags);
+
+/* chi^2 of Eq. chi2_src (analytic source of Sec. 3.1) for S samples.
+ * theta: device [S * P] FP64 in the parameters' own units; samples are cluster-major:
+ * sample s belongs to cluster s / (S / n_clusters) (S must divide evenly).
+ * chi2: device [S] FP64.  A sample with a non-finite magnification matrix or a singular
+ * G in some family gets +inf; a one-image family contributes 0. */
+lf_status lf_chi2_batch(lf_plan* plan, const double* theta, int32_t S, double* chi2,
+                        void* stream);
+
+/* chi^2 and its gradient d chi^2 / d theta (device [S * P] FP64).  Single-plane plans
+ * only (LF_EUNSUPPORTED otherwise).  The source position is held at its optimum
+ * (d chi^2 / d beta_model = 0), so only the explicit dependence is differentiated. */
+lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int32_t S, double* chi2,
+                             double* grad, void* stream);
+
+lf_status lf_plan_destroy(lf_plan* plan);
+
+/* Tile shape chosen by the plan (components per thread slice, threads per block). */
+lf_status lf_plan_info(const lf_plan* plan, int32_t* kslices, int32_t* block, int32_t* graph);
+
+/* ------------------------------------------------------------- host helpers ------ */
+
+/* Flat LCDM angular-diameter distance D_A(z1, z2) in Mpc (Gauss-Legendre quadrature). */
+double lf_angular_distance(double H0, double Om, double z1, double z2);
+/* a_dis = D_ds / D_s. */
+double lf_adis(double H0, double Om, double z_l, double z_s);
+/* Angular size of one kpc at redshift z, arcsec. */
+double lf_arcsec_per_kpc(double H0, double Om, double z);
+/* b = 4 pi (v/c)^2 in arcsec for a velocity dispersion v in km/s. */
+double lf_b_from_vdisp(double v_kms);
+/* Spherical NFW (M200 [Msun], concentration c) at z_l -> kappa_s and theta_s [arcsec]
+ * (200 x the critical density at z_l; Sigma_cr at a_dis = 1). */
+lf_status lf_nfw_params(double H0, double Om, double z_l, double m200, double conc,
+                        double* kappa_s, double* theta_s);
+
+/* Reads and clears the device error word (waits for `stream`): LF_OK or LF_ETIMEOUT. */
+lf_status lf_device_error(void* stream);
+
+/* Message of the last failing call on this host thread. */
+const char* lf_last_error(void);
+
+/* Library version string. */
+const char* lf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LF_H_ */

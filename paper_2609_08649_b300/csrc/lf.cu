@@ -1,0 +1,7 @@
+// Unity build of the library: one translation unit, so the device error word and the
+// helpers are single definitions without relocatable device code.
+#include <type_traits>
+#include "lf_host.cu"
+#include "lf_grid.cu"
+#include "lf_trace.cu"
+#include "lf_chi2.cu"

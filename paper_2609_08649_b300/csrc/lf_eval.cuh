@@ -1,0 +1,134 @@
+// Plane evaluation loops shared by the map, trace and chi^2 kernels.
+//
+// A plane's components are indexed 0..nc-1 (explicit components) then nc..nc+nm-1
+// (members).  accumulate_mixed sums the index range [k0, k1) for PPT positions: explicit
+// components go straight into float-float accumulators, members are summed in FP32
+// over `chunk` consecutive members and each chunk sum is folded into the float-float
+// accumulators (FP32 accumulation per component block, extended precision across blocks).
+#pragma once
+#include "lf_common.cuh"
+
+namespace lf {
+
+// Shared-memory layout of a staged plane (host and device agree on it).
+struct PlaneLayout {
+  uint32_t rawc, rawm, dc, dm, total;
+};
+
+template <class T>
+__host__ __device__ inline PlaneLayout plane_layout(int nc, int nm, uint32_t base) {
+  PlaneLayout L;
+  uint32_t o = (base + 15u) & ~15u;
+  L.rawc = o; o += (uint32_t)nc * 64u;
+  L.rawm = o; o += (uint32_t)nm * 32u;
+  o = (o + 15u) & ~15u;
+  L.dc = o; o += (uint32_t)nc * (uint32_t)sizeof(CompT<T>);
+  o = (o + 15u) & ~15u;
+  L.dm = o; o += (uint32_t)nm * (uint32_t)sizeof(MemT<T>);
+  L.total = (o + 15u) & ~15u;
+  return L;
+}
+
+// Validates and digests one raw component (device side; invalid -> kind 0 + error bit).
+template <class T>
+__device__ inline void digest_one_comp(const lf_comp& r, CompT<T>& out) {
+  bool ok = r.kind >= 1 && r.kind <= 4 && isfinite(r.x) && isfinite(r.y) && isfinite(r.b) &&
+            isfinite(r.pa);
+  if (r.kind == LF_SIE || r.kind == LF_DPIE)
+    ok = ok && r.eps >= 0.0 && r.eps < 1.0 && r.core >= 0.0 && isfinite(r.core);
+  if (r.kind == LF_DPIE) ok = ok && isfinite(r.cut) && r.cut > r.core;
+  if (r.kind == LF_NFW) ok = ok && r.core > 0.0 && isfinite(r.core);
+  digest_comp<T>(ok ? r.kind : 0, r.x, r.y, r.b, r.eps, r.pa, r.core, r.cut, out);
+  if (!ok) lf_flag_error(LF_DEVERR_BADCOMP);
+}
+
+// Member strength, core and cut from the scaling relations (Eq. scaling), FP64.
+__device__ inline void member_fields(const lf_scaling& sc, double log_l, double& b, double& s,
+                                     double& a, double& ll) {
+  ll = log_l * 2.302585092994045684;
+  b = sc.b_star * exp(2.0 * sc.lam * ll);
+  s = sc.core_star * exp(sc.beta * ll);
+  a = sc.cut_star * exp(sc.alpha * ll);
+}
+
+// Digests a staged plane (raw tables already in shared memory), whole block.
+template <class T>
+__device__ void digest_plane(const lf_comp* rawc, int nc, const lf_member* rawm, int nm,
+                             const lf_scaling& sc, CompT<T>* dc, MemT<T>* dm) {
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) digest_one_comp<T>(rawc[i], dc[i]);
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+    double b, s, a, ll;
+    member_fields(sc, rawm[i].log_l, b, s, a, ll);
+    digest_member<T>(rawm[i].x, rawm[i].y, b, s, a, ll, dm[i]);
+  }
+}
+
+template <int PPT>
+__device__ __forceinline__ void accumulate_mixed(const CompT<float>* dc, int nc,
+                                                 const MemT<float>* dm, int nm, int k0, int k1,
+                                                 int chunk, const float* pxh, const float* pxl,
+                                                 const float* pyh, const float* pyl,
+                                                 ff (&acc)[5][PPT]) {
+  const int c1 = min(k1, nc);
+  for (int c = k0; c < c1; ++c) {
+    const CompT<float>& C = dc[c];
+    if (C.kind == 0) continue;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      float dx = offset_of(pxh[k], pxl[k], C.xh, C.xl);
+      float dy = offset_of(pyh[k], pyl[k], C.yh, C.yl);
+      Out5<float> o;
+      eval_comp(C, dx, dy, o);
+      ff_add(acc[0][k], o.ax); ff_add(acc[1][k], o.ay);
+      ff_add(acc[2][k], o.pxx); ff_add(acc[3][k], o.pyy); ff_add(acc[4][k], o.pxy);
+    }
+  }
+  const int m_beg = max(k0, nc) - nc, m_end = min(k1, nc + nm) - nc;
+  for (int m0 = m_beg; m0 < m_end; m0 += chunk) {
+    const int m1 = min(m0 + chunk, m_end);
+    float cs[5][PPT];
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) cs[v][k] = 0.f;
+    for (int m = m0; m < m1; ++m) {
+      const MemT<float> M = dm[m];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        float dx = offset_of(pxh[k], pxl[k], M.xh, M.xl);
+        float dy = offset_of(pyh[k], pyl[k], M.yh, M.yl);
+        Out5<float> o;
+        eval_member(M, dx, dy, o);
+        cs[0][k] += o.ax; cs[1][k] += o.ay;
+        cs[2][k] += o.pxx; cs[3][k] += o.pyy; cs[4][k] += o.pxy;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) ff_add(acc[v][k], cs[v][k]);
+  }
+}
+
+// FP64 version for one position: plain sum.
+__device__ __forceinline__ void accumulate_fp64(const CompT<double>* dc, int nc,
+                                                const MemT<double>* dm, int nm, int k0, int k1,
+                                                double x, double y, double (&acc)[5]) {
+  const int c1 = min(k1, nc);
+  for (int c = k0; c < c1; ++c) {
+    const CompT<double>& C = dc[c];
+    if (C.kind == 0) continue;
+    Out5<double> o;
+    eval_comp(C, x - C.xh, y - C.yh, o);
+    acc[0] += o.ax; acc[1] += o.ay; acc[2] += o.pxx; acc[3] += o.pyy; acc[4] += o.pxy;
+  }
+  const int m_beg = max(k0, nc) - nc, m_end = min(k1, nc + nm) - nc;
+  for (int m = m_beg; m < m_end; ++m) {
+    const MemT<double>& M = dm[m];
+    Out5<double> o;
+    eval_member(M, x - M.xh, y - M.yh, o);
+    acc[0] += o.ax; acc[1] += o.ay; acc[2] += o.pxx; acc[3] += o.pyy; acc[4] += o.pxy;
+  }
+}
+
+}  // namespace lf

@@ -1,0 +1,220 @@
+// Multi-plane ray tracing with the Jacobian product (Sec. 2.2).
+//
+// For each ray: theta_j = theta_1 - sum_{i<j} r_ij alpha_i(theta_i) and
+// A_j = I - sum_{i<j} r_ij Psi_i(theta_i) A_i, then beta = theta_1 - sum_j rs_j alpha_j and
+// A = I - sum_j rs_j Psi_j A_j.  All planes are staged into shared memory once per
+// (persistent) block.  LF_MIXED evaluates each plane's components in FP32 on float-float
+// offsets from theta_j (carried in FP64) and keeps the recursion and the 2x2 Jacobian
+// product in FP64; LF_FP64 does everything in FP64.
+#include "lf_internal.h"
+#include "lf_eval.cuh"
+
+namespace lf {
+
+constexpr int LF_MAX_PLANES = 8;
+
+struct MultiPlaneArgs {
+  int np;
+  const lf_comp* comp[LF_MAX_PLANES];
+  const lf_member* mem[LF_MAX_PLANES];
+  int nc[LF_MAX_PLANES], nm[LF_MAX_PLANES];
+  lf_scaling sc[LF_MAX_PLANES];
+  uint32_t base[LF_MAX_PLANES];     // shared-memory offset of each plane's layout
+  double r[LF_MAX_PLANES][LF_MAX_PLANES];
+  double rs[LF_MAX_PLANES];
+};
+
+// Stages and digests every plane; returns false (all threads) if a bounded wait ran out.
+template <class T>
+__device__ bool stage_planes(unsigned char* smem, uint64_t* bar, const MultiPlaneArgs& A) {
+  uint32_t phase = 0;
+  for (int j = 0; j < A.np; ++j) {
+    PlaneLayout L = plane_layout<T>(A.nc[j], A.nm[j], A.base[j]);
+    if (A.nc[j] > 0) {
+      if (!stage_to_smem(smem + L.rawc, A.comp[j], (uint32_t)A.nc[j] * 64u, bar, phase & 1u))
+        return false;
+      ++phase;
+    }
+    if (A.nm[j] > 0) {
+      if (!stage_to_smem(smem + L.rawm, A.mem[j], (uint32_t)A.nm[j] * 32u, bar, phase & 1u))
+        return false;
+      ++phase;
+    }
+    digest_plane<T>(reinterpret_cast<lf_comp*>(smem + L.rawc), A.nc[j],
+                    reinterpret_cast<lf_member*>(smem + L.rawm), A.nm[j], A.sc[j],
+                    reinterpret_cast<CompT<T>*>(smem + L.dc), reinterpret_cast<MemT<T>*>(smem + L.dm));
+  }
+  __syncthreads();
+  return true;
+}
+
+struct RayIO {
+  const double* pts;
+  double x0, y0, dx, dy;
+  int nx;
+  long long n;
+  double* beta;
+  double* A;
+};
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256) k_trace(MultiPlaneArgs MP, RayIO io, int chunk) {
+  typedef typename std::conditional<MIXED, float, double>::type T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (!stage_planes<T>(smem, bar, MP)) return;
+
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < io.n;
+       p += (long long)gridDim.x * blockDim.x) {
+    double t1x, t1y;
+    if (io.pts) {
+      t1x = io.pts[2 * p];
+      t1y = io.pts[2 * p + 1];
+    } else {
+      long long j = p / io.nx, i = p - j * io.nx;
+      t1x = io.x0 + (double)i * io.dx;
+      t1y = io.y0 + (double)j * io.dy;
+    }
+    double al[LF_MAX_PLANES][2];
+    double PA[LF_MAX_PLANES][4];   // Psi_j A_j, row-major
+    for (int j = 0; j < MP.np; ++j) {
+      double tx = t1x, ty = t1y;
+      double a00 = 1, a01 = 0, a10 = 0, a11 = 1;
+      for (int i = 0; i < j; ++i) {
+        double r = MP.r[i][j];
+        tx -= r * al[i][0];
+        ty -= r * al[i][1];
+        a00 -= r * PA[i][0]; a01 -= r * PA[i][1];
+        a10 -= r * PA[i][2]; a11 -= r * PA[i][3];
+      }
+      PlaneLayout L = plane_layout<T>(MP.nc[j], MP.nm[j], MP.base[j]);
+      const CompT<T>* dc = reinterpret_cast<const CompT<T>*>(smem + L.dc);
+      const MemT<T>* dm = reinterpret_cast<const MemT<T>*>(smem + L.dm);
+      double s[5];
+      if constexpr (MIXED) {
+        float xh[1], xl[1], yh[1], yl[1];
+        split_ff(tx, xh[0], xl[0]);
+        split_ff(ty, yh[0], yl[0]);
+        ff acc[5][1];
+        for (int v = 0; v < 5; ++v) acc[v][0] = ff_zero();
+        accumulate_mixed<1>(dc, MP.nc[j], dm, MP.nm[j], 0, MP.nc[j] + MP.nm[j], chunk, xh, xl, yh,
+                            yl, acc);
+        for (int v = 0; v < 5; ++v) s[v] = ff_to_double(acc[v][0]);
+      } else {
+        for (int v = 0; v < 5; ++v) s[v] = 0.0;
+        accumulate_fp64(dc, MP.nc[j], dm, MP.nm[j], 0, MP.nc[j] + MP.nm[j], tx, ty, s);
+      }
+      al[j][0] = s[0];
+      al[j][1] = s[1];
+      // Psi_j A_j with Psi = [[pxx, pxy], [pxy, pyy]]
+      PA[j][0] = s[2] * a00 + s[4] * a10;
+      PA[j][1] = s[2] * a01 + s[4] * a11;
+      PA[j][2] = s[4] * a00 + s[3] * a10;
+      PA[j][3] = s[4] * a01 + s[3] * a11;
+    }
+    double bx = t1x, by = t1y, A00 = 1, A01 = 0, A10 = 0, A11 = 1;
+    for (int j = 0; j < MP.np; ++j) {
+      double r = MP.rs[j];
+      bx -= r * al[j][0];
+      by -= r * al[j][1];
+      A00 -= r * PA[j][0]; A01 -= r * PA[j][1];
+      A10 -= r * PA[j][2]; A11 -= r * PA[j][3];
+    }
+    if (io.beta) {
+      io.beta[2 * p] = bx;
+      io.beta[2 * p + 1] = by;
+    }
+    if (io.A) {
+      io.A[4 * p] = A00; io.A[4 * p + 1] = A01;
+      io.A[4 * p + 2] = A10; io.A[4 * p + 3] = A11;
+    }
+  }
+}
+
+// Fills the plane part of MultiPlaneArgs and returns the shared-memory bytes needed.
+template <class T>
+lf_status fill_planes(const lf_plane* planes, int np, MultiPlaneArgs& A, uint32_t& total);
+
+lf_status check_plane(const lf_plane* pl);
+
+template <class T>
+lf_status fill_planes(const lf_plane* planes, int np, MultiPlaneArgs& A, uint32_t& total) {
+  A.np = np;
+  uint32_t base = 16;
+  for (int j = 0; j < np; ++j) {
+    LF_TRY(check_plane(&planes[j]));
+    A.comp[j] = planes[j].comp;
+    A.mem[j] = planes[j].mem;
+    A.nc[j] = planes[j].n_comp;
+    A.nm[j] = planes[j].n_mem;
+    A.sc[j] = planes[j].scaling;
+    A.base[j] = base;
+    base = plane_layout<T>(planes[j].n_comp, planes[j].n_mem, base).total;
+  }
+  total = base;
+  if (total > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "planes too large for shared memory");
+  return LF_OK;
+}
+
+}  // namespace lf
+
+using namespace lf;
+
+extern "C" lf_status lf_trace_multiplane(const lf_plane* planes, int32_t n_planes,
+                                         const double* ratios, const double* theta, int32_t n,
+                                         const lf_grid* grid, int32_t precision, double* beta,
+                                         double* A, void* stream) {
+  if (!planes) return fail(LF_EINVAL, "planes is NULL");
+  if (n_planes < 1 || n_planes > LF_MAX_PLANES) return fail(LF_EINVAL, "need 1 <= n_planes <= 8");
+  if (!ratios) return fail(LF_EINVAL, "ratios is NULL");
+  if (precision != LF_FP64 && precision != LF_MIXED) return fail(LF_EINVAL, "unknown precision");
+  RayIO io{};
+  if (theta) {
+    if (n < 0) return fail(LF_EINVAL, "n must be >= 0");
+    io.pts = theta;
+    io.n = n;
+  } else {
+    if (!grid || grid->nx <= 0 || grid->ny <= 0) return fail(LF_EINVAL, "need theta or a grid");
+    io.x0 = grid->x0; io.y0 = grid->y0; io.dx = grid->dx; io.dy = grid->dy; io.nx = grid->nx;
+    io.n = (long long)grid->nx * grid->ny;
+  }
+  io.beta = beta;
+  io.A = A;
+  MultiPlaneArgs MP{};
+  for (int i = 0; i < n_planes; ++i)
+    for (int j = 0; j < n_planes; ++j) {
+      double v = ratios[i * n_planes + j];
+      if (j > i && !(std::isfinite(v) && v >= 0.0)) return fail(LF_EINVAL, "invalid ratio r[%d][%d]", i, j);
+      MP.r[i][j] = j > i ? v : 0.0;
+    }
+  for (int j = 0; j < n_planes; ++j) {
+    double v = ratios[n_planes * n_planes + j];
+    if (!(std::isfinite(v) && v >= 0.0)) return fail(LF_EINVAL, "invalid source ratio %d", j);
+    MP.rs[j] = v;
+  }
+  uint32_t total = 0;
+  if (precision == LF_MIXED) LF_TRY(fill_planes<float>(planes, n_planes, MP, total));
+  else LF_TRY(fill_planes<double>(planes, n_planes, MP, total));
+  if (io.n == 0) return LF_OK;
+  int dev = 0, nsm = 0, occ = 0;
+  LF_CUDA(cudaGetDevice(&dev));
+  LF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int block = 256;
+  cudaStream_t s = (cudaStream_t)stream;
+  long long tiles = (io.n + block - 1) / block;
+  if (precision == LF_MIXED) {
+    LF_CUDA(cudaFuncSetAttribute(k_trace<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total));
+    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<true>, block, total));
+    long long g = std::min<long long>(tiles, (long long)nsm * std::max(occ, 1));
+    k_trace<true><<<(unsigned)g, block, total, s>>>(MP, io, g_member_chunk);
+  } else {
+    LF_CUDA(cudaFuncSetAttribute(k_trace<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total));
+    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<false>, block, total));
+    long long g = std::min<long long>(tiles, (long long)nsm * std::max(occ, 1));
+    k_trace<false><<<(unsigned)g, block, total, s>>>(MP, io, g_member_chunk);
+  }
+  LF_CUDA(cudaGetLastError());
+  return LF_OK;
+}
