@@ -1,0 +1,367 @@
+"""Benchmark of the batched lens-equation path on B300.
+
+Headline (one JSON line on rank 0): lens evals/s (positions x components per second) of
+lf_jacobian_grid in LF_MIXED precision on the cluster grid-map workload (2 elliptical dPIE
+halos + 300 pseudo-Jaffe members on a 4096 x 4096 grid at 0.04", alpha, kappa, gamma, mu
+at z_s = 9).  One step = one call over the whole grid (component preparation, per-pixel
+sums, lens-map Jacobian and magnification in FP64).
+
+Secondary measurements in the same line: the plain FP64 comparator on the same grid, the
+batched source-plane chi^2 (4096 samples x 200 images, mixed and FP64), its gradient
+(16 clusters, 22 parameters, 1024 samples), and the 3-plane ray trace (2048^2 rays).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores (bounded sample of the same
+workload).  Under torchrun each rank runs the same workload (replicas; weak scaling) and
+rank 0 reports the total over ranks divided by the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "lens evals/s (samples×positions×components)"
+UNIT = "lens evals/s"
+WORKLOAD = ("cluster_dpie302_grid4096: 2 elliptical dPIE halos + 300 PJE members, "
+            "4096x4096 grid at 0.04\", alpha/kappa/gamma/mu at z_s=9")
+FP32_INSTR_PER_EVAL = 35      # FP32-pipe instructions of one member evaluation
+XU_INSTR_PER_EVAL = 4         # MUFU instructions of one member evaluation
+FP32_LANES_PER_SM, XU_LANES_PER_SM = 128, 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=4096)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reference_arm(args):
+    """FP64 CPU oracle on the host cores: a seeded row band of the same grid workload."""
+    import torch
+    world, rank, _ = dist_init()
+    if rank != 0:
+        return
+    from oracle import cosmology as cz
+    from oracle import lensing as OL
+    from oracle import model as OM
+    from paper_2609_08649_b300 import workloads as W
+    torch.set_num_threads(os.cpu_count() or 1)
+    wl = W.cluster_c1(args.grid)
+    pl = OM.build_planes(wl)[0]
+    a = cz.a_dis(0.5, 9.0)
+    g = wl.grid
+    rows = 8
+    xs = g.x0 + g.dx * np.arange(g.nx)
+    times = []
+    n_comp = len(pl.kind) + pl.n_members
+    for step in range(args.warmup + args.steps):
+        j0 = (step * 131) % (g.ny - rows)
+        ys = g.y0 + g.dy * np.arange(j0, j0 + rows)
+        X, Y = np.meshgrid(xs, ys)
+        t0 = time.perf_counter()
+        out = OL.plane_sum(pl, torch.tensor(X.ravel())[None], torch.tensor(Y.ravel())[None])
+        OL.jacobian_maps(*out, a)
+        t = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(t)
+    evals = rows * g.nx * n_comp
+    v = evals / statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64 CPU oracle",
+                       "sample": f"{rows} of {g.ny} grid rows per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(),
+                             "kind": "oracle", "sample": f"{rows} grid rows x {g.nx} px x {n_comp} components per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(wl, seconds_target=15.0):
+    """The oracle as it stands on the host cores, on a bounded row band of the grid."""
+    import torch
+    from oracle import cosmology as cz
+    from oracle import lensing as OL
+    from oracle import model as OM
+    torch.set_num_threads(os.cpu_count() or 1)
+    pl = OM.build_planes(wl)[0]
+    a = cz.a_dis(0.5, 9.0)
+    g = wl.grid
+    xs = g.x0 + g.dx * np.arange(g.nx)
+    n_comp = len(pl.kind) + pl.n_members
+    done, t_tot, rows = 0, 0.0, 4
+    j0 = g.ny // 3
+    while t_tot < seconds_target and done < 256:
+        ys = g.y0 + g.dy * np.arange(j0 + done, j0 + done + rows)
+        X, Y = np.meshgrid(xs, ys)
+        t0 = time.perf_counter()
+        out = OL.plane_sum(pl, torch.tensor(X.ravel())[None], torch.tensor(Y.ravel())[None])
+        OL.jacobian_maps(*out, a)
+        t_tot += time.perf_counter() - t0
+        done += rows
+    return {"value": done * g.nx * n_comp / t_tot, "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"{done} grid rows x {g.nx} px x {n_comp} components ({t_tot:.1f} s, FP64 torch CPU)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2609_08649_b300 import api
+    from paper_2609_08649_b300 import model as PM
+    from paper_2609_08649_b300 import workloads as W
+
+    wl = W.cluster_c1(args.grid)
+    g = wl.grid
+    dp = PM.device_planes(wl)[0]
+    a = PM.adis(wl.cosmo, 0.5, 9.0)
+    n_pix = g.nx * g.ny
+    n_comp = len(dp.comp_host) + len(dp.mem_host)
+    evals = n_pix * n_comp
+    outs = {k: torch.empty(n_pix, dtype=torch.float32 if k in ("kappa", "g1", "g2") else torch.float64,
+                           device="cuda") for k in api.ALL_OUTPUTS}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    import ctypes as C
+    from paper_2609_08649_b300 import _lib as L
+    ps, gs = dp.c_struct(), PM.grid_struct(g)
+    stream = torch.cuda.current_stream()
+
+    def step(prec=L.LF_MIXED):
+        L.check(L.lib.lf_jacobian_grid(C.byref(ps), C.byref(gs), a, prec,
+                                       *[C.c_void_p(outs[k].data_ptr()) for k in api.ALL_OUTPUTS],
+                                       C.c_void_p(stream.cuda_stream)))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_region = time.perf_counter()
+    for e0, e1 in evs:
+        flush.fill_(1)                       # L2 flush between steps, outside the step events
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    t_region = time.perf_counter() - t_region
+    clk = clocks.stop()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t)
+    value = world * evals / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers: tables host->device, maps device->host
+    host_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in outs.items()}
+    comp_h = torch.from_numpy(dp.comp_host.view(np.uint8).copy()).pin_memory()
+    mem_h = torch.from_numpy(dp.mem_host.view(np.uint8).copy()).pin_memory()
+    h2d = comp_h.numel() + mem_h.numel()
+    d2h = sum(v.numel() * v.element_size() for v in outs.values())
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dp.comp_dev.copy_(comp_h, non_blocking=True)
+        dp.mem_dev.copy_(mem_h, non_blocking=True)
+        step()
+        for k in outs:
+            host_out[k].copy_(outs[k], non_blocking=True)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e = {"value": world * evals / (statistics.mean(e2e_ms) * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "ms_per_step": statistics.mean(e2e_ms)}
+
+    # roofline of the dominant kernel (the per-pixel sum): FP32 and XU issue against peak
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_max = (clk.get("sm_max_mhz") or 2032.0) * 1e6
+    fp32_peak = nsm * FP32_LANES_PER_SM * sm_max / 1e12
+    xu_peak = nsm * XU_LANES_PER_SM * sm_max / 1e12
+    fp32_ach = evals * FP32_INSTR_PER_EVAL / (ms * 1e-3) / 1e12
+    xu_ach = evals * XU_INSTR_PER_EVAL / (ms * 1e-3) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "k_map_mixed_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+        except ValueError:
+            traffic = None
+    roofline = {"bound": "alu", "achieved": fp32_ach, "peak": fp32_peak, "unit": "Tinst/s (FP32 pipe)",
+                "frac": fp32_ach / fp32_peak, "traffic": traffic,
+                "xu": {"achieved": xu_ach, "peak": xu_peak, "frac": xu_ach / xu_peak},
+                "hbm_achieved_gbs": d2h / (ms * 1e-3) / 1e9,
+                "peak_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max/1e6:.0f} MHz (max SM clock)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "mixed (FP32 closed forms, float-float sums, FP64 det/mu)",
+                       "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "l2": "256 MiB buffer written between timed steps, outside the step events; "
+                             "each step writes 604 MB of maps (> 126 MB L2)",
+                       "region_s": t_region},
+            "e2e": e2e, "gpu_launches": args.steps, "clocks": clk, "roofline": roofline}
+
+    if rank == 0 and not args.no_secondary:
+        line["secondary"] = secondary(torch, api, PM, W, L, C, step, ms, evals)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def _time(torch, fn, reps=3, warm=1):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def secondary(torch, api, PM, W, L, C, step, ms_mixed, evals):
+    out = {}
+    ms64 = _time(torch, lambda: step(L.LF_FP64), reps=2)
+    out["grid_fp64"] = {"ms": ms64, "lens_evals_per_s": evals / (ms64 * 1e-3),
+                        "mixed_speedup": ms64 / ms_mixed}
+    # batched chi^2, 4096 samples x 200 images x 302 components
+    wl = W.cluster_c2()
+    cat = W.load_catalogue("cluster_200")
+    th = torch.tensor(W.sample_thetas(wl, wl.seed), device="cuda")
+    ev = th.shape[0] * len(cat.theta_obs) * (2 + 1 + 300)
+    res = {}
+    for prec in ("mixed", "fp64"):
+        plan = api.Plan([PM.cluster_input(wl, cat)], th.shape[0], prec, flags=api.FLAG_GRAPH | api.FLAG_AUTOTUNE)
+        t = _time(torch, lambda: plan.chi2(th), reps=5 if prec == "mixed" else 2)
+        res[prec] = {"ms": t, "chi2_per_s": th.shape[0] / (t * 1e-3), "lens_evals_per_s": ev / (t * 1e-3),
+                     "tile": plan.info()}
+        plan.close()
+    res["mixed_speedup"] = res["fp64"]["ms"] / res["mixed"]["ms"]
+    out["chi2_4096x200"] = res
+    # gradient over 16 clusters
+    try:
+        wls = W.multicluster_c4()
+        cats = [W.load_catalogue(f"multicluster_{c:02d}") for c in range(len(wls))]
+        ths = np.concatenate([W.sample_thetas(w, w.seed) for w in wls])
+        th4 = torch.tensor(ths, device="cuda")
+        ev4 = sum(w.n_samples * len(c.theta_obs) * (3 + len(w.planes[0].members.x)) for w, c in zip(wls, cats))
+        res = {}
+        for prec in ("mixed", "fp64"):
+            plan = api.Plan([PM.cluster_input(w, c) for w, c in zip(wls, cats)], th4.shape[0], prec,
+                            flags=api.FLAG_GRAPH)
+            t = _time(torch, lambda: plan.chi2_grad(th4), reps=3 if prec == "mixed" else 1)
+            tc = _time(torch, lambda: plan.chi2(th4), reps=3 if prec == "mixed" else 1)
+            res[prec] = {"grad_ms": t, "chi2_ms": tc, "grad_samples_per_s": th4.shape[0] / (t * 1e-3),
+                         "lens_evals_per_s_chi2": ev4 / (tc * 1e-3)}
+            plan.close()
+        res["mixed_speedup_grad"] = res["fp64"]["grad_ms"] / res["mixed"]["grad_ms"]
+        out["grad_16clusters_1024"] = res
+    except FileNotFoundError as e:
+        out["grad_16clusters_1024"] = {"skipped": str(e)}
+    # 3-plane trace of a 2048^2 grid
+    wl3 = W.multiplane_c3()
+    planes = PM.device_planes(wl3)
+    r = PM.multiplane_ratios(wl3.cosmo, [p.z for p in wl3.planes], wl3.z_s)
+    res = {}
+    nrays = wl3.grid.nx * wl3.grid.ny
+    ncomp = sum(len(p.comp_host) + len(p.mem_host) for p in planes)
+    for prec in ("mixed", "fp64"):
+        t = _time(torch, lambda: api.trace_multiplane(planes, r, grid=wl3.grid, precision=prec), reps=2)
+        res[prec] = {"ms": t, "rays_per_s": nrays / (t * 1e-3), "lens_evals_per_s": nrays * ncomp / (t * 1e-3)}
+    res["mixed_speedup"] = res["fp64"]["ms"] / res["mixed"]["ms"]
+    out["trace_3plane_2048"] = res
+    api.device_error()
+    return out
+
+
+if __name__ == "__main__":
+    main()

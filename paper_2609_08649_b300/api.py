@@ -89,3 +89,110 @@ def trace_multiplane(planes: Sequence[DevicePlane], ratios: np.ndarray, theta=No
 
 def device_error():
     L.check(L.lib.lf_device_error(_stream()))
+
+
+# ------------------------------------------------------------------ chi^2 plans -----
+class ClusterInput:
+    """Everything one cluster of a plan needs, in lensing units (host arrays)."""
+
+    def __init__(self, planes, arcsec_per_kpc, theta_obs, sinv, fam_off, fam_ratio,
+                 p_comp, p_field, p_xform, ratios=None):
+        self.planes = planes
+        self.apk = np.ascontiguousarray(arcsec_per_kpc, dtype=np.float64)
+        self.theta_obs = np.ascontiguousarray(theta_obs, dtype=np.float64)
+        self.sinv = np.ascontiguousarray(sinv, dtype=np.float64)
+        self.fam_off = np.ascontiguousarray(fam_off, dtype=np.int32)
+        self.fam_ratio = np.ascontiguousarray(fam_ratio, dtype=np.float64)
+        self.p_comp = np.ascontiguousarray(p_comp, dtype=np.int32)
+        self.p_field = np.ascontiguousarray(p_field, dtype=np.int32)
+        self.p_xform = np.ascontiguousarray(p_xform, dtype=np.int32)
+        n = len(planes)
+        self.ratios = (np.ascontiguousarray(ratios, dtype=np.float64).reshape(-1)[: n * n]
+                       if ratios is not None else None)
+
+    def c_struct(self):
+        self._planes_arr = (L.lf_plane * len(self.planes))(*[p.c_struct() for p in self.planes])
+        c = L.lf_cluster()
+        c.n_planes = len(self.planes)
+        c.planes = C.cast(self._planes_arr, C.c_void_p)
+        c.ratios = self.ratios.ctypes.data_as(C.c_void_p) if self.ratios is not None else None
+        c.arcsec_per_kpc = self.apk.ctypes.data_as(C.c_void_p)
+        im = L.lf_images()
+        im.n_img = len(self.theta_obs)
+        im.n_fam = len(self.fam_off) - 1
+        im.theta_obs = self.theta_obs.ctypes.data_as(C.c_void_p)
+        im.sinv = self.sinv.ctypes.data_as(C.c_void_p)
+        im.fam_off = self.fam_off.ctypes.data_as(C.c_void_p)
+        im.fam_ratio = self.fam_ratio.ctypes.data_as(C.c_void_p)
+        c.images = im
+        c.P = len(self.p_comp)
+        c.p_comp = self.p_comp.ctypes.data_as(C.c_void_p)
+        c.p_field = self.p_field.ctypes.data_as(C.c_void_p)
+        c.p_xform = self.p_xform.ctypes.data_as(C.c_void_p)
+        return c
+
+
+FLAG_GRAPH, FLAG_AUTOTUNE = 1, 2
+
+
+class Plan:
+    """lf_plan_create / lf_chi2_batch / lf_chi2_grad_batch / lf_plan_destroy."""
+
+    def __init__(self, clusters: Sequence[ClusterInput], max_samples, precision="mixed", flags=0):
+        arr = (L.lf_cluster * len(clusters))(*[c.c_struct() for c in clusters])
+        self._keep = clusters
+        self.handle = C.c_void_p()
+        self.n_clusters = len(clusters)
+        self.P = len(clusters[0].p_comp)
+        L.check(L.lib.lf_plan_create(C.byref(self.handle), arr, len(clusters), int(max_samples),
+                                     _prec(precision), int(flags)))
+
+    def chi2(self, theta: torch.Tensor, out: Optional[torch.Tensor] = None):
+        theta = theta.contiguous()
+        S = theta.shape[0]
+        out = torch.empty(S, dtype=torch.float64, device="cuda") if out is None else out
+        L.check(L.lib.lf_chi2_batch(self.handle, _ptr(theta), S, _ptr(out), _stream()))
+        return out
+
+    def chi2_grad(self, theta: torch.Tensor, out=None, grad=None):
+        theta = theta.contiguous()
+        S = theta.shape[0]
+        out = torch.empty(S, dtype=torch.float64, device="cuda") if out is None else out
+        grad = torch.empty(S, self.P, dtype=torch.float64, device="cuda") if grad is None else grad
+        L.check(L.lib.lf_chi2_grad_batch(self.handle, _ptr(theta), S, _ptr(out), _ptr(grad), _stream()))
+        return out, grad
+
+    def info(self):
+        ks, blk, g = C.c_int32(), C.c_int32(), C.c_int32()
+        L.check(L.lib.lf_plan_info(self.handle, C.byref(ks), C.byref(blk), C.byref(g)))
+        return {"kslices": ks.value, "block": blk.value, "graph": bool(g.value)}
+
+    def close(self):
+        if self.handle:
+            L.lib.lf_plan_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Chi2Function(torch.autograd.Function):
+    """chi^2 per sample with d chi^2 / d theta from the library's adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, theta, plan):
+        chi2, grad = plan.chi2_grad(theta.detach())
+        ctx.save_for_backward(grad)
+        return chi2
+
+    @staticmethod
+    def backward(ctx, g_out):
+        (grad,) = ctx.saved_tensors
+        return g_out[:, None] * grad, None
+
+
+def chi2(theta, plan):
+    return Chi2Function.apply(theta, plan)

@@ -1,20 +1,979 @@
-// Source-plane chi^2 plans (Eq. chi2_src, Sec. 3.1) -- under construction.
+// Batched source-plane chi^2 (Eq. chi2_src with the analytic source of Sec. 3.1) and its
+// parameter gradient, for thousands of parameter samples and many clusters per launch.
+//
+// One persistent launch: every block takes work items (one parameter sample of one
+// cluster) from an atomic counter.  Items are ordered cluster by cluster, most expensive
+// cluster first, so a block re-stages a cluster's tables (bulk copy into shared memory)
+// only when the cluster changes.  Per item the block
+//   A1  writes the sample's parameters into the component table (transforms km/s -> b,
+//       degrees -> radians, kpc -> arcsec) and re-derives the members from the scaling
+//       relations of Eq. scaling when those are sampled;
+//   A3-A4 sums alpha and psi_ij at every observed image: tasks (image, component slice)
+//       with KS slices per image reduced by warp shuffles;
+//   A5-A7 forms beta_i = theta_i - a_f alpha_i, A_i = I - a_f Psi_i (or the multi-plane
+//       recursion of Sec. 2.2), mu_i = A_i^-1 and M_i = mu_i^T S_i^-1 mu_i in FP64;
+//   A8  per family G = sum M_i, g = sum M_i beta_i, beta_model = G^-1 g and
+//       chi^2_f = sum (beta_i - beta_model)^T M_i (beta_i - beta_model), then a block
+//       reduction to chi^2 of the sample.
+// The gradient (A9) holds beta_model at its optimum (d chi^2 / d beta_model = 0), so with
+// d_i = beta_i - beta_model, w = M_i d_i and z = mu_i d_i,
+//   d chi^2 = sum_i 2 a_f [ -w^T d alpha_i + w^T d Psi_i z ],
+// i.e. cotangents alpha_bar = -2 a w and Psi_bar = 2 a sym(w z^T).  A second pass over the
+// same (image, slice) tasks contracts them with the derivative of each component's
+// (alpha, Psi) with respect to its own fields, obtained by forward-mode dual numbers, and
+// with the member scaling-relation chain rule.
 #include "lf_internal.h"
+#include "lf_eval.cuh"
+#include "lf_dual.cuh"
 
-struct lf_plan { int dummy; };
+namespace lf {
 
-extern "C" lf_status lf_plan_create(lf_plan** out, const lf_cluster*, int32_t, int32_t, int32_t,
-                                    int32_t) {
-  if (out) *out = nullptr;
-  return lf::fail(LF_EUNSUPPORTED, "chi^2 plans are not built yet");
+constexpr int LF_MAX_P = 64;
+constexpr int LF_MAX_FREE = 16;
+constexpr int LF_MAX_IMG = 2048;
+constexpr int LF_HDR = 512;          // shared header: barrier, item index, reduction scratch
+constexpr double LF_C_KMS = 299792.458;
+constexpr double LF_ARCSEC_PER_RAD = 206264.80624709636;
+constexpr double LF_PI = 3.14159265358979323846;
+
+struct MemPreF { float xh, xl, yh, yl, fb, fs, fa, lnl; };
+struct MemPreD { double x, y, fb, fs, fa, lnl, pad0, pad1; };
+
+struct PlaneDesc {
+  const lf_comp* comp;
+  const void* mpre;
+  int nc, nm;
+  lf_scaling sc;
+  double apk;
+  uint32_t off_rawc, off_mpre, off_dc, off_dm;
+};
+
+struct ClusterDesc {
+  int np;
+  PlaneDesc pl[LF_MAX_PLANES];
+  double r[LF_MAX_PLANES][LF_MAX_PLANES];
+  int n_img, n_fam;
+  const double* theta;
+  const double* sinv;
+  const int* fam_off;
+  const int* img_fam;
+  const double* fam_ratio;
+  int P;
+  int n_free;
+  int free_plane[LF_MAX_FREE], free_comp[LF_MAX_FREE];
+  int free_p[LF_MAX_FREE][7];
+  int scal_plane;
+  int scal_free;
+  int scal_p[6];
+  int p_xform[LF_MAX_P];
+  int p_plane[LF_MAX_P];
+  int ks;
+  int img_stride;                  // doubles per image record
+  uint32_t off_img, off_fam, off_par, off_free, smem;
+};
+
+// ------------------------------------------------------------------ transforms -----
+__host__ __device__ inline double apply_xform(int xf, double v, double apk) {
+  switch (xf) {
+    case LF_XF_VDISP: { double r = v / LF_C_KMS; return 4.0 * LF_PI * r * r * LF_ARCSEC_PER_RAD; }
+    case LF_XF_DEG: return v * (LF_PI / 180.0);
+    case LF_XF_KPC: return v * apk;
+    default: return v;
+  }
 }
-extern "C" lf_status lf_chi2_batch(lf_plan*, const double*, int32_t, double*, void*) {
-  return lf::fail(LF_EUNSUPPORTED, "chi^2 plans are not built yet");
+__host__ __device__ inline double xform_deriv(int xf, double v, double apk) {
+  switch (xf) {
+    case LF_XF_VDISP: return 8.0 * LF_PI * v / (LF_C_KMS * LF_C_KMS) * LF_ARCSEC_PER_RAD;
+    case LF_XF_DEG: return LF_PI / 180.0;
+    case LF_XF_KPC: return apk;
+    default: return 1.0;
+  }
 }
-extern "C" lf_status lf_chi2_grad_batch(lf_plan*, const double*, int32_t, double*, double*, void*) {
-  return lf::fail(LF_EUNSUPPORTED, "chi^2 plans are not built yet");
+
+
+// The scaling relation of the sample: base values with the sampled slots overwritten.
+__device__ __forceinline__ void sample_scaling(const ClusterDesc& C, const double* th, lf_scaling& sc) {
+  const double apk = C.pl[C.scal_plane].apk;
+  for (int k = 0; k < 6; ++k) {
+    const int p = C.scal_p[k];
+    if (p < 0) continue;
+    const double v = apply_xform(C.p_xform[p], th[p], apk);
+    if (k == LF_S_BSTAR) sc.b_star = v;
+    else if (k == LF_S_CORESTAR) sc.core_star = v;
+    else if (k == LF_S_CUTSTAR) sc.cut_star = v;
+    else if (k == LF_S_LAM) sc.lam = v;
+    else if (k == LF_S_BETA) sc.beta = v;
+    else sc.alpha = v;
+  }
 }
-extern "C" lf_status lf_plan_destroy(lf_plan*) { return LF_OK; }
-extern "C" lf_status lf_plan_info(const lf_plan*, int32_t*, int32_t*, int32_t*) {
-  return lf::fail(LF_EUNSUPPORTED, "chi^2 plans are not built yet");
+
+__device__ __forceinline__ void set_field(lf_comp& c, int f, double v) {
+  switch (f) {
+    case LF_F_X: c.x = v; break;
+    case LF_F_Y: c.y = v; break;
+    case LF_F_B: c.b = v; break;
+    case LF_F_EPS: c.eps = v; break;
+    case LF_F_PA: c.pa = v; break;
+    case LF_F_CORE: c.core = v; break;
+    default: c.cut = v; break;
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  const int nw = blockDim.x >> 5;
+  for (int i = 0; i < nw; ++i) r += scratch[i];
+  return r;
+}
+
+// ------------------------------------------------------- dual component evaluation -
+// Unit-strength (alpha, Psi) of one explicit component and its derivatives with respect to
+// (x, y, eps, pa, core, cut) in tangent slots 0..5.
+template <class T>
+__device__ void comp_dual(const lf_comp& rc, double px, double py, Out5<Dual<T, 6>>& o) {
+  typedef Dual<T, 6> DT;
+  // offsets taken in FP64; d(dx)/dx_c = -1, d(dy)/dy_c = -1
+  DT dx = DT::cst((T)(px - rc.x)), dy = DT::cst((T)(py - rc.y));
+  dx.d[0] = (T)-1;
+  dy.d[1] = (T)-1;
+  DT pa = DT::var((T)rc.pa, 3);
+  if (rc.kind == LF_SHEAR) {
+    DT two = DT::cst((T)2);
+    DT c2 = lf_cos(two * pa), s2 = lf_sin(two * pa);
+    o.ax = c2 * dx + s2 * dy;
+    o.ay = s2 * dx - c2 * dy;
+    o.pxx = c2; o.pyy = -c2; o.pxy = s2;
+    return;
+  }
+  DT core = DT::var((T)rc.core, 4);
+  if (rc.kind == LF_NFW) {
+    nfw_sph(dx, dy, DT::cst((T)1), lf_rcp(core), o);
+    return;
+  }
+  // elliptical form also at eps ~ 0, so that d/d eps exists there
+  double epsv = rc.eps < 1e-6 ? 1e-6 : rc.eps;
+  DT eps = DT::var((T)epsv, 2);
+  DT one = DT::cst((T)1);
+  DT q = (one - eps) / (one + eps);
+  DT q2 = q * q;
+  DT e = lf_sqrt((one - q) * (one + q));
+  DT qe = q / e;
+  DT c = lf_cos(pa), sn = lf_sin(pa);
+  DT u = c * dx + sn * dy;
+  DT v = c * dy - sn * dx;
+  DT au, av, puu, pvv, puv;
+  DT s2 = core * core;
+  sie_uv(u, v, q, q2, e, qe, core, s2, q2 * core, (one + q2) * s2, false, au, av, puu, pvv, puv);
+  if (rc.kind == LF_DPIE) {
+    DT cut = DT::var((T)rc.cut, 5);
+    DT c2 = cut * cut;
+    DT bu, bv, quu, qvv, quv;
+    sie_uv(u, v, q, q2, e, qe, cut, c2, q2 * cut, (one + q2) * c2, false, bu, bv, quu, qvv, quv);
+    au = au - bu; av = av - bv; puu = puu - quu; pvv = pvv - qvv; puv = puv - quv;
+  }
+  rotate_back(c, sn, au, av, puu, pvv, puv, o);
+}
+
+template <class T, int N>
+__device__ __forceinline__ T contract(const Out5<Dual<T, N>>& o, const T* cot, int slot) {
+  if (slot < 0)
+    return cot[0] * o.ax.v + cot[1] * o.ay.v + cot[2] * o.pxx.v + cot[3] * o.pyy.v + cot[4] * o.pxy.v;
+  return cot[0] * o.ax.d[slot] + cot[1] * o.ay.d[slot] + cot[2] * o.pxx.d[slot] +
+         cot[3] * o.pyy.d[slot] + cot[4] * o.pxy.d[slot];
+}
+
+// ------------------------------------------------------------------ the kernel -----
+template <bool MIXED, bool GRAD>
+__global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cds,
+                                              const int* __restrict__ corder, int spc, int S,
+                                              const double* __restrict__ theta, double* chi2,
+                                              double* grad, int* counter, int chunk) {
+  typedef typename std::conditional<MIXED, float, double>::type T;
+  typedef typename std::conditional<MIXED, MemPreF, MemPreD>::type MemPre;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  int* s_item = reinterpret_cast<int*>(smem + 8);
+  double* scratch = reinterpret_cast<double*>(smem + 16);   // 32 doubles
+  const int tid = threadIdx.x;
+  if (tid == 0) mbar_init(bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  int cur = -1;
+
+  for (;;) {
+    if (tid == 0) *s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int w = *s_item;
+    __syncthreads();
+    if (w >= S) break;
+    const int c = corder[w / spc];
+    const int s = c * spc + (w % spc);
+    const ClusterDesc& C = cds[c];
+    double* th = reinterpret_cast<double*>(smem + C.off_par);
+    double* gacc = th + C.P;
+    lf_comp* fraw = reinterpret_cast<lf_comp*>(smem + C.off_free);
+    double* img = reinterpret_cast<double*>(smem + C.off_img);
+    double* fam = reinterpret_cast<double*>(smem + C.off_fam);
+    for (int p = tid; p < C.P; p += blockDim.x) {
+      th[p] = theta[(size_t)s * C.P + p];
+      if (GRAD) gacc[p] = 0.0;
+    }
+    const bool fresh = (c != cur);
+    if (fresh) {
+      bool ok = true;
+      for (int j = 0; j < C.np && ok; ++j) {
+        const PlaneDesc& P = C.pl[j];
+        if (P.nc > 0) {
+          ok = stage_to_smem(smem + P.off_rawc, P.comp, (uint32_t)P.nc * 64u, bar, phase & 1u);
+          ++phase;
+        }
+        if (ok && P.nm > 0) {
+          ok = stage_to_smem(smem + P.off_mpre, P.mpre, (uint32_t)(P.nm * sizeof(MemPre)), bar,
+                             phase & 1u);
+          ++phase;
+        }
+      }
+      if (!ok) return;
+      for (int j = 0; j < C.np; ++j) {
+        const PlaneDesc& P = C.pl[j];
+        const lf_comp* rawc = reinterpret_cast<const lf_comp*>(smem + P.off_rawc);
+        CompT<T>* dc = reinterpret_cast<CompT<T>*>(smem + P.off_dc);
+        for (int i = tid; i < P.nc; i += blockDim.x) digest_one_comp<T>(rawc[i], dc[i]);
+      }
+      cur = c;
+    }
+    __syncthreads();
+
+    // ---- A1: this sample's parameters into the tables
+    for (int f = tid; f < C.n_free; f += blockDim.x) {
+      const PlaneDesc& P = C.pl[C.free_plane[f]];
+      const lf_comp* rawc = reinterpret_cast<const lf_comp*>(smem + P.off_rawc);
+      lf_comp rc = rawc[C.free_comp[f]];
+      for (int fld = 0; fld < 7; ++fld) {
+        int p = C.free_p[f][fld];
+        if (p >= 0) set_field(rc, fld, apply_xform(C.p_xform[p], th[p], P.apk));
+      }
+      fraw[f] = rc;
+      digest_one_comp<T>(rc, reinterpret_cast<CompT<T>*>(smem + P.off_dc)[C.free_comp[f]]);
+    }
+    for (int j = 0; j < C.np; ++j) {
+      const PlaneDesc& P = C.pl[j];
+      const bool sampled = (j == C.scal_plane) && C.scal_free;
+      if (P.nm == 0 || !(fresh || sampled)) continue;
+      lf_scaling sc = P.sc;
+      if (sampled) sample_scaling(C, th, sc);
+      const bool lam_free = sampled && C.scal_p[LF_S_LAM] >= 0;
+      const bool beta_free = sampled && C.scal_p[LF_S_BETA] >= 0;
+      const bool alpha_free = sampled && C.scal_p[LF_S_ALPHA] >= 0;
+      const MemPre* mp = reinterpret_cast<const MemPre*>(smem + P.off_mpre);
+      MemT<T>* dm = reinterpret_cast<MemT<T>*>(smem + P.off_dm);
+      for (int i = tid; i < P.nm; i += blockDim.x) {
+        const MemPre& m = mp[i];
+        T fb = lam_free ? (T)exp((T)(2.0 * sc.lam) * (T)m.lnl) : (T)m.fb;
+        T fs = beta_free ? (T)exp((T)sc.beta * (T)m.lnl) : (T)m.fs;
+        T fa = alpha_free ? (T)exp((T)sc.alpha * (T)m.lnl) : (T)m.fa;
+        MemT<T> d;
+        if constexpr (MIXED) {
+          d.xh = m.xh; d.xl = m.xl; d.yh = m.yh; d.yl = m.yl;
+        } else {
+          d.xh = m.x; d.xl = 0; d.yh = m.y; d.yl = 0;
+        }
+        d.b = (T)sc.b_star * fb;
+        d.s = (T)sc.core_star * fs;
+        d.a = (T)sc.cut_star * fa;
+        d.fb = fb;
+        d.fs = fs;
+        d.s2 = d.s * d.s;
+        d.a2 = d.a * d.a;
+        d.loglr = (T)m.lnl;
+        dm[i] = d;
+      }
+    }
+    __syncthreads();
+
+    // ---- A3-A6: alpha and Psi at every image, plane by plane
+    const int n_img = C.n_img, KS = C.ks, IS = C.img_stride;
+    const int ntask = n_img * KS;
+    for (int j = 0; j < C.np; ++j) {
+      const PlaneDesc& P = C.pl[j];
+      const CompT<T>* dc = reinterpret_cast<const CompT<T>*>(smem + P.off_dc);
+      const MemT<T>* dm = reinterpret_cast<const MemT<T>*>(smem + P.off_dm);
+      const int K = P.nc + P.nm;
+      for (int base = 0; base < ntask; base += blockDim.x) {
+        const int t = base + tid;
+        const bool act = t < ntask;
+        const int i = act ? t / KS : 0;
+        const int k = act ? t - i * KS : 0;
+        double v[5] = {0, 0, 0, 0, 0};
+        if (act) {
+          const int k0 = (int)((long long)K * k / KS), k1 = (int)((long long)K * (k + 1) / KS);
+          double x, y;
+          if (j == 0) {
+            x = C.theta[2 * i];
+            y = C.theta[2 * i + 1];
+          } else {
+            x = img[i * IS + 14];
+            y = img[i * IS + 15];
+          }
+          if constexpr (MIXED) {
+            float xh[1], xl[1], yh[1], yl[1];
+            split_ff(x, xh[0], xl[0]);
+            split_ff(y, yh[0], yl[0]);
+            ff acc[5][1];
+            for (int q = 0; q < 5; ++q) acc[q][0] = ff_zero();
+            accumulate_mixed<1>(dc, P.nc, dm, P.nm, k0, k1, chunk, xh, xl, yh, yl, acc);
+            for (int q = 0; q < 5; ++q) v[q] = ff_to_double(acc[q][0]);
+          } else {
+            accumulate_fp64(dc, P.nc, dm, P.nm, k0, k1, x, y, v);
+          }
+        }
+        for (int off = 1; off < KS; off <<= 1)
+#pragma unroll
+          for (int q = 0; q < 5; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+        if (act && k == 0)
+          for (int q = 0; q < 5; ++q) img[i * IS + q] = v[q];
+      }
+      __syncthreads();
+      if (C.np > 1) {
+        // recursion state: [14..15] theta_{j+1}, then per plane alpha (2) and Psi_j A_j (4)
+        for (int i = tid; i < n_img; i += blockDim.x) {
+          double* r = img + i * IS;
+          double a00 = 1, a01 = 0, a10 = 0, a11 = 1;
+          for (int l = 0; l < j; ++l) {
+            const double* pl = r + 16 + 6 * l;
+            double rr = C.r[l][j];
+            a00 -= rr * pl[2]; a01 -= rr * pl[3]; a10 -= rr * pl[4]; a11 -= rr * pl[5];
+          }
+          double* pj = r + 16 + 6 * j;
+          pj[0] = r[0]; pj[1] = r[1];
+          pj[2] = r[2] * a00 + r[4] * a10;
+          pj[3] = r[2] * a01 + r[4] * a11;
+          pj[4] = r[4] * a00 + r[3] * a10;
+          pj[5] = r[4] * a01 + r[3] * a11;
+          if (j + 1 < C.np) {
+            double tx = C.theta[2 * i], ty = C.theta[2 * i + 1];
+            for (int l = 0; l <= j; ++l) {
+              tx -= C.r[l][j + 1] * r[16 + 6 * l];
+              ty -= C.r[l][j + 1] * r[16 + 6 * l + 1];
+            }
+            r[14] = tx;
+            r[15] = ty;
+          }
+        }
+        __syncthreads();
+      }
+    }
+
+    // ---- A5, A7: beta_i, A_i, mu_i, M_i (FP64)
+    for (int i = tid; i < n_img; i += blockDim.x) {
+      double* r = img + i * IS;
+      const int f = C.img_fam[i];
+      const double tx = C.theta[2 * i], ty = C.theta[2 * i + 1];
+      double bx, by, A00, A01, A10, A11;
+      if (C.np == 1) {
+        const double a = C.fam_ratio[f];
+        bx = tx - a * r[0];
+        by = ty - a * r[1];
+        A00 = 1.0 - a * r[2]; A11 = 1.0 - a * r[3]; A01 = A10 = -a * r[4];
+      } else {
+        bx = tx; by = ty; A00 = 1; A01 = 0; A10 = 0; A11 = 1;
+        for (int l = 0; l < C.np; ++l) {
+          const double rs = C.fam_ratio[f * C.np + l];
+          const double* pl = r + 16 + 6 * l;
+          bx -= rs * pl[0]; by -= rs * pl[1];
+          A00 -= rs * pl[2]; A01 -= rs * pl[3]; A10 -= rs * pl[4]; A11 -= rs * pl[5];
+        }
+      }
+      const double id = 1.0 / (A00 * A11 - A01 * A10);
+      const double m00 = A11 * id, m01 = -A01 * id, m10 = -A10 * id, m11 = A00 * id;
+      const double s0 = C.sinv[3 * i], s1 = C.sinv[3 * i + 1], s2 = C.sinv[3 * i + 2];
+      const double X00 = s0 * m00 + s1 * m10, X01 = s0 * m01 + s1 * m11;
+      const double X10 = s1 * m00 + s2 * m10, X11 = s1 * m01 + s2 * m11;
+      r[5] = m00 * X00 + m10 * X10;
+      r[6] = m00 * X01 + m10 * X11;
+      r[7] = m01 * X01 + m11 * X11;
+      r[8] = bx; r[9] = by;
+      r[10] = m00; r[11] = m01; r[12] = m10; r[13] = m11;
+    }
+    __syncthreads();
+
+    // ---- A8: analytic source and chi^2 per family
+    double my = 0.0;
+    for (int f = tid; f < C.n_fam; f += blockDim.x) {
+      const int i0 = C.fam_off[f], i1 = C.fam_off[f + 1];
+      double G00 = 0, G01 = 0, G11 = 0, g0 = 0, g1 = 0;
+      for (int i = i0; i < i1; ++i) {
+        const double* r = img + i * IS;
+        G00 += r[5]; G01 += r[6]; G11 += r[7];
+        g0 += r[5] * r[8] + r[6] * r[9];
+        g1 += r[6] * r[8] + r[7] * r[9];
+      }
+      double bm0, bm1, cf = 0.0;
+      if (i1 - i0 == 1) {
+        bm0 = img[i0 * IS + 8];
+        bm1 = img[i0 * IS + 9];
+        if (!(isfinite(G00) && isfinite(G01) && isfinite(G11) && isfinite(bm0) && isfinite(bm1)))
+          cf = INFINITY;
+      } else {
+        const double dG = G00 * G11 - G01 * G01;
+        bm0 = (G11 * g0 - G01 * g1) / dG;
+        bm1 = (G00 * g1 - G01 * g0) / dG;
+        for (int i = i0; i < i1; ++i) {
+          const double* r = img + i * IS;
+          const double d0 = r[8] - bm0, d1 = r[9] - bm1;
+          cf += r[5] * d0 * d0 + 2.0 * r[6] * d0 * d1 + r[7] * d1 * d1;
+        }
+        if (!isfinite(cf) || !(dG > 0.0)) cf = INFINITY;
+      }
+      fam[3 * f] = cf;
+      fam[3 * f + 1] = bm0;
+      fam[3 * f + 2] = bm1;
+      my += cf;
+    }
+    const double total = block_sum(my, scratch);
+    if (tid == 0) chi2[s] = total;
+
+    if constexpr (GRAD) {
+      // cotangents of alpha and Psi at each image (stored over the sums)
+      for (int i = tid; i < n_img; i += blockDim.x) {
+        double* r = img + i * IS;
+        const int f = C.img_fam[i];
+        const double a = C.fam_ratio[f];
+        const int n_f = C.fam_off[f + 1] - C.fam_off[f];
+        const double d0 = r[8] - fam[3 * f + 1], d1 = r[9] - fam[3 * f + 2];
+        const double w0 = r[5] * d0 + r[6] * d1, w1 = r[6] * d0 + r[7] * d1;
+        const double z0 = r[10] * d0 + r[11] * d1, z1 = r[12] * d0 + r[13] * d1;
+        const double k2a = n_f > 1 ? 2.0 * a : 0.0;
+        r[0] = -k2a * w0;
+        r[1] = -k2a * w1;
+        r[2] = k2a * w0 * z0;
+        r[3] = k2a * w1 * z1;
+        r[4] = k2a * (w0 * z1 + w1 * z0);
+      }
+      __syncthreads();
+      const PlaneDesc& P = C.pl[0];
+      const MemT<T>* dm = reinterpret_cast<const MemT<T>*>(smem + P.off_dm);
+      const int K = P.nc + P.nm;
+      const bool mem_grad = (C.scal_plane == 0) && C.scal_free;
+      lf_scaling ssc = P.sc;
+      if (mem_grad) sample_scaling(C, th, ssc);
+      const T inv_cut_star = (T)(1.0 / ssc.cut_star);
+      for (int t = tid; t < ntask; t += blockDim.x) {
+        const int i = t / KS, k = t - i * KS;
+        const int k0 = (int)((long long)K * k / KS), k1 = (int)((long long)K * (k + 1) / KS);
+        const double* r = img + i * IS;
+        T cot[5] = {(T)r[0], (T)r[1], (T)r[2], (T)r[3], (T)r[4]};
+        const double px = C.theta[2 * i], py = C.theta[2 * i + 1];
+        for (int f = 0; f < C.n_free; ++f) {
+          const int kc = C.free_comp[f];
+          if (C.free_plane[f] != 0 || kc < k0 || kc >= k1) continue;
+          const lf_comp& rc = fraw[f];
+          if (rc.kind < 1 || rc.kind > 4) continue;
+          Out5<Dual<T, 6>> o;
+          comp_dual<T>(rc, px, py, o);
+          const T b = (T)rc.b;
+          // field order x, y, b, eps, pa, core, cut; tangent slots x0 y1 eps2 pa3 core4 cut5
+          const int slot[7] = {0, 1, -1, 2, 3, 4, 5};
+          for (int fld = 0; fld < 7; ++fld) {
+            const int p = C.free_p[f][fld];
+            if (p < 0) continue;
+            T g = (fld == LF_F_B) ? contract(o, cot, -1) : b * contract(o, cot, slot[fld]);
+            atomicAdd(&gacc[p], (double)g * xform_deriv(C.p_xform[p], th[p], P.apk));
+          }
+        }
+        if (mem_grad) {
+          const int m0 = max(k0, P.nc) - P.nc, m1 = min(k1, K) - P.nc;
+          T gs[6] = {0, 0, 0, 0, 0, 0};
+          for (int m = m0; m < m1; ++m) {
+            const MemT<T>& M = dm[m];
+            typedef Dual<T, 2> D2;
+            D2 sd = D2::var(M.s, 0), ad = D2::var(M.a, 1);
+            Out5<D2> o;
+            T dx, dy;
+            if constexpr (MIXED) {
+              float xh, xl, yh, yl;
+              split_ff(C.theta[2 * i], xh, xl);
+              split_ff(C.theta[2 * i + 1], yh, yl);
+              dx = offset_of(xh, xl, M.xh, M.xl);
+              dy = offset_of(yh, yl, M.yh, M.yl);
+            } else {
+              dx = C.theta[2 * i] - M.xh;
+              dy = C.theta[2 * i + 1] - M.yh;
+            }
+            pje_round(D2::cst(dx), D2::cst(dy), D2::cst((T)1), sd, sd * sd, ad, ad * ad, o);
+            const T Gb = contract(o, cot, -1);
+            const T Gs = M.b * contract(o, cot, 0);
+            const T Ga = M.b * contract(o, cot, 1);
+            const T fa = M.a * inv_cut_star;
+            gs[LF_S_BSTAR] += Gb * M.fb;
+            gs[LF_S_LAM] += Gb * M.b * (T)2 * M.loglr;
+            gs[LF_S_CORESTAR] += Gs * M.fs;
+            gs[LF_S_BETA] += Gs * M.s * M.loglr;
+            gs[LF_S_CUTSTAR] += Ga * fa;
+            gs[LF_S_ALPHA] += Ga * M.a * M.loglr;
+          }
+          for (int q = 0; q < 6; ++q) {
+            const int p = C.scal_p[q];
+            if (p >= 0 && m1 > m0)
+              atomicAdd(&gacc[p], (double)gs[q] * xform_deriv(C.p_xform[p], th[p], P.apk));
+          }
+        }
+      }
+      __syncthreads();
+      for (int p = tid; p < C.P; p += blockDim.x) grad[(size_t)s * C.P + p] = gacc[p];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace lf
+
+// ======================================================================= host =======
+using namespace lf;
+
+struct lf_plan {
+  int n_clusters = 0, P = 0, precision = LF_MIXED, flags = 0, max_samples = 0;
+  bool single_plane = true;
+  std::vector<ClusterDesc> desc;
+  std::vector<double> cost;
+  ClusterDesc* d_desc = nullptr;
+  int* d_counter = nullptr;
+  int* d_order = nullptr;
+  std::vector<void*> allocs;
+  int block = 256;
+  int ks_cap = 32;
+  bool tuned = false;
+  uint32_t smem = 0;
+  int grid_chi2 = 0, grid_grad = 0;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_theta = nullptr;
+  void* g_out = nullptr;
+  int g_S = -1;
+};
+
+namespace lf {
+
+static lf_status plan_alloc(lf_plan* pl, void** out, size_t bytes) {
+  *out = nullptr;
+  if (bytes == 0) return LF_OK;
+  cudaError_t e = cudaMalloc(out, bytes);
+  if (e != cudaSuccess) return fail(LF_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  pl->allocs.push_back(*out);
+  return LF_OK;
+}
+
+template <class X>
+static lf_status plan_upload(lf_plan* pl, const X* host, size_t n, X** dev) {
+  void* p = nullptr;
+  LF_TRY(plan_alloc(pl, &p, n * sizeof(X)));
+  if (n) LF_CUDA(cudaMemcpy(p, host, n * sizeof(X), cudaMemcpyHostToDevice));
+  *dev = reinterpret_cast<X*>(p);
+  return LF_OK;
+}
+
+static bool comp_ok(const lf_comp& r) {
+  bool ok = r.kind >= 1 && r.kind <= 4 && std::isfinite(r.x) && std::isfinite(r.y) &&
+            std::isfinite(r.b) && std::isfinite(r.pa);
+  if (r.kind == LF_SIE || r.kind == LF_DPIE)
+    ok = ok && r.eps >= 0.0 && r.eps < 1.0 && r.core >= 0.0 && std::isfinite(r.core);
+  if (r.kind == LF_DPIE) ok = ok && std::isfinite(r.cut) && r.cut > r.core;
+  if (r.kind == LF_NFW) ok = ok && r.core > 0.0 && std::isfinite(r.core);
+  return ok;
+}
+
+static int pow2_floor(int v) {
+  int r = 1;
+  while (r * 2 <= v) r *= 2;
+  return r;
+}
+
+// Component slices per image: the power of two minimising a simple cost model of one work
+// item, rounds x (components per slice + per-task overhead), capped by the tuner's choice.
+static int choose_ks(int n_img, int K, int block, int cap) {
+  const double overhead = 24.0;   // task set-up and shuffle reduction, in component evaluations
+  int best = 1;
+  double best_cost = 1e300;
+  for (int ks = 1; ks <= 32 && ks <= cap; ks *= 2) {
+    if (ks > 1 && K / ks < 8) break;
+    long long tasks = (long long)n_img * ks;
+    long long rounds = (tasks + block - 1) / block;
+    double cost = (double)rounds * ((double)K / ks + overhead);
+    if (cost < best_cost * 0.97) { best_cost = cost; best = ks; }
+  }
+  return best;
+}
+
+static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap) {
+  const bool mixed = precision == LF_MIXED;
+  uint32_t o = LF_HDR;
+  for (int j = 0; j < C.np; ++j) {
+    PlaneDesc& P = C.pl[j];
+    o = (o + 15u) & ~15u; P.off_rawc = o; o += (uint32_t)P.nc * 64u;
+    o = (o + 15u) & ~15u; P.off_mpre = o; o += (uint32_t)P.nm * (mixed ? sizeof(MemPreF) : sizeof(MemPreD));
+    o = (o + 15u) & ~15u; P.off_dc = o; o += (uint32_t)P.nc * (mixed ? sizeof(CompT<float>) : sizeof(CompT<double>));
+    o = (o + 15u) & ~15u; P.off_dm = o; o += (uint32_t)P.nm * (mixed ? sizeof(MemT<float>) : sizeof(MemT<double>));
+  }
+  C.img_stride = C.np > 1 ? 16 + 6 * C.np : 14;
+  o = (o + 15u) & ~15u; C.off_img = o; o += (uint32_t)C.n_img * C.img_stride * 8u;
+  C.off_fam = o; o += (uint32_t)C.n_fam * 3u * 8u;
+  C.off_par = o; o += (uint32_t)C.P * 2u * 8u;
+  o = (o + 15u) & ~15u; C.off_free = o; o += (uint32_t)C.n_free * 64u;
+  C.smem = (o + 15u) & ~15u;
+  int K = 0;
+  for (int j = 0; j < C.np; ++j) K = std::max(K, C.pl[j].nc + C.pl[j].nm);
+  C.ks = choose_ks(C.n_img, K, block, ks_cap);
+}
+
+static lf_status relayout(lf_plan* pl) {
+  pl->smem = 0;
+  for (auto& C : pl->desc) {
+    layout_cluster(C, pl->precision, pl->block, pl->ks_cap);
+    pl->smem = std::max(pl->smem, C.smem);
+  }
+  if (pl->smem > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "cluster too large for shared memory (%u B)", pl->smem);
+  LF_CUDA(cudaMemcpy(pl->d_desc, pl->desc.data(), pl->desc.size() * sizeof(ClusterDesc),
+                     cudaMemcpyHostToDevice));
+  int dev = 0, nsm = 0, occ = 0;
+  LF_CUDA(cudaGetDevice(&dev));
+  LF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  auto kset = [&](const void* k) -> lf_status {
+    LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem));
+    return LF_OK;
+  };
+  const void* kc = pl->precision == LF_MIXED ? (const void*)k_chi2<true, false> : (const void*)k_chi2<false, false>;
+  const void* kg = pl->precision == LF_MIXED ? (const void*)k_chi2<true, true> : (const void*)k_chi2<false, true>;
+  LF_TRY(kset(kc));
+  LF_TRY(kset(kg));
+  LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kc, pl->block, pl->smem));
+  pl->grid_chi2 = nsm * std::max(occ, 1);
+  LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kg, pl->block, pl->smem));
+  pl->grid_grad = nsm * std::max(occ, 1);
+  if (pl->gexec) {
+    cudaGraphExecDestroy(pl->gexec);
+    pl->gexec = nullptr;
+  }
+  return LF_OK;
+}
+
+static lf_status build_cluster(lf_plan* pl, const lf_cluster& cl, ClusterDesc& C, double& cost) {
+  memset(&C, 0, sizeof C);
+  if (cl.n_planes < 1 || cl.n_planes > LF_MAX_PLANES || !cl.planes)
+    return fail(LF_EINVAL, "cluster needs 1..8 planes");
+  if (cl.n_planes > 1 && !cl.ratios) return fail(LF_EINVAL, "multi-plane cluster needs ratios");
+  if (!cl.arcsec_per_kpc) return fail(LF_EINVAL, "arcsec_per_kpc is NULL");
+  C.np = cl.n_planes;
+  const bool mixed = pl->precision == LF_MIXED;
+  std::vector<int> comp_base(C.np + 1, 0);
+  std::vector<std::vector<lf_comp>> comps(C.np);
+  cost = 0.0;
+  for (int j = 0; j < C.np; ++j) {
+    const lf_plane& src = cl.planes[j];
+    LF_TRY(check_plane(&src));
+    PlaneDesc& P = C.pl[j];
+    P.nc = src.n_comp;
+    P.nm = src.n_mem;
+    P.sc = src.scaling;
+    P.apk = cl.arcsec_per_kpc[j];
+    if (!(std::isfinite(P.apk) && P.apk > 0)) return fail(LF_EINVAL, "invalid arcsec_per_kpc");
+    comps[j].resize(P.nc);
+    if (P.nc) LF_CUDA(cudaMemcpy(comps[j].data(), src.comp, P.nc * sizeof(lf_comp), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < P.nc; ++i)
+      if (!comp_ok(comps[j][i])) return fail(LF_EINVAL, "plane %d component %d is invalid", j, i);
+    lf_comp* dcomp = nullptr;
+    LF_TRY(plan_upload(pl, comps[j].data(), P.nc, &dcomp));
+    P.comp = dcomp;
+    std::vector<lf_member> mem(P.nm);
+    if (P.nm) LF_CUDA(cudaMemcpy(mem.data(), src.mem, P.nm * sizeof(lf_member), cudaMemcpyDeviceToHost));
+    const double LN10 = 2.302585092994045684;
+    if (mixed) {
+      std::vector<MemPreF> pre(P.nm);
+      for (int i = 0; i < P.nm; ++i) {
+        double lnl = mem[i].log_l * LN10;
+        split_ff(mem[i].x, pre[i].xh, pre[i].xl);
+        split_ff(mem[i].y, pre[i].yh, pre[i].yl);
+        pre[i].fb = (float)std::exp(2.0 * P.sc.lam * lnl);
+        pre[i].fs = (float)std::exp(P.sc.beta * lnl);
+        pre[i].fa = (float)std::exp(P.sc.alpha * lnl);
+        pre[i].lnl = (float)lnl;
+        if (!std::isfinite(mem[i].x) || !std::isfinite(mem[i].y) || !std::isfinite(lnl))
+          return fail(LF_EINVAL, "plane %d member %d is not finite", j, i);
+      }
+      MemPreF* d = nullptr;
+      LF_TRY(plan_upload(pl, pre.data(), pre.size(), &d));
+      P.mpre = d;
+    } else {
+      std::vector<MemPreD> pre(P.nm);
+      for (int i = 0; i < P.nm; ++i) {
+        double lnl = mem[i].log_l * LN10;
+        pre[i] = MemPreD{mem[i].x, mem[i].y, std::exp(2.0 * P.sc.lam * lnl), std::exp(P.sc.beta * lnl),
+                         std::exp(P.sc.alpha * lnl), lnl, 0.0, 0.0};
+        if (!std::isfinite(mem[i].x) || !std::isfinite(mem[i].y) || !std::isfinite(lnl))
+          return fail(LF_EINVAL, "plane %d member %d is not finite", j, i);
+      }
+      MemPreD* d = nullptr;
+      LF_TRY(plan_upload(pl, pre.data(), pre.size(), &d));
+      P.mpre = d;
+    }
+    comp_base[j + 1] = comp_base[j] + P.nc;
+    if (C.np > 1)
+      for (int l = 0; l < C.np; ++l) C.r[j][l] = (l > j) ? cl.ratios[j * C.np + l] : 0.0;
+  }
+  // images
+  const lf_images& im = cl.images;
+  if (im.n_img < 1 || im.n_img > LF_MAX_IMG) return fail(LF_EINVAL, "need 1..%d images", LF_MAX_IMG);
+  if (im.n_fam < 1 || !im.theta_obs || !im.sinv || !im.fam_off || !im.fam_ratio)
+    return fail(LF_EINVAL, "incomplete image set");
+  if (im.fam_off[0] != 0 || im.fam_off[im.n_fam] != im.n_img)
+    return fail(LF_EINVAL, "fam_off must run from 0 to n_img");
+  std::vector<int> img_fam(im.n_img);
+  for (int f = 0; f < im.n_fam; ++f) {
+    if (im.fam_off[f + 1] <= im.fam_off[f]) return fail(LF_EINVAL, "family %d is empty", f);
+    for (int i = im.fam_off[f]; i < im.fam_off[f + 1]; ++i) img_fam[i] = f;
+    for (int l = 0; l < C.np; ++l) {
+      double v = im.fam_ratio[f * C.np + l];
+      bool ok = std::isfinite(v) && (C.np == 1 ? (v > 0.0 && v <= 1.0) : (v >= 0.0 && v <= 1.0));
+      if (!ok) return fail(LF_EINVAL, "family %d has an invalid distance ratio", f);
+    }
+  }
+  for (int i = 0; i < im.n_img; ++i) {
+    double a = im.sinv[3 * i], b = im.sinv[3 * i + 1], c = im.sinv[3 * i + 2];
+    if (!(std::isfinite(im.theta_obs[2 * i]) && std::isfinite(im.theta_obs[2 * i + 1]) &&
+          std::isfinite(a) && std::isfinite(b) && std::isfinite(c) && a > 0 && c > 0 && a * c - b * b > 0))
+      return fail(LF_EINVAL, "image %d: non-finite position or S^-1 not positive definite", i);
+  }
+  C.n_img = im.n_img;
+  C.n_fam = im.n_fam;
+  double* dtheta = nullptr; double* dsinv = nullptr; double* dratio = nullptr;
+  int* doff = nullptr; int* dif = nullptr;
+  LF_TRY(plan_upload(pl, im.theta_obs, 2 * (size_t)im.n_img, &dtheta));
+  LF_TRY(plan_upload(pl, im.sinv, 3 * (size_t)im.n_img, &dsinv));
+  LF_TRY(plan_upload(pl, im.fam_ratio, (size_t)im.n_fam * C.np, &dratio));
+  LF_TRY(plan_upload(pl, im.fam_off, (size_t)im.n_fam + 1, &doff));
+  LF_TRY(plan_upload(pl, img_fam.data(), img_fam.size(), &dif));
+  C.theta = dtheta; C.sinv = dsinv; C.fam_ratio = dratio; C.fam_off = doff; C.img_fam = dif;
+  // parameter map
+  C.P = cl.P;
+  if (cl.P < 1 || cl.P > LF_MAX_P || !cl.p_comp || !cl.p_field || !cl.p_xform)
+    return fail(LF_EINVAL, "need 1..%d parameters with a complete map", LF_MAX_P);
+  C.scal_plane = -1;
+  for (int j = 0; j < C.np; ++j)
+    if (C.pl[j].nm > 0) { C.scal_plane = j; break; }
+  for (int k = 0; k < 6; ++k) C.scal_p[k] = -1;
+  C.n_free = 0;
+  for (int p = 0; p < cl.P; ++p) {
+    int gc = cl.p_comp[p], fld = cl.p_field[p], xf = cl.p_xform[p];
+    if (xf < 0 || xf > 3) return fail(LF_EINVAL, "parameter %d: unknown transform", p);
+    C.p_xform[p] = xf;
+    if (gc < 0) {
+      if (C.scal_plane < 0) return fail(LF_EINVAL, "parameter %d targets a scaling relation but no plane has members", p);
+      if (fld < 0 || fld > 5) return fail(LF_EINVAL, "parameter %d: unknown scaling slot", p);
+      if (C.scal_p[fld] >= 0) return fail(LF_EINVAL, "scaling slot %d targeted twice", fld);
+      C.scal_p[fld] = p;
+      C.scal_free = 1;
+      C.p_plane[p] = C.scal_plane;
+      continue;
+    }
+    if (fld < 0 || fld > 6) return fail(LF_EINVAL, "parameter %d: unknown field", p);
+    if (gc >= comp_base[C.np]) return fail(LF_EINVAL, "parameter %d: component %d out of range", p, gc);
+    int j = 0;
+    while (gc >= comp_base[j + 1]) ++j;
+    int k = gc - comp_base[j];
+    C.p_plane[p] = j;
+    int f = 0;
+    while (f < C.n_free && !(C.free_plane[f] == j && C.free_comp[f] == k)) ++f;
+    if (f == C.n_free) {
+      if (C.n_free == LF_MAX_FREE) return fail(LF_EUNSUPPORTED, "more than %d sampled components", LF_MAX_FREE);
+      C.free_plane[f] = j;
+      C.free_comp[f] = k;
+      for (int q = 0; q < 7; ++q) C.free_p[f][q] = -1;
+      ++C.n_free;
+    }
+    if (C.free_p[f][fld] >= 0) return fail(LF_EINVAL, "field targeted twice");
+    C.free_p[f][fld] = p;
+  }
+  int K = 0;
+  for (int j = 0; j < C.np; ++j) K += C.pl[j].nc + C.pl[j].nm;
+  cost = (double)C.n_img * K;
+  return LF_OK;
+}
+
+static lf_status launch_chi2(lf_plan* pl, const double* theta, int S, double* chi2, double* grad,
+                             cudaStream_t st) {
+  const int spc = S / pl->n_clusters;
+  LF_CUDA(cudaMemsetAsync(pl->d_counter, 0, sizeof(int), st));
+  const bool mixed = pl->precision == LF_MIXED;
+  if (grad) {
+    int g = std::min(pl->grid_grad, S);
+    if (mixed)
+      k_chi2<true, true><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2, grad, pl->d_counter, g_member_chunk);
+    else
+      k_chi2<false, true><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2, grad, pl->d_counter, g_member_chunk);
+  } else {
+    int g = std::min(pl->grid_chi2, S);
+    if (mixed)
+      k_chi2<true, false><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2, nullptr, pl->d_counter, g_member_chunk);
+    else
+      k_chi2<false, false><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2, nullptr, pl->d_counter, g_member_chunk);
+  }
+  LF_CUDA(cudaGetLastError());
+  return LF_OK;
+}
+
+// Times candidate (block, slice cap) shapes on the caller's inputs and keeps the fastest.
+static lf_status autotune(lf_plan* pl, const double* theta, int S, double* chi2, cudaStream_t st) {
+  const int blocks[3] = {128, 256, 512};
+  const int caps[4] = {1, 4, 8, 32};
+  cudaEvent_t e0, e1;
+  LF_CUDA(cudaEventCreate(&e0));
+  LF_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bb = pl->block, bc = pl->ks_cap;
+  for (int b : blocks)
+    for (int cap : caps) {
+      pl->block = b;
+      pl->ks_cap = cap;
+      if (relayout(pl) != LF_OK) continue;
+      LF_TRY(launch_chi2(pl, theta, S, chi2, nullptr, st));
+      LF_CUDA(cudaEventRecord(e0, st));
+      for (int r = 0; r < 3; ++r) LF_TRY(launch_chi2(pl, theta, S, chi2, nullptr, st));
+      LF_CUDA(cudaEventRecord(e1, st));
+      LF_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      LF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; bb = b; bc = cap; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pl->block = bb;
+  pl->ks_cap = bc;
+  LF_TRY(relayout(pl));
+  pl->tuned = true;
+  return LF_OK;
+}
+
+static lf_status run(lf_plan* pl, const double* theta, int S, double* chi2, double* grad, void* stream) {
+  if (!pl) return fail(LF_EINVAL, "plan is NULL");
+  if (!theta || !chi2) return fail(LF_EINVAL, "theta and chi2 are required");
+  if (S < 1 || S > pl->max_samples) return fail(LF_EINVAL, "S must be in 1..%d", pl->max_samples);
+  if (S % pl->n_clusters) return fail(LF_EINVAL, "S must be a multiple of the number of clusters");
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((pl->flags & 2) && !pl->tuned) LF_TRY(autotune(pl, theta, S, chi2, st));
+  if (!(pl->flags & 1)) return launch_chi2(pl, theta, S, chi2, grad, st);
+  // CUDA graph: the counter reset and the persistent launch, replayed while the buffers and
+  // S are unchanged, on the plan's stream ordered after / before the caller's stream.
+  void* out_key = grad ? (void*)grad : (void*)chi2;
+  if (!pl->gexec || pl->g_theta != theta || pl->g_out != out_key || pl->g_S != S) {
+    if (pl->gexec) { cudaGraphExecDestroy(pl->gexec); pl->gexec = nullptr; }
+    cudaGraph_t g = nullptr;
+    LF_CUDA(cudaStreamBeginCapture(pl->gstream, cudaStreamCaptureModeThreadLocal));
+    lf_status ls = launch_chi2(pl, theta, S, chi2, grad, pl->gstream);
+    cudaError_t ce = cudaStreamEndCapture(pl->gstream, &g);
+    if (ls != LF_OK) { if (g) cudaGraphDestroy(g); return ls; }
+    if (ce != cudaSuccess) return fail(LF_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&pl->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return fail(LF_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
+    pl->g_theta = theta; pl->g_out = out_key; pl->g_S = S;
+  }
+  LF_CUDA(cudaEventRecord(pl->ev_in, st));
+  LF_CUDA(cudaStreamWaitEvent(pl->gstream, pl->ev_in, 0));
+  LF_CUDA(cudaGraphLaunch(pl->gexec, pl->gstream));
+  LF_CUDA(cudaEventRecord(pl->ev_out, pl->gstream));
+  LF_CUDA(cudaStreamWaitEvent(st, pl->ev_out, 0));
+  return LF_OK;
+}
+
+}  // namespace lf
+
+extern "C" lf_status lf_plan_destroy(lf_plan* pl) {
+  if (!pl) return LF_OK;
+  if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+  if (pl->ev_in) cudaEventDestroy(pl->ev_in);
+  if (pl->ev_out) cudaEventDestroy(pl->ev_out);
+  if (pl->gstream) cudaStreamDestroy(pl->gstream);
+  for (void* p : pl->allocs) cudaFree(p);
+  delete pl;
+  return LF_OK;
+}
+
+extern "C" lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, int32_t n_clusters,
+                                    int32_t max_samples, int32_t precision, int32_t flags) {
+  if (!out) return fail(LF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!clusters || n_clusters < 1) return fail(LF_EINVAL, "need at least one cluster");
+  if (max_samples < n_clusters) return fail(LF_EINVAL, "max_samples must be >= n_clusters");
+  if (precision != LF_FP64 && precision != LF_MIXED) return fail(LF_EINVAL, "unknown precision");
+  if (flags & ~3) return fail(LF_EINVAL, "unknown flags");
+  lf_plan* pl = new lf_plan();
+  pl->n_clusters = n_clusters;
+  pl->precision = precision;
+  pl->flags = flags;
+  pl->max_samples = max_samples;
+  pl->P = clusters[0].P;
+  pl->desc.resize(n_clusters);
+  pl->cost.resize(n_clusters);
+  lf_status st = LF_OK;
+  for (int c = 0; c < n_clusters && st == LF_OK; ++c) {
+    if (clusters[c].P != pl->P) st = fail(LF_EINVAL, "every cluster must have the same P");
+    else st = build_cluster(pl, clusters[c], pl->desc[c], pl->cost[c]);
+    if (st == LF_OK && pl->desc[c].np > 1) pl->single_plane = false;
+  }
+  if (st == LF_OK) {
+    std::vector<int> order(n_clusters);
+    for (int c = 0; c < n_clusters; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pl->cost[a] > pl->cost[b]; });
+    void* p = nullptr;
+    st = plan_alloc(pl, &p, n_clusters * sizeof(int));
+    if (st == LF_OK) {
+      pl->d_order = (int*)p;
+      if (cudaMemcpy(pl->d_order, order.data(), n_clusters * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        st = fail(LF_ECUDA, "upload of the cluster order failed");
+    }
+    if (st == LF_OK) st = plan_alloc(pl, &p, sizeof(int));
+    if (st == LF_OK) pl->d_counter = (int*)p;
+    if (st == LF_OK) st = plan_alloc(pl, &p, n_clusters * sizeof(ClusterDesc));
+    if (st == LF_OK) pl->d_desc = (ClusterDesc*)p;
+    if (st == LF_OK) st = relayout(pl);
+    if (st == LF_OK && (flags & 1)) {
+      if (cudaStreamCreateWithFlags(&pl->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&pl->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&pl->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        st = fail(LF_ECUDA, "stream / event creation failed");
+    }
+  }
+  if (st != LF_OK) {
+    lf_plan_destroy(pl);
+    return st;
+  }
+  *out = pl;
+  return LF_OK;
+}
+
+extern "C" lf_status lf_chi2_batch(lf_plan* plan, const double* theta, int32_t S, double* chi2,
+                                   void* stream) {
+  return run(plan, theta, S, chi2, nullptr, stream);
+}
+
+extern "C" lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int32_t S, double* chi2,
+                                        double* grad, void* stream) {
+  if (!plan) return fail(LF_EINVAL, "plan is NULL");
+  if (!grad) return fail(LF_EINVAL, "grad is NULL");
+  if (!plan->single_plane) return fail(LF_EUNSUPPORTED, "the gradient is implemented for single-plane plans");
+  return run(plan, theta, S, chi2, grad, stream);
+}
+
+extern "C" lf_status lf_plan_info(const lf_plan* plan, int32_t* kslices, int32_t* block, int32_t* graph) {
+  if (!plan) return fail(LF_EINVAL, "plan is NULL");
+  if (kslices) *kslices = plan->desc.empty() ? 0 : plan->desc[0].ks;
+  if (block) *block = plan->block;
+  if (graph) *graph = (plan->flags & 1) ? 1 : 0;
+  return LF_OK;
 }

@@ -224,8 +224,8 @@ template <class T> struct CompT {
 // A cluster member (round pseudo-Jaffe) prepared for evaluation in precision T.
 template <class T> struct MemT {
   T xh, xl, yh, yl;
-  T b, s, a, pad;
-  T s2, a2, loglr, pad2;  // loglr = ln(L/L*)
+  T b, s, a, fb;          // fb = (L/L*)^(2 lam) = b / b*
+  T s2, a2, loglr, fs;    // loglr = ln(L/L*), fs = (L/L*)^beta = s / core*
 };
 
 // Builds the evaluation constants of one explicit component from its fields.
@@ -261,7 +261,8 @@ __host__ __device__ inline void digest_comp(int kind, double x, double y, double
 
 template <class T>
 __host__ __device__ inline void digest_member(double x, double y, double b, double s, double a,
-                                              double loglr, MemT<T>& m) {
+                                              double loglr, MemT<T>& m, double fb = 0.0,
+                                              double fs = 0.0) {
   if (sizeof(T) == 4) {
     float h, l;
     split_ff(x, h, l); m.xh = (T)h; m.xl = (T)l;
@@ -269,8 +270,8 @@ __host__ __device__ inline void digest_member(double x, double y, double b, doub
   } else {
     m.xh = (T)x; m.xl = (T)0; m.yh = (T)y; m.yl = (T)0;
   }
-  m.b = (T)b; m.s = (T)s; m.a = (T)a; m.pad = (T)0;
-  m.s2 = (T)(s * s); m.a2 = (T)(a * a); m.loglr = (T)loglr; m.pad2 = (T)0;
+  m.b = (T)b; m.s = (T)s; m.a = (T)a; m.fb = (T)fb;
+  m.s2 = (T)(s * s); m.a2 = (T)(a * a); m.loglr = (T)loglr; m.fs = (T)fs;
 }
 
 // Offset from a centre: float-float difference for FP32, plain for FP64.
@@ -383,6 +384,7 @@ LF_INLINE bool stage_to_smem(void* dst, const void* src, uint32_t bytes, uint64_
                              uint32_t parity) {
   if (bytes == 0) return true;
   if (threadIdx.x == 0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, bytes);
     const uint32_t CH = 32768u;
     for (uint32_t off = 0; off < bytes; off += CH) {

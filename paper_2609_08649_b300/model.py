@@ -127,3 +127,27 @@ def multiplane_ratios(cosmo, zs_planes, z_s):
         r[n, j] = (L.lib.lf_angular_distance(cosmo.H0, cosmo.Om, zs_planes[j], z_s) / ds
                    if z_s > zs_planes[j] else 0.0)
     return r
+
+
+def cluster_input(wl: W.Workload, cat: W.Catalogue, sigma_pos=None, device="cuda"):
+    """ClusterInput for a workload and its image catalogue: circular S_i = sigma^2 I
+    (Eq. chi2_img with sigma_1 = sigma_2), per-family distance ratios from the library's
+    cosmology, and the parameter map of the workload."""
+    from .api import ClusterInput
+    planes = device_planes(wl, device)
+    sig = wl.sigma_pos if sigma_pos is None else sigma_pos
+    n = len(cat.theta_obs)
+    sinv = np.tile([1.0 / sig ** 2, 0.0, 1.0 / sig ** 2], (n, 1))
+    zl = [p.z for p in wl.planes]
+    apk = [arcsec_per_kpc(wl.cosmo, z) for z in zl]
+    if len(planes) == 1:
+        fam_ratio = np.array([adis(wl.cosmo, zl[0], z) for z in cat.fam_zs])
+        ratios = None
+    else:
+        fam_ratio = np.array([multiplane_ratios(wl.cosmo, zl, z)[-1] for z in cat.fam_zs])
+        ratios = multiplane_ratios(wl.cosmo, zl, max(zl) + 1.0)[:-1]
+    p_comp = [p.comp for p in wl.params]
+    p_field = [p.field for p in wl.params]
+    p_xform = [p.xform for p in wl.params]
+    return ClusterInput(planes, apk, cat.theta_obs, sinv, cat.fam_off, fam_ratio, p_comp, p_field,
+                        p_xform, ratios)

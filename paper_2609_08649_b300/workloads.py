@@ -18,6 +18,7 @@ Component kinds (shared numeric codes): 1 SIE (cored isothermal ellipsoid),
 from __future__ import annotations
 
 import dataclasses
+import os
 from dataclasses import dataclass, field
 from typing import List, Optional
 
@@ -287,3 +288,28 @@ def random_positions(seed: int, n: int, half: float) -> np.ndarray:
 
 def replace(obj, **kw):
     return dataclasses.replace(obj, **kw)
+
+
+# ----------------------------------------------------------- stored catalogues -----
+CATALOGUE_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                             "tests", "golden", "catalogues")
+
+
+@dataclass
+class Catalogue:
+    theta_obs: np.ndarray      # (N, 2) observed positions (noisy)
+    theta_true: np.ndarray     # (N, 2) noise-free images
+    fam_off: np.ndarray        # (F + 1,)
+    fam_zs: np.ndarray         # (F,)
+
+
+def load_catalogue(name: str, directory: str = CATALOGUE_DIR) -> Catalogue:
+    """Multiple-image catalogue written by oracle/make_catalogues.py (forward ray-shooting
+    on the unjittered model); columns family, z_s, x_obs, y_obs, x_true, y_true."""
+    a = np.loadtxt(os.path.join(directory, name + ".txt"), ndmin=2)
+    fam = a[:, 0].astype(np.int64)
+    F = int(fam.max()) + 1
+    counts = np.bincount(fam, minlength=F)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    zs = np.array([a[fam == f, 1][0] for f in range(F)])
+    return Catalogue(a[:, 2:4].copy(), a[:, 4:6].copy(), off, zs)

@@ -1,0 +1,228 @@
+"""Parity of lf_chi2_batch / lf_chi2_grad_batch with the FP64 oracle (Eq. chi2_src with the
+analytic source of Sec. 3.1; gradient by the oracle's autograd and by central finite
+differences), plus the plan's edge cases.
+
+Tolerances: FP64 path 1e-10 relative on chi^2 and 1e-8 on the gradient; mixed path the
+stated targets, 1e-5 relative on chi^2 and 1e-4 on the gradient (relative to the larger of
+|g_p| and 1e-2 max_p |g_p| of the sample)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import gradient as OG
+from oracle import model as OM
+
+pytestmark = pytest.mark.gpu
+W = pytest.importorskip("paper_2609_08649_b300.workloads")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2609_08649_b300 import api, model
+    return api, model
+
+
+def oracle(wl, cat, theta, grad=False, sigma=None):
+    sig = wl.sigma_pos if sigma is None else sigma
+    n = len(cat.theta_obs)
+    sinv = torch.tensor(np.tile([1 / sig ** 2, 0, 1 / sig ** 2], (n, 1)))
+    tobs = torch.tensor(cat.theta_obs)
+    th = torch.as_tensor(theta)
+    kw = {}
+    if len(wl.planes) == 1:
+        kw["fam_adis"] = OM.single_plane_adis(wl, cat.fam_zs)
+    else:
+        kw["fam_zs"] = list(cat.fam_zs)
+    fn = OG.chi2_and_grad if grad else OG.chi2_only
+    return fn(wl, th, tobs, sinv, list(cat.fam_off), **kw)
+
+
+def grad_err(g, ref):
+    scale = np.maximum(np.abs(ref), 1e-2 * np.abs(ref).max(axis=1, keepdims=True))
+    return (np.abs(g - ref) / scale).max()
+
+
+@pytest.fixture(scope="module")
+def c2():
+    wl = W.cluster_c2()
+    return wl, W.load_catalogue("cluster_200"), W.sample_thetas(wl, wl.seed)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_cluster_chi2_matches_oracle(lib, c2, prec, tol):
+    api, PM = lib
+    wl, cat, th = c2
+    plan = api.Plan([PM.cluster_input(wl, cat)], 64, prec)
+    S = 24
+    c = plan.chi2(torch.tensor(th[:S], device="cuda")).cpu().numpy()
+    ref = oracle(wl, cat, th[:S]).numpy()
+    assert np.all(np.abs(c - ref) <= tol * np.abs(ref))
+    api.device_error()
+
+
+def test_full_size_chi2_sampled(lib, c2):
+    """The benchmark configuration: 4096 samples in one persistent launch (graph + tuner),
+    12 seeded samples checked against the oracle one by one."""
+    api, PM = lib
+    wl, cat, th = c2
+    plan = api.Plan([PM.cluster_input(wl, cat)], 4096, "mixed", flags=api.FLAG_GRAPH | api.FLAG_AUTOTUNE)
+    out = plan.chi2(torch.tensor(th, device="cuda"))
+    out2 = plan.chi2(torch.tensor(th, device="cuda"))      # graph re-capture (new theta buffer)
+    assert torch.equal(out, out2)
+    idx = np.concatenate([[0, 4095], np.random.default_rng(9).integers(0, 4096, 10)])
+    ref = oracle(wl, cat, th[idx]).numpy()
+    c = out.cpu().numpy()[idx]
+    assert np.all(np.abs(c - ref) <= 1e-5 * np.abs(ref))
+    api.device_error()
+
+
+def test_graph_and_tuner_do_not_change_results(lib, c2):
+    api, PM = lib
+    wl, cat, th = c2
+    t = torch.tensor(th[:256], device="cuda")
+    base = api.Plan([PM.cluster_input(wl, cat)], 256, "fp64").chi2(t)
+    for flags in (api.FLAG_GRAPH, api.FLAG_AUTOTUNE, api.FLAG_GRAPH | api.FLAG_AUTOTUNE):
+        p = api.Plan([PM.cluster_input(wl, cat)], 256, "fp64", flags=flags)
+        a = p.chi2(t)
+        b = p.chi2(t)                     # replay
+        assert torch.equal(a, b)
+        assert torch.allclose(a, base, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_gradient_matches_oracle_autograd(lib, c2, prec):
+    api, PM = lib
+    wl, cat, th = c2
+    plan = api.Plan([PM.cluster_input(wl, cat)], 16, prec)
+    S = 4
+    c, g = plan.chi2_grad(torch.tensor(th[:S], device="cuda"))
+    cref, gref = oracle(wl, cat, th[:S], grad=True)
+    assert grad_err(g.cpu().numpy(), gref.numpy()) < (1e-8 if prec == "fp64" else 1e-4)
+    assert np.all(np.abs(c.cpu().numpy() - cref.numpy()) <= (1e-10 if prec == "fp64" else 1e-5) * np.abs(cref.numpy()))
+
+
+def test_gradient_matches_central_differences(lib, c2):
+    """Mixed adjoint vs central differences (h = 1e-4 max(|theta_p|, 1), fourth order) of
+    the FP64 chi^2 of the library."""
+    api, PM = lib
+    wl, cat, th = c2
+    plan = api.Plan([PM.cluster_input(wl, cat)], 64, "mixed")
+    plan64 = api.Plan([PM.cluster_input(wl, cat)], 128, "fp64")
+    t0 = torch.tensor(th[:1], device="cuda")
+    _, g = plan.chi2_grad(t0)
+    P = t0.shape[1]
+    rows = []
+    for p in range(P):
+        h = 1e-4 * max(abs(float(t0[0, p])), 1.0)
+        for k in (1, -1, 2, -2):
+            t = t0.clone()
+            t[0, p] += k * h
+            rows.append(t)
+    f = plan64.chi2(torch.cat(rows)).cpu().numpy().reshape(P, 4)
+    fd = np.array([(8 * (f[p, 0] - f[p, 1]) - (f[p, 2] - f[p, 3])) /
+                   (12 * 1e-4 * max(abs(float(t0[0, p])), 1.0)) for p in range(P)])
+    assert grad_err(g.cpu().numpy(), fd[None]) < 1e-4
+
+
+@pytest.fixture(scope="module")
+def c4():
+    wls = W.multicluster_c4()
+    n = 4
+    cats = [W.load_catalogue(f"multicluster_{c:02d}") for c in range(n)]
+    return wls[:n], cats
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_multicluster_gradient_one_launch(lib, c4, prec):
+    """Four clusters of different sizes (22 parameters incl. all six scaling-relation
+    slots) in one launch; 2 samples per cluster against the oracle."""
+    api, PM = lib
+    wls, cats = c4
+    spc = 2
+    ths = [W.sample_thetas(W.replace(w, n_samples=spc), w.seed) for w in wls]
+    plan = api.Plan([PM.cluster_input(w, c) for w, c in zip(wls, cats)], spc * len(wls), prec)
+    c, g = plan.chi2_grad(torch.tensor(np.concatenate(ths), device="cuda"))
+    c, g = c.cpu().numpy(), g.cpu().numpy()
+    for k, (w, cat) in enumerate(zip(wls, cats)):
+        cref, gref = oracle(w, cat, ths[k], grad=True)
+        sl = slice(k * spc, (k + 1) * spc)
+        assert np.all(np.abs(c[sl] - cref.numpy()) <= (1e-10 if prec == "fp64" else 1e-5) * np.abs(cref.numpy()))
+        assert grad_err(g[sl], gref.numpy()) < (1e-8 if prec == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_multiplane_chi2(lib, c2, prec, tol):
+    api, PM = lib
+    _, cat, _ = c2
+    wl = W.multiplane_c3(n_grid=8, n_samples=6)
+    cat3 = W.Catalogue(cat.theta_obs, cat.theta_true, cat.fam_off, np.full(len(cat.fam_zs), 4.0))
+    th = W.sample_thetas(wl, wl.seed)
+    plan = api.Plan([PM.cluster_input(wl, cat3)], 6, prec)
+    c = plan.chi2(torch.tensor(th, device="cuda")).cpu().numpy()
+    ref = oracle(wl, cat3, th).numpy()
+    assert np.all(np.abs(c - ref) <= tol * np.abs(ref))
+    from paper_2609_08649_b300 import _lib as L
+    with pytest.raises(L.LFError) as e:
+        plan.chi2_grad(torch.tensor(th, device="cuda"))
+    assert e.value.status == L.LF_EUNSUPPORTED
+
+
+def test_single_image_family_contributes_zero_and_galaxy_chi2(lib):
+    api, PM = lib
+    wl = W.galaxy_c0()
+    cat = W.load_catalogue("galaxy_sie_shear")
+    wl.params = [W.ParamSpec(0, W.F_X, W.XF_IDENT, 0.0, 0.01, False),
+                 W.ParamSpec(0, W.F_Y, W.XF_IDENT, 0.0, 0.01, False),
+                 W.ParamSpec(0, W.F_EPS, W.XF_IDENT, wl.planes[0].comps[0].eps, 0.01, False),
+                 W.ParamSpec(0, W.F_PA, W.XF_DEG, 30.0, 1.0, False),
+                 W.ParamSpec(1, W.F_B, W.XF_IDENT, 0.05 / 0.6353908, 0.002, False)]
+    wl.n_samples = 8
+    th = W.sample_thetas(wl, 3)
+    # add a one-image family at the end
+    one = W.Catalogue(np.vstack([cat.theta_obs, [[0.3, 0.2]]]), np.vstack([cat.theta_true, [[0.3, 0.2]]]),
+                      np.append(cat.fam_off, cat.fam_off[-1] + 1), np.append(cat.fam_zs, 2.0))
+    for prec in ("fp64", "mixed"):
+        p1 = api.Plan([PM.cluster_input(wl, cat)], 8, prec)
+        p2 = api.Plan([PM.cluster_input(wl, one)], 8, prec)
+        t = torch.tensor(th, device="cuda")
+        a, b = p1.chi2(t), p2.chi2(t)
+        assert torch.equal(a, b)
+        ref = oracle(wl, cat, th).numpy()
+        assert np.all(np.abs(a.cpu().numpy() - ref) <= (1e-10 if prec == "fp64" else 1e-5) * ref)
+        _, g = p2.chi2_grad(t)
+        _, gref = oracle(wl, cat, th, grad=True)
+        assert grad_err(g.cpu().numpy(), gref.numpy()) < (1e-8 if prec == "fp64" else 1e-4)
+
+
+def test_plan_validation(lib, c2):
+    api, PM = lib
+    from paper_2609_08649_b300 import _lib as L
+    wl, cat, th = c2
+    plan = api.Plan([PM.cluster_input(wl, cat)], 8, "mixed")
+    with pytest.raises(L.LFError):
+        plan.chi2(torch.tensor(th[:9], device="cuda"))          # S > max_samples
+    ci = PM.cluster_input(wl, cat)
+    ci.fam_ratio[0] = 1.5
+    with pytest.raises(L.LFError) as e:
+        api.Plan([ci], 8, "mixed")
+    assert e.value.status == L.LF_EINVAL
+    ci = PM.cluster_input(wl, cat)
+    ci.p_field[0] = 9
+    with pytest.raises(L.LFError):
+        api.Plan([ci], 8, "mixed")
+    plan2 = api.Plan([PM.cluster_input(wl, cat), PM.cluster_input(wl, cat)], 8, "mixed")
+    with pytest.raises(L.LFError):
+        plan2.chi2(torch.tensor(th[:3], device="cuda"))         # not a multiple of 2 clusters
+
+
+def test_autograd_function(lib, c2):
+    api, PM = lib
+    wl, cat, th = c2
+    plan = api.Plan([PM.cluster_input(wl, cat)], 4, "fp64")
+    t = torch.tensor(th[:4], device="cuda", requires_grad=True)
+    y = api.chi2(t, plan)
+    y.sum().backward()
+    _, g = plan.chi2_grad(t.detach())
+    assert torch.allclose(t.grad, g)
