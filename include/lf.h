@@ -58,10 +58,14 @@ typedef enum {
 } lf_kind;
 
 /* LF_FP64: every operation in FP64, one thread per position (the plain comparator).
- * LF_MIXED: per-component closed forms in FP32 on offsets taken in float-float, FP32 sums
- * per component chunk folded into float-float accumulators, then FP64 for det A, mu, the
- * multi-plane Jacobian product and the chi^2 reduction. */
-typedef enum { LF_FP64 = 0, LF_MIXED = 1 } lf_precision;
+ * LF_MIXED: per-component closed forms in FP32 on offsets taken in float-float (the
+ * deflection of elliptical isothermal components and of the shear in float-float), FP32
+ * sums per member chunk folded into float-float accumulators, then FP64 for det A, mu, the
+ * multi-plane Jacobian product and the chi^2 reduction.
+ * LF_FF: as LF_MIXED, but the deflection of every member is also carried in float-float
+ * (about 48 significant bits on the FP32 pipe) and accumulated in float-float; psi_ij
+ * stays FP32.  Spherical NFW components stay FP32 in both mixed tiers. */
+typedef enum { LF_FP64 = 0, LF_MIXED = 1, LF_FF = 2 } lf_precision;
 
 /* One explicit component, 64 bytes (device arrays of these are staged into shared
  * memory by bulk copy, so the array must be 16-byte aligned). */

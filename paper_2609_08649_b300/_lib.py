@@ -7,11 +7,11 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liblf.so")
+LIB_PATH = os.environ.get("LF_LIBRARY") or os.path.join(HERE, "liblf.so")
 
 LF_OK, LF_EINVAL, LF_ECUDA, LF_ENOMEM, LF_ETIMEOUT, LF_EUNSUPPORTED = range(6)
 LF_SIE, LF_DPIE, LF_NFW, LF_SHEAR = 1, 2, 3, 4
-LF_FP64, LF_MIXED = 0, 1
+LF_FP64, LF_MIXED, LF_FF = 0, 1, 2
 STATUS_NAMES = {0: "LF_OK", 1: "LF_EINVAL", 2: "LF_ECUDA", 3: "LF_ENOMEM", 4: "LF_ETIMEOUT",
                 5: "LF_EUNSUPPORTED"}
 

@@ -11,7 +11,7 @@ import torch
 from . import _lib as L
 from .model import DevicePlane, grid_struct
 
-PRECISION = {"fp64": L.LF_FP64, "mixed": L.LF_MIXED}
+PRECISION = {"fp64": L.LF_FP64, "mixed": L.LF_MIXED, "ff": L.LF_FF}
 
 
 def _stream():

@@ -31,12 +31,17 @@ namespace lf {
 constexpr int LF_MAX_P = 64;
 constexpr int LF_MAX_FREE = 16;
 constexpr int LF_MAX_IMG = 2048;
-constexpr int LF_HDR = 512;          // shared header: barrier, item index, reduction scratch
+constexpr int LF_TAB_OFF = 512;      // shared header: barrier, item index, reduction scratch
+constexpr int LF_HDR = LF_TAB_OFF + 2 * LF_TAB_N * 8;   // then the float-float function tables
 constexpr double LF_C_KMS = 299792.458;
 constexpr double LF_ARCSEC_PER_RAD = 206264.80624709636;
 constexpr double LF_PI = 3.14159265358979323846;
 
-struct MemPreF { float xh, xl, yh, yl, fb, fs, fa, lnl; };
+// Per-cluster member tables built by the plan: (L/L*)^(2 lam0), ^beta0, ^alpha0 at the base
+// exponents (float-float for the mixed tier) and ln(L/L*).  A sampled exponent e changes a
+// factor to f0 exp((e - e0) k ln L), evaluated as f0 (1 + expm1(.)) so that the FP32 rounding
+// applies to the small perturbation only.
+struct MemPreF { float xh, xl, yh, yl, fb, fs, fa, lnl, fbl, fsl, fal, pad; };
 struct MemPreD { double x, y, fb, fs, fa, lnl, pad0, pad1; };
 
 struct PlaneDesc {
@@ -189,19 +194,29 @@ __device__ __forceinline__ T contract(const Out5<Dual<T, N>>& o, const T* cot, i
 }
 
 // ------------------------------------------------------------------ the kernel -----
-template <bool MIXED, bool GRAD>
+// Member accessors shared by the two member records.
+template <class T> __device__ __forceinline__ T mem_s(const MemT<T>& m) { return m.s; }
+template <class T> __device__ __forceinline__ T mem_a(const MemT<T>& m) { return m.a; }
+__device__ __forceinline__ float mem_s(const MemX& m) { return m.sh; }
+__device__ __forceinline__ float mem_a(const MemX& m) { return m.ah; }
+
+template <int MODE, bool GRAD>   // MODE: LF_FP64, LF_MIXED or LF_FF
 __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cds,
                                               const int* __restrict__ corder, int spc, int S,
                                               const double* __restrict__ theta, double* chi2,
                                               double* grad, int* counter, int chunk) {
+  constexpr bool MIXED = MODE != LF_FP64;
   typedef typename std::conditional<MIXED, float, double>::type T;
-  typedef typename std::conditional<MIXED, MemPreF, MemPreD>::type MemPre;
+  typedef typename std::conditional<MODE == LF_MIXED, MemPreF, MemPreD>::type MemPre;
+  typedef typename std::conditional<MODE == LF_FF, MemX, MemT<T>>::type Mem;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   int* s_item = reinterpret_cast<int*>(smem + 8);
   double* scratch = reinterpret_cast<double*>(smem + 16);   // 32 doubles
   const int tid = threadIdx.x;
+  float2* tab = reinterpret_cast<float2*>(smem + LF_TAB_OFF);
   if (tid == 0) mbar_init(bar, 1);
+  init_ff_tables(tab);
   __syncthreads();
   uint32_t phase = 0;
   int cur = -1;
@@ -272,16 +287,28 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
       const bool beta_free = sampled && C.scal_p[LF_S_BETA] >= 0;
       const bool alpha_free = sampled && C.scal_p[LF_S_ALPHA] >= 0;
       const MemPre* mp = reinterpret_cast<const MemPre*>(smem + P.off_mpre);
-      MemT<T>* dm = reinterpret_cast<MemT<T>*>(smem + P.off_dm);
+      Mem* dm = reinterpret_cast<Mem*>(smem + P.off_dm);
       for (int i = tid; i < P.nm; i += blockDim.x) {
         const MemPre& m = mp[i];
-        T fb = lam_free ? (T)exp((T)(2.0 * sc.lam) * (T)m.lnl) : (T)m.fb;
-        T fs = beta_free ? (T)exp((T)sc.beta * (T)m.lnl) : (T)m.fs;
-        T fa = alpha_free ? (T)exp((T)sc.alpha * (T)m.lnl) : (T)m.fa;
+        if constexpr (MODE == LF_FF) {
+          const double fb = lam_free ? exp(2.0 * sc.lam * m.lnl) : m.fb;
+          const double fs = beta_free ? exp(sc.beta * m.lnl) : m.fs;
+          const double fa = alpha_free ? exp(sc.alpha * m.lnl) : m.fa;
+          digest_member_x(m.x, m.y, sc.b_star * fb, sc.core_star * fs, sc.cut_star * fa, m.lnl,
+                          dm[i], fb, fs);
+          continue;
+        } else {
+        T fb, fs, fa;
         MemT<T> d;
-        if constexpr (MIXED) {
+        if constexpr (MODE == LF_MIXED) {
+          fb = lam_free ? m.fb + fmaf(m.fb, expm1f((float)(2.0 * (sc.lam - P.sc.lam)) * m.lnl), m.fbl) : m.fb;
+          fs = beta_free ? m.fs + fmaf(m.fs, expm1f((float)(sc.beta - P.sc.beta) * m.lnl), m.fsl) : m.fs;
+          fa = alpha_free ? m.fa + fmaf(m.fa, expm1f((float)(sc.alpha - P.sc.alpha) * m.lnl), m.fal) : m.fa;
           d.xh = m.xh; d.xl = m.xl; d.yh = m.yh; d.yl = m.yl;
         } else {
+          fb = lam_free ? exp(2.0 * sc.lam * m.lnl) : m.fb;
+          fs = beta_free ? exp(sc.beta * m.lnl) : m.fs;
+          fa = alpha_free ? exp(sc.alpha * m.lnl) : m.fa;
           d.xh = m.x; d.xl = 0; d.yh = m.y; d.yl = 0;
         }
         d.b = (T)sc.b_star * fb;
@@ -293,6 +320,7 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
         d.a2 = d.a * d.a;
         d.loglr = (T)m.lnl;
         dm[i] = d;
+        }
       }
     }
     __syncthreads();
@@ -303,7 +331,7 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
     for (int j = 0; j < C.np; ++j) {
       const PlaneDesc& P = C.pl[j];
       const CompT<T>* dc = reinterpret_cast<const CompT<T>*>(smem + P.off_dc);
-      const MemT<T>* dm = reinterpret_cast<const MemT<T>*>(smem + P.off_dm);
+      const Mem* dm = reinterpret_cast<const Mem*>(smem + P.off_dm);
       const int K = P.nc + P.nm;
       for (int base = 0; base < ntask; base += blockDim.x) {
         const int t = base + tid;
@@ -327,7 +355,10 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
             split_ff(y, yh[0], yl[0]);
             ff acc[5][1];
             for (int q = 0; q < 5; ++q) acc[q][0] = ff_zero();
-            accumulate_mixed<1>(dc, P.nc, dm, P.nm, k0, k1, chunk, xh, xl, yh, yl, acc);
+            if constexpr (MODE == LF_FF)
+              accumulate_ext<1>(dc, P.nc, dm, P.nm, k0, k1, xh, xl, yh, yl, tab, acc);
+            else
+              accumulate_mixed<1>(dc, P.nc, dm, P.nm, k0, k1, chunk, xh, xl, yh, yl, tab, acc);
             for (int q = 0; q < 5; ++q) v[q] = ff_to_double(acc[q][0]);
           } else {
             accumulate_fp64(dc, P.nc, dm, P.nm, k0, k1, x, y, v);
@@ -458,7 +489,7 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
       }
       __syncthreads();
       const PlaneDesc& P = C.pl[0];
-      const MemT<T>* dm = reinterpret_cast<const MemT<T>*>(smem + P.off_dm);
+      const Mem* dm = reinterpret_cast<const Mem*>(smem + P.off_dm);
       const int K = P.nc + P.nm;
       const bool mem_grad = (C.scal_plane == 0) && C.scal_free;
       lf_scaling ssc = P.sc;
@@ -491,9 +522,10 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
           const int m0 = max(k0, P.nc) - P.nc, m1 = min(k1, K) - P.nc;
           T gs[6] = {0, 0, 0, 0, 0, 0};
           for (int m = m0; m < m1; ++m) {
-            const MemT<T>& M = dm[m];
+            const Mem& M = dm[m];
             typedef Dual<T, 2> D2;
-            D2 sd = D2::var(M.s, 0), ad = D2::var(M.a, 1);
+            const T Ms = mem_s(M), Ma = mem_a(M);
+            D2 sd = D2::var(Ms, 0), ad = D2::var(Ma, 1);
             Out5<D2> o;
             T dx, dy;
             if constexpr (MIXED) {
@@ -510,13 +542,13 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
             const T Gb = contract(o, cot, -1);
             const T Gs = M.b * contract(o, cot, 0);
             const T Ga = M.b * contract(o, cot, 1);
-            const T fa = M.a * inv_cut_star;
+            const T fa = Ma * inv_cut_star;
             gs[LF_S_BSTAR] += Gb * M.fb;
             gs[LF_S_LAM] += Gb * M.b * (T)2 * M.loglr;
             gs[LF_S_CORESTAR] += Gs * M.fs;
-            gs[LF_S_BETA] += Gs * M.s * M.loglr;
+            gs[LF_S_BETA] += Gs * Ms * M.loglr;
             gs[LF_S_CUTSTAR] += Ga * fa;
-            gs[LF_S_ALPHA] += Ga * M.a * M.loglr;
+            gs[LF_S_ALPHA] += Ga * Ma * M.loglr;
           }
           for (int q = 0; q < 6; ++q) {
             const int p = C.scal_p[q];
@@ -612,14 +644,17 @@ static int choose_ks(int n_img, int K, int block, int cap) {
 }
 
 static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap) {
-  const bool mixed = precision == LF_MIXED;
+  const bool mixed = precision != LF_FP64;
+  const uint32_t pre_sz = precision == LF_MIXED ? sizeof(MemPreF) : sizeof(MemPreD);
+  const uint32_t mem_sz = precision == LF_FF ? sizeof(MemX) : precision == LF_MIXED ? sizeof(MemT<float>)
+                                                                                   : sizeof(MemT<double>);
   uint32_t o = LF_HDR;
   for (int j = 0; j < C.np; ++j) {
     PlaneDesc& P = C.pl[j];
     o = (o + 15u) & ~15u; P.off_rawc = o; o += (uint32_t)P.nc * 64u;
-    o = (o + 15u) & ~15u; P.off_mpre = o; o += (uint32_t)P.nm * (mixed ? sizeof(MemPreF) : sizeof(MemPreD));
+    o = (o + 15u) & ~15u; P.off_mpre = o; o += (uint32_t)P.nm * pre_sz;
     o = (o + 15u) & ~15u; P.off_dc = o; o += (uint32_t)P.nc * (mixed ? sizeof(CompT<float>) : sizeof(CompT<double>));
-    o = (o + 15u) & ~15u; P.off_dm = o; o += (uint32_t)P.nm * (mixed ? sizeof(MemT<float>) : sizeof(MemT<double>));
+    o = (o + 15u) & ~15u; P.off_dm = o; o += (uint32_t)P.nm * mem_sz;
   }
   C.img_stride = C.np > 1 ? 16 + 6 * C.np : 14;
   o = (o + 15u) & ~15u; C.off_img = o; o += (uint32_t)C.n_img * C.img_stride * 8u;
@@ -648,8 +683,12 @@ static lf_status relayout(lf_plan* pl) {
     LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem));
     return LF_OK;
   };
-  const void* kc = pl->precision == LF_MIXED ? (const void*)k_chi2<true, false> : (const void*)k_chi2<false, false>;
-  const void* kg = pl->precision == LF_MIXED ? (const void*)k_chi2<true, true> : (const void*)k_chi2<false, true>;
+  const void* kc = pl->precision == LF_MIXED ? (const void*)k_chi2<LF_MIXED, false>
+                   : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, false>
+                                             : (const void*)k_chi2<LF_FP64, false>;
+  const void* kg = pl->precision == LF_MIXED ? (const void*)k_chi2<LF_MIXED, true>
+                   : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, true>
+                                             : (const void*)k_chi2<LF_FP64, true>;
   LF_TRY(kset(kc));
   LF_TRY(kset(kg));
   LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kc, pl->block, pl->smem));
@@ -670,7 +709,7 @@ static lf_status build_cluster(lf_plan* pl, const lf_cluster& cl, ClusterDesc& C
   if (cl.n_planes > 1 && !cl.ratios) return fail(LF_EINVAL, "multi-plane cluster needs ratios");
   if (!cl.arcsec_per_kpc) return fail(LF_EINVAL, "arcsec_per_kpc is NULL");
   C.np = cl.n_planes;
-  const bool mixed = pl->precision == LF_MIXED;
+  const bool mixed = pl->precision == LF_MIXED;   // FP32 member pre-table (LF_FF keeps FP64)
   std::vector<int> comp_base(C.np + 1, 0);
   std::vector<std::vector<lf_comp>> comps(C.np);
   cost = 0.0;
@@ -699,10 +738,11 @@ static lf_status build_cluster(lf_plan* pl, const lf_cluster& cl, ClusterDesc& C
         double lnl = mem[i].log_l * LN10;
         split_ff(mem[i].x, pre[i].xh, pre[i].xl);
         split_ff(mem[i].y, pre[i].yh, pre[i].yl);
-        pre[i].fb = (float)std::exp(2.0 * P.sc.lam * lnl);
-        pre[i].fs = (float)std::exp(P.sc.beta * lnl);
-        pre[i].fa = (float)std::exp(P.sc.alpha * lnl);
+        split_ff(std::exp(2.0 * P.sc.lam * lnl), pre[i].fb, pre[i].fbl);
+        split_ff(std::exp(P.sc.beta * lnl), pre[i].fs, pre[i].fsl);
+        split_ff(std::exp(P.sc.alpha * lnl), pre[i].fa, pre[i].fal);
         pre[i].lnl = (float)lnl;
+        pre[i].pad = 0.f;
         if (!std::isfinite(mem[i].x) || !std::isfinite(mem[i].y) || !std::isfinite(lnl))
           return fail(LF_EINVAL, "plane %d member %d is not finite", j, i);
       }
@@ -805,24 +845,27 @@ static lf_status build_cluster(lf_plan* pl, const lf_cluster& cl, ClusterDesc& C
   return LF_OK;
 }
 
+template <int MODE>
+static void launch_mode(lf_plan* pl, const double* theta, int S, double* chi2, double* grad,
+                        cudaStream_t st, int spc) {
+  if (grad) {
+    int g = std::min(pl->grid_grad, S);
+    k_chi2<MODE, true><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
+                                                       grad, pl->d_counter, g_member_chunk);
+  } else {
+    int g = std::min(pl->grid_chi2, S);
+    k_chi2<MODE, false><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
+                                                        nullptr, pl->d_counter, g_member_chunk);
+  }
+}
+
 static lf_status launch_chi2(lf_plan* pl, const double* theta, int S, double* chi2, double* grad,
                              cudaStream_t st) {
   const int spc = S / pl->n_clusters;
   LF_CUDA(cudaMemsetAsync(pl->d_counter, 0, sizeof(int), st));
-  const bool mixed = pl->precision == LF_MIXED;
-  if (grad) {
-    int g = std::min(pl->grid_grad, S);
-    if (mixed)
-      k_chi2<true, true><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2, grad, pl->d_counter, g_member_chunk);
-    else
-      k_chi2<false, true><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2, grad, pl->d_counter, g_member_chunk);
-  } else {
-    int g = std::min(pl->grid_chi2, S);
-    if (mixed)
-      k_chi2<true, false><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2, nullptr, pl->d_counter, g_member_chunk);
-    else
-      k_chi2<false, false><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2, nullptr, pl->d_counter, g_member_chunk);
-  }
+  if (pl->precision == LF_MIXED) launch_mode<LF_MIXED>(pl, theta, S, chi2, grad, st, spc);
+  else if (pl->precision == LF_FF) launch_mode<LF_FF>(pl, theta, S, chi2, grad, st, spc);
+  else launch_mode<LF_FP64>(pl, theta, S, chi2, grad, st, spc);
   LF_CUDA(cudaGetLastError());
   return LF_OK;
 }
@@ -910,7 +953,7 @@ extern "C" lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, i
   *out = nullptr;
   if (!clusters || n_clusters < 1) return fail(LF_EINVAL, "need at least one cluster");
   if (max_samples < n_clusters) return fail(LF_EINVAL, "max_samples must be >= n_clusters");
-  if (precision != LF_FP64 && precision != LF_MIXED) return fail(LF_EINVAL, "unknown precision");
+  if (precision < LF_FP64 || precision > LF_FF) return fail(LF_EINVAL, "unknown precision");
   if (flags & ~3) return fail(LF_EINVAL, "unknown flags");
   lf_plan* pl = new lf_plan();
   pl->n_clusters = n_clusters;

@@ -18,6 +18,9 @@
 #include <math.h>
 
 #define LF_INLINE __device__ __forceinline__
+#ifndef LF_NOINLINE
+#define LF_NOINLINE __device__ __noinline__
+#endif
 
 // ------------------------------------------------------------------ scalar math ----
 LF_INLINE float lf_rsqrt(float x) { return rsqrtf(x); }
@@ -55,7 +58,7 @@ LF_INLINE void two_sum(float a, float b, float& s, float& e) {
 }
 
 // acc += x (x a plain float); the low word collects the rounding error of the high word.
-LF_INLINE void ff_add(ff& acc, float x) {
+LF_INLINE void ff_acc(ff& acc, float x) {
   float s, e;
   two_sum(acc.hi, x, s, e);
   acc.hi = s;
@@ -63,6 +66,134 @@ LF_INLINE void ff_add(ff& acc, float x) {
 }
 
 LF_INLINE double ff_to_double(const ff& a) { return (double)a.hi + (double)a.lo; }
+
+// Float-float arithmetic (Dekker 1971; Knuth TAOCP 4.2.2): each value is an unevaluated sum
+// hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits, built from FP32 operations and
+// the exact product error fmaf(a, b, -a b).
+LF_INLINE ff ff_make(float hi, float lo) { ff r; r.hi = hi; r.lo = lo; return r; }
+LF_INLINE ff fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = a + b;
+  return ff_make(s, b - (s - a));
+}
+LF_INLINE ff ff_add(const ff& a, const ff& b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e += a.lo + b.lo;
+  return fast_two_sum(s, e);
+}
+LF_INLINE ff ff_neg(const ff& a) { return ff_make(-a.hi, -a.lo); }
+LF_INLINE ff ff_sub(const ff& a, const ff& b) { return ff_add(a, ff_neg(b)); }
+LF_INLINE ff ff_add_f(const ff& a, float b) {
+  float s, e;
+  two_sum(a.hi, b, s, e);
+  e += a.lo;
+  return fast_two_sum(s, e);
+}
+LF_INLINE ff ff_mul(const ff& a, const ff& b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return fast_two_sum(p, e);
+}
+LF_INLINE ff ff_mul_f(const ff& a, float b) {
+  float p = a.hi * b;
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  return fast_two_sum(p, e);
+}
+LF_INLINE ff ff_sqr(const ff& a) {
+  float p = a.hi * a.hi;
+  float e = fmaf(a.hi, a.hi, -p);
+  e = fmaf(2.0f * a.hi, a.lo, e);
+  return fast_two_sum(p, e);
+}
+// 1 / a: FP32 reciprocal and one Newton step r + r (1 - a r) with the residual in float-float.
+LF_INLINE ff ff_rcp(const ff& a) {
+  float r = __fdividef(1.0f, a.hi);
+  float e = -fmaf(a.hi, r, -1.0f);
+  e = fmaf(-a.lo, r, e);
+  return fast_two_sum(r, r * e);
+}
+// a / b: the FP32 quotient refined twice with the exact remainder.
+LF_INLINE ff ff_div(const ff& a, const ff& b) {
+  float r = __fdividef(1.0f, b.hi);
+  float q1 = a.hi * r;
+  ff rem = ff_sub(a, ff_mul_f(b, q1));
+  float q2 = rem.hi * r;
+  ff q = fast_two_sum(q1, q2);
+  rem = ff_sub(a, ff_mul(b, q));
+  return ff_add_f(q, rem.hi * r);
+}
+// sqrt(a) for a > 0: FP32 root plus one Newton correction with the exact square error.
+LF_INLINE ff ff_sqrt(const ff& a) {
+  float ir = rsqrtf(a.hi);
+  float s = a.hi * ir;
+  float p = s * s;
+  float e = fmaf(s, s, -p);
+  float r = ((a.hi - p) - e) + a.lo;
+  return fast_two_sum(s, r * 0.5f * ir);
+}
+LF_INLINE ff ff_from_double(double v) {
+  float h = (float)v;
+  return ff_make(h, (float)(v - (double)h));
+}
+
+// atan and atanh in float-float by the addition formulas
+//   atan(z)  = atan(c)  + atan((z - c) / (1 + z c)),
+//   atanh(z) = atanh(c) + atanh((z - c) / (1 - z c)),
+// with c = k/64 the nearest table point (tables of atan(k/64), atanh(k/64) held in shared
+// memory as float-float, k = 0..64), and the reduced argument t handled by its odd Taylor
+// series t -+ t^3/3 + t^5/5 -+ ... : t exactly in float-float, the higher terms (relatively
+// below t^2/3) in FP32.  |z| > 1 for atan uses atan(z) = pi/2 - atan(1/z).
+#define LF_TAB_N 65
+LF_INLINE float series_corr(float t2, float sgn) {
+  // t^2 (-+1/3 + t^2 (1/5 -+ t^2 (1/7 + ...)))  (sgn = -1 atan, +1 atanh), through t^13
+  float p = sgn * (1.0f / 13.0f);
+  p = fmaf(p, t2, 1.0f / 11.0f);
+  p = fmaf(p, t2 * sgn, 1.0f / 9.0f);
+  p = fmaf(p, t2 * sgn, 1.0f / 7.0f);
+  p = fmaf(p, t2 * sgn, 1.0f / 5.0f);
+  p = fmaf(p, t2 * sgn, 1.0f / 3.0f);
+  return p * t2 * sgn;
+}
+LF_INLINE ff ff_atan(const ff& z, const float2* tab) {
+  const bool neg = z.hi < 0.f;
+  ff a = neg ? ff_neg(z) : z;
+  const bool inv = a.hi > 1.f;
+  if (inv) a = ff_div(ff_make(1.f, 0.f), a);
+  const int k = __float2int_rn(a.hi * 64.f);
+  const float c = (float)k * (1.0f / 64.0f);
+  ff num = ff_add_f(a, -c);
+  ff den = ff_add_f(ff_mul_f(a, c), 1.0f);
+  ff t = ff_div(num, den);
+  ff r = ff_add_f(t, t.hi * series_corr(t.hi * t.hi, -1.f));
+  r = ff_add(r, ff_make(tab[k].x, tab[k].y));
+  if (inv) r = ff_sub(ff_make(1.5707963705062866f, -4.371138828673793e-08f), r);
+  return neg ? ff_neg(r) : r;
+}
+LF_INLINE ff ff_atanh(const ff& z, const float2* tab) {
+  const bool neg = z.hi < 0.f;
+  ff a = neg ? ff_neg(z) : z;
+  int k = __float2int_rn(a.hi * 64.f);
+  k = k > 63 ? 63 : k;
+  const float c = (float)k * (1.0f / 64.0f);
+  ff num = ff_add_f(a, -c);
+  ff den = ff_add_f(ff_mul_f(a, -c), 1.0f);
+  ff t = ff_div(num, den);
+  ff r = ff_add_f(t, t.hi * series_corr(t.hi * t.hi, 1.f));
+  r = ff_add(r, ff_make(tab[LF_TAB_N + k].x, tab[LF_TAB_N + k].y));
+  return neg ? ff_neg(r) : r;
+}
+// Fills the two tables (2 * LF_TAB_N float2) from FP64 atan / atanh; whole block.
+__device__ inline void init_ff_tables(float2* tab) {
+  for (int i = threadIdx.x; i < 2 * LF_TAB_N; i += blockDim.x) {
+    const int k = i % LF_TAB_N;
+    const double c = k / 64.0;
+    const double v = (i < LF_TAB_N) ? atan(c) : (k < 64 ? atanh(c) : 0.0);
+    const float h = (float)v;
+    tab[i] = make_float2(h, (float)(v - (double)h));
+  }
+}
 
 // Splits a double into hi + lo floats (hi = nearest float, lo = nearest float of the rest).
 __host__ __device__ inline void split_ff(double v, float& hi, float& lo) {
@@ -119,15 +250,25 @@ LF_INLINE void cored_round(T r2, T s, T s2, T& kbar, T& t) {
   t = -P * P * iS;
 }
 
-// Round dPIE / pseudo-Jaffe of strength b: kbar = b (P - Q), t = b (Q^2/R - P^2/S).
+// Round dPIE / pseudo-Jaffe of strength b, core s and cut a.  With S = sqrt(s^2 + r^2),
+// R = sqrt(a^2 + r^2), P = 1/(S + s), Q = 1/(R + a), the mean convergence b (P - Q) is
+// written without the far-field cancellation (which loses log2(r / (a - s)) bits):
+//   kbar = b (a - s) [(a + s)/(R + S) + 1] P Q,
+// using R - S = (a^2 - s^2)/(R + S).  PQ takes one reciprocal of (S + s)(R + a), and
+// P = PQ (R + a), Q = PQ (S + s).  The tensor term t = 2 (kappa - kbar)/r^2 =
+// b (Q^2/R - P^2/S) cancels only where it is small (|t r^2| ~ 2 b (a - s)/r^2).
+// alpha = kbar x, psi_ij = kbar delta_ij + t x_i x_j.
 template <class T>
 LF_INLINE void pje_round(T dx, T dy, T b, T s, T s2, T a, T a2, Out5<T>& o) {
   T r2 = lf_fma(dx, dx, dy * dy);
-  T k1, t1, k2, t2;
-  cored_round(r2, s, s2, k1, t1);
-  cored_round(r2, a, a2, k2, t2);
-  T kbar = b * (k1 - k2);
-  T t = b * (t1 - t2);
+  T S2 = s2 + r2, R2 = a2 + r2;
+  T iS = lf_rsqrt(S2), iR = lf_rsqrt(R2);
+  T S = S2 * iS, R = R2 * iR;
+  T Ss = S + s, Ra = R + a;
+  T PQ = lf_rcp(Ss * Ra);
+  T P = PQ * Ra, Q = PQ * Ss;
+  T kbar = b * (a - s) * PQ * lf_fma(a + s, lf_rcp(R + S), (T)1);
+  T t = b * (Q * Q * iR - P * P * iS);
   o.ax = kbar * dx;
   o.ay = kbar * dy;
   o.pxx = lf_fma(t * dx, dx, kbar);
@@ -219,6 +360,9 @@ template <class T> struct CompT {
   T s1, s1sq, q2s1, D01;  // core terms
   T s2, s2sq, q2s2, D02;  // cut terms (dPIE)
   T irs;                  // NFW 1/rs
+  // low words of the float-float constants used by the extended-precision deflection of
+  // elliptical components and the shear (zero for double)
+  T lc, lsn, lb, lq2, le, lqe, ls1, ls1sq, lq2s1, ls2, ls2sq, lq2s2;
 };
 
 // A cluster member (round pseudo-Jaffe) prepared for evaluation in precision T.
@@ -257,6 +401,16 @@ __host__ __device__ inline void digest_comp(int kind, double x, double y, double
   c.s2 = (T)cut; c.s2sq = (T)(cut * cut); c.q2s2 = (T)(q * q * cut);
   c.D02 = (T)((1.0 + q * q) * cut * cut);
   c.irs = (T)(kind == K_NFW && core > 0 ? 1.0 / core : 0.0);
+  // low words: v - (T)v (zero when T is double)
+  const double cc = kind == K_SHEAR ? cos(2.0 * pa) : cos(pa);
+  const double ss = kind == K_SHEAR ? sin(2.0 * pa) : sin(pa);
+  const double q2 = q * q, qe = e > 0 ? q / e : 0.0;
+  c.lc = (T)(cc - (double)c.c); c.lsn = (T)(ss - (double)c.sn); c.lb = (T)(b - (double)c.b);
+  c.lq2 = (T)(q2 - (double)c.q2); c.le = (T)(e - (double)c.e); c.lqe = (T)(qe - (double)c.qe);
+  c.ls1 = (T)(core - (double)c.s1); c.ls1sq = (T)(core * core - (double)c.s1sq);
+  c.lq2s1 = (T)(q2 * core - (double)c.q2s1);
+  c.ls2 = (T)(cut - (double)c.s2); c.ls2sq = (T)(cut * cut - (double)c.s2sq);
+  c.lq2s2 = (T)(q2 * cut - (double)c.q2s2);
 }
 
 template <class T>
@@ -323,6 +477,145 @@ LF_INLINE void eval_comp(const CompT<T>& c, T dx, T dy, Out5<T>& o) {
 template <class T>
 LF_INLINE void eval_member(const MemT<T>& m, T dx, T dy, Out5<T>& o) {
   pje_round(dx, dy, m.b, m.s, m.s2, m.a, m.a2, o);
+}
+
+// ------------------------------------- extended-precision deflection (mixed path) ---
+// Offset from a centre as float-float: (x_h - c_h) with its exact rounding error, plus the
+// difference of the low words.
+LF_INLINE ff offset_ff(float ph, float pl, float ch, float cl) {
+  float s, e;
+  two_sum(ph, -ch, s, e);
+  e += pl - cl;
+  return fast_two_sum(s, e);
+}
+
+// psi_ij of a unit-strength softened isothermal ellipsoid in its (u, v) frame, FP32.
+LF_INLINE void sie_psi(float u, float v, float q, float q2, float s, float s2, float D0,
+                       float& puu, float& pvv, float& puv) {
+  float uu = u * u, vv = v * v;
+  float p2 = fmaf(q2, s2 + uu, vv);
+  float ip = rsqrtf(p2);
+  float psi = p2 * ip;
+  float D = D0 + 2.f * psi * s + uu + vv;
+  float f = q * ip * __fdividef(1.0f, D);
+  float sp = s * psi;
+  puu = f * (q2 * s2 + vv + sp);
+  pvv = f * (s2 + uu + sp);
+  puv = -f * u * v;
+}
+
+// alpha of a unit-strength softened isothermal ellipsoid in its (u, v) frame, float-float.
+LF_INLINE void sie_alpha_ff(const ff& u, const ff& v, const ff& uu, const ff& vv, const ff& q2,
+                            const ff& e, const ff& qe, const ff& s, const ff& ssq, const ff& q2s,
+                            const float2* tab, ff& au, ff& av) {
+  ff p2 = ff_add(ff_mul(q2, ff_add(ssq, uu)), vv);
+  ff psi = ff_sqrt(p2);
+  ff z1 = ff_div(ff_mul(e, u), ff_add(psi, s));
+  ff z2 = ff_div(ff_mul(e, v), ff_add(psi, q2s));
+  au = ff_mul(qe, ff_atan(z1, tab));
+  av = ff_mul(qe, ff_atanh(z2, tab));
+}
+
+// One explicit component for the mixed path: alpha in float-float for elliptical
+// isothermal components (SIE, dPIE) and the shear, FP32 otherwise; psi_ij in FP32.
+LF_NOINLINE void eval_comp_mixed(const CompT<float>& c, float ph_x, float pl_x, float ph_y,
+                               float pl_y, const float2* tab, ff& ax, ff& ay, Out5<float>& o) {
+  const bool ell = (c.kind == K_SIE || c.kind == K_DPIE) && !c.round;
+  if (!ell && c.kind != K_SHEAR) {
+    float dx = offset_of(ph_x, pl_x, c.xh, c.xl);
+    float dy = offset_of(ph_y, pl_y, c.yh, c.yl);
+    eval_comp(c, dx, dy, o);
+    ax = ff_make(o.ax, 0.f);
+    ay = ff_make(o.ay, 0.f);
+    return;
+  }
+  ff dx = offset_ff(ph_x, pl_x, c.xh, c.xl);
+  ff dy = offset_ff(ph_y, pl_y, c.yh, c.yl);
+  const ff cc = ff_make(c.c, c.lc), sn = ff_make(c.sn, c.lsn), b = ff_make(c.b, c.lb);
+  if (c.kind == K_SHEAR) {
+    ff g1 = ff_mul(b, cc), g2 = ff_mul(b, sn);
+    ax = ff_add(ff_mul(g1, dx), ff_mul(g2, dy));
+    ay = ff_sub(ff_mul(g2, dx), ff_mul(g1, dy));
+    o.pxx = g1.hi; o.pyy = -g1.hi; o.pxy = g2.hi;
+    return;
+  }
+  ff u = ff_add(ff_mul(cc, dx), ff_mul(sn, dy));
+  ff v = ff_sub(ff_mul(cc, dy), ff_mul(sn, dx));
+  ff uu = ff_mul(u, u), vv = ff_mul(v, v);
+  const ff q2 = ff_make(c.q2, c.lq2), e = ff_make(c.e, c.le), qe = ff_make(c.qe, c.lqe);
+  ff au, av;
+  sie_alpha_ff(u, v, uu, vv, q2, e, qe, ff_make(c.s1, c.ls1), ff_make(c.s1sq, c.ls1sq),
+               ff_make(c.q2s1, c.lq2s1), tab, au, av);
+  float puu, pvv, puv;
+  sie_psi(u.hi, v.hi, c.q, c.q2, c.s1, c.s1sq, c.D01, puu, pvv, puv);
+  if (c.kind == K_DPIE) {
+    ff bu, bv;
+    sie_alpha_ff(u, v, uu, vv, q2, e, qe, ff_make(c.s2, c.ls2), ff_make(c.s2sq, c.ls2sq),
+                 ff_make(c.q2s2, c.lq2s2), tab, bu, bv);
+    au = ff_sub(au, bu);
+    av = ff_sub(av, bv);
+    float quu, qvv, quv;
+    sie_psi(u.hi, v.hi, c.q, c.q2, c.s2, c.s2sq, c.D02, quu, qvv, quv);
+    puu -= quu; pvv -= qvv; puv -= quv;
+  }
+  au = ff_mul(b, au);
+  av = ff_mul(b, av);
+  ax = ff_sub(ff_mul(cc, au), ff_mul(sn, av));
+  ay = ff_add(ff_mul(sn, au), ff_mul(cc, av));
+  Out5<float> t;
+  rotate_back(c.c, c.sn, 0.f, 0.f, c.b * puu, c.b * pvv, c.b * puv, t);
+  o.pxx = t.pxx; o.pyy = t.pyy; o.pxy = t.pxy;
+}
+
+// Member record of the float-float tier: float-float centre and constants of the
+// cancellation-free mean convergence, FP32 values for psi_ij, and the scaling factors.
+struct MemX {
+  float xh, xl, yh, yl;
+  float s2h, s2l, a2h, a2l;      // core^2, cut^2
+  float sh, sl, ah, al;          // core, cut
+  float bdh, bdl, apch, apcl;    // b (cut - core), cut + core
+  float b, fb, fs, loglr;        // FP32 strength, (L/L*)^(2 lam), (L/L*)^beta, ln(L/L*)
+};
+
+__host__ __device__ inline void digest_member_x(double x, double y, double b, double s, double a,
+                                                double loglr, MemX& m, double fb = 0.0,
+                                                double fs = 0.0) {
+  split_ff(x, m.xh, m.xl);
+  split_ff(y, m.yh, m.yl);
+  split_ff(s * s, m.s2h, m.s2l);
+  split_ff(a * a, m.a2h, m.a2l);
+  split_ff(s, m.sh, m.sl);
+  split_ff(a, m.ah, m.al);
+  split_ff(b * (a - s), m.bdh, m.bdl);
+  split_ff(a + s, m.apch, m.apcl);
+  m.b = (float)b; m.fb = (float)fb; m.fs = (float)fs; m.loglr = (float)loglr;
+}
+
+// alpha of one member in float-float: kbar = b (a - s) [(a + s)/(R + S) + 1] / ((S + s)(R + a)),
+// alpha = kbar x; psi_ij in FP32 from the same form (pje_round).
+LF_INLINE void eval_member_x(const MemX& m, float ph_x, float pl_x, float ph_y, float pl_y, ff& ax,
+                             ff& ay, Out5<float>& o) {
+  ff dx = offset_ff(ph_x, pl_x, m.xh, m.xl);
+  ff dy = offset_ff(ph_y, pl_y, m.yh, m.yl);
+  ff r2 = ff_add(ff_sqr(dx), ff_sqr(dy));
+  ff S = ff_sqrt(ff_add(ff_make(m.s2h, m.s2l), r2));
+  ff R = ff_sqrt(ff_add(ff_make(m.a2h, m.a2l), r2));
+  ff Ss = ff_add(S, ff_make(m.sh, m.sl));
+  ff Ra = ff_add(R, ff_make(m.ah, m.al));
+  ff PQ = ff_rcp(ff_mul(Ss, Ra));
+  ff br = ff_add_f(ff_mul(ff_make(m.apch, m.apcl), ff_rcp(ff_add(R, S))), 1.0f);
+  ff kbar = ff_mul(ff_mul(ff_make(m.bdh, m.bdl), PQ), br);
+  ax = ff_mul(kbar, dx);
+  ay = ff_mul(kbar, dy);
+  // psi_ij in FP32
+  float r2f = r2.hi;
+  float iS = rsqrtf(m.s2h + r2f), iR = rsqrtf(m.a2h + r2f);
+  float P = __fdividef(1.0f, Ss.hi), Q = __fdividef(1.0f, Ra.hi);
+  float t = m.b * (Q * Q * iR - P * P * iS);
+  float kb = kbar.hi;
+  o.pxx = fmaf(t * dx.hi, dx.hi, kb);
+  o.pyy = fmaf(t * dy.hi, dy.hi, kb);
+  o.pxy = t * dx.hi * dy.hi;
 }
 
 // ---------------------------------------------------------------- error word ------

@@ -10,12 +10,16 @@
 
 namespace lf {
 
+// Shared memory of the map and trace kernels: mbarrier (16 B), the float-float atan / atanh
+// tables (2 x LF_TAB_N float2), then the staged planes.
+constexpr uint32_t LF_MAP_BASE = 16u + 2u * LF_TAB_N * 8u;
+
 // Shared-memory layout of a staged plane (host and device agree on it).
 struct PlaneLayout {
   uint32_t rawc, rawm, dc, dm, total;
 };
 
-template <class T>
+template <class T, class M = MemT<T>>
 __host__ __device__ inline PlaneLayout plane_layout(int nc, int nm, uint32_t base) {
   PlaneLayout L;
   uint32_t o = (base + 15u) & ~15u;
@@ -24,7 +28,7 @@ __host__ __device__ inline PlaneLayout plane_layout(int nc, int nm, uint32_t bas
   o = (o + 15u) & ~15u;
   L.dc = o; o += (uint32_t)nc * (uint32_t)sizeof(CompT<T>);
   o = (o + 15u) & ~15u;
-  L.dm = o; o += (uint32_t)nm * (uint32_t)sizeof(MemT<T>);
+  L.dm = o; o += (uint32_t)nm * (uint32_t)sizeof(M);
   L.total = (o + 15u) & ~15u;
   return L;
 }
@@ -63,24 +67,68 @@ __device__ void digest_plane(const lf_comp* rawc, int nc, const lf_member* rawm,
   }
 }
 
+__device__ inline void digest_plane_x(const lf_comp* rawc, int nc, const lf_member* rawm, int nm,
+                                      const lf_scaling& sc, CompT<float>* dc, MemX* dm) {
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) digest_one_comp<float>(rawc[i], dc[i]);
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+    double b, s, a, ll;
+    member_fields(sc, rawm[i].log_l, b, s, a, ll);
+    digest_member_x(rawm[i].x, rawm[i].y, b, s, a, ll, dm[i]);
+  }
+}
+
+// Float-float tier: every deflection in float-float, accumulated in float-float.
+template <int PPT>
+__device__ __forceinline__ void accumulate_ext(const CompT<float>* dc, int nc, const MemX* dm,
+                                               int nm, int k0, int k1, const float* pxh,
+                                               const float* pxl, const float* pyh,
+                                               const float* pyl, const float2* tab,
+                                               ff (&acc)[5][PPT]) {
+  const int c1 = min(k1, nc);
+  for (int c = k0; c < c1; ++c) {
+    const CompT<float>& C = dc[c];
+    if (C.kind == 0) continue;
+    for (int k = 0; k < PPT; ++k) {
+      ff ax, ay;
+      Out5<float> o;
+      eval_comp_mixed(C, pxh[k], pxl[k], pyh[k], pyl[k], tab, ax, ay, o);
+      acc[0][k] = ff_add(acc[0][k], ax);
+      acc[1][k] = ff_add(acc[1][k], ay);
+      ff_acc(acc[2][k], o.pxx); ff_acc(acc[3][k], o.pyy); ff_acc(acc[4][k], o.pxy);
+    }
+  }
+  const int m_beg = max(k0, nc) - nc, m_end = min(k1, nc + nm) - nc;
+  for (int m = m_beg; m < m_end; ++m) {
+    const MemX M = dm[m];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      ff ax, ay;
+      Out5<float> o;
+      eval_member_x(M, pxh[k], pxl[k], pyh[k], pyl[k], ax, ay, o);
+      acc[0][k] = ff_add(acc[0][k], ax);
+      acc[1][k] = ff_add(acc[1][k], ay);
+      ff_acc(acc[2][k], o.pxx); ff_acc(acc[3][k], o.pyy); ff_acc(acc[4][k], o.pxy);
+    }
+  }
+}
+
 template <int PPT>
 __device__ __forceinline__ void accumulate_mixed(const CompT<float>* dc, int nc,
                                                  const MemT<float>* dm, int nm, int k0, int k1,
                                                  int chunk, const float* pxh, const float* pxl,
                                                  const float* pyh, const float* pyl,
-                                                 ff (&acc)[5][PPT]) {
+                                                 const float2* tab, ff (&acc)[5][PPT]) {
   const int c1 = min(k1, nc);
   for (int c = k0; c < c1; ++c) {
     const CompT<float>& C = dc[c];
     if (C.kind == 0) continue;
-#pragma unroll
     for (int k = 0; k < PPT; ++k) {
-      float dx = offset_of(pxh[k], pxl[k], C.xh, C.xl);
-      float dy = offset_of(pyh[k], pyl[k], C.yh, C.yl);
+      ff ax, ay;
       Out5<float> o;
-      eval_comp(C, dx, dy, o);
-      ff_add(acc[0][k], o.ax); ff_add(acc[1][k], o.ay);
-      ff_add(acc[2][k], o.pxx); ff_add(acc[3][k], o.pyy); ff_add(acc[4][k], o.pxy);
+      eval_comp_mixed(C, pxh[k], pxl[k], pyh[k], pyl[k], tab, ax, ay, o);
+      acc[0][k] = ff_add(acc[0][k], ax);
+      acc[1][k] = ff_add(acc[1][k], ay);
+      ff_acc(acc[2][k], o.pxx); ff_acc(acc[3][k], o.pyy); ff_acc(acc[4][k], o.pxy);
     }
   }
   const int m_beg = max(k0, nc) - nc, m_end = min(k1, nc + nm) - nc;
@@ -106,7 +154,7 @@ __device__ __forceinline__ void accumulate_mixed(const CompT<float>* dc, int nc,
 #pragma unroll
     for (int v = 0; v < 5; ++v)
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) ff_add(acc[v][k], cs[v][k]);
+      for (int k = 0; k < PPT; ++k) ff_acc(acc[v][k], cs[v][k]);
   }
 }
 

@@ -56,23 +56,30 @@ __device__ __forceinline__ void write_out(const OutArgs& O, long long p, double 
 }
 
 // ------------------------------------------------------------------- LF_MIXED ------
-template <int PPT>
-__global__ void __launch_bounds__(256) k_map_mixed(const lf_comp* __restrict__ comp, int nc,
+#ifndef LF_MAP_MINB
+#define LF_MAP_MINB 1
+#endif
+template <int PPT, bool EXT>
+__global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_mixed(const lf_comp* __restrict__ comp, int nc,
                                                    const lf_member* __restrict__ mem, int nm,
                                                    lf_scaling sc, PosArgs P, OutArgs O, int chunk) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  const PlaneLayout L = plane_layout<float>(nc, nm, 16);
+  typedef typename std::conditional<EXT, MemX, MemT<float>>::type Mem;
+  const PlaneLayout L = plane_layout<float, Mem>(nc, nm, LF_MAP_BASE);
   lf_comp* rawc = reinterpret_cast<lf_comp*>(smem + L.rawc);
   lf_member* rawm = reinterpret_cast<lf_member*>(smem + L.rawm);
   CompT<float>* dc = reinterpret_cast<CompT<float>*>(smem + L.dc);
-  MemT<float>* dm = reinterpret_cast<MemT<float>*>(smem + L.dm);
+  Mem* dm = reinterpret_cast<Mem*>(smem + L.dm);
+  float2* tab = reinterpret_cast<float2*>(smem + 16);
   if (threadIdx.x == 0) mbar_init(bar, 1);
+  init_ff_tables(tab);
   __syncthreads();
   bool ok = stage_to_smem(rawc, comp, (uint32_t)nc * 64u + 0u, bar, 0);
   if (ok) ok = stage_to_smem(rawm, mem, (uint32_t)nm * 32u, bar, nc > 0 ? 1 : 0);
   if (!ok) return;
-  digest_plane<float>(rawc, nc, rawm, nm, sc, dc, dm);
+  if constexpr (EXT) digest_plane_x(rawc, nc, rawm, nm, sc, dc, dm);
+  else digest_plane<float>(rawc, nc, rawm, nm, sc, dc, dm);
   __syncthreads();
 
   const long long per_tile = (long long)PPT * blockDim.x;
@@ -94,7 +101,8 @@ __global__ void __launch_bounds__(256) k_map_mixed(const lf_comp* __restrict__ c
 #pragma unroll
       for (int k = 0; k < PPT; ++k) acc[v][k] = ff_zero();
 
-    accumulate_mixed<PPT>(dc, nc, dm, nm, 0, nc + nm, chunk, pxh, pxl, pyh, pyl, acc);
+    if constexpr (EXT) accumulate_ext<PPT>(dc, nc, dm, nm, 0, nc + nm, pxh, pxl, pyh, pyl, tab, acc);
+    else accumulate_mixed<PPT>(dc, nc, dm, nm, 0, nc + nm, chunk, pxh, pxl, pyh, pyl, tab, acc);
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       if (pid[k] < P.n)
@@ -151,11 +159,28 @@ lf_status check_plane(const lf_plane* pl) {
   return LF_OK;
 }
 
+template <int PPT, bool EXT>
+static lf_status launch_mixed(const lf_plane* pl, const PosArgs& P, const OutArgs& O, int nsm,
+                              int block, cudaStream_t s) {
+  typedef typename std::conditional<EXT, MemX, MemT<float>>::type Mem;
+  PlaneLayout L = plane_layout<float, Mem>(pl->n_comp, pl->n_mem, LF_MAP_BASE);
+  if (L.total > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "plane too large for shared memory");
+  auto k = k_map_mixed<PPT, EXT>;
+  LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  int occ = 0;
+  LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, L.total));
+  long long tiles = (P.n + (long long)PPT * block - 1) / ((long long)PPT * block);
+  long long grid = std::min<long long>(tiles, (long long)nsm * std::max(occ, 1));
+  k<<<(unsigned)grid, block, L.total, s>>>(pl->comp, pl->n_comp, pl->mem, pl->n_mem, pl->scaling, P, O,
+                                           g_member_chunk);
+  return LF_OK;
+}
+
 static lf_status launch_map(const lf_plane* pl, const PosArgs& P, const OutArgs& O,
                             int precision, void* stream) {
   lf_status st = check_plane(pl);
   if (st != LF_OK) return st;
-  if (precision != LF_FP64 && precision != LF_MIXED) return fail(LF_EINVAL, "unknown precision");
+  if (precision < LF_FP64 || precision > LF_FF) return fail(LF_EINVAL, "unknown precision");
   if (P.n == 0) return LF_OK;
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0;
@@ -164,18 +189,9 @@ static lf_status launch_map(const lf_plane* pl, const PosArgs& P, const OutArgs&
   LF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int block = 256;
   if (precision == LF_MIXED) {
-    const int PPT = 2;
-    PlaneLayout L = plane_layout<float>(pl->n_comp, pl->n_mem, 16);
-    if (L.total > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "plane too large for shared memory");
-    LF_CUDA(cudaFuncSetAttribute(k_map_mixed<PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L.total));
-    int occ = 0;
-    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_map_mixed<PPT>, block, L.total));
-    long long tiles = (P.n + (long long)PPT * block - 1) / ((long long)PPT * block);
-    long long grid = std::min<long long>(tiles, (long long)nsm * std::max(occ, 1));
-    k_map_mixed<PPT><<<(unsigned)grid, block, L.total, s>>>(pl->comp, pl->n_comp, pl->mem,
-                                                             pl->n_mem, pl->scaling, P, O,
-                                                             g_member_chunk);
+    LF_TRY((launch_mixed<2, false>(pl, P, O, nsm, block, s)));
+  } else if (precision == LF_FF) {
+    LF_TRY((launch_mixed<1, true>(pl, P, O, nsm, block, s)));
   } else {
     PlaneLayout L = plane_layout<double>(pl->n_comp, pl->n_mem, 16);
     if (L.total > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "plane too large for shared memory");

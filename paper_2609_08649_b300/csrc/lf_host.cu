@@ -4,7 +4,10 @@
 
 namespace lf {
 
-int g_member_chunk = 16;
+#ifndef LF_CHUNK
+#define LF_CHUNK 8
+#endif
+int g_member_chunk = LF_CHUNK;
 
 static thread_local std::string g_last_error;
 

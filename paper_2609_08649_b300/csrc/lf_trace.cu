@@ -25,11 +25,11 @@ struct MultiPlaneArgs {
 };
 
 // Stages and digests every plane; returns false (all threads) if a bounded wait ran out.
-template <class T>
+template <class T, class M>
 __device__ bool stage_planes(unsigned char* smem, uint64_t* bar, const MultiPlaneArgs& A) {
   uint32_t phase = 0;
   for (int j = 0; j < A.np; ++j) {
-    PlaneLayout L = plane_layout<T>(A.nc[j], A.nm[j], A.base[j]);
+    PlaneLayout L = plane_layout<T, M>(A.nc[j], A.nm[j], A.base[j]);
     if (A.nc[j] > 0) {
       if (!stage_to_smem(smem + L.rawc, A.comp[j], (uint32_t)A.nc[j] * 64u, bar, phase & 1u))
         return false;
@@ -40,9 +40,14 @@ __device__ bool stage_planes(unsigned char* smem, uint64_t* bar, const MultiPlan
         return false;
       ++phase;
     }
-    digest_plane<T>(reinterpret_cast<lf_comp*>(smem + L.rawc), A.nc[j],
-                    reinterpret_cast<lf_member*>(smem + L.rawm), A.nm[j], A.sc[j],
-                    reinterpret_cast<CompT<T>*>(smem + L.dc), reinterpret_cast<MemT<T>*>(smem + L.dm));
+    if constexpr (std::is_same<M, MemX>::value)
+      digest_plane_x(reinterpret_cast<lf_comp*>(smem + L.rawc), A.nc[j],
+                     reinterpret_cast<lf_member*>(smem + L.rawm), A.nm[j], A.sc[j],
+                     reinterpret_cast<CompT<float>*>(smem + L.dc), reinterpret_cast<MemX*>(smem + L.dm));
+    else
+      digest_plane<T>(reinterpret_cast<lf_comp*>(smem + L.rawc), A.nc[j],
+                      reinterpret_cast<lf_member*>(smem + L.rawm), A.nm[j], A.sc[j],
+                      reinterpret_cast<CompT<T>*>(smem + L.dc), reinterpret_cast<MemT<T>*>(smem + L.dm));
   }
   __syncthreads();
   return true;
@@ -57,14 +62,18 @@ struct RayIO {
   double* A;
 };
 
-template <bool MIXED>
+template <int MODE>   // LF_FP64, LF_MIXED or LF_FF
 __global__ void __launch_bounds__(256) k_trace(MultiPlaneArgs MP, RayIO io, int chunk) {
+  constexpr bool MIXED = MODE != LF_FP64;
   typedef typename std::conditional<MIXED, float, double>::type T;
+  typedef typename std::conditional<MODE == LF_FF, MemX, MemT<T>>::type Mem;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  float2* tab = reinterpret_cast<float2*>(smem + 16);
   if (threadIdx.x == 0) mbar_init(bar, 1);
+  init_ff_tables(tab);
   __syncthreads();
-  if (!stage_planes<T>(smem, bar, MP)) return;
+  if (!stage_planes<T, Mem>(smem, bar, MP)) return;
 
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < io.n;
        p += (long long)gridDim.x * blockDim.x) {
@@ -89,9 +98,9 @@ __global__ void __launch_bounds__(256) k_trace(MultiPlaneArgs MP, RayIO io, int 
         a00 -= r * PA[i][0]; a01 -= r * PA[i][1];
         a10 -= r * PA[i][2]; a11 -= r * PA[i][3];
       }
-      PlaneLayout L = plane_layout<T>(MP.nc[j], MP.nm[j], MP.base[j]);
+      PlaneLayout L = plane_layout<T, Mem>(MP.nc[j], MP.nm[j], MP.base[j]);
       const CompT<T>* dc = reinterpret_cast<const CompT<T>*>(smem + L.dc);
-      const MemT<T>* dm = reinterpret_cast<const MemT<T>*>(smem + L.dm);
+      const Mem* dm = reinterpret_cast<const Mem*>(smem + L.dm);
       double s[5];
       if constexpr (MIXED) {
         float xh[1], xl[1], yh[1], yl[1];
@@ -99,8 +108,11 @@ __global__ void __launch_bounds__(256) k_trace(MultiPlaneArgs MP, RayIO io, int 
         split_ff(ty, yh[0], yl[0]);
         ff acc[5][1];
         for (int v = 0; v < 5; ++v) acc[v][0] = ff_zero();
-        accumulate_mixed<1>(dc, MP.nc[j], dm, MP.nm[j], 0, MP.nc[j] + MP.nm[j], chunk, xh, xl, yh,
-                            yl, acc);
+        if constexpr (MODE == LF_FF)
+          accumulate_ext<1>(dc, MP.nc[j], dm, MP.nm[j], 0, MP.nc[j] + MP.nm[j], xh, xl, yh, yl, tab, acc);
+        else
+          accumulate_mixed<1>(dc, MP.nc[j], dm, MP.nm[j], 0, MP.nc[j] + MP.nm[j], chunk, xh, xl, yh,
+                              yl, tab, acc);
         for (int v = 0; v < 5; ++v) s[v] = ff_to_double(acc[v][0]);
       } else {
         for (int v = 0; v < 5; ++v) s[v] = 0.0;
@@ -134,15 +146,12 @@ __global__ void __launch_bounds__(256) k_trace(MultiPlaneArgs MP, RayIO io, int 
 }
 
 // Fills the plane part of MultiPlaneArgs and returns the shared-memory bytes needed.
-template <class T>
-lf_status fill_planes(const lf_plane* planes, int np, MultiPlaneArgs& A, uint32_t& total);
-
 lf_status check_plane(const lf_plane* pl);
 
-template <class T>
+template <class T, class M>
 lf_status fill_planes(const lf_plane* planes, int np, MultiPlaneArgs& A, uint32_t& total) {
   A.np = np;
-  uint32_t base = 16;
+  uint32_t base = LF_MAP_BASE;
   for (int j = 0; j < np; ++j) {
     LF_TRY(check_plane(&planes[j]));
     A.comp[j] = planes[j].comp;
@@ -151,7 +160,7 @@ lf_status fill_planes(const lf_plane* planes, int np, MultiPlaneArgs& A, uint32_
     A.nm[j] = planes[j].n_mem;
     A.sc[j] = planes[j].scaling;
     A.base[j] = base;
-    base = plane_layout<T>(planes[j].n_comp, planes[j].n_mem, base).total;
+    base = plane_layout<T, M>(planes[j].n_comp, planes[j].n_mem, base).total;
   }
   total = base;
   if (total > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "planes too large for shared memory");
@@ -169,7 +178,7 @@ extern "C" lf_status lf_trace_multiplane(const lf_plane* planes, int32_t n_plane
   if (!planes) return fail(LF_EINVAL, "planes is NULL");
   if (n_planes < 1 || n_planes > LF_MAX_PLANES) return fail(LF_EINVAL, "need 1 <= n_planes <= 8");
   if (!ratios) return fail(LF_EINVAL, "ratios is NULL");
-  if (precision != LF_FP64 && precision != LF_MIXED) return fail(LF_EINVAL, "unknown precision");
+  if (precision < LF_FP64 || precision > LF_FF) return fail(LF_EINVAL, "unknown precision");
   RayIO io{};
   if (theta) {
     if (n < 0) return fail(LF_EINVAL, "n must be >= 0");
@@ -195,8 +204,9 @@ extern "C" lf_status lf_trace_multiplane(const lf_plane* planes, int32_t n_plane
     MP.rs[j] = v;
   }
   uint32_t total = 0;
-  if (precision == LF_MIXED) LF_TRY(fill_planes<float>(planes, n_planes, MP, total));
-  else LF_TRY(fill_planes<double>(planes, n_planes, MP, total));
+  if (precision == LF_MIXED) LF_TRY((fill_planes<float, MemT<float>>(planes, n_planes, MP, total)));
+  else if (precision == LF_FF) LF_TRY((fill_planes<float, MemX>(planes, n_planes, MP, total)));
+  else LF_TRY((fill_planes<double, MemT<double>>(planes, n_planes, MP, total)));
   if (io.n == 0) return LF_OK;
   int dev = 0, nsm = 0, occ = 0;
   LF_CUDA(cudaGetDevice(&dev));
@@ -204,17 +214,11 @@ extern "C" lf_status lf_trace_multiplane(const lf_plane* planes, int32_t n_plane
   const int block = 256;
   cudaStream_t s = (cudaStream_t)stream;
   long long tiles = (io.n + block - 1) / block;
-  if (precision == LF_MIXED) {
-    LF_CUDA(cudaFuncSetAttribute(k_trace<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total));
-    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<true>, block, total));
-    long long g = std::min<long long>(tiles, (long long)nsm * std::max(occ, 1));
-    k_trace<true><<<(unsigned)g, block, total, s>>>(MP, io, g_member_chunk);
-  } else {
-    LF_CUDA(cudaFuncSetAttribute(k_trace<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total));
-    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<false>, block, total));
-    long long g = std::min<long long>(tiles, (long long)nsm * std::max(occ, 1));
-    k_trace<false><<<(unsigned)g, block, total, s>>>(MP, io, g_member_chunk);
-  }
+  auto k = precision == LF_MIXED ? k_trace<LF_MIXED> : precision == LF_FF ? k_trace<LF_FF> : k_trace<LF_FP64>;
+  LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total));
+  LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, total));
+  long long g = std::min<long long>(tiles, (long long)nsm * std::max(occ, 1));
+  k<<<(unsigned)g, block, total, s>>>(MP, io, g_member_chunk);
   LF_CUDA(cudaGetLastError());
   return LF_OK;
 }

@@ -50,3 +50,54 @@ def mu_det(pxx, pyy, pxy, a):
     g1 = 0.5 * (pxx - pyy)
     det = (1 - a * k) ** 2 - a * a * (g1 * g1 + pxy * pxy)
     return 1 / det, det
+
+
+def chi2_mixed_bound(wl, cat, theta, sigma=None, coef=4.0):
+    """First-order bound on |chi2_mixed - chi2| per sample from the FP32 rounding of each
+    component (relative coef * u): d chi2 = sum_i 2 a_f [-w_i . d alpha_i + w_i^T d Psi_i z_i]
+    (w = M d, z = mu d, d = beta_i - beta_model), with |d alpha_i| <= coef u sum_k |alpha_k|
+    and |d Psi_i| <= coef u sum_k |psi_k| at image i."""
+    from oracle import lensing as OLL
+    sig = wl.sigma_pos if sigma is None else sigma
+    th = torch.as_tensor(theta)
+    pl = OM.apply_params(wl, th)[0]
+    a_f = OM.single_plane_adis(wl, cat.fam_zs)
+    off = list(cat.fam_off)
+    n = len(cat.theta_obs)
+    tx = torch.tensor(cat.theta_obs[:, 0])[None]
+    ty = torch.tensor(cat.theta_obs[:, 1])[None]
+    S = th.shape[0]
+    sa = torch.zeros(S, n, dtype=torch.float64)
+    sp = torch.zeros(S, n, dtype=torch.float64)
+    for k, kind in enumerate(pl.kind):
+        col = lambda f: f[:, k:k + 1]
+        o = OLL.component(kind, tx - col(pl.x), ty - col(pl.y), col(pl.b), col(pl.eps), col(pl.pa),
+                          col(pl.core), col(pl.cut))
+        sa += torch.hypot(o[0], o[1])
+        sp += o[2].abs() + o[3].abs() + o[4].abs()
+    if pl.n_members:
+        bm, cm, tm = OLL.member_fields(pl)
+        for m in range(pl.n_members):
+            o = pr.pje_sph(tx - pl.mx[m], ty - pl.my[m], bm[:, m:m + 1], cm[:, m:m + 1], tm[:, m:m + 1])
+            sa += torch.hypot(o[0], o[1])
+            sp += o[2].abs() + o[3].abs() + o[4].abs()
+    beta, A = OLL.single_plane_source_terms(pl, torch.tensor(cat.theta_obs), off, a_f)
+    sinv = torch.tensor(np.tile([1 / sig ** 2, 0, 1 / sig ** 2], (n, 1)))
+    Sm = OLL.sinv_matrix(sinv)
+    mu = torch.linalg.inv(A)
+    M = mu.transpose(-1, -2) @ Sm[None] @ mu
+    bound = torch.zeros(S, dtype=torch.float64)
+    for f in range(len(off) - 1):
+        i0, i1 = off[f], off[f + 1]
+        if i1 - i0 < 2:
+            continue
+        Mf, bf = M[:, i0:i1], beta[:, i0:i1]
+        bmod = torch.linalg.solve(Mf.sum(1), (Mf @ bf[..., None]).sum(1))
+        d = bf[..., None] - bmod[:, None]
+        w = (Mf @ d)[..., 0]
+        z = (mu[:, i0:i1] @ d)[..., 0]
+        wn, zn = w.norm(dim=-1), z.norm(dim=-1)
+        da = coef * U32 * sa[:, i0:i1]
+        dp = coef * U32 * sp[:, i0:i1]
+        bound += (2 * a_f[f] * (wn * da + wn * zn * dp)).sum(1)
+    return bound.numpy()

@@ -36,7 +36,7 @@ def _abs_scale(wl, x, y):
     return tot
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "ff"])
 def test_three_plane_grid_matches_oracle(lib, prec):
     api, PM = lib
     wl = W.multiplane_c3(n_grid=8)
@@ -59,7 +59,7 @@ def test_three_plane_grid_matches_oracle(lib, prec):
     assert np.abs(A[:, 0, 1] - A[:, 1, 0]).max() > 1e-6
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "ff"])
 def test_single_plane_trace_equals_lens_map(lib, prec):
     api, PM = lib
     wl = W.cluster_c1()
@@ -70,7 +70,9 @@ def test_single_plane_trace_equals_lens_map(lib, prec):
     beta, A = api.trace_multiplane(dp, r, theta=pts, precision=prec)
     o = api.jacobian_points(dp[0], pts, a, prec)
     bx = pts[:, 0] - a * o["ax"]
-    assert torch.allclose(beta[:, 0], bx, rtol=0, atol=1e-12)
+    # the two kernels may contract multiply-adds differently: FP32-level differences in mixed
+    tol = {"fp64": 1e-12, "mixed": 5e-5, "ff": 1e-9}[prec]
+    assert torch.allclose(beta[:, 0], bx, rtol=0, atol=tol)
     # A11 = 1 - a psi_xx and kappa = (psi_xx + psi_yy)/2 -> trace check
     tr = A[:, 0, 0] + A[:, 1, 1]
     assert torch.allclose(tr, 2 - 2 * a * o["kappa"].double(), atol=1e-5)
