@@ -213,6 +213,23 @@ lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int32_t S, doub
 
 lf_status lf_plan_destroy(lf_plan* plan);
 
+/* lf_chi2_batch for one cluster with no device allocation (the paper has no counterpart;
+ * it exists for callers that cannot call cudaMalloc: a process whose GPU memory is already
+ * reserved by another framework's caching allocator, a sampler step that must not
+ * synchronise the device, or a plug-in host that forbids device allocation).
+ * Arguments are those of one lf_cluster (host arrays read during the call; comp / mem device
+ * arrays read on `stream`), theta device [S * P], chi2 device [S], all samples belonging to
+ * that cluster.  Every derived table lives in one fixed 1 MiB array of device memory inside
+ * the library (held by every GPU that loads the library until the process exits); a
+ * cluster that needs more returns LF_EINVAL with the size in lf_last_error().  All calls
+ * share that array and its contents persist between calls: calls that overlap on the GPU
+ * race and must not be issued.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), so it should come before any stream capture.  Host-side
+ * validation as in lf_plan_create; component fields are validated on the device
+ * (lf_device_error). */
+lf_status lf_chi2_batch_static(const lf_cluster* cluster, const double* theta, int32_t S,
+                               int32_t precision, double* chi2, void* stream);
+
 /* Tile shape chosen by the plan (components per thread slice, threads per block). */
 lf_status lf_plan_info(const lf_plan* plan, int32_t* kslices, int32_t* block, int32_t* graph);
 

@@ -5,3 +5,4 @@
 #include "lf_grid.cu"
 #include "lf_trace.cu"
 #include "lf_chi2.cu"
+#include "lf_static.cu"
