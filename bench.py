@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=4096)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "ff", "fp64"],
+                    help="precision of the headline step")
+    ap.add_argument("--workload", default="grid", choices=["grid", "chi2", "grad", "trace"],
+                    help="grid = the headline; the others run one secondary kernel alone (profiling)")
+    ap.add_argument("--samples", type=int, default=4096, help="samples for --workload chi2")
     return ap.parse_args()
 
 
@@ -185,6 +190,9 @@ def main():
     from paper_2609_08649_b300 import api
     from paper_2609_08649_b300 import model as PM
     from paper_2609_08649_b300 import workloads as W
+    if args.workload != "grid":
+        single_workload(args, torch, api, PM, W)
+        return
 
     wl = W.cluster_c1(args.grid)
     g = wl.grid
@@ -201,7 +209,9 @@ def main():
     ps, gs = dp.c_struct(), PM.grid_struct(g)
     stream = torch.cuda.current_stream()
 
-    def step(prec=L.LF_MIXED):
+    head_prec = api.PRECISION[args.precision]
+
+    def step(prec=head_prec):
         L.check(L.lib.lf_jacobian_grid(C.byref(ps), C.byref(gs), a, prec,
                                        *[C.c_void_p(outs[k].data_ptr()) for k in api.ALL_OUTPUTS],
                                        C.c_void_p(stream.cuda_stream)))
@@ -276,14 +286,20 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "mixed (FP32 closed forms, float-float sums, FP64 det/mu)",
+            "vs_baseline": None, "dtype": {"mixed": "f32+f64", "ff": "f32x2+f64", "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": {
+                "mixed": "LF_MIXED (FP32 closed forms, float-float halo/shear deflections and sums, FP64 det/mu)",
+                "ff": "LF_FF (float-float deflections of every component, FP32 psi_ij, FP64 det/mu)",
+                "fp64": "LF_FP64"}[args.precision],
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "l2": "256 MiB buffer written between timed steps, outside the step events; "
                              "each step writes 604 MB of maps (> 126 MB L2)",
                        "region_s": t_region},
             "e2e": e2e, "gpu_launches": args.steps, "clocks": clk, "roofline": roofline}
 
+    if rank == 0:
+        line["parity"] = sampled_parity(torch, api, PM, W, wl, dp, a, outs, args.precision)
     if rank == 0 and not args.no_secondary:
         line["secondary"] = secondary(torch, api, PM, W, L, C, step, ms, evals)
     if rank == 0:
@@ -312,20 +328,23 @@ def secondary(torch, api, PM, W, L, C, step, ms_mixed, evals):
     out = {}
     ms64 = _time(torch, lambda: step(L.LF_FP64), reps=2)
     out["grid_fp64"] = {"ms": ms64, "lens_evals_per_s": evals / (ms64 * 1e-3),
-                        "mixed_speedup": ms64 / ms_mixed}
+                        "headline_speedup": ms64 / ms_mixed}
+    msff = _time(torch, lambda: step(L.LF_FF), reps=3)
+    out["grid_ff"] = {"ms": msff, "lens_evals_per_s": evals / (msff * 1e-3), "fp64_over_ff": ms64 / msff}
     # batched chi^2, 4096 samples x 200 images x 302 components
     wl = W.cluster_c2()
     cat = W.load_catalogue("cluster_200")
     th = torch.tensor(W.sample_thetas(wl, wl.seed), device="cuda")
     ev = th.shape[0] * len(cat.theta_obs) * (2 + 1 + 300)
     res = {}
-    for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "ff", "fp64"):
         plan = api.Plan([PM.cluster_input(wl, cat)], th.shape[0], prec, flags=api.FLAG_GRAPH | api.FLAG_AUTOTUNE)
-        t = _time(torch, lambda: plan.chi2(th), reps=5 if prec == "mixed" else 2)
+        t = _time(torch, lambda: plan.chi2(th), reps=5 if prec != "fp64" else 2)
         res[prec] = {"ms": t, "chi2_per_s": th.shape[0] / (t * 1e-3), "lens_evals_per_s": ev / (t * 1e-3),
                      "tile": plan.info()}
         plan.close()
     res["mixed_speedup"] = res["fp64"]["ms"] / res["mixed"]["ms"]
+    res["ff_speedup"] = res["fp64"]["ms"] / res["ff"]["ms"]
     out["chi2_4096x200"] = res
     # gradient over 16 clusters
     try:
@@ -335,15 +354,16 @@ def secondary(torch, api, PM, W, L, C, step, ms_mixed, evals):
         th4 = torch.tensor(ths, device="cuda")
         ev4 = sum(w.n_samples * len(c.theta_obs) * (3 + len(w.planes[0].members.x)) for w, c in zip(wls, cats))
         res = {}
-        for prec in ("mixed", "fp64"):
+        for prec in ("mixed", "ff", "fp64"):
             plan = api.Plan([PM.cluster_input(w, c) for w, c in zip(wls, cats)], th4.shape[0], prec,
                             flags=api.FLAG_GRAPH)
-            t = _time(torch, lambda: plan.chi2_grad(th4), reps=3 if prec == "mixed" else 1)
-            tc = _time(torch, lambda: plan.chi2(th4), reps=3 if prec == "mixed" else 1)
+            t = _time(torch, lambda: plan.chi2_grad(th4), reps=3 if prec != "fp64" else 1)
+            tc = _time(torch, lambda: plan.chi2(th4), reps=3 if prec != "fp64" else 1)
             res[prec] = {"grad_ms": t, "chi2_ms": tc, "grad_samples_per_s": th4.shape[0] / (t * 1e-3),
                          "lens_evals_per_s_chi2": ev4 / (tc * 1e-3)}
             plan.close()
         res["mixed_speedup_grad"] = res["fp64"]["grad_ms"] / res["mixed"]["grad_ms"]
+        res["ff_speedup_grad"] = res["fp64"]["grad_ms"] / res["ff"]["grad_ms"]
         out["grad_16clusters_1024"] = res
     except FileNotFoundError as e:
         out["grad_16clusters_1024"] = {"skipped": str(e)}
@@ -354,13 +374,52 @@ def secondary(torch, api, PM, W, L, C, step, ms_mixed, evals):
     res = {}
     nrays = wl3.grid.nx * wl3.grid.ny
     ncomp = sum(len(p.comp_host) + len(p.mem_host) for p in planes)
-    for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "ff", "fp64"):
         t = _time(torch, lambda: api.trace_multiplane(planes, r, grid=wl3.grid, precision=prec), reps=2)
         res[prec] = {"ms": t, "rays_per_s": nrays / (t * 1e-3), "lens_evals_per_s": nrays * ncomp / (t * 1e-3)}
     res["mixed_speedup"] = res["fp64"]["ms"] / res["mixed"]["ms"]
     out["trace_3plane_2048"] = res
     api.device_error()
     return out
+
+
+def sampled_parity(torch, api, PM, W, wl, dp, a, outs, prec, n=2000):
+    """alpha error of the headline maps against the FP64 oracle at seeded sampled pixels
+    (the oracle evaluates them one by one; the bench step computed every pixel)."""
+    from oracle import lensing as OL
+    from oracle import model as OM
+    g = wl.grid
+    rng = np.random.default_rng(77)
+    idx = rng.integers(0, g.nx * g.ny, n)
+    j, i = idx // g.nx, idx % g.nx
+    x, y = g.x0 + i * g.dx, g.y0 + j * g.dy
+    ax, ay, *_ = OL.plane_sum(OM.build_planes(wl)[0], torch.tensor(x)[None], torch.tensor(y)[None])
+    ti = torch.tensor(idx, device="cuda")
+    gx = outs["ax"][ti].cpu().numpy()
+    gy = outs["ay"][ti].cpu().numpy()
+    d = np.hypot(gx - ax[0].numpy(), gy - ay[0].numpy())
+    return {"alpha_max_abs_err_arcsec": float(d.max()), "alpha_rms_err_arcsec": float(np.sqrt((d ** 2).mean())),
+            "pixels": n, "precision": prec}
+
+
+def single_workload(args, torch, api, PM, W):
+    """One secondary kernel alone, for profiling (prints a short JSON line)."""
+    prec = args.precision
+    if args.workload in ("chi2", "grad"):
+        wl = W.cluster_c2(n_samples=args.samples)
+        cat = W.load_catalogue("cluster_200")
+        th = torch.tensor(W.sample_thetas(wl, wl.seed), device="cuda")
+        plan = api.Plan([PM.cluster_input(wl, cat)], th.shape[0], prec)
+        fn = (lambda: plan.chi2(th)) if args.workload == "chi2" else (lambda: plan.chi2_grad(th))
+    else:
+        wl3 = W.multiplane_c3(n_grid=args.grid // 2)
+        planes = PM.device_planes(wl3)
+        r = PM.multiplane_ratios(wl3.cosmo, [p.z for p in wl3.planes], wl3.z_s)
+        fn = lambda: api.trace_multiplane(planes, r, grid=wl3.grid, precision=prec)
+    for _ in range(args.warmup):
+        fn()
+    ms = _time(torch, fn, reps=args.steps, warm=0)
+    print(json.dumps({"workload": args.workload, "precision": prec, "ms": ms}), flush=True)
 
 
 if __name__ == "__main__":

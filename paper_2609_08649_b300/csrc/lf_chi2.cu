@@ -248,11 +248,6 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
           ok = stage_to_smem(smem + P.off_rawc, P.comp, (uint32_t)P.nc * 64u, bar, phase & 1u);
           ++phase;
         }
-        if (ok && P.nm > 0) {
-          ok = stage_to_smem(smem + P.off_mpre, P.mpre, (uint32_t)(P.nm * sizeof(MemPre)), bar,
-                             phase & 1u);
-          ++phase;
-        }
       }
       if (!ok) return;
       for (int j = 0; j < C.np; ++j) {
@@ -286,7 +281,7 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
       const bool lam_free = sampled && C.scal_p[LF_S_LAM] >= 0;
       const bool beta_free = sampled && C.scal_p[LF_S_BETA] >= 0;
       const bool alpha_free = sampled && C.scal_p[LF_S_ALPHA] >= 0;
-      const MemPre* mp = reinterpret_cast<const MemPre*>(smem + P.off_mpre);
+      const MemPre* mp = reinterpret_cast<const MemPre*>(P.mpre);   // plan table, L2-resident
       Mem* dm = reinterpret_cast<Mem*>(smem + P.off_dm);
       for (int i = tid; i < P.nm; i += blockDim.x) {
         const MemPre& m = mp[i];
@@ -314,20 +309,26 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
         d.b = (T)sc.b_star * fb;
         d.s = (T)sc.core_star * fs;
         d.a = (T)sc.cut_star * fa;
+        d.bd = d.b * (d.a - d.s);
+        d.apc = d.a + d.s;
         d.fb = fb;
         d.fs = fs;
         d.s2 = d.s * d.s;
         d.a2 = d.a * d.a;
         d.loglr = (T)m.lnl;
+        d.pad0 = (T)0;
+        d.pad1 = (T)0;
         dm[i] = d;
         }
       }
     }
     __syncthreads();
 
-    // ---- A3-A6: alpha and Psi at every image, plane by plane
+    // ---- A3-A6: alpha and Psi at every image, plane by plane.  A task is (image pair,
+    // component slice): two images per thread give two independent evaluation chains.
     const int n_img = C.n_img, KS = C.ks, IS = C.img_stride;
-    const int ntask = n_img * KS;
+    const int n_pair = (n_img + 1) >> 1;
+    const int ntask = n_pair * KS;
     for (int j = 0; j < C.np; ++j) {
       const PlaneDesc& P = C.pl[j];
       const CompT<T>* dc = reinterpret_cast<const CompT<T>*>(smem + P.off_dc);
@@ -336,39 +337,59 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
       for (int base = 0; base < ntask; base += blockDim.x) {
         const int t = base + tid;
         const bool act = t < ntask;
-        const int i = act ? t / KS : 0;
-        const int k = act ? t - i * KS : 0;
-        double v[5] = {0, 0, 0, 0, 0};
+        const int pr = act ? t / KS : 0;
+        const int k = act ? t - pr * KS : 0;
+        const int ia = 2 * pr, ib = min(2 * pr + 1, n_img - 1);
+        double v[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
         if (act) {
           const int k0 = (int)((long long)K * k / KS), k1 = (int)((long long)K * (k + 1) / KS);
-          double x, y;
-          if (j == 0) {
-            x = C.theta[2 * i];
-            y = C.theta[2 * i + 1];
-          } else {
-            x = img[i * IS + 14];
-            y = img[i * IS + 15];
+          double x[2], y[2];
+          const int ii[2] = {ia, ib};
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            if (j == 0) {
+              x[q] = C.theta[2 * ii[q]];
+              y[q] = C.theta[2 * ii[q] + 1];
+            } else {
+              x[q] = img[ii[q] * IS + 14];
+              y[q] = img[ii[q] * IS + 15];
+            }
           }
           if constexpr (MIXED) {
-            float xh[1], xl[1], yh[1], yl[1];
-            split_ff(x, xh[0], xl[0]);
-            split_ff(y, yh[0], yl[0]);
-            ff acc[5][1];
-            for (int q = 0; q < 5; ++q) acc[q][0] = ff_zero();
+            float xh[2], xl[2], yh[2], yl[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              split_ff(x[q], xh[q], xl[q]);
+              split_ff(y[q], yh[q], yl[q]);
+            }
+            ff acc[5][2];
+#pragma unroll
+            for (int c5 = 0; c5 < 5; ++c5) acc[c5][0] = acc[c5][1] = ff_zero();
             if constexpr (MODE == LF_FF)
-              accumulate_ext<1>(dc, P.nc, dm, P.nm, k0, k1, xh, xl, yh, yl, tab, acc);
+              accumulate_ext<2>(dc, P.nc, dm, P.nm, k0, k1, xh, xl, yh, yl, tab, acc);
             else
-              accumulate_mixed<1>(dc, P.nc, dm, P.nm, k0, k1, chunk, xh, xl, yh, yl, tab, acc);
-            for (int q = 0; q < 5; ++q) v[q] = ff_to_double(acc[q][0]);
+              accumulate_mixed<2>(dc, P.nc, dm, P.nm, k0, k1, chunk, xh, xl, yh, yl, tab, acc);
+#pragma unroll
+            for (int c5 = 0; c5 < 5; ++c5) {
+              v[0][c5] = ff_to_double(acc[c5][0]);
+              v[1][c5] = ff_to_double(acc[c5][1]);
+            }
           } else {
-            accumulate_fp64(dc, P.nc, dm, P.nm, k0, k1, x, y, v);
+            accumulate_fp64(dc, P.nc, dm, P.nm, k0, k1, x[0], y[0], v[0]);
+            accumulate_fp64(dc, P.nc, dm, P.nm, k0, k1, x[1], y[1], v[1]);
           }
         }
         for (int off = 1; off < KS; off <<= 1)
 #pragma unroll
-          for (int q = 0; q < 5; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
-        if (act && k == 0)
-          for (int q = 0; q < 5; ++q) img[i * IS + q] = v[q];
+          for (int c5 = 0; c5 < 5; ++c5) {
+            v[0][c5] += __shfl_xor_sync(0xffffffffu, v[0][c5], off);
+            v[1][c5] += __shfl_xor_sync(0xffffffffu, v[1][c5], off);
+          }
+        if (act && k == 0) {
+          for (int c5 = 0; c5 < 5; ++c5) img[ia * IS + c5] = v[0][c5];
+          if (ib != ia)
+            for (int c5 = 0; c5 < 5; ++c5) img[ib * IS + c5] = v[1][c5];
+        }
       }
       __syncthreads();
       if (C.np > 1) {
@@ -423,14 +444,27 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
       }
       const double id = 1.0 / (A00 * A11 - A01 * A10);
       const double m00 = A11 * id, m01 = -A01 * id, m10 = -A10 * id, m11 = A00 * id;
-      const double s0 = C.sinv[3 * i], s1 = C.sinv[3 * i + 1], s2 = C.sinv[3 * i + 2];
-      const double X00 = s0 * m00 + s1 * m10, X01 = s0 * m01 + s1 * m11;
-      const double X10 = s1 * m00 + s2 * m10, X11 = s1 * m01 + s2 * m11;
-      r[5] = m00 * X00 + m10 * X10;
-      r[6] = m00 * X01 + m10 * X11;
-      r[7] = m01 * X01 + m11 * X11;
+      if constexpr (MIXED) {
+        // mu rounded once to FP32 (relative 2^-24, far inside the chi^2 budget); the
+        // magnification tensor M = mu^T S^-1 mu in FP32 saves the 1/72-rate FP64 pipe
+        const float f00 = (float)m00, f01 = (float)m01, f10 = (float)m10, f11 = (float)m11;
+        const float s0 = (float)C.sinv[3 * i], s1 = (float)C.sinv[3 * i + 1], s2 = (float)C.sinv[3 * i + 2];
+        const float X00 = fmaf(s0, f00, s1 * f10), X01 = fmaf(s0, f01, s1 * f11);
+        const float X10 = fmaf(s1, f00, s2 * f10), X11 = fmaf(s1, f01, s2 * f11);
+        r[5] = fmaf(f00, X00, f10 * X10);
+        r[6] = fmaf(f00, X01, f10 * X11);
+        r[7] = fmaf(f01, X01, f11 * X11);
+        r[10] = f00; r[11] = f01; r[12] = f10; r[13] = f11;
+      } else {
+        const double s0 = C.sinv[3 * i], s1 = C.sinv[3 * i + 1], s2 = C.sinv[3 * i + 2];
+        const double X00 = s0 * m00 + s1 * m10, X01 = s0 * m01 + s1 * m11;
+        const double X10 = s1 * m00 + s2 * m10, X11 = s1 * m01 + s2 * m11;
+        r[5] = m00 * X00 + m10 * X10;
+        r[6] = m00 * X01 + m10 * X11;
+        r[7] = m01 * X01 + m11 * X11;
+        r[10] = m00; r[11] = m01; r[12] = m10; r[13] = m11;
+      }
       r[8] = bx; r[9] = by;
-      r[10] = m00; r[11] = m01; r[12] = m10; r[13] = m11;
     }
     __syncthreads();
 
@@ -438,26 +472,32 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
     double my = 0.0;
     for (int f = tid; f < C.n_fam; f += blockDim.x) {
       const int i0 = C.fam_off[f], i1 = C.fam_off[f + 1];
+      // beta_model = beta_ref + G^-1 sum M_i (beta_i - beta_ref) with beta_ref the family's
+      // first image: the same minimiser, with the large common part of beta taken out
+      const double br0 = img[i0 * IS + 8], br1 = img[i0 * IS + 9];
       double G00 = 0, G01 = 0, G11 = 0, g0 = 0, g1 = 0;
       for (int i = i0; i < i1; ++i) {
         const double* r = img + i * IS;
+        const double e0 = r[8] - br0, e1 = r[9] - br1;
         G00 += r[5]; G01 += r[6]; G11 += r[7];
-        g0 += r[5] * r[8] + r[6] * r[9];
-        g1 += r[6] * r[8] + r[7] * r[9];
+        g0 += r[5] * e0 + r[6] * e1;
+        g1 += r[6] * e0 + r[7] * e1;
       }
       double bm0, bm1, cf = 0.0;
       if (i1 - i0 == 1) {
-        bm0 = img[i0 * IS + 8];
-        bm1 = img[i0 * IS + 9];
+        bm0 = br0;
+        bm1 = br1;
         if (!(isfinite(G00) && isfinite(G01) && isfinite(G11) && isfinite(bm0) && isfinite(bm1)))
           cf = INFINITY;
       } else {
         const double dG = G00 * G11 - G01 * G01;
-        bm0 = (G11 * g0 - G01 * g1) / dG;
-        bm1 = (G00 * g1 - G01 * g0) / dG;
+        const double idG = 1.0 / dG;
+        const double c0 = (G11 * g0 - G01 * g1) * idG, c1 = (G00 * g1 - G01 * g0) * idG;
+        bm0 = br0 + c0;
+        bm1 = br1 + c1;
         for (int i = i0; i < i1; ++i) {
           const double* r = img + i * IS;
-          const double d0 = r[8] - bm0, d1 = r[9] - bm1;
+          const double d0 = (r[8] - br0) - c0, d1 = (r[9] - br1) - c1;
           cf += r[5] * d0 * d0 + 2.0 * r[6] * d0 * d1 + r[7] * d1 * d1;
         }
         if (!isfinite(cf) || !(dG > 0.0)) cf = INFINITY;
@@ -495,7 +535,8 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
       lf_scaling ssc = P.sc;
       if (mem_grad) sample_scaling(C, th, ssc);
       const T inv_cut_star = (T)(1.0 / ssc.cut_star);
-      for (int t = tid; t < ntask; t += blockDim.x) {
+      const int ntask_img = n_img * KS;   // one image per task in the adjoint pass
+      for (int t = tid; t < ntask_img; t += blockDim.x) {
         const int i = t / KS, k = t - i * KS;
         const int k0 = (int)((long long)K * k / KS), k1 = (int)((long long)K * (k + 1) / KS);
         const double* r = img + i * IS;
@@ -635,7 +676,7 @@ static int choose_ks(int n_img, int K, int block, int cap) {
   double best_cost = 1e300;
   for (int ks = 1; ks <= 32 && ks <= cap; ks *= 2) {
     if (ks > 1 && K / ks < 8) break;
-    long long tasks = (long long)n_img * ks;
+    long long tasks = (long long)((n_img + 1) / 2) * ks;   // image pairs x slices
     long long rounds = (tasks + block - 1) / block;
     double cost = (double)rounds * ((double)K / ks + overhead);
     if (cost < best_cost * 0.97) { best_cost = cost; best = ks; }
@@ -645,14 +686,13 @@ static int choose_ks(int n_img, int K, int block, int cap) {
 
 static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap) {
   const bool mixed = precision != LF_FP64;
-  const uint32_t pre_sz = precision == LF_MIXED ? sizeof(MemPreF) : sizeof(MemPreD);
   const uint32_t mem_sz = precision == LF_FF ? sizeof(MemX) : precision == LF_MIXED ? sizeof(MemT<float>)
                                                                                    : sizeof(MemT<double>);
   uint32_t o = LF_HDR;
   for (int j = 0; j < C.np; ++j) {
     PlaneDesc& P = C.pl[j];
     o = (o + 15u) & ~15u; P.off_rawc = o; o += (uint32_t)P.nc * 64u;
-    o = (o + 15u) & ~15u; P.off_mpre = o; o += (uint32_t)P.nm * pre_sz;
+    P.off_mpre = 0;   // the member pre-table is read from global memory, not staged
     o = (o + 15u) & ~15u; P.off_dc = o; o += (uint32_t)P.nc * (mixed ? sizeof(CompT<float>) : sizeof(CompT<double>));
     o = (o + 15u) & ~15u; P.off_dm = o; o += (uint32_t)P.nm * mem_sz;
   }

@@ -17,6 +17,8 @@
 #include <stdint.h>
 #include <math.h>
 
+#include <type_traits>
+
 #define LF_INLINE __device__ __forceinline__
 #ifndef LF_NOINLINE
 #define LF_NOINLINE __device__ __noinline__
@@ -258,6 +260,8 @@ LF_INLINE void cored_round(T r2, T s, T s2, T& kbar, T& t) {
 // P = PQ (R + a), Q = PQ (S + s).  The tensor term t = 2 (kappa - kbar)/r^2 =
 // b (Q^2/R - P^2/S) cancels only where it is small (|t r^2| ~ 2 b (a - s)/r^2).
 // alpha = kbar x, psi_ij = kbar delta_ij + t x_i x_j.
+// In FP64 the plain difference b (P - Q) keeps ~48 bits in the far field, so the FP64
+// path (the plain comparator) uses it and saves a reciprocal.
 template <class T>
 LF_INLINE void pje_round(T dx, T dy, T b, T s, T s2, T a, T a2, Out5<T>& o) {
   T r2 = lf_fma(dx, dx, dy * dy);
@@ -267,7 +271,9 @@ LF_INLINE void pje_round(T dx, T dy, T b, T s, T s2, T a, T a2, Out5<T>& o) {
   T Ss = S + s, Ra = R + a;
   T PQ = lf_rcp(Ss * Ra);
   T P = PQ * Ra, Q = PQ * Ss;
-  T kbar = b * (a - s) * PQ * lf_fma(a + s, lf_rcp(R + S), (T)1);
+  T kbar;
+  if constexpr (std::is_same<T, double>::value) kbar = b * (P - Q);
+  else kbar = b * (a - s) * PQ * lf_fma(a + s, lf_rcp(R + S), (T)1);
   T t = b * (Q * Q * iR - P * P * iS);
   o.ax = kbar * dx;
   o.ay = kbar * dy;
@@ -366,10 +372,13 @@ template <class T> struct CompT {
 };
 
 // A cluster member (round pseudo-Jaffe) prepared for evaluation in precision T.
+// The first three 16-byte groups are what the evaluation reads; the fourth is read only by
+// the adjoint.
 template <class T> struct MemT {
   T xh, xl, yh, yl;
-  T b, s, a, fb;          // fb = (L/L*)^(2 lam) = b / b*
-  T s2, a2, loglr, fs;    // loglr = ln(L/L*), fs = (L/L*)^beta = s / core*
+  T bd, s, a, apc;        // bd = b (a - s), apc = a + s
+  T s2, a2, b, fb;        // fb = (L/L*)^(2 lam) = b / b*
+  T fs, loglr, pad0, pad1;  // fs = (L/L*)^beta = s / core*, loglr = ln(L/L*)
 };
 
 // Builds the evaluation constants of one explicit component from its fields.
@@ -387,13 +396,10 @@ __host__ __device__ inline void digest_comp(int kind, double x, double y, double
   }
   double q = (1.0 - eps) / (1.0 + eps);
   double e = sqrt((1.0 - q) * (1.0 + q));
-  if (kind == K_SHEAR) {
-    c.c = (T)cos(2.0 * pa);
-    c.sn = (T)sin(2.0 * pa);
-  } else {
-    c.c = (T)cos(pa);
-    c.sn = (T)sin(pa);
-  }
+  double cc, ss;
+  sincos(kind == K_SHEAR ? 2.0 * pa : pa, &ss, &cc);
+  c.c = (T)cc;
+  c.sn = (T)ss;
   c.b = (T)b;
   c.q = (T)q; c.q2 = (T)(q * q); c.e = (T)e; c.qe = (T)(e > 0 ? q / e : 0.0);
   c.s1 = (T)core; c.s1sq = (T)(core * core); c.q2s1 = (T)(q * q * core);
@@ -402,8 +408,6 @@ __host__ __device__ inline void digest_comp(int kind, double x, double y, double
   c.D02 = (T)((1.0 + q * q) * cut * cut);
   c.irs = (T)(kind == K_NFW && core > 0 ? 1.0 / core : 0.0);
   // low words: v - (T)v (zero when T is double)
-  const double cc = kind == K_SHEAR ? cos(2.0 * pa) : cos(pa);
-  const double ss = kind == K_SHEAR ? sin(2.0 * pa) : sin(pa);
   const double q2 = q * q, qe = e > 0 ? q / e : 0.0;
   c.lc = (T)(cc - (double)c.c); c.lsn = (T)(ss - (double)c.sn); c.lb = (T)(b - (double)c.b);
   c.lq2 = (T)(q2 - (double)c.q2); c.le = (T)(e - (double)c.e); c.lqe = (T)(qe - (double)c.qe);
@@ -424,8 +428,9 @@ __host__ __device__ inline void digest_member(double x, double y, double b, doub
   } else {
     m.xh = (T)x; m.xl = (T)0; m.yh = (T)y; m.yl = (T)0;
   }
-  m.b = (T)b; m.s = (T)s; m.a = (T)a; m.fb = (T)fb;
-  m.s2 = (T)(s * s); m.a2 = (T)(a * a); m.loglr = (T)loglr; m.fs = (T)fs;
+  m.bd = (T)(b * (a - s)); m.s = (T)s; m.a = (T)a; m.apc = (T)(a + s);
+  m.s2 = (T)(s * s); m.a2 = (T)(a * a); m.b = (T)b; m.fb = (T)fb;
+  m.fs = (T)fs; m.loglr = (T)loglr; m.pad0 = (T)0; m.pad1 = (T)0;
 }
 
 // Offset from a centre: float-float difference for FP32, plain for FP64.
@@ -474,9 +479,25 @@ LF_INLINE void eval_comp(const CompT<T>& c, T dx, T dy, Out5<T>& o) {
   rotate_back(c.c, c.sn, au, av, puu, pvv, puv, o);
 }
 
+// One member with its precomputed b (a - s) and a + s (same forms as pje_round).
 template <class T>
 LF_INLINE void eval_member(const MemT<T>& m, T dx, T dy, Out5<T>& o) {
-  pje_round(dx, dy, m.b, m.s, m.s2, m.a, m.a2, o);
+  T r2 = lf_fma(dx, dx, dy * dy);
+  T S2 = m.s2 + r2, R2 = m.a2 + r2;
+  T iS = lf_rsqrt(S2), iR = lf_rsqrt(R2);
+  T S = S2 * iS, R = R2 * iR;
+  T Ss = S + m.s, Ra = R + m.a;
+  T PQ = lf_rcp(Ss * Ra);
+  T P = PQ * Ra, Q = PQ * Ss;
+  T kbar;
+  if constexpr (std::is_same<T, double>::value) kbar = m.b * (P - Q);
+  else kbar = m.bd * PQ * lf_fma(m.apc, lf_rcp(R + S), (T)1);
+  T t = m.b * (Q * Q * iR - P * P * iS);
+  o.ax = kbar * dx;
+  o.ay = kbar * dy;
+  o.pxx = lf_fma(t * dx, dx, kbar);
+  o.pyy = lf_fma(t * dy, dy, kbar);
+  o.pxy = t * dx * dy;
 }
 
 // ------------------------------------- extended-precision deflection (mixed path) ---

@@ -132,6 +132,10 @@ __device__ __forceinline__ void accumulate_mixed(const CompT<float>* dc, int nc,
     }
   }
   const int m_beg = max(k0, nc) - nc, m_end = min(k1, nc + nm) - nc;
+  // all PPT positions on one row (the usual case on grids): one y offset per member
+  bool same_y = true;
+#pragma unroll
+  for (int k = 1; k < PPT; ++k) same_y = same_y && pyh[k] == pyh[0] && pyl[k] == pyl[0];
   for (int m0 = m_beg; m0 < m_end; m0 += chunk) {
     const int m1 = min(m0 + chunk, m_end);
     float cs[5][PPT];
@@ -139,16 +143,31 @@ __device__ __forceinline__ void accumulate_mixed(const CompT<float>* dc, int nc,
     for (int v = 0; v < 5; ++v)
 #pragma unroll
       for (int k = 0; k < PPT; ++k) cs[v][k] = 0.f;
-    for (int m = m0; m < m1; ++m) {
-      const MemT<float> M = dm[m];
+    if (same_y) {
+      for (int m = m0; m < m1; ++m) {
+        const MemT<float> M = dm[m];
+        const float dy = offset_of(pyh[0], pyl[0], M.yh, M.yl);
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        float dx = offset_of(pxh[k], pxl[k], M.xh, M.xl);
-        float dy = offset_of(pyh[k], pyl[k], M.yh, M.yl);
-        Out5<float> o;
-        eval_member(M, dx, dy, o);
-        cs[0][k] += o.ax; cs[1][k] += o.ay;
-        cs[2][k] += o.pxx; cs[3][k] += o.pyy; cs[4][k] += o.pxy;
+        for (int k = 0; k < PPT; ++k) {
+          float dx = offset_of(pxh[k], pxl[k], M.xh, M.xl);
+          Out5<float> o;
+          eval_member(M, dx, dy, o);
+          cs[0][k] += o.ax; cs[1][k] += o.ay;
+          cs[2][k] += o.pxx; cs[3][k] += o.pyy; cs[4][k] += o.pxy;
+        }
+      }
+    } else {
+      for (int m = m0; m < m1; ++m) {
+        const MemT<float> M = dm[m];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          float dx = offset_of(pxh[k], pxl[k], M.xh, M.xl);
+          float dy = offset_of(pyh[k], pyl[k], M.yh, M.yl);
+          Out5<float> o;
+          eval_member(M, dx, dy, o);
+          cs[0][k] += o.ax; cs[1][k] += o.ay;
+          cs[2][k] += o.pxx; cs[3][k] += o.pyy; cs[4][k] += o.pxy;
+        }
       }
     }
 #pragma unroll

@@ -57,7 +57,10 @@ __device__ __forceinline__ void write_out(const OutArgs& O, long long p, double 
 
 // ------------------------------------------------------------------- LF_MIXED ------
 #ifndef LF_MAP_MINB
-#define LF_MAP_MINB 1
+#define LF_MAP_MINB 3   // at most 85 registers: 3 blocks of 256 per SM
+#endif
+#ifndef LF_MAP_PPT
+#define LF_MAP_PPT 2
 #endif
 template <int PPT, bool EXT>
 __global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_mixed(const lf_comp* __restrict__ comp, int nc,
@@ -189,7 +192,7 @@ static lf_status launch_map(const lf_plane* pl, const PosArgs& P, const OutArgs&
   LF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int block = 256;
   if (precision == LF_MIXED) {
-    LF_TRY((launch_mixed<2, false>(pl, P, O, nsm, block, s)));
+    LF_TRY((launch_mixed<LF_MAP_PPT, false>(pl, P, O, nsm, block, s)));
   } else if (precision == LF_FF) {
     LF_TRY((launch_mixed<1, true>(pl, P, O, nsm, block, s)));
   } else {

@@ -5,7 +5,7 @@
 namespace lf {
 
 #ifndef LF_CHUNK
-#define LF_CHUNK 8
+#define LF_CHUNK 16
 #endif
 int g_member_chunk = LF_CHUNK;
 
