@@ -34,7 +34,7 @@ METRIC = "lens evals/s (samples×positions×components)"
 UNIT = "lens evals/s"
 WORKLOAD = ("cluster_dpie302_grid4096: 2 elliptical dPIE halos + 300 PJE members, "
             "4096x4096 grid at 0.04\", alpha/kappa/gamma/mu at z_s=9")
-FP32_INSTR_PER_EVAL = 35      # FP32-pipe instructions of one member evaluation
+FP32_INSTR_PER_EVAL = 39      # FP32-pipe instructions of one member evaluation
 XU_INSTR_PER_EVAL = 4         # MUFU instructions of one member evaluation
 FP32_LANES_PER_SM, XU_LANES_PER_SM = 128, 16
 
@@ -271,13 +271,7 @@ def main():
     xu_peak = nsm * XU_LANES_PER_SM * sm_max / 1e12
     fp32_ach = evals * FP32_INSTR_PER_EVAL / (ms * 1e-3) / 1e12
     xu_ach = evals * XU_INSTR_PER_EVAL / (ms * 1e-3) / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "k_map_mixed_traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
-        except ValueError:
-            traffic = None
+    traffic = map_kernel_traffic() if args.precision == "mixed" and args.grid == 4096 else None
     roofline = {"bound": "alu", "achieved": fp32_ach, "peak": fp32_peak, "unit": "Tinst/s (FP32 pipe)",
                 "frac": fp32_ach / fp32_peak, "traffic": traffic,
                 "xu": {"achieved": xu_ach, "peak": xu_peak, "frac": xu_ach / xu_peak},
@@ -309,6 +303,26 @@ def main():
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+KERNEL_SOURCES = ["lf_common.cuh", "lf_eval.cuh", "lf_grid.cu", "lf_host.cu", "lf_internal.h"]
+
+
+def map_kernel_traffic():
+    """DRAM bytes per launch of the headline kernel from the committed ncu capture, or None
+    when the kernel's sources changed since the counters were taken."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "k_map_mixed_traffic.json")
+    if not os.path.exists(prof):
+        return None
+    try:
+        rec = json.load(open(prof))
+    except ValueError:
+        return None
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2609_08649_b300", "csrc", f), "rb").read())
+    return rec.get("dram_bytes_per_launch") if h.hexdigest()[:16] == rec.get("source_digest") else None
 
 
 def _time(torch, fn, reps=3, warm=1):
