@@ -73,8 +73,14 @@ struct ClusterDesc {
   int p_xform[LF_MAX_P];
   int p_plane[LF_MAX_P];
   int ks;
-  int img_stride;                  // doubles per image record
-  uint32_t off_img, off_fam, off_par, off_free, smem;
+  int img_stride;                  // FP64 records: doubles per image (LF_FP64 tier)
+  int img_stride_f;                // mixed tiers: floats per image
+  int img_stride_d;                // mixed tiers: doubles per image (multi-plane state)
+  // mixed tiers: positions, distance ratios and S^-1 split for float-float / FP32 use
+  const float4* theta_ff;          // [n_img] (x_hi, x_lo, y_hi, y_lo)
+  const float2* ratio_ff;          // [n_fam * np]
+  const float4* sinv_f;            // [n_img] (xx, xy, yy, 0)
+  uint32_t off_img, off_imgd, off_fam, off_par, off_free, smem;
 };
 
 // ------------------------------------------------------------------ transforms -----
@@ -200,11 +206,39 @@ template <class T> __device__ __forceinline__ T mem_a(const MemT<T>& m) { return
 __device__ __forceinline__ float mem_s(const MemX& m) { return m.sh; }
 __device__ __forceinline__ float mem_a(const MemX& m) { return m.ah; }
 
+// Sampled components of every sample, digested in one pass over (sample, component) before the
+// chi^2 kernel (their FP64 set-up is then off the per-sample critical path).
+template <int MODE>
+__global__ void k_chi2_prep(const ClusterDesc* __restrict__ cds, int spc, int S,
+                            const double* __restrict__ theta, void* dig, lf_comp* raw) {
+  typedef typename std::conditional<MODE != LF_FP64, float, double>::type T;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = idx / LF_MAX_FREE, f = idx - s * LF_MAX_FREE;
+  if (s >= S) return;
+  const ClusterDesc& C = cds[s / spc];
+  if (f >= C.n_free) return;
+  const PlaneDesc& P = C.pl[C.free_plane[f]];
+  lf_comp rc = P.comp[C.free_comp[f]];
+  for (int fld = 0; fld < 7; ++fld) {
+    const int p = C.free_p[f][fld];
+    if (p >= 0) set_field(rc, fld, apply_xform(C.p_xform[p], theta[(size_t)s * C.P + p], P.apk));
+  }
+  raw[idx] = rc;
+  digest_one_comp<T>(rc, reinterpret_cast<CompT<T>*>(dig)[idx]);
+}
+
+// Record of one image in the mixed tiers (floats): [0..9] alpha, psi sums as float-float pairs
+// (then the five cotangents in [0..4]); [10..13] beta (x_hi, x_lo, y_hi, y_lo); [14..16] M;
+// [17..20] mu (00, 01, 10, 11).
+constexpr int IMGF = 22;
+
 template <int MODE, bool GRAD>   // MODE: LF_FP64, LF_MIXED or LF_FF
 __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cds,
                                               const int* __restrict__ corder, int spc, int S,
                                               const double* __restrict__ theta, double* chi2,
-                                              double* grad, int* counter, int chunk) {
+                                              double* grad, int* counter, int chunk,
+                                              const void* __restrict__ free_dig,
+                                              const lf_comp* __restrict__ free_raw) {
   constexpr bool MIXED = MODE != LF_FP64;
   typedef typename std::conditional<MIXED, float, double>::type T;
   typedef typename std::conditional<MODE == LF_MIXED, MemPreF, MemPreD>::type MemPre;
@@ -233,7 +267,9 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
     double* th = reinterpret_cast<double*>(smem + C.off_par);
     double* gacc = th + C.P;
     lf_comp* fraw = reinterpret_cast<lf_comp*>(smem + C.off_free);
-    double* img = reinterpret_cast<double*>(smem + C.off_img);
+    double* img = reinterpret_cast<double*>(smem + C.off_img);      // LF_FP64 records
+    float* imgf = reinterpret_cast<float*>(smem + C.off_img);       // mixed-tier records
+    double* imgd = reinterpret_cast<double*>(smem + C.off_imgd);    // mixed-tier multi-plane state
     double* fam = reinterpret_cast<double*>(smem + C.off_fam);
     for (int p = tid; p < C.P; p += blockDim.x) {
       th[p] = theta[(size_t)s * C.P + p];
@@ -263,14 +299,20 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
     // ---- A1: this sample's parameters into the tables
     for (int f = tid; f < C.n_free; f += blockDim.x) {
       const PlaneDesc& P = C.pl[C.free_plane[f]];
-      const lf_comp* rawc = reinterpret_cast<const lf_comp*>(smem + P.off_rawc);
-      lf_comp rc = rawc[C.free_comp[f]];
-      for (int fld = 0; fld < 7; ++fld) {
-        int p = C.free_p[f][fld];
-        if (p >= 0) set_field(rc, fld, apply_xform(C.p_xform[p], th[p], P.apk));
+      CompT<T>* slot = reinterpret_cast<CompT<T>*>(smem + P.off_dc) + C.free_comp[f];
+      if (free_dig) {            // digested by k_chi2_prep
+        *slot = reinterpret_cast<const CompT<T>*>(free_dig)[(size_t)s * LF_MAX_FREE + f];
+        if (GRAD) fraw[f] = free_raw[(size_t)s * LF_MAX_FREE + f];
+      } else {
+        const lf_comp* rawc = reinterpret_cast<const lf_comp*>(smem + P.off_rawc);
+        lf_comp rc = rawc[C.free_comp[f]];
+        for (int fld = 0; fld < 7; ++fld) {
+          int p = C.free_p[f][fld];
+          if (p >= 0) set_field(rc, fld, apply_xform(C.p_xform[p], th[p], P.apk));
+        }
+        fraw[f] = rc;
+        digest_one_comp<T>(rc, *slot);
       }
-      fraw[f] = rc;
-      digest_one_comp<T>(rc, reinterpret_cast<CompT<T>*>(smem + P.off_dc)[C.free_comp[f]]);
     }
     for (int j = 0; j < C.np; ++j) {
       const PlaneDesc& P = C.pl[j];
@@ -291,34 +333,33 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
           const double fa = alpha_free ? exp(sc.alpha * m.lnl) : m.fa;
           digest_member_x(m.x, m.y, sc.b_star * fb, sc.core_star * fs, sc.cut_star * fa, m.lnl,
                           dm[i], fb, fs);
-          continue;
         } else {
-        T fb, fs, fa;
-        MemT<T> d;
-        if constexpr (MODE == LF_MIXED) {
-          fb = lam_free ? m.fb + fmaf(m.fb, expm1f((float)(2.0 * (sc.lam - P.sc.lam)) * m.lnl), m.fbl) : m.fb;
-          fs = beta_free ? m.fs + fmaf(m.fs, expm1f((float)(sc.beta - P.sc.beta) * m.lnl), m.fsl) : m.fs;
-          fa = alpha_free ? m.fa + fmaf(m.fa, expm1f((float)(sc.alpha - P.sc.alpha) * m.lnl), m.fal) : m.fa;
-          d.xh = m.xh; d.xl = m.xl; d.yh = m.yh; d.yl = m.yl;
-        } else {
-          fb = lam_free ? exp(2.0 * sc.lam * m.lnl) : m.fb;
-          fs = beta_free ? exp(sc.beta * m.lnl) : m.fs;
-          fa = alpha_free ? exp(sc.alpha * m.lnl) : m.fa;
-          d.xh = m.x; d.xl = 0; d.yh = m.y; d.yl = 0;
-        }
-        d.b = (T)sc.b_star * fb;
-        d.s = (T)sc.core_star * fs;
-        d.a = (T)sc.cut_star * fa;
-        d.bd = d.b * (d.a - d.s);
-        d.apc = d.a + d.s;
-        d.fb = fb;
-        d.fs = fs;
-        d.s2 = d.s * d.s;
-        d.a2 = d.a * d.a;
-        d.loglr = (T)m.lnl;
-        d.pad0 = (T)0;
-        d.pad1 = (T)0;
-        dm[i] = d;
+          T fb, fs, fa;
+          MemT<T> d;
+          if constexpr (MODE == LF_MIXED) {
+            fb = lam_free ? m.fb + fmaf(m.fb, expm1f((float)(2.0 * (sc.lam - P.sc.lam)) * m.lnl), m.fbl) : m.fb;
+            fs = beta_free ? m.fs + fmaf(m.fs, expm1f((float)(sc.beta - P.sc.beta) * m.lnl), m.fsl) : m.fs;
+            fa = alpha_free ? m.fa + fmaf(m.fa, expm1f((float)(sc.alpha - P.sc.alpha) * m.lnl), m.fal) : m.fa;
+            d.xh = m.xh; d.xl = m.xl; d.yh = m.yh; d.yl = m.yl;
+          } else {
+            fb = lam_free ? exp(2.0 * sc.lam * m.lnl) : m.fb;
+            fs = beta_free ? exp(sc.beta * m.lnl) : m.fs;
+            fa = alpha_free ? exp(sc.alpha * m.lnl) : m.fa;
+            d.xh = m.x; d.xl = 0; d.yh = m.y; d.yl = 0;
+          }
+          d.b = (T)sc.b_star * fb;
+          d.s = (T)sc.core_star * fs;
+          d.a = (T)sc.cut_star * fa;
+          d.bd = d.b * (d.a - d.s);
+          d.apc = d.a + d.s;
+          d.fb = fb;
+          d.fs = fs;
+          d.s2 = d.s * d.s;
+          d.a2 = d.a * d.a;
+          d.loglr = (T)m.lnl;
+          d.pad0 = (T)0;
+          d.pad1 = (T)0;
+          dm[i] = d;
         }
       }
     }
@@ -326,7 +367,8 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
 
     // ---- A3-A6: alpha and Psi at every image, plane by plane.  A task is (image pair,
     // component slice): two images per thread give two independent evaluation chains.
-    const int n_img = C.n_img, KS = C.ks, IS = C.img_stride;
+    const int n_img = C.n_img, KS = C.ks, IS = C.img_stride, ISF = C.img_stride_f,
+              ISD = C.img_stride_d;
     const int n_pair = (n_img + 1) >> 1;
     const int ntask = n_pair * KS;
     for (int j = 0; j < C.np; ++j) {
@@ -340,122 +382,222 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
         const int pr = act ? t / KS : 0;
         const int k = act ? t - pr * KS : 0;
         const int ia = 2 * pr, ib = min(2 * pr + 1, n_img - 1);
-        double v[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
-        if (act) {
-          const int k0 = (int)((long long)K * k / KS), k1 = (int)((long long)K * (k + 1) / KS);
-          double x[2], y[2];
+        const int k0 = (int)((long long)K * k / KS), k1 = (int)((long long)K * (k + 1) / KS);
+        if constexpr (MIXED) {
+          float xh[2], xl[2], yh[2], yl[2];
           const int ii[2] = {ia, ib};
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
             if (j == 0) {
-              x[q] = C.theta[2 * ii[q]];
-              y[q] = C.theta[2 * ii[q] + 1];
+              const float4 tf = C.theta_ff[ii[q]];
+              xh[q] = tf.x; xl[q] = tf.y; yh[q] = tf.z; yl[q] = tf.w;
             } else {
-              x[q] = img[ii[q] * IS + 14];
-              y[q] = img[ii[q] * IS + 15];
+              split_ff(imgd[ii[q] * ISD + 0], xh[q], xl[q]);
+              split_ff(imgd[ii[q] * ISD + 1], yh[q], yl[q]);
             }
           }
-          if constexpr (MIXED) {
-            float xh[2], xl[2], yh[2], yl[2];
+          ff acc[5][2];
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              split_ff(x[q], xh[q], xl[q]);
-              split_ff(y[q], yh[q], yl[q]);
-            }
-            ff acc[5][2];
-#pragma unroll
-            for (int c5 = 0; c5 < 5; ++c5) acc[c5][0] = acc[c5][1] = ff_zero();
+          for (int c5 = 0; c5 < 5; ++c5) acc[c5][0] = acc[c5][1] = ff_zero();
+          if (act) {
             if constexpr (MODE == LF_FF)
               accumulate_ext<2>(dc, P.nc, dm, P.nm, k0, k1, xh, xl, yh, yl, tab, acc);
             else
               accumulate_mixed<2>(dc, P.nc, dm, P.nm, k0, k1, chunk, xh, xl, yh, yl, tab, acc);
+          }
+          for (int off = 1; off < KS; off <<= 1)
+#pragma unroll
+            for (int c5 = 0; c5 < 5; ++c5)
+#pragma unroll
+              for (int q = 0; q < 2; ++q) {
+                ff o;
+                o.hi = __shfl_xor_sync(0xffffffffu, acc[c5][q].hi, off);
+                o.lo = __shfl_xor_sync(0xffffffffu, acc[c5][q].lo, off);
+                acc[c5][q] = ff_add(acc[c5][q], o);
+              }
+          if (act && k == 0) {
+            for (int c5 = 0; c5 < 5; ++c5) {
+              imgf[ia * ISF + 2 * c5] = acc[c5][0].hi;
+              imgf[ia * ISF + 2 * c5 + 1] = acc[c5][0].lo;
+            }
+            if (ib != ia)
+              for (int c5 = 0; c5 < 5; ++c5) {
+                imgf[ib * ISF + 2 * c5] = acc[c5][1].hi;
+                imgf[ib * ISF + 2 * c5 + 1] = acc[c5][1].lo;
+              }
+          }
+        } else {
+          double v[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+          if (act) {
+            const int ii[2] = {ia, ib};
+            for (int q = 0; q < 2; ++q) {
+              const double x = j == 0 ? C.theta[2 * ii[q]] : img[ii[q] * IS + 14];
+              const double y = j == 0 ? C.theta[2 * ii[q] + 1] : img[ii[q] * IS + 15];
+              accumulate_fp64(dc, P.nc, dm, P.nm, k0, k1, x, y, v[q]);
+            }
+          }
+          for (int off = 1; off < KS; off <<= 1)
 #pragma unroll
             for (int c5 = 0; c5 < 5; ++c5) {
-              v[0][c5] = ff_to_double(acc[c5][0]);
-              v[1][c5] = ff_to_double(acc[c5][1]);
+              v[0][c5] += __shfl_xor_sync(0xffffffffu, v[0][c5], off);
+              v[1][c5] += __shfl_xor_sync(0xffffffffu, v[1][c5], off);
             }
-          } else {
-            accumulate_fp64(dc, P.nc, dm, P.nm, k0, k1, x[0], y[0], v[0]);
-            accumulate_fp64(dc, P.nc, dm, P.nm, k0, k1, x[1], y[1], v[1]);
+          if (act && k == 0) {
+            for (int c5 = 0; c5 < 5; ++c5) img[ia * IS + c5] = v[0][c5];
+            if (ib != ia)
+              for (int c5 = 0; c5 < 5; ++c5) img[ib * IS + c5] = v[1][c5];
           }
-        }
-        for (int off = 1; off < KS; off <<= 1)
-#pragma unroll
-          for (int c5 = 0; c5 < 5; ++c5) {
-            v[0][c5] += __shfl_xor_sync(0xffffffffu, v[0][c5], off);
-            v[1][c5] += __shfl_xor_sync(0xffffffffu, v[1][c5], off);
-          }
-        if (act && k == 0) {
-          for (int c5 = 0; c5 < 5; ++c5) img[ia * IS + c5] = v[0][c5];
-          if (ib != ia)
-            for (int c5 = 0; c5 < 5; ++c5) img[ib * IS + c5] = v[1][c5];
         }
       }
       __syncthreads();
       if (C.np > 1) {
-        // recursion state: [14..15] theta_{j+1}, then per plane alpha (2) and Psi_j A_j (4)
+        // recursion state (FP64): theta_{j+1}, then per plane alpha (2) and Psi_j A_j (4)
         for (int i = tid; i < n_img; i += blockDim.x) {
-          double* r = img + i * IS;
+          double sm[5];
+          double* st;
+          if constexpr (MIXED) {
+            for (int c5 = 0; c5 < 5; ++c5)
+              sm[c5] = (double)imgf[i * ISF + 2 * c5] + (double)imgf[i * ISF + 2 * c5 + 1];
+            st = imgd + i * ISD;
+          } else {
+            for (int c5 = 0; c5 < 5; ++c5) sm[c5] = img[i * IS + c5];
+            st = img + i * IS + 14;
+          }
           double a00 = 1, a01 = 0, a10 = 0, a11 = 1;
           for (int l = 0; l < j; ++l) {
-            const double* pl = r + 16 + 6 * l;
+            const double* pl = st + 2 + 6 * l;
             double rr = C.r[l][j];
             a00 -= rr * pl[2]; a01 -= rr * pl[3]; a10 -= rr * pl[4]; a11 -= rr * pl[5];
           }
-          double* pj = r + 16 + 6 * j;
-          pj[0] = r[0]; pj[1] = r[1];
-          pj[2] = r[2] * a00 + r[4] * a10;
-          pj[3] = r[2] * a01 + r[4] * a11;
-          pj[4] = r[4] * a00 + r[3] * a10;
-          pj[5] = r[4] * a01 + r[3] * a11;
+          double* pj = st + 2 + 6 * j;
+          pj[0] = sm[0]; pj[1] = sm[1];
+          pj[2] = sm[2] * a00 + sm[4] * a10;
+          pj[3] = sm[2] * a01 + sm[4] * a11;
+          pj[4] = sm[4] * a00 + sm[3] * a10;
+          pj[5] = sm[4] * a01 + sm[3] * a11;
           if (j + 1 < C.np) {
             double tx = C.theta[2 * i], ty = C.theta[2 * i + 1];
             for (int l = 0; l <= j; ++l) {
-              tx -= C.r[l][j + 1] * r[16 + 6 * l];
-              ty -= C.r[l][j + 1] * r[16 + 6 * l + 1];
+              tx -= C.r[l][j + 1] * st[2 + 6 * l];
+              ty -= C.r[l][j + 1] * st[2 + 6 * l + 1];
             }
-            r[14] = tx;
-            r[15] = ty;
+            st[0] = tx;
+            st[1] = ty;
           }
         }
         __syncthreads();
       }
     }
 
-    // ---- A5, A7: beta_i, A_i, mu_i, M_i (FP64)
-    for (int i = tid; i < n_img; i += blockDim.x) {
-      double* r = img + i * IS;
-      const int f = C.img_fam[i];
-      const double tx = C.theta[2 * i], ty = C.theta[2 * i + 1];
-      double bx, by, A00, A01, A10, A11;
-      if (C.np == 1) {
-        const double a = C.fam_ratio[f];
-        bx = tx - a * r[0];
-        by = ty - a * r[1];
-        A00 = 1.0 - a * r[2]; A11 = 1.0 - a * r[3]; A01 = A10 = -a * r[4];
-      } else {
-        bx = tx; by = ty; A00 = 1; A01 = 0; A10 = 0; A11 = 1;
-        for (int l = 0; l < C.np; ++l) {
-          const double rs = C.fam_ratio[f * C.np + l];
-          const double* pl = r + 16 + 6 * l;
-          bx -= rs * pl[0]; by -= rs * pl[1];
-          A00 -= rs * pl[2]; A01 -= rs * pl[3]; A10 -= rs * pl[4]; A11 -= rs * pl[5];
+    double my = 0.0;
+    if constexpr (MIXED) {
+      // ---- A5, A7 (mixed tiers): beta in float-float, det A in float-float, then
+      // mu = A^-1 and M = mu^T S^-1 mu in FP32
+      for (int i = tid; i < n_img; i += blockDim.x) {
+        float* r = imgf + i * ISF;
+        const int f = C.img_fam[i];
+        ff bx, by;
+        float a00, a01, a10, a11, det;
+        if (C.np == 1) {
+          const float2 af = C.ratio_ff[f];
+          const ff a = ff_make(af.x, af.y);
+          const float4 tf = C.theta_ff[i];
+          bx = ff_sub(ff_make(tf.x, tf.y), ff_mul(a, ff_make(r[0], r[1])));
+          by = ff_sub(ff_make(tf.z, tf.w), ff_mul(a, ff_make(r[2], r[3])));
+          const ff A00 = ff_add_f(ff_neg(ff_mul(a, ff_make(r[4], r[5]))), 1.0f);
+          const ff A11 = ff_add_f(ff_neg(ff_mul(a, ff_make(r[6], r[7]))), 1.0f);
+          const ff A01 = ff_neg(ff_mul(a, ff_make(r[8], r[9])));
+          det = ff_sub(ff_mul(A00, A11), ff_sqr(A01)).hi;
+          a00 = A00.hi; a11 = A11.hi; a01 = a10 = A01.hi;
+        } else {
+          const double* st = imgd + i * ISD;
+          double dbx = C.theta[2 * i], dby = C.theta[2 * i + 1];
+          double A00 = 1, A01 = 0, A10 = 0, A11 = 1;
+          for (int l = 0; l < C.np; ++l) {
+            const double rs = C.fam_ratio[f * C.np + l];
+            const double* pl = st + 2 + 6 * l;
+            dbx -= rs * pl[0]; dby -= rs * pl[1];
+            A00 -= rs * pl[2]; A01 -= rs * pl[3]; A10 -= rs * pl[4]; A11 -= rs * pl[5];
+          }
+          bx = ff_from_double(dbx);
+          by = ff_from_double(dby);
+          det = (float)(A00 * A11 - A01 * A10);
+          a00 = (float)A00; a01 = (float)A01; a10 = (float)A10; a11 = (float)A11;
         }
+        const float id = 1.0f / det;
+        const float m00 = a11 * id, m01 = -a01 * id, m10 = -a10 * id, m11 = a00 * id;
+        const float4 sv = C.sinv_f[i];
+        const float X00 = fmaf(sv.x, m00, sv.y * m10), X01 = fmaf(sv.x, m01, sv.y * m11);
+        const float X10 = fmaf(sv.y, m00, sv.z * m10), X11 = fmaf(sv.y, m01, sv.z * m11);
+        r[10] = bx.hi; r[11] = bx.lo; r[12] = by.hi; r[13] = by.lo;
+        r[14] = fmaf(m00, X00, m10 * X10);
+        r[15] = fmaf(m00, X01, m10 * X11);
+        r[16] = fmaf(m01, X01, m11 * X11);
+        r[17] = m00; r[18] = m01; r[19] = m10; r[20] = m11;
       }
-      const double id = 1.0 / (A00 * A11 - A01 * A10);
-      const double m00 = A11 * id, m01 = -A01 * id, m10 = -A10 * id, m11 = A00 * id;
-      if constexpr (MIXED) {
-        // mu rounded once to FP32 (relative 2^-24, far inside the chi^2 budget); the
-        // magnification tensor M = mu^T S^-1 mu in FP32 saves the 1/72-rate FP64 pipe
-        const float f00 = (float)m00, f01 = (float)m01, f10 = (float)m10, f11 = (float)m11;
-        const float s0 = (float)C.sinv[3 * i], s1 = (float)C.sinv[3 * i + 1], s2 = (float)C.sinv[3 * i + 2];
-        const float X00 = fmaf(s0, f00, s1 * f10), X01 = fmaf(s0, f01, s1 * f11);
-        const float X10 = fmaf(s1, f00, s2 * f10), X11 = fmaf(s1, f01, s2 * f11);
-        r[5] = fmaf(f00, X00, f10 * X10);
-        r[6] = fmaf(f00, X01, f10 * X11);
-        r[7] = fmaf(f01, X01, f11 * X11);
-        r[10] = f00; r[11] = f01; r[12] = f10; r[13] = f11;
-      } else {
+      __syncthreads();
+      // ---- A8 (mixed tiers): per family, offsets e_i = beta_i - beta_ref from the family's
+      // first image (float-float, then FP64), G and g in FP64 with the FP32 M_i, the 2x2
+      // solve and chi^2_f in FP64.  (The adjoint needs beta_model to FP64 accuracy: an error
+      // in it enters the gradient at first order.)
+      for (int f = tid; f < C.n_fam; f += blockDim.x) {
+        const int i0 = C.fam_off[f], i1 = C.fam_off[f + 1];
+        const float* r0 = imgf + i0 * ISF;
+        const ff br0 = ff_make(r0[10], r0[11]), br1 = ff_make(r0[12], r0[13]);
+        double G00 = 0, G01 = 0, G11 = 0, g0 = 0, g1 = 0;
+        for (int i = i0; i < i1; ++i) {
+          const float* r = imgf + i * ISF;
+          const double e0 = ff_to_double(ff_sub(ff_make(r[10], r[11]), br0));
+          const double e1 = ff_to_double(ff_sub(ff_make(r[12], r[13]), br1));
+          G00 += r[14]; G01 += r[15]; G11 += r[16];
+          g0 += (double)r[14] * e0 + (double)r[15] * e1;
+          g1 += (double)r[15] * e0 + (double)r[16] * e1;
+        }
+        double cf = 0.0, c0 = 0.0, c1 = 0.0;
+        if (i1 - i0 == 1) {
+          if (!(isfinite(G00) && isfinite(G01) && isfinite(G11) && isfinite(br0.hi) && isfinite(br1.hi)))
+            cf = INFINITY;
+        } else {
+          const double dG = G00 * G11 - G01 * G01;
+          const double idG = 1.0 / dG;
+          c0 = (G11 * g0 - G01 * g1) * idG;
+          c1 = (G00 * g1 - G01 * g0) * idG;
+          for (int i = i0; i < i1; ++i) {
+            const float* r = imgf + i * ISF;
+            const double d0 = ff_to_double(ff_sub(ff_make(r[10], r[11]), br0)) - c0;
+            const double d1 = ff_to_double(ff_sub(ff_make(r[12], r[13]), br1)) - c1;
+            cf += (double)r[14] * d0 * d0 + 2.0 * (double)r[15] * d0 * d1 + (double)r[16] * d1 * d1;
+          }
+          if (!isfinite(cf) || !(dG > 0.0)) cf = INFINITY;
+        }
+        fam[3 * f] = cf;
+        fam[3 * f + 1] = c0;
+        fam[3 * f + 2] = c1;
+        my += cf;
+      }
+    } else {
+      // ---- A5, A7 (FP64 tier): beta_i, A_i, mu_i, M_i
+      for (int i = tid; i < n_img; i += blockDim.x) {
+        double* r = img + i * IS;
+        const int f = C.img_fam[i];
+        const double tx = C.theta[2 * i], ty = C.theta[2 * i + 1];
+        double bx, by, A00, A01, A10, A11;
+        if (C.np == 1) {
+          const double a = C.fam_ratio[f];
+          bx = tx - a * r[0];
+          by = ty - a * r[1];
+          A00 = 1.0 - a * r[2]; A11 = 1.0 - a * r[3]; A01 = A10 = -a * r[4];
+        } else {
+          bx = tx; by = ty; A00 = 1; A01 = 0; A10 = 0; A11 = 1;
+          for (int l = 0; l < C.np; ++l) {
+            const double rs = C.fam_ratio[f * C.np + l];
+            const double* pl = r + 16 + 6 * l;
+            bx -= rs * pl[0]; by -= rs * pl[1];
+            A00 -= rs * pl[2]; A01 -= rs * pl[3]; A10 -= rs * pl[4]; A11 -= rs * pl[5];
+          }
+        }
+        const double id = 1.0 / (A00 * A11 - A01 * A10);
+        const double m00 = A11 * id, m01 = -A01 * id, m10 = -A10 * id, m11 = A00 * id;
         const double s0 = C.sinv[3 * i], s1 = C.sinv[3 * i + 1], s2 = C.sinv[3 * i + 2];
         const double X00 = s0 * m00 + s1 * m10, X01 = s0 * m01 + s1 * m11;
         const double X10 = s1 * m00 + s2 * m10, X11 = s1 * m01 + s2 * m11;
@@ -463,69 +605,81 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
         r[6] = m00 * X01 + m10 * X11;
         r[7] = m01 * X01 + m11 * X11;
         r[10] = m00; r[11] = m01; r[12] = m10; r[13] = m11;
+        r[8] = bx; r[9] = by;
       }
-      r[8] = bx; r[9] = by;
-    }
-    __syncthreads();
-
-    // ---- A8: analytic source and chi^2 per family
-    double my = 0.0;
-    for (int f = tid; f < C.n_fam; f += blockDim.x) {
-      const int i0 = C.fam_off[f], i1 = C.fam_off[f + 1];
-      // beta_model = beta_ref + G^-1 sum M_i (beta_i - beta_ref) with beta_ref the family's
-      // first image: the same minimiser, with the large common part of beta taken out
-      const double br0 = img[i0 * IS + 8], br1 = img[i0 * IS + 9];
-      double G00 = 0, G01 = 0, G11 = 0, g0 = 0, g1 = 0;
-      for (int i = i0; i < i1; ++i) {
-        const double* r = img + i * IS;
-        const double e0 = r[8] - br0, e1 = r[9] - br1;
-        G00 += r[5]; G01 += r[6]; G11 += r[7];
-        g0 += r[5] * e0 + r[6] * e1;
-        g1 += r[6] * e0 + r[7] * e1;
-      }
-      double bm0, bm1, cf = 0.0;
-      if (i1 - i0 == 1) {
-        bm0 = br0;
-        bm1 = br1;
-        if (!(isfinite(G00) && isfinite(G01) && isfinite(G11) && isfinite(bm0) && isfinite(bm1)))
-          cf = INFINITY;
-      } else {
-        const double dG = G00 * G11 - G01 * G01;
-        const double idG = 1.0 / dG;
-        const double c0 = (G11 * g0 - G01 * g1) * idG, c1 = (G00 * g1 - G01 * g0) * idG;
-        bm0 = br0 + c0;
-        bm1 = br1 + c1;
+      __syncthreads();
+      // ---- A8 (FP64 tier): analytic source and chi^2 per family
+      for (int f = tid; f < C.n_fam; f += blockDim.x) {
+        const int i0 = C.fam_off[f], i1 = C.fam_off[f + 1];
+        // beta_model = beta_ref + G^-1 sum M_i (beta_i - beta_ref), beta_ref the first image
+        const double br0 = img[i0 * IS + 8], br1 = img[i0 * IS + 9];
+        double G00 = 0, G01 = 0, G11 = 0, g0 = 0, g1 = 0;
         for (int i = i0; i < i1; ++i) {
           const double* r = img + i * IS;
-          const double d0 = (r[8] - br0) - c0, d1 = (r[9] - br1) - c1;
-          cf += r[5] * d0 * d0 + 2.0 * r[6] * d0 * d1 + r[7] * d1 * d1;
+          const double e0 = r[8] - br0, e1 = r[9] - br1;
+          G00 += r[5]; G01 += r[6]; G11 += r[7];
+          g0 += r[5] * e0 + r[6] * e1;
+          g1 += r[6] * e0 + r[7] * e1;
         }
-        if (!isfinite(cf) || !(dG > 0.0)) cf = INFINITY;
+        double c0 = 0.0, c1 = 0.0, cf = 0.0;
+        if (i1 - i0 == 1) {
+          if (!(isfinite(G00) && isfinite(G01) && isfinite(G11) && isfinite(br0) && isfinite(br1)))
+            cf = INFINITY;
+        } else {
+          const double dG = G00 * G11 - G01 * G01;
+          const double idG = 1.0 / dG;
+          c0 = (G11 * g0 - G01 * g1) * idG;
+          c1 = (G00 * g1 - G01 * g0) * idG;
+          for (int i = i0; i < i1; ++i) {
+            const double* r = img + i * IS;
+            const double d0 = (r[8] - br0) - c0, d1 = (r[9] - br1) - c1;
+            cf += r[5] * d0 * d0 + 2.0 * r[6] * d0 * d1 + r[7] * d1 * d1;
+          }
+          if (!isfinite(cf) || !(dG > 0.0)) cf = INFINITY;
+        }
+        fam[3 * f] = cf;
+        fam[3 * f + 1] = c0;      // beta_model - beta_ref
+        fam[3 * f + 2] = c1;
+        my += cf;
       }
-      fam[3 * f] = cf;
-      fam[3 * f + 1] = bm0;
-      fam[3 * f + 2] = bm1;
-      my += cf;
     }
     const double total = block_sum(my, scratch);
     if (tid == 0) chi2[s] = total;
 
     if constexpr (GRAD) {
-      // cotangents of alpha and Psi at each image (stored over the sums)
+      // cotangents of alpha and Psi at each image: with d = beta_i - beta_model, w = M d,
+      // z = mu d: alpha_bar = -2 a w, Psi_bar = 2 a sym(w z^T)
       for (int i = tid; i < n_img; i += blockDim.x) {
-        double* r = img + i * IS;
         const int f = C.img_fam[i];
-        const double a = C.fam_ratio[f];
         const int n_f = C.fam_off[f + 1] - C.fam_off[f];
-        const double d0 = r[8] - fam[3 * f + 1], d1 = r[9] - fam[3 * f + 2];
-        const double w0 = r[5] * d0 + r[6] * d1, w1 = r[6] * d0 + r[7] * d1;
-        const double z0 = r[10] * d0 + r[11] * d1, z1 = r[12] * d0 + r[13] * d1;
+        const int i0 = C.fam_off[f];
+        double d0, d1, M00, M01, M11, u00, u01, u10, u11;
+        if constexpr (MIXED) {
+          const float* r = imgf + i * ISF;
+          const float* r0 = imgf + i0 * ISF;
+          d0 = ff_to_double(ff_sub(ff_make(r[10], r[11]), ff_make(r0[10], r0[11]))) - fam[3 * f + 1];
+          d1 = ff_to_double(ff_sub(ff_make(r[12], r[13]), ff_make(r0[12], r0[13]))) - fam[3 * f + 2];
+          M00 = r[14]; M01 = r[15]; M11 = r[16];
+          u00 = r[17]; u01 = r[18]; u10 = r[19]; u11 = r[20];
+        } else {
+          const double* r = img + i * IS;
+          d0 = (r[8] - img[i0 * IS + 8]) - fam[3 * f + 1];
+          d1 = (r[9] - img[i0 * IS + 9]) - fam[3 * f + 2];
+          M00 = r[5]; M01 = r[6]; M11 = r[7];
+          u00 = r[10]; u01 = r[11]; u10 = r[12]; u11 = r[13];
+        }
+        const double a = C.fam_ratio[f];
+        const double w0 = M00 * d0 + M01 * d1, w1 = M01 * d0 + M11 * d1;
+        const double z0 = u00 * d0 + u01 * d1, z1 = u10 * d0 + u11 * d1;
         const double k2a = n_f > 1 ? 2.0 * a : 0.0;
-        r[0] = -k2a * w0;
-        r[1] = -k2a * w1;
-        r[2] = k2a * w0 * z0;
-        r[3] = k2a * w1 * z1;
-        r[4] = k2a * (w0 * z1 + w1 * z0);
+        double cot[5] = {-k2a * w0, -k2a * w1, k2a * w0 * z0, k2a * w1 * z1, k2a * (w0 * z1 + w1 * z0)};
+        if constexpr (MIXED) {
+          float* r = imgf + i * ISF;
+          for (int q = 0; q < 5; ++q) r[q] = (float)cot[q];
+        } else {
+          double* r = img + i * IS;
+          for (int q = 0; q < 5; ++q) r[q] = cot[q];
+        }
       }
       __syncthreads();
       const PlaneDesc& P = C.pl[0];
@@ -539,8 +693,12 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
       for (int t = tid; t < ntask_img; t += blockDim.x) {
         const int i = t / KS, k = t - i * KS;
         const int k0 = (int)((long long)K * k / KS), k1 = (int)((long long)K * (k + 1) / KS);
-        const double* r = img + i * IS;
-        T cot[5] = {(T)r[0], (T)r[1], (T)r[2], (T)r[3], (T)r[4]};
+        T cot[5];
+        if constexpr (MIXED) {
+          for (int q = 0; q < 5; ++q) cot[q] = imgf[i * ISF + q];
+        } else {
+          for (int q = 0; q < 5; ++q) cot[q] = img[i * IS + q];
+        }
         const double px = C.theta[2 * i], py = C.theta[2 * i + 1];
         for (int f = 0; f < C.n_free; ++f) {
           const int kc = C.free_comp[f];
@@ -571,13 +729,13 @@ __global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cd
             T dx, dy;
             if constexpr (MIXED) {
               float xh, xl, yh, yl;
-              split_ff(C.theta[2 * i], xh, xl);
-              split_ff(C.theta[2 * i + 1], yh, yl);
+              split_ff(px, xh, xl);
+              split_ff(py, yh, yl);
               dx = offset_of(xh, xl, M.xh, M.xl);
               dy = offset_of(yh, yl, M.yh, M.yl);
             } else {
-              dx = C.theta[2 * i] - M.xh;
-              dy = C.theta[2 * i + 1] - M.yh;
+              dx = px - M.xh;
+              dy = py - M.yh;
             }
             pje_round(D2::cst(dx), D2::cst(dy), D2::cst((T)1), sd, sd * sd, ad, ad * ad, o);
             const T Gb = contract(o, cot, -1);
@@ -618,6 +776,8 @@ struct lf_plan {
   ClusterDesc* d_desc = nullptr;
   int* d_counter = nullptr;
   int* d_order = nullptr;
+  void* d_free_dig = nullptr;      // [max_samples * LF_MAX_FREE] digested sampled components
+  lf_comp* d_free_raw = nullptr;   // [max_samples * LF_MAX_FREE] their fields (adjoint)
   std::vector<void*> allocs;
   int block = 256;
   int ks_cap = 32;
@@ -697,7 +857,12 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
     o = (o + 15u) & ~15u; P.off_dm = o; o += (uint32_t)P.nm * mem_sz;
   }
   C.img_stride = C.np > 1 ? 16 + 6 * C.np : 14;
-  o = (o + 15u) & ~15u; C.off_img = o; o += (uint32_t)C.n_img * C.img_stride * 8u;
+  C.img_stride_f = IMGF;
+  C.img_stride_d = C.np > 1 ? 2 + 6 * C.np : 0;
+  o = (o + 15u) & ~15u; C.off_img = o;
+  o += mixed ? (uint32_t)C.n_img * IMGF * 4u : (uint32_t)C.n_img * C.img_stride * 8u;
+  o = (o + 15u) & ~15u; C.off_imgd = o;
+  if (mixed) o += (uint32_t)C.n_img * C.img_stride_d * 8u;
   C.off_fam = o; o += (uint32_t)C.n_fam * 3u * 8u;
   C.off_par = o; o += (uint32_t)C.P * 2u * 8u;
   o = (o + 15u) & ~15u; C.off_free = o; o += (uint32_t)C.n_free * 64u;
@@ -721,6 +886,8 @@ static lf_status relayout(lf_plan* pl) {
   LF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   auto kset = [&](const void* k) -> lf_status {
     LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem));
+    LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
     return LF_OK;
   };
   const void* kc = pl->precision == LF_MIXED ? (const void*)k_chi2<LF_MIXED, false>
@@ -839,6 +1006,21 @@ static lf_status build_cluster(lf_plan* pl, const lf_cluster& cl, ClusterDesc& C
   LF_TRY(plan_upload(pl, im.fam_off, (size_t)im.n_fam + 1, &doff));
   LF_TRY(plan_upload(pl, img_fam.data(), img_fam.size(), &dif));
   C.theta = dtheta; C.sinv = dsinv; C.fam_ratio = dratio; C.fam_off = doff; C.img_fam = dif;
+  {
+    std::vector<float4> tf(im.n_img), sf(im.n_img);
+    std::vector<float2> rf((size_t)im.n_fam * C.np);
+    for (int i = 0; i < im.n_img; ++i) {
+      split_ff(im.theta_obs[2 * i], tf[i].x, tf[i].y);
+      split_ff(im.theta_obs[2 * i + 1], tf[i].z, tf[i].w);
+      sf[i] = make_float4((float)im.sinv[3 * i], (float)im.sinv[3 * i + 1], (float)im.sinv[3 * i + 2], 0.f);
+    }
+    for (size_t q = 0; q < rf.size(); ++q) split_ff(im.fam_ratio[q], rf[q].x, rf[q].y);
+    float4* dtf = nullptr; float4* dsf = nullptr; float2* drf = nullptr;
+    LF_TRY(plan_upload(pl, tf.data(), tf.size(), &dtf));
+    LF_TRY(plan_upload(pl, sf.data(), sf.size(), &dsf));
+    LF_TRY(plan_upload(pl, rf.data(), rf.size(), &drf));
+    C.theta_ff = dtf; C.sinv_f = dsf; C.ratio_ff = drf;
+  }
   // parameter map
   C.P = cl.P;
   if (cl.P < 1 || cl.P > LF_MAX_P || !cl.p_comp || !cl.p_field || !cl.p_xform)
@@ -888,14 +1070,19 @@ static lf_status build_cluster(lf_plan* pl, const lf_cluster& cl, ClusterDesc& C
 template <int MODE>
 static void launch_mode(lf_plan* pl, const double* theta, int S, double* chi2, double* grad,
                         cudaStream_t st, int spc) {
+  const int nprep = S * LF_MAX_FREE;
+  k_chi2_prep<MODE><<<(nprep + 255) / 256, 256, 0, st>>>(pl->d_desc, spc, S, theta, pl->d_free_dig,
+                                                         pl->d_free_raw);
   if (grad) {
     int g = std::min(pl->grid_grad, S);
     k_chi2<MODE, true><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
-                                                       grad, pl->d_counter, g_member_chunk);
+                                                       grad, pl->d_counter, g_member_chunk,
+                                                       pl->d_free_dig, pl->d_free_raw);
   } else {
     int g = std::min(pl->grid_chi2, S);
     k_chi2<MODE, false><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
-                                                        nullptr, pl->d_counter, g_member_chunk);
+                                                        nullptr, pl->d_counter, g_member_chunk,
+                                                        pl->d_free_dig, nullptr);
   }
 }
 
@@ -1022,6 +1209,12 @@ extern "C" lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, i
     }
     if (st == LF_OK) st = plan_alloc(pl, &p, sizeof(int));
     if (st == LF_OK) pl->d_counter = (int*)p;
+    const size_t nfree = (size_t)max_samples * LF_MAX_FREE;
+    const size_t dsz = precision == LF_FP64 ? sizeof(CompT<double>) : sizeof(CompT<float>);
+    if (st == LF_OK) st = plan_alloc(pl, &p, nfree * dsz);
+    if (st == LF_OK) pl->d_free_dig = p;
+    if (st == LF_OK) st = plan_alloc(pl, &p, nfree * sizeof(lf_comp));
+    if (st == LF_OK) pl->d_free_raw = (lf_comp*)p;
     if (st == LF_OK) st = plan_alloc(pl, &p, n_clusters * sizeof(ClusterDesc));
     if (st == LF_OK) pl->d_desc = (ClusterDesc*)p;
     if (st == LF_OK) st = relayout(pl);

@@ -51,9 +51,23 @@ static lf_status static_scratch(void** out) {
 
 // Fills the member factor tables and the image -> family map inside the scratch array.
 template <class MemPre>
-__global__ void k_static_prep(ClusterDesc* C, const lf_member* const* mems, int* img_fam) {
+__global__ void k_static_prep(ClusterDesc* C, const lf_member* const* mems, int* img_fam,
+                              float4* theta_ff, float4* sinv_f, float2* ratio_ff) {
   const ClusterDesc& cd = *C;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int i = tid; i < cd.n_img; i += nth) {
+    float4 t, v;
+    split_ff(cd.theta[2 * i], t.x, t.y);
+    split_ff(cd.theta[2 * i + 1], t.z, t.w);
+    v = make_float4((float)cd.sinv[3 * i], (float)cd.sinv[3 * i + 1], (float)cd.sinv[3 * i + 2], 0.f);
+    theta_ff[i] = t;
+    sinv_f[i] = v;
+  }
+  for (int q = tid; q < cd.n_fam * cd.np; q += nth) {
+    float2 r;
+    split_ff(cd.fam_ratio[q], r.x, r.y);
+    ratio_ff[q] = r;
+  }
   for (int j = 0; j < cd.np; ++j) {
     const PlaneDesc& P = cd.pl[j];
     MemPre* pre = const_cast<MemPre*>(reinterpret_cast<const MemPre*>(P.mpre));
@@ -188,6 +202,9 @@ extern "C" lf_status lf_chi2_batch_static(const lf_cluster* cl, const double* th
   const size_t o_ratio = off; off = align256(off + sizeof(double) * im.n_fam * np);
   const size_t o_off = off; off = align256(off + sizeof(int) * (im.n_fam + 1));
   const size_t o_if = off; off = align256(off + sizeof(int) * im.n_img);
+  const size_t o_tff = off; off = align256(off + sizeof(float4) * im.n_img);
+  const size_t o_sf = off; off = align256(off + sizeof(float4) * im.n_img);
+  const size_t o_rff = off; off = align256(off + sizeof(float2) * im.n_fam * np);
   if (off > LF_STATIC_SCRATCH_BYTES)
     return fail(LF_EINVAL, "cluster needs %zu bytes of scratch, more than the %zu-byte static array "
                 "(too many members or images for this entry point; use a plan)", off,
@@ -206,6 +223,9 @@ extern "C" lf_status lf_chi2_batch_static(const lf_cluster* cl, const double* th
   C.fam_ratio = reinterpret_cast<const double*>(base + o_ratio);
   C.fam_off = reinterpret_cast<const int*>(base + o_off);
   C.img_fam = reinterpret_cast<const int*>(base + o_if);
+  C.theta_ff = reinterpret_cast<const float4*>(base + o_tff);
+  C.sinv_f = reinterpret_cast<const float4*>(base + o_sf);
+  C.ratio_ff = reinterpret_cast<const float2*>(base + o_rff);
 
   cudaStream_t st = (cudaStream_t)stream;
   LF_CUDA(cudaMemcpyAsync(base + o_desc, &C, sizeof C, cudaMemcpyHostToDevice, st));
@@ -218,8 +238,11 @@ extern "C" lf_status lf_chi2_batch_static(const lf_cluster* cl, const double* th
   ClusterDesc* dC = reinterpret_cast<ClusterDesc*>(base + o_desc);
   const lf_member* const* dm = reinterpret_cast<const lf_member* const*>(base + o_mems);
   int* dif = reinterpret_cast<int*>(base + o_if);
-  if (precision == LF_MIXED) k_static_prep<MemPreF><<<32, 256, 0, st>>>(dC, dm, dif);
-  else k_static_prep<MemPreD><<<32, 256, 0, st>>>(dC, dm, dif);
+  float4* dtf = reinterpret_cast<float4*>(base + o_tff);
+  float4* dsf = reinterpret_cast<float4*>(base + o_sf);
+  float2* drf = reinterpret_cast<float2*>(base + o_rff);
+  if (precision == LF_MIXED) k_static_prep<MemPreF><<<32, 256, 0, st>>>(dC, dm, dif, dtf, dsf, drf);
+  else k_static_prep<MemPreD><<<32, 256, 0, st>>>(dC, dm, dif, dtf, dsf, drf);
   LF_CUDA(cudaGetLastError());
 
   int dev = 0, nsm = 0, occ = 0;
@@ -234,11 +257,11 @@ extern "C" lf_status lf_chi2_batch_static(const lf_cluster* cl, const double* th
   LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, block, C.smem));
   const int grid = std::min(nsm * std::max(occ, 1), S);
   if (precision == LF_MIXED)
-    k_chi2<LF_MIXED, false><<<grid, block, C.smem, st>>>(dC, order, S, S, theta, chi2, nullptr, counter, g_member_chunk);
+    k_chi2<LF_MIXED, false><<<grid, block, C.smem, st>>>(dC, order, S, S, theta, chi2, nullptr, counter, g_member_chunk, nullptr, nullptr);
   else if (precision == LF_FF)
-    k_chi2<LF_FF, false><<<grid, block, C.smem, st>>>(dC, order, S, S, theta, chi2, nullptr, counter, g_member_chunk);
+    k_chi2<LF_FF, false><<<grid, block, C.smem, st>>>(dC, order, S, S, theta, chi2, nullptr, counter, g_member_chunk, nullptr, nullptr);
   else
-    k_chi2<LF_FP64, false><<<grid, block, C.smem, st>>>(dC, order, S, S, theta, chi2, nullptr, counter, g_member_chunk);
+    k_chi2<LF_FP64, false><<<grid, block, C.smem, st>>>(dC, order, S, S, theta, chi2, nullptr, counter, g_member_chunk, nullptr, nullptr);
   LF_CUDA(cudaGetLastError());
   return LF_OK;
 }
