@@ -209,14 +209,15 @@ __device__ __forceinline__ float mem_a(const MemX& m) { return m.ah; }
 // Sampled components of every sample, digested in one pass over (sample, component) before the
 // chi^2 kernel (their FP64 set-up is then off the per-sample critical path).
 template <int MODE>
-__global__ void k_chi2_prep(const ClusterDesc* __restrict__ cds, int spc, int S,
+__global__ void k_chi2_prep(const ClusterDesc* __restrict__ cds, int spc, int S, int nfree_max,
                             const double* __restrict__ theta, void* dig, lf_comp* raw) {
   typedef typename std::conditional<MODE != LF_FP64, float, double>::type T;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = idx / LF_MAX_FREE, f = idx - s * LF_MAX_FREE;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;    // dense over (sample, component)
+  const int s = t / nfree_max, f = t - s * nfree_max;
   if (s >= S) return;
   const ClusterDesc& C = cds[s / spc];
   if (f >= C.n_free) return;
+  const int idx = s * LF_MAX_FREE + f;
   const PlaneDesc& P = C.pl[C.free_plane[f]];
   lf_comp rc = P.comp[C.free_comp[f]];
   for (int fld = 0; fld < 7; ++fld) {
@@ -232,8 +233,17 @@ __global__ void k_chi2_prep(const ClusterDesc* __restrict__ cds, int spc, int S,
 // [17..20] mu (00, 01, 10, 11).
 constexpr int IMGF = 22;
 
+#ifndef LF_CHI2_THREADS
+#define LF_CHI2_THREADS 512
+#endif
+#ifndef LF_CHI2_MINB
+#define LF_CHI2_MINB 1
+#endif
+#ifndef LF_CHI2_BLOCK
+#define LF_CHI2_BLOCK 256
+#endif
 template <int MODE, bool GRAD>   // MODE: LF_FP64, LF_MIXED or LF_FF
-__global__ void __launch_bounds__(512) k_chi2(const ClusterDesc* __restrict__ cds,
+__global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const ClusterDesc* __restrict__ cds,
                                               const int* __restrict__ corder, int spc, int S,
                                               const double* __restrict__ theta, double* chi2,
                                               double* grad, int* counter, int chunk,
@@ -776,10 +786,11 @@ struct lf_plan {
   ClusterDesc* d_desc = nullptr;
   int* d_counter = nullptr;
   int* d_order = nullptr;
+  int nfree_max = 0;               // largest number of sampled components of a cluster
   void* d_free_dig = nullptr;      // [max_samples * LF_MAX_FREE] digested sampled components
   lf_comp* d_free_raw = nullptr;   // [max_samples * LF_MAX_FREE] their fields (adjoint)
   std::vector<void*> allocs;
-  int block = 256;
+  int block = LF_CHI2_BLOCK;
   int ks_cap = 32;
   bool tuned = false;
   uint32_t smem = 0;
@@ -1070,9 +1081,10 @@ static lf_status build_cluster(lf_plan* pl, const lf_cluster& cl, ClusterDesc& C
 template <int MODE>
 static void launch_mode(lf_plan* pl, const double* theta, int S, double* chi2, double* grad,
                         cudaStream_t st, int spc) {
-  const int nprep = S * LF_MAX_FREE;
-  k_chi2_prep<MODE><<<(nprep + 255) / 256, 256, 0, st>>>(pl->d_desc, spc, S, theta, pl->d_free_dig,
-                                                         pl->d_free_raw);
+  const int nprep = S * pl->nfree_max;
+  if (nprep > 0)
+    k_chi2_prep<MODE><<<(nprep + 63) / 64, 64, 0, st>>>(pl->d_desc, spc, S, pl->nfree_max, theta,
+                                                        pl->d_free_dig, pl->d_free_raw);
   if (grad) {
     int g = std::min(pl->grid_grad, S);
     k_chi2<MODE, true><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
@@ -1099,8 +1111,9 @@ static lf_status launch_chi2(lf_plan* pl, const double* theta, int S, double* ch
 
 // Times candidate (block, slice cap) shapes on the caller's inputs and keeps the fastest.
 static lf_status autotune(lf_plan* pl, const double* theta, int S, double* chi2, cudaStream_t st) {
-  const int blocks[3] = {128, 256, 512};
-  const int caps[4] = {1, 4, 8, 32};
+  // any multiple of a warp lets (image pair x slice) tasks fill the block
+  const int blocks[15] = {64, 96, 128, 160, 192, 224, 256, 288, 320, 352, 384, 416, 448, 480, 512};
+  const int caps[4] = {1, 2, 4, 8};
   cudaEvent_t e0, e1;
   LF_CUDA(cudaEventCreate(&e0));
   LF_CUDA(cudaEventCreate(&e1));
@@ -1113,7 +1126,7 @@ static lf_status autotune(lf_plan* pl, const double* theta, int S, double* chi2,
       if (relayout(pl) != LF_OK) continue;
       LF_TRY(launch_chi2(pl, theta, S, chi2, nullptr, st));
       LF_CUDA(cudaEventRecord(e0, st));
-      for (int r = 0; r < 3; ++r) LF_TRY(launch_chi2(pl, theta, S, chi2, nullptr, st));
+      for (int r = 0; r < 2; ++r) LF_TRY(launch_chi2(pl, theta, S, chi2, nullptr, st));
       LF_CUDA(cudaEventRecord(e1, st));
       LF_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -1195,6 +1208,7 @@ extern "C" lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, i
     if (clusters[c].P != pl->P) st = fail(LF_EINVAL, "every cluster must have the same P");
     else st = build_cluster(pl, clusters[c], pl->desc[c], pl->cost[c]);
     if (st == LF_OK && pl->desc[c].np > 1) pl->single_plane = false;
+    if (st == LF_OK) pl->nfree_max = std::max(pl->nfree_max, pl->desc[c].n_free);
   }
   if (st == LF_OK) {
     std::vector<int> order(n_clusters);
