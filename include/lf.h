@@ -211,6 +211,17 @@ lf_status lf_chi2_batch(lf_plan* plan, const double* theta, int32_t S, double* c
 lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int32_t S, double* chi2,
                              double* grad, void* stream);
 
+/* Image-plane chi^2 of Eq. chi2_img: for every image the model image is found by `iters`
+ * Newton-Raphson steps theta <- theta - A(theta)^-1 (beta(theta) - beta_model) started at the
+ * observed position (the paper's image-plane scheme, Sec. 3.5), towards the family's analytic
+ * source beta_model = G^-1 g of Sec. 3.1; then chi2_img = sum_i (theta_obs - theta_model)^T
+ * S_i^-1 (theta_obs - theta_model) and rms = sqrt(mean_i |theta_obs - theta_model|^2), the
+ * image-plane rms the paper reports.  chi2_img, rms: device [S] FP64 (rms may be NULL).
+ * 1 <= iters <= 64.  Single-plane plans only (LF_EUNSUPPORTED otherwise).  A sample whose
+ * Newton iteration leaves the finite range gets chi2_img = +inf. */
+lf_status lf_chi2_img_batch(lf_plan* plan, const double* theta, int32_t S, int32_t iters,
+                            double* chi2_img, double* rms, void* stream);
+
 lf_status lf_plan_destroy(lf_plan* plan);
 
 /* lf_chi2_batch for one cluster with no device allocation (the paper has no counterpart;

@@ -162,6 +162,16 @@ class Plan:
         L.check(L.lib.lf_chi2_grad_batch(self.handle, _ptr(theta), S, _ptr(out), _ptr(grad), _stream()))
         return out, grad
 
+    def chi2_img(self, theta: torch.Tensor, iters=8):
+        """Image-plane chi^2 and rms per sample (Newton model images)."""
+        theta = theta.contiguous()
+        S = theta.shape[0]
+        out = torch.empty(S, dtype=torch.float64, device="cuda")
+        rms = torch.empty(S, dtype=torch.float64, device="cuda")
+        L.check(L.lib.lf_chi2_img_batch(self.handle, _ptr(theta), S, int(iters), _ptr(out), _ptr(rms),
+                                        _stream()))
+        return out, rms
+
     def info(self):
         ks, blk, g = C.c_int32(), C.c_int32(), C.c_int32()
         L.check(L.lib.lf_plan_info(self.handle, C.byref(ks), C.byref(blk), C.byref(g)))

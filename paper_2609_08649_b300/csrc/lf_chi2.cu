@@ -80,7 +80,7 @@ struct ClusterDesc {
   const float4* theta_ff;          // [n_img] (x_hi, x_lo, y_hi, y_lo)
   const float2* ratio_ff;          // [n_fam * np]
   const float4* sinv_f;            // [n_img] (xx, xy, yy, 0)
-  uint32_t off_img, off_imgd, off_fam, off_par, off_free, smem;
+  uint32_t off_img, off_imgd, off_fam, off_par, off_free, off_newton, smem;
 };
 
 // ------------------------------------------------------------------ transforms -----
@@ -242,13 +242,17 @@ constexpr int IMGF = 22;
 #ifndef LF_CHI2_BLOCK
 #define LF_CHI2_BLOCK 256
 #endif
-template <int MODE, bool GRAD>   // MODE: LF_FP64, LF_MIXED or LF_FF
+// PASS 0: source-plane chi^2 (and its gradient when GRAD).  PASS 1: image-plane chi^2 of
+// Eq. chi2_img with model images found by `iters` Newton steps from the observed images
+// towards the family's analytic source (written to chi2), and the image-plane rms (to rms).
+template <int MODE, bool GRAD, int PASS = 0>   // MODE: LF_FP64, LF_MIXED or LF_FF
 __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const ClusterDesc* __restrict__ cds,
                                               const int* __restrict__ corder, int spc, int S,
                                               const double* __restrict__ theta, double* chi2,
                                               double* grad, int* counter, int chunk,
                                               const void* __restrict__ free_dig,
-                                              const lf_comp* __restrict__ free_raw) {
+                                              const lf_comp* __restrict__ free_raw,
+                                              int iters = 0, double* rms = nullptr) {
   constexpr bool MIXED = MODE != LF_FP64;
   typedef typename std::conditional<MIXED, float, double>::type T;
   typedef typename std::conditional<MODE == LF_MIXED, MemPreF, MemPreD>::type MemPre;
@@ -381,6 +385,8 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
               ISD = C.img_stride_d;
     const int n_pair = (n_img + 1) >> 1;
     const int ntask = n_pair * KS;
+    // pos: null = the observed images; else positions (x, y) at pos[4 i], pos[4 i + 1]
+    auto eval_planes = [&](const double* pos) {
     for (int j = 0; j < C.np; ++j) {
       const PlaneDesc& P = C.pl[j];
       const CompT<T>* dc = reinterpret_cast<const CompT<T>*>(smem + P.off_dc);
@@ -398,9 +404,12 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
           const int ii[2] = {ia, ib};
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
-            if (j == 0) {
+            if (j == 0 && !pos) {
               const float4 tf = C.theta_ff[ii[q]];
               xh[q] = tf.x; xl[q] = tf.y; yh[q] = tf.z; yl[q] = tf.w;
+            } else if (j == 0) {
+              split_ff(pos[4 * ii[q]], xh[q], xl[q]);
+              split_ff(pos[4 * ii[q] + 1], yh[q], yl[q]);
             } else {
               split_ff(imgd[ii[q] * ISD + 0], xh[q], xl[q]);
               split_ff(imgd[ii[q] * ISD + 1], yh[q], yl[q]);
@@ -441,8 +450,8 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
           if (act) {
             const int ii[2] = {ia, ib};
             for (int q = 0; q < 2; ++q) {
-              const double x = j == 0 ? C.theta[2 * ii[q]] : img[ii[q] * IS + 14];
-              const double y = j == 0 ? C.theta[2 * ii[q] + 1] : img[ii[q] * IS + 15];
+              const double x = j > 0 ? img[ii[q] * IS + 14] : pos ? pos[4 * ii[q]] : C.theta[2 * ii[q]];
+              const double y = j > 0 ? img[ii[q] * IS + 15] : pos ? pos[4 * ii[q] + 1] : C.theta[2 * ii[q] + 1];
               accumulate_fp64(dc, P.nc, dm, P.nm, k0, k1, x, y, v[q]);
             }
           }
@@ -498,6 +507,8 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
         __syncthreads();
       }
     }
+    };
+    eval_planes(nullptr);
 
     double my = 0.0;
     if constexpr (MIXED) {
@@ -652,6 +663,64 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
         fam[3 * f + 2] = c1;
         my += cf;
       }
+    }
+    if constexpr (PASS == 1) {
+      // ---- image-plane chi^2: Newton steps theta <- theta - A^-1 (beta(theta) - beta_model)
+      // from the observed images, then chi^2_img = sum (theta_obs - theta)^T S^-1 (...)
+      double* nst = reinterpret_cast<double*>(smem + C.off_newton);   // [4 i]: theta, beta_model
+      __syncthreads();
+      for (int i = tid; i < n_img; i += blockDim.x) {
+        const int f = C.img_fam[i], i0 = C.fam_off[f];
+        double bm0, bm1;
+        if constexpr (MIXED) {
+          const float* r0 = imgf + i0 * ISF;
+          bm0 = ff_to_double(ff_make(r0[10], r0[11])) + fam[3 * f + 1];
+          bm1 = ff_to_double(ff_make(r0[12], r0[13])) + fam[3 * f + 2];
+        } else {
+          bm0 = img[i0 * IS + 8] + fam[3 * f + 1];
+          bm1 = img[i0 * IS + 9] + fam[3 * f + 2];
+        }
+        nst[4 * i] = C.theta[2 * i];
+        nst[4 * i + 1] = C.theta[2 * i + 1];
+        nst[4 * i + 2] = bm0;
+        nst[4 * i + 3] = bm1;
+      }
+      __syncthreads();
+      for (int it = 0; it < iters; ++it) {
+        eval_planes(nst);
+        for (int i = tid; i < n_img; i += blockDim.x) {
+          double sm[5];
+          if constexpr (MIXED) {
+            for (int c5 = 0; c5 < 5; ++c5)
+              sm[c5] = (double)imgf[i * ISF + 2 * c5] + (double)imgf[i * ISF + 2 * c5 + 1];
+          } else {
+            for (int c5 = 0; c5 < 5; ++c5) sm[c5] = img[i * IS + c5];
+          }
+          const double a = C.fam_ratio[C.img_fam[i]];
+          const double tx = nst[4 * i], ty = nst[4 * i + 1];
+          const double rx = tx - a * sm[0] - nst[4 * i + 2];
+          const double ry = ty - a * sm[1] - nst[4 * i + 3];
+          const double A00 = 1.0 - a * sm[2], A11 = 1.0 - a * sm[3], A01 = -a * sm[4];
+          const double id = 1.0 / (A00 * A11 - A01 * A01);
+          nst[4 * i] = tx - (A11 * rx - A01 * ry) * id;
+          nst[4 * i + 1] = ty - (A00 * ry - A01 * rx) * id;
+        }
+        __syncthreads();
+      }
+      double c2 = 0.0, d2 = 0.0;
+      for (int i = tid; i < n_img; i += blockDim.x) {
+        const double d0 = C.theta[2 * i] - nst[4 * i], d1 = C.theta[2 * i + 1] - nst[4 * i + 1];
+        c2 += C.sinv[3 * i] * d0 * d0 + 2.0 * C.sinv[3 * i + 1] * d0 * d1 + C.sinv[3 * i + 2] * d1 * d1;
+        d2 += d0 * d0 + d1 * d1;
+      }
+      const double tc = block_sum(c2, scratch);
+      const double td = block_sum(d2, scratch);
+      if (tid == 0) {
+        chi2[s] = isfinite(tc) ? tc : INFINITY;
+        if (rms) rms[s] = sqrt(td / n_img);
+      }
+      __syncthreads();
+      continue;
     }
     const double total = block_sum(my, scratch);
     if (tid == 0) chi2[s] = total;
@@ -877,6 +946,7 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
   C.off_fam = o; o += (uint32_t)C.n_fam * 3u * 8u;
   C.off_par = o; o += (uint32_t)C.P * 2u * 8u;
   o = (o + 15u) & ~15u; C.off_free = o; o += (uint32_t)C.n_free * 64u;
+  o = (o + 15u) & ~15u; C.off_newton = o; o += (uint32_t)C.n_img * 4u * 8u;
   C.smem = (o + 15u) & ~15u;
   int K = 0;
   for (int j = 0; j < C.np; ++j) K = std::max(K, C.pl[j].nc + C.pl[j].nm);
@@ -907,8 +977,12 @@ static lf_status relayout(lf_plan* pl) {
   const void* kg = pl->precision == LF_MIXED ? (const void*)k_chi2<LF_MIXED, true>
                    : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, true>
                                              : (const void*)k_chi2<LF_FP64, true>;
+  const void* ki = pl->precision == LF_MIXED ? (const void*)k_chi2<LF_MIXED, false, 1>
+                   : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, false, 1>
+                                             : (const void*)k_chi2<LF_FP64, false, 1>;
   LF_TRY(kset(kc));
   LF_TRY(kset(kg));
+  LF_TRY(kset(ki));
   LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kc, pl->block, pl->smem));
   pl->grid_chi2 = nsm * std::max(occ, 1);
   LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kg, pl->block, pl->smem));
@@ -1098,6 +1172,19 @@ static void launch_mode(lf_plan* pl, const double* theta, int S, double* chi2, d
   }
 }
 
+template <int MODE>
+static void launch_img(lf_plan* pl, const double* theta, int S, int iters, double* chi2, double* rms,
+                       cudaStream_t st, int spc) {
+  const int nprep = S * pl->nfree_max;
+  if (nprep > 0)
+    k_chi2_prep<MODE><<<(nprep + 63) / 64, 64, 0, st>>>(pl->d_desc, spc, S, pl->nfree_max, theta,
+                                                        pl->d_free_dig, pl->d_free_raw);
+  int g = std::min(pl->grid_chi2, S);
+  k_chi2<MODE, false, 1><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
+                                                         nullptr, pl->d_counter, g_member_chunk,
+                                                         pl->d_free_dig, nullptr, iters, rms);
+}
+
 static lf_status launch_chi2(lf_plan* pl, const double* theta, int S, double* chi2, double* grad,
                              cudaStream_t st) {
   const int spc = S / pl->n_clusters;
@@ -1258,6 +1345,24 @@ extern "C" lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int3
   if (!grad) return fail(LF_EINVAL, "grad is NULL");
   if (!plan->single_plane) return fail(LF_EUNSUPPORTED, "the gradient is implemented for single-plane plans");
   return run(plan, theta, S, chi2, grad, stream);
+}
+
+extern "C" lf_status lf_chi2_img_batch(lf_plan* plan, const double* theta, int32_t S, int32_t iters,
+                                       double* chi2_img, double* rms, void* stream) {
+  if (!plan) return fail(LF_EINVAL, "plan is NULL");
+  if (!theta || !chi2_img) return fail(LF_EINVAL, "theta and chi2_img are required");
+  if (S < 1 || S > plan->max_samples) return fail(LF_EINVAL, "S must be in 1..%d", plan->max_samples);
+  if (S % plan->n_clusters) return fail(LF_EINVAL, "S must be a multiple of the number of clusters");
+  if (iters < 1 || iters > 64) return fail(LF_EINVAL, "iters must be in 1..64");
+  if (!plan->single_plane) return fail(LF_EUNSUPPORTED, "the image-plane chi^2 is implemented for single-plane plans");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int spc = S / plan->n_clusters;
+  LF_CUDA(cudaMemsetAsync(plan->d_counter, 0, sizeof(int), st));
+  if (plan->precision == LF_MIXED) launch_img<LF_MIXED>(plan, theta, S, iters, chi2_img, rms, st, spc);
+  else if (plan->precision == LF_FF) launch_img<LF_FF>(plan, theta, S, iters, chi2_img, rms, st, spc);
+  else launch_img<LF_FP64>(plan, theta, S, iters, chi2_img, rms, st, spc);
+  LF_CUDA(cudaGetLastError());
+  return LF_OK;
 }
 
 extern "C" lf_status lf_plan_info(const lf_plan* plan, int32_t* kslices, int32_t* block, int32_t* graph) {
