@@ -222,6 +222,22 @@ lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int32_t S, doub
 lf_status lf_chi2_img_batch(lf_plan* plan, const double* theta, int32_t S, int32_t iters,
                             double* chi2_img, double* rms, void* stream);
 
+/* Affine-invariant ensemble sampler (Goodman & Weare 2010; the paper's posterior sampler,
+ * Sec. 3.5) on a single-cluster plan: likelihood exp(-chi^2/2) with the plan's chi^2, uniform
+ * priors on the box [lo, hi].  Each of n_steps steps updates the two halves of the S walkers
+ * in turn with the stretch move: walker k of one half takes partner j = floor(u0 S/2) of the
+ * other half and z = ((a - 1) u1 + 1)^2 / a, proposes y = x_j + z (x_k - x_j), and accepts if
+ * log u2 < (P - 1) log z - (chi^2(y) - chi^2(x_k)) / 2 (FP64); proposals outside the box are
+ * rejected.  walkers: device [S * P] in/out; chi2: device [S] in/out (chi^2 of the walkers on
+ * entry, e.g. from lf_chi2_batch); uniforms: device [n_steps * S * 3] in [0, 1), rows of the
+ * first S/2 walkers drive the first half; lo, hi: device [P]; chain: device
+ * [n_steps * S * P] (the walkers after each step) or NULL; n_accept: device counter added to,
+ * or NULL.  S even, S/2 <= max_samples, a > 1.  The first call allocates the sampler's
+ * workspace inside the plan. */
+lf_status lf_aies_run(lf_plan* plan, double* walkers, double* chi2, int32_t S, int32_t n_steps,
+                      const double* uniforms, double a, const double* lo, const double* hi,
+                      double* chain, unsigned long long* n_accept, void* stream);
+
 lf_status lf_plan_destroy(lf_plan* plan);
 
 /* lf_chi2_batch for one cluster with no device allocation (the paper has no counterpart;

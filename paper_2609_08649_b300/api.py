@@ -172,6 +172,19 @@ class Plan:
                                         _stream()))
         return out, rms
 
+    def aies_run(self, walkers: torch.Tensor, chi2: torch.Tensor, uniforms: torch.Tensor, a: float,
+                 lo: torch.Tensor, hi: torch.Tensor, chain=False):
+        """Stretch-move steps in place on (walkers, chi2); uniforms (n_steps, S, 3) on the device.
+        Returns (n_accepted, chain or None)."""
+        S = walkers.shape[0]
+        n_steps = uniforms.shape[0]
+        ch = torch.empty(n_steps, S, self.P, dtype=torch.float64, device="cuda") if chain else None
+        acc = torch.zeros(1, dtype=torch.int64, device="cuda")
+        L.check(L.lib.lf_aies_run(self.handle, _ptr(walkers), _ptr(chi2), S, n_steps,
+                                  _ptr(uniforms.contiguous()), float(a), _ptr(lo.contiguous()),
+                                  _ptr(hi.contiguous()), _ptr(ch), _ptr(acc), _stream()))
+        return acc, ch
+
     def info(self):
         ks, blk, g = C.c_int32(), C.c_int32(), C.c_int32()
         L.check(L.lib.lf_plan_info(self.handle, C.byref(ks), C.byref(blk), C.byref(g)))

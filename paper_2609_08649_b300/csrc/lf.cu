@@ -5,4 +5,5 @@
 #include "lf_grid.cu"
 #include "lf_trace.cu"
 #include "lf_chi2.cu"
+#include "lf_sampler.cu"
 #include "lf_static.cu"

@@ -856,6 +856,12 @@ struct lf_plan {
   int* d_counter = nullptr;
   int* d_order = nullptr;
   int nfree_max = 0;               // largest number of sampled components of a cluster
+  // sampler workspace (allocated on the first lf_aies_run): proposals of one half, their z,
+  // prior flags and chi^2
+  double* d_prop = nullptr;
+  double* d_z = nullptr;
+  int* d_inside = nullptr;
+  double* d_chi2_prop = nullptr;
   void* d_free_dig = nullptr;      // [max_samples * LF_MAX_FREE] digested sampled components
   lf_comp* d_free_raw = nullptr;   // [max_samples * LF_MAX_FREE] their fields (adjoint)
   std::vector<void*> allocs;
@@ -1183,6 +1189,21 @@ static void launch_img(lf_plan* pl, const double* theta, int S, int iters, doubl
   k_chi2<MODE, false, 1><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
                                                          nullptr, pl->d_counter, g_member_chunk,
                                                          pl->d_free_dig, nullptr, iters, rms);
+}
+
+static lf_status ensure_sampler_workspace(lf_plan* pl) {
+  if (pl->d_prop) return LF_OK;
+  const size_t h = (size_t)pl->max_samples;
+  void* p = nullptr;
+  LF_TRY(plan_alloc(pl, &p, h * pl->P * sizeof(double)));
+  pl->d_prop = (double*)p;
+  LF_TRY(plan_alloc(pl, &p, h * sizeof(double)));
+  pl->d_z = (double*)p;
+  LF_TRY(plan_alloc(pl, &p, h * sizeof(int)));
+  pl->d_inside = (int*)p;
+  LF_TRY(plan_alloc(pl, &p, h * sizeof(double)));
+  pl->d_chi2_prop = (double*)p;
+  return LF_OK;
 }
 
 static lf_status launch_chi2(lf_plan* pl, const double* theta, int S, double* chi2, double* grad,

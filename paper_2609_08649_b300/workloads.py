@@ -281,6 +281,12 @@ def position_noise(seed: int, n: int, sigma: float) -> np.ndarray:
     return np.random.default_rng(seed).normal(0.0, sigma, (n, 2))
 
 
+def sampler_uniforms(seed: int, n_steps: int, n_walkers: int) -> np.ndarray:
+    """(n_steps, n_walkers, 3) uniforms in [0, 1) for the stretch-move sampler
+    (partner choice, stretch factor, acceptance)."""
+    return np.random.default_rng(seed).uniform(0.0, 1.0, (n_steps, n_walkers, 3))
+
+
 def random_positions(seed: int, n: int, half: float) -> np.ndarray:
     """(n, 2) positions uniform in a square of half-width `half` (sampled-pixel checks)."""
     return np.random.default_rng(seed).uniform(-half, half, (n, 2))
