@@ -381,6 +381,39 @@ def secondary(torch, api, PM, W, L, C, step, ms_mixed, evals):
         out["grad_16clusters_1024"] = res
     except FileNotFoundError as e:
         out["grad_16clusters_1024"] = {"skipped": str(e)}
+    # image-plane chi^2 (Newton model images) and the on-device sampler on the same cluster
+    res = {}
+    wl2 = W.cluster_c2()
+    th2 = torch.tensor(W.sample_thetas(wl2, wl2.seed), device="cuda")
+    for prec in ("mixed", "ff"):
+        plan = api.Plan([PM.cluster_input(wl2, cat)], th2.shape[0], prec, flags=api.FLAG_AUTOTUNE)
+        plan.chi2(th2)
+        t = _time(torch, lambda: plan.chi2_img(th2, iters=8), reps=3)
+        res[prec] = {"ms": t, "chi2_img_per_s": th2.shape[0] / (t * 1e-3), "newton_iters": 8}
+        plan.close()
+    out["chi2_img_4096x200"] = res
+    res = {}
+    sd = np.array([p.jitter * (abs(p.base) if p.relative else 1) for p in wl2.params])
+    lo = torch.tensor(th2[0].cpu().numpy() - 20 * sd, device="cuda")
+    hi = torch.tensor(th2[0].cpu().numpy() + 20 * sd, device="cuda")
+    steps = 10
+    u = torch.tensor(W.sampler_uniforms(3, steps, th2.shape[0]), device="cuda")
+    for prec in ("mixed", "ff"):
+        plan = api.Plan([PM.cluster_input(wl2, cat)], th2.shape[0] // 2, prec, flags=api.FLAG_AUTOTUNE)
+        x = th2.clone()
+        c = torch.cat([plan.chi2(x[:x.shape[0] // 2].contiguous()), plan.chi2(x[x.shape[0] // 2:].contiguous())])
+        plan.aies_run(x, c, u[:1], 2.0, lo, hi)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        acc, _ = plan.aies_run(x, c, u, 2.0, lo, hi)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[prec] = {"walkers": int(x.shape[0]), "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+                     "chi2_per_s": x.shape[0] * 1e3 / ms, "acceptance": int(acc) / (steps * x.shape[0])}
+        plan.close()
+    out["aies_4096_walkers"] = res
     # 3-plane trace of a 2048^2 grid
     wl3 = W.multiplane_c3()
     planes = PM.device_planes(wl3)
