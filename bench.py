@@ -34,8 +34,8 @@ METRIC = "lens evals/s (samples×positions×components)"
 UNIT = "lens evals/s"
 WORKLOAD = ("cluster_dpie302_grid4096: 2 elliptical dPIE halos + 300 PJE members, "
             "4096x4096 grid at 0.04\", alpha/kappa/gamma/mu at z_s=9")
-FP32_INSTR_PER_EVAL = 39      # FP32-pipe instructions of one member evaluation
-XU_INSTR_PER_EVAL = 4         # MUFU instructions of one member evaluation
+FP32_INSTR_PER_EVAL = 33      # FP32 lane operations of one member evaluation
+XU_INSTR_PER_EVAL = 4         # MUFU operations of one member evaluation
 FP32_LANES_PER_SM, XU_LANES_PER_SM = 128, 16
 
 
@@ -272,7 +272,7 @@ def main():
     fp32_ach = evals * FP32_INSTR_PER_EVAL / (ms * 1e-3) / 1e12
     xu_ach = evals * XU_INSTR_PER_EVAL / (ms * 1e-3) / 1e12
     traffic = map_kernel_traffic() if args.precision == "mixed" and args.grid == 4096 else None
-    roofline = {"bound": "alu", "achieved": fp32_ach, "peak": fp32_peak, "unit": "Tinst/s (FP32 pipe)",
+    roofline = {"bound": "alu", "achieved": fp32_ach, "peak": fp32_peak, "unit": "T FP32 lane-ops/s",
                 "frac": fp32_ach / fp32_peak, "traffic": traffic,
                 "xu": {"achieved": xu_ach, "peak": xu_peak, "frac": xu_ach / xu_peak},
                 "hbm_achieved_gbs": d2h / (ms * 1e-3) / 1e9,

@@ -500,6 +500,82 @@ LF_INLINE void eval_member(const MemT<T>& m, T dx, T dy, Out5<T>& o) {
   o.pxy = t * dx * dy;
 }
 
+// ------------------------------------------------------- packed member pairs ---
+// Two members per record (lane x = member 2j, lane y = member 2j + 1) so that the packed
+// FP32 instructions of sm_100 and later (add / mul / fma .rn.f32x2) evaluate both at one
+// position: every packed instruction does two members' work in one issue slot.  Centres
+// are stored negated so that each offset is a pair of adds, rounded exactly as
+// (x_h - c_h) + (x_l - c_l).  A lane past the last member holds a zero-strength member
+// (b = 0), whose every contribution is exactly zero.
+struct __align__(16) MemPair {
+  float2 nxh, nxl, nyh, nyl;  // -(float-float centre)
+  float2 s2, a2, s, a;        // core^2, cut^2, core, cut
+  float2 apc, bd, b, pad;     // a + s, b (a - s), b
+};
+
+LF_INLINE void set_lane(float2& v, int lane, float x) {
+  if (lane) v.y = x; else v.x = x;
+}
+
+__device__ inline void digest_member_lane(double x, double y, double b, double s, double a,
+                                          MemPair& p, int lane) {
+  float h, l;
+  split_ff(x, h, l); set_lane(p.nxh, lane, -h); set_lane(p.nxl, lane, -l);
+  split_ff(y, h, l); set_lane(p.nyh, lane, -h); set_lane(p.nyl, lane, -l);
+  set_lane(p.s2, lane, (float)(s * s)); set_lane(p.a2, lane, (float)(a * a));
+  set_lane(p.s, lane, (float)s); set_lane(p.a, lane, (float)a);
+  set_lane(p.apc, lane, (float)(a + s)); set_lane(p.bd, lane, (float)(b * (a - s)));
+  set_lane(p.b, lane, (float)b); set_lane(p.pad, lane, 0.f);
+}
+__device__ inline void digest_pad_lane(MemPair& p, int lane) {
+  digest_member_lane(0.0, 0.0, 0.0, 1.0, 2.0, p, lane);
+}
+
+LF_INLINE float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+LF_INLINE float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+LF_INLINE float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+LF_INLINE float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// The round-PJE closed form (pje_round) for the two members of a record at one position,
+// added into packed chunk sums laid out so that psi needs no per-member diagonal terms:
+//   c[0] += kbar dx, c[1] += kbar dy, c[2] += kbar, c[3] += t dx^2, c[4] += t dx dy,
+//   c[5] += t r^2;  then psi_xx = c2 + c3, psi_yy = c2 + c5 - c3, psi_xy = c4
+// (psi_ij = kbar delta_ij + t x_i x_j, so psi_yy = kbar + t (r^2 - dx^2)).
+// 33 packed FP32 instructions and 8 MUFU (4 per member).
+LF_INLINE void member_pair_acc(const MemPair& m, float2 pxh, float2 pxl, float2 pyh, float2 pyl,
+                               float2 (&c)[6]) {
+  const float2 one = make_float2(1.f, 1.f);
+  const float2 dx = add2(add2(pxh, m.nxh), add2(pxl, m.nxl));
+  const float2 dy = add2(add2(pyh, m.nyh), add2(pyl, m.nyl));
+  const float2 r2 = fma2(dx, dx, mul2(dy, dy));
+  const float2 S2 = add2(m.s2, r2), R2 = add2(m.a2, r2);
+  const float2 iS = make_float2(rsqrtf(S2.x), rsqrtf(S2.y));
+  const float2 iR = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
+  const float2 S = mul2(S2, iS), R = mul2(R2, iR);
+  const float2 Ss = add2(S, m.s), Ra = add2(R, m.a);
+  const float2 X = mul2(Ss, Ra);
+  const float2 RS = add2(R, S);
+#if LF_PAIR_ONE_RCP
+  // one reciprocal for both: Z = 1 / (X (R + S)), PQ = Z (R + S), 1 / (R + S) = Z X
+  const float2 XR = mul2(X, RS);
+  const float2 Z = make_float2(__fdividef(1.f, XR.x), __fdividef(1.f, XR.y));
+  const float2 PQ = mul2(Z, RS), iRS = mul2(Z, X);
+#else
+  const float2 PQ = make_float2(__fdividef(1.f, X.x), __fdividef(1.f, X.y));
+  const float2 iRS = make_float2(__fdividef(1.f, RS.x), __fdividef(1.f, RS.y));
+#endif
+  const float2 kb = mul2(mul2(m.bd, PQ), fma2(m.apc, iRS, one));
+  const float2 P = mul2(PQ, Ra), Q = mul2(PQ, Ss);
+  const float2 t = mul2(m.b, fma2(neg2(mul2(P, P)), iS, mul2(mul2(Q, Q), iR)));
+  c[0] = fma2(kb, dx, c[0]);
+  c[1] = fma2(kb, dy, c[1]);
+  c[2] = add2(c[2], kb);
+  const float2 tdx = mul2(t, dx);
+  c[3] = fma2(tdx, dx, c[3]);
+  c[4] = fma2(tdx, dy, c[4]);
+  c[5] = fma2(t, r2, c[5]);
+}
+
 // ------------------------------------- extended-precision deflection (mixed path) ---
 // Offset from a centre as float-float: (x_h - c_h) with its exact rounding error, plus the
 // difference of the low words.

@@ -19,6 +19,12 @@ struct PlaneLayout {
   uint32_t rawc, rawm, dc, dm, total;
 };
 
+// Number of digested member records: one per member, or one per pair of members.
+template <class M> __host__ __device__ inline uint32_t mem_records(int nm) { return (uint32_t)nm; }
+template <> __host__ __device__ inline uint32_t mem_records<MemPair>(int nm) {
+  return (uint32_t)(nm + 1) / 2u;
+}
+
 template <class T, class M = MemT<T>>
 __host__ __device__ inline PlaneLayout plane_layout(int nc, int nm, uint32_t base) {
   PlaneLayout L;
@@ -28,7 +34,7 @@ __host__ __device__ inline PlaneLayout plane_layout(int nc, int nm, uint32_t bas
   o = (o + 15u) & ~15u;
   L.dc = o; o += (uint32_t)nc * (uint32_t)sizeof(CompT<T>);
   o = (o + 15u) & ~15u;
-  L.dm = o; o += (uint32_t)nm * (uint32_t)sizeof(M);
+  L.dm = o; o += mem_records<M>(nm) * (uint32_t)sizeof(M);
   L.total = (o + 15u) & ~15u;
   return L;
 }
@@ -74,6 +80,80 @@ __device__ inline void digest_plane_x(const lf_comp* rawc, int nc, const lf_memb
     double b, s, a, ll;
     member_fields(sc, rawm[i].log_l, b, s, a, ll);
     digest_member_x(rawm[i].x, rawm[i].y, b, s, a, ll, dm[i]);
+  }
+}
+
+// Digests a staged plane into explicit components and packed member pairs, whole block.
+__device__ inline void digest_plane_pairs(const lf_comp* rawc, int nc, const lf_member* rawm,
+                                          int nm, const lf_scaling& sc, CompT<float>* dc,
+                                          MemPair* dp) {
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) digest_one_comp<float>(rawc[i], dc[i]);
+  const int n2 = 2 * (int)mem_records<MemPair>(nm);
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    if (i < nm) {
+      double b, s, a, ll;
+      member_fields(sc, rawm[i].log_l, b, s, a, ll);
+      digest_member_lane(rawm[i].x, rawm[i].y, b, s, a, dp[i >> 1], i & 1);
+    } else {
+      digest_pad_lane(dp[i >> 1], i & 1);
+    }
+  }
+}
+
+// LF_MIXED with packed member pairs: explicit components as in accumulate_mixed; members two
+// at a time (f32x2), `chunk` pairs per FP32 partial sum, each folded into the float-float
+// accumulators.
+template <int PPT>
+__device__ __forceinline__ void accumulate_packed(const CompT<float>* dc, int nc, const MemPair* dp,
+                                                  int nm, int chunk, const float* pxh,
+                                                  const float* pxl, const float* pyh,
+                                                  const float* pyl, const float2* tab,
+                                                  ff (&acc)[5][PPT]) {
+  for (int c = 0; c < nc; ++c) {
+    const CompT<float>& C = dc[c];
+    if (C.kind == 0) continue;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      ff ax, ay;
+      Out5<float> o;
+      eval_comp_mixed(C, pxh[k], pxl[k], pyh[k], pyl[k], tab, ax, ay, o);
+      acc[0][k] = ff_add(acc[0][k], ax);
+      acc[1][k] = ff_add(acc[1][k], ay);
+      ff_acc(acc[2][k], o.pxx); ff_acc(acc[3][k], o.pyy); ff_acc(acc[4][k], o.pxy);
+    }
+  }
+  float2 qxh[PPT], qxl[PPT], qyh[PPT], qyl[PPT];
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    qxh[k] = make_float2(pxh[k], pxh[k]); qxl[k] = make_float2(pxl[k], pxl[k]);
+    qyh[k] = make_float2(pyh[k], pyh[k]); qyl[k] = make_float2(pyl[k], pyl[k]);
+  }
+  const int np = (int)mem_records<MemPair>(nm);
+  for (int j0 = 0; j0 < np; j0 += chunk) {
+    const int j1 = min(j0 + chunk, np);
+    float2 cs[PPT][6];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k)
+#pragma unroll
+      for (int v = 0; v < 6; ++v) cs[k][v] = make_float2(0.f, 0.f);
+#if LF_MAP_UNROLL == 2
+#pragma unroll 2
+#endif
+    for (int j = j0; j < j1; ++j) {
+      const MemPair M = dp[j];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) member_pair_acc(M, qxh[k], qxl[k], qyh[k], qyl[k], cs[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const float kb = cs[k][2].x + cs[k][2].y, txx = cs[k][3].x + cs[k][3].y;
+      const float trr = cs[k][5].x + cs[k][5].y;
+      ff_acc(acc[0][k], cs[k][0].x + cs[k][0].y);
+      ff_acc(acc[1][k], cs[k][1].x + cs[k][1].y);
+      ff_acc(acc[2][k], kb + txx);
+      ff_acc(acc[3][k], kb + (trr - txx));
+      ff_acc(acc[4][k], cs[k][4].x + cs[k][4].y);
+    }
   }
 }
 

@@ -57,18 +57,32 @@ __device__ __forceinline__ void write_out(const OutArgs& O, long long p, double 
 
 // ------------------------------------------------------------------- LF_MIXED ------
 #ifndef LF_MAP_MINB
-#define LF_MAP_MINB 3   // at most 85 registers: 3 blocks of 256 per SM
+#define LF_MAP_MINB 3   // scalar and float-float variants: at most 85 registers, 3 blocks of 256
+#endif
+#ifndef LF_MAP_MINB_PACK
+#define LF_MAP_MINB_PACK 4   // packed variant: 64 registers, 4 blocks of 256 per SM
+#endif
+#ifndef LF_MAP_PACK
+#define LF_MAP_PACK 1   // members in packed pairs (f32x2)
 #endif
 #ifndef LF_MAP_PPT
-#define LF_MAP_PPT 2
+#define LF_MAP_PPT 1
 #endif
-template <int PPT, bool EXT>
-__global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_mixed(const lf_comp* __restrict__ comp, int nc,
+#ifndef LF_MAP_CHUNK
+#define LF_MAP_CHUNK 16   // packed variant: member pairs per FP32 partial sum (16 terms per lane)
+#endif
+// Member record of each variant: float-float (EXT), packed pairs (PACK), or scalar.
+template <bool EXT, bool PACK>
+using MapMem = typename std::conditional<EXT, MemX,
+                                         typename std::conditional<PACK, MemPair, MemT<float>>::type>::type;
+
+template <int PPT, bool EXT, bool PACK>
+__global__ void __launch_bounds__(256, PACK ? LF_MAP_MINB_PACK : LF_MAP_MINB) k_map_mixed(const lf_comp* __restrict__ comp, int nc,
                                                    const lf_member* __restrict__ mem, int nm,
                                                    lf_scaling sc, PosArgs P, OutArgs O, int chunk) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  typedef typename std::conditional<EXT, MemX, MemT<float>>::type Mem;
+  typedef MapMem<EXT, PACK> Mem;
   const PlaneLayout L = plane_layout<float, Mem>(nc, nm, LF_MAP_BASE);
   lf_comp* rawc = reinterpret_cast<lf_comp*>(smem + L.rawc);
   lf_member* rawm = reinterpret_cast<lf_member*>(smem + L.rawm);
@@ -82,6 +96,7 @@ __global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_mixed(const lf_comp* _
   if (ok) ok = stage_to_smem(rawm, mem, (uint32_t)nm * 32u, bar, nc > 0 ? 1 : 0);
   if (!ok) return;
   if constexpr (EXT) digest_plane_x(rawc, nc, rawm, nm, sc, dc, dm);
+  else if constexpr (PACK) digest_plane_pairs(rawc, nc, rawm, nm, sc, dc, dm);
   else digest_plane<float>(rawc, nc, rawm, nm, sc, dc, dm);
   __syncthreads();
 
@@ -105,6 +120,7 @@ __global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_mixed(const lf_comp* _
       for (int k = 0; k < PPT; ++k) acc[v][k] = ff_zero();
 
     if constexpr (EXT) accumulate_ext<PPT>(dc, nc, dm, nm, 0, nc + nm, pxh, pxl, pyh, pyl, tab, acc);
+    else if constexpr (PACK) accumulate_packed<PPT>(dc, nc, dm, nm, chunk, pxh, pxl, pyh, pyl, tab, acc);
     else accumulate_mixed<PPT>(dc, nc, dm, nm, 0, nc + nm, chunk, pxh, pxl, pyh, pyl, tab, acc);
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
@@ -162,20 +178,20 @@ lf_status check_plane(const lf_plane* pl) {
   return LF_OK;
 }
 
-template <int PPT, bool EXT>
+template <int PPT, bool EXT, bool PACK>
 static lf_status launch_mixed(const lf_plane* pl, const PosArgs& P, const OutArgs& O, int nsm,
                               int block, cudaStream_t s) {
-  typedef typename std::conditional<EXT, MemX, MemT<float>>::type Mem;
+  typedef MapMem<EXT, PACK> Mem;
   PlaneLayout L = plane_layout<float, Mem>(pl->n_comp, pl->n_mem, LF_MAP_BASE);
   if (L.total > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "plane too large for shared memory");
-  auto k = k_map_mixed<PPT, EXT>;
+  auto k = k_map_mixed<PPT, EXT, PACK>;
   LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
   int occ = 0;
   LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, L.total));
   long long tiles = (P.n + (long long)PPT * block - 1) / ((long long)PPT * block);
   long long grid = std::min<long long>(tiles, (long long)nsm * std::max(occ, 1));
   k<<<(unsigned)grid, block, L.total, s>>>(pl->comp, pl->n_comp, pl->mem, pl->n_mem, pl->scaling, P, O,
-                                           g_member_chunk);
+                                           PACK ? LF_MAP_CHUNK : g_member_chunk);
   return LF_OK;
 }
 
@@ -192,9 +208,13 @@ static lf_status launch_map(const lf_plane* pl, const PosArgs& P, const OutArgs&
   LF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int block = 256;
   if (precision == LF_MIXED) {
-    LF_TRY((launch_mixed<LF_MAP_PPT, false>(pl, P, O, nsm, block, s)));
+#if LF_MAP_PACK
+    LF_TRY((launch_mixed<LF_MAP_PPT, false, true>(pl, P, O, nsm, block, s)));
+#else
+    LF_TRY((launch_mixed<LF_MAP_PPT, false, false>(pl, P, O, nsm, block, s)));
+#endif
   } else if (precision == LF_FF) {
-    LF_TRY((launch_mixed<1, true>(pl, P, O, nsm, block, s)));
+    LF_TRY((launch_mixed<1, true, false>(pl, P, O, nsm, block, s)));
   } else {
     PlaneLayout L = plane_layout<double>(pl->n_comp, pl->n_mem, 16);
     if (L.total > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "plane too large for shared memory");
