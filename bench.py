@@ -414,6 +414,22 @@ def secondary(torch, api, PM, W, L, C, step, ms_mixed, evals):
                      "chi2_per_s": x.shape[0] * 1e3 / ms, "acceptance": int(acc) / (steps * x.shape[0])}
         plan.close()
     out["aies_4096_walkers"] = res
+    # lens-equation solver: 60 seeded sources (z_s of the catalogue's families) on a 1601^2
+    # vertex grid over the 160" field, Newton polish in FP64
+    srcs = torch.tensor(W.source_candidates(23, 60, 12.0, 4.0, -3.0), device="cuda")
+    adis = torch.tensor([PM.adis(wl2.cosmo, wl2.planes[0].z, z) for z in wl2.family_zs],
+                        dtype=torch.float64, device="cuda")
+    fgrid = W.Grid(-80.0, -80.0, 0.1, 0.1, 1601, 1601)
+    fplane = PM.device_planes(wl2)[0]
+    ws = torch.empty(api.find_images_workspace(fgrid, 60, 32), dtype=torch.uint8, device="cuda")
+    res = {}
+    for prec in ("mixed", "fp64"):
+        t = _time(torch, lambda: api.find_images(fplane, fgrid, srcs, adis, max_img=32, polish_iters=50,
+                                                 precision=prec, workspace=ws), reps=3)
+        _, nimg = api.find_images(fplane, fgrid, srcs, adis, max_img=32, polish_iters=50, precision=prec,
+                                  workspace=ws)
+        res[prec] = {"ms": t, "sources_per_s": 60 / (t * 1e-3), "images": int(nimg.clamp(min=0).sum())}
+    out["find_images_60src_1601sq"] = res
     # 3-plane trace of a 2048^2 grid
     wl3 = W.multiplane_c3()
     planes = PM.device_planes(wl3)
@@ -459,15 +475,17 @@ def single_workload(args, torch, api, PM, W):
         plan = api.Plan([PM.cluster_input(wl, cat)], th.shape[0], prec, flags=api.FLAG_AUTOTUNE)
         plan.chi2(th)   # tunes the tile shape once
         fn = (lambda: plan.chi2(th)) if args.workload == "chi2" else (lambda: plan.chi2_grad(th))
+        info = plan.info()
     else:
         wl3 = W.multiplane_c3(n_grid=args.grid // 2)
         planes = PM.device_planes(wl3)
         r = PM.multiplane_ratios(wl3.cosmo, [p.z for p in wl3.planes], wl3.z_s)
         fn = lambda: api.trace_multiplane(planes, r, grid=wl3.grid, precision=prec)
+        info = {}
     for _ in range(args.warmup):
         fn()
     ms = _time(torch, fn, reps=args.steps, warm=0)
-    print(json.dumps({"workload": args.workload, "precision": prec, "ms": ms}), flush=True)
+    print(json.dumps({"workload": args.workload, "precision": prec, "ms": ms, "tile": info}), flush=True)
 
 
 if __name__ == "__main__":

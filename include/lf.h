@@ -34,6 +34,7 @@
 #ifndef LF_H_
 #define LF_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -148,6 +149,35 @@ lf_status lf_jacobian_points(const lf_plane* plane, const double* theta, int32_t
 lf_status lf_trace_multiplane(const lf_plane* planes, int32_t n_planes, const double* ratios,
                               const double* theta, int32_t n, const lf_grid* grid,
                               int32_t precision, double* beta, double* A, void* stream);
+
+/* ---------------------------------------------------------- image finder ------- */
+
+/* Lens-equation solver of Sec. 2.3: the images of a source beta are the common zeros of
+ * f(theta) = beta - theta + a alpha(theta).  Each component's zero contour is traced over the
+ * vertex grid `grid` (vertices x0 + i dx, y0 + j dy, i < nx, j < ny; nx, ny >= 2) by marching
+ * squares (linear interpolation along cell edges, a saddle cell resolved by its centre value,
+ * f > 0 counted as positive), and the images are the exact intersections of pairs of contour
+ * segments in one cell (segment parameters within [0, 1] up to 1e-12).  Candidates are
+ * ordered by cell (row-major) and segment pair and merged when closer than 1e-6 dx.  With
+ * polish_iters > 0 each image is then refined by up to polish_iters Newton steps
+ * theta <- theta - A^-1 (theta - a alpha - beta), evaluated in FP64, stopping once the
+ * residual is below 1e-12; images closer than 1e-7 (arcsec) after the polish are merged and
+ * non-finite ones dropped (the polish is not part of the paper's solver).
+ * precision selects the tier of the deflection grid (LF_FP64 / LF_MIXED / LF_FF).
+ *   beta    device [n_src * 2] source positions, arcsec
+ *   a_src   device [n_src] a_dis = D_ds / D_s of each source, in (0, 1]; a source outside
+ *           that range is skipped with n_img = 0 and raises the device error word
+ *   img     device [n_src * max_img * 2] images of source s at img[2 (s max_img + k)]
+ *   n_img   device [n_src] number of images found (may exceed max_img: only the first
+ *           max_img are stored), or -1 when more than 4 max_img + 16 raw candidates arose
+ *   workspace  device, 256-byte aligned, at least lf_find_images_workspace(nx, ny, n_src,
+ *           max_img) bytes; caller-owned, reusable after the stream reaches the call's end
+ * Stream-ordered; LF_EINVAL for invalid host arguments (nothing launched). */
+size_t lf_find_images_workspace(int32_t nx, int32_t ny, int32_t n_src, int32_t max_img);
+lf_status lf_find_images(const lf_plane* plane, const lf_grid* grid, int32_t precision,
+                         const double* beta, const double* a_src, int32_t n_src, int32_t max_img,
+                         int32_t polish_iters, void* workspace, size_t workspace_bytes,
+                         double* img, int32_t* n_img, void* stream);
 
 /* ------------------------------------------------------------ chi^2 plans ------- */
 

@@ -22,6 +22,16 @@ def _ptr(t: Optional[torch.Tensor]):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _dev64(t: torch.Tensor, name: str, inplace=False) -> torch.Tensor:
+    """A float64 CUDA tensor for the C ABI (which reads raw double pointers): other dtypes or
+    host tensors are rejected rather than reinterpreted."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if inplace and not t.is_contiguous():
+        raise ValueError(f"{name} is updated in place and must be contiguous")
+    return t.contiguous()
+
+
 def _prec(p):
     return PRECISION[p] if isinstance(p, str) else int(p)
 
@@ -58,7 +68,7 @@ def jacobian_grid(plane: DevicePlane, grid, a_dis, precision="mixed", outputs=AL
 
 def jacobian_points(plane: DevicePlane, theta: torch.Tensor, a_dis, precision="mixed",
                     outputs=ALL_OUTPUTS):
-    theta = theta.contiguous()
+    theta = _dev64(theta, "theta")
     n = theta.shape[0]
     o = _jac_outputs(n, outputs)
     ps = plane.c_struct()
@@ -73,7 +83,7 @@ def trace_multiplane(planes: Sequence[DevicePlane], ratios: np.ndarray, theta=No
     arr = (L.lf_plane * len(planes))(*[p.c_struct() for p in planes])
     rat = np.ascontiguousarray(ratios, dtype=np.float64)
     if theta is not None:
-        theta = theta.contiguous()
+        theta = _dev64(theta, "theta")
         n = theta.shape[0]
         gptr = None
     else:
@@ -85,6 +95,30 @@ def trace_multiplane(planes: Sequence[DevicePlane], ratios: np.ndarray, theta=No
     L.check(L.lib.lf_trace_multiplane(arr, len(planes), rat.ctypes.data_as(C.c_void_p), _ptr(theta),
                                       n, gptr, _prec(precision), _ptr(beta), _ptr(A), _stream()))
     return beta, A
+
+
+def find_images(plane: DevicePlane, grid, beta: torch.Tensor, a_src: torch.Tensor, max_img=8,
+                polish_iters=0, precision="fp64", workspace: Optional[torch.Tensor] = None):
+    """Images of n_src sources (beta (n_src, 2), a_src (n_src,)) on a vertex grid.
+    Returns (img (n_src, max_img, 2), n_img (n_src,) int32); n_img = -1 flags an overflow of
+    the candidate buffer.  `workspace` (uint8, from find_images_workspace) may be reused."""
+    beta = _dev64(beta, "beta")
+    a_src = _dev64(a_src, "a_src")
+    n = beta.shape[0]
+    need = find_images_workspace(grid, n, max_img)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+    img = torch.full((n, max_img, 2), float("nan"), dtype=torch.float64, device="cuda")
+    n_img = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ps, gs = plane.c_struct(), grid_struct(grid)
+    L.check(L.lib.lf_find_images(C.byref(ps), C.byref(gs), _prec(precision), _ptr(beta), _ptr(a_src),
+                                 n, int(max_img), int(polish_iters), _ptr(workspace),
+                                 workspace.numel(), _ptr(img), _ptr(n_img), _stream()))
+    return img, n_img
+
+
+def find_images_workspace(grid, n_src, max_img=8):
+    return int(L.lib.lf_find_images_workspace(grid.nx, grid.ny, n_src, max_img))
 
 
 def device_error():
@@ -148,23 +182,24 @@ class Plan:
                                      _prec(precision), int(flags)))
 
     def chi2(self, theta: torch.Tensor, out: Optional[torch.Tensor] = None):
-        theta = theta.contiguous()
+        theta = _dev64(theta, "theta")
         S = theta.shape[0]
-        out = torch.empty(S, dtype=torch.float64, device="cuda") if out is None else out
+        out = torch.empty(S, dtype=torch.float64, device="cuda") if out is None else _dev64(out, "out", True)
         L.check(L.lib.lf_chi2_batch(self.handle, _ptr(theta), S, _ptr(out), _stream()))
         return out
 
     def chi2_grad(self, theta: torch.Tensor, out=None, grad=None):
-        theta = theta.contiguous()
+        theta = _dev64(theta, "theta")
         S = theta.shape[0]
-        out = torch.empty(S, dtype=torch.float64, device="cuda") if out is None else out
-        grad = torch.empty(S, self.P, dtype=torch.float64, device="cuda") if grad is None else grad
+        out = torch.empty(S, dtype=torch.float64, device="cuda") if out is None else _dev64(out, "out", True)
+        grad = (torch.empty(S, self.P, dtype=torch.float64, device="cuda") if grad is None
+                else _dev64(grad, "grad", True))
         L.check(L.lib.lf_chi2_grad_batch(self.handle, _ptr(theta), S, _ptr(out), _ptr(grad), _stream()))
         return out, grad
 
     def chi2_img(self, theta: torch.Tensor, iters=8):
         """Image-plane chi^2 and rms per sample (Newton model images)."""
-        theta = theta.contiguous()
+        theta = _dev64(theta, "theta")
         S = theta.shape[0]
         out = torch.empty(S, dtype=torch.float64, device="cuda")
         rms = torch.empty(S, dtype=torch.float64, device="cuda")
@@ -176,13 +211,16 @@ class Plan:
                  lo: torch.Tensor, hi: torch.Tensor, chain=False):
         """Stretch-move steps in place on (walkers, chi2); uniforms (n_steps, S, 3) on the device.
         Returns (n_accepted, chain or None)."""
+        walkers = _dev64(walkers, "walkers", True)
+        chi2 = _dev64(chi2, "chi2", True)
+        uniforms, lo, hi = _dev64(uniforms, "uniforms"), _dev64(lo, "lo"), _dev64(hi, "hi")
         S = walkers.shape[0]
         n_steps = uniforms.shape[0]
         ch = torch.empty(n_steps, S, self.P, dtype=torch.float64, device="cuda") if chain else None
         acc = torch.zeros(1, dtype=torch.int64, device="cuda")
         L.check(L.lib.lf_aies_run(self.handle, _ptr(walkers), _ptr(chi2), S, n_steps,
-                                  _ptr(uniforms.contiguous()), float(a), _ptr(lo.contiguous()),
-                                  _ptr(hi.contiguous()), _ptr(ch), _ptr(acc), _stream()))
+                                  _ptr(uniforms), float(a), _ptr(lo), _ptr(hi), _ptr(ch), _ptr(acc),
+                                  _stream()))
         return acc, ch
 
     def info(self):

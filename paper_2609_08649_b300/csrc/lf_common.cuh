@@ -534,39 +534,41 @@ __device__ inline void digest_pad_lane(MemPair& p, int lane) {
 LF_INLINE float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 LF_INLINE float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 LF_INLINE float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-LF_INLINE float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 // The round-PJE closed form (pje_round) for the two members of a record at one position,
 // added into packed chunk sums laid out so that psi needs no per-member diagonal terms:
 //   c[0] += kbar dx, c[1] += kbar dy, c[2] += kbar, c[3] += t dx^2, c[4] += t dx dy,
 //   c[5] += t r^2;  then psi_xx = c2 + c3, psi_yy = c2 + c5 - c3, psi_xy = c4
 // (psi_ij = kbar delta_ij + t x_i x_j, so psi_yy = kbar + t (r^2 - dx^2)).
-// 33 packed FP32 instructions and 8 MUFU (4 per member).
+// 33 FP32 lane-operations and 4 MUFU per member.
 LF_INLINE void member_pair_acc(const MemPair& m, float2 pxh, float2 pxl, float2 pyh, float2 pyl,
                                float2 (&c)[6]) {
-  const float2 one = make_float2(1.f, 1.f);
   const float2 dx = add2(add2(pxh, m.nxh), add2(pxl, m.nxl));
   const float2 dy = add2(add2(pyh, m.nyh), add2(pyl, m.nyl));
   const float2 r2 = fma2(dx, dx, mul2(dy, dy));
   const float2 S2 = add2(m.s2, r2), R2 = add2(m.a2, r2);
-  const float2 iS = make_float2(rsqrtf(S2.x), rsqrtf(S2.y));
-  const float2 iR = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
-  const float2 S = mul2(S2, iS), R = mul2(R2, iR);
+  // Every consumer of a MUFU result is a scalar FP32 operation on one lane, writing its half
+  // of the pair directly (packing MUFU results first costs extra FP32-pipe cycles).
+  float2 iS, iR, S, R;
+  iS.x = rsqrtf(S2.x); iS.y = rsqrtf(S2.y);
+  iR.x = rsqrtf(R2.x); iR.y = rsqrtf(R2.y);
+  S.x = S2.x * iS.x; S.y = S2.y * iS.y;
+  R.x = R2.x * iR.x; R.y = R2.y * iR.y;
   const float2 Ss = add2(S, m.s), Ra = add2(R, m.a);
   const float2 X = mul2(Ss, Ra);
   const float2 RS = add2(R, S);
-#if LF_PAIR_ONE_RCP
-  // one reciprocal for both: Z = 1 / (X (R + S)), PQ = Z (R + S), 1 / (R + S) = Z X
-  const float2 XR = mul2(X, RS);
-  const float2 Z = make_float2(__fdividef(1.f, XR.x), __fdividef(1.f, XR.y));
-  const float2 PQ = mul2(Z, RS), iRS = mul2(Z, X);
-#else
-  const float2 PQ = make_float2(__fdividef(1.f, X.x), __fdividef(1.f, X.y));
-  const float2 iRS = make_float2(__fdividef(1.f, RS.x), __fdividef(1.f, RS.y));
-#endif
-  const float2 kb = mul2(mul2(m.bd, PQ), fma2(m.apc, iRS, one));
-  const float2 P = mul2(PQ, Ra), Q = mul2(PQ, Ss);
-  const float2 t = mul2(m.b, fma2(neg2(mul2(P, P)), iS, mul2(mul2(Q, Q), iR)));
+  float2 PQ, iRS, P, Q, bq, w;
+  PQ.x = __fdividef(1.f, X.x); PQ.y = __fdividef(1.f, X.y);
+  iRS.x = __fdividef(1.f, RS.x); iRS.y = __fdividef(1.f, RS.y);
+  P.x = PQ.x * Ra.x; P.y = PQ.y * Ra.y;
+  Q.x = PQ.x * Ss.x; Q.y = PQ.y * Ss.y;
+  bq.x = m.bd.x * PQ.x; bq.y = m.bd.y * PQ.y;
+  w.x = fmaf(m.apc.x, iRS.x, 1.f); w.y = fmaf(m.apc.y, iRS.y, 1.f);
+  const float2 kb = mul2(bq, w);
+  const float2 Q2 = mul2(Q, Q), P2 = mul2(P, P);
+  float2 tt;
+  tt.x = fmaf(-P2.x, iS.x, Q2.x * iR.x); tt.y = fmaf(-P2.y, iS.y, Q2.y * iR.y);
+  const float2 t = mul2(m.b, tt);
   c[0] = fma2(kb, dx, c[0]);
   c[1] = fma2(kb, dy, c[1]);
   c[2] = add2(c[2], kb);
@@ -727,6 +729,7 @@ LF_INLINE void lf_flag_error(unsigned int code) { atomicOr(&g_lf_err, code); }
 // LF_DEVERR_TIMEOUT in the error word and gives up.
 #define LF_DEVERR_TIMEOUT 1u
 #define LF_DEVERR_BADCOMP 2u
+#define LF_DEVERR_BADARG 4u    // an invalid per-item argument (e.g. a_dis outside (0, 1]) was skipped
 #define LF_WAIT_LIMIT (1u << 24)
 
 LF_INLINE uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }

@@ -121,6 +121,7 @@ extern "C" lf_status lf_device_error(void* stream) {
   LF_CUDA(cudaMemcpyToSymbol(g_lf_err, &zero, sizeof zero));
   if (v & LF_DEVERR_TIMEOUT) return fail(LF_ETIMEOUT, "a bounded device wait ran out");
   if (v & LF_DEVERR_BADCOMP) return fail(LF_EINVAL, "an invalid component was skipped on the device");
+  if (v & LF_DEVERR_BADARG) return fail(LF_EINVAL, "an invalid per-source argument was skipped on the device");
   return LF_OK;
 }
 

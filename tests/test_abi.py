@@ -65,3 +65,16 @@ def test_invalid_arguments_are_rejected_before_launch():
     assert st == L.LF_EINVAL
     st = L.lib.lf_trace_multiplane(C.byref(p), 9, None, None, 0, None, L.LF_MIXED, None, None, None)
     assert st == L.LF_EINVAL
+
+
+def test_python_layer_rejects_tensors_the_abi_would_misread():
+    """The C ABI reads raw double pointers on the device: float32 or host tensors must be
+    refused by the binding, not reinterpreted."""
+    import torch
+    from paper_2609_08649_b300 import api
+    with pytest.raises(TypeError):
+        api._dev64(torch.zeros(3, dtype=torch.float32), "x")
+    with pytest.raises(TypeError):
+        api._dev64(torch.zeros(3, dtype=torch.float64), "x")   # host memory
+    with pytest.raises(TypeError):
+        api._dev64([1.0, 2.0], "x")

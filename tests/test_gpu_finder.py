@@ -1,0 +1,183 @@
+"""Parity of lf_find_images (the lens-equation solver of Sec. 2.3: marching-squares zero
+contours of f = beta - theta + a alpha and their exact segment intersections, optional Newton
+polish) with the oracle's solver on the same vertex grids.
+
+Tolerances: unpolished images 1e-9 arcsec (both sides intersect the same segments; the FP64
+deflection grids differ by rounding only), polished images 1e-10 arcsec (both converge to the
+same root of the FP64 lens equation).  Counts must be equal.  The mixed and float-float tiers
+change only the deflection grid; their polished images are compared at the same 1e-10."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import images as OI
+from oracle import lensing as OL
+from oracle import model as OM
+
+pytestmark = pytest.mark.gpu
+W = pytest.importorskip("paper_2609_08649_b300.workloads")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2609_08649_b300 import api, model
+    return api, model
+
+
+def alpha_fn(pl):
+    def fn(tx, ty):
+        out = OL.plane_sum(pl, torch.as_tensor(np.asarray(tx, dtype=np.float64))[None],
+                           torch.as_tensor(np.asarray(ty, dtype=np.float64))[None])
+        return [o[0].numpy() for o in out]
+    return fn
+
+
+def oracle_grid(fn, x0, h, n):
+    xs = x0 + h * np.arange(n)
+    TX, TY = np.meshgrid(xs, xs)
+    ax, ay = fn(TX.ravel(), TY.ravel())[:2]
+    return ax.reshape(n, n), ay.reshape(n, n)
+
+
+def run_gpu(api, PM, wl, srcs, a, x0, h, n, polish, prec, max_img=8):
+    plane = PM.device_planes(wl)[0]
+    grid = W.Grid(x0, x0, h, h, n, n)
+    img, nimg = api.find_images(plane, grid, torch.tensor(srcs, device="cuda"),
+                                torch.tensor(a, device="cuda"), max_img=max_img,
+                                polish_iters=50 if polish else 0, precision=prec)
+    api.device_error()
+    return img.cpu().numpy(), nimg.cpu().numpy()
+
+
+def match(gpu_imgs, ref_imgs, tol):
+    """Every reference image has a GPU image within tol, one-to-one (counts already equal)."""
+    used = set()
+    for p in ref_imgs:
+        d = np.hypot(*(gpu_imgs - p).T)
+        k = int(np.argmin(d))
+        assert d[k] <= tol and k not in used, (p, gpu_imgs, d)
+        used.add(k)
+
+
+def galaxy():
+    wl = W.galaxy_c0()
+    srcs = W.source_candidates(21, 5, 0.12, 0.0, 0.0)
+    a = np.full(5, OM.single_plane_adis(wl, [wl.z_s])[0])
+    return wl, srcs, a
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "ff"])
+@pytest.mark.parametrize("polish", [False, True])
+def test_galaxy_images_match_oracle(lib, prec, polish):
+    api, PM = lib
+    wl, srcs, a = galaxy()
+    x0, h, n = -2.5, 0.01, 501
+    img, nimg = run_gpu(api, PM, wl, srcs, a, x0, h, n, polish, prec)
+    fn = alpha_fn(OM.build_planes(wl)[0])
+    ag = oracle_grid(fn, x0, h, n)
+    for s in range(len(srcs)):
+        ref = OI.find_images(fn, a[s], srcs[s], x0, x0, h, n, newton=polish, alpha_grid=ag)
+        assert nimg[s] == len(ref), (s, nimg[s], len(ref))
+        tol = 1e-10 if polish else (1e-9 if prec == "fp64" else 1e-7)
+        match(img[s, :nimg[s]], ref, tol)
+        if not polish and prec == "fp64":   # same key order as the oracle
+            assert np.allclose(img[s, :nimg[s]], ref, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cluster_images_match_oracle(lib, prec):
+    api, PM = lib
+    wl = W.cluster_c2()
+    srcs = W.source_candidates(22, 8, 12.0, 4.0, -3.0)
+    zs = np.array([1.5, 2.0, 3.0, 4.5, 6.0, 1.2, 2.5, 9.0])
+    a = np.array(OM.single_plane_adis(wl, zs))
+    x0, h, n = -80.0, 0.4, 401
+    img, nimg = run_gpu(api, PM, wl, srcs, a, x0, h, n, True, prec, max_img=16)
+    fn = alpha_fn(OM.build_planes(wl)[0])
+    ag = oracle_grid(fn, x0, h, n)
+    total = 0
+    for s in range(len(srcs)):
+        ref = OI.find_images(fn, a[s], srcs[s], x0, x0, h, n, newton=True, alpha_grid=ag)
+        assert nimg[s] == len(ref), (s, nimg[s], len(ref))
+        match(img[s, :nimg[s]], ref, 1e-9)
+        total += len(ref)
+    assert total > 8
+
+
+def test_cluster_catalogue_images_found_at_full_size(lib):
+    """The benchmark's field (1601^2 vertices at 0.1") and the 60 families of the 200-image
+    catalogue, whose noise-free images the oracle's solver produced on this grid: each
+    family's source is recovered from its images with the oracle's lens equation, and the GPU
+    solver must return every catalogue image of it."""
+    api, PM = lib
+    wl = W.cluster_c2()
+    cat = W.load_catalogue("cluster_200")
+    a = np.array(OM.single_plane_adis(wl, cat.fam_zs))
+    pl = OM.build_planes(wl)[0]
+    t = torch.tensor(cat.theta_true)
+    ax, ay = [o[0].numpy() for o in OL.plane_sum(pl, t[None, :, 0], t[None, :, 1])[:2]]
+    F = len(cat.fam_off) - 1
+    srcs = np.zeros((F, 2))
+    for f in range(F):
+        i0, i1 = cat.fam_off[f], cat.fam_off[f + 1]
+        b = np.stack([cat.theta_true[i0:i1, 0] - a[f] * ax[i0:i1],
+                      cat.theta_true[i0:i1, 1] - a[f] * ay[i0:i1]], 1)
+        assert np.ptp(b, axis=0).max() < 1e-9      # the images share one source
+        srcs[f] = b[0]
+    img, nimg = run_gpu(api, PM, wl, srcs, a, -80.0, 0.1, 1601, True, "mixed", max_img=32)
+    assert np.all(nimg >= np.diff(cat.fam_off)) and np.all(nimg <= 32)   # member galaxies add images
+    for f in range(F):
+        g = img[f, :nimg[f]]
+        for p in cat.theta_true[cat.fam_off[f]:cat.fam_off[f + 1]]:
+            assert np.hypot(*(g - p).T).min() < 1e-8
+    # every returned image solves the lens equation (oracle FP64 evaluation)
+    allp = np.concatenate([img[f, :nimg[f]] for f in range(F)])
+    fa = np.concatenate([np.full(nimg[f], a[f]) for f in range(F)])
+    fs = np.concatenate([np.repeat(srcs[f][None], nimg[f], 0) for f in range(F)])
+    tt = torch.tensor(allp)
+    bx, by = [o[0].numpy() for o in OL.plane_sum(pl, tt[None, :, 0], tt[None, :, 1])[:2]]
+    res = np.hypot(allp[:, 0] - fa * bx - fs[:, 0], allp[:, 1] - fa * by - fs[:, 1])
+    assert res.max() < 1e-10
+
+
+def test_edge_cases(lib):
+    api, PM = lib
+    from paper_2609_08649_b300 import _lib as L
+    wl, srcs, a = galaxy()
+    plane = PM.device_planes(wl)[0]
+    grid = W.Grid(-2.5, -2.5, 0.01, 0.01, 501, 501)
+    # a source far outside every caustic: one image far away, outside the grid -> none
+    far = torch.tensor([[50.0, 50.0]], dtype=torch.float64, device="cuda")
+    img, n = api.find_images(plane, grid, far, torch.tensor(a[:1], device="cuda"), polish_iters=10)
+    assert int(n[0]) == 0
+    # max_img smaller than the count: the true count is reported, the first ones stored
+    s4 = torch.tensor(srcs, device="cuda")
+    full, nf = api.find_images(plane, grid, s4, torch.tensor(a, device="cuda"), max_img=8)
+    one, n1 = api.find_images(plane, grid, s4, torch.tensor(a, device="cuda"), max_img=1)
+    assert torch.equal(nf, n1) and int(nf.min()) > 1
+    assert torch.equal(one[:, 0], full[:, 0])
+    # nothing to do
+    img0, n0 = api.find_images(plane, grid, torch.zeros(0, 2, dtype=torch.float64, device="cuda"),
+                               torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert n0.numel() == 0
+    # invalid host arguments: nothing launched
+    with pytest.raises(L.LFError):
+        api.find_images(plane, W.Grid(0.0, 0.0, 0.1, 0.1, 1, 5), s4, torch.tensor(a, device="cuda"))
+    with pytest.raises(L.LFError):
+        api.find_images(plane, W.Grid(0.0, 0.0, -0.1, 0.1, 5, 5), s4, torch.tensor(a, device="cuda"))
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    need = api.find_images_workspace(grid, 5, 8)
+    with pytest.raises(L.LFError):
+        ps, gs = plane.c_struct(), api.grid_struct(grid)
+        import ctypes as C
+        L.check(L.lib.lf_find_images(C.byref(ps), C.byref(gs), 0, api._ptr(s4), api._ptr(s4), 5, 8, 0,
+                                     api._ptr(ws), 16, api._ptr(full), api._ptr(nf), api._stream()))
+    assert need > 16
+    # an invalid a_dis on the device: that source gets no images and the error word is set
+    bad = torch.tensor([a[0], 0.0], dtype=torch.float64, device="cuda")
+    img, n = api.find_images(plane, grid, s4[:2], bad)
+    assert int(n[1]) == 0 and int(n[0]) == int(nf[0])
+    with pytest.raises(L.LFError):
+        api.device_error()
