@@ -16,7 +16,7 @@ from . import model as om
 def _terms(wl, theta, tobs, fam_off, fam_adis=None, fam_zs=None):
     planes = om.apply_params(wl, theta)
     if len(planes) == 1:
-        return L.single_plane_source_terms(planes[0], tobs, fam_off, fam_adis)
+        return L.single_plane_source_terms(planes[0], tobs, fam_off, om.family_adis(wl, theta, fam_adis))
     zs = [p.z for p in wl.planes]
     r, _ = cz.multiplane_ratios(zs, zs[-1] + 1.0, wl.cosmo.H0, wl.cosmo.Om)
     fam_rs = [cz.multiplane_ratios(zs, z, wl.cosmo.H0, wl.cosmo.Om)[1] for z in fam_zs]

@@ -33,15 +33,16 @@ def source_models(beta, A, sinv, fam_off):
 def chi2_img(wl, theta, tobs, sinv, fam_off, fam_adis, iters=8):
     """(chi2_img (S,), rms (S,), theta_model (S, N, 2)) for sampled parameters theta (S, P)."""
     with torch.no_grad():
-        pl = om.apply_params(wl, torch.as_tensor(theta))[0]
-        beta, A = L.single_plane_source_terms(pl, tobs, fam_off, fam_adis)
+        theta = torch.as_tensor(theta)
+        pl = om.apply_params(wl, theta)[0]
+        fa = om.family_adis(wl, theta, fam_adis)                      # (S, F)
+        beta, A = L.single_plane_source_terms(pl, tobs, fam_off, fa)
         bm = source_models(beta, A, sinv, fam_off)
         N = tobs.shape[0]
         fam = torch.empty(N, dtype=torch.long)
-        a = torch.empty(N, dtype=torch.float64)
         for f in range(len(fam_off) - 1):
             fam[int(fam_off[f]):int(fam_off[f + 1])] = f
-            a[int(fam_off[f]):int(fam_off[f + 1])] = float(fam_adis[f])
+        a = fa[:, fam]                                                # (S, N)
         target = bm[:, fam]                                   # (S, N, 2)
         th = tobs[None].expand(beta.shape[0], N, 2).clone()
         for _ in range(iters):

@@ -201,11 +201,16 @@ def chi2_src(beta, A, sinv, fam_off):
 
 def single_plane_source_terms(pl: LPlane, theta_obs, fam_off, fam_adis):
     """beta_i = theta_i - a_f alpha(theta_i), A_i = I - a_f Psi(theta_i) for every
-    observed image i of family f (Eq. lens_eq, Eq. jac)."""
+    observed image i of family f (Eq. lens_eq, Eq. jac).  fam_adis: one a_dis per family,
+    or an (S, F) tensor of per-sample values."""
     N = theta_obs.shape[0]
-    a = torch.empty(N, dtype=torch.float64)
+    fam = torch.empty(N, dtype=torch.long)
     for f in range(len(fam_off) - 1):
-        a[int(fam_off[f]):int(fam_off[f + 1])] = float(fam_adis[f])
+        fam[int(fam_off[f]):int(fam_off[f + 1])] = f
+    if torch.is_tensor(fam_adis) and fam_adis.dim() == 2:
+        a = fam_adis[:, fam]
+    else:
+        a = torch.tensor([float(v) for v in fam_adis], dtype=torch.float64)[fam]
     tx, ty = theta_obs[None, :, 0], theta_obs[None, :, 1]
     ax, ay, pxx, pyy, pxy = plane_sum(pl, tx, ty)
     bx, by = tx - a * ax, ty - a * ay

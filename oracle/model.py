@@ -116,12 +116,26 @@ def apply_params(wl, theta):
             col = getattr(pl, name).clone()
             col[:, k] = transform(spec.xform, theta[:, p], apk)
             setattr(pl, name, col)
+        elif spec.comp == -2:
+            continue   # a family's distance ratio: see family_adis
         else:
             # scaling slots live on the first plane that has members
             j = next(i for i, pp in enumerate(wl.planes) if pp.members is not None)
             apk = cz.arcsec_per_kpc(wl.planes[j].z, wl.cosmo.H0, wl.cosmo.Om)
             setattr(planes[j], SCALING[spec.field], transform(spec.xform, theta[:, p], apk))
     return planes
+
+
+def family_adis(wl, theta, base_adis):
+    """(S, F) distance ratios a_dis of the families for each sample: the fixed values
+    `base_adis`, except the families whose a_dis is itself a sampled parameter (comp = -2,
+    field = family index; sampled directly in a_dis, Sec. 3.5).  Differentiable in theta."""
+    S = theta.shape[0]
+    cols = [torch.full((S,), float(a), dtype=torch.float64) for a in base_adis]
+    for p, spec in enumerate(wl.params):
+        if spec.comp == -2:
+            cols[spec.field] = theta[:, p]
+    return torch.stack(cols, 1)
 
 
 def single_plane_adis(wl, family_zs):

@@ -292,6 +292,18 @@ def random_positions(seed: int, n: int, half: float) -> np.ndarray:
     return np.random.default_rng(seed).uniform(-half, half, (n, 2))
 
 
+F_ADIS = -2   # ParamSpec.comp of a family's sampled distance ratio (field = family index)
+
+
+def with_free_adis(wl: Workload, families, base_adis, jitter=0.01) -> Workload:
+    """A copy of `wl` whose listed families have their a_dis = D_ds/D_s sampled directly
+    (free source redshifts), jittered by `jitter` around the caller's `base_adis` (one value
+    per listed family, from the caller's cosmology)."""
+    extra = [ParamSpec(F_ADIS, int(f), XF_IDENT, float(a), float(jitter), False)
+             for f, a in zip(families, base_adis)]
+    return dataclasses.replace(wl, params=list(wl.params) + extra)
+
+
 def replace(obj, **kw):
     return dataclasses.replace(obj, **kw)
 
