@@ -381,6 +381,20 @@ def secondary(torch, api, PM, W, L, C, step, ms_mixed, evals):
         out["grad_16clusters_1024"] = res
     except FileNotFoundError as e:
         out["grad_16clusters_1024"] = {"skipped": str(e)}
+    # free source redshifts: 12 families' a_dis sampled as parameters (30 parameters in all)
+    base_a = [PM.adis(wl.cosmo, wl.planes[0].z, z) for z in cat.fam_zs]
+    fr = list(range(0, 60, 5))
+    wlf = W.with_free_adis(wl, fr, [base_a[f] for f in fr], jitter=0.005)
+    thf = torch.tensor(W.sample_thetas(wlf, wlf.seed), device="cuda")
+    res = {}
+    for prec in ("mixed", "ff"):
+        plan = api.Plan([PM.cluster_input(wlf, cat)], thf.shape[0], prec, flags=api.FLAG_GRAPH | api.FLAG_AUTOTUNE)
+        tc = _time(torch, lambda: plan.chi2(thf), reps=5)
+        tg = _time(torch, lambda: plan.chi2_grad(thf), reps=3)
+        res[prec] = {"chi2_ms": tc, "grad_ms": tg, "chi2_per_s": thf.shape[0] / (tc * 1e-3),
+                     "grad_samples_per_s": thf.shape[0] / (tg * 1e-3)}
+        plan.close()
+    out["free_adis_4096x200_P30"] = res
     # image-plane chi^2 (Newton model images) and the on-device sampler on the same cluster
     res = {}
     wl2 = W.cluster_c2()

@@ -212,9 +212,14 @@ typedef struct {
   lf_images images;
   int32_t P;                        /* parameters per sample, 1..64 */
   const int32_t* p_comp;            /* host [P]: component index counted over all planes
-                                       in order, or -1 for a scaling slot of the first
-                                       plane that has members                     */
-  const int32_t* p_field;           /* host [P]: lf_field, or lf_scaling_slot if -1 */
+                                       in order, -1 for a scaling slot of the first
+                                       plane that has members, or -2 for the a_dis =
+                                       D_ds/D_s of one family, sampled directly (free
+                                       source redshift, Sec. 3.5; single-plane
+                                       clusters, transform LF_XF_IDENT; a sampled value
+                                       outside (0, 1] gives chi^2 = +inf)          */
+  const int32_t* p_field;           /* host [P]: lf_field; lf_scaling_slot if -1; the
+                                       family index if -2                             */
   const int32_t* p_xform;           /* host [P]: lf_xform                            */
 } lf_cluster;
 

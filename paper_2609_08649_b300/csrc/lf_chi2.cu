@@ -70,6 +70,8 @@ struct ClusterDesc {
   int scal_plane;
   int scal_free;
   int scal_p[6];
+  int n_afree;                     // families whose a_dis is a sampled parameter (one plane)
+  int afree_fam[LF_MAX_P], afree_p[LF_MAX_P];
   int p_xform[LF_MAX_P];
   int p_plane[LF_MAX_P];
   int ks;
@@ -80,7 +82,7 @@ struct ClusterDesc {
   const float4* theta_ff;          // [n_img] (x_hi, x_lo, y_hi, y_lo)
   const float2* ratio_ff;          // [n_fam * np]
   const float4* sinv_f;            // [n_img] (xx, xy, yy, 0)
-  uint32_t off_img, off_imgd, off_fam, off_par, off_free, off_newton, smem;
+  uint32_t off_img, off_imgd, off_fam, off_par, off_free, off_newton, off_fama, smem;
 };
 
 // ------------------------------------------------------------------ transforms -----
@@ -285,6 +287,10 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
     float* imgf = reinterpret_cast<float*>(smem + C.off_img);       // mixed-tier records
     double* imgd = reinterpret_cast<double*>(smem + C.off_imgd);    // mixed-tier multi-plane state
     double* fam = reinterpret_cast<double*>(smem + C.off_fam);
+    // single plane: this sample's a_dis per family (fixed, or a sampled parameter)
+    double* fa = reinterpret_cast<double*>(smem + C.off_fama);
+    float2* faf = reinterpret_cast<float2*>(fa + C.n_fam);
+    int* fap = reinterpret_cast<int*>(faf + C.n_fam);
     for (int p = tid; p < C.P; p += blockDim.x) {
       th[p] = theta[(size_t)s * C.P + p];
       if (GRAD) gacc[p] = 0.0;
@@ -326,6 +332,24 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
         }
         fraw[f] = rc;
         digest_one_comp<T>(rc, *slot);
+      }
+    }
+    if (C.np == 1) {
+      // a sampled a_dis outside (0, 1] makes the family's chi^2 non-finite, i.e. +inf
+      for (int f = tid; f < C.n_fam; f += blockDim.x) {
+        int p = -1;
+        for (int q = 0; q < C.n_afree; ++q)
+          if (C.afree_fam[q] == f) p = C.afree_p[q];
+        double a = C.fam_ratio[f];
+        float2 a2 = C.ratio_ff[f];
+        if (p >= 0) {
+          a = th[p];
+          if (!(a > 0.0 && a <= 1.0)) a = NAN;
+          split_ff(a, a2.x, a2.y);
+        }
+        fa[f] = a;
+        faf[f] = a2;
+        fap[f] = p;
       }
     }
     for (int j = 0; j < C.np; ++j) {
@@ -520,7 +544,7 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
         ff bx, by;
         float a00, a01, a10, a11, det;
         if (C.np == 1) {
-          const float2 af = C.ratio_ff[f];
+          const float2 af = faf[f];
           const ff a = ff_make(af.x, af.y);
           const float4 tf = C.theta_ff[i];
           bx = ff_sub(ff_make(tf.x, tf.y), ff_mul(a, ff_make(r[0], r[1])));
@@ -604,7 +628,7 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
         const double tx = C.theta[2 * i], ty = C.theta[2 * i + 1];
         double bx, by, A00, A01, A10, A11;
         if (C.np == 1) {
-          const double a = C.fam_ratio[f];
+          const double a = fa[f];
           bx = tx - a * r[0];
           by = ty - a * r[1];
           A00 = 1.0 - a * r[2]; A11 = 1.0 - a * r[3]; A01 = A10 = -a * r[4];
@@ -696,7 +720,7 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
           } else {
             for (int c5 = 0; c5 < 5; ++c5) sm[c5] = img[i * IS + c5];
           }
-          const double a = C.fam_ratio[C.img_fam[i]];
+          const double a = fa[C.img_fam[i]];
           const double tx = nst[4 * i], ty = nst[4 * i + 1];
           const double rx = tx - a * sm[0] - nst[4 * i + 2];
           const double ry = ty - a * sm[1] - nst[4 * i + 3];
@@ -747,11 +771,26 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
           M00 = r[5]; M01 = r[6]; M11 = r[7];
           u00 = r[10]; u01 = r[11]; u10 = r[12]; u11 = r[13];
         }
-        const double a = C.fam_ratio[f];
+        const double a = fa[f];
         const double w0 = M00 * d0 + M01 * d1, w1 = M01 * d0 + M11 * d1;
         const double z0 = u00 * d0 + u01 * d1, z1 = u10 * d0 + u11 * d1;
         const double k2a = n_f > 1 ? 2.0 * a : 0.0;
         double cot[5] = {-k2a * w0, -k2a * w1, k2a * w0 * z0, k2a * w1 * z1, k2a * (w0 * z1 + w1 * z0)};
+        if (fap[f] >= 0 && n_f > 1) {
+          // a sampled a_dis: beta = theta - a alpha and A = I - a Psi give
+          // d chi^2 / d a = (1/a) sum_i (alpha_bar . alpha_i + Psi_bar : Psi_i)
+          double sm[5];
+          if constexpr (MIXED) {
+            const float* r = imgf + i * ISF;
+            for (int q = 0; q < 5; ++q) sm[q] = (double)r[2 * q] + (double)r[2 * q + 1];
+          } else {
+            const double* r = img + i * IS;
+            for (int q = 0; q < 5; ++q) sm[q] = r[q];
+          }
+          double g = 0.0;
+          for (int q = 0; q < 5; ++q) g += cot[q] * sm[q];
+          atomicAdd(&gacc[fap[f]], g / a);
+        }
         if constexpr (MIXED) {
           float* r = imgf + i * ISF;
           for (int q = 0; q < 5; ++q) r[q] = (float)cot[q];
@@ -930,6 +969,67 @@ static int choose_ks(int n_img, int K, int block, int cap) {
   return best;
 }
 
+// Parameter map of one cluster into its descriptor (C.np, C.pl[].nm and C.n_fam set):
+// p_comp >= 0 a component field, -1 a scaling-relation slot of the first plane that has
+// members, -2 the a_dis of family p_field (single-plane clusters, sampled directly).
+static lf_status parse_params(const lf_cluster& cl, const int* comp_base, ClusterDesc& C) {
+  if (cl.P < 1 || cl.P > LF_MAX_P || !cl.p_comp || !cl.p_field || !cl.p_xform)
+    return fail(LF_EINVAL, "need 1..%d parameters with a complete map", LF_MAX_P);
+  C.P = cl.P;
+  C.scal_plane = -1;
+  for (int j = 0; j < C.np; ++j)
+    if (C.pl[j].nm > 0) { C.scal_plane = j; break; }
+  for (int k = 0; k < 6; ++k) C.scal_p[k] = -1;
+  C.scal_free = 0;
+  C.n_free = 0;
+  C.n_afree = 0;
+  for (int p = 0; p < cl.P; ++p) {
+    const int gc = cl.p_comp[p], fld = cl.p_field[p], xf = cl.p_xform[p];
+    if (xf < 0 || xf > 3) return fail(LF_EINVAL, "parameter %d: unknown transform", p);
+    C.p_xform[p] = xf;
+    if (gc == -2) {
+      if (C.np != 1) return fail(LF_EUNSUPPORTED, "parameter %d: a sampled a_dis needs a single-plane cluster", p);
+      if (fld < 0 || fld >= C.n_fam) return fail(LF_EINVAL, "parameter %d: family %d out of range", p, fld);
+      if (xf != LF_XF_IDENT) return fail(LF_EINVAL, "parameter %d: a_dis is sampled directly (transform 0)", p);
+      for (int q = 0; q < C.n_afree; ++q)
+        if (C.afree_fam[q] == fld) return fail(LF_EINVAL, "a_dis of family %d targeted twice", fld);
+      C.afree_fam[C.n_afree] = fld;
+      C.afree_p[C.n_afree] = p;
+      ++C.n_afree;
+      C.p_plane[p] = 0;
+      continue;
+    }
+    if (gc == -1) {
+      if (C.scal_plane < 0) return fail(LF_EINVAL, "parameter %d targets a scaling relation but no plane has members", p);
+      if (fld < 0 || fld > 5) return fail(LF_EINVAL, "parameter %d: unknown scaling slot", p);
+      if (C.scal_p[fld] >= 0) return fail(LF_EINVAL, "scaling slot %d targeted twice", fld);
+      C.scal_p[fld] = p;
+      C.scal_free = 1;
+      C.p_plane[p] = C.scal_plane;
+      continue;
+    }
+    if (gc < 0) return fail(LF_EINVAL, "parameter %d: unknown target %d", p, gc);
+    if (fld < 0 || fld > 6) return fail(LF_EINVAL, "parameter %d: unknown field", p);
+    if (gc >= comp_base[C.np]) return fail(LF_EINVAL, "parameter %d: component %d out of range", p, gc);
+    int j = 0;
+    while (gc >= comp_base[j + 1]) ++j;
+    const int k = gc - comp_base[j];
+    C.p_plane[p] = j;
+    int f = 0;
+    while (f < C.n_free && !(C.free_plane[f] == j && C.free_comp[f] == k)) ++f;
+    if (f == C.n_free) {
+      if (C.n_free == LF_MAX_FREE) return fail(LF_EUNSUPPORTED, "more than %d sampled components", LF_MAX_FREE);
+      C.free_plane[f] = j;
+      C.free_comp[f] = k;
+      for (int q = 0; q < 7; ++q) C.free_p[f][q] = -1;
+      ++C.n_free;
+    }
+    if (C.free_p[f][fld] >= 0) return fail(LF_EINVAL, "field targeted twice");
+    C.free_p[f][fld] = p;
+  }
+  return LF_OK;
+}
+
 static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap) {
   const bool mixed = precision != LF_FP64;
   const uint32_t mem_sz = precision == LF_FF ? sizeof(MemX) : precision == LF_MIXED ? sizeof(MemT<float>)
@@ -953,6 +1053,8 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
   C.off_par = o; o += (uint32_t)C.P * 2u * 8u;
   o = (o + 15u) & ~15u; C.off_free = o; o += (uint32_t)C.n_free * 64u;
   o = (o + 15u) & ~15u; C.off_newton = o; o += (uint32_t)C.n_img * 4u * 8u;
+  // per sample: a_dis of each family (double, float-float) and the parameter setting it
+  o = (o + 15u) & ~15u; C.off_fama = o; o += (uint32_t)C.n_fam * (8u + 8u + 4u);
   C.smem = (o + 15u) & ~15u;
   int K = 0;
   for (int j = 0; j < C.np; ++j) K = std::max(K, C.pl[j].nc + C.pl[j].nm);
@@ -1113,45 +1215,7 @@ static lf_status build_cluster(lf_plan* pl, const lf_cluster& cl, ClusterDesc& C
     C.theta_ff = dtf; C.sinv_f = dsf; C.ratio_ff = drf;
   }
   // parameter map
-  C.P = cl.P;
-  if (cl.P < 1 || cl.P > LF_MAX_P || !cl.p_comp || !cl.p_field || !cl.p_xform)
-    return fail(LF_EINVAL, "need 1..%d parameters with a complete map", LF_MAX_P);
-  C.scal_plane = -1;
-  for (int j = 0; j < C.np; ++j)
-    if (C.pl[j].nm > 0) { C.scal_plane = j; break; }
-  for (int k = 0; k < 6; ++k) C.scal_p[k] = -1;
-  C.n_free = 0;
-  for (int p = 0; p < cl.P; ++p) {
-    int gc = cl.p_comp[p], fld = cl.p_field[p], xf = cl.p_xform[p];
-    if (xf < 0 || xf > 3) return fail(LF_EINVAL, "parameter %d: unknown transform", p);
-    C.p_xform[p] = xf;
-    if (gc < 0) {
-      if (C.scal_plane < 0) return fail(LF_EINVAL, "parameter %d targets a scaling relation but no plane has members", p);
-      if (fld < 0 || fld > 5) return fail(LF_EINVAL, "parameter %d: unknown scaling slot", p);
-      if (C.scal_p[fld] >= 0) return fail(LF_EINVAL, "scaling slot %d targeted twice", fld);
-      C.scal_p[fld] = p;
-      C.scal_free = 1;
-      C.p_plane[p] = C.scal_plane;
-      continue;
-    }
-    if (fld < 0 || fld > 6) return fail(LF_EINVAL, "parameter %d: unknown field", p);
-    if (gc >= comp_base[C.np]) return fail(LF_EINVAL, "parameter %d: component %d out of range", p, gc);
-    int j = 0;
-    while (gc >= comp_base[j + 1]) ++j;
-    int k = gc - comp_base[j];
-    C.p_plane[p] = j;
-    int f = 0;
-    while (f < C.n_free && !(C.free_plane[f] == j && C.free_comp[f] == k)) ++f;
-    if (f == C.n_free) {
-      if (C.n_free == LF_MAX_FREE) return fail(LF_EUNSUPPORTED, "more than %d sampled components", LF_MAX_FREE);
-      C.free_plane[f] = j;
-      C.free_comp[f] = k;
-      for (int q = 0; q < 7; ++q) C.free_p[f][q] = -1;
-      ++C.n_free;
-    }
-    if (C.free_p[f][fld] >= 0) return fail(LF_EINVAL, "field targeted twice");
-    C.free_p[f][fld] = p;
-  }
+  LF_TRY(parse_params(cl, comp_base.data(), C));
   int K = 0;
   for (int j = 0; j < C.np; ++j) K += C.pl[j].nc + C.pl[j].nm;
   cost = (double)C.n_img * K;

@@ -129,8 +129,6 @@ extern "C" lf_status lf_chi2_batch_static(const lf_cluster* cl, const double* th
       if (!(std::isfinite(v) && (np == 1 ? (v > 0.0 && v <= 1.0) : (v >= 0.0 && v <= 1.0))))
         return fail(LF_EINVAL, "family %d has an invalid distance ratio", f);
     }
-  if (cl->P < 1 || cl->P > LF_MAX_P || !cl->p_comp || !cl->p_field || !cl->p_xform)
-    return fail(LF_EINVAL, "need 1..%d parameters with a complete map", LF_MAX_P);
 
   // descriptor (host side, on the stack) -------------------------------------------
   ClusterDesc C;
@@ -155,40 +153,7 @@ extern "C" lf_status lf_chi2_batch_static(const lf_cluster* cl, const double* th
   }
   C.n_img = im.n_img;
   C.n_fam = im.n_fam;
-  C.P = cl->P;
-  C.scal_plane = -1;
-  for (int j = 0; j < np; ++j)
-    if (C.pl[j].nm > 0) { C.scal_plane = j; break; }
-  for (int k = 0; k < 6; ++k) C.scal_p[k] = -1;
-  for (int p = 0; p < cl->P; ++p) {
-    const int gc = cl->p_comp[p], fld = cl->p_field[p], xf = cl->p_xform[p];
-    if (xf < 0 || xf > 3) return fail(LF_EINVAL, "parameter %d: unknown transform", p);
-    C.p_xform[p] = xf;
-    if (gc < 0) {
-      if (C.scal_plane < 0 || fld < 0 || fld > 5 || C.scal_p[fld] >= 0)
-        return fail(LF_EINVAL, "parameter %d: invalid scaling-relation target", p);
-      C.scal_p[fld] = p;
-      C.scal_free = 1;
-      C.p_plane[p] = C.scal_plane;
-      continue;
-    }
-    if (fld < 0 || fld > 6 || gc >= comp_base[np]) return fail(LF_EINVAL, "parameter %d: invalid target", p);
-    int j = 0;
-    while (gc >= comp_base[j + 1]) ++j;
-    const int k = gc - comp_base[j];
-    C.p_plane[p] = j;
-    int f = 0;
-    while (f < C.n_free && !(C.free_plane[f] == j && C.free_comp[f] == k)) ++f;
-    if (f == C.n_free) {
-      if (C.n_free == LF_MAX_FREE) return fail(LF_EUNSUPPORTED, "more than %d sampled components", LF_MAX_FREE);
-      C.free_plane[f] = j;
-      C.free_comp[f] = k;
-      for (int q = 0; q < 7; ++q) C.free_p[f][q] = -1;
-      ++C.n_free;
-    }
-    if (C.free_p[f][fld] >= 0) return fail(LF_EINVAL, "field targeted twice");
-    C.free_p[f][fld] = p;
-  }
+  LF_TRY(parse_params(*cl, comp_base, C));
   // carve the scratch array -------------------------------------------------------------
   const size_t pre_sz = precision == LF_MIXED ? sizeof(MemPreF) : sizeof(MemPreD);
   size_t off = 0;

@@ -61,7 +61,7 @@ def chi2_mixed_bound(wl, cat, theta, sigma=None, coef=4.0):
     sig = wl.sigma_pos if sigma is None else sigma
     th = torch.as_tensor(theta)
     pl = OM.apply_params(wl, th)[0]
-    a_f = OM.single_plane_adis(wl, cat.fam_zs)
+    a_f = OM.family_adis(wl, th, OM.single_plane_adis(wl, cat.fam_zs))   # (S, F)
     off = list(cat.fam_off)
     n = len(cat.theta_obs)
     tx = torch.tensor(cat.theta_obs[:, 0])[None]
@@ -99,5 +99,5 @@ def chi2_mixed_bound(wl, cat, theta, sigma=None, coef=4.0):
         wn, zn = w.norm(dim=-1), z.norm(dim=-1)
         da = coef * U32 * sa[:, i0:i1]
         dp = coef * U32 * sp[:, i0:i1]
-        bound += (2 * a_f[f] * (wn * da + wn * zn * dp)).sum(1)
+        bound += (2 * a_f[:, f:f + 1] * (wn * da + wn * zn * dp)).sum(1)
     return bound.numpy()
