@@ -15,7 +15,7 @@ import torch
 
 from . import profiles as pr
 
-SIE, DPIE, NFW, SHEAR = 1, 2, 3, 4
+SIE, DPIE, NFW, SHEAR, MPOLE3 = 1, 2, 3, 4, 5
 C_KMS = 299792.458
 ARCSEC_PER_RAD = 180.0 / math.pi * 3600.0
 
@@ -74,6 +74,8 @@ def component(kind, dx, dy, b, eps, pa, core, cut):
         return pr.nfw_sph(dx, dy, b, core)
     if kind == SHEAR:
         return pr.shear(dx, dy, b, pa)
+    if kind == MPOLE3:
+        return pr.multipole3(dx, dy, b, pa)
     raise ValueError(f"unknown component kind {kind}")
 
 

@@ -20,7 +20,7 @@ import torch
 from . import cosmology as cz
 from .lensing import LPlane, b_from_vdisp, q_from_eps
 
-SIE, DPIE, NFW, SHEAR = 1, 2, 3, 4
+SIE, DPIE, NFW, SHEAR, MPOLE3 = 1, 2, 3, 4, 5
 XF_IDENT, XF_VDISP, XF_DEG, XF_KPC = 0, 1, 2, 3
 FIELDS = ("x", "y", "b", "eps", "pa", "core", "cut")
 SCALING = ("b_star", "core_star", "cut_star", "lam", "beta", "alpha")
@@ -60,6 +60,8 @@ def comp_fields(c, z_l, cosmo):
         if c.z_ref is not None:
             g = g / cz.a_dis(z_l, c.z_ref, H0, Om)
         return [c.x, c.y, g, 0.0, pa, 0.0, 0.0]
+    if c.kind == MPOLE3:
+        return [c.x, c.y, c.amp, 0.0, pa, 0.0, 0.0]
     raise ValueError(c.kind)
 
 

@@ -163,3 +163,31 @@ def shear(dx, dy, gamma, pa):
     g1 = gamma * torch.cos(2.0 * pa)
     g2 = gamma * torch.sin(2.0 * pa)
     return g1 * dx + g2 * dy, g2 * dx - g1 * dy, g1, -g1, g2
+
+
+def multipole3(dx, dy, amp, pa):
+    """Third-order multipole whose potential grows as theta^2 (Sec. 4.2):
+    psi = amp r^2 cos 3(phi - pa), phi the polar angle of (dx, dy).  From the polar
+    derivatives psi_rr = 2 amp cos 3D, psi_r / r + psi_phiphi / r^2 = -7 amp cos 3D and
+    d(psi_phi / r)/dr = -3 amp sin 3D (D = phi - pa), rotated to (x, y); kappa is
+    -(5/2) amp cos 3D at every radius.  At r = 0 exactly everything is set to 0."""
+    dx, dy, amp, pa = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64)
+                                                for t in (dx, dy, amp, pa)])
+    r = torch.hypot(dx, dy)
+    phi = torch.atan2(dy, dx)
+    c3, s3 = torch.cos(3.0 * (phi - pa)), torch.sin(3.0 * (phi - pa))
+    a_r = 2.0 * amp * r * c3
+    a_phi = -3.0 * amp * r * s3
+    c, s = torch.cos(phi), torch.sin(phi)
+    ax = a_r * c - a_phi * s
+    ay = a_r * s + a_phi * c
+    p_rr = 2.0 * amp * c3
+    p_tt = -7.0 * amp * c3
+    p_rt = -3.0 * amp * s3
+    pxx = p_rr * c * c - 2.0 * p_rt * s * c + p_tt * s * s
+    pyy = p_rr * s * s + 2.0 * p_rt * s * c + p_tt * c * c
+    pxy = (p_rr - p_tt) * s * c + p_rt * (c * c - s * s)
+    zero = r == 0
+    out = [ax, ay, pxx, pyy, pxy]
+    return tuple(torch.where(zero, torch.zeros_like(v), v) for v in out)
+

@@ -58,6 +58,8 @@ def comp_record(c: W.PhysComp, z_l, cosmo):
     if c.kind == W.SHEAR:
         g = c.gamma if c.z_ref is None else c.gamma / adis(cosmo, z_l, c.z_ref)
         return (c.x, c.y, g, 0.0, pa, 0.0, 0.0, c.kind)
+    if c.kind == W.MPOLE3:
+        return (c.x, c.y, c.amp, 0.0, pa, 0.0, 0.0, c.kind)
     raise ValueError(c.kind)
 
 

@@ -13,7 +13,8 @@ pseudo-Jaffe galaxies on the luminosity scaling relations of Eq. scaling) since
 the paper's own catalogues are not public inputs here.
 
 Component kinds (shared numeric codes): 1 SIE (cored isothermal ellipsoid),
-2 DPIE (pseudo-Jaffe / dPIE ellipsoid), 3 NFW (spherical), 4 SHEAR.
+2 DPIE (pseudo-Jaffe / dPIE ellipsoid), 3 NFW (spherical), 4 SHEAR, 5 MPOLE3 (third-order
+multipole with a theta^2 potential).
 """
 from __future__ import annotations
 
@@ -24,7 +25,7 @@ from typing import List, Optional
 
 import numpy as np
 
-SIE, DPIE, NFW, SHEAR = 1, 2, 3, 4
+SIE, DPIE, NFW, SHEAR, MPOLE3 = 1, 2, 3, 4, 5
 
 # Parameter-field codes of a component and transforms applied to a sampled
 # parameter before it lands in that field (shared by the param map of both sides).
@@ -56,6 +57,7 @@ class PhysComp:
     m200: Optional[float] = None
     conc: Optional[float] = None
     gamma: Optional[float] = None
+    amp: Optional[float] = None      # MPOLE3 amplitude A of psi = A theta^2 cos 3(phi - pa)
 
 
 @dataclass
@@ -194,6 +196,20 @@ def cluster_c2(n_samples: int = 4096, seed: int = 2) -> Workload:
     zs = list(rng.uniform(1.0, 6.0, len(sizes)))
     return Workload("cluster_chi2_4096x200", Cosmo(), [pl], params=params, n_samples=n_samples,
                     seed=seed, sigma_pos=0.1, family_sizes=sizes, family_zs=zs)
+
+
+def cluster_c2_mpole(n_samples: int = 4096, seed: int = 2) -> Workload:
+    """C2's model plus an m = 3 multipole at the centre (amplitude 0.004, orientation 10
+    deg), both sampled: 20 parameters (the angular-structure term of the paper's Hera
+    model)."""
+    wl = cluster_c2(n_samples, seed)
+    pl = wl.planes[0]
+    comps = list(pl.comps) + [PhysComp(MPOLE3, 0.0, 0.0, amp=0.004, pa_deg=10.0)]
+    k = len(comps) - 1
+    params = list(wl.params) + [ParamSpec(k, F_B, XF_IDENT, 0.004, 0.0005, False),
+                                ParamSpec(k, F_PA, XF_DEG, 10.0, 5.0, False)]
+    return dataclasses.replace(wl, name="cluster_mpole_4096x200",
+                               planes=[dataclasses.replace(pl, comps=comps)], params=params)
 
 
 def multiplane_c3(n_grid: int = 2048, n_samples: int = 1024, seed: int = 4) -> Workload:

@@ -192,3 +192,58 @@ def test_shear_is_linear_and_traceless():
     ox = pr.shear(T(x), T(y), g, pa)
     assert abs(float(ox[0]) - dpsi_dx) < 1e-8
     assert abs(psi(phi) - 0.5 * g * r * r * math.cos(2 * (phi - pa))) == 0
+
+
+# ---------------------------------------------------------------- m = 3 multipole ----
+def _mp_potential(x, y, amp, pa):
+    """The definition, psi = amp r^2 cos 3(phi - pa)."""
+    return amp * (x * x + y * y) * np.cos(3.0 * (np.arctan2(y, x) - pa))
+
+
+def test_multipole3_alpha_is_the_gradient_of_its_potential():
+    rng = np.random.default_rng(5)
+    x, y = rng.uniform(-40, 40, 50), rng.uniform(-40, 40, 50)
+    amp, pa = 0.004, 0.3
+    ax, ay, *_ = pr.multipole3(torch.tensor(x), torch.tensor(y), amp, pa)
+    h = 1e-4
+    fx = (_mp_potential(x + h, y, amp, pa) - _mp_potential(x - h, y, amp, pa)) / (2 * h)
+    fy = (_mp_potential(x, y + h, amp, pa) - _mp_potential(x, y - h, amp, pa)) / (2 * h)
+    assert np.allclose(ax.numpy(), fx, rtol=1e-7, atol=1e-9)
+    assert np.allclose(ay.numpy(), fy, rtol=1e-7, atol=1e-9)
+
+
+def test_multipole3_hessian_and_convergence():
+    rng = np.random.default_rng(6)
+    x, y = torch.tensor(rng.uniform(-40, 40, 50)), torch.tensor(rng.uniform(-40, 40, 50))
+    amp, pa = 0.004, -0.7
+    ax, ay, pxx, pyy, pxy = pr.multipole3(x, y, amp, pa)
+    h = 1e-5
+    axp, ayp, *_ = pr.multipole3(x + h, y, amp, pa)
+    axm, aym, *_ = pr.multipole3(x - h, y, amp, pa)
+    bxp, byp, *_ = pr.multipole3(x, y + h, amp, pa)
+    bxm, bym, *_ = pr.multipole3(x, y - h, amp, pa)
+    assert torch.allclose(pxx, (axp - axm) / (2 * h), rtol=1e-6, atol=1e-9)
+    assert torch.allclose(pyy, (byp - bym) / (2 * h), rtol=1e-6, atol=1e-9)
+    assert torch.allclose(pxy, (ayp - aym) / (2 * h), rtol=1e-6, atol=1e-9)
+    assert torch.allclose(pxy, (bxp - bxm) / (2 * h), rtol=1e-6, atol=1e-9)   # curl-free
+    # Laplacian of amp r^2 cos 3D: (n^2 - m^2) amp cos 3D with n = 2, m = 3
+    kappa = 0.5 * (pxx + pyy)
+    ref = -2.5 * amp * torch.cos(3.0 * (torch.atan2(y, x) - pa))
+    assert torch.allclose(kappa, ref, rtol=1e-12, atol=1e-15)
+
+
+def test_multipole3_threefold_symmetry_and_orientation():
+    x = torch.tensor([3.0, -7.0, 12.5], dtype=torch.float64)
+    y = torch.tensor([4.0, 1.0, -9.0], dtype=torch.float64)
+    amp, pa = 0.01, 0.2
+    t = 2.0 * math.pi / 3.0
+    xr, yr = math.cos(t) * x - math.sin(t) * y, math.sin(t) * x + math.cos(t) * y
+    a0 = pr.multipole3(x, y, amp, pa)
+    a1 = pr.multipole3(xr, yr, amp, pa)
+    assert torch.allclose(a1[0], math.cos(t) * a0[0] - math.sin(t) * a0[1], atol=1e-13)
+    assert torch.allclose(a1[1], math.sin(t) * a0[0] + math.cos(t) * a0[1], atol=1e-13)
+    # along the orientation axis the deflection is radial and outward, 2 amp r
+    ax, ay, *_ = pr.multipole3(torch.tensor([5.0 * math.cos(pa)], dtype=torch.float64),
+                               torch.tensor([5.0 * math.sin(pa)], dtype=torch.float64), amp, pa)
+    ref = torch.tensor([10 * amp * math.cos(pa), 10 * amp * math.sin(pa)], dtype=torch.float64)
+    assert torch.allclose(torch.stack([ax, ay]).flatten(), ref, atol=1e-14)
