@@ -55,7 +55,9 @@ typedef enum {
   LF_SIE = 1,    /* cored isothermal ellipsoid: b, eps, pa, core (= s)                 */
   LF_DPIE = 2,   /* dPIE / pseudo-Jaffe ellipsoid: b, eps, pa, core, cut; eps = 0 is round */
   LF_NFW = 3,    /* spherical NFW: b = kappa_s, core = theta_s (scale radius, arcsec)  */
-  LF_SHEAR = 4   /* external shear: b = gamma, pa = shear angle; x, y = reference point */
+  LF_SHEAR = 4,  /* external shear: b = gamma, pa = shear angle; x, y = reference point */
+  LF_MULTIPOLE3 = 5  /* third-order multipole with a theta^2 potential (Sec. 4.2):
+                        psi = b r^2 cos 3(phi - pa) about (x, y); eps, core, cut unused */
 } lf_kind;
 
 /* LF_FP64: every operation in FP64, one thread per position (the plain comparator).

@@ -156,6 +156,11 @@ __device__ void comp_dual(const lf_comp& rc, double px, double py, Out5<Dual<T, 
   dx.d[0] = (T)-1;
   dy.d[1] = (T)-1;
   DT pa = DT::var((T)rc.pa, 3);
+  if (rc.kind == LF_MULTIPOLE3) {
+    DT three = DT::cst((T)3);
+    multipole3(dx, dy, lf_cos(three * pa), lf_sin(three * pa), o);
+    return;
+  }
   if (rc.kind == LF_SHEAR) {
     DT two = DT::cst((T)2);
     DT c2 = lf_cos(two * pa), s2 = lf_sin(two * pa);
@@ -822,7 +827,7 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
           const int kc = C.free_comp[f];
           if (C.free_plane[f] != 0 || kc < k0 || kc >= k1) continue;
           const lf_comp& rc = fraw[f];
-          if (rc.kind < 1 || rc.kind > 4) continue;
+          if (rc.kind < 1 || rc.kind > 5) continue;
           Out5<Dual<T, 6>> o;
           comp_dual<T>(rc, px, py, o);
           const T b = (T)rc.b;
@@ -938,7 +943,7 @@ static lf_status plan_upload(lf_plan* pl, const X* host, size_t n, X** dev) {
 }
 
 static bool comp_ok(const lf_comp& r) {
-  bool ok = r.kind >= 1 && r.kind <= 4 && std::isfinite(r.x) && std::isfinite(r.y) &&
+  bool ok = r.kind >= 1 && r.kind <= 5 && std::isfinite(r.x) && std::isfinite(r.y) &&
             std::isfinite(r.b) && std::isfinite(r.pa);
   if (r.kind == LF_SIE || r.kind == LF_DPIE)
     ok = ok && r.eps >= 0.0 && r.eps < 1.0 && r.core >= 0.0 && std::isfinite(r.core);

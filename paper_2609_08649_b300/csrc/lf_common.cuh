@@ -353,14 +353,14 @@ LF_INLINE void nfw_sph(T dx, T dy, T ks, T irs, Out5<T>& o) {
 
 // ------------------------------------------------------------ digested tables ------
 // Component kinds as stored in the digested tables.
-enum { K_SIE = 1, K_DPIE = 2, K_NFW = 3, K_SHEAR = 4 };
+enum { K_SIE = 1, K_DPIE = 2, K_NFW = 3, K_SHEAR = 4, K_MPOLE3 = 5 };
 
 // An explicit component prepared for evaluation in precision T.  Centre as
 // float-float for T = float (offsets are taken in two FP32 subtractions), double else.
 template <class T> struct CompT {
   int kind, round;
   T xh, xl, yh, yl;     // centre (xl = yl = 0 for double)
-  T c, sn;              // cos / sin of the position angle (shear: cos 2pa, sin 2pa)
+  T c, sn;              // cos / sin of the position angle (shear: 2 pa, multipole: 3 pa)
   T b;                  // strength (NFW: kappa_s, shear: gamma)
   T q, q2, e, qe;
   T s1, s1sq, q2s1, D01;  // core terms
@@ -397,7 +397,7 @@ __host__ __device__ inline void digest_comp(int kind, double x, double y, double
   double q = (1.0 - eps) / (1.0 + eps);
   double e = sqrt((1.0 - q) * (1.0 + q));
   double cc, ss;
-  sincos(kind == K_SHEAR ? 2.0 * pa : pa, &ss, &cc);
+  sincos(kind == K_SHEAR ? 2.0 * pa : kind == K_MPOLE3 ? 3.0 * pa : pa, &ss, &cc);
   c.c = (T)cc;
   c.sn = (T)ss;
   c.b = (T)b;
@@ -437,9 +437,47 @@ __host__ __device__ inline void digest_member(double x, double y, double b, doub
 LF_INLINE float offset_of(float ph, float pl, float ch, float cl) { return (ph - ch) + (pl - cl); }
 LF_INLINE double offset_of(double ph, double pl, double ch, double cl) { return ph - ch; }
 
+// Third-order multipole psi = r^2 cos 3(phi - phi_3) (unit amplitude; c3, s3 = cos, sin of
+// 3 phi_3).  With the unit vector n = (dx, dy) / r and G = cos 3(phi - phi_3)
+// = c3 (nx^3 - 3 nx ny^2) + s3 (3 nx^2 ny - ny^3):
+//   alpha = r (3 (c3 (nx^2 - ny^2) + 2 s3 nx ny) - G nx, 3 (s3 (nx^2 - ny^2) - 2 c3 nx ny) - G ny),
+//   and psi_ij, homogeneous of degree 0, a function of n alone:
+//   psi_xx =  6 (c3 nx + s3 ny) - 2 nx Hx - G + 3 G nx^2,
+//   psi_yy = -6 (c3 nx + s3 ny) - 2 ny Hy - G + 3 G ny^2,
+//   psi_xy =  6 (s3 nx - c3 ny) - ny Hx - nx Hy + 3 G nx ny,
+// with (Hx, Hy) = 3 (c3 (nx^2 - ny^2) + 2 s3 nx ny, s3 (nx^2 - ny^2) - 2 c3 nx ny); this is
+// the Cartesian derivative chain of the cubic harmonic F = r^3 G, free of overflow at small
+// r.  Zero at r = 0 exactly.  Also evaluated on dual numbers for the adjoint.
+template <class T>
+LF_INLINE void multipole3(T dx, T dy, T c3, T s3, Out5<T>& o) {
+  const T r2 = dx * dx + dy * dy;
+  if (!(r2 > (T)0)) {
+    o.ax = (T)0; o.ay = (T)0; o.pxx = (T)0; o.pyy = (T)0; o.pxy = (T)0;
+    return;
+  }
+  const T ir = lf_rsqrt(r2);
+  const T r = r2 * ir, nx = dx * ir, ny = dy * ir;
+  const T xx = nx * nx, yy = ny * ny, xy = nx * ny, d = xx - yy;
+  const T G = c3 * nx * (xx - (T)3 * yy) + s3 * ny * ((T)3 * xx - yy);
+  const T Hx = (T)3 * (c3 * d + (T)2 * s3 * xy);
+  const T Hy = (T)3 * (s3 * d - (T)2 * c3 * xy);
+  const T L = (T)6 * (c3 * nx + s3 * ny);
+  o.ax = r * (Hx - G * nx);
+  o.ay = r * (Hy - G * ny);
+  o.pxx = L - (T)2 * nx * Hx - G + (T)3 * G * xx;
+  o.pyy = -L - (T)2 * ny * Hy - G + (T)3 * G * yy;
+  o.pxy = (T)6 * (s3 * nx - c3 * ny) - ny * Hx - nx * Hy + (T)3 * G * xy;
+}
+
 // alpha and psi_ij of one explicit component at offset (dx, dy).
 template <class T>
 LF_INLINE void eval_comp(const CompT<T>& c, T dx, T dy, Out5<T>& o) {
+  if (c.kind == K_MPOLE3) {
+    multipole3(dx, dy, c.c, c.sn, o);
+    o.ax = c.b * o.ax; o.ay = c.b * o.ay; o.pxx = c.b * o.pxx; o.pyy = c.b * o.pyy;
+    o.pxy = c.b * o.pxy;
+    return;
+  }
   if (c.kind == K_SHEAR) {
     T g1 = c.b * c.c, g2 = c.b * c.sn;
     o.ax = g1 * dx + g2 * dy;
@@ -620,6 +658,26 @@ LF_INLINE void sie_alpha_ff(const ff& u, const ff& v, const ff& uu, const ff& vv
 LF_NOINLINE void eval_comp_mixed(const CompT<float>& c, float ph_x, float pl_x, float ph_y,
                                float pl_y, const float2* tab, ff& ax, ff& ay, Out5<float>& o) {
   const bool ell = (c.kind == K_SIE || c.kind == K_DPIE) && !c.round;
+  if (c.kind == K_MPOLE3) {
+    // psi_ij in FP32; alpha = b r (Hx - G nx, Hy - G ny) in float-float (see multipole3)
+    ff dx = offset_ff(ph_x, pl_x, c.xh, c.xl);
+    ff dy = offset_ff(ph_y, pl_y, c.yh, c.yl);
+    eval_comp(c, dx.hi, dy.hi, o);
+    const ff r2 = ff_add(ff_sqr(dx), ff_sqr(dy));
+    if (!(r2.hi > 0.f)) { ax = ff_zero(); ay = ff_zero(); return; }
+    const ff cc = ff_make(c.c, c.lc), sn = ff_make(c.sn, c.lsn), b = ff_make(c.b, c.lb);
+    const ff r = ff_sqrt(r2);
+    const ff nx = ff_div(dx, r), ny = ff_div(dy, r);
+    const ff xx = ff_sqr(nx), yy = ff_sqr(ny), xy = ff_mul(nx, ny), d = ff_sub(xx, yy);
+    const ff G = ff_add(ff_mul(cc, ff_mul(nx, ff_sub(xx, ff_mul_f(yy, 3.f)))),
+                        ff_mul(sn, ff_mul(ny, ff_sub(ff_mul_f(xx, 3.f), yy))));
+    const ff Hx = ff_mul_f(ff_add(ff_mul(cc, d), ff_mul_f(ff_mul(sn, xy), 2.f)), 3.f);
+    const ff Hy = ff_mul_f(ff_sub(ff_mul(sn, d), ff_mul_f(ff_mul(cc, xy), 2.f)), 3.f);
+    const ff br = ff_mul(b, r);
+    ax = ff_mul(br, ff_sub(Hx, ff_mul(G, nx)));
+    ay = ff_mul(br, ff_sub(Hy, ff_mul(G, ny)));
+    return;
+  }
   if (!ell && c.kind != K_SHEAR) {
     float dx = offset_of(ph_x, pl_x, c.xh, c.xl);
     float dy = offset_of(ph_y, pl_y, c.yh, c.yl);

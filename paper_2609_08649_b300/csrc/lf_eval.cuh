@@ -42,7 +42,7 @@ __host__ __device__ inline PlaneLayout plane_layout(int nc, int nm, uint32_t bas
 // Validates and digests one raw component (device side; invalid -> kind 0 + error bit).
 template <class T>
 __device__ inline void digest_one_comp(const lf_comp& r, CompT<T>& out) {
-  bool ok = r.kind >= 1 && r.kind <= 4 && isfinite(r.x) && isfinite(r.y) && isfinite(r.b) &&
+  bool ok = r.kind >= 1 && r.kind <= 5 && isfinite(r.x) && isfinite(r.y) && isfinite(r.b) &&
             isfinite(r.pa);
   if (r.kind == LF_SIE || r.kind == LF_DPIE)
     ok = ok && r.eps >= 0.0 && r.eps < 1.0 && r.core >= 0.0 && isfinite(r.core);
