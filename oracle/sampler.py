@@ -1,4 +1,5 @@
-"""Affine-invariant ensemble sampler, stretch move (oracle).  TEST INFRASTRUCTURE ONLY.
+"""Posterior samplers of Sec. 3.5 (oracle): the affine-invariant ensemble sampler's stretch
+move and random-walk Metropolis-Hastings.  TEST INFRASTRUCTURE ONLY.
 
 The paper samples the posterior with the AIES of Goodman & Weare (2010) (Sec. 3.5), with
 likelihood L ~ exp(-chi^2/2) (Sec. 3) and uniform priors.  One step updates the two halves
@@ -57,3 +58,32 @@ def run(x, chi2, uniforms, a, lo, hi, chi2_fn):
         n_acc += half_step(x, chi2, 0, uniforms[step, :h], a, lo, hi, chi2_fn).sum()
         n_acc += half_step(x, chi2, 1, uniforms[step, h:], a, lo, hi, chi2_fn).sum()
     return n_acc
+
+
+def mh_step(x, chi2, z, u, step, lo, hi, chi2_fn):
+    """One Metropolis-Hastings step of S independent chains with the symmetric Gaussian
+    random-walk proposal y_k = x_k + step * z_k (z: (S, P) standard normals, step: (P,)):
+    y_k is accepted when it lies in the prior box, chi^2(y_k) is finite and
+    log u_k < -(chi^2(y_k) - chi^2(x_k)) / 2 (u: (S,) uniforms); a symmetric proposal has no
+    Hastings factor.  Updates x, chi2 in place; returns the accept flags."""
+    props = x + step[None, :] * z
+    inside = np.all((props >= lo) & (props <= hi), axis=1)
+    c_new = chi2_fn(props)
+    acc = np.zeros(x.shape[0], dtype=bool)
+    for k in range(x.shape[0]):
+        if not inside[k] or not np.isfinite(c_new[k]):
+            continue
+        if math.log(u[k]) < -0.5 * (c_new[k] - chi2[k]):
+            x[k] = props[k]
+            chi2[k] = c_new[k]
+            acc[k] = True
+    return acc
+
+
+def mh_run(x, chi2, normals, uniforms, step, lo, hi, chi2_fn):
+    """normals: (n_steps, S, P); uniforms: (n_steps, S).  Returns the number accepted."""
+    n_acc = 0
+    for t in range(normals.shape[0]):
+        n_acc += mh_step(x, chi2, normals[t], uniforms[t], step, lo, hi, chi2_fn).sum()
+    return n_acc
+

@@ -85,3 +85,60 @@ def test_prior_box_rejects():
     assert list(acc) == list(inside)
     for n in range(2):
         assert np.array_equal(x[n], props[n] if inside[n] else x0[n])
+
+
+# ------------------------------------------------------------ Metropolis-Hastings ----
+def test_mh_acceptance_rate_on_a_standard_normal():
+    """For a N(0, 1) target and a N(0, s^2) random-walk proposal, the stationary acceptance
+    probability is (2 / pi) arctan(2 / s)."""
+    rng = np.random.default_rng(3)
+    f = _gauss_chi2(np.zeros(1), np.eye(1))
+    S, steps = 2000, 60
+    x = rng.normal(0, 1, (S, 1))         # start in the stationary distribution
+    c = f(x)
+    lo, hi = np.full(1, -1e9), np.full(1, 1e9)
+    for s in (0.5, 2.0, 6.0):
+        acc = smp.mh_run(x, c, rng.normal(0, 1, (steps, S, 1)), rng.uniform(0, 1, (steps, S)),
+                         np.array([s]), lo, hi, f)
+        rate = acc / (steps * S)
+        ref = 2 / math.pi * math.atan(2 / s)
+        assert abs(rate - ref) < 0.01, (s, rate, ref)
+
+
+def test_mh_stationary_distribution_is_the_target():
+    rng = np.random.default_rng(4)
+    mu = np.array([1.0, -2.0])
+    C = np.array([[1.0, 0.5], [0.5, 2.0]])
+    f = _gauss_chi2(mu, np.linalg.inv(C))
+    S = 400
+    x = mu + rng.normal(0, 0.1, (S, 2))
+    c = f(x)
+    lo, hi = np.full(2, -1e9), np.full(2, 1e9)
+    smp.mh_run(x, c, rng.normal(0, 1, (300, S, 2)), rng.uniform(0, 1, (300, S)), np.array([1.2, 1.6]),
+               lo, hi, f)
+    samples = []
+    for _ in range(30):
+        smp.mh_run(x, c, rng.normal(0, 1, (10, S, 2)), rng.uniform(0, 1, (10, S)), np.array([1.2, 1.6]),
+                   lo, hi, f)
+        samples.append(x.copy())
+    s = np.concatenate(samples)
+    assert np.allclose(s.mean(0), mu, atol=0.08)
+    assert np.allclose(np.cov(s.T), C, atol=0.15)
+
+
+def test_mh_prior_box_and_acceptance_rule():
+    f = _gauss_chi2(np.zeros(2), np.eye(2))
+    x = np.array([[0.0, 0.0], [0.9, 0.0], [0.0, 0.0]])
+    c = f(x)
+    z = np.array([[0.5, 0.0], [1.0, 0.0], [0.0, 2.0]])
+    u = np.array([1e-300, 1e-300, 0.999])
+    lo, hi = np.full(2, -1.0), np.full(2, 1.5)
+    acc = smp.mh_step(x, c, z, u, np.array([1.0, 1.0]), lo, hi, f)
+    # chain 0: y = (0.5, 0) inside, accepted; chains 1 and 2: y = (1.9, 0) and (0, 2) leave
+    # the box (hi = 1.5), rejected whatever u
+    assert list(acc) == [True, False, False]
+    x2 = np.array([[0.0, 0.0]]); c2 = f(x2)
+    u_acc = math.exp(-0.5 * 0.25) * 0.999          # just below exp(-d chi^2 / 2) for y = (0.5, 0)
+    u_rej = math.exp(-0.5 * 0.25) * 1.001
+    assert smp.mh_step(x2.copy(), c2.copy(), np.array([[0.5, 0.0]]), np.array([u_acc]), np.ones(2), lo, hi, f)[0]
+    assert not smp.mh_step(x2.copy(), c2.copy(), np.array([[0.5, 0.0]]), np.array([u_rej]), np.ones(2), lo, hi, f)[0]
