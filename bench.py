@@ -428,6 +428,26 @@ def secondary(torch, api, PM, W, L, C, step, ms_mixed, evals):
                      "chi2_per_s": x.shape[0] * 1e3 / ms, "acceptance": int(acc) / (steps * x.shape[0])}
         plan.close()
     out["aies_4096_walkers"] = res
+    res = {}
+    zn, un = W.mh_randoms(5, steps, th2.shape[0], th2.shape[1])
+    zn, un = torch.tensor(zn, device="cuda"), torch.tensor(un, device="cuda")
+    st = torch.tensor(0.3 * sd, device="cuda")
+    for prec in ("mixed", "ff"):
+        plan = api.Plan([PM.cluster_input(wl2, cat)], th2.shape[0], prec, flags=api.FLAG_AUTOTUNE)
+        x = th2.clone()
+        c = plan.chi2(x)
+        plan.mh_run(x, c, zn[:1], un[:1], st, lo, hi)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        acc, _ = plan.mh_run(x, c, zn, un, st, lo, hi)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[prec] = {"chains": int(x.shape[0]), "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+                     "chi2_per_s": x.shape[0] * 1e3 / ms, "acceptance": int(acc) / (steps * x.shape[0])}
+        plan.close()
+    out["mh_4096_chains"] = res
     # lens-equation solver: 60 seeded sources (z_s of the catalogue's families) on a 1601^2
     # vertex grid over the 160" field, Newton polish in FP64
     srcs = torch.tensor(W.source_candidates(23, 60, 12.0, 4.0, -3.0), device="cuda")

@@ -275,6 +275,20 @@ lf_status lf_aies_run(lf_plan* plan, double* walkers, double* chi2, int32_t S, i
                       const double* uniforms, double a, const double* lo, const double* hi,
                       double* chain, unsigned long long* n_accept, void* stream);
 
+/* Random-walk Metropolis-Hastings (the paper's other sampler, Sec. 3.5) on a single-cluster
+ * plan: S independent chains, likelihood exp(-chi^2/2), uniform priors on [lo, hi].  Each of
+ * n_steps steps proposes y_k = x_k + step (.) z_k for every chain (z: standard normals) and
+ * accepts if y_k is in the box, chi^2(y_k) is finite and log u_k < -(chi^2(y_k) - chi^2(x_k))/2
+ * (FP64).  chains: device [S * P] in/out; chi2: device [S] in/out (chi^2 of the chains on
+ * entry); normals: device [n_steps * S * P]; uniforms: device [n_steps * S] in (0, 1);
+ * step, lo, hi: device [P]; trace: device [n_steps * S * P] (the chains after each step) or
+ * NULL; n_accept: device counter added to, or NULL.  1 <= S <= max_samples.  The first call
+ * allocates the sampler's workspace inside the plan. */
+lf_status lf_mh_run(lf_plan* plan, double* chains, double* chi2, int32_t S, int32_t n_steps,
+                    const double* normals, const double* uniforms, const double* step,
+                    const double* lo, const double* hi, double* trace,
+                    unsigned long long* n_accept, void* stream);
+
 lf_status lf_plan_destroy(lf_plan* plan);
 
 /* lf_chi2_batch for one cluster with no device allocation (the paper has no counterpart;

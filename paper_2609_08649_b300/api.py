@@ -223,6 +223,23 @@ class Plan:
                                   _stream()))
         return acc, ch
 
+    def mh_run(self, chains: torch.Tensor, chi2: torch.Tensor, normals: torch.Tensor,
+               uniforms: torch.Tensor, step: torch.Tensor, lo: torch.Tensor, hi: torch.Tensor,
+               trace=False):
+        """Random-walk Metropolis-Hastings steps in place on (chains, chi2); normals
+        (n_steps, S, P), uniforms (n_steps, S) on the device.  Returns (n_accepted, trace)."""
+        chains = _dev64(chains, "chains", True)
+        chi2 = _dev64(chi2, "chi2", True)
+        normals, uniforms = _dev64(normals, "normals"), _dev64(uniforms, "uniforms")
+        step, lo, hi = _dev64(step, "step"), _dev64(lo, "lo"), _dev64(hi, "hi")
+        S, n_steps = chains.shape[0], normals.shape[0]
+        tr = torch.empty(n_steps, S, self.P, dtype=torch.float64, device="cuda") if trace else None
+        acc = torch.zeros(1, dtype=torch.int64, device="cuda")
+        L.check(L.lib.lf_mh_run(self.handle, _ptr(chains), _ptr(chi2), S, n_steps, _ptr(normals),
+                                _ptr(uniforms), _ptr(step), _ptr(lo), _ptr(hi), _ptr(tr), _ptr(acc),
+                                _stream()))
+        return acc, tr
+
     def info(self):
         ks, blk, g = C.c_int32(), C.c_int32(), C.c_int32()
         L.check(L.lib.lf_plan_info(self.handle, C.byref(ks), C.byref(blk), C.byref(g)))

@@ -1,5 +1,6 @@
-// On-device affine-invariant ensemble sampler (Goodman & Weare 2010, the paper's posterior
-// sampler, Sec. 3.5) driving the batched chi^2 of a plan.  Likelihood exp(-chi^2/2), uniform
+// On-device posterior samplers of Sec. 3.5 driving the batched chi^2 of a plan: the
+// affine-invariant ensemble sampler (Goodman & Weare 2010) and random-walk Metropolis-Hastings.
+// AIES:  Likelihood exp(-chi^2/2), uniform
 // priors on a box.  One step updates the two halves of the ensemble in turn: walker k of one
 // half takes a partner j from the other half and z from g(z) ~ 1/sqrt(z) on [1/a, a],
 // proposes y = x_j + z (x_k - x_j), and accepts with probability
@@ -57,9 +58,71 @@ __global__ void k_aies_accept(double* __restrict__ x, double* __restrict__ chi2,
   }
 }
 
+// Random-walk Metropolis-Hastings (the paper's other sampler, Sec. 3.5): S independent
+// chains, proposal y_k = x_k + step * z_k with caller-supplied standard normals z.
+__global__ void k_mh_propose(const double* __restrict__ x, int S, int P, const double* __restrict__ z,
+                             const double* __restrict__ step, const double* __restrict__ lo,
+                             const double* __restrict__ hi, double* __restrict__ prop,
+                             int* __restrict__ inside) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= S) return;
+  int in = 1;
+  for (int p = 0; p < P; ++p) {
+    const double y = x[(size_t)k * P + p] + step[p] * z[(size_t)k * P + p];
+    prop[(size_t)k * P + p] = y;
+    in &= (y >= lo[p]) && (y <= hi[p]);
+  }
+  inside[k] = in;
+}
+
+// Accepts y_k when it is in the box, chi^2(y_k) is finite and log u_k < -(chi^2(y) - chi^2(x))/2
+// (a symmetric proposal has no Hastings factor).
+__global__ void k_mh_accept(double* __restrict__ x, double* __restrict__ chi2, int S, int P,
+                            const double* __restrict__ u, const double* __restrict__ prop,
+                            const int* __restrict__ inside, const double* __restrict__ chi2_new,
+                            unsigned long long* n_accept) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= S) return;
+  const double cn = chi2_new[k];
+  if (inside[k] && isfinite(cn) && log(u[k]) < -0.5 * (cn - chi2[k])) {
+    for (int p = 0; p < P; ++p) x[(size_t)k * P + p] = prop[(size_t)k * P + p];
+    chi2[k] = cn;
+    if (n_accept) atomicAdd(n_accept, 1ull);
+  }
+}
+
 }  // namespace lf
 
 using namespace lf;
+
+extern "C" lf_status lf_mh_run(lf_plan* plan, double* chains, double* chi2, int32_t S,
+                               int32_t n_steps, const double* normals, const double* uniforms,
+                               const double* step, const double* lo, const double* hi, double* trace,
+                               unsigned long long* n_accept, void* stream) {
+  if (!plan) return fail(LF_EINVAL, "plan is NULL");
+  if (!chains || !chi2 || !normals || !uniforms || !step || !lo || !hi)
+    return fail(LF_EINVAL, "NULL argument");
+  if (plan->n_clusters != 1) return fail(LF_EUNSUPPORTED, "the sampler runs on single-cluster plans");
+  if (S < 1 || S > plan->max_samples) return fail(LF_EINVAL, "need 1 <= S <= the plan's max_samples");
+  if (n_steps < 0) return fail(LF_EINVAL, "n_steps must be >= 0");
+  LF_TRY(ensure_sampler_workspace(plan));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int P = plan->P;
+  const int blk = 128, grd = (S + blk - 1) / blk;
+  for (int t = 0; t < n_steps; ++t) {
+    k_mh_propose<<<grd, blk, 0, st>>>(chains, S, P, normals + (size_t)t * S * P, step, lo, hi,
+                                      plan->d_prop, plan->d_inside);
+    LF_CUDA(cudaGetLastError());
+    LF_TRY(launch_chi2(plan, plan->d_prop, S, plan->d_chi2_prop, nullptr, st));
+    k_mh_accept<<<grd, blk, 0, st>>>(chains, chi2, S, P, uniforms + (size_t)t * S, plan->d_prop,
+                                     plan->d_inside, plan->d_chi2_prop, n_accept);
+    LF_CUDA(cudaGetLastError());
+    if (trace)
+      LF_CUDA(cudaMemcpyAsync(trace + (size_t)t * S * P, chains, (size_t)S * P * sizeof(double),
+                              cudaMemcpyDeviceToDevice, st));
+  }
+  return LF_OK;
+}
 
 extern "C" lf_status lf_aies_run(lf_plan* plan, double* walkers, double* chi2, int32_t S,
                                  int32_t n_steps, const double* uniforms, double a,

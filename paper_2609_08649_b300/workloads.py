@@ -303,6 +303,13 @@ def sampler_uniforms(seed: int, n_steps: int, n_walkers: int) -> np.ndarray:
     return np.random.default_rng(seed).uniform(0.0, 1.0, (n_steps, n_walkers, 3))
 
 
+def mh_randoms(seed: int, n_steps: int, n_chains: int, P: int):
+    """(normals (n_steps, n_chains, P), uniforms (n_steps, n_chains)) for the random-walk
+    Metropolis-Hastings chains."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((n_steps, n_chains, P)), rng.uniform(0.0, 1.0, (n_steps, n_chains))
+
+
 def random_positions(seed: int, n: int, half: float) -> np.ndarray:
     """(n, 2) positions uniform in a square of half-width `half` (sampled-pixel checks)."""
     return np.random.default_rng(seed).uniform(-half, half, (n, 2))

@@ -82,3 +82,55 @@ def test_sampler_validation(setup):
     with pytest.raises(L.LFError):        # odd number of walkers
         plan.aies_run(x, c, torch.zeros(1, 5, 3, dtype=torch.float64, device="cuda"), 2.0,
                       torch.tensor(lo, device="cuda"), torch.tensor(hi, device="cuda"))
+
+
+# ------------------------------------------------------------ Metropolis-Hastings ----
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_mh_matches_oracle(setup, prec):
+    api, PM, wl, cat, th, lo, hi, f = setup
+    S, steps = 16, 4
+    sd = np.array([p.jitter * (abs(p.base) if p.relative else 1) for p in wl.params])
+    step = 0.7 * sd
+    z, u = W.mh_randoms(9, steps, S, th.shape[1])
+    plan = api.Plan([PM.cluster_input(wl, cat)], S, prec)
+    x = torch.tensor(th[:S], device="cuda")
+    c = plan.chi2(x)
+    dev = lambda a: torch.tensor(a, device="cuda")
+    acc, tr = plan.mh_run(x, c, dev(z), dev(u), dev(step), dev(lo), dev(hi), trace=True)
+    xo, co = th[:S].copy(), f(th[:S])
+    if prec == "fp64":
+        n_acc = OS.mh_run(xo, co, z, u, step, lo, hi, f)
+        assert int(acc) == n_acc and 0 < n_acc < S * steps
+        assert np.allclose(x.cpu().numpy(), xo, rtol=0, atol=1e-12)
+        assert np.allclose(c.cpu().numpy(), co, rtol=1e-10, atol=0)
+        assert np.allclose(tr[-1].cpu().numpy(), xo, rtol=0, atol=1e-12)
+    else:
+        # one step: identical proposals; a decision may differ only inside the chi^2 band
+        x1 = torch.tensor(th[:S], device="cuda")
+        c1 = plan.chi2(x1)
+        plan.mh_run(x1, c1, dev(z[:1]), dev(u[:1]), dev(step), dev(lo), dev(hi))
+        xo, co = th[:S].copy(), f(th[:S])
+        OS.mh_run(xo, co, z[:1], u[:1], step, lo, hi, f)
+        same = np.all(np.abs(x1.cpu().numpy() - xo) <= 1e-12, axis=1)
+        assert same.mean() >= 0.9
+        for k in np.nonzero(~same)[0]:
+            y = th[k] + step * z[0, k]
+            cy, ck = f(y[None])[0], f(th[k:k + 1])[0]
+            assert abs(np.log(u[0, k]) + 0.5 * (cy - ck)) < 1e-5 * (abs(cy) + abs(ck))
+
+
+def test_mh_validation(setup):
+    api, PM, wl, cat, th, lo, hi, f = setup
+    from paper_2609_08649_b300 import _lib as L
+    plan = api.Plan([PM.cluster_input(wl, cat)], 4, "mixed")
+    x = torch.tensor(th[:8], device="cuda")
+    c = torch.zeros(8, dtype=torch.float64, device="cuda")
+    P = th.shape[1]
+    z = torch.zeros(1, 8, P, dtype=torch.float64, device="cuda")
+    u = torch.full((1, 8), 0.5, dtype=torch.float64, device="cuda")
+    s = torch.ones(P, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.LFError):      # more chains than the plan's max_samples
+        plan.mh_run(x, c, z, u, s, torch.tensor(lo, device="cuda"), torch.tensor(hi, device="cuda"))
+    with pytest.raises(TypeError):      # float32 input refused by the binding
+        plan.mh_run(x[:4], c[:4], z[:, :4].float(), u[:, :4], s, torch.tensor(lo, device="cuda"),
+                    torch.tensor(hi, device="cuda"))
