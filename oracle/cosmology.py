@@ -42,6 +42,19 @@ def arcsec_per_kpc(z, H0=70.0, Om=0.3):
     return ARCSEC_PER_RAD / (d_ang(0.0, z, H0, Om) * 1000.0)
 
 
+M_PER_MPC = 3.0856775814913673e22
+SECONDS_PER_DAY = 86400.0
+
+
+def td_scale(z_d, H0=70.0, Om=0.3):
+    """(1 + z_d) D_d theta_0^2 / c in days, theta_0 = 1 arcsec: the time-delay factor of
+    Eq. time_delay at a_dis = 1 (the factor of a family is this over its a_dis, since
+    D_d D_s / D_ds = D_d / a_dis)."""
+    dd_m = d_ang(0.0, z_d, H0, Om) * M_PER_MPC
+    theta0 = 1.0 / ARCSEC_PER_RAD
+    return (1.0 + z_d) * dd_m * theta0 * theta0 / (C_KMS * 1e3) / SECONDS_PER_DAY
+
+
 def rho_crit(z, H0=70.0, Om=0.3):
     """Critical density 3 H(z)^2 / (8 pi G) in Msun / Mpc^3."""
     Hz = H0 * E(z, Om)

@@ -79,6 +79,36 @@ def component(kind, dx, dy, b, eps, pa, core, cut):
     raise ValueError(f"unknown component kind {kind}")
 
 
+def component_potential(kind, dx, dy, b, eps, pa, core, cut):
+    if kind == SIE:
+        return pr.sie_potential(dx, dy, b, q_from_eps(eps), pa, core)
+    if kind == DPIE:
+        return pr.dpie_potential(dx, dy, b, q_from_eps(eps), pa, core, cut)
+    if kind == NFW:
+        return pr.nfw_potential(dx, dy, b, core)
+    if kind == SHEAR:
+        return pr.shear_potential(dx, dy, b, pa)
+    if kind == MPOLE3:
+        return pr.multipole3_potential(dx, dy, b, pa)
+    raise ValueError(f"unknown component kind {kind}")
+
+
+def plane_potential(pl: LPlane, tx, ty):
+    """psi (up to a constant per component) summed over the plane's components and members,
+    (S, N) for positions (1, N) or (S, N)."""
+    out = torch.zeros(torch.broadcast_shapes(tx.shape, (pl.x.shape[0], 1)), dtype=torch.float64)
+    for k, kind in enumerate(pl.kind):
+        col = lambda f: f[:, k:k + 1]
+        out = out + component_potential(kind, tx - col(pl.x), ty - col(pl.y), col(pl.b), col(pl.eps),
+                                         col(pl.pa), col(pl.core), col(pl.cut))
+    if pl.n_members:
+        bm, cm, tm = member_fields(pl)
+        for m in range(pl.n_members):
+            out = out + pr.pje_sph_potential(tx - pl.mx[m], ty - pl.my[m], bm[:, m:m + 1],
+                                             cm[:, m:m + 1], tm[:, m:m + 1])
+    return out
+
+
 def plane_sum(pl: LPlane, tx, ty):
     """alpha and psi_ij summed over every component and member of one plane
     (Sec. 2.1: the potential of a composite lens is the sum of its parts).

@@ -87,6 +87,38 @@ def write(name, rows, header):
     print("wrote", name, rows.shape)
 
 
+def make_aux(wl, cat, seed, flux_fams, td_fams, sig_m=0.1, sig_t=2.0):
+    """Flux and time-delay measurements of a catalogue's noise-free images on the unjittered
+    model (Sec. 3.2-3.3): m_i = m_src - 2.5 log10|mu_i| + N(0, sig_m) with m_src ~ U[24, 27]
+    per family, and delays T_i - T_first + N(0, sig_t) days with T the arrival time of
+    Eq. time_delay about the family's true source; NaN where a family has no measurement."""
+    pl = om.build_planes(wl)[0]
+    t = torch.tensor(cat.theta_true)
+    ax, ay, pxx, pyy, pxy = [o[0] for o in L.plane_sum(pl, t[None, :, 0], t[None, :, 1])]
+    psi = L.plane_potential(pl, t[None, :, 0], t[None, :, 1])[0]
+    adis = om.single_plane_adis(wl, cat.fam_zs)
+    K0 = cz.td_scale(wl.planes[0].z, wl.cosmo.H0, wl.cosmo.Om)
+    rng = np.random.default_rng(seed)
+    n = len(cat.theta_true)
+    mag, me, td, te = (np.full(n, np.nan) for _ in range(4))
+    for f in range(len(cat.fam_off) - 1):
+        i0, i1 = cat.fam_off[f], cat.fam_off[f + 1]
+        a = adis[f]
+        m_src = rng.uniform(24.0, 27.0)
+        det = (1 - a * pxx[i0:i1]) * (1 - a * pyy[i0:i1]) - (a * pxy[i0:i1]) ** 2
+        bx = t[i0:i1, 0] - a * ax[i0:i1]
+        by = t[i0:i1, 1] - a * ay[i0:i1]
+        T = (K0 / a) * (0.5 * ((t[i0:i1, 0] - bx) ** 2 + (t[i0:i1, 1] - by) ** 2) - a * psi[i0:i1])
+        nm, nt = rng.normal(0, sig_m, i1 - i0), rng.normal(0, sig_t, i1 - i0)
+        if f in flux_fams:
+            mag[i0:i1] = m_src + 2.5 * np.log10(np.abs(det.numpy())) + nm
+            me[i0:i1] = sig_m
+        if f in td_fams:
+            td[i0:i1] = (T - T[0]).numpy() + nt
+            te[i0:i1] = sig_t
+    return np.stack([mag, me, td, te], 1)
+
+
 def main(names):
     if not names or "galaxy" in names:
         wl = W.galaxy_c0()
@@ -96,6 +128,14 @@ def main(names):
         wl = W.cluster_c2()
         rows = make(wl, seed=11, src_radius=12.0, src_centre=(4.0, -3.0), half=80.0, h=0.1)
         write("cluster_200", rows, "C2-shaped cluster: 60 families / 200 images, z_s ~ U[1, 6], sigma_pos = 0.1")
+    if not names or "cluster_aux" in names:
+        wl = W.cluster_c2()
+        cat = W.load_catalogue("cluster_200", OUT)
+        rows = make_aux(wl, cat, seed=12, flux_fams=range(0, 30), td_fams=range(40, 55))
+        np.savetxt(os.path.join(OUT, "cluster_200_aux.txt"), rows, fmt="%.10f",
+                   header="flux and time-delay measurements of cluster_200 (rows = its images)\n"
+                          "mag mag_err td_days td_err_days (nan: no measurement)")
+        print("wrote cluster_200_aux", rows.shape)
     if not names or "multicluster" in names:
         for c, wl in enumerate(W.multicluster_c4()):
             x2, y2 = wl.planes[0].comps[1].x, wl.planes[0].comps[1].y

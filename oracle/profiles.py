@@ -191,3 +191,68 @@ def multipole3(dx, dy, amp, pa):
     out = [ax, ay, pxx, pyy, pxy]
     return tuple(torch.where(zero, torch.zeros_like(v), v) for v in out)
 
+
+# ------------------------------------------------------------------ potentials ----
+# The lens potential psi of each profile (up to a constant), needed by the time delay
+# (Eq. time_delay).  Pins: grad psi = alpha (tests/test_oracle_potentials.py).
+
+def sie_potential(dx, dy, b, q, pa, s):
+    """Cored isothermal ellipsoid (Keeton 2001): in the (u, v) frame of sie(),
+    psi = u alpha_u + v alpha_v - b q s ln sqrt((psi~ + s)^2 + (1 - q^2) u^2)."""
+    dx, dy, b, q, pa, s = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64)
+                                                     for t in (dx, dy, b, q, pa, s)])
+    ax, ay, *_ = sie(dx, dy, b, q, pa, s)
+    c, sn = torch.cos(pa), torch.sin(pa)
+    u = c * dx + sn * dy
+    psit = torch.sqrt(q * q * (s * s + u * u) + (-sn * dx + c * dy) ** 2)
+    lg = 0.5 * torch.log((psit + s) ** 2 + (1.0 - q * q) * u * u)
+    return dx * ax + dy * ay - b * q * s * lg
+
+
+def dpie_potential(dx, dy, b, q, pa, core, cut):
+    return sie_potential(dx, dy, b, q, pa, core) - sie_potential(dx, dy, b, q, pa, cut)
+
+
+def pje_sph_potential(dx, dy, b, core, cut):
+    """Round pseudo-Jaffe: psi = b [(S - core ln(S + core)) - (R - cut ln(R + cut))], whose
+    radial derivative is b r [1/(S + core) - 1/(R + cut)]."""
+    dx, dy, b, core, cut = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64)
+                                                     for t in (dx, dy, b, core, cut)])
+    r2 = dx * dx + dy * dy
+    S = torch.sqrt(core * core + r2)
+    R = torch.sqrt(cut * cut + r2)
+    return b * ((S - core * torch.log(S + core)) - (R - cut * torch.log(R + cut)))
+
+
+def nfw_potential(dx, dy, ks, rs):
+    """Spherical NFW: psi = 2 ks rs^2 [ln^2(x/2) - atanh^2 sqrt(1 - x^2)] (x < 1),
+    [ln^2(x/2) + atan^2 sqrt(x^2 - 1)] (x > 1), ln^2(1/2) at x = 1; its derivative in x is
+    4 ks rs h(x)/x as in nfw_sph().  For x < 1, atanh sqrt(1 - x^2) = ln((1 + w)/x) with
+    w = sqrt(1 - x^2), and the difference of squares is evaluated as the product
+    ln(x^2 / (2 (1 + w))) ln((1 + w) / 2), free of the cancellation of the two squares."""
+    dx, dy, ks, rs = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64)
+                                               for t in (dx, dy, ks, rs)])
+    x = torch.sqrt(dx * dx + dy * dy) / rs
+    w2 = (1.0 - x) * (1.0 + x)
+    lt = w2 > 0
+    w = torch.sqrt(torch.where(lt, w2, torch.zeros_like(w2)))
+    g_lt = torch.log(x * x / (2.0 * (1.0 + w))) * torch.log((1.0 + w) / 2.0)
+    wg = torch.where(~lt, -w2, torch.zeros_like(w2))
+    g_gt = torch.log(x / 2.0) ** 2 + torch.atan(torch.sqrt(wg)) ** 2
+    return 2.0 * ks * rs * rs * torch.where(lt, g_lt, g_gt)
+
+
+def shear_potential(dx, dy, gamma, pa):
+    """psi = (gamma/2) r^2 cos 2(phi - pa) = (g1 (x^2 - y^2) + 2 g2 x y) / 2."""
+    dx, dy, gamma, pa = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64)
+                                                  for t in (dx, dy, gamma, pa)])
+    g1, g2 = gamma * torch.cos(2.0 * pa), gamma * torch.sin(2.0 * pa)
+    return 0.5 * g1 * (dx * dx - dy * dy) + g2 * dx * dy
+
+
+def multipole3_potential(dx, dy, amp, pa):
+    """psi = amp r^2 cos 3(phi - pa), the definition."""
+    dx, dy, amp, pa = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64)
+                                                for t in (dx, dy, amp, pa)])
+    return amp * (dx * dx + dy * dy) * torch.cos(3.0 * (torch.atan2(dy, dx) - pa))
+

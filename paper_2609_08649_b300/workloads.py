@@ -344,6 +344,13 @@ class Catalogue:
     fam_zs: np.ndarray         # (F,)
 
 
+def load_aux(name: str, directory: str = CATALOGUE_DIR):
+    """Flux and time-delay measurements of a catalogue's images written by
+    oracle/make_catalogues.py: (mag, mag_err, td_days, td_err_days), NaN where absent."""
+    a = np.loadtxt(os.path.join(directory, name + "_aux.txt"), ndmin=2)
+    return a[:, 0].copy(), a[:, 1].copy(), a[:, 2].copy(), a[:, 3].copy()
+
+
 def load_catalogue(name: str, directory: str = CATALOGUE_DIR) -> Catalogue:
     """Multiple-image catalogue written by oracle/make_catalogues.py (forward ray-shooting
     on the unjittered model); columns family, z_s, x_obs, y_obs, x_true, y_true."""
