@@ -381,6 +381,16 @@ def secondary(torch, api, PM, W, L, C, step, ms_mixed, evals):
         out["grad_16clusters_1024"] = res
     except FileNotFoundError as e:
         out["grad_16clusters_1024"] = {"skipped": str(e)}
+    # total chi^2 with the flux and time-delay terms (75 magnitudes, 15 families with delays)
+    aux = W.load_aux("cluster_200")
+    res = {}
+    for prec in ("mixed", "ff", "fp64"):
+        plan = api.Plan([PM.cluster_input(wl, cat, aux=aux)], th.shape[0], prec,
+                        flags=api.FLAG_GRAPH | api.FLAG_AUTOTUNE)
+        t = _time(torch, lambda: plan.chi2(th), reps=5 if prec != "fp64" else 2)
+        res[prec] = {"ms": t, "chi2_per_s": th.shape[0] / (t * 1e-3)}
+        plan.close()
+    out["chi2_flux_delay_4096x200"] = res
     # free source redshifts: 12 families' a_dis sampled as parameters (30 parameters in all)
     base_a = [PM.adis(wl.cosmo, wl.planes[0].z, z) for z in cat.fam_zs]
     fr = list(range(0, 60, 5))

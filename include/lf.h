@@ -201,6 +201,17 @@ typedef struct {
   const int32_t* fam_off;    /* [n_fam + 1] image offsets, fam_off[0] = 0            */
   const double* fam_ratio;   /* single plane: [n_fam] a_dis of each family;
                                 multi-plane: [n_fam * n_planes] D_js/D_s per family  */
+  /* Optional flux and time-delay measurements (Sec. 3.2-3.3; single-plane clusters; the
+   * chi^2 of lf_chi2_batch then adds Eq. chi2_flux and Eq. chi2_td in their source-plane
+   * forms, with m_src and Delta t_0 per family solved analytically; no gradient).  An image
+   * takes part in a term when its value and its error are finite and the error is > 0.    */
+  const double* mag;         /* [n_img] observed magnitudes, or NULL (no flux term)          */
+  const double* mag_err;     /* [n_img] magnitude errors                                      */
+  const double* td;          /* [n_img] observed time delays in days (any zero point per
+                                family), or NULL (no time-delay term)                         */
+  const double* td_err;      /* [n_img] time-delay errors in days                             */
+  double td_scale;           /* (1 + z_d) D_d theta_0^2 / c in days (lf_td_scale); the factor
+                                of a family is td_scale / a_dis                               */
 } lf_images;
 
 /* One cluster of a plan: its base model, images and parameter map.  The sampled
@@ -319,6 +330,9 @@ double lf_angular_distance(double H0, double Om, double z1, double z2);
 double lf_adis(double H0, double Om, double z_l, double z_s);
 /* Angular size of one kpc at redshift z, arcsec. */
 double lf_arcsec_per_kpc(double H0, double Om, double z);
+/* (1 + z_d) D_d theta_0^2 / c in days with theta_0 = 1 arcsec: the time-delay factor of
+ * Eq. time_delay at a_dis = 1 (a family's factor is this over its a_dis). */
+double lf_td_scale(double H0, double Om, double z_d);
 /* b = 4 pi (v/c)^2 in arcsec for a velocity dispersion v in km/s. */
 double lf_b_from_vdisp(double v_kms);
 /* Spherical NFW (M200 [Msun], concentration c) at z_l -> kappa_s and theta_s [arcsec]

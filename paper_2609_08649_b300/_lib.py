@@ -43,7 +43,9 @@ class lf_grid(C.Structure):
 
 class lf_images(C.Structure):
     _fields_ = [("n_img", C.c_int32), ("n_fam", C.c_int32), ("theta_obs", C.c_void_p),
-                ("sinv", C.c_void_p), ("fam_off", C.c_void_p), ("fam_ratio", C.c_void_p)]
+                ("sinv", C.c_void_p), ("fam_off", C.c_void_p), ("fam_ratio", C.c_void_p),
+                ("mag", C.c_void_p), ("mag_err", C.c_void_p), ("td", C.c_void_p),
+                ("td_err", C.c_void_p), ("td_scale", C.c_double)]
 
 
 class lf_cluster(C.Structure):
@@ -89,7 +91,8 @@ def _load():
         fn.argtypes = args
         fn.restype = C.c_int
     for name, args in {"lf_angular_distance": [f64] * 4, "lf_adis": [f64] * 4,
-                       "lf_arcsec_per_kpc": [f64] * 3, "lf_b_from_vdisp": [f64]}.items():
+                       "lf_arcsec_per_kpc": [f64] * 3, "lf_b_from_vdisp": [f64],
+                       "lf_td_scale": [f64] * 3}.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = C.c_double
@@ -108,7 +111,7 @@ EXPORTS = ["lf_deflect_grid", "lf_jacobian_grid", "lf_jacobian_points", "lf_trac
            "lf_chi2_img_batch", "lf_aies_run", "lf_mh_run", "lf_find_images", "lf_find_images_workspace",
            "lf_chi2_batch_static",
            "lf_plan_info", "lf_angular_distance", "lf_adis", "lf_arcsec_per_kpc",
-           "lf_b_from_vdisp", "lf_nfw_params", "lf_device_error", "lf_last_error", "lf_version"]
+           "lf_b_from_vdisp", "lf_td_scale", "lf_nfw_params", "lf_device_error", "lf_last_error", "lf_version"]
 
 
 def check(status):

@@ -130,7 +130,12 @@ class ClusterInput:
     """Everything one cluster of a plan needs, in lensing units (host arrays)."""
 
     def __init__(self, planes, arcsec_per_kpc, theta_obs, sinv, fam_off, fam_ratio,
-                 p_comp, p_field, p_xform, ratios=None):
+                 p_comp, p_field, p_xform, ratios=None, aux=None, td_scale=0.0):
+        """aux: optional (mag, mag_err, td, td_err) per image (NaN where absent; either pair
+        may be None) for the flux and time-delay terms; td_scale from model.td_scale."""
+        f64 = lambda v: None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+        self.aux = tuple(f64(v) for v in aux) if aux is not None else (None, None, None, None)
+        self.td_scale = float(td_scale)
         self.planes = planes
         self.apk = np.ascontiguousarray(arcsec_per_kpc, dtype=np.float64)
         self.theta_obs = np.ascontiguousarray(theta_obs, dtype=np.float64)
@@ -158,6 +163,9 @@ class ClusterInput:
         im.sinv = self.sinv.ctypes.data_as(C.c_void_p)
         im.fam_off = self.fam_off.ctypes.data_as(C.c_void_p)
         im.fam_ratio = self.fam_ratio.ctypes.data_as(C.c_void_p)
+        ptr = lambda v: None if v is None else v.ctypes.data_as(C.c_void_p)
+        im.mag, im.mag_err, im.td, im.td_err = (ptr(v) for v in self.aux)
+        im.td_scale = self.td_scale
         c.images = im
         c.P = len(self.p_comp)
         c.p_comp = self.p_comp.ctypes.data_as(C.c_void_p)

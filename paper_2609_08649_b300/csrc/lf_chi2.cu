@@ -70,6 +70,9 @@ struct ClusterDesc {
   int scal_plane;
   int scal_free;
   int scal_p[6];
+  int aux;                         // flux (1) and time-delay (2) terms present (one plane)
+  const double *aux_mag, *aux_wmag, *aux_td, *aux_wtd;   // per image; weight 0: no measurement
+  double td_scale;                 // (1 + z_d) D_d theta_0^2 / c, days
   int n_afree;                     // families whose a_dis is a sampled parameter (one plane)
   int afree_fam[LF_MAX_P], afree_p[LF_MAX_P];
   int p_xform[LF_MAX_P];
@@ -82,7 +85,7 @@ struct ClusterDesc {
   const float4* theta_ff;          // [n_img] (x_hi, x_lo, y_hi, y_lo)
   const float2* ratio_ff;          // [n_fam * np]
   const float4* sinv_f;            // [n_img] (xx, xy, yy, 0)
-  uint32_t off_img, off_imgd, off_fam, off_par, off_free, off_newton, off_fama, smem;
+  uint32_t off_img, off_imgd, off_fam, off_par, off_free, off_newton, off_fama, off_aux, smem;
 };
 
 // ------------------------------------------------------------------ transforms -----
@@ -252,6 +255,55 @@ constexpr int IMGF = 22;
 // PASS 0: source-plane chi^2 (and its gradient when GRAD).  PASS 1: image-plane chi^2 of
 // Eq. chi2_img with model images found by `iters` Newton steps from the observed images
 // towards the family's analytic source (written to chi2), and the image-plane rms (to rms).
+// ----------------------------------------------------- flux / time-delay helpers ---
+__device__ __forceinline__ void mem_geom(const MemT<float>& m, float& xh, float& xl, float& yh,
+                                         float& yl, float& b, float& s, float& a) {
+  xh = m.xh; xl = m.xl; yh = m.yh; yl = m.yl; b = m.b; s = m.s; a = m.a;
+}
+__device__ __forceinline__ void mem_geom(const MemT<double>& m, double& xh, double& xl, double& yh,
+                                         double& yl, double& b, double& s, double& a) {
+  xh = m.xh; xl = 0.0; yh = m.yh; yl = 0.0; b = m.b; s = m.s; a = m.a;
+}
+__device__ __forceinline__ void mem_geom(const MemX& m, float& xh, float& xl, float& yh, float& yl,
+                                         float& b, float& s, float& a) {
+  xh = m.xh; xl = m.xl; yh = m.yh; yl = m.yl; b = m.b; s = m.sh; a = m.ah;
+}
+
+// psi and its third derivatives summed over the components [k0, k1) of one plane at one
+// position: out = (psi, psi_xxx, psi_xxy, psi_xyy, psi_yyy); psi in float-float (mixed tiers)
+// or FP64, the third derivatives in T.
+template <class T, class Mem>
+__device__ void aux_sum(const CompT<T>* dc, int nc, const Mem* dm, int nm, int k0, int k1, T pxh,
+                        T pxl, T pyh, T pyl, double (&out)[5]) {
+  ff pf = ff_zero();
+  double pd = 0.0;
+  T s3[4] = {(T)0, (T)0, (T)0, (T)0};
+  const int c1 = min(k1, nc);
+  for (int c = k0; c < c1; ++c) {
+    const CompT<T>& C = dc[c];
+    if (C.kind == 0) continue;
+    const T dx = offset_of(pxh, pxl, C.xh, C.xl), dy = offset_of(pyh, pyl, C.yh, C.yl);
+    const T p = comp_potential(C, dx, dy);
+    T d3[4];
+    comp_d3(C, dx, dy, d3);
+    if constexpr (std::is_same<T, float>::value) ff_acc(pf, p); else pd += p;
+    for (int q = 0; q < 4; ++q) s3[q] += d3[q];
+  }
+  const int m_beg = max(k0, nc) - nc, m_end = min(k1, nc + nm) - nc;
+  for (int m = m_beg; m < m_end; ++m) {
+    T xh, xl, yh, yl, b, sc, ac;
+    mem_geom(dm[m], xh, xl, yh, yl, b, sc, ac);
+    const T dx = offset_of(pxh, pxl, xh, xl), dy = offset_of(pyh, pyl, yh, yl);
+    const T p = pje_potential(::lf_fma(dx, dx, dy * dy), b, sc, ac);
+    T d3[4];
+    member_d3(dx, dy, b, sc, ac, d3);
+    if constexpr (std::is_same<T, float>::value) ff_acc(pf, p); else pd += p;
+    for (int q = 0; q < 4; ++q) s3[q] += d3[q];
+  }
+  if constexpr (std::is_same<T, float>::value) out[0] = ff_to_double(pf); else out[0] = pd;
+  for (int q = 0; q < 4; ++q) out[q + 1] = (double)s3[q];
+}
+
 template <int MODE, bool GRAD, int PASS = 0>   // MODE: LF_FP64, LF_MIXED or LF_FF
 __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const ClusterDesc* __restrict__ cds,
                                               const int* __restrict__ corder, int spc, int S,
@@ -693,6 +745,112 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
         my += cf;
       }
     }
+    if constexpr (PASS == 2) {
+      if (C.aux) {
+        // ---- flux and time-delay terms in their source-plane forms (Sec. 3.2-3.3): psi and its
+        // third derivatives at every observed image, the linearised magnification
+        // mu + [A^-1 (beta_model - beta_i)] . grad mu and arrival time
+        // K [(theta - beta_i)^2 / 2 - a psi] + K (beta_model - beta_i) . (beta_i - theta),
+        // K = td_scale / a, then per family the nuisances m_src and Delta t_0
+        double* aux = reinterpret_cast<double*>(smem + C.off_aux);
+        __syncthreads();
+        const PlaneDesc& P = C.pl[0];
+        const CompT<T>* dc = reinterpret_cast<const CompT<T>*>(smem + P.off_dc);
+        const Mem* dm = reinterpret_cast<const Mem*>(smem + P.off_dm);
+        const int K = P.nc + P.nm;
+        const int ntask_img = n_img * KS;
+        for (int base = 0; base < ntask_img; base += blockDim.x) {
+          const int t = base + tid;
+          const bool act = t < ntask_img;
+          const int i = act ? t / KS : 0, k = act ? t - i * KS : 0;
+          const int k0 = (int)((long long)K * k / KS), k1 = (int)((long long)K * (k + 1) / KS);
+          double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+          if (act) {
+            T xh, xl, yh, yl;
+            if constexpr (MIXED) {
+              const float4 tf = C.theta_ff[i];
+              xh = tf.x; xl = tf.y; yh = tf.z; yl = tf.w;
+            } else {
+              xh = C.theta[2 * i]; xl = (T)0; yh = C.theta[2 * i + 1]; yl = (T)0;
+            }
+            aux_sum<T, Mem>(dc, P.nc, dm, P.nm, k0, k1, xh, xl, yh, yl, v);
+          }
+          for (int off = 1; off < KS; off <<= 1)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+          if (act && k == 0)
+            for (int q = 0; q < 5; ++q) aux[6 * i + q] = v[q];
+        }
+        __syncthreads();
+        for (int i = tid; i < n_img; i += blockDim.x) {
+          const int f = C.img_fam[i], i0 = C.fam_off[f];
+          const double a = fa[f];
+          double sm[5], bx, by, bmx, bmy;
+          if constexpr (MIXED) {
+            const float* r = imgf + i * ISF;
+            const float* r0 = imgf + i0 * ISF;
+            for (int q = 0; q < 5; ++q) sm[q] = (double)r[2 * q] + (double)r[2 * q + 1];
+            bx = ff_to_double(ff_make(r[10], r[11]));
+            by = ff_to_double(ff_make(r[12], r[13]));
+            bmx = ff_to_double(ff_make(r0[10], r0[11])) + fam[3 * f + 1];
+            bmy = ff_to_double(ff_make(r0[12], r0[13])) + fam[3 * f + 2];
+          } else {
+            const double* r = img + i * IS;
+            for (int q = 0; q < 5; ++q) sm[q] = r[q];
+            bx = r[8]; by = r[9];
+            bmx = img[i0 * IS + 8] + fam[3 * f + 1];
+            bmy = img[i0 * IS + 9] + fam[3 * f + 2];
+          }
+          const double tx = C.theta[2 * i], ty = C.theta[2 * i + 1];
+          const double A00 = 1.0 - a * sm[2], A11 = 1.0 - a * sm[3], A01 = -a * sm[4];
+          const double det = A00 * A11 - A01 * A01, mu = 1.0 / det;
+          const double* d3 = aux + 6 * i + 1;
+          // grad det A from psi_xxx, psi_xxy, psi_xyy, psi_yyy; grad mu = -mu^2 grad det A
+          const double gx = -a * (d3[0] * A11 + d3[2] * A00) + 2.0 * a * A01 * d3[1];
+          const double gy = -a * (d3[1] * A11 + d3[3] * A00) + 2.0 * a * A01 * d3[2];
+          const double db0 = bmx - bx, db1 = bmy - by;
+          const double dt0 = (A11 * db0 - A01 * db1) / det, dt1 = (A00 * db1 - A01 * db0) / det;
+          double y = 0.0, dd = 0.0;
+          if (C.aux_wmag[i] > 0.0) {
+            const double mu_m = mu - mu * mu * (dt0 * gx + dt1 * gy);
+            y = C.aux_mag[i] + 2.5 * log10(fabs(mu_m));
+          }
+          if (C.aux_wtd[i] > 0.0) {
+            const double Kf = C.td_scale / a;
+            const double geo = 0.5 * ((tx - bx) * (tx - bx) + (ty - by) * (ty - by));
+            const double Ti = Kf * (geo - a * aux[6 * i]) + Kf * (db0 * (bx - tx) + db1 * (by - ty));
+            dd = C.aux_td[i] - Ti;
+          }
+          aux[6 * i + 1] = y;
+          aux[6 * i + 2] = dd;
+        }
+        __syncthreads();
+        for (int f = tid; f < C.n_fam; f += blockDim.x) {
+          const int i0 = C.fam_off[f], i1 = C.fam_off[f + 1];
+          double wm = 0.0, ym = 0.0, wt = 0.0, yt = 0.0;
+          for (int i = i0; i < i1; ++i) {
+            wm += C.aux_wmag[i]; ym += C.aux_wmag[i] * aux[6 * i + 1];
+            wt += C.aux_wtd[i]; yt += C.aux_wtd[i] * aux[6 * i + 2];
+          }
+          double add = 0.0;
+          if (wm > 0.0) {
+            const double m_src = ym / wm;
+            for (int i = i0; i < i1; ++i) {
+              const double e = aux[6 * i + 1] - m_src;
+              add += C.aux_wmag[i] * e * e;
+            }
+          }
+          if (wt > 0.0) {
+            const double t0 = yt / wt;
+            for (int i = i0; i < i1; ++i) {
+              const double e = aux[6 * i + 2] - t0;
+              add += C.aux_wtd[i] * e * e;
+            }
+          }
+          my += isfinite(add) ? add : INFINITY;
+        }
+      }
+    }
     if constexpr (PASS == 1) {
       // ---- image-plane chi^2: Newton steps theta <- theta - A^-1 (beta(theta) - beta_model)
       // from the observed images, then chi^2_img = sum (theta_obs - theta)^T S^-1 (...)
@@ -894,6 +1052,7 @@ using namespace lf;
 struct lf_plan {
   int n_clusters = 0, P = 0, precision = LF_MIXED, flags = 0, max_samples = 0;
   bool single_plane = true;
+  bool has_aux = false;            // some cluster carries flux / time-delay measurements
   std::vector<ClusterDesc> desc;
   std::vector<double> cost;
   ClusterDesc* d_desc = nullptr;
@@ -913,7 +1072,7 @@ struct lf_plan {
   int ks_cap = 32;
   bool tuned = false;
   uint32_t smem = 0;
-  int grid_chi2 = 0, grid_grad = 0;
+  int grid_chi2 = 0, grid_grad = 0, grid_aux = 0;
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -1060,6 +1219,8 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
   o = (o + 15u) & ~15u; C.off_newton = o; o += (uint32_t)C.n_img * 4u * 8u;
   // per sample: a_dis of each family (double, float-float) and the parameter setting it
   o = (o + 15u) & ~15u; C.off_fama = o; o += (uint32_t)C.n_fam * (8u + 8u + 4u);
+  // flux / time-delay pass: per image psi, the third derivatives, then y_i and d_i
+  o = (o + 15u) & ~15u; C.off_aux = o; o += C.aux ? (uint32_t)C.n_img * 6u * 8u : 0u;
   C.smem = (o + 15u) & ~15u;
   int K = 0;
   for (int j = 0; j < C.np; ++j) K = std::max(K, C.pl[j].nc + C.pl[j].nm);
@@ -1093,9 +1254,17 @@ static lf_status relayout(lf_plan* pl) {
   const void* ki = pl->precision == LF_MIXED ? (const void*)k_chi2<LF_MIXED, false, 1>
                    : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, false, 1>
                                              : (const void*)k_chi2<LF_FP64, false, 1>;
+  const void* ka = pl->precision == LF_MIXED ? (const void*)k_chi2<LF_MIXED, false, 2>
+                   : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, false, 2>
+                                             : (const void*)k_chi2<LF_FP64, false, 2>;
   LF_TRY(kset(kc));
   LF_TRY(kset(kg));
   LF_TRY(kset(ki));
+  if (pl->has_aux) {
+    LF_TRY(kset(ka));
+    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ka, pl->block, pl->smem));
+    pl->grid_aux = nsm * std::max(occ, 1);
+  }
   LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kc, pl->block, pl->smem));
   pl->grid_chi2 = nsm * std::max(occ, 1);
   LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kg, pl->block, pl->smem));
@@ -1219,6 +1388,31 @@ static lf_status build_cluster(lf_plan* pl, const lf_cluster& cl, ClusterDesc& C
     LF_TRY(plan_upload(pl, rf.data(), rf.size(), &drf));
     C.theta_ff = dtf; C.sinv_f = dsf; C.ratio_ff = drf;
   }
+  // flux and time-delay measurements (optional)
+  C.aux = 0;
+  if (im.mag || im.td) {
+    if (C.np != 1) return fail(LF_EUNSUPPORTED, "flux and time-delay terms need a single-plane cluster");
+    if (im.mag && !im.mag_err) return fail(LF_EINVAL, "mag given without mag_err");
+    if (im.td && !im.td_err) return fail(LF_EINVAL, "td given without td_err");
+    if (im.td && !(std::isfinite(im.td_scale) && im.td_scale > 0))
+      return fail(LF_EINVAL, "td_scale must be finite and > 0");
+    std::vector<double> v(4 * (size_t)im.n_img, 0.0);
+    for (int i = 0; i < im.n_img; ++i) {
+      if (im.mag && std::isfinite(im.mag[i]) && std::isfinite(im.mag_err[i]) && im.mag_err[i] > 0) {
+        v[i] = im.mag[i];
+        v[im.n_img + i] = 1.0 / (im.mag_err[i] * im.mag_err[i]);
+      }
+      if (im.td && std::isfinite(im.td[i]) && std::isfinite(im.td_err[i]) && im.td_err[i] > 0) {
+        v[2 * im.n_img + i] = im.td[i];
+        v[3 * im.n_img + i] = 1.0 / (im.td_err[i] * im.td_err[i]);
+      }
+    }
+    double* dv = nullptr;
+    LF_TRY(plan_upload(pl, v.data(), v.size(), &dv));
+    C.aux_mag = dv; C.aux_wmag = dv + im.n_img; C.aux_td = dv + 2 * im.n_img; C.aux_wtd = dv + 3 * im.n_img;
+    C.td_scale = im.td ? im.td_scale : 0.0;
+    C.aux = (im.mag ? 1 : 0) | (im.td ? 2 : 0);
+  }
   // parameter map
   LF_TRY(parse_params(cl, comp_base.data(), C));
   int K = 0;
@@ -1239,6 +1433,11 @@ static void launch_mode(lf_plan* pl, const double* theta, int S, double* chi2, d
     k_chi2<MODE, true><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
                                                        grad, pl->d_counter, g_member_chunk,
                                                        pl->d_free_dig, pl->d_free_raw);
+  } else if (pl->has_aux) {
+    int g = std::min(pl->grid_aux, S);
+    k_chi2<MODE, false, 2><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
+                                                           nullptr, pl->d_counter, g_member_chunk,
+                                                           pl->d_free_dig, nullptr);
   } else {
     int g = std::min(pl->grid_chi2, S);
     k_chi2<MODE, false><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
@@ -1385,6 +1584,7 @@ extern "C" lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, i
     if (clusters[c].P != pl->P) st = fail(LF_EINVAL, "every cluster must have the same P");
     else st = build_cluster(pl, clusters[c], pl->desc[c], pl->cost[c]);
     if (st == LF_OK && pl->desc[c].np > 1) pl->single_plane = false;
+    if (st == LF_OK && pl->desc[c].aux) pl->has_aux = true;
     if (st == LF_OK) pl->nfree_max = std::max(pl->nfree_max, pl->desc[c].n_free);
   }
   if (st == LF_OK) {
@@ -1434,6 +1634,7 @@ extern "C" lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int3
   if (!plan) return fail(LF_EINVAL, "plan is NULL");
   if (!grad) return fail(LF_EINVAL, "grad is NULL");
   if (!plan->single_plane) return fail(LF_EUNSUPPORTED, "the gradient is implemented for single-plane plans");
+  if (plan->has_aux) return fail(LF_EUNSUPPORTED, "no gradient of the flux and time-delay terms");
   return run(plan, theta, S, chi2, grad, stream);
 }
 

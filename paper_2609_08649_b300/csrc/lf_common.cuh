@@ -469,34 +469,35 @@ LF_INLINE void multipole3(T dx, T dy, T c3, T s3, Out5<T>& o) {
   o.pxy = (T)6 * (s3 * nx - c3 * ny) - ny * Hx - nx * Hy + (T)3 * G * xy;
 }
 
-// alpha and psi_ij of one explicit component at offset (dx, dy).
-template <class T>
-LF_INLINE void eval_comp(const CompT<T>& c, T dx, T dy, Out5<T>& o) {
+// alpha and psi_ij of one explicit component at offset (dx, dy), evaluated in U (T itself, or
+// dual numbers over the offset for third derivatives) with the component's constants in T.
+template <class T, class U>
+LF_INLINE void eval_comp_g(const CompT<T>& c, U dx, U dy, Out5<U>& o) {
+  const U b = U(c.b), cc = U(c.c), sn = U(c.sn);
   if (c.kind == K_MPOLE3) {
-    multipole3(dx, dy, c.c, c.sn, o);
-    o.ax = c.b * o.ax; o.ay = c.b * o.ay; o.pxx = c.b * o.pxx; o.pyy = c.b * o.pyy;
-    o.pxy = c.b * o.pxy;
+    multipole3(dx, dy, cc, sn, o);
+    o.ax = b * o.ax; o.ay = b * o.ay; o.pxx = b * o.pxx; o.pyy = b * o.pyy; o.pxy = b * o.pxy;
     return;
   }
   if (c.kind == K_SHEAR) {
-    T g1 = c.b * c.c, g2 = c.b * c.sn;
+    U g1 = b * cc, g2 = b * sn;
     o.ax = g1 * dx + g2 * dy;
     o.ay = g2 * dx - g1 * dy;
     o.pxx = g1; o.pyy = -g1; o.pxy = g2;
     return;
   }
   if (c.kind == K_NFW) {
-    nfw_sph(dx, dy, c.b, c.irs, o);
+    nfw_sph(dx, dy, b, U(c.irs), o);
     return;
   }
   if (c.round) {
     if (c.kind == K_DPIE) {
-      pje_round(dx, dy, c.b, c.s1, c.s1sq, c.s2, c.s2sq, o);
+      pje_round(dx, dy, b, U(c.s1), U(c.s1sq), U(c.s2), U(c.s2sq), o);
     } else {
-      T r2 = lf_fma(dx, dx, dy * dy);
-      T kbar, t;
-      cored_round(r2, c.s1, c.s1sq, kbar, t);
-      kbar = c.b * kbar; t = c.b * t;
+      U r2 = lf_fma(dx, dx, dy * dy);
+      U kbar, t;
+      cored_round(r2, U(c.s1), U(c.s1sq), kbar, t);
+      kbar = b * kbar; t = b * t;
       o.ax = kbar * dx; o.ay = kbar * dy;
       o.pxx = lf_fma(t * dx, dx, kbar);
       o.pyy = lf_fma(t * dy, dy, kbar);
@@ -504,17 +505,24 @@ LF_INLINE void eval_comp(const CompT<T>& c, T dx, T dy, Out5<T>& o) {
     }
     return;
   }
-  T u = c.c * dx + c.sn * dy;
-  T v = c.c * dy - c.sn * dx;
-  T au, av, puu, pvv, puv;
-  sie_uv(u, v, c.q, c.q2, c.e, c.qe, c.s1, c.s1sq, c.q2s1, c.D01, false, au, av, puu, pvv, puv);
+  U u = cc * dx + sn * dy;
+  U v = cc * dy - sn * dx;
+  U au, av, puu, pvv, puv;
+  sie_uv(u, v, U(c.q), U(c.q2), U(c.e), U(c.qe), U(c.s1), U(c.s1sq), U(c.q2s1), U(c.D01), false, au, av,
+         puu, pvv, puv);
   if (c.kind == K_DPIE) {
-    T bu, bv, quu, qvv, quv;
-    sie_uv(u, v, c.q, c.q2, c.e, c.qe, c.s2, c.s2sq, c.q2s2, c.D02, false, bu, bv, quu, qvv, quv);
+    U bu, bv, quu, qvv, quv;
+    sie_uv(u, v, U(c.q), U(c.q2), U(c.e), U(c.qe), U(c.s2), U(c.s2sq), U(c.q2s2), U(c.D02), false, bu, bv,
+           quu, qvv, quv);
     au -= bu; av -= bv; puu -= quu; pvv -= qvv; puv -= quv;
   }
-  au *= c.b; av *= c.b; puu *= c.b; pvv *= c.b; puv *= c.b;
-  rotate_back(c.c, c.sn, au, av, puu, pvv, puv, o);
+  au *= b; av *= b; puu *= b; pvv *= b; puv *= b;
+  rotate_back(cc, sn, au, av, puu, pvv, puv, o);
+}
+
+template <class T>
+LF_INLINE void eval_comp(const CompT<T>& c, T dx, T dy, Out5<T>& o) {
+  eval_comp_g<T, T>(c, dx, dy, o);
 }
 
 // One member with its precomputed b (a - s) and a + s (same forms as pje_round).
@@ -536,6 +544,76 @@ LF_INLINE void eval_member(const MemT<T>& m, T dx, T dy, Out5<T>& o) {
   o.pxx = lf_fma(t * dx, dx, kbar);
   o.pyy = lf_fma(t * dy, dy, kbar);
   o.pxy = t * dx * dy;
+}
+
+// ----------------------------------------------- potential and third derivatives ---
+// The lens potential psi (up to a constant per component), for the arrival time of the
+// time-delay term (Eq. time_delay), and the third derivatives psi_xxx, psi_xxy, psi_xyy, psi_yyy,
+// for grad mu of the flux term (Sec. 3.2).
+//   softened isothermal ellipsoid (Keeton 2001), in its (u, v) frame:
+//     psi = u alpha_u + v alpha_v - b q s ln sqrt((psi~ + s)^2 + (1 - q^2) u^2)   (round: q = 1)
+//   round pseudo-Jaffe member: psi = b [(S - s ln(S + s)) - (R - a ln(R + a))], with
+//     S - R = (s^2 - a^2) / (S + R);
+//   NFW: psi = 2 ks rs^2 g(x), g = ln(x^2 / (2 (1 + w))) ln((1 + w) / 2), w = sqrt(1 - x^2) (x < 1),
+//     g = ln^2(x/2) + atan^2 sqrt(x^2 - 1) (x >= 1);
+//   shear: psi = (g1 (x^2 - y^2) + 2 g2 x y) / 2;  multipole: psi = A r^2 cos 3(phi - phi_3).
+template <class T>
+LF_INLINE T sie_potential_uv(T u, T v, T q, T q2, T e, T qe, T s, T s2, T q2s, T D0, bool round) {
+  T au, av, puu, pvv, puv;
+  T psit;
+  if (round) {
+    const T r2 = lf_fma(u, u, v * v);
+    psit = lf_sqrt(s2 + r2);
+    au = u * lf_rcp(psit + s);
+    av = v * lf_rcp(psit + s);
+  } else {
+    sie_uv(u, v, q, q2, e, qe, s, s2, q2s, D0, false, au, av, puu, pvv, puv);
+    psit = lf_sqrt(lf_fma(q2, s2 + u * u, v * v));
+  }
+  const T w = psit + s;
+  return u * au + v * av - (T)0.5 * q * s * lf_log(lf_fma(w, w, ((T)1 - q2) * u * u));
+}
+
+template <class T>
+LF_INLINE T nfw_potential(T dx, T dy, T ks, T irs) {
+  const T x = lf_sqrt(lf_fma(dx, dx, dy * dy)) * irs;
+  if (!(x > (T)0)) return (T)0;
+  const T rs = lf_rcp(irs);
+  T g;
+  if (x < (T)1) {
+    const T w = lf_sqrt(((T)1 - x) * ((T)1 + x));
+    g = lf_log(x * x / ((T)2 * ((T)1 + w))) * lf_log(((T)1 + w) * (T)0.5);
+  } else {
+    const T l = lf_log(x * (T)0.5), t = lf_atan(lf_sqrt((x - (T)1) * (x + (T)1)));
+    g = l * l + t * t;
+  }
+  return (T)2 * ks * rs * rs * g;
+}
+
+template <class T>
+LF_INLINE T pje_potential(T r2, T b, T s, T a) {
+  const T S = lf_sqrt(s * s + r2), R = lf_sqrt(a * a + r2);
+  return b * ((s - a) * (s + a) * lf_rcp(S + R) - s * lf_log(S + s) + a * lf_log(R + a));
+}
+
+template <class T>
+LF_INLINE T comp_potential(const CompT<T>& c, T dx, T dy) {
+  if (c.kind == K_MPOLE3) {
+    const T r2 = lf_fma(dx, dx, dy * dy);
+    if (!(r2 > (T)0)) return (T)0;
+    const T ir = lf_rsqrt(r2), nx = dx * ir, ny = dy * ir;
+    const T G = c.c * nx * (nx * nx - (T)3 * ny * ny) + c.sn * ny * ((T)3 * nx * nx - ny * ny);
+    return c.b * r2 * G;
+  }
+  if (c.kind == K_SHEAR)
+    return c.b * ((T)0.5 * c.c * (dx * dx - dy * dy) + c.sn * dx * dy);
+  if (c.kind == K_NFW) return nfw_potential(dx, dy, c.b, c.irs);
+  const T u = c.round ? dx : c.c * dx + c.sn * dy;
+  const T v = c.round ? dy : c.c * dy - c.sn * dx;
+  T p = sie_potential_uv(u, v, c.q, c.q2, c.e, c.qe, c.s1, c.s1sq, c.q2s1, c.D01, (bool)c.round);
+  if (c.kind == K_DPIE)
+    p -= sie_potential_uv(u, v, c.q, c.q2, c.e, c.qe, c.s2, c.s2sq, c.q2s2, c.D02, (bool)c.round);
+  return c.b * p;
 }
 
 // ------------------------------------------------------- packed member pairs ---

@@ -102,4 +102,24 @@ DUAL_T __device__ __forceinline__ D lf_sin(const D& a) { return chain(a, sin(a.v
 #undef D
 #undef DUAL_T
 
+// Third derivatives (psi_xxx, psi_xxy, psi_xyy, psi_yyy) of one explicit component: psi_ij of
+// the closed form on dual numbers over the offset.
+template <class T>
+LF_INLINE void comp_d3(const CompT<T>& c, T dx, T dy, T (&d3)[4]) {
+  typedef Dual<T, 2> D;
+  Out5<D> o;
+  eval_comp_g<T, D>(c, D::var(dx, 0), D::var(dy, 1), o);
+  d3[0] = o.pxx.d[0]; d3[1] = o.pxx.d[1]; d3[2] = o.pyy.d[0]; d3[3] = o.pyy.d[1];
+}
+
+// The same for one round pseudo-Jaffe member of strength b, core s, cut a.
+template <class T>
+LF_INLINE void member_d3(T dx, T dy, T b, T s, T a, T (&d3)[4]) {
+  typedef Dual<T, 2> D;
+  Out5<D> o;
+  pje_round(D::var(dx, 0), D::var(dy, 1), D(b), D(s), D(s * s), D(a), D(a * a), o);
+  d3[0] = o.pxx.d[0]; d3[1] = o.pxx.d[1]; d3[2] = o.pyy.d[0]; d3[3] = o.pyy.d[1];
+}
+
+
 }  // namespace lf

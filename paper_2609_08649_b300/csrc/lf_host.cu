@@ -93,6 +93,13 @@ extern "C" double lf_arcsec_per_kpc(double H0, double Om, double z) {
   return ARCSEC_PER_RAD / (lf_angular_distance(H0, Om, 0.0, z) * 1000.0);
 }
 
+extern "C" double lf_td_scale(double H0, double Om, double z_d) {
+  constexpr double KM_PER_MPC = 3.0856775814913673e19, S_PER_DAY = 86400.0;
+  const double dd_km = lf_angular_distance(H0, Om, 0.0, z_d) * KM_PER_MPC;
+  const double theta0 = 1.0 / ARCSEC_PER_RAD;
+  return (1.0 + z_d) * dd_km / C_KMS * theta0 * theta0 / S_PER_DAY;
+}
+
 extern "C" double lf_b_from_vdisp(double v_kms) {
   double r = v_kms / C_KMS;
   return 4.0 * M_PI * r * r * ARCSEC_PER_RAD;

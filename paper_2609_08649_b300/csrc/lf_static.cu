@@ -114,6 +114,8 @@ extern "C" lf_status lf_chi2_batch_static(const lf_cluster* cl, const double* th
     return fail(LF_EINVAL, "incomplete image set (1..%d images)", LF_MAX_IMG);
   if (im.fam_off[0] != 0 || im.fam_off[im.n_fam] != im.n_img)
     return fail(LF_EINVAL, "fam_off must run from 0 to n_img");
+  if (im.mag || im.td)
+    return fail(LF_EUNSUPPORTED, "the static entry point has no flux or time-delay terms (use a plan)");
   for (int f = 0; f < im.n_fam; ++f)
     if (im.fam_off[f + 1] <= im.fam_off[f]) return fail(LF_EINVAL, "family %d is empty", f);
   for (int i = 0; i < im.n_img; ++i) {

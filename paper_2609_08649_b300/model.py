@@ -25,6 +25,11 @@ def adis(cosmo, z_l, z_s):
     return L.lib.lf_adis(cosmo.H0, cosmo.Om, z_l, z_s)
 
 
+def td_scale(cosmo, z_d):
+    """(1 + z_d) D_d theta_0^2 / c in days (the library's cosmology)."""
+    return L.lib.lf_td_scale(cosmo.H0, cosmo.Om, z_d)
+
+
 def arcsec_per_kpc(cosmo, z):
     return L.lib.lf_arcsec_per_kpc(cosmo.H0, cosmo.Om, z)
 
@@ -131,7 +136,7 @@ def multiplane_ratios(cosmo, zs_planes, z_s):
     return r
 
 
-def cluster_input(wl: W.Workload, cat: W.Catalogue, sigma_pos=None, device="cuda"):
+def cluster_input(wl: W.Workload, cat: W.Catalogue, sigma_pos=None, device="cuda", aux=None):
     """ClusterInput for a workload and its image catalogue: circular S_i = sigma^2 I
     (Eq. chi2_img with sigma_1 = sigma_2), per-family distance ratios from the library's
     cosmology, and the parameter map of the workload."""
@@ -151,5 +156,6 @@ def cluster_input(wl: W.Workload, cat: W.Catalogue, sigma_pos=None, device="cuda
     p_comp = [p.comp for p in wl.params]
     p_field = [p.field for p in wl.params]
     p_xform = [p.xform for p in wl.params]
+    ts = td_scale(wl.cosmo, zl[0]) if aux is not None else 0.0
     return ClusterInput(planes, apk, cat.theta_obs, sinv, cat.fam_off, fam_ratio, p_comp, p_field,
-                        p_xform, ratios)
+                        p_xform, ratios, aux=aux, td_scale=ts)
