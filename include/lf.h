@@ -300,6 +300,20 @@ lf_status lf_mh_run(lf_plan* plan, double* chains, double* chi2, int32_t S, int3
                     const double* lo, const double* hi, double* trace,
                     unsigned long long* n_accept, void* stream);
 
+/* Multi-start Nelder-Mead downhill simplex (Nelder & Mead 1965; the paper's optimizer,
+ * Sec. 3.5) for M independent runs on a single-cluster plan, minimising the plan's chi^2 with
+ * chi^2 = +inf outside the prior box [lo, hi].  Coefficients and rules of Lagarias et al.
+ * (1998): each iteration orders a run's P + 1 vertices stably by chi^2, reflects the worst
+ * through the centroid of the others (summed in vertex order), then expands (2), contracts
+ * outside or inside (1/2) or shrinks towards the best vertex (1/2); vector arithmetic is one
+ * IEEE operation per component.  simplex: device [M * (P+1) * P] in/out; fvals: device
+ * [M * (P+1)] in/out, the vertices' chi^2 on entry (finite or +inf); steps: device [5]
+ * counters of reflections, expansions, outside and inside contractions and shrinks added to,
+ * or NULL.  1 <= M <= max_samples.  Synchronises the stream once per iteration (to learn
+ * whether some run shrinks).  The first call allocates the workspace inside the plan. */
+lf_status lf_nm_run(lf_plan* plan, double* simplex, double* fvals, int32_t M, int32_t n_iter,
+                    const double* lo, const double* hi, unsigned long long* steps, void* stream);
+
 lf_status lf_plan_destroy(lf_plan* plan);
 
 /* lf_chi2_batch for one cluster with no device allocation (the paper has no counterpart;

@@ -80,6 +80,7 @@ def _load():
         "lf_chi2_img_batch": [vp, vp, i32, i32, vp, vp, vp],
         "lf_aies_run": [vp, vp, vp, i32, i32, vp, f64, vp, vp, vp, vp, vp],
         "lf_mh_run": [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp],
+        "lf_nm_run": [vp, vp, vp, i32, i32, vp, vp, vp, vp],
         "lf_chi2_batch_static": [vp, vp, i32, i32, vp, vp],
         "lf_plan_info": [vp, vp, vp, vp],
         "lf_nfw_params": [f64, f64, f64, f64, f64, vp, vp],
@@ -108,7 +109,7 @@ lib = _load()
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTS = ["lf_deflect_grid", "lf_jacobian_grid", "lf_jacobian_points", "lf_trace_multiplane",
            "lf_plan_create", "lf_chi2_batch", "lf_chi2_grad_batch", "lf_plan_destroy",
-           "lf_chi2_img_batch", "lf_aies_run", "lf_mh_run", "lf_find_images", "lf_find_images_workspace",
+           "lf_chi2_img_batch", "lf_aies_run", "lf_mh_run", "lf_nm_run", "lf_find_images", "lf_find_images_workspace",
            "lf_chi2_batch_static",
            "lf_plan_info", "lf_angular_distance", "lf_adis", "lf_arcsec_per_kpc",
            "lf_b_from_vdisp", "lf_td_scale", "lf_nfw_params", "lf_device_error", "lf_last_error", "lf_version"]

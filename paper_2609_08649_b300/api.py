@@ -248,6 +248,19 @@ class Plan:
                                 _stream()))
         return acc, tr
 
+    def nm_run(self, simplex: torch.Tensor, fvals: torch.Tensor, n_iter: int, lo: torch.Tensor,
+               hi: torch.Tensor):
+        """Nelder-Mead iterations in place on simplex (M, P+1, P) and fvals (M, P+1) (the
+        vertices' chi^2).  Returns the step counts (reflect, expand, outside contraction,
+        inside contraction, shrink)."""
+        simplex = _dev64(simplex, "simplex", True)
+        fvals = _dev64(fvals, "fvals", True)
+        lo, hi = _dev64(lo, "lo"), _dev64(hi, "hi")
+        steps = torch.zeros(5, dtype=torch.int64, device="cuda")
+        L.check(L.lib.lf_nm_run(self.handle, _ptr(simplex), _ptr(fvals), simplex.shape[0], int(n_iter),
+                                _ptr(lo), _ptr(hi), _ptr(steps), _stream()))
+        return steps
+
     def info(self):
         ks, blk, g = C.c_int32(), C.c_int32(), C.c_int32()
         L.check(L.lib.lf_plan_info(self.handle, C.byref(ks), C.byref(blk), C.byref(g)))

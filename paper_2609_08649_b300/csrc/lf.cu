@@ -7,4 +7,5 @@
 #include "lf_trace.cu"
 #include "lf_chi2.cu"
 #include "lf_sampler.cu"
+#include "lf_optimizer.cu"
 #include "lf_static.cu"

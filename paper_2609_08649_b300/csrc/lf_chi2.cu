@@ -1049,8 +1049,16 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
 // ======================================================================= host =======
 using namespace lf;
 
+// Nelder-Mead workspace (allocated on the first lf_nm_run, for max_samples runs).
+struct NmWork {
+  double *tmp = nullptr, *xb = nullptr, *xr = nullptr, *fr = nullptr, *x2 = nullptr,
+         *f2 = nullptr, *shrink = nullptr, *fs = nullptr;
+  int *step = nullptr, *flag = nullptr, *flag_host = nullptr;   // flag_host: pinned
+};
+
 struct lf_plan {
   int n_clusters = 0, P = 0, precision = LF_MIXED, flags = 0, max_samples = 0;
+  NmWork nm;
   bool single_plane = true;
   bool has_aux = false;            // some cluster carries flux / time-delay measurements
   std::vector<ClusterDesc> desc;
@@ -1459,6 +1467,27 @@ static void launch_img(lf_plan* pl, const double* theta, int S, int iters, doubl
                                                          pl->d_free_dig, nullptr, iters, rms);
 }
 
+static lf_status ensure_nm_workspace(lf_plan* pl, int M) {
+  if (pl->nm.xb) return LF_OK;
+  const size_t m = (size_t)pl->max_samples, P = (size_t)pl->P;
+  void* p = nullptr;
+  NmWork& w = pl->nm;
+  LF_TRY(plan_alloc(pl, &p, m * (P + 1) * P * sizeof(double))); w.tmp = (double*)p;
+  LF_TRY(plan_alloc(pl, &p, m * P * sizeof(double))); w.xb = (double*)p;
+  LF_TRY(plan_alloc(pl, &p, m * P * sizeof(double))); w.xr = (double*)p;
+  LF_TRY(plan_alloc(pl, &p, m * P * sizeof(double))); w.x2 = (double*)p;
+  LF_TRY(plan_alloc(pl, &p, m * sizeof(double))); w.fr = (double*)p;
+  LF_TRY(plan_alloc(pl, &p, m * sizeof(double))); w.f2 = (double*)p;
+  LF_TRY(plan_alloc(pl, &p, m * P * P * sizeof(double))); w.shrink = (double*)p;
+  LF_TRY(plan_alloc(pl, &p, m * P * sizeof(double))); w.fs = (double*)p;
+  LF_TRY(plan_alloc(pl, &p, m * sizeof(int))); w.step = (int*)p;
+  LF_TRY(plan_alloc(pl, &p, sizeof(int))); w.flag = (int*)p;
+  LF_CUDA(cudaMallocHost(&p, sizeof(int)));
+  w.flag_host = (int*)p;
+  (void)M;
+  return LF_OK;
+}
+
 static lf_status ensure_sampler_workspace(lf_plan* pl) {
   if (pl->d_prop) return LF_OK;
   const size_t h = (size_t)pl->max_samples;
@@ -1559,6 +1588,7 @@ extern "C" lf_status lf_plan_destroy(lf_plan* pl) {
   if (pl->ev_out) cudaEventDestroy(pl->ev_out);
   if (pl->gstream) cudaStreamDestroy(pl->gstream);
   for (void* p : pl->allocs) cudaFree(p);
+  if (pl->nm.flag_host) cudaFreeHost(pl->nm.flag_host);
   delete pl;
   return LF_OK;
 }
