@@ -272,9 +272,14 @@ def main():
     fp32_ach = evals * FP32_INSTR_PER_EVAL / (ms * 1e-3) / 1e12
     xu_ach = evals * XU_INSTR_PER_EVAL / (ms * 1e-3) / 1e12
     traffic = map_kernel_traffic() if args.precision == "mixed" and args.grid == 4096 else None
+    fma_s, rsq_s, dfma_s = api.probe_alu()
     roofline = {"bound": "alu", "achieved": fp32_ach, "peak": fp32_peak, "unit": "T FP32 lane-ops/s",
                 "frac": fp32_ach / fp32_peak, "traffic": traffic,
                 "xu": {"achieved": xu_ach, "peak": xu_peak, "frac": xu_ach / xu_peak},
+                "measured_rates": {"fp32_fma_T_per_s": fma_s / 1e12, "mufu_rsqrt_T_per_s": rsq_s / 1e12,
+                                   "fp64_fma_T_per_s": dfma_s / 1e12,
+                                   "frac_of_measured_fp32": fp32_ach / (fma_s / 1e12),
+                                   "frac_of_measured_xu": xu_ach / (rsq_s / 1e12)},
                 "hbm_achieved_gbs": d2h / (ms * 1e-3) / 1e9,
                 "peak_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max/1e6:.0f} MHz (max SM clock)"}
 

@@ -354,6 +354,14 @@ double lf_b_from_vdisp(double v_kms);
 lf_status lf_nfw_params(double H0, double Om, double z_l, double m200, double conc,
                         double* kappa_s, double* theta_s);
 
+/* Measured arithmetic rates of the current GPU (the roofline denominators of the
+ * lens-equation kernels): FP32 fused multiply-adds, MUFU reciprocal square roots and FP64
+ * fused multiply-adds per second, each from a kernel of independent dependency chains on
+ * every SM timed with CUDA events on `stream` (synchronises it; allocates and frees a
+ * scratch buffer). */
+lf_status lf_probe_alu(double* fp32_fma_per_s, double* mufu_rsqrt_per_s, double* fp64_fma_per_s,
+                       void* stream);
+
 /* Reads and clears the device error word (waits for `stream`): LF_OK or LF_ETIMEOUT. */
 lf_status lf_device_error(void* stream);
 

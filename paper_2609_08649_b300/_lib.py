@@ -81,6 +81,7 @@ def _load():
         "lf_aies_run": [vp, vp, vp, i32, i32, vp, f64, vp, vp, vp, vp, vp],
         "lf_mh_run": [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp],
         "lf_nm_run": [vp, vp, vp, i32, i32, vp, vp, vp, vp],
+        "lf_probe_alu": [vp, vp, vp, vp],
         "lf_chi2_batch_static": [vp, vp, i32, i32, vp, vp],
         "lf_plan_info": [vp, vp, vp, vp],
         "lf_nfw_params": [f64, f64, f64, f64, f64, vp, vp],
@@ -112,7 +113,7 @@ EXPORTS = ["lf_deflect_grid", "lf_jacobian_grid", "lf_jacobian_points", "lf_trac
            "lf_chi2_img_batch", "lf_aies_run", "lf_mh_run", "lf_nm_run", "lf_find_images", "lf_find_images_workspace",
            "lf_chi2_batch_static",
            "lf_plan_info", "lf_angular_distance", "lf_adis", "lf_arcsec_per_kpc",
-           "lf_b_from_vdisp", "lf_td_scale", "lf_nfw_params", "lf_device_error", "lf_last_error", "lf_version"]
+           "lf_b_from_vdisp", "lf_td_scale", "lf_nfw_params", "lf_device_error", "lf_probe_alu", "lf_last_error", "lf_version"]
 
 
 def check(status):

@@ -121,6 +121,13 @@ def find_images_workspace(grid, n_src, max_img=8):
     return int(L.lib.lf_find_images_workspace(grid.nx, grid.ny, n_src, max_img))
 
 
+def probe_alu():
+    """Measured (FP32 FMA, MUFU rsqrt, FP64 FMA) operations per second of the current GPU."""
+    r = [C.c_double() for _ in range(3)]
+    L.check(L.lib.lf_probe_alu(*[C.byref(v) for v in r], _stream()))
+    return tuple(v.value for v in r)
+
+
 def device_error():
     L.check(L.lib.lf_device_error(_stream()))
 

@@ -9,3 +9,4 @@
 #include "lf_sampler.cu"
 #include "lf_optimizer.cu"
 #include "lf_static.cu"
+#include "lf_probe.cu"
