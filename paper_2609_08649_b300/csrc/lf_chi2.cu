@@ -316,6 +316,12 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
   typedef typename std::conditional<MIXED, float, double>::type T;
   typedef typename std::conditional<MODE == LF_MIXED, MemPreF, MemPreD>::type MemPre;
   typedef typename std::conditional<MODE == LF_FF, MemX, MemT<T>>::type Mem;
+  // the mixed tier's forward passes evaluate members two at a time (packed pair records, f32x2);
+  // the adjoint and the flux / time-delay pass read the scalar records
+  constexpr bool PACKM = (MODE == LF_MIXED) && !GRAD && PASS != 2;
+  // images per evaluation task (two independent chains per thread; with packed members, four
+  // member evaluations per pair of instructions)
+  constexpr int IPT = 2;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   int* s_item = reinterpret_cast<int*>(smem + 8);
@@ -420,7 +426,15 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
       const bool alpha_free = sampled && C.scal_p[LF_S_ALPHA] >= 0;
       const MemPre* mp = reinterpret_cast<const MemPre*>(P.mpre);   // plan table, L2-resident
       Mem* dm = reinterpret_cast<Mem*>(smem + P.off_dm);
-      for (int i = tid; i < P.nm; i += blockDim.x) {
+      const int n_lanes = PACKM ? 2 * (int)mem_records<MemPair>(P.nm) : P.nm;
+      for (int i = tid; i < n_lanes; i += blockDim.x) {
+        if constexpr (PACKM) {
+          MemPair* dp = reinterpret_cast<MemPair*>(smem + P.off_dm);
+          if (i >= P.nm) {      // zero-strength pad of an odd member count
+            pair_lane(dp[i >> 1], i & 1, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 2.f);
+            continue;
+          }
+        }
         const MemPre& m = mp[i];
         if constexpr (MODE == LF_FF) {
           const double fb = lam_free ? exp(2.0 * sc.lam * m.lnl) : m.fb;
@@ -454,7 +468,11 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
           d.loglr = (T)m.lnl;
           d.pad0 = (T)0;
           d.pad1 = (T)0;
-          dm[i] = d;
+          if constexpr (PACKM)
+            pair_lane(reinterpret_cast<MemPair*>(smem + P.off_dm)[i >> 1], i & 1, d.xh, d.xl, d.yh, d.yl,
+                      d.b, d.s, d.a);
+          else
+            dm[i] = d;
         }
       }
     }
@@ -464,15 +482,15 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
     // component slice): two images per thread give two independent evaluation chains.
     const int n_img = C.n_img, KS = C.ks, IS = C.img_stride, ISF = C.img_stride_f,
               ISD = C.img_stride_d;
-    const int n_pair = (n_img + 1) >> 1;
-    const int ntask = n_pair * KS;
+    const int n_unit = IPT == 2 ? (n_img + 1) >> 1 : n_img;
+    const int ntask = n_unit * KS;
     // pos: null = the observed images; else positions (x, y) at pos[4 i], pos[4 i + 1]
     auto eval_planes = [&](const double* pos) {
     for (int j = 0; j < C.np; ++j) {
       const PlaneDesc& P = C.pl[j];
       const CompT<T>* dc = reinterpret_cast<const CompT<T>*>(smem + P.off_dc);
       const Mem* dm = reinterpret_cast<const Mem*>(smem + P.off_dm);
-      const int K = P.nc + P.nm;
+      const int K = P.nc + (PACKM ? (int)mem_records<MemPair>(P.nm) : P.nm);   // slices of these units
       for (int base = 0; base < ntask; base += blockDim.x) {
         const int t = base + tid;
         const bool act = t < ntask;
@@ -481,10 +499,12 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
         const int ia = 2 * pr, ib = min(2 * pr + 1, n_img - 1);
         const int k0 = (int)((long long)K * k / KS), k1 = (int)((long long)K * (k + 1) / KS);
         if constexpr (MIXED) {
-          float xh[2], xl[2], yh[2], yl[2];
-          const int ii[2] = {ia, ib};
+          float xh[IPT], xl[IPT], yh[IPT], yl[IPT];
+          int ii[IPT];
+          ii[0] = IPT * pr;
+          if constexpr (IPT == 2) ii[1] = min(2 * pr + 1, n_img - 1);
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
+          for (int q = 0; q < IPT; ++q) {
             if (j == 0 && !pos) {
               const float4 tf = C.theta_ff[ii[q]];
               xh[q] = tf.x; xl[q] = tf.y; yh[q] = tf.z; yl[q] = tf.w;
@@ -496,35 +516,40 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
               split_ff(imgd[ii[q] * ISD + 1], yh[q], yl[q]);
             }
           }
-          ff acc[5][2];
+          ff acc[5][IPT];
 #pragma unroll
-          for (int c5 = 0; c5 < 5; ++c5) acc[c5][0] = acc[c5][1] = ff_zero();
+          for (int c5 = 0; c5 < 5; ++c5)
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) acc[c5][q] = ff_zero();
           if (act) {
             if constexpr (MODE == LF_FF)
-              accumulate_ext<2>(dc, P.nc, dm, P.nm, k0, k1, xh, xl, yh, yl, tab, acc);
+              accumulate_ext<IPT>(dc, P.nc, dm, P.nm, k0, k1, xh, xl, yh, yl, tab, acc);
             else
-              accumulate_mixed<2>(dc, P.nc, dm, P.nm, k0, k1, chunk, xh, xl, yh, yl, tab, acc);
+              if constexpr (PACKM)
+                accumulate_packed<IPT>(dc, P.nc, reinterpret_cast<const MemPair*>(smem + P.off_dm), P.nm,
+                                       k0, k1, chunk, xh, xl, yh, yl, tab, acc);
+              else
+                accumulate_mixed<IPT>(dc, P.nc, dm, P.nm, k0, k1, chunk, xh, xl, yh, yl, tab, acc);
           }
           for (int off = 1; off < KS; off <<= 1)
 #pragma unroll
             for (int c5 = 0; c5 < 5; ++c5)
 #pragma unroll
-              for (int q = 0; q < 2; ++q) {
+              for (int q = 0; q < IPT; ++q) {
                 ff o;
                 o.hi = __shfl_xor_sync(0xffffffffu, acc[c5][q].hi, off);
                 o.lo = __shfl_xor_sync(0xffffffffu, acc[c5][q].lo, off);
                 acc[c5][q] = ff_add(acc[c5][q], o);
               }
           if (act && k == 0) {
-            for (int c5 = 0; c5 < 5; ++c5) {
-              imgf[ia * ISF + 2 * c5] = acc[c5][0].hi;
-              imgf[ia * ISF + 2 * c5 + 1] = acc[c5][0].lo;
-            }
-            if (ib != ia)
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+              if (q > 0 && ii[q] == ii[0]) break;
               for (int c5 = 0; c5 < 5; ++c5) {
-                imgf[ib * ISF + 2 * c5] = acc[c5][1].hi;
-                imgf[ib * ISF + 2 * c5 + 1] = acc[c5][1].lo;
+                imgf[ii[q] * ISF + 2 * c5] = acc[c5][q].hi;
+                imgf[ii[q] * ISF + 2 * c5 + 1] = acc[c5][q].lo;
               }
+            }
           }
         } else {
           double v[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
@@ -1127,13 +1152,13 @@ static int pow2_floor(int v) {
 
 // Component slices per image: the power of two minimising a simple cost model of one work
 // item, rounds x (components per slice + per-task overhead), capped by the tuner's choice.
-static int choose_ks(int n_img, int K, int block, int cap) {
+static int choose_ks(int n_img, int K, int block, int cap, int ipt) {
   const double overhead = 24.0;   // task set-up and shuffle reduction, in component evaluations
   int best = 1;
   double best_cost = 1e300;
   for (int ks = 1; ks <= 32 && ks <= cap; ks *= 2) {
     if (ks > 1 && K / ks < 8) break;
-    long long tasks = (long long)((n_img + 1) / 2) * ks;   // image pairs x slices
+    long long tasks = (long long)((n_img + ipt - 1) / ipt) * ks;   // image groups x slices
     long long rounds = (tasks + block - 1) / block;
     double cost = (double)rounds * ((double)K / ks + overhead);
     if (cost < best_cost * 0.97) { best_cost = cost; best = ks; }
@@ -1212,7 +1237,9 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
     o = (o + 15u) & ~15u; P.off_rawc = o; o += (uint32_t)P.nc * 64u;
     P.off_mpre = 0;   // the member pre-table is read from global memory, not staged
     o = (o + 15u) & ~15u; P.off_dc = o; o += (uint32_t)P.nc * (mixed ? sizeof(CompT<float>) : sizeof(CompT<double>));
-    o = (o + 15u) & ~15u; P.off_dm = o; o += (uint32_t)P.nm * mem_sz;
+    o = (o + 15u) & ~15u; P.off_dm = o;
+    o += std::max((uint32_t)P.nm * mem_sz,            // scalar records, or the mixed tier's pairs
+                  mixed ? mem_records<MemPair>(P.nm) * (uint32_t)sizeof(MemPair) : 0u);
   }
   C.img_stride = C.np > 1 ? 16 + 6 * C.np : 14;
   C.img_stride_f = IMGF;
@@ -1232,7 +1259,7 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
   C.smem = (o + 15u) & ~15u;
   int K = 0;
   for (int j = 0; j < C.np; ++j) K = std::max(K, C.pl[j].nc + C.pl[j].nm);
-  C.ks = choose_ks(C.n_img, K, block, ks_cap);
+  C.ks = choose_ks(C.n_img, K, block, ks_cap, 2);
 }
 
 static lf_status relayout(lf_plan* pl) {
@@ -1526,6 +1553,7 @@ static lf_status autotune(lf_plan* pl, const double* theta, int S, double* chi2,
   int bb = pl->block, bc = pl->ks_cap;
   for (int b : blocks)
     for (int cap : caps) {
+      if (b > LF_CHI2_THREADS) continue;   // beyond the kernels' launch bounds
       pl->block = b;
       pl->ks_cap = cap;
       if (relayout(pl) != LF_OK) continue;

@@ -102,14 +102,15 @@ __device__ inline void digest_plane_pairs(const lf_comp* rawc, int nc, const lf_
 
 // LF_MIXED with packed member pairs: explicit components as in accumulate_mixed; members two
 // at a time (f32x2), `chunk` pairs per FP32 partial sum, each folded into the float-float
-// accumulators.
+// accumulators.  [k0, k1) counts explicit components first, then member pairs.
 template <int PPT>
 __device__ __forceinline__ void accumulate_packed(const CompT<float>* dc, int nc, const MemPair* dp,
-                                                  int nm, int chunk, const float* pxh,
-                                                  const float* pxl, const float* pyh,
-                                                  const float* pyl, const float2* tab,
-                                                  ff (&acc)[5][PPT]) {
-  for (int c = 0; c < nc; ++c) {
+                                                  int nm, int k0, int k1, int chunk,
+                                                  const float* pxh, const float* pxl,
+                                                  const float* pyh, const float* pyl,
+                                                  const float2* tab, ff (&acc)[5][PPT]) {
+  const int c1 = min(k1, nc);
+  for (int c = k0; c < c1; ++c) {
     const CompT<float>& C = dc[c];
     if (C.kind == 0) continue;
 #pragma unroll
@@ -129,8 +130,9 @@ __device__ __forceinline__ void accumulate_packed(const CompT<float>* dc, int nc
     qyh[k] = make_float2(pyh[k], pyh[k]); qyl[k] = make_float2(pyl[k], pyl[k]);
   }
   const int np = (int)mem_records<MemPair>(nm);
-  for (int j0 = 0; j0 < np; j0 += chunk) {
-    const int j1 = min(j0 + chunk, np);
+  const int j_beg = max(k0, nc) - nc, j_end = min(k1, nc + np) - nc;
+  for (int j0 = j_beg; j0 < j_end; j0 += chunk) {
+    const int j1 = min(j0 + chunk, j_end);
     float2 cs[PPT][6];
 #pragma unroll
     for (int k = 0; k < PPT; ++k)
@@ -155,6 +157,16 @@ __device__ __forceinline__ void accumulate_packed(const CompT<float>* dc, int nc
       ff_acc(acc[4][k], cs[k][4].x + cs[k][4].y);
     }
   }
+}
+
+// Writes one member (FP32 fields: float-float centre, strength b, core s, cut a) into lane
+// `lane` of a packed pair record, with the same derived constants as the scalar record.
+__device__ __forceinline__ void pair_lane(MemPair& p, int lane, float xh, float xl, float yh, float yl,
+                                          float b, float s, float a) {
+  float* f = reinterpret_cast<float*>(&p) + lane;     // field k of the lane at f[2 k]
+  f[0] = -xh; f[2] = -xl; f[4] = -yh; f[6] = -yl;
+  f[8] = s * s; f[10] = a * a; f[12] = s; f[14] = a;
+  f[16] = a + s; f[18] = b * (a - s); f[20] = b; f[22] = 0.f;
 }
 
 // Float-float tier: every deflection in float-float, accumulated in float-float.

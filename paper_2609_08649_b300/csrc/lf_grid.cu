@@ -120,7 +120,9 @@ __global__ void __launch_bounds__(256, PACK ? LF_MAP_MINB_PACK : LF_MAP_MINB) k_
       for (int k = 0; k < PPT; ++k) acc[v][k] = ff_zero();
 
     if constexpr (EXT) accumulate_ext<PPT>(dc, nc, dm, nm, 0, nc + nm, pxh, pxl, pyh, pyl, tab, acc);
-    else if constexpr (PACK) accumulate_packed<PPT>(dc, nc, dm, nm, chunk, pxh, pxl, pyh, pyl, tab, acc);
+    else if constexpr (PACK)
+      accumulate_packed<PPT>(dc, nc, dm, nm, 0, nc + (int)mem_records<MemPair>(nm), chunk, pxh, pxl,
+                             pyh, pyl, tab, acc);
     else accumulate_mixed<PPT>(dc, nc, dm, nm, 0, nc + nm, chunk, pxh, pxl, pyh, pyl, tab, acc);
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
