@@ -253,9 +253,12 @@ lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, int32_t n_cl
 lf_status lf_chi2_batch(lf_plan* plan, const double* theta, int32_t S, double* chi2,
                         void* stream);
 
-/* chi^2 and its gradient d chi^2 / d theta (device [S * P] FP64).  Single-plane plans
- * only (LF_EUNSUPPORTED otherwise).  The source position is held at its optimum
- * (d chi^2 / d beta_model = 0), so only the explicit dependence is differentiated. */
+/* chi^2 and its gradient d chi^2 / d theta (device [S * P] FP64).  The source position is
+ * held at its optimum (d chi^2 / d beta_model = 0), so only the explicit dependence is
+ * differentiated.  Multi-plane plans run the adjoint of the recursion of Sec. 2.2 (reverse
+ * sweep over the planes with the third derivatives of psi at every later plane's ray
+ * positions); their per-image records must fit in shared memory next to the forward state
+ * (LF_EUNSUPPORTED otherwise).  Plans with flux or time-delay terms: LF_EUNSUPPORTED. */
 lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int32_t S, double* chi2,
                              double* grad, void* stream);
 

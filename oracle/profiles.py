@@ -40,7 +40,12 @@ def sie(dx, dy, b, q, pa, s):
       psi_uu = (b q / psi~) (q^2 s^2 + v^2 + s psi~) / D,
       psi_vv = (b q / psi~) (s^2 + u^2 + s psi~) / D,
       psi_uv = -(b q / psi~) u v / D,    D = (1 + q^2) s^2 + 2 psi~ s + u^2 + v^2.
-    q = 1 takes the limit alpha = b (u, v) / (psi~ + s).
+    q = 1 takes the limit alpha = b (u, v) / (psi~ + s), written to first order in
+    e^2 = 1 - q^2 from the Taylor series of atan and atanh,
+      alpha_u = b q X (1 - e^2 X^2 / 3),  alpha_v = b q Y (1 + e^2 Y^2 / 3),
+      X = u / (psi~ + s),  Y = v / (psi~ + q^2 s),
+    whose value is the limit and whose derivative in q there is exact (the next terms are
+    O(e^4)), so that autograd through the round branch differentiates in eps correctly.
     """
     dx, dy, b, q, pa, s = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64)
                                                      for t in (dx, dy, b, q, pa, s)])
@@ -49,13 +54,15 @@ def sie(dx, dy, b, q, pa, s):
     v = -sn * dx + c * dy
     q2 = q * q
     psi = torch.sqrt(q2 * (s * s + u * u) + v * v)
-    e = torch.sqrt((1.0 - q) * (1.0 + q))
-    round_ = e == 0
-    e_safe = torch.where(round_, torch.ones_like(e), e)
+    e2 = (1.0 - q) * (1.0 + q)
+    round_ = e2 == 0
+    # the square root only of e^2 > 0 (its derivative at 0 is infinite)
+    e_safe = torch.sqrt(torch.where(round_, torch.ones_like(e2), e2))
     au_ell = b * q / e_safe * torch.atan(e_safe * u / (psi + s))
     av_ell = b * q / e_safe * torch.atanh(e_safe * v / (psi + q2 * s))
-    au = torch.where(round_, b * u / (psi + s), au_ell)
-    av = torch.where(round_, b * v / (psi + s), av_ell)
+    X, Y = u / (psi + s), v / (psi + q2 * s)
+    au = torch.where(round_, b * q * X * (1.0 - e2 * X * X / 3.0), au_ell)
+    av = torch.where(round_, b * q * Y * (1.0 + e2 * Y * Y / 3.0), av_ell)
     D = (1.0 + q2) * s * s + 2.0 * psi * s + u * u + v * v
     f = b * q / (psi * D)
     puu = f * (q2 * s * s + v * v + s * psi)

@@ -85,7 +85,9 @@ struct ClusterDesc {
   const float4* theta_ff;          // [n_img] (x_hi, x_lo, y_hi, y_lo)
   const float2* ratio_ff;          // [n_fam * np]
   const float4* sinv_f;            // [n_img] (xx, xy, yy, 0)
-  uint32_t off_img, off_imgd, off_fam, off_par, off_free, off_newton, off_fama, off_aux, smem;
+  int mpg_stride;                  // multi-plane adjoint: doubles per image record
+  uint32_t off_img, off_imgd, off_fam, off_par, off_free, off_newton, off_fama, off_aux, off_mpg, smem;
+  uint32_t smem_grad;              // smem plus the multi-plane adjoint's records
 };
 
 // ------------------------------------------------------------------ transforms -----
@@ -177,25 +179,26 @@ __device__ void comp_dual(const lf_comp& rc, double px, double py, Out5<Dual<T, 
     nfw_sph(dx, dy, DT::cst((T)1), lf_rcp(core), o);
     return;
   }
-  // elliptical form also at eps ~ 0, so that d/d eps exists there
-  double epsv = rc.eps < 1e-6 ? 1e-6 : rc.eps;
-  DT eps = DT::var((T)epsv, 2);
+  // eps = 0 is the round profile, as in the forward pass (sie_uv's q = 1 branch keeps the
+  // exact first derivative in eps); else the elliptical closed form
+  const bool round = rc.eps == 0.0;
+  DT eps = DT::var((T)rc.eps, 2);
   DT one = DT::cst((T)1);
   DT q = (one - eps) / (one + eps);
   DT q2 = q * q;
-  DT e = lf_sqrt((one - q) * (one + q));
-  DT qe = q / e;
+  DT e = round ? DT::cst((T)0) : lf_sqrt((one - q) * (one + q));
+  DT qe = round ? DT::cst((T)0) : q / e;
   DT c = lf_cos(pa), sn = lf_sin(pa);
   DT u = c * dx + sn * dy;
   DT v = c * dy - sn * dx;
   DT au, av, puu, pvv, puv;
   DT s2 = core * core;
-  sie_uv(u, v, q, q2, e, qe, core, s2, q2 * core, (one + q2) * s2, false, au, av, puu, pvv, puv);
+  sie_uv(u, v, q, q2, e, qe, core, s2, q2 * core, (one + q2) * s2, round, au, av, puu, pvv, puv);
   if (rc.kind == LF_DPIE) {
     DT cut = DT::var((T)rc.cut, 5);
     DT c2 = cut * cut;
     DT bu, bv, quu, qvv, quv;
-    sie_uv(u, v, q, q2, e, qe, cut, c2, q2 * cut, (one + q2) * c2, false, bu, bv, quu, qvv, quv);
+    sie_uv(u, v, q, q2, e, qe, cut, c2, q2 * cut, (one + q2) * c2, round, bu, bv, quu, qvv, quv);
     au = au - bu; av = av - bv; puu = puu - quu; pvv = pvv - qvv; puv = puv - quv;
   }
   rotate_back(c, sn, au, av, puu, pvv, puv, o);
@@ -302,6 +305,30 @@ __device__ void aux_sum(const CompT<T>* dc, int nc, const Mem* dm, int nm, int k
   }
   if constexpr (std::is_same<T, float>::value) out[0] = ff_to_double(pf); else out[0] = pd;
   for (int q = 0; q < 4; ++q) out[q + 1] = (double)s3[q];
+}
+
+// The third derivatives of psi alone, summed over [k0, k1) at one position (multi-plane adjoint).
+template <class T, class Mem>
+__device__ void d3_sum(const CompT<T>* dc, int nc, const Mem* dm, int nm, int k0, int k1, T pxh,
+                       T pxl, T pyh, T pyl, double (&out)[4]) {
+  T s3[4] = {(T)0, (T)0, (T)0, (T)0};
+  const int c1 = min(k1, nc);
+  for (int c = k0; c < c1; ++c) {
+    const CompT<T>& C = dc[c];
+    if (C.kind == 0) continue;
+    T d3[4];
+    comp_d3(C, offset_of(pxh, pxl, C.xh, C.xl), offset_of(pyh, pyl, C.yh, C.yl), d3);
+    for (int q = 0; q < 4; ++q) s3[q] += d3[q];
+  }
+  const int m_beg = max(k0, nc) - nc, m_end = min(k1, nc + nm) - nc;
+  for (int m = m_beg; m < m_end; ++m) {
+    T xh, xl, yh, yl, b, sc, ac;
+    mem_geom(dm[m], xh, xl, yh, yl, b, sc, ac);
+    T d3[4];
+    member_d3(offset_of(pxh, pxl, xh, xl), offset_of(pyh, pyl, yh, yl), b, sc, ac, d3);
+    for (int q = 0; q < 4; ++q) s3[q] += d3[q];
+  }
+  for (int q = 0; q < 4; ++q) out[q] = (double)s3[q];
 }
 
 template <int MODE, bool GRAD, int PASS = 0>   // MODE: LF_FP64, LF_MIXED or LF_FF
@@ -593,6 +620,12 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
             const double* pl = st + 2 + 6 * l;
             double rr = C.r[l][j];
             a00 -= rr * pl[2]; a01 -= rr * pl[3]; a10 -= rr * pl[4]; a11 -= rr * pl[5];
+          }
+          if constexpr (GRAD) {       // theta_j and Psi_j for the reverse sweep
+            double* rec = reinterpret_cast<double*>(smem + C.off_mpg) + i * C.mpg_stride + 10 * j;
+            if (j == 0) { rec[0] = C.theta[2 * i]; rec[1] = C.theta[2 * i + 1]; }
+            else { rec[0] = st[0]; rec[1] = st[1]; }
+            rec[2] = sm[2]; rec[3] = sm[3]; rec[4] = sm[4];
           }
           double* pj = st + 2 + 6 * j;
           pj[0] = sm[0]; pj[1] = sm[1];
@@ -938,8 +971,41 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
     if (tid == 0) chi2[s] = total;
 
     if constexpr (GRAD) {
+      double* mpg = reinterpret_cast<double*>(smem + C.off_mpg);
+      const int MPS = C.mpg_stride;
+      if (C.np > 1) {
+        // third derivatives of psi at theta_j of every plane after the first (the positions
+        // theta_j depend on the parameters through the earlier planes' deflections)
+        for (int j = 1; j < C.np; ++j) {
+          const PlaneDesc& P = C.pl[j];
+          const CompT<T>* dc = reinterpret_cast<const CompT<T>*>(smem + P.off_dc);
+          const Mem* dm = reinterpret_cast<const Mem*>(smem + P.off_dm);
+          const int K = P.nc + P.nm, nt = n_img * KS;
+          for (int base = 0; base < nt; base += blockDim.x) {
+            const int t = base + tid;
+            const bool act = t < nt;
+            const int i = act ? t / KS : 0, k = act ? t - i * KS : 0;
+            const int k0 = (int)((long long)K * k / KS), k1 = (int)((long long)K * (k + 1) / KS);
+            double d3[4] = {0, 0, 0, 0};
+            if (act) {
+              const double* rec = mpg + i * MPS + 10 * j;
+              T xh, xl, yh, yl;
+              if constexpr (MIXED) { split_ff(rec[0], xh, xl); split_ff(rec[1], yh, yl); }
+              else { xh = rec[0]; xl = 0.0; yh = rec[1]; yl = 0.0; }
+              d3_sum(dc, P.nc, dm, P.nm, k0, k1, xh, xl, yh, yl, d3);
+            }
+            for (int off = 1; off < KS; off <<= 1)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) d3[q] += __shfl_xor_sync(0xffffffffu, d3[q], off);
+            if (act && k == 0)
+              for (int q = 0; q < 4; ++q) mpg[i * MPS + 10 * C.np + 4 * (j - 1) + q] = d3[q];
+          }
+        }
+        __syncthreads();
+      }
       // cotangents of alpha and Psi at each image: with d = beta_i - beta_model, w = M d,
-      // z = mu d: alpha_bar = -2 a w, Psi_bar = 2 a sym(w z^T)
+      // z = mu d: beta_bar = 2 w, A_bar = -2 w z^T; one plane: alpha_bar = -2 a w,
+      // Psi_bar = 2 a sym(w z^T)
       for (int i = tid; i < n_img; i += blockDim.x) {
         const int f = C.img_fam[i];
         const int n_f = C.fam_off[f + 1] - C.fam_off[f];
@@ -959,9 +1025,52 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
           M00 = r[5]; M01 = r[6]; M11 = r[7];
           u00 = r[10]; u01 = r[11]; u10 = r[12]; u11 = r[13];
         }
-        const double a = fa[f];
         const double w0 = M00 * d0 + M01 * d1, w1 = M01 * d0 + M11 * d1;
         const double z0 = u00 * d0 + u01 * d1, z1 = u10 * d0 + u11 * d1;
+        if (C.np > 1) {
+          // reverse sweep of the recursion theta_{j} = theta - sum_{l<j} r_lj alpha_l,
+          // A_j = I - sum_{l<j} r_lj Psi_l A_l, beta = theta - sum_l r_ls alpha_l,
+          // A = I - sum_l r_ls Psi_l A_l, with P_l = Psi_l A_l:
+          //   P_bar -> Psi_bar_j = P_bar A_j^T, A_bar_j = Psi_j P_bar;
+          //   theta_bar_j = Psi_j alpha_bar_j + Psi_bar_j : d Psi / d theta (at theta_j)
+          double* rec = mpg + i * MPS;
+          const double* stp = MIXED ? imgd + i * ISD + 2 : img + i * IS + 16;   // alpha_l, P_l
+          const double k2 = n_f > 1 ? 2.0 : 0.0;
+          double ab[LF_MAX_PLANES][2], pb[LF_MAX_PLANES][4];
+          for (int l = 0; l < C.np; ++l) {
+            const double rs = k2 * C.fam_ratio[f * C.np + l];
+            ab[l][0] = -rs * w0; ab[l][1] = -rs * w1;
+            pb[l][0] = rs * w0 * z0; pb[l][1] = rs * w0 * z1; pb[l][2] = rs * w1 * z0; pb[l][3] = rs * w1 * z1;
+          }
+          for (int j = C.np - 1; j >= 0; --j) {
+            double a00 = 1, a01 = 0, a10 = 0, a11 = 1;
+            for (int l = 0; l < j; ++l) {
+              const double rr = C.r[l][j];
+              const double* pl = stp + 6 * l;
+              a00 -= rr * pl[2]; a01 -= rr * pl[3]; a10 -= rr * pl[4]; a11 -= rr * pl[5];
+            }
+            double* rj = rec + 10 * j;
+            const double pxx = rj[2], pyy = rj[3], pxy = rj[4];
+            const double* b = pb[j];
+            const double G00 = b[0] * a00 + b[1] * a01, G01 = b[0] * a10 + b[1] * a11;
+            const double G10 = b[2] * a00 + b[3] * a01, G11 = b[2] * a10 + b[3] * a11;
+            const double Gs = G01 + G10;
+            rj[5] = ab[j][0]; rj[6] = ab[j][1]; rj[7] = G00; rj[8] = G11; rj[9] = Gs;
+            if (j == 0) break;
+            const double* d3 = rec + 10 * C.np + 4 * (j - 1);   // xxx, xxy, xyy, yyy
+            const double tbx = pxx * ab[j][0] + pxy * ab[j][1] + G00 * d3[0] + Gs * d3[1] + G11 * d3[2];
+            const double tby = pxy * ab[j][0] + pyy * ab[j][1] + G00 * d3[1] + Gs * d3[2] + G11 * d3[3];
+            const double A00 = pxx * b[0] + pxy * b[2], A01 = pxx * b[1] + pxy * b[3];
+            const double A10 = pxy * b[0] + pyy * b[2], A11 = pxy * b[1] + pyy * b[3];
+            for (int l = 0; l < j; ++l) {
+              const double rr = C.r[l][j];
+              ab[l][0] -= rr * tbx; ab[l][1] -= rr * tby;
+              pb[l][0] -= rr * A00; pb[l][1] -= rr * A01; pb[l][2] -= rr * A10; pb[l][3] -= rr * A11;
+            }
+          }
+          continue;
+        }
+        const double a = fa[f];
         const double k2a = n_f > 1 ? 2.0 * a : 0.0;
         double cot[5] = {-k2a * w0, -k2a * w1, k2a * w0 * z0, k2a * w1 * z1, k2a * (w0 * z1 + w1 * z0)};
         if (fap[f] >= 0 && n_f > 1) {
@@ -988,10 +1097,12 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
         }
       }
       __syncthreads();
-      const PlaneDesc& P = C.pl[0];
+      // contraction with each plane's components at theta_j
+      for (int j = 0; j < C.np; ++j) {
+      const PlaneDesc& P = C.pl[j];
       const Mem* dm = reinterpret_cast<const Mem*>(smem + P.off_dm);
       const int K = P.nc + P.nm;
-      const bool mem_grad = (C.scal_plane == 0) && C.scal_free;
+      const bool mem_grad = (C.scal_plane == j) && C.scal_free;
       lf_scaling ssc = P.sc;
       if (mem_grad) sample_scaling(C, th, ssc);
       const T inv_cut_star = (T)(1.0 / ssc.cut_star);
@@ -1000,15 +1111,22 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
         const int i = t / KS, k = t - i * KS;
         const int k0 = (int)((long long)K * k / KS), k1 = (int)((long long)K * (k + 1) / KS);
         T cot[5];
-        if constexpr (MIXED) {
-          for (int q = 0; q < 5; ++q) cot[q] = imgf[i * ISF + q];
+        double px, py;
+        if (C.np > 1) {
+          const double* rj = mpg + i * MPS + 10 * j;
+          for (int q = 0; q < 5; ++q) cot[q] = (T)rj[5 + q];
+          px = rj[0]; py = rj[1];
         } else {
-          for (int q = 0; q < 5; ++q) cot[q] = img[i * IS + q];
+          if constexpr (MIXED) {
+            for (int q = 0; q < 5; ++q) cot[q] = imgf[i * ISF + q];
+          } else {
+            for (int q = 0; q < 5; ++q) cot[q] = img[i * IS + q];
+          }
+          px = C.theta[2 * i]; py = C.theta[2 * i + 1];
         }
-        const double px = C.theta[2 * i], py = C.theta[2 * i + 1];
         for (int f = 0; f < C.n_free; ++f) {
           const int kc = C.free_comp[f];
-          if (C.free_plane[f] != 0 || kc < k0 || kc >= k1) continue;
+          if (C.free_plane[f] != j || kc < k0 || kc >= k1) continue;
           const lf_comp& rc = fraw[f];
           if (rc.kind < 1 || rc.kind > 5) continue;
           Out5<Dual<T, 6>> o;
@@ -1062,6 +1180,7 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
           }
         }
       }
+      }
       __syncthreads();
       for (int p = tid; p < C.P; p += blockDim.x) grad[(size_t)s * C.P + p] = gacc[p];
     }
@@ -1105,6 +1224,7 @@ struct lf_plan {
   int ks_cap = 32;
   bool tuned = false;
   uint32_t smem = 0;
+  uint32_t smem_grad = 0;          // gradient launches (0: the plan has no gradient kernel)
   int grid_chi2 = 0, grid_grad = 0, grid_aux = 0;
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -1256,7 +1376,14 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
   o = (o + 15u) & ~15u; C.off_fama = o; o += (uint32_t)C.n_fam * (8u + 8u + 4u);
   // flux / time-delay pass: per image psi, the third derivatives, then y_i and d_i
   o = (o + 15u) & ~15u; C.off_aux = o; o += C.aux ? (uint32_t)C.n_img * 6u * 8u : 0u;
-  C.smem = (o + 15u) & ~15u;
+  o = (o + 15u) & ~15u;
+  C.smem = o;
+  // multi-plane adjoint (gradient launches only): per image and plane the position theta_j
+  // (2), Psi_j (3) and the cotangents of (alpha_j, Psi_j) (5); then the third derivatives of
+  // psi (4) at every plane after the first
+  C.off_mpg = o;
+  C.mpg_stride = C.np > 1 ? 10 * C.np + 4 * (C.np - 1) : 0;
+  C.smem_grad = o + (uint32_t)C.n_img * (uint32_t)C.mpg_stride * 8u;
   int K = 0;
   for (int j = 0; j < C.np; ++j) K = std::max(K, C.pl[j].nc + C.pl[j].nm);
   C.ks = choose_ks(C.n_img, K, block, ks_cap, 2);
@@ -1264,18 +1391,21 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
 
 static lf_status relayout(lf_plan* pl) {
   pl->smem = 0;
+  pl->smem_grad = 0;
   for (auto& C : pl->desc) {
     layout_cluster(C, pl->precision, pl->block, pl->ks_cap);
     pl->smem = std::max(pl->smem, C.smem);
+    pl->smem_grad = std::max(pl->smem_grad, C.smem_grad);
   }
   if (pl->smem > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "cluster too large for shared memory (%u B)", pl->smem);
+  if (pl->smem_grad > LF_SMEM_MAX) pl->smem_grad = 0;   // the gradient is refused at call time
   LF_CUDA(cudaMemcpy(pl->d_desc, pl->desc.data(), pl->desc.size() * sizeof(ClusterDesc),
                      cudaMemcpyHostToDevice));
   int dev = 0, nsm = 0, occ = 0;
   LF_CUDA(cudaGetDevice(&dev));
   LF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  auto kset = [&](const void* k) -> lf_status {
-    LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem));
+  auto kset = [&](const void* k, uint32_t bytes) -> lf_status {
+    LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared));
     return LF_OK;
@@ -1292,18 +1422,21 @@ static lf_status relayout(lf_plan* pl) {
   const void* ka = pl->precision == LF_MIXED ? (const void*)k_chi2<LF_MIXED, false, 2>
                    : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, false, 2>
                                              : (const void*)k_chi2<LF_FP64, false, 2>;
-  LF_TRY(kset(kc));
-  LF_TRY(kset(kg));
-  LF_TRY(kset(ki));
+  LF_TRY(kset(kc, pl->smem));
+  LF_TRY(kset(ki, pl->smem));
   if (pl->has_aux) {
-    LF_TRY(kset(ka));
+    LF_TRY(kset(ka, pl->smem));
     LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ka, pl->block, pl->smem));
     pl->grid_aux = nsm * std::max(occ, 1);
   }
   LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kc, pl->block, pl->smem));
   pl->grid_chi2 = nsm * std::max(occ, 1);
-  LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kg, pl->block, pl->smem));
-  pl->grid_grad = nsm * std::max(occ, 1);
+  pl->grid_grad = 0;
+  if (pl->smem_grad > 0) {
+    LF_TRY(kset(kg, pl->smem_grad));
+    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kg, pl->block, pl->smem_grad));
+    pl->grid_grad = nsm * std::max(occ, 1);
+  }
   if (pl->gexec) {
     cudaGraphExecDestroy(pl->gexec);
     pl->gexec = nullptr;
@@ -1465,7 +1598,7 @@ static void launch_mode(lf_plan* pl, const double* theta, int S, double* chi2, d
                                                         pl->d_free_dig, pl->d_free_raw);
   if (grad) {
     int g = std::min(pl->grid_grad, S);
-    k_chi2<MODE, true><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
+    k_chi2<MODE, true><<<g, pl->block, pl->smem_grad, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
                                                        grad, pl->d_counter, g_member_chunk,
                                                        pl->d_free_dig, pl->d_free_raw);
   } else if (pl->has_aux) {
@@ -1691,7 +1824,8 @@ extern "C" lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int3
                                         double* grad, void* stream) {
   if (!plan) return fail(LF_EINVAL, "plan is NULL");
   if (!grad) return fail(LF_EINVAL, "grad is NULL");
-  if (!plan->single_plane) return fail(LF_EUNSUPPORTED, "the gradient is implemented for single-plane plans");
+  if (plan->smem_grad == 0)
+    return fail(LF_EUNSUPPORTED, "the multi-plane adjoint's per-image records do not fit in shared memory");
   if (plan->has_aux) return fail(LF_EUNSUPPORTED, "no gradient of the flux and time-delay terms");
   return run(plan, theta, S, chi2, grad, stream);
 }

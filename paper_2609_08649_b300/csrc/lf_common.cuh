@@ -205,7 +205,10 @@ __host__ __device__ inline void split_ff(double v, float& hi, float& lo) {
 
 // ----------------------------------------------------------- profile closed forms ----
 // Softened isothermal ellipsoid of unit strength in its own (u, v) frame.
-// qe = q / e; round != 0 uses the q = 1 limit.
+// qe = q / e; round != 0 evaluates at q = 1 (e and qe unused): alpha from the expansions
+// (q/e) atan(e X) = q X (1 - e^2 X^2 / 3 + O(e^4)) and (q/e) atanh(e Y) = q Y (1 + e^2 Y^2 / 3
+// + O(e^4)), X = u / (psi~ + s), Y = v / (psi~ + q^2 s), whose dropped terms have a vanishing
+// first derivative in q there, so that dual numbers over q (or eps) get the exact derivative.
 template <class T>
 LF_INLINE void sie_uv(T u, T v, T q, T q2, T e, T qe, T s, T s2, T q2s, T D0, bool round,
                       T& au, T& av, T& puu, T& pvv, T& puv) {
@@ -214,9 +217,11 @@ LF_INLINE void sie_uv(T u, T v, T q, T q2, T e, T qe, T s, T s2, T q2s, T D0, bo
   T ip = lf_rsqrt(p2);
   T psi = p2 * ip;
   if (round) {
-    T r = lf_rcp(psi + s);
-    au = u * r;
-    av = v * r;
+    const T third = (T)(1.0 / 3.0);
+    T e2 = ((T)1 - q) * ((T)1 + q);
+    T X = u * lf_rcp(psi + s), Y = v * lf_rcp(psi + q2s);
+    au = q * X * ((T)1 - e2 * X * X * third);
+    av = q * Y * ((T)1 + e2 * Y * Y * third);
   } else {
     au = qe * lf_atan(e * u * lf_rcp(psi + s));
     av = qe * lf_atanh(e * v * lf_rcp(psi + q2s));

@@ -101,3 +101,20 @@ def chi2_mixed_bound(wl, cat, theta, sigma=None, coef=4.0):
         dp = coef * U32 * sp[:, i0:i1]
         bound += (2 * a_f[:, f:f + 1] * (wn * da + wn * zn * dp)).sum(1)
     return bound.numpy()
+
+
+def families_off_critical(wl, cat, theta, thr):
+    """The catalogue restricted to the families whose images all keep |det A_i| >= thr for
+    every sample (oracle FP64 source-plane terms).  Near a critical curve the chi^2 gradient
+    grows like 1/det^3 and the FP32 arithmetic of the mixed tiers no longer resolves it."""
+    from oracle import gradient as OG
+    kw = {"fam_zs": list(cat.fam_zs)} if len(wl.planes) > 1 else \
+        {"fam_adis": OM.single_plane_adis(wl, cat.fam_zs)}
+    with torch.no_grad():
+        _, A = OG._terms(wl, torch.as_tensor(theta), torch.tensor(cat.theta_obs), list(cat.fam_off), **kw)
+    det = torch.linalg.det(A).abs().min(0).values.numpy()
+    keep = [f for f in range(len(cat.fam_off) - 1)
+            if det[cat.fam_off[f]:cat.fam_off[f + 1]].min() >= thr]
+    idx = np.concatenate([np.arange(cat.fam_off[f], cat.fam_off[f + 1]) for f in keep])
+    off = np.concatenate([[0], np.cumsum([cat.fam_off[f + 1] - cat.fam_off[f] for f in keep])])
+    return W.Catalogue(cat.theta_obs[idx], cat.theta_true[idx], off, np.asarray(cat.fam_zs)[keep])

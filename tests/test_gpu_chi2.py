@@ -20,7 +20,7 @@ import torch
 
 from oracle import gradient as OG
 from oracle import model as OM
-from tests.helpers import chi2_mixed_bound
+from tests.helpers import chi2_mixed_bound, families_off_critical
 
 pytestmark = pytest.mark.gpu
 W = pytest.importorskip("paper_2609_08649_b300.workloads")
@@ -129,6 +129,22 @@ def test_gradient_matches_oracle_autograd(lib, c2, prec):
     assert np.all(np.abs(c.cpu().numpy() - cref.numpy()) <= CHI2_TOL[prec] * np.abs(cref.numpy()))
 
 
+@pytest.mark.parametrize("prec", ["fp64", "ff"])
+def test_gradient_at_round_halo(lib, c2, prec):
+    """A sampled ellipticity at exactly eps = 0 (the round profile in the forward pass): the
+    adjoint takes the round branch with its exact derivative in eps there."""
+    api, PM = lib
+    wl, cat, th = c2
+    t = th[:3].copy()
+    k_eps = [i for i, p in enumerate(wl.params) if p.comp == 0 and p.field == W.F_EPS][0]
+    t[:, k_eps] = 0.0
+    plan = api.Plan([PM.cluster_input(wl, cat)], 4, prec)
+    c, g = plan.chi2_grad(torch.tensor(t, device="cuda"))
+    cref, gref = oracle(wl, cat, t, grad=True)
+    assert np.all(np.abs(c.cpu().numpy() - cref.numpy()) <= CHI2_TOL[prec] * np.abs(cref.numpy()))
+    assert grad_ok(g.cpu().numpy(), gref.numpy(), prec)
+
+
 @pytest.mark.parametrize("prec", ["mixed", "ff"])
 def test_gradient_matches_central_differences(lib, c2, prec):
     """Adjoint vs central differences (h = 1e-4 max(|theta_p|, 1), fourth order) of the FP64
@@ -182,6 +198,28 @@ def test_multicluster_gradient_one_launch(lib, c4, prec):
         assert grad_ok(g[sl], gref.numpy(), prec)
 
 
+def multiplane_case(n_samples=6):
+    """Three planes; besides the main plane's halos and scaling relation, the sampled
+    parameters include components of both later planes (an NFW's position, a dPIE's
+    position, strength and cut), so the gradient runs through the recursion's positions."""
+    wl = W.multiplane_c3(n_grid=8, n_samples=n_samples)
+    n1, n2 = len(wl.planes[0].comps), len(wl.planes[1].comps)
+    nfw2, pje2 = n1, n1 + 30                  # plane 2: 30 NFW then 30 dPIE
+    nfw3, pje3 = n1 + n2, n1 + n2 + 20        # plane 3: 20 NFW then 20 dPIE
+    extra = []
+    for ci in (nfw2, nfw3):
+        c = wl.planes[1 if ci == nfw2 else 2].comps[ci - (n1 if ci == nfw2 else n1 + n2)]
+        extra += [W.ParamSpec(ci, W.F_X, W.XF_IDENT, c.x, 0.3, False),
+                  W.ParamSpec(ci, W.F_Y, W.XF_IDENT, c.y, 0.3, False)]
+    for ci, pl in ((pje2, 1), (pje3, 2)):
+        c = wl.planes[pl].comps[ci - (n1 if pl == 1 else n1 + n2)]
+        extra += [W.ParamSpec(ci, W.F_X, W.XF_IDENT, c.x, 0.3, False),
+                  W.ParamSpec(ci, W.F_Y, W.XF_IDENT, c.y, 0.3, False),
+                  W.ParamSpec(ci, W.F_B, W.XF_VDISP, c.vdisp, 0.01, True),
+                  W.ParamSpec(ci, W.F_CUT, W.XF_KPC, c.cut_kpc, 0.01, True)]
+    return W.replace(wl, params=list(wl.params) + extra)
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5), ("ff", 1e-5)])
 def test_multiplane_chi2(lib, c2, prec, tol):
     api, PM = lib
@@ -193,10 +231,56 @@ def test_multiplane_chi2(lib, c2, prec, tol):
     c = plan.chi2(torch.tensor(th, device="cuda")).cpu().numpy()
     ref = oracle(wl, cat3, th).numpy()
     assert np.all(np.abs(c - ref) <= tol * np.abs(ref))
-    from paper_2609_08649_b300 import _lib as L
-    with pytest.raises(L.LFError) as e:
-        plan.chi2_grad(torch.tensor(th, device="cuda"))
-    assert e.value.status == L.LF_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "ff"])
+def test_multiplane_gradient_matches_oracle_autograd(lib, c2, prec):
+    """The adjoint of the multi-plane recursion (reverse sweep over the planes, third
+    derivatives at every later plane's positions) against the oracle's autograd through
+    the same recursion; the families sit at z = 2.5 (behind two planes) and z = 4.  The
+    catalogue's images are not images of this synthetic model, and many of them fall near
+    its critical curves: the families kept are those with |det A| >= 0.05 at every image."""
+    api, PM = lib
+    _, cat, _ = c2
+    wl = multiplane_case()
+    zs = np.where(np.arange(len(cat.fam_zs)) % 2 == 0, 4.0, 2.5)
+    th = W.sample_thetas(wl, wl.seed)
+    cat3 = families_off_critical(wl, W.Catalogue(cat.theta_obs, cat.theta_true, cat.fam_off, zs), th, 0.05)
+    assert len(cat3.theta_obs) >= 30
+    plan = api.Plan([PM.cluster_input(wl, cat3)], 6, prec)
+    c, g = plan.chi2_grad(torch.tensor(th, device="cuda"))
+    cref, gref = oracle(wl, cat3, th, grad=True)
+    assert np.all(np.abs(c.cpu().numpy() - cref.numpy()) <= CHI2_TOL[prec] * np.abs(cref.numpy()))
+    assert grad_ok(g.cpu().numpy(), gref.numpy(), prec)
+    # the later planes' parameters carry gradient
+    P0 = len(W.multiplane_c3(n_grid=8, n_samples=6).params)
+    assert np.all(np.abs(gref.numpy()[:, P0:]).max(axis=0) > 0)
+    api.device_error()
+
+
+def test_multiplane_gradient_matches_central_differences(lib, c2):
+    """Float-float adjoint vs fourth-order central differences of the library's FP64 chi^2."""
+    api, PM = lib
+    _, cat, _ = c2
+    wl = multiplane_case(n_samples=1)
+    th = W.sample_thetas(wl, wl.seed)
+    cat3 = families_off_critical(wl, W.Catalogue(cat.theta_obs, cat.theta_true, cat.fam_off,
+                                                 np.full(len(cat.fam_zs), 4.0)), th, 0.05)
+    plan = api.Plan([PM.cluster_input(wl, cat3)], 1, "ff")
+    plan64 = api.Plan([PM.cluster_input(wl, cat3)], 4 * th.shape[1], "fp64")
+    t0 = torch.tensor(th[:1], device="cuda")
+    _, g = plan.chi2_grad(t0)
+    P = t0.shape[1]
+    hs = [1e-4 * max(abs(float(t0[0, p])), 1.0) for p in range(P)]
+    rows = []
+    for p in range(P):
+        for k in (1, -1, 2, -2):
+            t = t0.clone()
+            t[0, p] += k * hs[p]
+            rows.append(t)
+    f = plan64.chi2(torch.cat(rows)).cpu().numpy().reshape(P, 4)
+    fd = np.array([(8 * (f[p, 0] - f[p, 1]) - (f[p, 2] - f[p, 3])) / (12 * hs[p]) for p in range(P)])
+    assert grad_ok(g.cpu().numpy(), fd[None], "ff")
 
 
 def test_single_image_family_contributes_zero_and_galaxy_chi2(lib):

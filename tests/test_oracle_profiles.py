@@ -247,3 +247,27 @@ def test_multipole3_threefold_symmetry_and_orientation():
                                torch.tensor([5.0 * math.sin(pa)], dtype=torch.float64), amp, pa)
     ref = torch.tensor([10 * amp * math.cos(pa), 10 * amp * math.sin(pa)], dtype=torch.float64)
     assert torch.allclose(torch.stack([ax, ay]).flatten(), ref, atol=1e-14)
+
+
+@pytest.mark.parametrize("prof", ["sie", "dpie"])
+def test_round_branch_derivative_in_q_is_the_elliptical_limit(prof):
+    """At q = 1 the closed forms take the round branch; its derivative in q (autograd) must
+    equal the one-sided limit q -> 1- of the elliptical branch's derivative, here by
+    Richardson extrapolation of difference quotients of the elliptical values (the
+    derivative in eps = (1 - q)/(1 + q) follows by dq/deps = -2 at eps = 0)."""
+    fn = (lambda q: pr.sie(PTS_X, PTS_Y, 1.3, q, 0.5, 0.2)) if prof == "sie" else \
+         (lambda q: pr.dpie(PTS_X, PTS_Y, 1.0, q, -0.3, 0.1, 3.0))
+    q1 = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    out = fn(q1)
+    f1 = [o.detach() for o in out]
+    for k in range(5):
+        g = torch.stack([torch.autograd.grad(out[k][i], q1, retain_graph=True)[0]
+                         for i in range(len(PTS_X))])
+        # D(h) = (f(1) - f(1 - h)) / h = f' - h f''/2 + ...; two Richardson levels
+        D = lambda h: (f1[k] - fn(torch.tensor(1.0 - h, dtype=torch.float64))[k]) / h
+        h = 1e-3
+        d1, d2, d4 = D(h), D(h / 2), D(h / 4)
+        r1, r2 = 2 * d2 - d1, 2 * d4 - d2
+        lim = (4 * r2 - r1) / 3
+        scale = max(float(g.abs().max()), 1e-3)
+        assert float((g - lim).abs().max()) < 1e-7 * scale, (k, g, lim)
