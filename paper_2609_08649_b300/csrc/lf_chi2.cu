@@ -50,7 +50,9 @@ struct PlaneDesc {
   int nc, nm;
   lf_scaling sc;
   double apk;
-  uint32_t off_rawc, off_mpre, off_dc, off_dm;
+  uint32_t off_rawc, off_mpre, off_dc;
+  uint32_t off_dm;                 // scalar member records (adjoint, flux / time-delay pass)
+  uint32_t off_dmp;                // the mixed tier's packed pairs (forward passes); = off_dm else
 };
 
 struct ClusterDesc {
@@ -86,8 +88,10 @@ struct ClusterDesc {
   const float2* ratio_ff;          // [n_fam * np]
   const float4* sinv_f;            // [n_img] (xx, xy, yy, 0)
   int mpg_stride;                  // multi-plane adjoint: doubles per image record
-  uint32_t off_img, off_imgd, off_fam, off_par, off_free, off_newton, off_fama, off_aux, off_mpg, smem;
-  uint32_t smem_grad;              // smem plus the multi-plane adjoint's records
+  uint32_t off_img, off_imgd, off_fam, off_par, off_free, off_newton, off_fama, off_aux, off_mpg;
+  // shared memory of each launch kind: the common regions, then only the member records and
+  // scratch that kind reads (source-plane chi^2; image-plane chi^2; flux / time delay; adjoint)
+  uint32_t smem, smem_img, smem_aux, smem_grad;
 };
 
 // ------------------------------------------------------------------ transforms -----
@@ -255,6 +259,21 @@ constexpr int IMGF = 22;
 #ifndef LF_CHI2_BLOCK
 #define LF_CHI2_BLOCK 256
 #endif
+// The mixed tier's forward passes (packed members) run under a register cap that lets
+// LF_CHI2_FWD_MINB blocks of up to LF_CHI2_FWD_THREADS threads share an SM: each block works
+// on one sample, whose ~100 image pairs fill only a few warps, so warps come from more
+// resident samples.
+#ifndef LF_CHI2_FWD_THREADS
+#define LF_CHI2_FWD_THREADS 128
+#endif
+#ifndef LF_CHI2_FWD_MINB
+#define LF_CHI2_FWD_MINB 5
+#endif
+#define LF_CHI2_CAPPED(MODE, GRAD, PASS) ((MODE) == LF_MIXED && !(GRAD) && (PASS) != 2)
+// largest block a plan of this tier may use
+static inline int chi2_max_block(int precision) {
+  return precision == LF_MIXED ? std::min(LF_CHI2_THREADS, LF_CHI2_FWD_THREADS) : LF_CHI2_THREADS;
+}
 // PASS 0: source-plane chi^2 (and its gradient when GRAD).  PASS 1: image-plane chi^2 of
 // Eq. chi2_img with model images found by `iters` Newton steps from the observed images
 // towards the family's analytic source (written to chi2), and the image-plane rms (to rms).
@@ -332,7 +351,8 @@ __device__ void d3_sum(const CompT<T>* dc, int nc, const Mem* dm, int nm, int k0
 }
 
 template <int MODE, bool GRAD, int PASS = 0>   // MODE: LF_FP64, LF_MIXED or LF_FF
-__global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const ClusterDesc* __restrict__ cds,
+__global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD_THREADS : LF_CHI2_THREADS,
+                                  LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD_MINB : LF_CHI2_MINB) k_chi2(const ClusterDesc* __restrict__ cds,
                                               const int* __restrict__ corder, int spc, int S,
                                               const double* __restrict__ theta, double* chi2,
                                               double* grad, int* counter, int chunk,
@@ -456,7 +476,7 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
       const int n_lanes = PACKM ? 2 * (int)mem_records<MemPair>(P.nm) : P.nm;
       for (int i = tid; i < n_lanes; i += blockDim.x) {
         if constexpr (PACKM) {
-          MemPair* dp = reinterpret_cast<MemPair*>(smem + P.off_dm);
+          MemPair* dp = reinterpret_cast<MemPair*>(smem + P.off_dmp);
           if (i >= P.nm) {      // zero-strength pad of an odd member count
             pair_lane(dp[i >> 1], i & 1, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 2.f);
             continue;
@@ -496,7 +516,7 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
           d.pad0 = (T)0;
           d.pad1 = (T)0;
           if constexpr (PACKM)
-            pair_lane(reinterpret_cast<MemPair*>(smem + P.off_dm)[i >> 1], i & 1, d.xh, d.xl, d.yh, d.yl,
+            pair_lane(reinterpret_cast<MemPair*>(smem + P.off_dmp)[i >> 1], i & 1, d.xh, d.xl, d.yh, d.yl,
                       d.b, d.s, d.a);
           else
             dm[i] = d;
@@ -510,7 +530,15 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
     const int n_img = C.n_img, KS = C.ks, IS = C.img_stride, ISF = C.img_stride_f,
               ISD = C.img_stride_d;
     const int n_unit = IPT == 2 ? (n_img + 1) >> 1 : n_img;
-    const int ntask = n_unit * KS;
+    // The units that do not fill whole warps (the tail) share one warp with more component
+    // slices each (KST), so that no warp runs the whole component loop with a few active
+    // lanes.  Main tasks end on a warp boundary, so each warp has one slice count.
+    const int n_main = (n_unit * KS / 32) * (32 / KS);
+    const int n_tail = n_unit - n_main;
+    int KST = KS;
+    while (n_tail > 0 && n_tail * KST * 2 <= 32) KST *= 2;
+    const int t_main = n_main * KS;
+    const int ntask = t_main + n_tail * KST;
     // pos: null = the observed images; else positions (x, y) at pos[4 i], pos[4 i + 1]
     auto eval_planes = [&](const double* pos) {
     for (int j = 0; j < C.np; ++j) {
@@ -521,10 +549,13 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
       for (int base = 0; base < ntask; base += blockDim.x) {
         const int t = base + tid;
         const bool act = t < ntask;
-        const int pr = act ? t / KS : 0;
-        const int k = act ? t - pr * KS : 0;
+        const bool tail = t >= t_main;
+        const int ks = tail ? KST : KS;             // uniform over each warp
+        const int tt = tail ? t - t_main : t;
+        const int pr = act ? (tail ? n_main + tt / KST : tt / KS) : 0;
+        const int k = act ? (tail ? tt - (pr - n_main) * KST : tt - pr * KS) : 0;
         const int ia = 2 * pr, ib = min(2 * pr + 1, n_img - 1);
-        const int k0 = (int)((long long)K * k / KS), k1 = (int)((long long)K * (k + 1) / KS);
+        const int k0 = (int)((long long)K * k / ks), k1 = (int)((long long)K * (k + 1) / ks);
         if constexpr (MIXED) {
           float xh[IPT], xl[IPT], yh[IPT], yl[IPT];
           int ii[IPT];
@@ -553,12 +584,12 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
               accumulate_ext<IPT>(dc, P.nc, dm, P.nm, k0, k1, xh, xl, yh, yl, tab, acc);
             else
               if constexpr (PACKM)
-                accumulate_packed<IPT>(dc, P.nc, reinterpret_cast<const MemPair*>(smem + P.off_dm), P.nm,
+                accumulate_packed<IPT>(dc, P.nc, reinterpret_cast<const MemPair*>(smem + P.off_dmp), P.nm,
                                        k0, k1, chunk, xh, xl, yh, yl, tab, acc);
               else
                 accumulate_mixed<IPT>(dc, P.nc, dm, P.nm, k0, k1, chunk, xh, xl, yh, yl, tab, acc);
           }
-          for (int off = 1; off < KS; off <<= 1)
+          for (int off = 1; off < ks; off <<= 1)
 #pragma unroll
             for (int c5 = 0; c5 < 5; ++c5)
 #pragma unroll
@@ -588,7 +619,7 @@ __global__ void __launch_bounds__(LF_CHI2_THREADS, LF_CHI2_MINB) k_chi2(const Cl
               accumulate_fp64(dc, P.nc, dm, P.nm, k0, k1, x, y, v[q]);
             }
           }
-          for (int off = 1; off < KS; off <<= 1)
+          for (int off = 1; off < ks; off <<= 1)
 #pragma unroll
             for (int c5 = 0; c5 < 5; ++c5) {
               v[0][c5] += __shfl_xor_sync(0xffffffffu, v[0][c5], off);
@@ -1223,9 +1254,9 @@ struct lf_plan {
   int block = LF_CHI2_BLOCK;
   int ks_cap = 32;
   bool tuned = false;
-  uint32_t smem = 0;
+  uint32_t smem = 0, smem_img = 0, smem_aux = 0;
   uint32_t smem_grad = 0;          // gradient launches (0: the plan has no gradient kernel)
-  int grid_chi2 = 0, grid_grad = 0, grid_aux = 0;
+  int grid_chi2 = 0, grid_grad = 0, grid_aux = 0, grid_img = 0;
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -1351,53 +1382,70 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
   const bool mixed = precision != LF_FP64;
   const uint32_t mem_sz = precision == LF_FF ? sizeof(MemX) : precision == LF_MIXED ? sizeof(MemT<float>)
                                                                                    : sizeof(MemT<double>);
+  auto al = [](uint32_t v) { return (v + 15u) & ~15u; };
+  // regions every launch reads
   uint32_t o = LF_HDR;
   for (int j = 0; j < C.np; ++j) {
     PlaneDesc& P = C.pl[j];
-    o = (o + 15u) & ~15u; P.off_rawc = o; o += (uint32_t)P.nc * 64u;
+    o = al(o); P.off_rawc = o; o += (uint32_t)P.nc * 64u;
     P.off_mpre = 0;   // the member pre-table is read from global memory, not staged
-    o = (o + 15u) & ~15u; P.off_dc = o; o += (uint32_t)P.nc * (mixed ? sizeof(CompT<float>) : sizeof(CompT<double>));
-    o = (o + 15u) & ~15u; P.off_dm = o;
-    o += std::max((uint32_t)P.nm * mem_sz,            // scalar records, or the mixed tier's pairs
-                  mixed ? mem_records<MemPair>(P.nm) * (uint32_t)sizeof(MemPair) : 0u);
+    o = al(o); P.off_dc = o; o += (uint32_t)P.nc * (mixed ? sizeof(CompT<float>) : sizeof(CompT<double>));
   }
   C.img_stride = C.np > 1 ? 16 + 6 * C.np : 14;
   C.img_stride_f = IMGF;
   C.img_stride_d = C.np > 1 ? 2 + 6 * C.np : 0;
-  o = (o + 15u) & ~15u; C.off_img = o;
+  o = al(o); C.off_img = o;
   o += mixed ? (uint32_t)C.n_img * IMGF * 4u : (uint32_t)C.n_img * C.img_stride * 8u;
-  o = (o + 15u) & ~15u; C.off_imgd = o;
+  o = al(o); C.off_imgd = o;
   if (mixed) o += (uint32_t)C.n_img * C.img_stride_d * 8u;
   C.off_fam = o; o += (uint32_t)C.n_fam * 3u * 8u;
   C.off_par = o; o += (uint32_t)C.P * 2u * 8u;
-  o = (o + 15u) & ~15u; C.off_free = o; o += (uint32_t)C.n_free * 64u;
-  o = (o + 15u) & ~15u; C.off_newton = o; o += (uint32_t)C.n_img * 4u * 8u;
+  o = al(o); C.off_free = o; o += (uint32_t)C.n_free * 64u;
   // per sample: a_dis of each family (double, float-float) and the parameter setting it
-  o = (o + 15u) & ~15u; C.off_fama = o; o += (uint32_t)C.n_fam * (8u + 8u + 4u);
-  // flux / time-delay pass: per image psi, the third derivatives, then y_i and d_i
-  o = (o + 15u) & ~15u; C.off_aux = o; o += C.aux ? (uint32_t)C.n_img * 6u * 8u : 0u;
-  o = (o + 15u) & ~15u;
-  C.smem = o;
-  // multi-plane adjoint (gradient launches only): per image and plane the position theta_j
-  // (2), Psi_j (3) and the cotangents of (alpha_j, Psi_j) (5); then the third derivatives of
-  // psi (4) at every plane after the first
-  C.off_mpg = o;
+  o = al(o); C.off_fama = o; o += (uint32_t)C.n_fam * (8u + 8u + 4u);
+  const uint32_t var = al(o);
+  // forward passes: the members as packed pairs (mixed tier) or scalar records
+  uint32_t of = var, os = var;
+  for (int j = 0; j < C.np; ++j) {
+    PlaneDesc& P = C.pl[j];
+    P.off_dmp = al(of);
+    of = P.off_dmp + (precision == LF_MIXED ? mem_records<MemPair>(P.nm) * (uint32_t)sizeof(MemPair)
+                                            : (uint32_t)P.nm * mem_sz);
+    P.off_dm = al(os);
+    os = P.off_dm + (uint32_t)P.nm * mem_sz;
+  }
+  if (precision != LF_MIXED)
+    for (int j = 0; j < C.np; ++j) C.pl[j].off_dmp = C.pl[j].off_dm;
+  C.smem = al(of);
+  // image-plane chi^2: + Newton state per image
+  C.off_newton = al(of);
+  C.smem_img = al(C.off_newton + (uint32_t)C.n_img * 4u * 8u);
+  // flux / time-delay pass: scalar members + per image psi, the third derivatives, y_i and d_i
+  C.off_aux = al(os);
+  C.smem_aux = al(C.off_aux + (C.aux ? (uint32_t)C.n_img * 6u * 8u : 0u));
+  // adjoint: scalar members + (several planes) per image and plane the position theta_j (2),
+  // Psi_j (3) and the cotangents of (alpha_j, Psi_j) (5); then the third derivatives of psi
+  // (4) at every plane after the first
+  C.off_mpg = al(os);
   C.mpg_stride = C.np > 1 ? 10 * C.np + 4 * (C.np - 1) : 0;
-  C.smem_grad = o + (uint32_t)C.n_img * (uint32_t)C.mpg_stride * 8u;
+  C.smem_grad = al(C.off_mpg + (uint32_t)C.n_img * (uint32_t)C.mpg_stride * 8u);
   int K = 0;
   for (int j = 0; j < C.np; ++j) K = std::max(K, C.pl[j].nc + C.pl[j].nm);
   C.ks = choose_ks(C.n_img, K, block, ks_cap, 2);
 }
 
 static lf_status relayout(lf_plan* pl) {
-  pl->smem = 0;
-  pl->smem_grad = 0;
+  pl->smem = pl->smem_img = pl->smem_aux = pl->smem_grad = 0;
   for (auto& C : pl->desc) {
     layout_cluster(C, pl->precision, pl->block, pl->ks_cap);
     pl->smem = std::max(pl->smem, C.smem);
+    pl->smem_img = std::max(pl->smem_img, C.smem_img);
+    pl->smem_aux = std::max(pl->smem_aux, C.smem_aux);
     pl->smem_grad = std::max(pl->smem_grad, C.smem_grad);
   }
-  if (pl->smem > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "cluster too large for shared memory (%u B)", pl->smem);
+  if (pl->smem > LF_SMEM_MAX || pl->smem_aux > LF_SMEM_MAX)
+    return fail(LF_EUNSUPPORTED, "cluster too large for shared memory (%u B)", std::max(pl->smem, pl->smem_aux));
+  if (pl->smem_img > LF_SMEM_MAX) pl->smem_img = 0;     // the image-plane chi^2 is refused at call time
   if (pl->smem_grad > LF_SMEM_MAX) pl->smem_grad = 0;   // the gradient is refused at call time
   LF_CUDA(cudaMemcpy(pl->d_desc, pl->desc.data(), pl->desc.size() * sizeof(ClusterDesc),
                      cudaMemcpyHostToDevice));
@@ -1423,10 +1471,15 @@ static lf_status relayout(lf_plan* pl) {
                    : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, false, 2>
                                              : (const void*)k_chi2<LF_FP64, false, 2>;
   LF_TRY(kset(kc, pl->smem));
-  LF_TRY(kset(ki, pl->smem));
+  pl->grid_img = 0;
+  if (pl->smem_img > 0) {
+    LF_TRY(kset(ki, pl->smem_img));
+    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ki, pl->block, pl->smem_img));
+    pl->grid_img = nsm * std::max(occ, 1);
+  }
   if (pl->has_aux) {
-    LF_TRY(kset(ka, pl->smem));
-    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ka, pl->block, pl->smem));
+    LF_TRY(kset(ka, pl->smem_aux));
+    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ka, pl->block, pl->smem_aux));
     pl->grid_aux = nsm * std::max(occ, 1);
   }
   LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kc, pl->block, pl->smem));
@@ -1603,7 +1656,7 @@ static void launch_mode(lf_plan* pl, const double* theta, int S, double* chi2, d
                                                        pl->d_free_dig, pl->d_free_raw);
   } else if (pl->has_aux) {
     int g = std::min(pl->grid_aux, S);
-    k_chi2<MODE, false, 2><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
+    k_chi2<MODE, false, 2><<<g, pl->block, pl->smem_aux, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
                                                            nullptr, pl->d_counter, g_member_chunk,
                                                            pl->d_free_dig, nullptr);
   } else {
@@ -1621,8 +1674,8 @@ static void launch_img(lf_plan* pl, const double* theta, int S, int iters, doubl
   if (nprep > 0)
     k_chi2_prep<MODE><<<(nprep + 63) / 64, 64, 0, st>>>(pl->d_desc, spc, S, pl->nfree_max, theta,
                                                         pl->d_free_dig, pl->d_free_raw);
-  int g = std::min(pl->grid_chi2, S);
-  k_chi2<MODE, false, 1><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
+  int g = std::min(pl->grid_img, S);
+  k_chi2<MODE, false, 1><<<g, pl->block, pl->smem_img, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
                                                          nullptr, pl->d_counter, g_member_chunk,
                                                          pl->d_free_dig, nullptr, iters, rms);
 }
@@ -1686,7 +1739,7 @@ static lf_status autotune(lf_plan* pl, const double* theta, int S, double* chi2,
   int bb = pl->block, bc = pl->ks_cap;
   for (int b : blocks)
     for (int cap : caps) {
-      if (b > LF_CHI2_THREADS) continue;   // beyond the kernels' launch bounds
+      if (b > chi2_max_block(pl->precision)) continue;   // beyond the kernels' launch bounds
       pl->block = b;
       pl->ks_cap = cap;
       if (relayout(pl) != LF_OK) continue;
@@ -1765,6 +1818,7 @@ extern "C" lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, i
   lf_plan* pl = new lf_plan();
   pl->n_clusters = n_clusters;
   pl->precision = precision;
+  pl->block = std::min(pl->block, chi2_max_block(precision));
   pl->flags = flags;
   pl->max_samples = max_samples;
   pl->P = clusters[0].P;
@@ -1838,6 +1892,7 @@ extern "C" lf_status lf_chi2_img_batch(lf_plan* plan, const double* theta, int32
   if (S % plan->n_clusters) return fail(LF_EINVAL, "S must be a multiple of the number of clusters");
   if (iters < 1 || iters > 64) return fail(LF_EINVAL, "iters must be in 1..64");
   if (!plan->single_plane) return fail(LF_EUNSUPPORTED, "the image-plane chi^2 is implemented for single-plane plans");
+  if (plan->smem_img == 0) return fail(LF_EUNSUPPORTED, "the image-plane Newton state does not fit in shared memory");
   cudaStream_t st = (cudaStream_t)stream;
   const int spc = S / plan->n_clusters;
   LF_CUDA(cudaMemsetAsync(plan->d_counter, 0, sizeof(int), st));

@@ -177,7 +177,7 @@ extern "C" lf_status lf_chi2_batch_static(const lf_cluster* cl, const double* th
                 "(too many members or images for this entry point; use a plan)", off,
                 LF_STATIC_SCRATCH_BYTES);
 
-  const int block = 256;
+  const int block = std::min(256, chi2_max_block(precision));
   layout_cluster(C, precision, block, 32);
   if (C.smem > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "cluster too large for shared memory");
 
