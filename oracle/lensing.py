@@ -14,8 +14,9 @@ from typing import List, Optional
 import torch
 
 from . import profiles as pr
+from . import cse_nfw
 
-SIE, DPIE, NFW, SHEAR, MPOLE3 = 1, 2, 3, 4, 5
+SIE, DPIE, NFW, SHEAR, MPOLE3, ENFW = 1, 2, 3, 4, 5, 6
 C_KMS = 299792.458
 ARCSEC_PER_RAD = 180.0 / math.pi * 3600.0
 
@@ -76,6 +77,8 @@ def component(kind, dx, dy, b, eps, pa, core, cut):
         return pr.shear(dx, dy, b, pa)
     if kind == MPOLE3:
         return pr.multipole3(dx, dy, b, pa)
+    if kind == ENFW:     # b = kappa_s, core = r_s
+        return pr.enfw(dx, dy, b, q_from_eps(eps), pa, core, *cse_nfw.table())
     raise ValueError(f"unknown component kind {kind}")
 
 
@@ -90,6 +93,8 @@ def component_potential(kind, dx, dy, b, eps, pa, core, cut):
         return pr.shear_potential(dx, dy, b, pa)
     if kind == MPOLE3:
         return pr.multipole3_potential(dx, dy, b, pa)
+    if kind == ENFW:
+        return pr.enfw_potential(dx, dy, b, q_from_eps(eps), pa, core, *cse_nfw.table())
     raise ValueError(f"unknown component kind {kind}")
 
 

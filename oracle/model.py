@@ -20,7 +20,7 @@ import torch
 from . import cosmology as cz
 from .lensing import LPlane, b_from_vdisp, q_from_eps
 
-SIE, DPIE, NFW, SHEAR, MPOLE3 = 1, 2, 3, 4, 5
+SIE, DPIE, NFW, SHEAR, MPOLE3, ENFW = 1, 2, 3, 4, 5, 6
 XF_IDENT, XF_VDISP, XF_DEG, XF_KPC = 0, 1, 2, 3
 FIELDS = ("x", "y", "b", "eps", "pa", "core", "cut")
 SCALING = ("b_star", "core_star", "cut_star", "lam", "beta", "alpha")
@@ -55,6 +55,9 @@ def comp_fields(c, z_l, cosmo):
     if c.kind == NFW:
         ks, ts = nfw_lensing(c.m200, c.conc, z_l, H0, Om)
         return [c.x, c.y, ks, 0.0, 0.0, ts, 0.0]
+    if c.kind == ENFW:   # the spherical normalisation, with the ellipticity on xi
+        ks, ts = nfw_lensing(c.m200, c.conc, z_l, H0, Om)
+        return [c.x, c.y, ks, c.eps, pa, ts, 0.0]
     if c.kind == SHEAR:
         g = c.gamma
         if c.z_ref is not None:

@@ -80,6 +80,48 @@ def dpie(dx, dy, b, q, pa, core, cut):
     return tuple(p - m for p, m in zip(a1, a2))
 
 
+def cse_uv(u, v, q, s):
+    """Unit cored steep ellipsoid (CSE) in its (u, v) frame: kappa = 1 / (2 (s^2 + xi^2)^(3/2)),
+    xi^2 = u^2 + v^2/q^2.  This density is -(1/s) d/ds of the unit cored isothermal ellipsoid
+    kappa = 1 / (2 sqrt(s^2 + xi^2)) of sie(), so its deflection is -(1/s) d alpha_sie / ds;
+    the atan / atanh drop out and, with P = sqrt(q^2 (s^2 + u^2) + v^2),
+    D = (1 + q^2) s^2 + 2 P s + u^2 + v^2, A = P + q^2 s, B = P + s:
+      alpha_u = q u A / (s P D),  alpha_v = q v B / (s P D),
+      psi_uu = q / (s P D) [A - q^4 s u^2 / P^2 - 2 u^2 A^2 / (P D)],
+      psi_vv = q / (s P D) [B - s v^2 / P^2 - 2 v^2 B^2 / (P D)],
+      psi_uv = -q u v / (s P D) [q^2 s / P^2 + 2 A B / (P D)].
+    Valid at q = 1 as written.  Arguments broadcast."""
+    q2 = q * q
+    P = torch.sqrt(q2 * (s * s + u * u) + v * v)
+    D = (1.0 + q2) * s * s + 2.0 * P * s + u * u + v * v
+    A, B = P + q2 * s, P + s
+    f = q / (s * P * D)
+    au, av = f * u * A, f * v * B
+    iP2, PD = 1.0 / (P * P), P * D
+    puu = f * (A - q2 * q2 * s * u * u * iP2 - 2.0 * u * u * A * A / PD)
+    pvv = f * (B - s * v * v * iP2 - 2.0 * v * v * B * B / PD)
+    puv = -f * u * v * (q2 * s * iP2 + 2.0 * A * B / PD)
+    return au, av, puu, pvv, puv
+
+
+def enfw(dx, dy, ks, q, pa, rs, s_tab, a_tab):
+    """Elliptical NFW of scale radius rs approximated by a CSE sum (Oguri 2021):
+    kappa = 2 ks sum_i a_i / (2 (s_i^2 + xi^2 / rs^2)^(3/2)), xi^2 = u^2 + v^2/q^2, so
+    alpha = 2 ks rs sum_i a_i alpha_cse(u/rs, v/rs; s_i) and Psi = 2 ks sum_i a_i Psi_cse.
+    (s_tab, a_tab): the coefficient table (oracle.cse_nfw.table())."""
+    dx, dy, ks, q, pa, rs = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64)
+                                                      for t in (dx, dy, ks, q, pa, rs)])
+    c, sn = torch.cos(pa), torch.sin(pa)
+    u = (c * dx + sn * dy) / rs
+    v = (-sn * dx + c * dy) / rs
+    st = torch.as_tensor(s_tab, dtype=torch.float64)
+    at = torch.as_tensor(a_tab, dtype=torch.float64)
+    terms = cse_uv(u[..., None], v[..., None], q[..., None], st)
+    au, av, puu, pvv, puv = [(t * at).sum(-1) for t in terms]
+    k2 = 2.0 * ks
+    return _rotate_back(c, sn, k2 * rs * au, k2 * rs * av, k2 * puu, k2 * pvv, k2 * puv)
+
+
 def _axisym(dx, dy, kbar, kappa, r2):
     """Axially symmetric lens: alpha = kbar (dx, dy) with kbar the mean convergence
     inside r, Psi_ij = kbar delta_ij + 2 (kappa - kbar) x_i x_j / r^2."""
@@ -247,6 +289,35 @@ def nfw_potential(dx, dy, ks, rs):
     wg = torch.where(~lt, -w2, torch.zeros_like(w2))
     g_gt = torch.log(x / 2.0) ** 2 + torch.atan(torch.sqrt(wg)) ** 2
     return 2.0 * ks * rs * rs * torch.where(lt, g_lt, g_gt)
+
+
+def cse_potential_uv(u, v, q, s):
+    """Unit CSE potential: -(1/s) d/ds of the cored isothermal potential
+    u alpha_u + v alpha_v - q s ln sqrt(D) (sie_potential),
+      u alpha_u + v alpha_v + (q / (2 s)) ln D + (q / (2 D)) dD/ds,
+    dD/ds = 2 (1 + q^2) s + 2 P + 2 q^2 s^2 / P, less its value at the centre,
+    (q / (2 s)) ln((1 + q)^2 s^2) + q / s (there P = q s, D = (1 + q)^2 s^2), so that psi(0) = 0:
+      u alpha_u + v alpha_v + (q / (2 s)) ln(D / ((1 + q)^2 s^2))
+        - q [s (q^2 u^2 + v^2) / P + u^2 + v^2] / (s D)."""
+    q2 = q * q
+    P = torch.sqrt(q2 * (s * s + u * u) + v * v)
+    D = (1.0 + q2) * s * s + 2.0 * P * s + u * u + v * v
+    au, av = cse_uv(u, v, q, s)[:2]
+    return (u * au + v * av + q / (2.0 * s) * torch.log(D / ((1.0 + q) ** 2 * s * s))
+            - q * (s * (q2 * u * u + v * v) / P + u * u + v * v) / (s * D))
+
+
+def enfw_potential(dx, dy, ks, q, pa, rs, s_tab, a_tab):
+    """psi = 2 ks rs^2 sum_i a_i psi_cse(u/rs, v/rs; s_i) (the potential scales as length^2)."""
+    dx, dy, ks, q, pa, rs = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64)
+                                                      for t in (dx, dy, ks, q, pa, rs)])
+    c, sn = torch.cos(pa), torch.sin(pa)
+    u = (c * dx + sn * dy) / rs
+    v = (-sn * dx + c * dy) / rs
+    st = torch.as_tensor(s_tab, dtype=torch.float64)
+    at = torch.as_tensor(a_tab, dtype=torch.float64)
+    p = (cse_potential_uv(u[..., None], v[..., None], q[..., None], st) * at).sum(-1)
+    return 2.0 * ks * rs * rs * p
 
 
 def shear_potential(dx, dy, gamma, pa):

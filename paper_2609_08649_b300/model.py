@@ -60,6 +60,9 @@ def comp_record(c: W.PhysComp, z_l, cosmo):
     if c.kind == W.NFW:
         ks, ts = nfw_params(cosmo, z_l, c.m200, c.conc)
         return (c.x, c.y, ks, 0.0, 0.0, ts, 0.0, c.kind)
+    if c.kind == W.ENFW:   # spherical NFW normalisation, ellipticity applied to xi
+        ks, ts = nfw_params(cosmo, z_l, c.m200, c.conc)
+        return (c.x, c.y, ks, c.eps, pa, ts, 0.0, c.kind)
     if c.kind == W.SHEAR:
         g = c.gamma if c.z_ref is None else c.gamma / adis(cosmo, z_l, c.z_ref)
         return (c.x, c.y, g, 0.0, pa, 0.0, 0.0, c.kind)

@@ -14,7 +14,7 @@ the paper's own catalogues are not public inputs here.
 
 Component kinds (shared numeric codes): 1 SIE (cored isothermal ellipsoid),
 2 DPIE (pseudo-Jaffe / dPIE ellipsoid), 3 NFW (spherical), 4 SHEAR, 5 MPOLE3 (third-order
-multipole with a theta^2 potential).
+multipole with a theta^2 potential), 6 ENFW (elliptical NFW as a sum of cored steep ellipsoids).
 """
 from __future__ import annotations
 
@@ -25,7 +25,7 @@ from typing import List, Optional
 
 import numpy as np
 
-SIE, DPIE, NFW, SHEAR, MPOLE3 = 1, 2, 3, 4, 5
+SIE, DPIE, NFW, SHEAR, MPOLE3, ENFW = 1, 2, 3, 4, 5, 6
 
 # Parameter-field codes of a component and transforms applied to a sampled
 # parameter before it lands in that field (shared by the param map of both sides).
@@ -41,7 +41,8 @@ class PhysComp:
 
     kind: SIE/DPIE: x, y [arcsec], vdisp [km/s] (or theta_e [arcsec], the
     area-equivalent Einstein radius at source redshift z_ref), eps, pa_deg,
-    core_kpc / core_arcsec, cut_kpc.  NFW: m200 [Msun], conc.  SHEAR: gamma, pa_deg.
+    core_kpc / core_arcsec, cut_kpc.  NFW: m200 [Msun], conc.  ENFW: m200, conc, eps,
+    pa_deg.  SHEAR: gamma, pa_deg.
     """
     kind: int
     x: float = 0.0

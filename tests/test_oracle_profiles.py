@@ -10,6 +10,7 @@ import pytest
 import torch
 from scipy.integrate import quad
 
+from oracle import cse_nfw as C
 from oracle import profiles as pr
 
 T = lambda *v: torch.tensor(v, dtype=torch.float64)
@@ -32,6 +33,8 @@ PROFILES = {
     "pje_sph": lambda x, y: pr.pje_sph(x, y, 1.0, 0.1, 3.0),
     "nfw": lambda x, y: pr.nfw_sph(x, y, 0.2, 1.5),
     "shear": lambda x, y: pr.shear(x, y, 0.07, 0.4),
+    "cse": lambda x, y: pr.cse_uv(x, y, 0.7, 0.3),
+    "enfw": lambda x, y: pr.enfw(x, y, 0.2, 0.75, 0.5, 2.5, *C.table()),
 }
 
 
