@@ -317,7 +317,7 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-KERNEL_SOURCES = ["lf_common.cuh", "lf_eval.cuh", "lf_grid.cu", "lf_host.cu", "lf_internal.h"]
+KERNEL_SOURCES = ["lf_common.cuh", "lf_cse_table.h", "lf_eval.cuh", "lf_grid.cu", "lf_host.cu", "lf_internal.h"]
 
 
 def map_kernel_traffic():
@@ -417,6 +417,20 @@ def secondary(torch, api, PM, W, L, C, step, ms_mixed, evals):
                      "grad_samples_per_s": thf.shape[0] / (tg * 1e-3)}
         plan.close()
     out["free_adis_4096x200_P30"] = res
+    # the Hera-like model: two elliptical NFW halos (38-term CSE sums), shear, multipole,
+    # 300 members; 14 parameters
+    wle = W.cluster_c5_enfw()
+    the = torch.tensor(W.sample_thetas(wle, wle.seed), device="cuda")
+    res = {}
+    for prec in ("mixed", "ff", "fp64"):
+        plan = api.Plan([PM.cluster_input(wle, cat)], the.shape[0], prec, flags=api.FLAG_GRAPH | api.FLAG_AUTOTUNE)
+        tc = _time(torch, lambda: plan.chi2(the), reps=5 if prec != "fp64" else 1)
+        tg = _time(torch, lambda: plan.chi2_grad(the), reps=3 if prec != "fp64" else 1)
+        res[prec] = {"chi2_ms": tc, "grad_ms": tg, "chi2_per_s": the.shape[0] / (tc * 1e-3),
+                     "grad_samples_per_s": the.shape[0] / (tg * 1e-3)}
+        plan.close()
+    res["mixed_speedup_chi2"] = res["fp64"]["chi2_ms"] / res["mixed"]["chi2_ms"]
+    out["chi2_enfw_4096x200"] = res
     # image-plane chi^2 (Newton model images) and the on-device sampler on the same cluster
     res = {}
     wl2 = W.cluster_c2()

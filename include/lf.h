@@ -56,8 +56,13 @@ typedef enum {
   LF_DPIE = 2,   /* dPIE / pseudo-Jaffe ellipsoid: b, eps, pa, core, cut; eps = 0 is round */
   LF_NFW = 3,    /* spherical NFW: b = kappa_s, core = theta_s (scale radius, arcsec)  */
   LF_SHEAR = 4,  /* external shear: b = gamma, pa = shear angle; x, y = reference point */
-  LF_MULTIPOLE3 = 5  /* third-order multipole with a theta^2 potential (Sec. 4.2):
+  LF_MULTIPOLE3 = 5, /* third-order multipole with a theta^2 potential (Sec. 4.2):
                         psi = b r^2 cos 3(phi - pa) about (x, y); eps, core, cut unused */
+  LF_ENFW = 6        /* elliptical NFW (Sec. 4.1-4.2, approximated as in Oguri 2021): b = kappa_s,
+                        core = theta_s, eps, pa; kappa = 2 kappa_s g(xi / theta_s),
+                        xi^2 = u^2 + v^2/q^2, with g the spherical NFW's convergence written as a
+                        sum of 38 cored steep ellipsoids (relative error < 2e-6 for
+                        1e-4 < xi / theta_s < 1e3); cut unused */
 } lf_kind;
 
 /* LF_FP64: every operation in FP64, one thread per position (the plain comparator).

@@ -56,7 +56,7 @@ def comp_fields(c, z_l, cosmo):
         ks, ts = nfw_lensing(c.m200, c.conc, z_l, H0, Om)
         return [c.x, c.y, ks, 0.0, 0.0, ts, 0.0]
     if c.kind == ENFW:   # the spherical normalisation, with the ellipticity on xi
-        ks, ts = nfw_lensing(c.m200, c.conc, z_l, H0, Om)
+        ks, ts = (c.kappa_s, c.theta_s) if c.kappa_s is not None else nfw_lensing(c.m200, c.conc, z_l, H0, Om)
         return [c.x, c.y, ks, c.eps, pa, ts, 0.0]
     if c.kind == SHEAR:
         g = c.gamma

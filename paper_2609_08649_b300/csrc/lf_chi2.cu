@@ -183,6 +183,19 @@ __device__ void comp_dual(const lf_comp& rc, double px, double py, Out5<Dual<T, 
     nfw_sph(dx, dy, DT::cst((T)1), lf_rcp(core), o);
     return;
   }
+  if (rc.kind == LF_ENFW) {   // unit kappa_s; tangents x, y, eps, pa and core (= r_s)
+    DT eps = DT::var((T)rc.eps, 2);
+    DT one = DT::cst((T)1), two = DT::cst((T)2);
+    DT q = (one - eps) / (one + eps);
+    DT c = lf_cos(pa), sn = lf_sin(pa);
+    DT irs = lf_rcp(core);
+    DT u = (c * dx + sn * dy) * irs, v = (c * dy - sn * dx) * irs;
+    DT au, av, puu, pvv, puv;
+    enfw_uv<T, DT>(u, v, q, q * q, au, av, puu, pvv, puv);
+    DT k2r = two * core;
+    rotate_back(c, sn, k2r * au, k2r * av, two * puu, two * pvv, two * puv, o);
+    return;
+  }
   // eps = 0 is the round profile, as in the forward pass (sie_uv's q = 1 branch keeps the
   // exact first derivative in eps); else the elliptical closed form
   const bool round = rc.eps == 0.0;
@@ -1159,7 +1172,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           const int kc = C.free_comp[f];
           if (C.free_plane[f] != j || kc < k0 || kc >= k1) continue;
           const lf_comp& rc = fraw[f];
-          if (rc.kind < 1 || rc.kind > 5) continue;
+          if (rc.kind < 1 || rc.kind > 6) continue;
           Out5<Dual<T, 6>> o;
           comp_dual<T>(rc, px, py, o);
           const T b = (T)rc.b;
@@ -1286,12 +1299,14 @@ static lf_status plan_upload(lf_plan* pl, const X* host, size_t n, X** dev) {
 }
 
 static bool comp_ok(const lf_comp& r) {
-  bool ok = r.kind >= 1 && r.kind <= 5 && std::isfinite(r.x) && std::isfinite(r.y) &&
+  bool ok = r.kind >= 1 && r.kind <= 6 && std::isfinite(r.x) && std::isfinite(r.y) &&
             std::isfinite(r.b) && std::isfinite(r.pa);
   if (r.kind == LF_SIE || r.kind == LF_DPIE)
     ok = ok && r.eps >= 0.0 && r.eps < 1.0 && r.core >= 0.0 && std::isfinite(r.core);
   if (r.kind == LF_DPIE) ok = ok && std::isfinite(r.cut) && r.cut > r.core;
   if (r.kind == LF_NFW) ok = ok && r.core > 0.0 && std::isfinite(r.core);
+  if (r.kind == LF_ENFW)
+    ok = ok && r.core > 0.0 && std::isfinite(r.core) && r.eps >= 0.0 && r.eps < 1.0;
   return ok;
 }
 

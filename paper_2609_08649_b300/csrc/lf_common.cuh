@@ -19,6 +19,8 @@
 
 #include <type_traits>
 
+#include "lf_cse_table.h"
+
 #define LF_INLINE __device__ __forceinline__
 #ifndef LF_NOINLINE
 #define LF_NOINLINE __device__ __noinline__
@@ -358,7 +360,7 @@ LF_INLINE void nfw_sph(T dx, T dy, T ks, T irs, Out5<T>& o) {
 
 // ------------------------------------------------------------ digested tables ------
 // Component kinds as stored in the digested tables.
-enum { K_SIE = 1, K_DPIE = 2, K_NFW = 3, K_SHEAR = 4, K_MPOLE3 = 5 };
+enum { K_SIE = 1, K_DPIE = 2, K_NFW = 3, K_SHEAR = 4, K_MPOLE3 = 5, K_ENFW = 6 };
 
 // An explicit component prepared for evaluation in precision T.  Centre as
 // float-float for T = float (offsets are taken in two FP32 subtractions), double else.
@@ -411,7 +413,7 @@ __host__ __device__ inline void digest_comp(int kind, double x, double y, double
   c.D01 = (T)((1.0 + q * q) * core * core);
   c.s2 = (T)cut; c.s2sq = (T)(cut * cut); c.q2s2 = (T)(q * q * cut);
   c.D02 = (T)((1.0 + q * q) * cut * cut);
-  c.irs = (T)(kind == K_NFW && core > 0 ? 1.0 / core : 0.0);
+  c.irs = (T)((kind == K_NFW || kind == K_ENFW) && core > 0 ? 1.0 / core : 0.0);
   // low words: v - (T)v (zero when T is double)
   const double q2 = q * q, qe = e > 0 ? q / e : 0.0;
   c.lc = (T)(cc - (double)c.c); c.lsn = (T)(ss - (double)c.sn); c.lb = (T)(b - (double)c.b);
@@ -474,11 +476,94 @@ LF_INLINE void multipole3(T dx, T dy, T c3, T s3, Out5<T>& o) {
   o.pxy = (T)6 * (s3 * nx - c3 * ny) - ny * Hx - nx * Hy + (T)3 * G * xy;
 }
 
+// ------------------------------------------------------- elliptical NFW (CSE sum) ---
+// The spherical NFW convergence 2 kappa_s g(x), x = r / r_s, as a sum of cored steep
+// ellipsoids g(x) = sum_i a_i / (2 (s_i^2 + x^2)^(3/2)) (the method of Oguri 2021; table from
+// gen_cse_table.py), made elliptical by x^2 -> xi^2 = u^2 + v^2/q^2 in r_s units.
+__constant__ double c_cse_sd[LF_CSE_N] = {LF_CSE_S_LIST};
+__constant__ double c_cse_ad[LF_CSE_N] = {LF_CSE_A_LIST};
+__constant__ float c_cse_sf[LF_CSE_N] = {LF_CSE_S_LIST};
+__constant__ float c_cse_af[LF_CSE_N] = {LF_CSE_A_LIST};
+template <class T> __device__ __forceinline__ T cse_s(int i);
+template <class T> __device__ __forceinline__ T cse_a(int i);
+template <> __device__ __forceinline__ float cse_s<float>(int i) { return c_cse_sf[i]; }
+template <> __device__ __forceinline__ float cse_a<float>(int i) { return c_cse_af[i]; }
+template <> __device__ __forceinline__ double cse_s<double>(int i) { return c_cse_sd[i]; }
+template <> __device__ __forceinline__ double cse_a<double>(int i) { return c_cse_ad[i]; }
+
+// Sum over the table of unit CSEs in the (u, v) frame, offsets in r_s units.  A CSE of core s
+// is -(1/s) d/ds of the unit cored isothermal ellipsoid, which removes its atan / atanh: with
+// P = sqrt(q^2 (s^2 + u^2) + v^2), D = (1 + q^2) s^2 + 2 P s + u^2 + v^2, A = P + q^2 s,
+// B = P + s and f = q / (s P D):
+//   alpha_u = f u A, alpha_v = f v B,
+//   psi_uu = f [A - q^4 s u^2 / P^2 - 2 u^2 A^2 / (P D)],
+//   psi_vv = f [B - s v^2 / P^2 - 2 v^2 B^2 / (P D)],
+//   psi_uv = -f u v [q^2 s / P^2 + 2 A B / (P D)].
+// T: the table's precision; U: T or dual numbers over it.
+template <class T, class U>
+LF_INLINE void enfw_uv(U u, U v, U q, U q2, U& au, U& av, U& puu, U& pvv, U& puv) {
+  const U uu = u * u, vv = v * v, r2 = uu + vv, q4 = q2 * q2, opq2 = U(1.0) + q2;
+  au = U(0.0); av = U(0.0); puu = U(0.0); pvv = U(0.0); puv = U(0.0);
+#pragma unroll 2
+  for (int i = 0; i < LF_CSE_N; ++i) {
+    const T si = cse_s<T>(i);
+    const U s = U(si), s2 = U(si * si);
+    const U P2 = lf_fma(q2, s2 + uu, vv);
+    const U iP = lf_rsqrt(P2);
+    const U P = P2 * iP;
+    const U D = lf_fma(opq2, s2, lf_fma(U(2.0) * P, s, r2));
+    const U iD = lf_rcp(D);
+    const U A = lf_fma(q2, s, P), B = P + s;
+    const U f = U(cse_a<T>(i) / si) * q * iP * iD;
+    const U iP2 = iP * iP, g = U(2.0) * iP * iD;
+    au = lf_fma(f * u, A, au);
+    av = lf_fma(f * v, B, av);
+    puu = lf_fma(f, A - q4 * s * uu * iP2 - g * uu * A * A, puu);
+    pvv = lf_fma(f, B - s * vv * iP2 - g * vv * B * B, pvv);
+    puv = puv - f * u * v * (q2 * s * iP2 + g * A * B);
+  }
+}
+
+// The unit CSE sum's potential (offsets in r_s units): per term, -(1/s) d/ds of the cored
+// isothermal potential less its value at the centre,
+//   u alpha_u + v alpha_v + (q / (2 s)) ln(D / ((1 + q)^2 s^2))
+//     - q [s (q^2 u^2 + v^2) / P + u^2 + v^2] / (s D).
+template <class T>
+LF_INLINE T enfw_potential_uv(T u, T v, T q, T q2) {
+  const T uu = u * u, vv = v * v, r2 = uu + vv, opq2 = (T)1 + q2, opq = (T)1 + q;
+  const T w = lf_fma(q2, uu, vv);
+  T p = (T)0;
+  for (int i = 0; i < LF_CSE_N; ++i) {
+    const T s = cse_s<T>(i), s2 = s * s;
+    const T P2 = lf_fma(q2, s2 + uu, vv);
+    const T iP = lf_rsqrt(P2);
+    const T P = P2 * iP;
+    const T D = lf_fma(opq2, s2, lf_fma((T)2 * P, s, r2));
+    const T iD = lf_rcp(D);
+    const T qs = q * lf_rcp(s);
+    const T lin = qs * iP * iD * (u * u * lf_fma(q2, s, P) + vv * (P + s));   // u alpha_u + v alpha_v
+    const T lg = (T)0.5 * qs * lf_log(D * lf_rcp(opq * opq * s2));
+    const T cst = qs * iD * lf_fma(s * w, iP, r2);
+    p = lf_fma(cse_a<T>(i), lin + lg - cst, p);
+  }
+  return p;
+}
+
 // alpha and psi_ij of one explicit component at offset (dx, dy), evaluated in U (T itself, or
 // dual numbers over the offset for third derivatives) with the component's constants in T.
 template <class T, class U>
 LF_INLINE void eval_comp_g(const CompT<T>& c, U dx, U dy, Out5<U>& o) {
   const U b = U(c.b), cc = U(c.c), sn = U(c.sn);
+  if (c.kind == K_ENFW) {
+    // offsets in r_s units; alpha = 2 kappa_s r_s alpha_cse, Psi = 2 kappa_s Psi_cse
+    const U irs = U(c.irs);
+    const U u = (cc * dx + sn * dy) * irs, v = (cc * dy - sn * dx) * irs;
+    U au, av, puu, pvv, puv;
+    enfw_uv<T, U>(u, v, U(c.q), U(c.q2), au, av, puu, pvv, puv);
+    const U k2 = U(2.0) * b, k2r = k2 * U(c.s1);
+    rotate_back(cc, sn, k2r * au, k2r * av, k2 * puu, k2 * pvv, k2 * puv, o);
+    return;
+  }
   if (c.kind == K_MPOLE3) {
     multipole3(dx, dy, cc, sn, o);
     o.ax = b * o.ax; o.ay = b * o.ay; o.pxx = b * o.pxx; o.pyy = b * o.pyy; o.pxy = b * o.pxy;
@@ -613,6 +698,10 @@ LF_INLINE T comp_potential(const CompT<T>& c, T dx, T dy) {
   if (c.kind == K_SHEAR)
     return c.b * ((T)0.5 * c.c * (dx * dx - dy * dy) + c.sn * dx * dy);
   if (c.kind == K_NFW) return nfw_potential(dx, dy, c.b, c.irs);
+  if (c.kind == K_ENFW) {   // psi = 2 kappa_s r_s^2 psi_cse(u / r_s, v / r_s)
+    const T u = (c.c * dx + c.sn * dy) * c.irs, v = (c.c * dy - c.sn * dx) * c.irs;
+    return (T)2 * c.b * c.s1sq * enfw_potential_uv(u, v, c.q, c.q2);
+  }
   const T u = c.round ? dx : c.c * dx + c.sn * dy;
   const T v = c.round ? dy : c.c * dy - c.sn * dx;
   T p = sie_potential_uv(u, v, c.q, c.q2, c.e, c.qe, c.s1, c.s1sq, c.q2s1, c.D01, (bool)c.round);
@@ -736,8 +825,28 @@ LF_INLINE void sie_alpha_ff(const ff& u, const ff& v, const ff& uu, const ff& vv
   av = ff_mul(qe, ff_atanh(z2, tab));
 }
 
+// alpha of the elliptical NFW's CSE sum (enfw_uv) with every operation in float-float: offsets
+// (u, v) in r_s units; returns the unit-kappa_s, r_s = 1 deflection in the (u, v) frame.
+__constant__ float2 c_cse_sff[LF_CSE_N] = {LF_CSE_S_FF_LIST};
+__constant__ float2 c_cse_cff[LF_CSE_N] = {LF_CSE_C_FF_LIST};   // a_i / s_i
+LF_INLINE void enfw_alpha_ff(const ff& u, const ff& v, const ff& q, const ff& q2, ff& au, ff& av) {
+  const ff uu = ff_sqr(u), vv = ff_sqr(v), r2 = ff_add(uu, vv), opq2 = ff_add_f(q2, 1.f);
+  au = ff_zero();
+  av = ff_zero();
+  for (int i = 0; i < LF_CSE_N; ++i) {
+    const float2 sv = c_cse_sff[i], cv = c_cse_cff[i];
+    const ff s = ff_make(sv.x, sv.y), s2 = ff_sqr(s);
+    const ff P = ff_sqrt(ff_add(ff_mul(q2, ff_add(s2, uu)), vv));
+    const ff D = ff_add(ff_add(ff_mul(opq2, s2), ff_mul_f(ff_mul(P, s), 2.f)), r2);
+    const ff f = ff_div(ff_mul(ff_make(cv.x, cv.y), q), ff_mul(P, D));
+    au = ff_add(au, ff_mul(ff_mul(f, u), ff_add(P, ff_mul(q2, s))));
+    av = ff_add(av, ff_mul(ff_mul(f, v), ff_add(P, s)));
+  }
+}
+
 // One explicit component for the mixed path: alpha in float-float for elliptical
-// isothermal components (SIE, dPIE) and the shear, FP32 otherwise; psi_ij in FP32.
+// isothermal components (SIE, dPIE), the elliptical NFW and the shear, FP32 otherwise;
+// psi_ij in FP32.
 LF_NOINLINE void eval_comp_mixed(const CompT<float>& c, float ph_x, float pl_x, float ph_y,
                                float pl_y, const float2* tab, ff& ax, ff& ay, Out5<float>& o) {
   const bool ell = (c.kind == K_SIE || c.kind == K_DPIE) && !c.round;
@@ -759,6 +868,24 @@ LF_NOINLINE void eval_comp_mixed(const CompT<float>& c, float ph_x, float pl_x, 
     const ff br = ff_mul(b, r);
     ax = ff_mul(br, ff_sub(Hx, ff_mul(G, nx)));
     ay = ff_mul(br, ff_sub(Hy, ff_mul(G, ny)));
+    return;
+  }
+  if (c.kind == K_ENFW) {
+    // psi_ij from the FP32 CSE sum; alpha recomputed in float-float
+    ff dx = offset_ff(ph_x, pl_x, c.xh, c.xl);
+    ff dy = offset_ff(ph_y, pl_y, c.yh, c.yl);
+    eval_comp(c, dx.hi, dy.hi, o);
+    const ff cc = ff_make(c.c, c.lc), sn = ff_make(c.sn, c.lsn), b = ff_make(c.b, c.lb);
+    const ff rs = ff_make(c.s1, c.ls1), q2 = ff_make(c.q2, c.lq2), q = ff_sqrt(q2);
+    const ff u = ff_div(ff_add(ff_mul(cc, dx), ff_mul(sn, dy)), rs);
+    const ff v = ff_div(ff_sub(ff_mul(cc, dy), ff_mul(sn, dx)), rs);
+    ff au, av;
+    enfw_alpha_ff(u, v, q, q2, au, av);
+    const ff k = ff_mul_f(ff_mul(b, rs), 2.f);
+    au = ff_mul(k, au);
+    av = ff_mul(k, av);
+    ax = ff_sub(ff_mul(cc, au), ff_mul(sn, av));
+    ay = ff_add(ff_mul(sn, au), ff_mul(cc, av));
     return;
   }
   if (!ell && c.kind != K_SHEAR) {

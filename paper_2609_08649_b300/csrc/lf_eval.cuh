@@ -42,12 +42,14 @@ __host__ __device__ inline PlaneLayout plane_layout(int nc, int nm, uint32_t bas
 // Validates and digests one raw component (device side; invalid -> kind 0 + error bit).
 template <class T>
 __device__ inline void digest_one_comp(const lf_comp& r, CompT<T>& out) {
-  bool ok = r.kind >= 1 && r.kind <= 5 && isfinite(r.x) && isfinite(r.y) && isfinite(r.b) &&
+  bool ok = r.kind >= 1 && r.kind <= 6 && isfinite(r.x) && isfinite(r.y) && isfinite(r.b) &&
             isfinite(r.pa);
   if (r.kind == LF_SIE || r.kind == LF_DPIE)
     ok = ok && r.eps >= 0.0 && r.eps < 1.0 && r.core >= 0.0 && isfinite(r.core);
   if (r.kind == LF_DPIE) ok = ok && isfinite(r.cut) && r.cut > r.core;
   if (r.kind == LF_NFW) ok = ok && r.core > 0.0 && isfinite(r.core);
+  if (r.kind == LF_ENFW)
+    ok = ok && r.core > 0.0 && isfinite(r.core) && r.eps >= 0.0 && r.eps < 1.0;
   digest_comp<T>(ok ? r.kind : 0, r.x, r.y, r.b, r.eps, r.pa, r.core, r.cut, out);
   if (!ok) lf_flag_error(LF_DEVERR_BADCOMP);
 }

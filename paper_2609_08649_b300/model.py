@@ -61,7 +61,7 @@ def comp_record(c: W.PhysComp, z_l, cosmo):
         ks, ts = nfw_params(cosmo, z_l, c.m200, c.conc)
         return (c.x, c.y, ks, 0.0, 0.0, ts, 0.0, c.kind)
     if c.kind == W.ENFW:   # spherical NFW normalisation, ellipticity applied to xi
-        ks, ts = nfw_params(cosmo, z_l, c.m200, c.conc)
+        ks, ts = (c.kappa_s, c.theta_s) if c.kappa_s is not None else nfw_params(cosmo, z_l, c.m200, c.conc)
         return (c.x, c.y, ks, c.eps, pa, ts, 0.0, c.kind)
     if c.kind == W.SHEAR:
         g = c.gamma if c.z_ref is None else c.gamma / adis(cosmo, z_l, c.z_ref)

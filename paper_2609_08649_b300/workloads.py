@@ -41,8 +41,8 @@ class PhysComp:
 
     kind: SIE/DPIE: x, y [arcsec], vdisp [km/s] (or theta_e [arcsec], the
     area-equivalent Einstein radius at source redshift z_ref), eps, pa_deg,
-    core_kpc / core_arcsec, cut_kpc.  NFW: m200 [Msun], conc.  ENFW: m200, conc, eps,
-    pa_deg.  SHEAR: gamma, pa_deg.
+    core_kpc / core_arcsec, cut_kpc.  NFW: m200 [Msun], conc.  ENFW: m200, conc (or kappa_s,
+    theta_s [arcsec]), eps, pa_deg.  SHEAR: gamma, pa_deg.
     """
     kind: int
     x: float = 0.0
@@ -59,6 +59,8 @@ class PhysComp:
     conc: Optional[float] = None
     gamma: Optional[float] = None
     amp: Optional[float] = None      # MPOLE3 amplitude A of psi = A theta^2 cos 3(phi - pa)
+    kappa_s: Optional[float] = None  # ENFW given in lensing units (instead of m200, conc)
+    theta_s: Optional[float] = None  # ENFW scale radius [arcsec]
 
 
 @dataclass
@@ -211,6 +213,36 @@ def cluster_c2_mpole(n_samples: int = 4096, seed: int = 2) -> Workload:
                                 ParamSpec(k, F_PA, XF_DEG, 10.0, 5.0, False)]
     return dataclasses.replace(wl, name="cluster_mpole_4096x200",
                                planes=[dataclasses.replace(pl, comps=comps)], params=params)
+
+
+def cluster_c5_enfw(n_samples: int = 4096, seed: int = 6) -> Workload:
+    """A cluster shaped like the paper's Hera model (Sec. 4.2): two elliptical NFW halos at
+    fixed positions (kappa_s, theta_s of M200 = 1.2e15 and 3e14 Msun with c = 5 and 6 at
+    z = 0.5), external shear, an m = 3 multipole and C1's 300 members on the scaling
+    relations.  14 sampled parameters as in that model: per halo kappa_s, theta_s, eps and pa;
+    the shear's strength and angle; the multipole's amplitude and angle; v* and cut*.  The
+    families are C2's (200 images)."""
+    c1 = cluster_c1()
+    halos = [PhysComp(ENFW, 0.0, 0.0, kappa_s=0.5618, theta_s=60.03, eps=0.2, pa_deg=30.0),
+             PhysComp(ENFW, 25.0, -15.0, kappa_s=0.4486, theta_s=31.51, eps=0.3, pa_deg=-20.0)]
+    comps = halos + [PhysComp(SHEAR, gamma=0.05, pa_deg=0.0),
+                     PhysComp(MPOLE3, 0.0, 0.0, amp=0.004, pa_deg=10.0)]
+    params = []
+    for k, h in enumerate(halos):
+        params += [ParamSpec(k, F_B, XF_IDENT, h.kappa_s, 0.01, True),
+                   ParamSpec(k, F_CORE, XF_IDENT, h.theta_s, 0.01, True),
+                   ParamSpec(k, F_EPS, XF_IDENT, h.eps, 0.02, False),
+                   ParamSpec(k, F_PA, XF_DEG, h.pa_deg, 2.0, False)]
+    params += [ParamSpec(2, F_B, XF_IDENT, 0.05, 0.005, False),
+               ParamSpec(2, F_PA, XF_DEG, 0.0, 5.0, False),
+               ParamSpec(3, F_B, XF_IDENT, 0.004, 0.0005, False),
+               ParamSpec(3, F_PA, XF_DEG, 10.0, 5.0, False),
+               ParamSpec(-1, 0, XF_VDISP, 250.0, 0.01, True),
+               ParamSpec(-1, 2, XF_KPC, 45.0, 0.01, True)]
+    c2 = cluster_c2()
+    return Workload("cluster_enfw_4096x200", Cosmo(), [PhysPlane(0.5, comps, c1.planes[0].members)],
+                    params=params, n_samples=n_samples, seed=seed, sigma_pos=0.1,
+                    family_sizes=c2.family_sizes, family_zs=c2.family_zs)
 
 
 def multiplane_c3(n_grid: int = 2048, n_samples: int = 1024, seed: int = 4) -> Workload:
