@@ -741,38 +741,42 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
       }
       __syncthreads();
       // ---- A8 (mixed tiers): per family, offsets e_i = beta_i - beta_ref from the family's
-      // first image (float-float, then FP64), G and g in FP64 with the FP32 M_i, the 2x2
-      // solve and chi^2_f in FP64.  (The adjoint needs beta_model to FP64 accuracy: an error
-      // in it enters the gradient at first order.)
+      // first image, G = sum M_i, g = sum M_i e_i, the 2x2 solve and chi^2_f, all in
+      // float-float on the FP32 pipe (the FP64 pipe is the slow one on this part).  The
+      // 48-bit float-float result carries beta_model to the accuracy the adjoint needs (an
+      // error in it enters the gradient at first order); it is stored as FP64.
       for (int f = tid; f < C.n_fam; f += blockDim.x) {
         const int i0 = C.fam_off[f], i1 = C.fam_off[f + 1];
         const float* r0 = imgf + i0 * ISF;
         const ff br0 = ff_make(r0[10], r0[11]), br1 = ff_make(r0[12], r0[13]);
-        double G00 = 0, G01 = 0, G11 = 0, g0 = 0, g1 = 0;
+        ff G00 = ff_zero(), G01 = ff_zero(), G11 = ff_zero(), g0 = ff_zero(), g1 = ff_zero();
         for (int i = i0; i < i1; ++i) {
           const float* r = imgf + i * ISF;
-          const double e0 = ff_to_double(ff_sub(ff_make(r[10], r[11]), br0));
-          const double e1 = ff_to_double(ff_sub(ff_make(r[12], r[13]), br1));
-          G00 += r[14]; G01 += r[15]; G11 += r[16];
-          g0 += (double)r[14] * e0 + (double)r[15] * e1;
-          g1 += (double)r[15] * e0 + (double)r[16] * e1;
+          const ff e0 = ff_sub(ff_make(r[10], r[11]), br0), e1 = ff_sub(ff_make(r[12], r[13]), br1);
+          ff_acc(G00, r[14]); ff_acc(G01, r[15]); ff_acc(G11, r[16]);
+          g0 = ff_add(g0, ff_add(ff_mul_f(e0, r[14]), ff_mul_f(e1, r[15])));
+          g1 = ff_add(g1, ff_add(ff_mul_f(e0, r[15]), ff_mul_f(e1, r[16])));
         }
         double cf = 0.0, c0 = 0.0, c1 = 0.0;
         if (i1 - i0 == 1) {
-          if (!(isfinite(G00) && isfinite(G01) && isfinite(G11) && isfinite(br0.hi) && isfinite(br1.hi)))
+          if (!(isfinite(G00.hi) && isfinite(G01.hi) && isfinite(G11.hi) && isfinite(br0.hi) && isfinite(br1.hi)))
             cf = INFINITY;
         } else {
-          const double dG = G00 * G11 - G01 * G01;
-          const double idG = 1.0 / dG;
-          c0 = (G11 * g0 - G01 * g1) * idG;
-          c1 = (G00 * g1 - G01 * g0) * idG;
+          const ff dG = ff_sub(ff_mul(G00, G11), ff_sqr(G01));
+          const ff cx = ff_div(ff_sub(ff_mul(G11, g0), ff_mul(G01, g1)), dG);
+          const ff cy = ff_div(ff_sub(ff_mul(G00, g1), ff_mul(G01, g0)), dG);
+          ff acc = ff_zero();
           for (int i = i0; i < i1; ++i) {
             const float* r = imgf + i * ISF;
-            const double d0 = ff_to_double(ff_sub(ff_make(r[10], r[11]), br0)) - c0;
-            const double d1 = ff_to_double(ff_sub(ff_make(r[12], r[13]), br1)) - c1;
-            cf += (double)r[14] * d0 * d0 + 2.0 * (double)r[15] * d0 * d1 + (double)r[16] * d1 * d1;
+            const ff d0 = ff_sub(ff_sub(ff_make(r[10], r[11]), br0), cx);
+            const ff d1 = ff_sub(ff_sub(ff_make(r[12], r[13]), br1), cy);
+            acc = ff_add(acc, ff_add(ff_mul_f(ff_sqr(d0), r[14]),
+                                     ff_add(ff_mul_f(ff_mul(d0, d1), 2.f * r[15]), ff_mul_f(ff_sqr(d1), r[16]))));
           }
-          if (!isfinite(cf) || !(dG > 0.0)) cf = INFINITY;
+          cf = ff_to_double(acc);
+          c0 = ff_to_double(cx);
+          c1 = ff_to_double(cy);
+          if (!isfinite(cf) || !(dG.hi > 0.f)) cf = INFINITY;
         }
         fam[3 * f] = cf;
         fam[3 * f + 1] = c0;
