@@ -189,6 +189,14 @@ def nfw_sph(dx, dy, ks, rs):
     Hs = _series(torch.where(nu, u, torch.zeros_like(u)))
     Hsum = torch.where(nu, Hs, torch.where(u > 0, Hl, Hg))
     h = torch.log(x / 2.0) + 2.0 / (1.0 + x) * Hsum
+    # Toward the centre the two terms cancel (h ~ x^2 ln(2/x) / 2 while each is ~ ln(2/x)).  For
+    # x < 1, 2 atanh(sqrt(u)) = ln((1 + s)/x) with s = sqrt(1 - x^2), and 1 - s = d = x^2/(1 + s),
+    # so h = [s ln(x/2) + ln((1 + s)/x)] / s = [d ln(2/x) + ln(1 - d/2)] / s, free of it.
+    sm = (x < 0.5) & (x > 0)
+    xs = torch.where(sm, x, torch.full_like(x, 0.25))
+    sq = torch.sqrt((1.0 - xs) * (1.0 + xs))
+    d = xs * xs / (1.0 + sq)
+    h = torch.where(sm, (d * torch.log(2.0 / xs) + torch.log1p(-0.5 * d)) / sq, h)
     kbar = 4.0 * ks * h / x2
     return _axisym(dx, dy, kbar, kappa, r2)
 

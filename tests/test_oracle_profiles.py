@@ -274,3 +274,22 @@ def test_round_branch_derivative_in_q_is_the_elliptical_limit(prof):
         lim = (4 * r2 - r1) / 3
         scale = max(float(g.abs().max()), 1e-3)
         assert float((g - lim).abs().max()) < 1e-7 * scale, (k, g, lim)
+
+
+def test_nfw_mean_convergence_near_the_centre_to_full_precision():
+    """alpha = 4 ks rs h(x) / x with h = ln(x/2) + arccosh(1/x)/sqrt(1 - x^2) (x < 1), or
+    ln(x/2) + arccos(1/x)/sqrt(x^2 - 1) (x > 1), against the same formula evaluated with 50
+    digits (mpmath): near the centre the two terms of h cancel, and h must still carry full
+    FP64 precision (the multi-plane Jacobian multiplies its error by 1/x^2)."""
+    import mpmath as mp
+    mp.mp.dps = 50
+    ks, rs = 0.3, 4.0
+    for x in (1e-4, 1e-3, 3.6e-3, 1e-2, 0.1, 0.4, 0.49, 0.51, 0.8, 1.5, 4.0):
+        X = mp.mpf(x)
+        if x < 1:
+            h = mp.log(X / 2) + mp.acosh(1 / X) / mp.sqrt(1 - X * X)
+        else:
+            h = mp.log(X / 2) + mp.acos(1 / X) / mp.sqrt(X * X - 1)
+        ref = float(4 * ks * rs * h / X)
+        o = pr.nfw_sph(T(x * rs), T(0.0), ks, rs)
+        assert abs(float(o[0]) / ref - 1) < 1e-13, (x, float(o[0]), ref)
