@@ -92,3 +92,32 @@ def test_trace_images_of_chi2_workload(lib):
     sa = _abs_scale(wl, cat.theta_obs[:, 0].copy(), cat.theta_obs[:, 1].copy())
     assert np.all(np.abs(beta.cpu().numpy() - b0).max(1) <= 1e-6 + 16 * U32 * sa)
     api.device_error()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "ff"])
+def test_three_plane_trace_with_elliptical_nfw_halos(lib, prec):
+    """The three-plane model with the main plane's two halos replaced by the elliptical NFW
+    halos of the Hera-like workload (38-term cored-steep-ellipsoid sums), against the
+    oracle's recursion; tolerances as for the three-plane grid (one ray lands 0.04" from an
+    NFW centre on the second plane, where the Jacobian magnifies errors in psi_ij)."""
+    api, PM = lib
+    wl = W.multiplane_c3(n_grid=8)
+    halos = [c for c in W.cluster_c5_enfw(n_samples=1).planes[0].comps if c.kind == W.ENFW]
+    p0 = wl.planes[0]
+    wl = W.replace(wl, planes=[W.replace(p0, comps=halos + list(p0.comps[2:]))] + list(wl.planes[1:]),
+                   params=[])
+    grid = W.Grid(-80.0, -79.0, 2.3, 2.1, 71, 77)
+    X, Y = grid_xy(grid)
+    planes = PM.device_planes(wl)
+    r = PM.multiplane_ratios(wl.cosmo, [p.z for p in wl.planes], wl.z_s)
+    beta, A = api.trace_multiplane(planes, r, grid=grid, precision=prec)
+    b0, A0 = _oracle_trace(wl, X.ravel(), Y.ravel())
+    beta, A = beta.cpu().numpy(), A.cpu().numpy()
+    api.device_error()
+    if prec == "fp64":
+        assert np.abs(beta - b0).max() < 1e-10
+        assert np.abs(A - A0).max() < 1e-10
+    else:
+        sa = _abs_scale(wl, X.ravel(), Y.ravel())
+        assert np.all(np.abs(beta - b0).max(1) <= 1e-6 + 16 * U32 * sa)
+        assert np.abs(A - A0).max() < 1e-4
