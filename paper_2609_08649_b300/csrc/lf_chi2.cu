@@ -276,6 +276,9 @@ constexpr int IMGF = 22;
 // LF_CHI2_FWD_MINB blocks of up to LF_CHI2_FWD_THREADS threads share an SM: each block works
 // on one sample, whose ~100 image pairs fill only a few warps, so warps come from more
 // resident samples.
+#ifndef LF_CHI2_IPT
+#define LF_CHI2_IPT 2     // images per task in the mixed tiers' evaluation
+#endif
 #ifndef LF_CHI2_FWD_THREADS
 #define LF_CHI2_FWD_THREADS 128
 #endif
@@ -379,9 +382,9 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
   // the mixed tier's forward passes evaluate members two at a time (packed pair records, f32x2);
   // the adjoint and the flux / time-delay pass read the scalar records
   constexpr bool PACKM = (MODE == LF_MIXED) && !GRAD && PASS != 2;
-  // images per evaluation task (two independent chains per thread; with packed members, four
-  // member evaluations per pair of instructions)
-  constexpr int IPT = 2;
+  // images per evaluation task (independent chains per thread; with packed members, two
+  // member evaluations per instruction and chain); the FP64 tier takes two
+  constexpr int IPT = MIXED ? LF_CHI2_IPT : 2;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   int* s_item = reinterpret_cast<int*>(smem + 8);
@@ -542,7 +545,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
     // component slice): two images per thread give two independent evaluation chains.
     const int n_img = C.n_img, KS = C.ks, IS = C.img_stride, ISF = C.img_stride_f,
               ISD = C.img_stride_d;
-    const int n_unit = IPT == 2 ? (n_img + 1) >> 1 : n_img;
+    const int n_unit = (n_img + IPT - 1) / IPT;
     // The units that do not fill whole warps (the tail) share one warp with more component
     // slices each (KST), so that no warp runs the whole component loop with a few active
     // lanes.  Main tasks end on a warp boundary, so each warp has one slice count.
@@ -572,8 +575,8 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         if constexpr (MIXED) {
           float xh[IPT], xl[IPT], yh[IPT], yl[IPT];
           int ii[IPT];
-          ii[0] = IPT * pr;
-          if constexpr (IPT == 2) ii[1] = min(2 * pr + 1, n_img - 1);
+#pragma unroll
+          for (int q = 0; q < IPT; ++q) ii[q] = min(IPT * pr + q, n_img - 1);
 #pragma unroll
           for (int q = 0; q < IPT; ++q) {
             if (j == 0 && !pos) {
@@ -615,7 +618,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           if (act && k == 0) {
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
-              if (q > 0 && ii[q] == ii[0]) break;
+              if (q > 0 && ii[q] == ii[q - 1]) break;     // the clamped repeats of the last unit
               for (int c5 = 0; c5 < 5; ++c5) {
                 imgf[ii[q] * ISF + 2 * c5] = acc[c5][q].hi;
                 imgf[ii[q] * ISF + 2 * c5 + 1] = acc[c5][q].lo;
@@ -1192,27 +1195,42 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         if (mem_grad) {
           const int m0 = max(k0, P.nc) - P.nc, m1 = min(k1, K) - P.nc;
           T gs[6] = {0, 0, 0, 0, 0, 0};
+          T qxh, qxl, qyh, qyl;
+          if constexpr (MIXED) {
+            float a_, b_, c_, d_;
+            split_ff(px, a_, b_);
+            split_ff(py, c_, d_);
+            qxh = a_; qxl = b_; qyh = c_; qyl = d_;
+          } else {
+            qxh = (T)px; qxl = (T)0; qyh = (T)py; qyl = (T)0;
+          }
+          // Each member's (alpha, Psi) per unit strength is kbar (dx, dy) and
+          // Psi_ij = kbar delta_ij + t x_i x_j; its derivative in a parameter contracts with the
+          // cotangents as kbar' U + t' V, with U and V below.  Closed forms, P = 1/(S + s),
+          // Q = 1/(R + a): dkbar/ds = -P/S, dkbar/da = Q/R, dt/ds = (P^2/S^2)(2 + s/S),
+          // dt/da = -(Q^2/R^2)(2 + a/R); kbar = P - Q is taken in its cancellation-free form.
           for (int m = m0; m < m1; ++m) {
             const Mem& M = dm[m];
-            typedef Dual<T, 2> D2;
             const T Ms = mem_s(M), Ma = mem_a(M);
-            D2 sd = D2::var(Ms, 0), ad = D2::var(Ma, 1);
-            Out5<D2> o;
             T dx, dy;
             if constexpr (MIXED) {
-              float xh, xl, yh, yl;
-              split_ff(px, xh, xl);
-              split_ff(py, yh, yl);
-              dx = offset_of(xh, xl, M.xh, M.xl);
-              dy = offset_of(yh, yl, M.yh, M.yl);
+              dx = offset_of(qxh, qxl, M.xh, M.xl);
+              dy = offset_of(qyh, qyl, M.yh, M.yl);
             } else {
-              dx = px - M.xh;
-              dy = py - M.yh;
+              dx = qxh - M.xh;
+              dy = qyh - M.yh;
             }
-            pje_round(D2::cst(dx), D2::cst(dy), D2::cst((T)1), sd, sd * sd, ad, ad * ad, o);
-            const T Gb = contract(o, cot, -1);
-            const T Gs = M.b * contract(o, cot, 0);
-            const T Ga = M.b * contract(o, cot, 1);
+            const T dxx = dx * dx, dyy = dy * dy, r2 = dxx + dyy;
+            const T iS = ::lf_rsqrt(::lf_fma(Ms, Ms, r2)), iR = ::lf_rsqrt(::lf_fma(Ma, Ma, r2));
+            const T S = ::lf_fma(Ms, Ms, r2) * iS, R = ::lf_fma(Ma, Ma, r2) * iR;
+            const T Pq = ::lf_rcp(S + Ms), Qq = ::lf_rcp(R + Ma);
+            const T kb = (Ma - Ms) * Pq * Qq * ::lf_fma(Ma + Ms, ::lf_rcp(R + S), (T)1);
+            const T P2iS = Pq * Pq * iS, Q2iR = Qq * Qq * iR;
+            const T U = ::lf_fma(cot[0], dx, ::lf_fma(cot[1], dy, cot[2] + cot[3]));
+            const T V = ::lf_fma(cot[2], dxx, ::lf_fma(cot[3], dyy, cot[4] * dx * dy));
+            const T Gb = ::lf_fma(kb, U, (Q2iR - P2iS) * V);
+            const T Gs = M.b * ::lf_fma(-Pq * iS, U, P2iS * iS * ::lf_fma(Ms, iS, (T)2) * V);
+            const T Ga = M.b * ::lf_fma(Qq * iR, U, -Q2iR * iR * ::lf_fma(Ma, iR, (T)2) * V);
             const T fa = Ma * inv_cut_star;
             gs[LF_S_BSTAR] += Gb * M.fb;
             gs[LF_S_LAM] += Gb * M.b * (T)2 * M.loglr;
