@@ -273,8 +273,10 @@ lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int32_t S, doub
  * source beta_model = G^-1 g of Sec. 3.1; then chi2_img = sum_i (theta_obs - theta_model)^T
  * S_i^-1 (theta_obs - theta_model) and rms = sqrt(mean_i |theta_obs - theta_model|^2), the
  * image-plane rms the paper reports.  chi2_img, rms: device [S] FP64 (rms may be NULL).
- * 1 <= iters <= 64.  Single-plane plans only (LF_EUNSUPPORTED otherwise).  A sample whose
- * Newton iteration leaves the finite range gets chi2_img = +inf. */
+ * 1 <= iters <= 64.  Multi-plane plans take beta(theta) and the non-symmetric A(theta) of the
+ * recursion of Sec. 2.2 to each family's source plane.  A plan whose Newton state does not fit
+ * in shared memory next to its tables returns LF_EUNSUPPORTED.  A sample whose Newton
+ * iteration leaves the finite range gets chi2_img = +inf. */
 lf_status lf_chi2_img_batch(lf_plan* plan, const double* theta, int32_t S, int32_t iters,
                             double* chi2_img, double* rms, void* stream);
 

@@ -256,16 +256,27 @@ def single_plane_source_terms(pl: LPlane, theta_obs, fam_off, fam_adis):
     return beta, A
 
 
+def image_ratios(fam_rs, fam_off, n_planes):
+    """(n_planes, N) ratios D_js/D_s of each image's family."""
+    N = int(fam_off[-1])
+    rs = torch.zeros(n_planes, N, dtype=torch.float64)
+    for f in range(len(fam_off) - 1):
+        for j in range(n_planes):
+            rs[j, int(fam_off[f]):int(fam_off[f + 1])] = float(fam_rs[f][j])
+    return rs
+
+
 def multi_plane_source_terms(planes, r, fam_rs, theta_obs, fam_off):
     """Per image, beta and A traced through all planes to its family's source
     (fam_rs[f][j] = D_js/D_s for that family's redshift)."""
-    tx, ty = theta_obs[None, :, 0], theta_obs[None, :, 1]
+    rs = image_ratios(fam_rs, fam_off, len(planes))
+    return multi_plane_beta_A(planes, r, rs, theta_obs[None, :, 0], theta_obs[None, :, 1])
+
+
+def multi_plane_beta_A(planes, r, rs, tx, ty):
+    """beta (S, N, 2) and A (S, N, 2, 2) of the recursion at positions (tx, ty) of shape
+    (S or 1, N), each position traced to its own source plane with ratios rs (n_planes, N)."""
     t1, alphas, psis, As = multiplane_parts(planes, r, tx, ty)
-    N = theta_obs.shape[0]
-    rs = torch.zeros(len(planes), N, dtype=torch.float64)
-    for f in range(len(fam_off) - 1):
-        for j in range(len(planes)):
-            rs[j, int(fam_off[f]):int(fam_off[f + 1])] = float(fam_rs[f][j])
     beta = t1.clone()
     eye = torch.eye(2, dtype=torch.float64)
     A = eye.expand_as(As[0]).clone()

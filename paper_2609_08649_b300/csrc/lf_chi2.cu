@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           pj[4] = sm[4] * a00 + sm[3] * a10;
           pj[5] = sm[4] * a01 + sm[3] * a11;
           if (j + 1 < C.np) {
-            double tx = C.theta[2 * i], ty = C.theta[2 * i + 1];
+            double tx = pos ? pos[4 * i] : C.theta[2 * i], ty = pos ? pos[4 * i + 1] : C.theta[2 * i + 1];
             for (int l = 0; l <= j; ++l) {
               tx -= C.r[l][j + 1] * st[2 + 6 * l];
               ty -= C.r[l][j + 1] * st[2 + 6 * l + 1];
@@ -992,8 +992,25 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           } else {
             for (int c5 = 0; c5 < 5; ++c5) sm[c5] = img[i * IS + c5];
           }
-          const double a = fa[C.img_fam[i]];
           const double tx = nst[4 * i], ty = nst[4 * i + 1];
+          if (C.np > 1) {
+            // beta and the (non-symmetric) A of the recursion to the family's source plane
+            const int f = C.img_fam[i];
+            const double* st = MIXED ? imgd + i * ISD : img + i * IS + 14;
+            double bx = tx, by = ty, A00 = 1, A01 = 0, A10 = 0, A11 = 1;
+            for (int l = 0; l < C.np; ++l) {
+              const double rs = C.fam_ratio[f * C.np + l];
+              const double* pl = st + 2 + 6 * l;
+              bx -= rs * pl[0]; by -= rs * pl[1];
+              A00 -= rs * pl[2]; A01 -= rs * pl[3]; A10 -= rs * pl[4]; A11 -= rs * pl[5];
+            }
+            const double rx = bx - nst[4 * i + 2], ry = by - nst[4 * i + 3];
+            const double id = 1.0 / (A00 * A11 - A01 * A10);
+            nst[4 * i] = tx - (A11 * rx - A01 * ry) * id;
+            nst[4 * i + 1] = ty - (A00 * ry - A10 * rx) * id;
+            continue;
+          }
+          const double a = fa[C.img_fam[i]];
           const double rx = tx - a * sm[0] - nst[4 * i + 2];
           const double ry = ty - a * sm[1] - nst[4 * i + 3];
           const double A00 = 1.0 - a * sm[2], A11 = 1.0 - a * sm[3], A01 = -a * sm[4];
@@ -1928,7 +1945,6 @@ extern "C" lf_status lf_chi2_img_batch(lf_plan* plan, const double* theta, int32
   if (S < 1 || S > plan->max_samples) return fail(LF_EINVAL, "S must be in 1..%d", plan->max_samples);
   if (S % plan->n_clusters) return fail(LF_EINVAL, "S must be a multiple of the number of clusters");
   if (iters < 1 || iters > 64) return fail(LF_EINVAL, "iters must be in 1..64");
-  if (!plan->single_plane) return fail(LF_EUNSUPPORTED, "the image-plane chi^2 is implemented for single-plane plans");
   if (plan->smem_img == 0) return fail(LF_EUNSUPPORTED, "the image-plane Newton state does not fit in shared memory");
   cudaStream_t st = (cudaStream_t)stream;
   const int spc = S / plan->n_clusters;

@@ -3,6 +3,7 @@ zero on noise-free images, model images equal to the marching-squares solver's i
 beta_model, the lens equation satisfied at the model images, and chi^2_src close to
 chi^2_img for small offsets (Eq. delta)."""
 import numpy as np
+import pytest
 import torch
 
 from oracle import images as im
@@ -75,3 +76,70 @@ def test_source_plane_chi2_approximates_image_plane_chi2():
     csrc = OG.chi2_only(wl, th, tobs, sinv, list(cat.fam_off), adis)
     cimg, _, _ = ip.chi2_img(wl, th, tobs, sinv, list(cat.fam_off), adis)
     assert abs(float(csrc[0]) / float(cimg[0]) - 1) < 0.05
+
+
+@pytest.fixture(scope="module")
+def three_plane():
+    from tests.helpers import three_plane_images
+    return three_plane_images()
+
+
+def test_multiplane_reduces_to_single_plane_with_massless_later_planes():
+    """Three planes whose second and third carry nothing: the multi-plane chi2_img equals the
+    single-plane one with a_dis = D_ds/D_s of each family."""
+    from oracle import cosmology as cz
+    wl3 = W.multiplane_c3(n_grid=8, n_samples=3)
+    wl3 = W.replace(wl3, planes=[wl3.planes[0]] + [W.replace(p, comps=[], members=None) for p in wl3.planes[1:]])
+    wl1 = W.replace(wl3, planes=[wl3.planes[0]])
+    cat = W.load_catalogue("cluster_200")
+    zs = np.where(np.arange(len(cat.fam_zs)) % 2 == 0, 4.0, 2.5)
+    th = torch.tensor(W.sample_thetas(wl3, wl3.seed))
+    th[:, :] = th[0]                     # the unjittered model: Newton from the catalogue stays tame
+    n = len(cat.theta_obs)
+    sinv = torch.tensor(np.tile([1e4, 0, 1e4], (n, 1)))
+    tobs = torch.tensor(cat.theta_true)
+    c3, r3, t3 = ip.chi2_img(wl3, th, tobs, sinv, list(cat.fam_off), iters=8, fam_zs=list(zs))
+    z = [p.z for p in wl3.planes]
+    adis = [cz.multiplane_ratios(z, zf, wl3.cosmo.H0, wl3.cosmo.Om)[1][0] for zf in zs]
+    c1, r1, t1 = ip.chi2_img(wl1, th, tobs, sinv, list(cat.fam_off), adis, iters=8)
+    fin = torch.isfinite(c1)
+    assert fin.all()
+    assert torch.allclose(c3, c1, rtol=1e-11, atol=0)
+    assert torch.allclose(t3, t1, rtol=0, atol=1e-10)
+
+
+def test_multiplane_noise_free_images_give_zero(three_plane):
+    """True images of the three-plane model (found on a grid and polished with the multi-plane
+    lens equation): with the model that made them, the model images are the observed ones."""
+    wl, cat = three_plane
+    th = torch.tensor(W.sample_thetas(wl, wl.seed)[:1])
+    n = len(cat.theta_true)
+    sinv = torch.tensor(np.tile([1e6, 0, 1e6], (n, 1)))
+    c, r, tm = ip.chi2_img(wl, th, torch.tensor(cat.theta_true), sinv, list(cat.fam_off), iters=6,
+                           fam_zs=list(cat.fam_zs))
+    assert float(r[0]) < 1e-10 and float(c[0]) < 1e-12
+
+
+def test_multiplane_model_images_solve_the_lens_equation(three_plane):
+    """With 1 mas noise, every model image satisfies the multi-plane lens equation for its
+    family's analytic source to 1e-10 arcsec, within a few mas of the observed image."""
+    from oracle import cosmology as cz
+    wl, cat = three_plane
+    th = torch.tensor(W.sample_thetas(wl, wl.seed)[:1])
+    n = len(cat.theta_obs)
+    sinv = torch.tensor(np.tile([1e6, 0, 1e6], (n, 1)))
+    tobs = torch.tensor(cat.theta_obs)
+    c, r, tm = ip.chi2_img(wl, th, tobs, sinv, list(cat.fam_off), iters=8, fam_zs=list(cat.fam_zs))
+    planes = om.apply_params(wl, th)
+    zs = [p.z for p in wl.planes]
+    rr, _ = cz.multiplane_ratios(zs, zs[-1] + 1.0, wl.cosmo.H0, wl.cosmo.Om)
+    fam_rs = [cz.multiplane_ratios(zs, z, wl.cosmo.H0, wl.cosmo.Om)[1] for z in cat.fam_zs]
+    beta, A = L.multi_plane_source_terms(planes, rr, fam_rs, tobs, list(cat.fam_off))
+    bm = ip.source_models(beta, A, sinv, list(cat.fam_off))[0]
+    rs = L.image_ratios(fam_rs, list(cat.fam_off), len(planes))
+    b, _ = L.multi_plane_beta_A(planes, rr, rs, tm[:, :, 0], tm[:, :, 1])
+    for f in range(len(cat.fam_off) - 1):
+        i0, i1 = cat.fam_off[f], cat.fam_off[f + 1]
+        assert float((b[0, i0:i1] - bm[f]).abs().max()) < 1e-10
+    assert float((tm[0] - tobs).norm(dim=-1).max()) < 0.01
+    assert 0 < float(r[0]) < 0.005
