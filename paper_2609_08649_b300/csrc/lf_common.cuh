@@ -289,41 +289,32 @@ LF_INLINE void pje_round(T dx, T dy, T b, T s, T s2, T a, T a2, Out5<T>& o) {
   o.pxy = t * dx * dy;
 }
 
-// sum_{n>=0} w^n / (2n + 1) truncated (for |w| < 0.1, 9 terms reach 1e-10 relative).
-template <class T> LF_INLINE T series_odd(T w) {
-  T r = (T)(1.0 / 19.0);
-  r = lf_fma(r, w, (T)(1.0 / 17.0));
-  r = lf_fma(r, w, (T)(1.0 / 15.0));
-  r = lf_fma(r, w, (T)(1.0 / 13.0));
-  r = lf_fma(r, w, (T)(1.0 / 11.0));
-  r = lf_fma(r, w, (T)(1.0 / 9.0));
-  r = lf_fma(r, w, (T)(1.0 / 7.0));
-  r = lf_fma(r, w, (T)(1.0 / 5.0));
-  r = lf_fma(r, w, (T)(1.0 / 3.0));
-  r = lf_fma(r, w, (T)1);
+// Scalar type of an evaluation type (float, double, or dual numbers over one of them).
+template <class T> struct scalar_of { typedef T type; };
+
+// Near x = 1 (w = 1 - x^2 small) the NFW functions as series in w, free of the cancellation
+// of their closed forms there:
+//   g = (F - 1)/(1 - x^2) = sum_{n>=1} w^(n-1) / (2n + 1),
+//   h = (1 - ln 2) - (1/2) sum_{n>=1} w^n / (n (2n + 1))   (from dh/dx = x g, h(1) = 1 - ln 2).
+// FP32 uses them for |w| < 0.5 (26 and 24 terms), FP64 for |w| < 0.1 (17 and 16 terms).
+template <class T, int N> LF_INLINE T nfw_series_g(T w) {
+  T r = (T)(1.0 / (2.0 * N + 1.0));
+#pragma unroll
+  for (int n = N - 1; n >= 1; --n) r = lf_fma(r, w, (T)(1.0 / (2.0 * n + 1.0)));
   return r;
 }
-// sum_{n>=1} w^(n-1) / (2n + 1)
-template <class T> LF_INLINE T series_tail(T w) {
-  T r = (T)(1.0 / 21.0);
-  r = lf_fma(r, w, (T)(1.0 / 19.0));
-  r = lf_fma(r, w, (T)(1.0 / 17.0));
-  r = lf_fma(r, w, (T)(1.0 / 15.0));
-  r = lf_fma(r, w, (T)(1.0 / 13.0));
-  r = lf_fma(r, w, (T)(1.0 / 11.0));
-  r = lf_fma(r, w, (T)(1.0 / 9.0));
-  r = lf_fma(r, w, (T)(1.0 / 7.0));
-  r = lf_fma(r, w, (T)(1.0 / 5.0));
-  r = lf_fma(r, w, (T)(1.0 / 3.0));
-  return r;
+template <class T, int N> LF_INLINE T nfw_series_h(T w) {
+  T r = (T)(1.0 / (N * (2.0 * N + 1.0)));
+#pragma unroll
+  for (int n = N - 1; n >= 1; --n) r = lf_fma(r, w, (T)(1.0 / (n * (2.0 * n + 1.0))));
+  return r * w;
 }
 
 // Spherical NFW of strength ks and scale radius rs (irs = 1/rs).
 //  g = (F - 1)/(1 - x^2) so that kappa = 2 ks g;
 //  h(x) for x < 1 in the cancellation-free arrangement
 //     h = [d (ln 2 - ln x) + log1p(-d/2)] / w,  w = sqrt(1 - x^2), d = x^2 / (1 + w),
-//  for x > 1: h = ln(x/2) + acos(1/x) / sqrt(x^2 - 1); near x = 1 the power series
-//     h = ln(x/2) + (2/(1+x)) sum_n u^n/(2n+1), u = (1-x)/(1+x).
+//  for x > 1: h = ln(x/2) + acos(1/x) / sqrt(x^2 - 1); near x = 1 the series above.
 template <class T>
 LF_INLINE void nfw_sph(T dx, T dy, T ks, T irs, Out5<T>& o) {
   T r2 = lf_fma(dx, dx, dy * dy);
@@ -332,10 +323,16 @@ LF_INLINE void nfw_sph(T dx, T dy, T ks, T irs, Out5<T>& o) {
   T w2 = ((T)1 - x) * ((T)1 + x);  // 1 - x^2
   T g, h;
   const T ln2 = (T)0.69314718055994530942;
-  if (w2 < (T)0.1 && w2 > (T)-0.1) {
-    g = series_tail(w2);
-    T u = ((T)1 - x) * lf_rcp((T)1 + x);
-    h = lf_log(x * (T)0.5) + (T)2 * lf_rcp((T)1 + x) * series_odd(u);
+  constexpr bool f32 = std::is_same<typename scalar_of<T>::type, float>::value;
+  const T band = (T)(f32 ? 0.5 : 0.1);
+  if (w2 < band && w2 > -band) {
+    if constexpr (f32) {
+      g = nfw_series_g<T, 26>(w2);
+      h = (T)0.30685281944005469058 - (T)0.5 * nfw_series_h<T, 24>(w2);
+    } else {
+      g = nfw_series_g<T, 17>(w2);
+      h = (T)0.30685281944005469058 - (T)0.5 * nfw_series_h<T, 16>(w2);
+    }
   } else if (w2 > (T)0) {
     T w = lf_sqrt(w2);
     T F = lf_log(((T)1 + w) * lf_rcp(x)) * lf_rcp(w);   // atanh(w) = ln((1 + w)/x)
@@ -932,6 +929,90 @@ LF_NOINLINE void eval_comp_mixed(const CompT<float>& c, float ph_x, float pl_x, 
   Out5<float> t;
   rotate_back(c.c, c.sn, 0.f, 0.f, c.b * puu, c.b * pvv, c.b * puv, t);
   o.pxx = t.pxx; o.pyy = t.pyy; o.pxy = t.pxy;
+}
+
+// ln(y), y > 0, in float-float: y = m 2^e with m in [1/sqrt 2, sqrt 2) (exact scaling by a
+// power of two), ln y = e ln 2 + 2 atanh((m - 1)/(m + 1)), |(m - 1)/(m + 1)| <= 0.172.
+LF_INLINE ff ff_log(const ff& y, const float2* tab) {
+  int e;
+  float m = frexpf(y.hi, &e);                 // y.hi = m 2^e, m in [0.5, 1)
+  if (m < 0.70710678f) e -= 1;
+  const float sc = ldexpf(1.f, -e);
+  const ff mm = ff_make(y.hi * sc, y.lo * sc);
+  const ff z = ff_div(ff_add_f(mm, -1.f), ff_add_f(mm, 1.f));
+  const ff ln2 = ff_make(0.693147182464599609375f, -1.904654323148236e-09f);
+  return ff_add(ff_mul_f(ff_atanh(z, tab), 2.f), ff_mul_f(ln2, (float)e));
+}
+
+// The float-float tier's evaluation of one explicit component: as eval_comp_mixed, plus
+// float-float deflections for the round isothermal and pseudo-Jaffe components and the
+// spherical NFW (psi_ij stays FP32):
+//   round cored isothermal: kbar = b / (S + s), S = sqrt(s^2 + r^2);
+//   round pseudo-Jaffe: kbar = b (a - s) P Q [1 + (a + s)/(R + S)], P = 1/(S + s), Q = 1/(R + a);
+//   NFW: kbar = 4 ks h(x) / x^2, x = r / r_s, with
+//     1 - x^2 >= 0.02:  h = [d ln(2/x) + ln(1 - d/2)] / w, w = sqrt(1 - x^2), d = x^2/(1 + w);
+//     |1 - x^2| < 0.02: h = (1 - ln 2) - (1/2) sum_n w^n / (n (2n + 1)), w = 1 - x^2;
+//     x^2 - 1 >= 0.02:  h = ln(x/2) + atan(w) / w, w = sqrt(x^2 - 1).
+LF_NOINLINE void eval_comp_ext(const CompT<float>& c, float ph_x, float pl_x, float ph_y, float pl_y,
+                               const float2* tab, ff& ax, ff& ay, Out5<float>& o) {
+  const bool rnd = (c.kind == K_SIE || c.kind == K_DPIE) && c.round;
+  if (!rnd && c.kind != K_NFW) {
+    eval_comp_mixed(c, ph_x, pl_x, ph_y, pl_y, tab, ax, ay, o);
+    return;
+  }
+  const ff dx = offset_ff(ph_x, pl_x, c.xh, c.xl), dy = offset_ff(ph_y, pl_y, c.yh, c.yl);
+  eval_comp(c, dx.hi, dy.hi, o);              // psi_ij (and an FP32 alpha, replaced below)
+  const ff r2 = ff_add(ff_sqr(dx), ff_sqr(dy));
+  const ff b = ff_make(c.b, c.lb);
+  ff kb;
+  if (!(r2.hi > 0.f)) {
+    ax = ff_zero();
+    ay = ff_zero();
+    return;
+  }
+  if (rnd) {
+    const ff s = ff_make(c.s1, c.ls1);
+    const ff S = ff_sqrt(ff_add(ff_make(c.s1sq, c.ls1sq), r2));
+    const ff P = ff_div(ff_make(1.f, 0.f), ff_add(S, s));
+    if (c.kind == K_SIE) {
+      kb = ff_mul(b, P);
+    } else {
+      const ff a = ff_make(c.s2, c.ls2);
+      const ff R = ff_sqrt(ff_add(ff_make(c.s2sq, c.ls2sq), r2));
+      const ff Q = ff_div(ff_make(1.f, 0.f), ff_add(R, a));
+      const ff w = ff_add_f(ff_div(ff_add(a, s), ff_add(R, S)), 1.f);
+      kb = ff_mul(ff_mul(b, ff_sub(a, s)), ff_mul(ff_mul(P, Q), w));
+    }
+  } else {
+    const ff rs2 = ff_make(c.s1sq, c.ls1sq);
+    const ff x2 = ff_div(r2, rs2);
+    const ff x = ff_sqrt(x2);
+    const ff w2 = ff_sub(ff_make(1.f, 0.f), x2);
+    ff h;
+    if (w2.hi >= 0.02f) {
+      const ff w = ff_sqrt(w2);
+      const ff d = ff_div(x2, ff_add_f(w, 1.f));
+      const ff l2x = ff_log(ff_div(ff_make(2.f, 0.f), x), tab);
+      const ff l1 = ff_log(ff_add_f(ff_mul_f(d, -0.5f), 1.f), tab);
+      h = ff_div(ff_add(ff_mul(d, l2x), l1), w);
+    } else if (w2.hi > -0.02f) {
+      // h = (1 - ln 2) - (1/2) sum_n w^n / (n (2n + 1)): the n = 1, 2 terms in float-float, the
+      // rest (below |w|^3 / 21 <= 4e-7) in FP32
+      float t = 1.f / 136.f;
+      for (int n = 7; n >= 3; --n) t = fmaf(t, w2.hi, 1.f / (float)(n * (2 * n + 1)));
+      const ff third = ff_make(3.333333433e-01f, -9.934107759e-09f);
+      const ff tenth = ff_make(1.000000015e-01f, -1.490116142e-09f);
+      const ff sum = ff_add(ff_add(ff_mul(w2, third), ff_mul(ff_sqr(w2), tenth)),
+                            ff_make(t * w2.hi * w2.hi * w2.hi, 0.f));
+      h = ff_sub(ff_make(3.068528175e-01f, 1.904654212e-09f), ff_mul_f(sum, 0.5f));
+    } else {
+      const ff w = ff_sqrt(ff_neg(w2));
+      h = ff_add(ff_log(ff_mul_f(x, 0.5f), tab), ff_div(ff_atan(w, tab), w));
+    }
+    kb = ff_div(ff_mul_f(ff_mul(b, h), 4.f), x2);
+  }
+  ax = ff_mul(kb, dx);
+  ay = ff_mul(kb, dy);
 }
 
 // Member record of the float-float tier: float-float centre and constants of the

@@ -123,3 +123,6 @@ LF_INLINE void member_d3(T dx, T dy, T b, T s, T a, T (&d3)[4]) {
 
 
 }  // namespace lf
+
+template <class T, int N> struct scalar_of<lf::Dual<T, N>> { typedef T type; };
+

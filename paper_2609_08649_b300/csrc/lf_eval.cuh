@@ -185,7 +185,7 @@ __device__ __forceinline__ void accumulate_ext(const CompT<float>* dc, int nc, c
     for (int k = 0; k < PPT; ++k) {
       ff ax, ay;
       Out5<float> o;
-      eval_comp_mixed(C, pxh[k], pxl[k], pyh[k], pyl[k], tab, ax, ay, o);
+      eval_comp_ext(C, pxh[k], pxl[k], pyh[k], pyl[k], tab, ax, ay, o);
       acc[0][k] = ff_add(acc[0][k], ax);
       acc[1][k] = ff_add(acc[1][k], ay);
       ff_acc(acc[2][k], o.pxx); ff_acc(acc[3][k], o.pyy); ff_acc(acc[4][k], o.pxy);

@@ -90,10 +90,8 @@ def test_three_plane_image_plane_chi2_matches_oracle(lib, prec):
     """Three lens planes: true images of the three-plane model (made by the oracle, 11
     families at z = 4) observed with 1 mas noise, parameters jittered by 1 % of the sampler's
     widths; Newton with the recursion's beta and non-symmetric A against the oracle's.  The
-    later planes hold spherical NFW and round dPIE components, whose deflections both mixed
-    tiers evaluate in FP32 (only elliptical isothermal halos, elliptical NFW, shear and
-    multipole get float-float), so the float-float tier is held to the mixed bound here
-    (measured 8.8e-4)."""
+    later planes hold spherical NFW and round dPIE components: FP32 deflections in the mixed
+    tier, float-float in the float-float tier."""
     api, PM = lib
     from tests.helpers import three_plane_images
     wl, cat = three_plane_images()
@@ -110,7 +108,6 @@ def test_three_plane_image_plane_chi2_matches_oracle(lib, prec):
     rel = np.abs(c.cpu().numpy() - cref) / cref
     print(f"three-plane image-plane chi^2 ({prec}): relative error {rel.max():.3e}; rms {rref}")
     assert np.all(np.isfinite(cref)) and np.all(rref < 0.01)
-    tol = TOL["mixed"] if prec == "ff" else TOL[prec]
-    assert np.all(rel <= tol)
-    assert np.allclose(r.cpu().numpy(), rref, rtol=tol, atol=0)
+    assert np.all(rel <= TOL[prec])
+    assert np.allclose(r.cpu().numpy(), rref, rtol=TOL[prec], atol=0)
     api.device_error()
