@@ -431,6 +431,23 @@ def secondary(torch, api, PM, W, L, C, step, ms_mixed, evals):
         plan.close()
     res["mixed_speedup_chi2"] = res["fp64"]["chi2_ms"] / res["mixed"]["chi2_ms"]
     out["chi2_enfw_4096x200"] = res
+    # three lens planes: chi^2, chi^2 + gradient (the recursion's adjoint) and the image-plane
+    # chi^2 (Newton with the recursion's beta and A), 1024 samples, C2's 200 image positions
+    # traced to z = 4
+    wl3 = W.multiplane_c3(n_grid=8)
+    cat3 = W.Catalogue(cat.theta_obs, cat.theta_true, cat.fam_off, np.full(len(cat.fam_zs), 4.0))
+    th3 = torch.tensor(W.sample_thetas(wl3, wl3.seed), device="cuda")
+    res = {}
+    for prec in ("mixed", "ff", "fp64"):
+        plan = api.Plan([PM.cluster_input(wl3, cat3)], th3.shape[0], prec, flags=api.FLAG_GRAPH | api.FLAG_AUTOTUNE)
+        reps = 3 if prec != "fp64" else 1
+        tc = _time(torch, lambda: plan.chi2(th3), reps=reps)
+        tg = _time(torch, lambda: plan.chi2_grad(th3), reps=reps)
+        ti = _time(torch, lambda: plan.chi2_img(th3, iters=8), reps=reps)
+        res[prec] = {"chi2_ms": tc, "grad_ms": tg, "chi2_img_ms": ti,
+                     "grad_samples_per_s": th3.shape[0] / (tg * 1e-3)}
+        plan.close()
+    out["multiplane_3planes_1024x200"] = res
     # image-plane chi^2 (Newton model images) and the on-device sampler on the same cluster
     res = {}
     wl2 = W.cluster_c2()

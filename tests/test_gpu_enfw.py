@@ -172,3 +172,25 @@ def test_enfw_flux_and_delay_terms(lib, hera, prec):
     print(f"eNFW flux+delay ({prec}): relative error {rel.max():.2e}")
     assert np.all(rel <= {"fp64": 1e-9, "mixed": 1e-3}[prec])
     api.device_error()
+
+
+def test_invalid_enfw_components_are_refused(lib):
+    """A scale radius <= 0 or an ellipticity >= 1: a plan refuses the cluster before any launch;
+    a map skips the component and raises the device error word."""
+    api, PM = lib
+    from paper_2609_08649_b300 import _lib as L
+    good = W.PhysComp(W.ENFW, 0.0, 0.0, kappa_s=0.3, theta_s=20.0, eps=0.2, pa_deg=10.0)
+    grid = W.Grid(-10.0, -10.0, 1.0, 1.0, 21, 21)
+    ref = api.jacobian_grid(PM.device_plane(W.PhysPlane(0.5, [good]), W.Cosmo()), grid, 0.5, "mixed")
+    api.device_error()
+    for bad in (W.replace(good, theta_s=0.0), W.replace(good, theta_s=-3.0), W.replace(good, eps=1.0)):
+        dp = PM.device_plane(W.PhysPlane(0.5, [good, bad]), W.Cosmo())
+        o = api.jacobian_grid(dp, grid, 0.5, "mixed")
+        with pytest.raises(L.LFError):
+            api.device_error()
+        assert torch.equal(o["ax"], ref["ax"]) and torch.equal(o["mu"], ref["mu"])
+        wl = W.Workload("bad", W.Cosmo(), [W.PhysPlane(0.5, [good, bad])],
+                        params=[W.ParamSpec(0, W.F_B, W.XF_IDENT, 0.3, 0.01, True)], n_samples=2)
+        cat = W.load_catalogue("galaxy_sie_shear")
+        with pytest.raises(L.LFError):
+            api.Plan([PM.cluster_input(wl, cat)], 2, "mixed")
