@@ -60,6 +60,28 @@ def test_cluster_image_plane_chi2_matches_oracle(lib, prec):
     api.device_error()
 
 
+def test_full_size_image_plane_sampled(lib):
+    """The benchmark's image-plane chi^2: 4096 samples x 200 images in one launch (mixed tier,
+    8 Newton steps), in the regime of the parity test above; 8 seeded samples against the
+    oracle one by one."""
+    api, PM = lib
+    wl = W.cluster_c2()
+    wl.params = [W.replace(p, jitter=p.jitter * 0.01) for p in wl.params]
+    wl.sigma_pos = 0.001
+    base = W.load_catalogue("cluster_200")
+    tobs = base.theta_true + W.position_noise(31, len(base.theta_true), 0.001)
+    cat = W.Catalogue(tobs, base.theta_true, base.fam_off, base.fam_zs)
+    th = W.sample_thetas(wl, wl.seed)
+    plan = api.Plan([PM.cluster_input(wl, cat)], th.shape[0], "mixed", flags=api.FLAG_GRAPH)
+    c, r = plan.chi2_img(torch.tensor(th, device="cuda"), iters=8)
+    c, r = c.cpu().numpy(), r.cpu().numpy()
+    idx = np.concatenate([[0, th.shape[0] - 1], np.random.default_rng(37).integers(0, th.shape[0], 6)])
+    cref, rref = oracle(wl, cat, th[idx])
+    assert np.all(np.abs(c[idx] - cref) <= TOL["mixed"] * cref)
+    assert np.allclose(r[idx], rref, rtol=TOL["mixed"], atol=0)
+    api.device_error()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "ff"])
 def test_noise_free_images_give_zero(lib, prec):
     api, PM = lib

@@ -121,3 +121,25 @@ def test_three_plane_trace_with_elliptical_nfw_halos(lib, prec):
         sa = _abs_scale(wl, X.ravel(), Y.ravel())
         assert np.all(np.abs(beta - b0).max(1) <= 1e-6 + 16 * U32 * sa)
         assert np.abs(A - A0).max() < 1e-4
+
+
+def test_full_size_trace_sampled(lib):
+    """The benchmark's trace: the 2048^2 grid at 0.08" through the three planes in one launch
+    (mixed tier); 400 seeded pixels against the oracle's recursion one by one."""
+    api, PM = lib
+    wl = W.multiplane_c3()
+    planes = PM.device_planes(wl)
+    r = PM.multiplane_ratios(wl.cosmo, [p.z for p in wl.planes], wl.z_s)
+    beta, A = api.trace_multiplane(planes, r, grid=wl.grid, precision="mixed")
+    api.device_error()
+    n = wl.grid.nx * wl.grid.ny
+    idx = np.random.default_rng(23).integers(0, n, 400)
+    idx[:2] = [0, n - 1]
+    X = wl.grid.x0 + wl.grid.dx * (idx % wl.grid.nx)
+    Y = wl.grid.y0 + wl.grid.dy * (idx // wl.grid.nx)
+    b0, A0 = _oracle_trace(wl, X, Y)
+    bt = torch.as_tensor(idx, device=beta.device)
+    b, Ag = beta[bt].cpu().numpy(), A[bt].cpu().numpy()
+    sa = _abs_scale(wl, X, Y)
+    assert np.all(np.abs(b - b0).max(1) <= 1e-6 + 16 * U32 * sa)
+    assert np.abs(Ag - A0).max() < 1e-4
