@@ -517,6 +517,20 @@ def secondary(torch, api, PM, W, L, C, step, ms_mixed, evals):
                                   workspace=ws)
         res[prec] = {"ms": t, "sources_per_s": 60 / (t * 1e-3), "images": int(nimg.clamp(min=0).sum())}
     out["find_images_60src_1601sq"] = res
+    # the same solver behind three planes: 60 sources at z = 4, the 1601^2 vertex grid traced
+    # through the recursion, Newton polish on the FP64 recursion
+    wl3f = W.multiplane_c3(n_grid=8)
+    planes3 = PM.device_planes(wl3f)
+    rt = PM.multiplane_ratios(wl3f.cosmo, [p.z for p in wl3f.planes], 4.0)
+    wsm = torch.empty(api.find_images_multiplane_workspace(fgrid, 60, 32), dtype=torch.uint8, device="cuda")
+    res = {}
+    for prec in ("mixed", "fp64"):
+        t = _time(torch, lambda: api.find_images_multiplane(planes3, rt, fgrid, srcs, max_img=32, polish_iters=20,
+                                                            precision=prec, workspace=wsm), reps=3)
+        _, nimg = api.find_images_multiplane(planes3, rt, fgrid, srcs, max_img=32, polish_iters=20,
+                                             precision=prec, workspace=wsm)
+        res[prec] = {"ms": t, "sources_per_s": 60 / (t * 1e-3), "images": int(nimg.clamp(min=0).sum())}
+    out["find_images_3planes_60src_1601sq"] = res
     # 3-plane trace of a 2048^2 grid
     wl3 = W.multiplane_c3()
     planes = PM.device_planes(wl3)

@@ -87,6 +87,7 @@ def _load():
         "lf_nfw_params": [f64, f64, f64, f64, f64, vp, vp],
         "lf_device_error": [vp],
         "lf_find_images": [vp, vp, i32, vp, vp, i32, i32, i32, vp, C.c_size_t, vp, vp, vp],
+        "lf_find_images_multiplane": [vp, i32, vp, vp, i32, vp, i32, i32, i32, vp, C.c_size_t, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -100,6 +101,8 @@ def _load():
         fn.restype = C.c_double
     lib.lf_find_images_workspace.argtypes = [i32, i32, i32, i32]
     lib.lf_find_images_workspace.restype = C.c_size_t
+    lib.lf_find_images_multiplane_workspace.argtypes = [i32, i32, i32, i32]
+    lib.lf_find_images_multiplane_workspace.restype = C.c_size_t
     lib.lf_last_error.restype = C.c_char_p
     lib.lf_version.restype = C.c_char_p
     return lib
@@ -110,7 +113,8 @@ lib = _load()
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTS = ["lf_deflect_grid", "lf_jacobian_grid", "lf_jacobian_points", "lf_trace_multiplane",
            "lf_plan_create", "lf_chi2_batch", "lf_chi2_grad_batch", "lf_plan_destroy",
-           "lf_chi2_img_batch", "lf_aies_run", "lf_mh_run", "lf_nm_run", "lf_find_images", "lf_find_images_workspace",
+           "lf_chi2_img_batch", "lf_aies_run", "lf_mh_run", "lf_nm_run", "lf_find_images", "lf_find_images_workspace", "lf_find_images_multiplane",
+           "lf_find_images_multiplane_workspace",
            "lf_chi2_batch_static",
            "lf_plan_info", "lf_angular_distance", "lf_adis", "lf_arcsec_per_kpc",
            "lf_b_from_vdisp", "lf_td_scale", "lf_nfw_params", "lf_device_error", "lf_probe_alu", "lf_last_error", "lf_version"]

@@ -121,6 +121,33 @@ def find_images_workspace(grid, n_src, max_img=8):
     return int(L.lib.lf_find_images_workspace(grid.nx, grid.ny, n_src, max_img))
 
 
+def find_images_multiplane_workspace(grid, n_src, max_img=8):
+    return int(L.lib.lf_find_images_multiplane_workspace(grid.nx, grid.ny, n_src, max_img))
+
+
+def find_images_multiplane(planes: Sequence[DevicePlane], ratios: np.ndarray, grid, beta: torch.Tensor,
+                           max_img=8, polish_iters=0, precision="fp64",
+                           workspace: Optional[torch.Tensor] = None):
+    """Images of n_src sources (beta (n_src, 2)) behind several planes, all at the source
+    redshift of the ratios table ((n+1) x n, as for trace_multiplane).  Returns
+    (img (n_src, max_img, 2), n_img (n_src,) int32) as find_images does."""
+    beta = _dev64(beta, "beta")
+    n = beta.shape[0]
+    need = find_images_multiplane_workspace(grid, n, max_img)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+    img = torch.full((n, max_img, 2), float("nan"), dtype=torch.float64, device="cuda")
+    n_img = torch.zeros(n, dtype=torch.int32, device="cuda")
+    arr = (L.lf_plane * len(planes))(*[p.c_struct() for p in planes])
+    rat = np.ascontiguousarray(ratios, dtype=np.float64)
+    gs = grid_struct(grid)
+    L.check(L.lib.lf_find_images_multiplane(arr, len(planes), rat.ctypes.data_as(C.c_void_p), C.byref(gs),
+                                            _prec(precision), _ptr(beta), n, int(max_img), int(polish_iters),
+                                            _ptr(workspace), workspace.numel(), _ptr(img), _ptr(n_img),
+                                            _stream()))
+    return img, n_img
+
+
 def probe_alu():
     """Measured (FP32 FMA, MUFU rsqrt, FP64 FMA) operations per second of the current GPU."""
     r = [C.c_double() for _ in range(3)]

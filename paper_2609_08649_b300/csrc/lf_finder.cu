@@ -404,3 +404,135 @@ extern "C" lf_status lf_find_images(const lf_plane* plane, const lf_grid* grid, 
   LF_CUDA(cudaGetLastError());
   return LF_OK;
 }
+
+// ------------------------------------------------------------------ several planes -----
+// Sources at one redshift behind several planes: beta(theta) is the recursion's (Sec. 2.2),
+// so f = beta_s - beta(theta) = beta_s - theta + alpha_eff(theta) with the effective
+// deflection alpha_eff = theta - beta(theta) on the vertices (the trace kernel, in the chosen
+// tier) and a = 1; steps 2-4 and 6 are those above.  The polish alternates the FP64 recursion
+// at the candidates with Newton steps theta <- theta - A^-1 (beta(theta) - beta_s) on its
+// non-symmetric A.
+namespace lf {
+
+struct FinderMPWS {
+  double* bvert;   // beta on the vertices, nx * ny * 2
+  double* ones;    // a = 1 per source
+  double* pb;      // per candidate slot: beta (2) and A (4) of the polish
+  double* pA;
+};
+
+static size_t finder_mp_layout(long long nx, long long ny, long long n_src, int max_img, char* base,
+                               FinderWS* w, FinderMPWS* m) {
+  size_t o = finder_layout(nx, ny, n_src, max_img, base, w);
+  const long long slots = n_src * finder_max_cand(max_img);
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = (o + bytes + 255) & ~(size_t)255;
+    return base ? base + at : nullptr;
+  };
+  char* p;
+  p = take((size_t)(nx * ny) * 16); if (m) m->bvert = (double*)p;
+  p = take((size_t)n_src * 8); if (m) m->ones = (double*)p;
+  p = take((size_t)slots * 16); if (m) m->pb = (double*)p;
+  p = take((size_t)slots * 32); if (m) m->pA = (double*)p;
+  return o;
+}
+
+__global__ void k_mp_alpha(const double* __restrict__ bvert, long long nv, int nx, double x0, double y0,
+                           double dx, double dy, double* ax, double* ay, double* ones, int n_src) {
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+  for (long long v = t0; v < nv; v += nt) {
+    const long long iy = v / nx, ix = v - iy * nx;
+    ax[v] = (x0 + dx * (double)ix) - bvert[2 * v];
+    ay[v] = (y0 + dy * (double)iy) - bvert[2 * v + 1];
+  }
+  for (long long i = t0; i < n_src; i += nt) ones[i] = 1.0;
+}
+
+// A step longer than max_step (the grid step) leaves the candidate where it is: the raw
+// candidate lies within O(h^2) of its root, so such a step means A is near-singular there (a
+// critical curve) and the iteration has left the root's basin.
+__global__ void k_mp_newton(int n_src, int max_cand, const int* __restrict__ kept,
+                            const double* __restrict__ beta, const double* __restrict__ pb,
+                            const double* __restrict__ pA, double max_step, double* cxy) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= (long long)n_src * max_cand) return;
+  const int src = (int)(q / max_cand), k = (int)(q - (long long)src * max_cand);
+  if (k >= kept[src]) return;
+  const double rx = pb[2 * q] - beta[2 * src], ry = pb[2 * q + 1] - beta[2 * src + 1];
+  const double* A = pA + 4 * q;
+  const double id = 1.0 / (A[0] * A[3] - A[1] * A[2]);
+  const double sx = (A[3] * rx - A[1] * ry) * id, sy = (A[0] * ry - A[2] * rx) * id;
+  if (!(sx * sx + sy * sy <= max_step * max_step)) return;
+  cxy[2 * q] -= sx;
+  cxy[2 * q + 1] -= sy;
+}
+
+}  // namespace lf
+
+extern "C" size_t lf_find_images_multiplane_workspace(int32_t nx, int32_t ny, int32_t n_src, int32_t max_img) {
+  if (nx < 2 || ny < 2 || n_src < 0 || max_img < 1) return 0;
+  return finder_mp_layout(nx, ny, n_src, max_img, nullptr, nullptr, nullptr);
+}
+
+extern "C" lf_status lf_find_images_multiplane(const lf_plane* planes, int32_t n_planes, const double* ratios,
+                                               const lf_grid* grid, int32_t precision, const double* beta,
+                                               int32_t n_src, int32_t max_img, int32_t polish_iters,
+                                               void* workspace, size_t workspace_bytes, double* img,
+                                               int32_t* n_img, void* stream) {
+  if (!planes || n_planes < 1 || n_planes > LF_MAX_PLANES) return fail(LF_EINVAL, "need 1 <= n_planes <= 8 planes");
+  if (!ratios) return fail(LF_EINVAL, "ratios is NULL");
+  for (int j = 0; j < n_planes; ++j) LF_TRY(check_plane(&planes[j]));
+  if (!grid) return fail(LF_EINVAL, "grid is NULL");
+  if (grid->nx < 2 || grid->ny < 2) return fail(LF_EINVAL, "the vertex grid needs nx, ny >= 2");
+  if (!(std::isfinite(grid->x0) && std::isfinite(grid->y0) && grid->dx > 0 && grid->dy > 0 &&
+        std::isfinite(grid->dx) && std::isfinite(grid->dy)))
+    return fail(LF_EINVAL, "grid origin must be finite and its steps positive");
+  if (precision < LF_FP64 || precision > LF_FF) return fail(LF_EINVAL, "unknown precision");
+  if (n_src < 0) return fail(LF_EINVAL, "n_src must be >= 0");
+  if (max_img < 1) return fail(LF_EINVAL, "max_img must be >= 1");
+  if (polish_iters < 0) return fail(LF_EINVAL, "polish_iters must be >= 0");
+  if (n_src == 0) return LF_OK;
+  if (!beta || !img || !n_img) return fail(LF_EINVAL, "beta, img and n_img are required");
+  const size_t need = finder_mp_layout(grid->nx, grid->ny, n_src, max_img, nullptr, nullptr, nullptr);
+  if (!workspace || workspace_bytes < need)
+    return fail(LF_EINVAL, "workspace of %zu bytes needed (lf_find_images_multiplane_workspace)", need);
+  if ((uintptr_t)workspace & 255u) return fail(LF_EINVAL, "workspace must be 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  FinderWS W;
+  FinderMPWS M;
+  finder_mp_layout(grid->nx, grid->ny, n_src, max_img, (char*)workspace, &W, &M);
+  const int max_cand = finder_max_cand(max_img);
+  int dev = 0, nsm = 0;
+  LF_CUDA(cudaGetDevice(&dev));
+  LF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  // 1. alpha_eff = theta - beta(theta) on the vertices
+  const long long nv = (long long)grid->nx * grid->ny;
+  LF_TRY(lf_trace_multiplane(planes, n_planes, ratios, nullptr, 0, grid, precision, M.bvert, nullptr, stream));
+  const unsigned g1 = (unsigned)std::min<long long>((nv + 255) / 256, (long long)nsm * 16);
+  k_mp_alpha<<<g1, 256, 0, s>>>(M.bvert, nv, grid->nx, grid->x0, grid->y0, grid->dx, grid->dy, W.ax, W.ay,
+                                M.ones, n_src);
+  // 2-4. cell ranges, candidates, order and merge (a = 1)
+  const long long ncell = (long long)(grid->nx - 1) * (grid->ny - 1);
+  const unsigned g2 = (unsigned)std::min<long long>((ncell + 255) / 256, (long long)nsm * 16);
+  k_cell_ranges<<<g2, 256, 0, s>>>(W.ax, W.ay, grid->nx, ncell, W.rng);
+  LF_CUDA(cudaMemsetAsync(W.ccnt, 0, (size_t)n_src * 4, s));
+  const unsigned g3 = (unsigned)std::min<long long>((ncell + 255) / 256, (long long)nsm * 8);
+  k_find_cells<<<g3, 256, 0, s>>>(W.ax, W.ay, W.rng, grid->nx, ncell, grid->x0, grid->y0, grid->dx,
+                                   grid->dy, beta, M.ones, n_src, max_cand, W.cxy, W.ckey, W.ccnt);
+  const unsigned gs = (unsigned)((n_src + 127) / 128);
+  k_sort_merge<<<gs, 128, 0, s>>>(n_src, max_cand, 1e-6 * grid->dx, W.cxy, W.ckey, W.ccnt, W.kept);
+  // 5. polish: FP64 recursion at every candidate slot, Newton step on the kept ones
+  const long long slots = (long long)n_src * max_cand;
+  for (int it = 0; it < polish_iters; ++it) {
+    LF_TRY(lf_trace_multiplane(planes, n_planes, ratios, W.cxy, (int32_t)slots, nullptr, LF_FP64, M.pb, M.pA,
+                               stream));
+    k_mp_newton<<<(unsigned)((slots + 255) / 256), 256, 0, s>>>(n_src, max_cand, W.kept, beta, M.pb, M.pA,
+                                                                std::max(grid->dx, grid->dy), W.cxy);
+  }
+  // 6. output
+  k_find_finish<<<gs, 128, 0, s>>>(n_src, max_cand, max_img, polish_iters > 0, 1e-7, W.cxy, W.kept,
+                                    img, n_img);
+  LF_CUDA(cudaGetLastError());
+  return LF_OK;
+}

@@ -17,6 +17,7 @@ namespace lf {
 
 // Largest dynamic shared memory a block may ask for on sm_103a (227 KiB).
 constexpr uint32_t LF_SMEM_MAX = 227u * 1024u;
+constexpr int LF_MAX_PLANES = 8;   // lens planes of one model
 
 // Members summed in FP32 before each fold into the float-float accumulators.
 extern int g_member_chunk;

@@ -11,8 +11,6 @@
 
 namespace lf {
 
-constexpr int LF_MAX_PLANES = 8;
-
 struct MultiPlaneArgs {
   int np;
   const lf_comp* comp[LF_MAX_PLANES];

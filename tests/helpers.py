@@ -122,38 +122,56 @@ def families_off_critical(wl, cat, theta, thr):
 
 
 @functools.lru_cache(maxsize=2)
-def three_plane_images(n_src=12, seed=41, z_src=4.0, sigma=0.001):
-    """A catalogue of true images of the three-plane model (multiplane_c3) for sources at
-    z_src, made with oracle code only: the effective deflection theta - beta(theta) of the
-    recursion on a 401^2 vertex grid over 160", marching squares (oracle images.find_images
-    with a = 1), then Newton steps of the multi-plane lens equation toward each image's own
-    source.  Families keep the sources with 2-5 images; the observed positions carry seeded
-    Gaussian noise of sigma.  Returns (workload, Catalogue)."""
+def three_plane_field(z_src=4.0, x0=-80.0, h=0.4, n=401):
+    """The three-plane model (multiplane_c3) and, on an n^2 vertex grid from (x0, x0) with step
+    h, the effective deflection alpha_eff = theta - beta(theta) of its recursion to z_src
+    (oracle code only).  Returns (wl, planes, r, rs, ax, ay)."""
     from oracle import cosmology as cz
-    from oracle import images as OI
     wl = W.multiplane_c3(n_grid=8)
     planes = OM.build_planes(wl)
     zs = [p.z for p in wl.planes]
     r, _ = cz.multiplane_ratios(zs, zs[-1] + 1.0, wl.cosmo.H0, wl.cosmo.Om)
     rs1 = cz.multiplane_ratios(zs, z_src, wl.cosmo.H0, wl.cosmo.Om)[1]
-    x0, h, n = -80.0, 0.4, 401
     xs = x0 + h * np.arange(n)
     X, Y = np.meshgrid(xs, xs)
     rs = torch.tensor([[float(v)] * (n * n) for v in rs1], dtype=torch.float64)
     beta, _ = OL.multi_plane_beta_A(planes, r, rs, torch.tensor(X.ravel())[None], torch.tensor(Y.ravel())[None])
     ax = (X.ravel() - beta[0, :, 0].numpy()).reshape(n, n)
     ay = (Y.ravel() - beta[0, :, 1].numpy()).reshape(n, n)
+    return wl, planes, r, rs1, ax, ay
+
+
+def three_plane_polish(planes, r, rs1, src, th, iters=20, max_step=None):
+    """Newton steps of the multi-plane lens equation beta(theta) = src from positions th (k, 2);
+    with max_step, a longer step is not taken (the position stays)."""
+    th = torch.tensor(np.asarray(th, dtype=np.float64))
+    rsk = torch.tensor([[float(v)] * len(th) for v in rs1], dtype=torch.float64)
+    for _ in range(iters):
+        b, A = OL.multi_plane_beta_A(planes, r, rsk, th[None, :, 0], th[None, :, 1])
+        step = torch.linalg.solve(A[0], (b[0] - torch.tensor(src))[..., None])[..., 0]
+        if max_step is not None:
+            ok = (step * step).sum(-1) <= max_step * max_step
+            step = torch.where(ok[:, None], step, torch.zeros_like(step))
+        th = th - step
+    return th.numpy()
+
+
+@functools.lru_cache(maxsize=2)
+def three_plane_images(n_src=12, seed=41, z_src=4.0, sigma=0.001):
+    """A catalogue of true images of the three-plane model (multiplane_c3) for sources at
+    z_src, made with oracle code only: marching squares on the effective deflection of
+    three_plane_field (oracle images.find_images with a = 1), then Newton steps of the
+    multi-plane lens equation toward each image's own source.  Families keep the sources
+    with 2-5 images; the observed positions carry seeded Gaussian noise of sigma.  Returns
+    (workload, Catalogue)."""
+    from oracle import images as OI
+    wl, planes, r, rs1, ax, ay = three_plane_field(z_src)
     fams = []
     for src in W.source_candidates(seed, n_src, 10.0, 2.0, -2.0):
-        imgs = OI.find_images(None, 1.0, src, x0, x0, h, n, newton=False, alpha_grid=(ax, ay))
+        imgs = OI.find_images(None, 1.0, src, -80.0, -80.0, 0.4, 401, newton=False, alpha_grid=(ax, ay))
         if len(imgs) < 2:
             continue
-        th = torch.tensor(np.asarray(imgs[:5]))
-        rsk = torch.tensor([[float(v)] * len(th) for v in rs1], dtype=torch.float64)
-        for _ in range(20):
-            b, A = OL.multi_plane_beta_A(planes, r, rsk, th[None, :, 0], th[None, :, 1])
-            th = th - torch.linalg.solve(A[0], (b[0] - torch.tensor(src))[..., None])[..., 0]
-        fams.append(th.numpy())
+        fams.append(three_plane_polish(planes, r, rs1, src, imgs[:5]))
     true = np.concatenate(fams)
     off = np.concatenate([[0], np.cumsum([len(f) for f in fams])]).astype(np.int32)
     obs = true + W.position_noise(seed + 1, len(true), sigma)
