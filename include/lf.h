@@ -192,14 +192,16 @@ lf_status lf_find_images(const lf_plane* plane, const lf_grid* grid, int32_t pre
  * f = beta_s - theta + alpha_eff(theta), alpha_eff = theta - beta(theta) on the vertices
  * (traced in the chosen tier), and the zero contours, candidates, ordering and merging are
  * those of lf_find_images with a = 1.  The polish (polish_iters > 0) takes polish_iters
- * Newton steps theta <- theta - A^-1 (beta(theta) - beta_s) with the FP64 recursion's
+ * Newton steps theta <- theta - A^-1 (beta(theta) - beta_s) on the recursion (FP64 for
+ * LF_FP64, else float-float: float-float deflections, about 1e-12 relative) with its
  * (non-symmetric) A; a step longer than the grid step is not taken (an image next to a
- * critical curve keeps its unpolished position).
+ * critical curve keeps its unpolished position).  The polish reads the number of kept
+ * candidates back to the host: with polish_iters > 0 the call synchronises the stream once.
  *   beta, img, n_img  as for lf_find_images (no a_src)
  *   workspace  device, 256-byte aligned, at least lf_find_images_multiplane_workspace(nx, ny,
  *           n_src, max_img) bytes (the single-plane workspace plus the traced vertices and the
  *           polish state); caller-owned
- * Stream-ordered; LF_EINVAL for invalid host arguments (nothing launched). */
+ * LF_EINVAL for invalid host arguments (nothing launched). */
 size_t lf_find_images_multiplane_workspace(int32_t nx, int32_t ny, int32_t n_src, int32_t max_img);
 lf_status lf_find_images_multiplane(const lf_plane* planes, int32_t n_planes, const double* ratios,
                                     const lf_grid* grid, int32_t precision, const double* beta,

@@ -409,16 +409,24 @@ extern "C" lf_status lf_find_images(const lf_plane* plane, const lf_grid* grid, 
 // Sources at one redshift behind several planes: beta(theta) is the recursion's (Sec. 2.2),
 // so f = beta_s - beta(theta) = beta_s - theta + alpha_eff(theta) with the effective
 // deflection alpha_eff = theta - beta(theta) on the vertices (the trace kernel, in the chosen
-// tier) and a = 1; steps 2-4 and 6 are those above.  The polish alternates the FP64 recursion
-// at the candidates with Newton steps theta <- theta - A^-1 (beta(theta) - beta_s) on its
-// non-symmetric A.
+// tier) and a = 1; steps 2-4 and 6 are those above.  The polish alternates the recursion at
+// the candidates (FP64 for the FP64 tier, else float-float: float-float deflections, about
+// 1e-12 relative), traced in 32-thread blocks so that a few hundred rays spread over many
+// SMs, with Newton steps theta <- theta - A^-1 (beta(theta) - beta_s) on its non-symmetric A.
 namespace lf {
+
+lf_status trace_rays(const lf_plane* planes, int32_t n_planes, const double* ratios, const double* theta,
+                     int32_t n, const lf_grid* grid, int32_t precision, double* beta, double* A,
+                     void* stream, int block);   // lf_trace.cu
 
 struct FinderMPWS {
   double* bvert;   // beta on the vertices, nx * ny * 2
   double* ones;    // a = 1 per source
-  double* pb;      // per candidate slot: beta (2) and A (4) of the polish
+  double* pb;      // per polished candidate: beta (2) and A (4) of the recursion
   double* pA;
+  double* pos;     // the kept candidates, compacted (2 each)
+  int* map;        // their slot (source * max_cand + k)
+  int* count;      // how many
 };
 
 static size_t finder_mp_layout(long long nx, long long ny, long long n_src, int max_img, char* base,
@@ -435,6 +443,9 @@ static size_t finder_mp_layout(long long nx, long long ny, long long n_src, int 
   p = take((size_t)n_src * 8); if (m) m->ones = (double*)p;
   p = take((size_t)slots * 16); if (m) m->pb = (double*)p;
   p = take((size_t)slots * 32); if (m) m->pA = (double*)p;
+  p = take((size_t)slots * 16); if (m) m->pos = (double*)p;
+  p = take((size_t)slots * 4); if (m) m->map = (int*)p;
+  p = take(4); if (m) m->count = (int*)p;
   return o;
 }
 
@@ -449,23 +460,42 @@ __global__ void k_mp_alpha(const double* __restrict__ bvert, long long nv, int n
   for (long long i = t0; i < n_src; i += nt) ones[i] = 1.0;
 }
 
-// A step longer than max_step (the grid step) leaves the candidate where it is: the raw
-// candidate lies within O(h^2) of its root, so such a step means A is near-singular there (a
-// critical curve) and the iteration has left the root's basin.
-__global__ void k_mp_newton(int n_src, int max_cand, const int* __restrict__ kept,
-                            const double* __restrict__ beta, const double* __restrict__ pb,
-                            const double* __restrict__ pA, double max_step, double* cxy) {
+// The kept candidates of every source into one list (order immaterial: each is polished alone).
+__global__ void k_mp_compact(int n_src, int max_cand, const int* __restrict__ kept,
+                             const double* __restrict__ cxy, double* pos, int* map, int* count) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= (long long)n_src * max_cand) return;
   const int src = (int)(q / max_cand), k = (int)(q - (long long)src * max_cand);
   if (k >= kept[src]) return;
-  const double rx = pb[2 * q] - beta[2 * src], ry = pb[2 * q + 1] - beta[2 * src + 1];
-  const double* A = pA + 4 * q;
+  const int i = atomicAdd(count, 1);
+  map[i] = (int)q;
+  pos[2 * i] = cxy[2 * q];
+  pos[2 * i + 1] = cxy[2 * q + 1];
+}
+
+__global__ void k_mp_scatter(int n, const int* __restrict__ map, const double* __restrict__ pos, double* cxy) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cxy[2 * map[i]] = pos[2 * i];
+  cxy[2 * map[i] + 1] = pos[2 * i + 1];
+}
+
+// A step longer than max_step (the grid step) leaves the candidate where it is: the raw
+// candidate lies within O(h^2) of its root, so such a step means A is near-singular there (a
+// critical curve) and the iteration has left the root's basin.
+__global__ void k_mp_newton(int n, int max_cand, const int* __restrict__ map, const double* __restrict__ beta,
+                            const double* __restrict__ pb, const double* __restrict__ pA, double max_step,
+                            double* pos) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int src = map[i] / max_cand;
+  const double rx = pb[2 * i] - beta[2 * src], ry = pb[2 * i + 1] - beta[2 * src + 1];
+  const double* A = pA + 4 * i;
   const double id = 1.0 / (A[0] * A[3] - A[1] * A[2]);
   const double sx = (A[3] * rx - A[1] * ry) * id, sy = (A[0] * ry - A[2] * rx) * id;
   if (!(sx * sx + sy * sy <= max_step * max_step)) return;
-  cxy[2 * q] -= sx;
-  cxy[2 * q + 1] -= sy;
+  pos[2 * i] -= sx;
+  pos[2 * i + 1] -= sy;
 }
 
 }  // namespace lf
@@ -522,13 +552,25 @@ extern "C" lf_status lf_find_images_multiplane(const lf_plane* planes, int32_t n
                                    grid->dy, beta, M.ones, n_src, max_cand, W.cxy, W.ckey, W.ccnt);
   const unsigned gs = (unsigned)((n_src + 127) / 128);
   k_sort_merge<<<gs, 128, 0, s>>>(n_src, max_cand, 1e-6 * grid->dx, W.cxy, W.ckey, W.ccnt, W.kept);
-  // 5. polish: FP64 recursion at every candidate slot, Newton step on the kept ones
-  const long long slots = (long long)n_src * max_cand;
-  for (int it = 0; it < polish_iters; ++it) {
-    LF_TRY(lf_trace_multiplane(planes, n_planes, ratios, W.cxy, (int32_t)slots, nullptr, LF_FP64, M.pb, M.pA,
-                               stream));
-    k_mp_newton<<<(unsigned)((slots + 255) / 256), 256, 0, s>>>(n_src, max_cand, W.kept, beta, M.pb, M.pA,
-                                                                std::max(grid->dx, grid->dy), W.cxy);
+  // 5. polish: the kept candidates compacted (their count read back, one stream synchronisation),
+  //    then the recursion at them and a Newton step, polish_iters times
+  if (polish_iters > 0) {
+    const long long slots = (long long)n_src * max_cand;
+    LF_CUDA(cudaMemsetAsync(M.count, 0, sizeof(int), s));
+    k_mp_compact<<<(unsigned)((slots + 255) / 256), 256, 0, s>>>(n_src, max_cand, W.kept, W.cxy, M.pos, M.map,
+                                                                 M.count);
+    int nk = 0;
+    LF_CUDA(cudaMemcpyAsync(&nk, M.count, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LF_CUDA(cudaStreamSynchronize(s));
+    if (nk > 0) {
+      for (int it = 0; it < polish_iters; ++it) {
+        LF_TRY(trace_rays(planes, n_planes, ratios, M.pos, nk, nullptr, precision == LF_FP64 ? LF_FP64 : LF_FF,
+                          M.pb, M.pA, stream, 32));
+        k_mp_newton<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(nk, max_cand, M.map, beta, M.pb, M.pA,
+                                                                std::max(grid->dx, grid->dy), M.pos);
+      }
+      k_mp_scatter<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(nk, M.map, M.pos, W.cxy);
+    }
   }
   // 6. output
   k_find_finish<<<gs, 128, 0, s>>>(n_src, max_cand, max_img, polish_iters > 0, 1e-7, W.cxy, W.kept,

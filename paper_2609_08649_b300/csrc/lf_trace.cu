@@ -169,10 +169,10 @@ lf_status fill_planes(const lf_plane* planes, int np, MultiPlaneArgs& A, uint32_
 
 using namespace lf;
 
-extern "C" lf_status lf_trace_multiplane(const lf_plane* planes, int32_t n_planes,
-                                         const double* ratios, const double* theta, int32_t n,
-                                         const lf_grid* grid, int32_t precision, double* beta,
-                                         double* A, void* stream) {
+// The trace with a chosen block size (small blocks spread a few rays over many SMs).
+lf_status lf::trace_rays(const lf_plane* planes, int32_t n_planes, const double* ratios, const double* theta,
+                         int32_t n, const lf_grid* grid, int32_t precision, double* beta, double* A,
+                         void* stream, int block) {
   if (!planes) return fail(LF_EINVAL, "planes is NULL");
   if (n_planes < 1 || n_planes > LF_MAX_PLANES) return fail(LF_EINVAL, "need 1 <= n_planes <= 8");
   if (!ratios) return fail(LF_EINVAL, "ratios is NULL");
@@ -209,7 +209,6 @@ extern "C" lf_status lf_trace_multiplane(const lf_plane* planes, int32_t n_plane
   int dev = 0, nsm = 0, occ = 0;
   LF_CUDA(cudaGetDevice(&dev));
   LF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const int block = 256;
   cudaStream_t s = (cudaStream_t)stream;
   long long tiles = (io.n + block - 1) / block;
   auto k = precision == LF_MIXED ? k_trace<LF_MIXED> : precision == LF_FF ? k_trace<LF_FF> : k_trace<LF_FP64>;
@@ -219,4 +218,11 @@ extern "C" lf_status lf_trace_multiplane(const lf_plane* planes, int32_t n_plane
   k<<<(unsigned)g, block, total, s>>>(MP, io, g_member_chunk);
   LF_CUDA(cudaGetLastError());
   return LF_OK;
+}
+
+extern "C" lf_status lf_trace_multiplane(const lf_plane* planes, int32_t n_planes,
+                                         const double* ratios, const double* theta, int32_t n,
+                                         const lf_grid* grid, int32_t precision, double* beta,
+                                         double* A, void* stream) {
+  return trace_rays(planes, n_planes, ratios, theta, n, grid, precision, beta, A, stream, 256);
 }
