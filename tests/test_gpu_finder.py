@@ -226,3 +226,35 @@ def test_three_plane_images_match_oracle(lib, prec, polish):
         total += len(ref)
     assert total >= 20
     assert not polish or close >= 0.8 * total, (close, total)
+
+
+def test_three_plane_finder_edge_cases(lib):
+    api, PM = lib
+    from paper_2609_08649_b300 import _lib as L
+    import ctypes as C
+    wl = W.multiplane_c3(n_grid=8)
+    planes = PM.device_planes(wl)
+    rt = PM.multiplane_ratios(wl.cosmo, [p.z for p in wl.planes], 4.0)
+    grid = W.Grid(-80.0, -80.0, 0.8, 0.8, 201, 201)
+    # nothing to do
+    img, n = api.find_images_multiplane(planes, rt, grid, torch.zeros(0, 2, dtype=torch.float64, device="cuda"))
+    assert n.numel() == 0
+    # a source far outside every caustic: its only image lies outside the grid
+    img, n = api.find_images_multiplane(planes, rt, grid, torch.tensor([[300.0, 300.0]], device="cuda"),
+                                        polish_iters=5)
+    assert int(n[0]) == 0
+    # an undersized workspace and an invalid grid are refused before any launch
+    src = torch.tensor([[2.0, -2.0]], device="cuda")
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    out = torch.empty(8, 2, dtype=torch.float64, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int32, device="cuda")
+    arr = (L.lf_plane * len(planes))(*[p.c_struct() for p in planes])
+    rat = np.ascontiguousarray(rt, dtype=np.float64)
+    gs = api.grid_struct(grid)
+    with pytest.raises(L.LFError):
+        L.check(L.lib.lf_find_images_multiplane(arr, len(planes), rat.ctypes.data_as(C.c_void_p), C.byref(gs), 0,
+                                                api._ptr(src), 1, 8, 0, api._ptr(ws), 16, api._ptr(out),
+                                                api._ptr(cnt), api._stream()))
+    with pytest.raises(L.LFError):
+        api.find_images_multiplane(planes, rt, W.Grid(0.0, 0.0, -0.1, 0.1, 5, 5), src)
+    api.device_error()
