@@ -141,6 +141,13 @@ __device__ __forceinline__ void set_field(lf_comp& c, int f, double v) {
   }
 }
 
+// Sum over the 32 lanes of a warp (every lane takes part and gets the sum).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __device__ __forceinline__ double block_sum(double v, double* scratch) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1175,9 +1182,16 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
       if (mem_grad) sample_scaling(C, th, ssc);
       const T inv_cut_star = (T)(1.0 / ssc.cut_star);
       const int ntask_img = n_img * KS;   // one image per task in the adjoint pass
-      for (int t = tid; t < ntask_img; t += blockDim.x) {
-        const int i = t / KS, k = t - i * KS;
-        const int k0 = (int)((long long)K * k / KS), k1 = (int)((long long)K * (k + 1) / KS);
+      // Every lane of a warp runs each round (inactive ones with zero terms), so that each
+      // parameter's terms are summed over the warp by shuffles and added to the block's
+      // accumulator by one lane: one shared-memory atomic per warp, not one per lane.
+      for (int base = 0; base < ntask_img; base += blockDim.x) {
+        const int t = base + tid;
+        const bool act = t < ntask_img;
+        const int i = act ? t / KS : 0, k = act ? t - i * KS : 0;
+        const int k0 = act ? (int)((long long)K * k / KS) : 0;
+        const int k1 = act ? (int)((long long)K * (k + 1) / KS) : 0;
+        const bool lead = (tid & 31) == 0;
         T cot[5];
         double px, py;
         if (C.np > 1) {
@@ -1194,23 +1208,30 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         }
         for (int f = 0; f < C.n_free; ++f) {
           const int kc = C.free_comp[f];
-          if (C.free_plane[f] != j || kc < k0 || kc >= k1) continue;
+          if (C.free_plane[f] != j) continue;
           const lf_comp& rc = fraw[f];
           if (rc.kind < 1 || rc.kind > 6) continue;
-          Out5<Dual<T, 6>> o;
-          comp_dual<T>(rc, px, py, o);
-          const T b = (T)rc.b;
+          const bool mine = kc >= k0 && kc < k1;      // false for inactive lanes (k0 = k1)
           // field order x, y, b, eps, pa, core, cut; tangent slots x0 y1 eps2 pa3 core4 cut5
           const int slot[7] = {0, 1, -1, 2, 3, 4, 5};
+          T g[7] = {0, 0, 0, 0, 0, 0, 0};
+          if (mine) {
+            Out5<Dual<T, 6>> o;
+            comp_dual<T>(rc, px, py, o);
+            const T b = (T)rc.b;
+            for (int fld = 0; fld < 7; ++fld)
+              if (C.free_p[f][fld] >= 0)
+                g[fld] = (fld == LF_F_B) ? contract(o, cot, -1) : b * contract(o, cot, slot[fld]);
+          }
           for (int fld = 0; fld < 7; ++fld) {
             const int p = C.free_p[f][fld];
             if (p < 0) continue;
-            T g = (fld == LF_F_B) ? contract(o, cot, -1) : b * contract(o, cot, slot[fld]);
-            atomicAdd(&gacc[p], (double)g * xform_deriv(C.p_xform[p], th[p], P.apk));
+            const double gw = warp_sum((double)g[fld]);
+            if (lead) atomicAdd(&gacc[p], gw * xform_deriv(C.p_xform[p], th[p], P.apk));
           }
         }
         if (mem_grad) {
-          const int m0 = max(k0, P.nc) - P.nc, m1 = min(k1, K) - P.nc;
+          const int m0 = act ? max(k0, P.nc) - P.nc : 0, m1 = act ? min(k1, K) - P.nc : 0;
           T gs[6] = {0, 0, 0, 0, 0, 0};
           T qxh, qxl, qyh, qyl;
           if constexpr (MIXED) {
@@ -1258,8 +1279,9 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           }
           for (int q = 0; q < 6; ++q) {
             const int p = C.scal_p[q];
-            if (p >= 0 && m1 > m0)
-              atomicAdd(&gacc[p], (double)gs[q] * xform_deriv(C.p_xform[p], th[p], P.apk));
+            if (p < 0) continue;
+            const double gw = warp_sum((double)gs[q]);
+            if (lead) atomicAdd(&gacc[p], gw * xform_deriv(C.p_xform[p], th[p], P.apk));
           }
         }
       }

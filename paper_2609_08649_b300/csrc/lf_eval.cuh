@@ -217,6 +217,17 @@ __device__ __forceinline__ void accumulate_mixed(const CompT<float>* dc, int nc,
     const CompT<float>& C = dc[c];
     if (C.kind == 0) continue;
     for (int k = 0; k < PPT; ++k) {
+      if (C.kind == K_NFW) {
+        // the spherical NFW is all FP32 (the same operations as eval_comp_mixed's): inline,
+        // so that planes with many of them make no out-of-line call per component
+        Out5<float> o;
+        nfw_sph(offset_of(pxh[k], pxl[k], C.xh, C.xl), offset_of(pyh[k], pyl[k], C.yh, C.yl), C.b,
+                C.irs, o);
+        acc[0][k] = ff_add(acc[0][k], ff_make(o.ax, 0.f));
+        acc[1][k] = ff_add(acc[1][k], ff_make(o.ay, 0.f));
+        ff_acc(acc[2][k], o.pxx); ff_acc(acc[3][k], o.pyy); ff_acc(acc[4][k], o.pxy);
+        continue;
+      }
       ff ax, ay;
       Out5<float> o;
       eval_comp_mixed(C, pxh[k], pxl[k], pyh[k], pyl[k], tab, ax, ay, o);
