@@ -95,9 +95,11 @@ struct ClusterDesc {
 };
 
 // ------------------------------------------------------------------ transforms -----
+// b = 4 pi (v / c)^2 in arcsec, as one constant times v^2 (no FP64 division per sample)
+constexpr double LF_VDISP_K = 4.0 * LF_PI * LF_ARCSEC_PER_RAD / (LF_C_KMS * LF_C_KMS);
 __host__ __device__ inline double apply_xform(int xf, double v, double apk) {
   switch (xf) {
-    case LF_XF_VDISP: { double r = v / LF_C_KMS; return 4.0 * LF_PI * r * r * LF_ARCSEC_PER_RAD; }
+    case LF_XF_VDISP: return LF_VDISP_K * v * v;
     case LF_XF_DEG: return v * (LF_PI / 180.0);
     case LF_XF_KPC: return v * apk;
     default: return v;
@@ -105,7 +107,7 @@ __host__ __device__ inline double apply_xform(int xf, double v, double apk) {
 }
 __host__ __device__ inline double xform_deriv(int xf, double v, double apk) {
   switch (xf) {
-    case LF_XF_VDISP: return 8.0 * LF_PI * v / (LF_C_KMS * LF_C_KMS) * LF_ARCSEC_PER_RAD;
+    case LF_XF_VDISP: return 2.0 * LF_VDISP_K * v;
     case LF_XF_DEG: return LF_PI / 180.0;
     case LF_XF_KPC: return apk;
     default: return 1.0;
@@ -148,16 +150,18 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Sum over the block; the total is returned on thread 0 (0 elsewhere).
 __device__ __forceinline__ double block_sum(double v, double* scratch) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  v = warp_sum(v);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) scratch[warp] = v;
   __syncthreads();
   double r = 0.0;
-  const int nw = blockDim.x >> 5;
-  for (int i = 0; i < nw; ++i) r += scratch[i];
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) r += scratch[i];
+  }
   return r;
 }
 
