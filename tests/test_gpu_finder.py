@@ -240,11 +240,11 @@ def test_three_plane_finder_edge_cases(lib):
     img, n = api.find_images_multiplane(planes, rt, grid, torch.zeros(0, 2, dtype=torch.float64, device="cuda"))
     assert n.numel() == 0
     # a source far outside every caustic: its only image lies outside the grid
-    img, n = api.find_images_multiplane(planes, rt, grid, torch.tensor([[300.0, 300.0]], device="cuda"),
-                                        polish_iters=5)
+    far = torch.tensor([[300.0, 300.0]], dtype=torch.float64, device="cuda")
+    img, n = api.find_images_multiplane(planes, rt, grid, far, polish_iters=5)
     assert int(n[0]) == 0
     # an undersized workspace and an invalid grid are refused before any launch
-    src = torch.tensor([[2.0, -2.0]], device="cuda")
+    src = torch.tensor([[2.0, -2.0]], dtype=torch.float64, device="cuda")
     ws = torch.empty(16, dtype=torch.uint8, device="cuda")
     out = torch.empty(8, 2, dtype=torch.float64, device="cuda")
     cnt = torch.empty(1, dtype=torch.int32, device="cuda")
