@@ -152,7 +152,11 @@ lf_status lf_jacobian_points(const lf_plane* plane, const double* theta, int32_t
  *   (only j > i is read), the last row holds rs[0..n_planes-1].
  * Positions: theta device [n * 2] FP64, or theta == NULL and `grid` (n ignored).
  * beta: device [n * 2] FP64; A: device [n * 4] FP64 row-major (A00, A01, A10, A11);
- * either may be NULL. */
+ * either may be NULL.
+ * Precision: LF_FP64 computes everything in FP64.  LF_MIXED evaluates the components in FP32
+ * on float-float offsets, carries theta_j, the deflections and beta in float-float, and
+ * forms the Jacobian product in FP32.  LF_FF evaluates the deflections in float-float and
+ * keeps the recursion in FP64. */
 lf_status lf_trace_multiplane(const lf_plane* planes, int32_t n_planes, const double* ratios,
                               const double* theta, int32_t n, const lf_grid* grid,
                               int32_t precision, double* beta, double* A, void* stream);

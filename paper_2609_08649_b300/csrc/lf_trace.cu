@@ -4,8 +4,9 @@
 // A_j = I - sum_{i<j} r_ij Psi_i(theta_i) A_i, then beta = theta_1 - sum_j rs_j alpha_j and
 // A = I - sum_j rs_j Psi_j A_j.  All planes are staged into shared memory once per
 // (persistent) block.  LF_MIXED evaluates each plane's components in FP32 on float-float
-// offsets from theta_j (carried in FP64) and keeps the recursion and the 2x2 Jacobian
-// product in FP64; LF_FP64 does everything in FP64.
+// offsets from theta_j, carries theta_j, the deflections and beta in float-float and the 2x2
+// Jacobian product in FP32; LF_FF evaluates in float-float and keeps the recursion in FP64;
+// LF_FP64 does everything in FP64.
 #include "lf_internal.h"
 #include "lf_eval.cuh"
 
@@ -20,6 +21,8 @@ struct MultiPlaneArgs {
   uint32_t base[LF_MAX_PLANES];     // shared-memory offset of each plane's layout
   double r[LF_MAX_PLANES][LF_MAX_PLANES];
   double rs[LF_MAX_PLANES];
+  float2 rf[LF_MAX_PLANES][LF_MAX_PLANES];   // the same ratios as float-float (hi, lo)
+  float2 rsf[LF_MAX_PLANES];
 };
 
 // Stages and digests every plane; returns false (all threads) if a bounded wait ran out.
@@ -83,6 +86,65 @@ __global__ void __launch_bounds__(256) k_trace(MultiPlaneArgs MP, RayIO io, int 
       long long j = p / io.nx, i = p - j * io.nx;
       t1x = io.x0 + (double)i * io.dx;
       t1y = io.y0 + (double)j * io.dy;
+    }
+    if constexpr (MODE == LF_MIXED) {
+      // The recursion with theta_j, the deflections and beta in float-float and the Jacobian
+      // product in FP32 (Psi is FP32-accurate in this tier), on the FP32 pipe.
+      ff t1xf, t1yf;
+      {
+        float h, l;
+        split_ff(t1x, h, l); t1xf = ff_make(h, l);
+        split_ff(t1y, h, l); t1yf = ff_make(h, l);
+      }
+      ff alx[LF_MAX_PLANES], aly[LF_MAX_PLANES];
+      float PAf[LF_MAX_PLANES][4];   // Psi_j A_j, row-major
+      for (int j = 0; j < MP.np; ++j) {
+        ff tx = t1xf, ty = t1yf;
+        float a00 = 1.f, a01 = 0.f, a10 = 0.f, a11 = 1.f;
+        for (int i = 0; i < j; ++i) {
+          const float2 r = MP.rf[i][j];
+          const ff rr = ff_make(r.x, r.y);
+          tx = ff_sub(tx, ff_mul(rr, alx[i]));
+          ty = ff_sub(ty, ff_mul(rr, aly[i]));
+          a00 = fmaf(-r.x, PAf[i][0], a00); a01 = fmaf(-r.x, PAf[i][1], a01);
+          a10 = fmaf(-r.x, PAf[i][2], a10); a11 = fmaf(-r.x, PAf[i][3], a11);
+        }
+        PlaneLayout L = plane_layout<T, Mem>(MP.nc[j], MP.nm[j], MP.base[j]);
+        const CompT<T>* dc = reinterpret_cast<const CompT<T>*>(smem + L.dc);
+        const Mem* dm = reinterpret_cast<const Mem*>(smem + L.dm);
+        float xh[1] = {tx.hi}, xl[1] = {tx.lo}, yh[1] = {ty.hi}, yl[1] = {ty.lo};
+        ff acc[5][1];
+        for (int v = 0; v < 5; ++v) acc[v][0] = ff_zero();
+        accumulate_mixed<1>(dc, MP.nc[j], dm, MP.nm[j], 0, MP.nc[j] + MP.nm[j], chunk, xh, xl, yh, yl,
+                            tab, acc);
+        alx[j] = acc[0][0];
+        aly[j] = acc[1][0];
+        const float pxx = acc[2][0].hi + acc[2][0].lo, pyy = acc[3][0].hi + acc[3][0].lo,
+                    pxy = acc[4][0].hi + acc[4][0].lo;
+        PAf[j][0] = fmaf(pxx, a00, pxy * a10);
+        PAf[j][1] = fmaf(pxx, a01, pxy * a11);
+        PAf[j][2] = fmaf(pxy, a00, pyy * a10);
+        PAf[j][3] = fmaf(pxy, a01, pyy * a11);
+      }
+      ff bx = t1xf, by = t1yf;
+      float A00 = 1.f, A01 = 0.f, A10 = 0.f, A11 = 1.f;
+      for (int j = 0; j < MP.np; ++j) {
+        const float2 r = MP.rsf[j];
+        const ff rr = ff_make(r.x, r.y);
+        bx = ff_sub(bx, ff_mul(rr, alx[j]));
+        by = ff_sub(by, ff_mul(rr, aly[j]));
+        A00 = fmaf(-r.x, PAf[j][0], A00); A01 = fmaf(-r.x, PAf[j][1], A01);
+        A10 = fmaf(-r.x, PAf[j][2], A10); A11 = fmaf(-r.x, PAf[j][3], A11);
+      }
+      if (io.beta) {
+        io.beta[2 * p] = ff_to_double(bx);
+        io.beta[2 * p + 1] = ff_to_double(by);
+      }
+      if (io.A) {
+        io.A[4 * p] = A00; io.A[4 * p + 1] = A01;
+        io.A[4 * p + 2] = A10; io.A[4 * p + 3] = A11;
+      }
+      continue;
     }
     double al[LF_MAX_PLANES][2];
     double PA[LF_MAX_PLANES][4];   // Psi_j A_j, row-major
@@ -200,6 +262,14 @@ lf_status lf::trace_rays(const lf_plane* planes, int32_t n_planes, const double*
     double v = ratios[n_planes * n_planes + j];
     if (!(std::isfinite(v) && v >= 0.0)) return fail(LF_EINVAL, "invalid source ratio %d", j);
     MP.rs[j] = v;
+  }
+  for (int i = 0; i < n_planes; ++i) {
+    for (int j = 0; j < n_planes; ++j) {
+      const float h = (float)MP.r[i][j];
+      MP.rf[i][j] = make_float2(h, (float)(MP.r[i][j] - (double)h));
+    }
+    const float h = (float)MP.rs[i];
+    MP.rsf[i] = make_float2(h, (float)(MP.rs[i] - (double)h));
   }
   uint32_t total = 0;
   if (precision == LF_MIXED) LF_TRY((fill_planes<float, MemT<float>>(planes, n_planes, MP, total)));
