@@ -135,6 +135,31 @@ lf_status lf_jacobian_grid(const lf_plane* plane, const lf_grid* grid, double a_
                            int32_t precision, double* ax, double* ay, float* kappa,
                            float* g1, float* g2, double* mu, void* stream);
 
+/* The maps of lf_jacobian_grid written to HOST memory, with the device-to-host copies
+ * overlapped with the computation (the paper has no counterpart: this is the I/O path of the
+ * Sec. 2.1 maps).  The grid is split into `bands` bands of whole rows (at most ny; the last
+ * one may be shorter).  Each band is computed on `stream` into one of two device slots of
+ * `workspace` while the previous band is copied to the host on a second stream owned by the
+ * library (one per device, created on first use).
+ * ax, ay, kappa, g1, g2, mu: HOST [ny * nx] row-major, types as in lf_jacobian_grid; any may
+ *   be NULL (all NULL: nothing is computed).  Page-locked (pinned) memory lets the copies
+ *   run concurrently with the computation; pageable memory gives the same results without
+ *   the overlap.  The caller must not touch them until `stream` has been synchronised.
+ * workspace: device, 256-byte aligned, at least lf_jacobian_grid_host_workspace(grid, bands)
+ *   bytes, owned by the caller and reusable once the call's work on `stream` has finished.
+ * The work is ordered on `stream`: it starts after the caller's earlier work there, and
+ * later work there runs after the last copy.
+ * Band k's rows start at y0 + r0 dy (r0 = its first row), so FP64 pixel positions may differ
+ * from one lf_jacobian_grid call over the whole grid by one rounding (about 1e-16 relative);
+ * the first band's are identical.
+ * Errors: LF_EINVAL (invalid grid, plane, a_dis, precision, bands < 1, or a missing,
+ * undersized or misaligned workspace) before any launch; LF_ECUDA from the CUDA runtime. */
+size_t lf_jacobian_grid_host_workspace(const lf_grid* grid, int32_t bands);
+lf_status lf_jacobian_grid_host(const lf_plane* plane, const lf_grid* grid, double a_dis,
+                                int32_t precision, double* ax, double* ay, float* kappa,
+                                float* g1, float* g2, double* mu, int32_t bands,
+                                void* workspace, size_t workspace_bytes, void* stream);
+
 /* Same quantities at arbitrary positions: theta device [n * 2] FP64 (x, y interleaved). */
 lf_status lf_jacobian_points(const lf_plane* plane, const double* theta, int32_t n,
                              double a_dis, int32_t precision, double* ax, double* ay,

@@ -72,6 +72,7 @@ def _load():
         "lf_deflect_grid": [vp, vp, i32, vp, vp, vp],
         "lf_jacobian_grid": [vp, vp, f64, i32, vp, vp, vp, vp, vp, vp, vp],
         "lf_jacobian_points": [vp, vp, i32, f64, i32, vp, vp, vp, vp, vp, vp, vp],
+        "lf_jacobian_grid_host": [vp, vp, f64, i32, vp, vp, vp, vp, vp, vp, i32, vp, C.c_size_t, vp],
         "lf_trace_multiplane": [vp, i32, vp, vp, i32, vp, i32, vp, vp, vp],
         "lf_plan_create": [vp, vp, i32, i32, i32, i32],
         "lf_chi2_batch": [vp, vp, i32, vp, vp],
@@ -99,6 +100,8 @@ def _load():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = C.c_double
+    lib.lf_jacobian_grid_host_workspace.argtypes = [vp, i32]
+    lib.lf_jacobian_grid_host_workspace.restype = C.c_size_t
     lib.lf_find_images_workspace.argtypes = [i32, i32, i32, i32]
     lib.lf_find_images_workspace.restype = C.c_size_t
     lib.lf_find_images_multiplane_workspace.argtypes = [i32, i32, i32, i32]
@@ -111,7 +114,8 @@ def _load():
 lib = _load()
 
 # Every symbol the header declares (checked by the CPU test-suite).
-EXPORTS = ["lf_deflect_grid", "lf_jacobian_grid", "lf_jacobian_points", "lf_trace_multiplane",
+EXPORTS = ["lf_deflect_grid", "lf_jacobian_grid", "lf_jacobian_grid_host", "lf_jacobian_grid_host_workspace",
+           "lf_jacobian_points", "lf_trace_multiplane",
            "lf_plan_create", "lf_chi2_batch", "lf_chi2_grad_batch", "lf_plan_destroy",
            "lf_chi2_img_batch", "lf_aies_run", "lf_mh_run", "lf_nm_run", "lf_find_images", "lf_find_images_workspace", "lf_find_images_multiplane",
            "lf_find_images_multiplane_workspace",

@@ -66,6 +66,38 @@ def jacobian_grid(plane: DevicePlane, grid, a_dis, precision="mixed", outputs=AL
     return {k: v.view(grid.ny, grid.nx) for k, v in o.items()}
 
 
+def jacobian_grid_host_workspace(grid, bands=16) -> int:
+    gs = grid_struct(grid)
+    return int(L.lib.lf_jacobian_grid_host_workspace(C.byref(gs), int(bands)))
+
+
+def jacobian_grid_host(plane: DevicePlane, grid, a_dis, precision="mixed", out=None, bands=16,
+                       workspace=None, outputs=ALL_OUTPUTS):
+    """The maps of jacobian_grid written to host tensors (`out`: name -> contiguous CPU tensor
+    of ny*nx elements, float64 for ax, ay, mu and float32 for kappa, g1, g2, pinned for
+    overlap; allocated pinned when None), computed in `bands` row bands whose device-to-host
+    copies overlap the computation.  `workspace`: uint8 CUDA tensor of at least
+    jacobian_grid_host_workspace(grid, bands) bytes (allocated when None).  Returns `out`
+    after synchronising the current stream."""
+    n = grid.nx * grid.ny
+    if out is None:
+        out = {k: torch.empty(n, dtype=torch.float32 if k in ("kappa", "g1", "g2") else torch.float64,
+                              pin_memory=True) for k in outputs}
+    for k, t in out.items():
+        want = torch.float32 if k in ("kappa", "g1", "g2") else torch.float64
+        if k not in ALL_OUTPUTS or t.is_cuda or t.dtype != want or not t.is_contiguous() or t.numel() != n:
+            raise TypeError(f"out[{k!r}] must be a contiguous CPU {want} tensor of {n} elements")
+    need = jacobian_grid_host_workspace(grid, bands)
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device="cuda")
+    ps, gs = plane.c_struct(), grid_struct(grid)
+    L.check(L.lib.lf_jacobian_grid_host(C.byref(ps), C.byref(gs), float(a_dis), _prec(precision),
+                                        *[_ptr(out.get(k)) for k in ALL_OUTPUTS], int(bands),
+                                        _ptr(workspace), workspace.numel(), _stream()))
+    torch.cuda.current_stream().synchronize()
+    return out
+
+
 def jacobian_points(plane: DevicePlane, theta: torch.Tensor, a_dis, precision="mixed",
                     outputs=ALL_OUTPUTS):
     theta = _dev64(theta, "theta")

@@ -3,6 +3,7 @@
 #include <type_traits>
 #include "lf_host.cu"
 #include "lf_grid.cu"
+#include "lf_hostio.cu"
 #include "lf_finder.cu"
 #include "lf_trace.cu"
 #include "lf_chi2.cu"

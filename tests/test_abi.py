@@ -78,3 +78,33 @@ def test_python_layer_rejects_tensors_the_abi_would_misread():
         api._dev64(torch.zeros(3, dtype=torch.float64), "x")   # host memory
     with pytest.raises(TypeError):
         api._dev64([1.0, 2.0], "x")
+
+
+def test_host_maps_workspace_and_validation():
+    """lf_jacobian_grid_host: the workspace size follows the band split (two slots of
+    ceil(ny / bands) rows, 36 bytes a pixel rounded to 256 per map), and invalid arguments
+    are refused before any CUDA call."""
+    from paper_2609_08649_b300 import _lib as L
+    up = lambda b: (b + 255) // 256 * 256
+    g = L.lf_grid(0, 0, 0.1, 0.1, 100, 263)
+    for bands, rows in [(1, 263), (5, 53), (16, 17), (263, 1), (1000, 1)]:
+        px = 100 * rows
+        assert L.lib.lf_jacobian_grid_host_workspace(C.byref(g), bands) == 2 * (3 * up(8 * px) + 3 * up(4 * px))
+    assert L.lib.lf_jacobian_grid_host_workspace(C.byref(g), 0) == 0
+    assert L.lib.lf_jacobian_grid_host_workspace(None, 4) == 0
+    p = L.lf_plane()
+    p.n_comp, p.n_mem = 0, 0
+    need = L.lib.lf_jacobian_grid_host_workspace(C.byref(g), 4)
+    host = C.c_void_p(64)
+    call = lambda grid, a, prec, bands, ws, nbytes: L.lib.lf_jacobian_grid_host(
+        C.byref(p), grid, a, prec, host, None, None, None, None, None, bands, ws, nbytes, None)
+    assert call(C.byref(g), 0.5, L.LF_MIXED, 0, C.c_void_p(256), need) == L.LF_EINVAL           # bands
+    assert b"bands" in L.lib.lf_last_error()
+    assert call(C.byref(g), 0.5, L.LF_MIXED, 4, None, need) == L.LF_EINVAL                       # no workspace
+    assert call(C.byref(g), 0.5, L.LF_MIXED, 4, C.c_void_p(256), need - 1) == L.LF_EINVAL        # undersized
+    assert b"workspace" in L.lib.lf_last_error()
+    assert call(C.byref(g), 0.5, L.LF_MIXED, 4, C.c_void_p(128), need) == L.LF_EINVAL            # misaligned
+    assert call(C.byref(g), 1.5, L.LF_MIXED, 4, C.c_void_p(256), need) == L.LF_EINVAL            # a_dis
+    assert call(C.byref(g), 0.5, 7, 4, C.c_void_p(256), need) == L.LF_EINVAL                     # precision
+    bad = L.lf_grid(0, 0, 0.1, 0.1, 100, 0)
+    assert call(C.byref(bad), 0.5, L.LF_MIXED, 4, C.c_void_p(256), need) == L.LF_EINVAL          # grid

@@ -199,3 +199,29 @@ def test_round_and_nfw_components(lib, prec):
     wl = W.Workload("round_nfw", W.Cosmo(), [W.PhysPlane(0.5, comps)], z_s=3.0,
                     grid=W.Grid(-60.0, -60.0, 0.37, 0.41, 325, 293))
     _check(lib, wl, wl.grid, cz.a_dis(0.5, 3.0), prec, coef=16.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_maps_to_host_in_bands(lib, prec):
+    """lf_jacobian_grid_host writes the maps to pinned host memory in row bands whose copies
+    overlap the computation.  On a grid with dyadic origin and spacing every band's pixel
+    positions are exact, so the host maps equal one lf_jacobian_grid call bit for bit: one
+    band, a ragged split, more bands than rows, and a subset of the outputs."""
+    api, PM = lib
+    from paper_2609_08649_b300 import _lib as L
+    wl = W.cluster_c1()
+    dp = PM.device_planes(wl)[0]
+    a = cz.a_dis(0.5, 9.0)
+    grid = W.Grid(-81.875, -80.0, 0.78125, 1.0, 211, 157)
+    ref = {k: v.cpu().numpy().ravel() for k, v in api.jacobian_grid(dp, grid, a, prec).items()}
+    for bands in (1, 5, 16, 1000):
+        out = api.jacobian_grid_host(dp, grid, a, prec, bands=bands)
+        for k in api.ALL_OUTPUTS:
+            assert np.array_equal(out[k].numpy(), ref[k]), (k, bands)
+    out = api.jacobian_grid_host(dp, grid, a, prec, bands=3, outputs=("kappa", "mu"))
+    assert set(out) == {"kappa", "mu"}
+    assert np.array_equal(out["kappa"].numpy(), ref["kappa"]) and np.array_equal(out["mu"].numpy(), ref["mu"])
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(L.LFError):
+        api.jacobian_grid_host(dp, grid, a, prec, bands=4, workspace=ws)
+    api.device_error()
