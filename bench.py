@@ -326,7 +326,7 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-E2E_BANDS = 16   # row bands of the end-to-end call (each band's maps are copied while the next is computed)
+E2E_BANDS = 32   # row bands of the end-to-end call (each band's maps are copied while the next is computed)
 
 KERNEL_SOURCES = ["lf_common.cuh", "lf_cse_table.h", "lf_eval.cuh", "lf_grid.cu", "lf_host.cu", "lf_internal.h"]
 

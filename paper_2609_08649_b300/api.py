@@ -66,12 +66,12 @@ def jacobian_grid(plane: DevicePlane, grid, a_dis, precision="mixed", outputs=AL
     return {k: v.view(grid.ny, grid.nx) for k, v in o.items()}
 
 
-def jacobian_grid_host_workspace(grid, bands=16) -> int:
+def jacobian_grid_host_workspace(grid, bands=32) -> int:
     gs = grid_struct(grid)
     return int(L.lib.lf_jacobian_grid_host_workspace(C.byref(gs), int(bands)))
 
 
-def jacobian_grid_host(plane: DevicePlane, grid, a_dis, precision="mixed", out=None, bands=16,
+def jacobian_grid_host(plane: DevicePlane, grid, a_dis, precision="mixed", out=None, bands=32,
                        workspace=None, outputs=ALL_OUTPUTS):
     """The maps of jacobian_grid written to host tensors (`out`: name -> contiguous CPU tensor
     of ny*nx elements, float64 for ax, ay, mu and float32 for kappa, g1, g2, pinned for
