@@ -108,3 +108,21 @@ def test_host_maps_workspace_and_validation():
     assert call(C.byref(g), 0.5, 7, 4, C.c_void_p(256), need) == L.LF_EINVAL                     # precision
     bad = L.lf_grid(0, 0, 0.1, 0.1, 100, 0)
     assert call(C.byref(bad), 0.5, L.LF_MIXED, 4, C.c_void_p(256), need) == L.LF_EINVAL          # grid
+
+
+def test_host_maps_binding_rejects_wrong_outputs():
+    """api.jacobian_grid_host checks the host tensors before any CUDA call: dtype, device,
+    size, contiguity and the output names."""
+    import torch
+    from paper_2609_08649_b300 import api
+    from paper_2609_08649_b300 import workloads as W
+    grid = W.Grid(0.0, 0.0, 0.1, 0.1, 8, 4)
+    n = 32
+    bad = [{"ax": torch.zeros(n, dtype=torch.float32)},                 # alpha is FP64
+           {"kappa": torch.zeros(n, dtype=torch.float64)},              # kappa is FP32
+           {"mu": torch.zeros(n - 1, dtype=torch.float64)},             # wrong size
+           {"ay": torch.zeros(2 * n, dtype=torch.float64)[::2]},        # not contiguous
+           {"beta": torch.zeros(n, dtype=torch.float64)}]               # not a map
+    for out in bad:
+        with pytest.raises(TypeError):
+            api.jacobian_grid_host(None, grid, 0.5, "mixed", out=out)
