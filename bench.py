@@ -34,8 +34,12 @@ METRIC = "lens evals/s (samples×positions×components)"
 UNIT = "lens evals/s"
 WORKLOAD = ("cluster_dpie302_grid4096: 2 elliptical dPIE halos + 300 PJE members, "
             "4096x4096 grid at 0.04\", alpha/kappa/gamma/mu at z_s=9")
-FP32_INSTR_PER_EVAL = 33      # FP32 lane operations of one member evaluation
-XU_INSTR_PER_EVAL = 4         # MUFU operations of one member evaluation
+# One member evaluation (alpha and psi_ij of a round pseudo-Jaffe member at one position, with
+# its float-float offset and the accumulation): 33 FP32 lane operations -- offsets 6, r^2 2,
+# S^2 and R^2 2, S and R 2, S + s and R + a 2, their product 1, P and Q 2, R + S 1, kbar 3,
+# t 5, sums 7 -- and 4 MUFU operations (2 rsqrt, 2 rcp).
+FP32_INSTR_PER_EVAL = 33
+XU_INSTR_PER_EVAL = 4
 FP32_LANES_PER_SM, XU_LANES_PER_SM = 128, 16
 
 
