@@ -69,10 +69,16 @@ typedef enum {
  * LF_MIXED: per-component closed forms in FP32 on offsets taken in float-float (the
  * deflection of elliptical isothermal components and of the shear in float-float), FP32
  * sums per member chunk folded into float-float accumulators, then FP64 for det A, mu, the
- * multi-plane Jacobian product and the chi^2 reduction.
+ * multi-plane Jacobian product and the chi^2 reduction.  The maps (lf_deflect_grid,
+ * lf_jacobian_grid, lf_jacobian_points, lf_jacobian_grid_host) anchor each tile of 16 x 16
+ * pixels (or 256 points) at its centre: every member's deflection there in float-float,
+ * its change across the tile in FP32 from cancellation-free differences, members that
+ * change fast across the tile and every explicit component in float-float; alpha within
+ * 1e-6 arcsec of FP64 at cluster scale, psi_ij FP32.
  * LF_FF: as LF_MIXED, but the deflection of every member is also carried in float-float
  * (about 48 significant bits on the FP32 pipe) and accumulated in float-float; psi_ij
- * stays FP32.  Spherical NFW components stay FP32 in both mixed tiers. */
+ * stays FP32.  Spherical NFW components stay FP32 in the mixed tier's chi^2 and trace
+ * kernels. */
 typedef enum { LF_FP64 = 0, LF_MIXED = 1, LF_FF = 2 } lf_precision;
 
 /* One explicit component, 64 bytes (device arrays of these are staged into shared
@@ -137,8 +143,8 @@ lf_status lf_jacobian_grid(const lf_plane* plane, const lf_grid* grid, double a_
 
 /* The maps of lf_jacobian_grid written to HOST memory, with the device-to-host copies
  * overlapped with the computation (the paper has no counterpart: this is the I/O path of the
- * Sec. 2.1 maps).  The grid is split into `bands` bands of whole rows (at most ny; the last
- * one may be shorter).  Each band is computed on `stream` into one of two device slots of
+ * Sec. 2.1 maps).  The grid is split into at most `bands` bands of whole rows, each a
+ * multiple of 16 rows (the mixed maps' tile height; the last band may be shorter).  Each band is computed on `stream` into one of two device slots of
  * `workspace` while the previous band is copied to the host on a second stream owned by the
  * library (one per device, created on first use).
  * ax, ay, kappa, g1, g2, mu: HOST [ny * nx] row-major, types as in lf_jacobian_grid; any may

@@ -1039,6 +1039,18 @@ __host__ __device__ inline void digest_member_x(double x, double y, double b, do
   m.b = (float)b; m.fb = (float)fb; m.fs = (float)fs; m.loglr = (float)loglr;
 }
 
+// alpha of one member at the float-float offset (dx, dy), in float-float (the form below).
+LF_INLINE void member_alpha_ff(const MemX& m, const ff& dx, const ff& dy, ff& ax, ff& ay) {
+  const ff r2 = ff_add(ff_sqr(dx), ff_sqr(dy));
+  const ff S = ff_sqrt(ff_add(ff_make(m.s2h, m.s2l), r2));
+  const ff R = ff_sqrt(ff_add(ff_make(m.a2h, m.a2l), r2));
+  const ff PQ = ff_rcp(ff_mul(ff_add(S, ff_make(m.sh, m.sl)), ff_add(R, ff_make(m.ah, m.al))));
+  const ff br = ff_add_f(ff_mul(ff_make(m.apch, m.apcl), ff_rcp(ff_add(R, S))), 1.0f);
+  const ff kbar = ff_mul(ff_mul(ff_make(m.bdh, m.bdl), PQ), br);
+  ax = ff_mul(kbar, dx);
+  ay = ff_mul(kbar, dy);
+}
+
 // alpha of one member in float-float: kbar = b (a - s) [(a + s)/(R + S) + 1] / ((S + s)(R + a)),
 // alpha = kbar x; psi_ij in FP32 from the same form (pje_round).
 LF_INLINE void eval_member_x(const MemX& m, float ph_x, float pl_x, float ph_y, float pl_y, ff& ax,

@@ -133,6 +133,307 @@ __global__ void __launch_bounds__(256, PACK ? LF_MAP_MINB_PACK : LF_MAP_MINB) k_
   }
 }
 
+// ---------------------------------------------------- LF_MIXED: anchored tiles ------
+// The LF_MIXED maps.  A block owns a tile of positions (16 x 16 pixels of a grid, or 256
+// consecutive points of a list) and an anchor theta0 at the tile's centre.  Each member's
+// deflection at theta0 is evaluated once per tile in float-float; at each position only the
+// change alpha_k(theta) - alpha_k(theta0) is evaluated in FP32, from exact differences:
+// with d0 = theta0 - c, e = theta - theta0 and u = |d0 + e|^2,
+//   du = u - u0 = 2 d0.e + |e|^2,   S - S0 = du / (S + S0)   (S = sqrt(s^2 + u)),
+//   1/(S + s) - 1/(S0 + s) = -du / ((S + S0)(S + s)(S0 + s)),  likewise for R = sqrt(a^2 + u),
+//   kbar = b [1/(S + s) - 1/(R + a)],  alpha_k(theta) - alpha_k(theta0) = dkbar d0 + kbar e.
+// No term cancels, so the FP32 rounding scales with the change (about 3 kbar(theta0) h over a
+// tile of half-diagonal h) instead of with |alpha_k|: on the cluster field at 0.04" pixels this
+// cuts the deflection error from ~1e-6" rms to ~2e-8".  Members whose change across the tile
+// is not small (3 kbar(theta0) h > T, or closer to theta0 than 2 h) are evaluated per position
+// in float-float instead, as are the explicit components.  psi_ij is FP32 as in the other
+// mixed kernels.  T = LF_ANCHOR_T min(1, LF_ANCHOR_H0 / h): coarse tiles send more members to
+// the float-float path, so the precision does not depend on the pixel scale.
+#ifndef LF_ANCHOR_MINB
+#define LF_ANCHOR_MINB 4
+#endif
+#ifndef LF_ANCHOR_T
+#define LF_ANCHOR_T 0.3f
+#endif
+#ifndef LF_ANCHOR_H0
+#define LF_ANCHOR_H0 0.5
+#endif
+constexpr int LF_ATILE = 16;   // anchored grid tile: 16 x 16 pixels (one per thread of a 256-thread block)
+
+// Two members per record at one tile's anchor (lane x: member 2j, lane y: member 2j + 1).
+struct __align__(16) AnchorPair {
+  float2 dx0, dy0;   // theta0 - c, rounded to FP32
+  float2 S20, R20;   // s^2 + u0, a^2 + u0, u0 = |d0|^2
+  float2 S0s, R0a;   // S0 s, R0 a
+  float2 cs, ca;     // S0 + s, R0 + a
+  float2 P0, Q0;     // 1 / (S0 + s), 1 / (R0 + a)
+  float2 b, kb0;     // strength (0 for a member evaluated per position), kbar(theta0)
+};
+
+__device__ __forceinline__ void anchor_pad_lane(AnchorPair& p, int lane) {
+  float* f = reinterpret_cast<float*>(&p) + lane;   // field k of the lane at f[2 k]
+  f[0] = 0.f; f[2] = 0.f; f[4] = 1.f; f[6] = 1.f; f[8] = 0.f; f[10] = 0.f;
+  f[12] = 1.f; f[14] = 1.f; f[16] = 0.f; f[18] = 0.f; f[20] = 0.f; f[22] = 0.f;
+}
+
+// The change of both members' alpha and their psi_ij at one position (offset e from the
+// anchor; e2 = 2 e, ee = |e|^2, all duplicated into both halves), added into packed chunk
+// sums: c[0], c[1] += change of alpha_x, alpha_y; c[2] += kbar; c[3] += t dx^2;
+// c[4] += t dx dy; c[5] += t dy^2 (psi_ij = kbar delta_ij + t x_i x_j, t = b (Q^2/R - P^2/S)).
+// 36 FP32 lane-operations and 4 MUFU per member.
+__device__ __forceinline__ void anchor_pair_acc(const AnchorPair& m, float2 e2x, float2 e2y, float2 ee,
+                                                float2 ex, float2 ey, float2 (&c)[6]) {
+  const float2 du = fma2(m.dx0, e2x, fma2(m.dy0, e2y, ee));
+  const float2 S2 = add2(m.S20, du), R2 = add2(m.R20, du);
+  float2 iS, iR, S, R;
+  iS.x = rsqrtf(S2.x); iS.y = rsqrtf(S2.y);
+  iR.x = rsqrtf(R2.x); iR.y = rsqrtf(R2.y);
+  S.x = S2.x * iS.x; S.y = S2.y * iS.y;
+  R.x = R2.x * iR.x; R.y = R2.y * iR.y;
+  // (S + S0)(S + s)(S0 + s) = (S^2 + S0 s + S (S0 + s)) (S0 + s), likewise for R
+  const float2 As = mul2(fma2(S, m.cs, add2(S2, m.S0s)), m.cs);
+  const float2 Aa = mul2(fma2(R, m.ca, add2(R2, m.R0a)), m.ca);
+  float2 gS, gA;     // the decrease of 1/(S + s) and of 1/(R + a) from the anchor
+  gS.x = du.x * __fdividef(1.f, As.x); gS.y = du.y * __fdividef(1.f, As.y);
+  gA.x = du.x * __fdividef(1.f, Aa.x); gA.y = du.y * __fdividef(1.f, Aa.y);
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 P = fma2(gS, m1, m.P0), Q = fma2(gA, m1, m.Q0);
+  const float2 dk = mul2(m.b, fma2(gS, m1, gA));
+  const float2 kb = add2(m.kb0, dk);
+  c[0] = fma2(kb, ex, fma2(dk, m.dx0, c[0]));
+  c[1] = fma2(kb, ey, fma2(dk, m.dy0, c[1]));
+  const float2 P2 = mul2(P, P), Q2 = mul2(Q, Q);
+  float2 tt;
+  tt.x = fmaf(-P2.x, iS.x, Q2.x * iR.x); tt.y = fmaf(-P2.y, iS.y, Q2.y * iR.y);
+  const float2 t = mul2(m.b, tt);
+  const float2 dx = add2(m.dx0, ex), dy = add2(m.dy0, ey);
+  c[2] = add2(c[2], kb);
+  const float2 tdx = mul2(t, dx), tdy = mul2(t, dy);
+  c[3] = fma2(tdx, dx, c[3]);
+  c[4] = fma2(tdx, dy, c[4]);
+  c[5] = fma2(tdy, dy, c[5]);
+}
+
+// Shared memory of the anchored kernel (host and device agree on it).
+struct AnchorLayout {
+  uint32_t rawc, rawm, dc, dm, ap, bits, red, total;
+};
+__host__ __device__ inline AnchorLayout anchor_layout(int nc, int nm) {
+  AnchorLayout L;
+  uint32_t o = (LF_MAP_BASE + 15u) & ~15u;
+  L.rawc = o; o += (uint32_t)nc * 64u;
+  L.rawm = o; o += (uint32_t)nm * 32u;
+  o = (o + 15u) & ~15u;
+  L.dc = o; o += (uint32_t)nc * (uint32_t)sizeof(CompT<float>);
+  o = (o + 15u) & ~15u;
+  L.dm = o; o += (uint32_t)nm * (uint32_t)sizeof(MemX);
+  o = (o + 15u) & ~15u;
+  L.ap = o; o += (uint32_t)((nm + 1) / 2) * (uint32_t)sizeof(AnchorPair);
+  o = (o + 15u) & ~15u;
+  L.bits = o; o += (uint32_t)((nm + 31) / 32) * 4u;
+  o = (o + 15u) & ~15u;
+  L.red = o; o += 8u * 4u * 8u;      // 8 warps x 4 doubles
+  L.total = (o + 15u) & ~15u;
+  return L;
+}
+
+__device__ __forceinline__ ff ff_shfl_xor(const ff& v, int off) {
+  return ff_make(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
+}
+
+template <bool GRID>
+__global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_comp* __restrict__ comp, int nc,
+                                                                  const lf_member* __restrict__ mem, int nm,
+                                                                  lf_scaling sc, PosArgs P, OutArgs O, int chunk) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  const AnchorLayout L = anchor_layout(nc, nm);
+  lf_comp* rawc = reinterpret_cast<lf_comp*>(smem + L.rawc);
+  lf_member* rawm = reinterpret_cast<lf_member*>(smem + L.rawm);
+  CompT<float>* dc = reinterpret_cast<CompT<float>*>(smem + L.dc);
+  MemX* dm = reinterpret_cast<MemX*>(smem + L.dm);
+  AnchorPair* ap = reinterpret_cast<AnchorPair*>(smem + L.ap);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(smem + L.bits);
+  double* red = reinterpret_cast<double*>(smem + L.red);
+  float2* tab = reinterpret_cast<float2*>(smem + 16);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) mbar_init(bar, 1);
+  init_ff_tables(tab);
+  __syncthreads();
+  bool ok = stage_to_smem(rawc, comp, (uint32_t)nc * 64u, bar, 0);
+  if (ok) ok = stage_to_smem(rawm, mem, (uint32_t)nm * 32u, bar, nc > 0 ? 1 : 0);
+  if (!ok) return;
+  digest_plane_x(rawc, nc, rawm, nm, sc, dc, dm);
+  __syncthreads();
+
+  const int np = (nm + 1) / 2, nw = (nm + 31) / 32;
+  const long long tiles_x = GRID ? (P.nx + LF_ATILE - 1) / LF_ATILE : 1;
+  const long long ny = GRID ? P.n / P.nx : 0;
+  const long long n_tiles = GRID ? tiles_x * ((ny + LF_ATILE - 1) / LF_ATILE) : (P.n + 255) / 256;
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    // this thread's position and the tile's anchor (FP64)
+    double x, y, cx, cy, h;
+    long long pid;
+    bool valid;
+    if constexpr (GRID) {
+      const long long tx = tile % tiles_x, ty = tile / tiles_x;
+      const long long i = tx * LF_ATILE + (tid & (LF_ATILE - 1)), j = ty * LF_ATILE + tid / LF_ATILE;
+      valid = i < P.nx && j < ny;
+      pid = j * P.nx + i;
+      x = P.x0 + (double)i * P.dx;
+      y = P.y0 + (double)j * P.dy;
+      cx = P.x0 + ((double)(tx * LF_ATILE) + 0.5 * (LF_ATILE - 1)) * P.dx;
+      cy = P.y0 + ((double)(ty * LF_ATILE) + 0.5 * (LF_ATILE - 1)) * P.dy;
+      h = 0.5 * (LF_ATILE - 1) * sqrt(P.dx * P.dx + P.dy * P.dy);
+    } else {
+      pid = tile * 256 + tid;
+      valid = pid < P.n;
+      x = valid ? P.pts[2 * pid] : 0.0;
+      y = valid ? P.pts[2 * pid + 1] : 0.0;
+      // the tile's bounding box (non-finite positions ignored)
+      const bool fin = valid && isfinite(x) && isfinite(y);
+      double b4[4] = {fin ? x : INFINITY, fin ? -x : INFINITY, fin ? y : INFINITY, fin ? -y : INFINITY};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        for (int off = 16; off > 0; off >>= 1) b4[q] = fmin(b4[q], __shfl_xor_sync(0xffffffffu, b4[q], off));
+      if (lane == 0)
+        for (int q = 0; q < 4; ++q) red[warp * 4 + q] = b4[q];
+      __syncthreads();
+      for (int q = 0; q < 4; ++q) {
+        b4[q] = red[q];
+        for (int w = 1; w < 8; ++w) b4[q] = fmin(b4[q], red[w * 4 + q]);
+      }
+      __syncthreads();
+      if (!(b4[0] <= -b4[1])) { b4[0] = 0.0; b4[1] = 0.0; }     // no finite position in the tile
+      if (!(b4[2] <= -b4[3])) { b4[2] = 0.0; b4[3] = 0.0; }
+      cx = 0.5 * (b4[0] - b4[1]);
+      cy = 0.5 * (b4[2] - b4[3]);
+      h = 0.5 * sqrt((b4[0] + b4[1]) * (b4[0] + b4[1]) + (b4[2] + b4[3]) * (b4[2] + b4[3]));
+      if (!valid) { x = cx; y = cy; }
+    }
+    float ahx, alx, ahy, aly;
+    split_ff(cx, ahx, alx);
+    split_ff(cy, ahy, aly);
+    const float hf = (float)h;
+    const float thr = LF_ANCHOR_T * (float)fmin(1.0, LF_ANCHOR_H0 / fmax(h, 1e-300));
+
+    // ---- anchor pass: each member's record, its float-float deflection at theta0 (summed
+    // over the block), and the members left to the per-position float-float path
+    ff sax = ff_zero(), say = ff_zero();
+    for (int k0 = 0; k0 < 2 * np; k0 += 256) {
+      const int k = k0 + tid;
+      bool near = false;
+      if (k < 2 * np) {
+        AnchorPair& rec = ap[k >> 1];
+        float* f = reinterpret_cast<float*>(&rec) + (k & 1);
+        if (k < nm) {
+          const MemX& m = dm[k];
+          const ff d0x = offset_ff(ahx, alx, m.xh, m.xl), d0y = offset_ff(ahy, aly, m.yh, m.yl);
+          const float dx0 = d0x.hi, dy0 = d0y.hi;
+          const float u0 = fmaf(dx0, dx0, dy0 * dy0);
+          const float S20 = m.s2h + u0, R20 = m.a2h + u0;
+          const float S0 = S20 * rsqrtf(S20), R0 = R20 * rsqrtf(R20);
+          const float cs = S0 + m.sh, ca = R0 + m.ah;
+          const float P0 = __fdividef(1.f, cs), Q0 = __fdividef(1.f, ca);
+          const float kb0 = m.bdh * P0 * Q0 * fmaf(m.apch, __fdividef(1.f, R0 + S0), 1.f);
+          near = (3.f * kb0 * hf > thr) || ((double)u0 < 4.0 * h * h);
+          if (!near) {
+            ff ax, ay;
+            member_alpha_ff(m, d0x, d0y, ax, ay);
+            sax = ff_add(sax, ax);
+            say = ff_add(say, ay);
+            f[0] = dx0; f[2] = dy0; f[4] = S20; f[6] = R20; f[8] = S0 * m.sh; f[10] = R0 * m.ah;
+            f[12] = cs; f[14] = ca; f[16] = P0; f[18] = Q0; f[20] = m.b; f[22] = kb0;
+          } else {
+            anchor_pad_lane(rec, k & 1);
+          }
+        } else {
+          anchor_pad_lane(rec, k & 1);   // the zero-strength partner of an odd member count
+        }
+      }
+      const uint32_t word = __ballot_sync(0xffffffffu, near);
+      const int wi = (k0 >> 5) + warp;
+      if (lane == 0 && wi < nw) bits[wi] = word;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      sax = ff_add(sax, ff_shfl_xor(sax, off));
+      say = ff_add(say, ff_shfl_xor(say, off));
+    }
+    float* redf = reinterpret_cast<float*>(red);
+    if (lane == 0) {
+      redf[warp * 4 + 0] = sax.hi; redf[warp * 4 + 1] = sax.lo;
+      redf[warp * 4 + 2] = say.hi; redf[warp * 4 + 3] = say.lo;
+    }
+    __syncthreads();
+    sax = ff_make(redf[0], redf[1]);
+    say = ff_make(redf[2], redf[3]);
+    for (int w = 1; w < 8; ++w) {
+      sax = ff_add(sax, ff_make(redf[w * 4 + 0], redf[w * 4 + 1]));
+      say = ff_add(say, ff_make(redf[w * 4 + 2], redf[w * 4 + 3]));
+    }
+
+    // ---- per position: the anchored members' changes, then the float-float terms
+    const double exd = x - cx, eyd = y - cy;
+    const float ex = (float)exd, ey = (float)eyd;
+    const float exl = (float)(exd - (double)ex), eyl = (float)(eyd - (double)ey);
+    const float2 e2x = make_float2(2.f * ex, 2.f * ex), e2y = make_float2(2.f * ey, 2.f * ey);
+    const float2 ee = make_float2(fmaf(ex, ex, ey * ey), fmaf(ex, ex, ey * ey));
+    const float2 ex2 = make_float2(ex, ex), ey2 = make_float2(ey, ey);
+    ff acc[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] = ff_zero();
+    for (int j0 = 0; j0 < np; j0 += chunk) {
+      const int j1 = min(j0 + chunk, np);
+      float2 c6[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) c6[v] = make_float2(0.f, 0.f);
+#pragma unroll 2
+      for (int j = j0; j < j1; ++j) anchor_pair_acc(ap[j], e2x, e2y, ee, ex2, ey2, c6);
+      const float kb = c6[2].x + c6[2].y;
+      ff_acc(acc[0], c6[0].x + c6[0].y);
+      ff_acc(acc[1], c6[1].x + c6[1].y);
+      ff_acc(acc[2], kb + (c6[3].x + c6[3].y));
+      ff_acc(acc[3], kb + (c6[5].x + c6[5].y));
+      ff_acc(acc[4], c6[4].x + c6[4].y);
+    }
+    // the offset e was rounded to FP32: first-order correction with these members' psi
+    ff_acc(acc[0], fmaf(acc[2].hi, exl, acc[4].hi * eyl));
+    ff_acc(acc[1], fmaf(acc[4].hi, exl, acc[3].hi * eyl));
+    acc[0] = ff_add(acc[0], sax);
+    acc[1] = ff_add(acc[1], say);
+    float pxh, pxl, pyh, pyl;
+    split_ff(x, pxh, pxl);
+    split_ff(y, pyh, pyl);
+    for (int c = 0; c < nc; ++c) {
+      const CompT<float>& C = dc[c];
+      if (C.kind == 0) continue;
+      ff ax, ay;
+      Out5<float> o;
+      eval_comp_ext(C, pxh, pxl, pyh, pyl, tab, ax, ay, o);
+      acc[0] = ff_add(acc[0], ax);
+      acc[1] = ff_add(acc[1], ay);
+      ff_acc(acc[2], o.pxx); ff_acc(acc[3], o.pyy); ff_acc(acc[4], o.pxy);
+    }
+    for (int w = 0; w < nw; ++w) {
+      uint32_t word = bits[w];
+      while (word) {
+        const int k = w * 32 + __ffs(word) - 1;
+        word &= word - 1u;
+        ff ax, ay;
+        Out5<float> o;
+        eval_member_x(dm[k], pxh, pxl, pyh, pyl, ax, ay, o);
+        acc[0] = ff_add(acc[0], ax);
+        acc[1] = ff_add(acc[1], ay);
+        ff_acc(acc[2], o.pxx); ff_acc(acc[3], o.pyy); ff_acc(acc[4], o.pxy);
+      }
+    }
+    if (valid)
+      write_out(O, pid, ff_to_double(acc[0]), ff_to_double(acc[1]), ff_to_double(acc[2]),
+                ff_to_double(acc[3]), ff_to_double(acc[4]));
+    __syncthreads();     // the next tile rewrites the records, the bits and the sums
+  }
+}
+
 // -------------------------------------------------------------------- LF_FP64 ------
 __global__ void __launch_bounds__(256) k_map_fp64(const lf_comp* __restrict__ comp, int nc,
                                                   const lf_member* __restrict__ mem, int nm,
@@ -197,6 +498,28 @@ static lf_status launch_mixed(const lf_plane* pl, const PosArgs& P, const OutArg
   return LF_OK;
 }
 
+template <bool GRID>
+static lf_status launch_anchor(const lf_plane* pl, const PosArgs& P, const OutArgs& O, int nsm,
+                               cudaStream_t s) {
+  const AnchorLayout L = anchor_layout(pl->n_comp, pl->n_mem);
+  if (L.total > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "plane too large for shared memory");
+  auto k = k_map_anchor<GRID>;
+  LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  int occ = 0;
+  LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 256, L.total));
+  long long tiles;
+  if (GRID) {
+    const long long ny = P.n / P.nx;
+    tiles = ((P.nx + LF_ATILE - 1) / LF_ATILE) * ((ny + LF_ATILE - 1) / LF_ATILE);
+  } else {
+    tiles = (P.n + 255) / 256;
+  }
+  const long long grid = std::min<long long>(tiles, (long long)nsm * std::max(occ, 1));
+  k<<<(unsigned)grid, 256, L.total, s>>>(pl->comp, pl->n_comp, pl->mem, pl->n_mem, pl->scaling, P, O,
+                                         LF_MAP_CHUNK);
+  return LF_OK;
+}
+
 static lf_status launch_map(const lf_plane* pl, const PosArgs& P, const OutArgs& O,
                             int precision, void* stream) {
   lf_status st = check_plane(pl);
@@ -210,11 +533,8 @@ static lf_status launch_map(const lf_plane* pl, const PosArgs& P, const OutArgs&
   LF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int block = 256;
   if (precision == LF_MIXED) {
-#if LF_MAP_PACK
-    LF_TRY((launch_mixed<LF_MAP_PPT, false, true>(pl, P, O, nsm, block, s)));
-#else
-    LF_TRY((launch_mixed<LF_MAP_PPT, false, false>(pl, P, O, nsm, block, s)));
-#endif
+    if (P.pts) LF_TRY(launch_anchor<false>(pl, P, O, nsm, s));
+    else LF_TRY(launch_anchor<true>(pl, P, O, nsm, s));
   } else if (precision == LF_FF) {
     LF_TRY((launch_mixed<1, true, false>(pl, P, O, nsm, block, s)));
   } else {

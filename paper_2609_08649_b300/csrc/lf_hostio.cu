@@ -15,10 +15,12 @@ static size_t hostio_slot_bytes(long long px) {
   return 3 * up((size_t)px * 8u) + 3 * up((size_t)px * 4u);
 }
 
-// Rows per band for `bands` requested bands of an ny-row grid (at least one row per band).
+// Rows per band for `bands` requested bands of an ny-row grid: a multiple of the mixed maps'
+// 16-row anchor tiles, so that every band's tiles (and anchors) are those of the whole grid.
 static int hostio_rows(int ny, int bands) {
   const int nb = std::min(bands, ny);
-  return (ny + nb - 1) / nb;
+  const int rows = (ny + nb - 1) / nb;
+  return std::min(ny, (rows + 15) / 16 * 16);
 }
 
 // One non-blocking copy stream per device, created on first use and kept for the process.

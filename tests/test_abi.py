@@ -87,7 +87,7 @@ def test_host_maps_workspace_and_validation():
     from paper_2609_08649_b300 import _lib as L
     up = lambda b: (b + 255) // 256 * 256
     g = L.lf_grid(0, 0, 0.1, 0.1, 100, 263)
-    for bands, rows in [(1, 263), (5, 53), (16, 17), (263, 1), (1000, 1)]:
+    for bands, rows in [(1, 263), (5, 64), (16, 32), (263, 16), (1000, 16)]:   # multiples of 16 rows
         px = 100 * rows
         assert L.lib.lf_jacobian_grid_host_workspace(C.byref(g), bands) == 2 * (3 * up(8 * px) + 3 * up(4 * px))
     assert L.lib.lf_jacobian_grid_host_workspace(C.byref(g), 0) == 0

@@ -3,11 +3,11 @@ with the FP64 oracle on the same seeded inputs, plus edge cases.
 
 Tolerances.  FP64 path: the same closed forms in FP64, so |d alpha| <= 1e-13 (1 + S_a)
 with S_a = sum_k |alpha_k| (rounding of a sum of K terms); kappa and gamma are stored as
-FP32, so they get half an FP32 ulp on top.  Mixed path: every component's closed form is
-evaluated in FP32 (relative rounding c u, u = 2^-24, c a few units per operation chain) on
-exact float-float offsets and summed in float-float, so |d alpha| <= 1e-6" + 4 u S_a; at
-galaxy scale the stated 1e-6" target is checked directly.  mu is compared where
-|det A| >= 1e-3, relative error bounded by the error of det A over |det A|."""
+FP32, so they get half an FP32 ulp on top.  Mixed path: the stated 1e-6" on alpha at every
+scale (each member's deflection at the tile's anchor in float-float, its change across the
+tile in FP32, the explicit components in float-float); psi_ij is FP32 per component, held to
+4 u sum_k |psi_k|.  mu is compared where |det A| >= 1e-3, relative error bounded by the error
+of det A over |det A|."""
 import math
 
 import numpy as np
@@ -46,8 +46,9 @@ def _check(lib, wl, grid, a, prec, alpha_tol=None, coef=4.0):
         # float-float deflection: ~2^-44 relative per component; psi_ij as in the mixed tier
         ta, tp = 1e-10 + 2.0 ** -40 * sa, coef * U32 * sp + 1e-9
     else:
-        ta = (alpha_tol if alpha_tol is not None else 1e-6) + coef * U32 * sa
-        tp = 1e-6 * 0 + coef * U32 * sp + 1e-9
+        ta = np.full_like(sa, alpha_tol if alpha_tol is not None else 1e-6)
+        tp = coef * U32 * sp + 1e-9
+    print(f"{prec}: max |d alpha| = {max(np.abs(g['ax'] - ax).max(), np.abs(g['ay'] - ay).max()):.3e}")
     assert np.all(np.abs(g["ax"] - ax) <= ta), np.abs(g["ax"] - ax).max()
     assert np.all(np.abs(g["ay"] - ay) <= ta), np.abs(g["ay"] - ay).max()
     k0, g10, g20 = 0.5 * (pxx + pyy), 0.5 * (pxx - pyy), pxy
@@ -72,13 +73,26 @@ def test_galaxy_grid_matches_oracle(lib, prec):
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "ff"])
 def test_cluster_ragged_grid_matches_oracle(lib, prec):
     """The cluster model (2 dPIE halos + 300 members) on a 211 x 157 grid that spans the
-    whole field, several pixel tiles and a ragged last tile.  The float-float tier meets
-    the stated 1e-6" on alpha at cluster scale."""
+    whole field, several pixel tiles and a ragged last tile: the stated 1e-6" on alpha at
+    cluster scale in the mixed and float-float tiers."""
     wl = W.cluster_c1()
     grid = W.Grid(-81.9, -80.0, 0.777, 1.03, 211, 157)
     g, (ax, ay) = _check(lib, wl, grid, cz.a_dis(0.5, 9.0), prec)
-    if prec == "ff":
+    if prec != "fp64":
         assert np.abs(g["ax"] - ax).max() < 1e-6 and np.abs(g["ay"] - ay).max() < 1e-6
+
+
+def test_cluster_fine_tiles_near_members(lib):
+    """The benchmark's pixel scale (0.04") on 96 x 80 pixel patches centred on the three
+    brightest members and on the main halo, where the members' deflections change fastest
+    across a tile: the mixed tier's alpha within the stated 1e-6"."""
+    wl = W.cluster_c1()
+    m = wl.planes[0].members
+    order = np.argsort(-m.log_l)[:3]
+    centres = [(float(m.x[k]), float(m.y[k])) for k in order] + [(0.0, 0.0)]
+    for cx, cy in centres:
+        grid = W.Grid(cx - 1.9, cy - 1.58, 0.04, 0.04, 96, 80)
+        _check(lib, wl, grid, cz.a_dis(0.5, 9.0), "mixed")
 
 
 def test_full_size_cluster_grid_sampled_pixels(lib):
@@ -96,8 +110,9 @@ def test_full_size_cluster_grid_sampled_pixels(lib):
     (ax, ay, pxx, pyy, pxy), sa, sp = oracle_plane_terms(OM.build_planes(wl)[0], x, y)
     gx = o["ax"].view(-1)[torch.tensor(idx, device="cuda")].cpu().numpy()
     gy = o["ay"].view(-1)[torch.tensor(idx, device="cuda")].cpu().numpy()
-    tol = 1e-6 + 4 * U32 * sa
-    assert np.all(np.abs(gx - ax) <= tol) and np.all(np.abs(gy - ay) <= tol)
+    err = max(np.abs(gx - ax).max(), np.abs(gy - ay).max())
+    print(f"4096^2 mixed, 3003 sampled pixels: max |d alpha| = {err:.3e}")
+    assert err <= 1e-6
     api.device_error()
 
 
@@ -114,7 +129,7 @@ def test_points_equal_grid(lib, prec):
     a = 0.6
     og = api.jacobian_grid(dp, grid, a, prec)
     op = api.jacobian_points(dp, pts, a, prec)
-    tol = {"fp64": 1e-11, "mixed": 5e-5, "ff": 1e-9}[prec]
+    tol = {"fp64": 1e-11, "mixed": 1e-6, "ff": 1e-9}[prec]
     for k in ("ax", "ay"):
         assert torch.allclose(og[k].reshape(-1), op[k], rtol=0, atol=tol), k
     for k in ("kappa", "g1", "g2"):
@@ -153,7 +168,7 @@ def test_edge_cases(lib):
     for prec in ("fp64", "mixed", "ff"):
         o = api.jacobian_grid(dp, grid, 0.5, prec)
         d = np.abs(o["ax"].cpu().numpy().ravel() - ax)
-        assert np.all(d <= 1e-6 + 4 * U32 * sa)
+        assert np.all(d <= (1e-6 if prec != "fp64" else 1e-13 * (1 + sa)))
     # zero positions
     o = api.jacobian_points(dp, torch.zeros(0, 2, dtype=torch.float64, device="cuda"), 0.5, "mixed")
     assert o["ax"].numel() == 0
@@ -181,12 +196,12 @@ def test_invalid_component_is_skipped_and_reported(lib):
 def test_round_and_nfw_components(lib, prec):
     """Spherical NFW halos (one pixel 1 mas from a centre, others across r = r_s and out to
     20 r_s), a round cored isothermal and two round pseudo-Jaffe components, with a shear.  The
-    float-float tier evaluates their deflections in float-float (bound 1e-10 + 2^-40 S_a, as
-    for the other components); the mixed tier in FP32.  The FP32 NFW is held to 16 u S
-    instead of 4 u S: beside the series band around r = r_s (|1 - x^2| < 0.5) its closed forms
-    cancel, (F - 1)/(1 - x^2) by up to 7.7x and h = ln(x/2) + atan(w)/w by 2.3x, on top of the
-    few-ulp error of the FP32 log and atan (measured: 1.8e-5" on |alpha| = 51", 1.3e-6 in
-    kappa)."""
+    mixed and float-float maps evaluate their deflections in float-float (mixed: the stated
+    1e-6"; float-float: 1e-10 + 2^-40 S_a, as for the other components).  Their psi_ij are FP32,
+    and the FP32 NFW is held to 16 u S instead of 4 u S: beside the series band around r = r_s
+    (|1 - x^2| < 0.5) its closed forms cancel, (F - 1)/(1 - x^2) by up to 7.7x and
+    h = ln(x/2) + atan(w)/w by 2.3x, on top of the few-ulp error of the FP32 log and atan
+    (measured 1.3e-6 in kappa)."""
     rng = np.random.default_rng(17)
     comps = [W.PhysComp(W.NFW, 0.001, -0.002, m200=8e14, conc=5.0),
              W.PhysComp(W.NFW, 31.0, 18.0, m200=2e14, conc=7.0),
