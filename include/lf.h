@@ -386,8 +386,11 @@ lf_status lf_plan_destroy(lf_plan* plan);
 
 /* lf_chi2_batch for one cluster with no device allocation (the paper has no counterpart;
  * it exists for callers that cannot call cudaMalloc: a process whose GPU memory is already
- * reserved by another framework's caching allocator, a sampler step that must not
- * synchronise the device, or a plug-in host that forbids device allocation).
+ * reserved by another framework's caching allocator, or a plug-in host that forbids device
+ * allocation).  The call uploads its host-side tables with cudaMemcpyAsync from pageable
+ * memory, which waits for the stream's earlier work (the host returns once the stream has
+ * drained up to the call), and it cannot be captured into a CUDA graph: on a capturing
+ * stream it returns LF_EUNSUPPORTED before any work.
  * Arguments are those of one lf_cluster (host arrays read during the call; comp / mem device
  * arrays read on `stream`), theta device [S * P], chi2 device [S], all samples belonging to
  * that cluster.  Every derived table lives in one fixed 1 MiB array of device memory inside
@@ -421,6 +424,54 @@ double lf_b_from_vdisp(double v_kms);
  * (200 x the critical density at z_l; Sigma_cr at a_dis = 1). */
 lf_status lf_nfw_params(double H0, double Om, double z_l, double m200, double conc,
                         double* kappa_s, double* theta_s);
+
+/* One explicit component in physical units, for lf_comp_from_physical.  A field that is
+ * not given holds NaN. */
+typedef struct {
+  int32_t kind;              /* lf_kind */
+  int32_t pad;
+  double x, y;               /* centre, arcsec */
+  double vdisp;              /* isothermal: velocity dispersion, km/s */
+  double theta_e, z_ref;     /* isothermal (instead of vdisp): area-equivalent Einstein radius
+                                in arcsec at source redshift z_ref; shear: z_ref at which gamma
+                                is quoted */
+  double eps, pa_deg;        /* ellipticity (1-q)/(1+q); position angle in degrees */
+  double core_kpc, core_arcsec, cut_kpc;   /* isothermal core (either unit), dPIE cut */
+  double m200, conc;         /* NFW / elliptical NFW: M200 [Msun] (200 x rho_crit(z_l)), c */
+  double kappa_s, theta_s;   /* NFW / elliptical NFW given in lensing units instead */
+  double gamma;              /* shear */
+  double amp;                /* multipole amplitude A of psi = A theta^2 cos 3(phi - pa) */
+} lf_phys_comp;
+
+/* Physical description -> lensing-unit component at a_dis = 1 (the unit conversions of the
+ * A1 set-up, Sec. 3.4-3.5): b = 4 pi (v/c)^2 from vdisp, or b = theta_E / (a sqrt(q)) with
+ * q = (1 - eps)/(1 + eps) and a = a_dis(z_l, z_ref); kpc -> arcsec at z_l; NFW through
+ * lf_nfw_params; a shear quoted at z_ref divided by a_dis(z_l, z_ref); degrees -> radians.
+ * Host only.  Errors: LF_EINVAL for a missing or invalid field. */
+lf_status lf_comp_from_physical(const lf_phys_comp* in, double H0, double Om, double z_l,
+                                lf_comp* out);
+
+/* Eq. scaling from physical units: b_star = 4 pi (v_star / c)^2, core_star and cut_star from kpc to arcsec at
+ * z_l; the exponents are copied.  Host only.  Errors: LF_EINVAL. */
+lf_status lf_scaling_from_physical(double vstar_kms, double core_star_kpc, double cut_star_kpc,
+                                   double lam, double beta, double alpha, double H0, double Om,
+                                   double z_l, lf_scaling* out);
+
+/* The distance-ratio table of the Sec. 2.2 recursion for planes at increasing redshifts
+ * z_planes[0..n-1] and a source at z_s: ratios[i * n + j] = D_ij / D_j for i < j (0 else),
+ * and the last row ratios[n * n + j] = D_js / D_s (0 for a plane behind the source); the
+ * (n + 1) x n row-major layout that lf_trace_multiplane takes.  Host only.  Errors: LF_EINVAL
+ * (n outside 1..8, redshifts not positive and increasing, NULL pointers). */
+lf_status lf_multiplane_ratios(double H0, double Om, const double* z_planes, int32_t n_planes,
+                               double z_s, double* ratios);
+
+/* Failure-detection self-test (the paper has no counterpart): a one-block kernel arms a
+ * shared-memory mbarrier for 16 bytes of bulk-copy transactions, issues no copy, and waits
+ * with the library's bounded wait limited to `polls` polls (1..65536).  The wait runs out,
+ * the kernel records the timeout in the device error word and returns, so the next
+ * lf_device_error(stream) reports LF_ETIMEOUT (and clears the word).  No copy is ever in
+ * flight and no thread spins past the limit.  Errors: LF_EINVAL for polls outside the range. */
+lf_status lf_selftest_wait_timeout(uint32_t polls, void* stream);
 
 /* Measured arithmetic rates of the current GPU (the roofline denominators of the
  * lens-equation kernels): FP32 fused multiply-adds, MUFU reciprocal square roots and FP64

@@ -17,6 +17,7 @@ from . import profiles as pr
 from . import cse_nfw
 
 SIE, DPIE, NFW, SHEAR, MPOLE3, ENFW = 1, 2, 3, 4, 5, 6
+SHEET = 101   # oracle-only test profile: a uniform mass sheet of convergence b
 C_KMS = 299792.458
 ARCSEC_PER_RAD = 180.0 / math.pi * 3600.0
 
@@ -79,6 +80,8 @@ def component(kind, dx, dy, b, eps, pa, core, cut):
         return pr.multipole3(dx, dy, b, pa)
     if kind == ENFW:     # b = kappa_s, core = r_s
         return pr.enfw(dx, dy, b, q_from_eps(eps), pa, core, *cse_nfw.table())
+    if kind == SHEET:
+        return pr.mass_sheet(dx, dy, b)
     raise ValueError(f"unknown component kind {kind}")
 
 
@@ -95,6 +98,8 @@ def component_potential(kind, dx, dy, b, eps, pa, core, cut):
         return pr.multipole3_potential(dx, dy, b, pa)
     if kind == ENFW:
         return pr.enfw_potential(dx, dy, b, q_from_eps(eps), pa, core, *cse_nfw.table())
+    if kind == SHEET:
+        return pr.mass_sheet_potential(dx, dy, b)
     raise ValueError(f"unknown component kind {kind}")
 
 

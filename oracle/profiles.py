@@ -222,6 +222,13 @@ def shear(dx, dy, gamma, pa):
     return g1 * dx + g2 * dy, g2 * dx - g1 * dy, g1, -g1, g2
 
 
+def mass_sheet(dx, dy, k0):
+    """A uniform sheet of convergence k0 (oracle-only test profile): psi = k0 r^2 / 2, so
+    alpha = k0 (dx, dy), psi_xx = psi_yy = k0, psi_xy = 0."""
+    dx, dy, k0 = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64) for t in (dx, dy, k0)])
+    return k0 * dx, k0 * dy, k0.clone(), k0.clone(), torch.zeros_like(k0)
+
+
 def multipole3(dx, dy, amp, pa):
     """Third-order multipole whose potential grows as theta^2 (Sec. 4.2):
     psi = amp r^2 cos 3(phi - pa), phi the polar angle of (dx, dy).  From the polar
@@ -334,6 +341,12 @@ def shear_potential(dx, dy, gamma, pa):
                                                   for t in (dx, dy, gamma, pa)])
     g1, g2 = gamma * torch.cos(2.0 * pa), gamma * torch.sin(2.0 * pa)
     return 0.5 * g1 * (dx * dx - dy * dy) + g2 * dx * dy
+
+
+def mass_sheet_potential(dx, dy, k0):
+    """psi = k0 r^2 / 2."""
+    dx, dy, k0 = torch.broadcast_tensors(*[torch.as_tensor(t, dtype=torch.float64) for t in (dx, dy, k0)])
+    return 0.5 * k0 * (dx * dx + dy * dy)
 
 
 def multipole3_potential(dx, dy, amp, pa):

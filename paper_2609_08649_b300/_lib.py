@@ -36,6 +36,15 @@ class lf_plane(C.Structure):
                 ("mem", C.c_void_p), ("scaling", lf_scaling)]
 
 
+class lf_phys_comp(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("x", C.c_double), ("y", C.c_double),
+                ("vdisp", C.c_double), ("theta_e", C.c_double), ("z_ref", C.c_double),
+                ("eps", C.c_double), ("pa_deg", C.c_double), ("core_kpc", C.c_double),
+                ("core_arcsec", C.c_double), ("cut_kpc", C.c_double), ("m200", C.c_double),
+                ("conc", C.c_double), ("kappa_s", C.c_double), ("theta_s", C.c_double),
+                ("gamma", C.c_double), ("amp", C.c_double)]
+
+
 class lf_grid(C.Structure):
     _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("dx", C.c_double), ("dy", C.c_double),
                 ("nx", C.c_int32), ("ny", C.c_int32)]
@@ -83,9 +92,13 @@ def _load():
         "lf_mh_run": [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp],
         "lf_nm_run": [vp, vp, vp, i32, i32, vp, vp, vp, vp],
         "lf_probe_alu": [vp, vp, vp, vp],
+        "lf_selftest_wait_timeout": [C.c_uint32, vp],
         "lf_chi2_batch_static": [vp, vp, i32, i32, vp, vp],
         "lf_plan_info": [vp, vp, vp, vp],
         "lf_nfw_params": [f64, f64, f64, f64, f64, vp, vp],
+        "lf_comp_from_physical": [vp, f64, f64, f64, vp],
+        "lf_scaling_from_physical": [f64] * 9 + [vp],
+        "lf_multiplane_ratios": [f64, f64, vp, i32, f64, vp],
         "lf_device_error": [vp],
         "lf_find_images": [vp, vp, i32, vp, vp, i32, i32, i32, vp, C.c_size_t, vp, vp, vp],
         "lf_find_images_multiplane": [vp, i32, vp, vp, i32, vp, i32, i32, i32, vp, C.c_size_t, vp, vp, vp],
@@ -121,7 +134,8 @@ EXPORTS = ["lf_deflect_grid", "lf_jacobian_grid", "lf_jacobian_grid_host", "lf_j
            "lf_find_images_multiplane_workspace",
            "lf_chi2_batch_static",
            "lf_plan_info", "lf_angular_distance", "lf_adis", "lf_arcsec_per_kpc",
-           "lf_b_from_vdisp", "lf_td_scale", "lf_nfw_params", "lf_device_error", "lf_probe_alu", "lf_last_error", "lf_version"]
+           "lf_b_from_vdisp", "lf_td_scale", "lf_nfw_params", "lf_comp_from_physical", "lf_scaling_from_physical",
+           "lf_multiplane_ratios", "lf_device_error", "lf_selftest_wait_timeout", "lf_probe_alu", "lf_last_error", "lf_version"]
 
 
 def check(status):

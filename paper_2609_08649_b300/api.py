@@ -345,10 +345,15 @@ class Plan:
 
 
 class Chi2Function(torch.autograd.Function):
-    """chi^2 per sample with d chi^2 / d theta from the library's adjoint kernel."""
+    """chi^2 per sample with d chi^2 / d theta from the library's adjoint kernel.  The adjoint
+    runs in forward (with the chi^2) only when theta needs a gradient; otherwise forward is one
+    lf_chi2_batch call."""
 
     @staticmethod
     def forward(ctx, theta, plan):
+        if not ctx.needs_input_grad[0]:
+            ctx.save_for_backward(None)
+            return plan.chi2(theta.detach())
         chi2, grad = plan.chi2_grad(theta.detach())
         ctx.save_for_backward(grad)
         return chi2

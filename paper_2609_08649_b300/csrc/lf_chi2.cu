@@ -1341,6 +1341,11 @@ struct lf_plan {
   const void* g_theta = nullptr;
   void* g_out = nullptr;
   int g_S = -1;
+  // LF_MIXED plans: the LF_FF plan over the same clusters that serves lf_chi2_grad_batch.
+  // The cotangents of the adjoint are weighted by the offsets d_i = beta_i - beta_model,
+  // which are only ~sigma_pos: FP32 member deflections (a few 1e-6 arcsec) would put ~1e-4
+  // relative errors on them, so the gradient evaluates the deflections in float-float.
+  lf_plan* grad_ff = nullptr;
 };
 
 namespace lf {
@@ -1541,7 +1546,7 @@ static lf_status relayout(lf_plan* pl) {
   const void* kc = pl->precision == LF_MIXED ? (const void*)k_chi2<LF_MIXED, false>
                    : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, false>
                                              : (const void*)k_chi2<LF_FP64, false>;
-  const void* kg = pl->precision == LF_MIXED ? (const void*)k_chi2<LF_MIXED, true>
+  const void* kg = pl->precision == LF_MIXED ? nullptr     // gradient on the plan's LF_FF companion
                    : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, true>
                                              : (const void*)k_chi2<LF_FP64, true>;
   const void* ki = pl->precision == LF_MIXED ? (const void*)k_chi2<LF_MIXED, false, 1>
@@ -1565,7 +1570,7 @@ static lf_status relayout(lf_plan* pl) {
   LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kc, pl->block, pl->smem));
   pl->grid_chi2 = nsm * std::max(occ, 1);
   pl->grid_grad = 0;
-  if (pl->smem_grad > 0) {
+  if (pl->smem_grad > 0 && kg) {
     LF_TRY(kset(kg, pl->smem_grad));
     LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kg, pl->block, pl->smem_grad));
     pl->grid_grad = nsm * std::max(occ, 1);
@@ -1730,10 +1735,12 @@ static void launch_mode(lf_plan* pl, const double* theta, int S, double* chi2, d
     k_chi2_prep<MODE><<<(nprep + 63) / 64, 64, 0, st>>>(pl->d_desc, spc, S, pl->nfree_max, theta,
                                                         pl->d_free_dig, pl->d_free_raw);
   if (grad) {
-    int g = std::min(pl->grid_grad, S);
-    k_chi2<MODE, true><<<g, pl->block, pl->smem_grad, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
-                                                       grad, pl->d_counter, g_member_chunk,
-                                                       pl->d_free_dig, pl->d_free_raw);
+    if constexpr (MODE != LF_MIXED) {   // a mixed plan's gradient runs on its LF_FF plan
+      int g = std::min(pl->grid_grad, S);
+      k_chi2<MODE, true><<<g, pl->block, pl->smem_grad, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
+                                                         grad, pl->d_counter, g_member_chunk,
+                                                         pl->d_free_dig, pl->d_free_raw);
+    }
   } else if (pl->has_aux) {
     int g = std::min(pl->grid_aux, S);
     k_chi2<MODE, false, 2><<<g, pl->block, pl->smem_aux, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
@@ -1877,6 +1884,7 @@ static lf_status run(lf_plan* pl, const double* theta, int S, double* chi2, doub
 
 extern "C" lf_status lf_plan_destroy(lf_plan* pl) {
   if (!pl) return LF_OK;
+  if (pl->grad_ff) lf_plan_destroy(pl->grad_ff);
   if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
   if (pl->ev_in) cudaEventDestroy(pl->ev_in);
   if (pl->ev_out) cudaEventDestroy(pl->ev_out);
@@ -1941,6 +1949,8 @@ extern "C" lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, i
         st = fail(LF_ECUDA, "stream / event creation failed");
     }
   }
+  if (st == LF_OK && precision == LF_MIXED)
+    st = lf_plan_create(&pl->grad_ff, clusters, n_clusters, max_samples, LF_FF, flags);
   if (st != LF_OK) {
     lf_plan_destroy(pl);
     return st;
@@ -1958,6 +1968,7 @@ extern "C" lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int3
                                         double* grad, void* stream) {
   if (!plan) return fail(LF_EINVAL, "plan is NULL");
   if (!grad) return fail(LF_EINVAL, "grad is NULL");
+  if (plan->grad_ff) plan = plan->grad_ff;
   if (plan->smem_grad == 0)
     return fail(LF_EUNSUPPORTED, "the multi-plane adjoint's per-image records do not fit in shared memory");
   if (plan->has_aux) return fail(LF_EUNSUPPORTED, "no gradient of the flux and time-delay terms");

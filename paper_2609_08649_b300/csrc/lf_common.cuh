@@ -1114,10 +1114,11 @@ LF_INLINE void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* ba
       : "memory");
 }
 
-// Returns true when the phase with the given parity has completed.
-LF_INLINE bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Returns true when the phase with the given parity has completed, false once `limit` polls
+// have found it still pending.
+LF_INLINE bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = LF_WAIT_LIMIT) {
   uint32_t done = 0;
-  for (uint32_t it = 0; it < LF_WAIT_LIMIT; ++it) {
+  for (uint32_t it = 0; it < limit; ++it) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"

@@ -2,13 +2,14 @@
 //
 // Persistent kernels: one block per SM slot stages the component and member tables
 // into shared memory once with the bulk-copy engine, digests them (member scaling
-// relations of Eq. scaling, trigonometry, float-float centres), then walks pixel tiles
-// with a grid stride.  Every thread owns PPT positions so that each component read from
-// shared memory (a broadcast) is reused PPT times.
+// relations of Eq. scaling, trigonometry, float-float centres), then walks tiles of
+// positions with a grid stride.
 //
-//  LF_MIXED: per-component closed forms in FP32 on float-float offsets; per-chunk FP32 sums
-//            folded into float-float accumulators every `chunk` members; FP64 det A and mu.
-//  LF_FP64:  the same loop in FP64 throughout, one position per thread.
+//  LF_MIXED: tiles of 16 x 16 pixels (or 256 points) anchored at their centre: each member's
+//            deflection there in float-float and its change across the tile in FP32 (below);
+//            FP64 det A and mu.
+//  LF_FF:    every deflection in float-float at every position, psi_ij in FP32.
+//  LF_FP64:  the same closed forms in FP64 throughout, one position per thread.
 #include "lf_internal.h"
 #include "lf_eval.cuh"
 
@@ -55,81 +56,48 @@ __device__ __forceinline__ void write_out(const OutArgs& O, long long p, double 
   }
 }
 
-// ------------------------------------------------------------------- LF_MIXED ------
+// --------------------------------------------------------------------- LF_FF -------
 #ifndef LF_MAP_MINB
-#define LF_MAP_MINB 3   // scalar and float-float variants: at most 85 registers, 3 blocks of 256
-#endif
-#ifndef LF_MAP_MINB_PACK
-#define LF_MAP_MINB_PACK 4   // packed variant: 64 registers, 4 blocks of 256 per SM
-#endif
-#ifndef LF_MAP_PACK
-#define LF_MAP_PACK 1   // members in packed pairs (f32x2)
-#endif
-#ifndef LF_MAP_PPT
-#define LF_MAP_PPT 1
+#define LF_MAP_MINB 3   // at most 85 registers, 3 blocks of 256
 #endif
 #ifndef LF_MAP_CHUNK
-#define LF_MAP_CHUNK 16   // packed variant: member pairs per FP32 partial sum (16 terms per lane)
+#define LF_MAP_CHUNK 16   // anchored maps: member pairs per FP32 partial sum (16 terms per lane)
 #endif
-// Member record of each variant: float-float (EXT), packed pairs (PACK), or scalar.
-template <bool EXT, bool PACK>
-using MapMem = typename std::conditional<EXT, MemX,
-                                         typename std::conditional<PACK, MemPair, MemT<float>>::type>::type;
 
-template <int PPT, bool EXT, bool PACK>
-__global__ void __launch_bounds__(256, PACK ? LF_MAP_MINB_PACK : LF_MAP_MINB) k_map_mixed(const lf_comp* __restrict__ comp, int nc,
-                                                   const lf_member* __restrict__ mem, int nm,
-                                                   lf_scaling sc, PosArgs P, OutArgs O, int chunk) {
+// The float-float tier's maps: every component's deflection in float-float at every position.
+__global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_ff(const lf_comp* __restrict__ comp, int nc,
+                                                             const lf_member* __restrict__ mem, int nm,
+                                                             lf_scaling sc, PosArgs P, OutArgs O) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  typedef MapMem<EXT, PACK> Mem;
-  const PlaneLayout L = plane_layout<float, Mem>(nc, nm, LF_MAP_BASE);
+  const PlaneLayout L = plane_layout<float, MemX>(nc, nm, LF_MAP_BASE);
   lf_comp* rawc = reinterpret_cast<lf_comp*>(smem + L.rawc);
   lf_member* rawm = reinterpret_cast<lf_member*>(smem + L.rawm);
   CompT<float>* dc = reinterpret_cast<CompT<float>*>(smem + L.dc);
-  Mem* dm = reinterpret_cast<Mem*>(smem + L.dm);
+  MemX* dm = reinterpret_cast<MemX*>(smem + L.dm);
   float2* tab = reinterpret_cast<float2*>(smem + 16);
   if (threadIdx.x == 0) mbar_init(bar, 1);
   init_ff_tables(tab);
   __syncthreads();
-  bool ok = stage_to_smem(rawc, comp, (uint32_t)nc * 64u + 0u, bar, 0);
+  bool ok = stage_to_smem(rawc, comp, (uint32_t)nc * 64u, bar, 0);
   if (ok) ok = stage_to_smem(rawm, mem, (uint32_t)nm * 32u, bar, nc > 0 ? 1 : 0);
   if (!ok) return;
-  if constexpr (EXT) digest_plane_x(rawc, nc, rawm, nm, sc, dc, dm);
-  else if constexpr (PACK) digest_plane_pairs(rawc, nc, rawm, nm, sc, dc, dm);
-  else digest_plane<float>(rawc, nc, rawm, nm, sc, dc, dm);
+  digest_plane_x(rawc, nc, rawm, nm, sc, dc, dm);
   __syncthreads();
 
-  const long long per_tile = (long long)PPT * blockDim.x;
-  const long long n_tiles = (P.n + per_tile - 1) / per_tile;
-  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    float pxh[PPT], pxl[PPT], pyh[PPT], pyl[PPT];
-    long long pid[PPT];
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P.n;
+       p += (long long)gridDim.x * blockDim.x) {
+    float pxh[1], pxl[1], pyh[1], pyl[1];
+    double x, y;
+    position_of(P, p, x, y);
+    split_ff(x, pxh[0], pxl[0]);
+    split_ff(y, pyh[0], pyl[0]);
+    ff acc[5][1];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      pid[k] = tile * per_tile + threadIdx.x + (long long)k * blockDim.x;
-      double x, y;
-      position_of(P, pid[k] < P.n ? pid[k] : 0, x, y);
-      split_ff(x, pxh[k], pxl[k]);
-      split_ff(y, pyh[k], pyl[k]);
-    }
-    ff acc[5][PPT];
-#pragma unroll
-    for (int v = 0; v < 5; ++v)
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) acc[v][k] = ff_zero();
-
-    if constexpr (EXT) accumulate_ext<PPT>(dc, nc, dm, nm, 0, nc + nm, pxh, pxl, pyh, pyl, tab, acc);
-    else if constexpr (PACK)
-      accumulate_packed<PPT>(dc, nc, dm, nm, 0, nc + (int)mem_records<MemPair>(nm), chunk, pxh, pxl,
-                             pyh, pyl, tab, acc);
-    else accumulate_mixed<PPT>(dc, nc, dm, nm, 0, nc + nm, chunk, pxh, pxl, pyh, pyl, tab, acc);
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      if (pid[k] < P.n)
-        write_out(O, pid[k], ff_to_double(acc[0][k]), ff_to_double(acc[1][k]),
-                  ff_to_double(acc[2][k]), ff_to_double(acc[3][k]), ff_to_double(acc[4][k]));
-    }
+    for (int v = 0; v < 5; ++v) acc[v][0] = ff_zero();
+    accumulate_ext<1>(dc, nc, dm, nm, 0, nc + nm, pxh, pxl, pyh, pyl, tab, acc);
+    write_out(O, p, ff_to_double(acc[0][0]), ff_to_double(acc[1][0]), ff_to_double(acc[2][0]),
+              ff_to_double(acc[3][0]), ff_to_double(acc[4][0]));
   }
 }
 
@@ -481,20 +449,15 @@ lf_status check_plane(const lf_plane* pl) {
   return LF_OK;
 }
 
-template <int PPT, bool EXT, bool PACK>
-static lf_status launch_mixed(const lf_plane* pl, const PosArgs& P, const OutArgs& O, int nsm,
-                              int block, cudaStream_t s) {
-  typedef MapMem<EXT, PACK> Mem;
-  PlaneLayout L = plane_layout<float, Mem>(pl->n_comp, pl->n_mem, LF_MAP_BASE);
+static lf_status launch_ff(const lf_plane* pl, const PosArgs& P, const OutArgs& O, int nsm, cudaStream_t s) {
+  PlaneLayout L = plane_layout<float, MemX>(pl->n_comp, pl->n_mem, LF_MAP_BASE);
   if (L.total > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "plane too large for shared memory");
-  auto k = k_map_mixed<PPT, EXT, PACK>;
-  LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  LF_CUDA(cudaFuncSetAttribute(k_map_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
   int occ = 0;
-  LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, L.total));
-  long long tiles = (P.n + (long long)PPT * block - 1) / ((long long)PPT * block);
-  long long grid = std::min<long long>(tiles, (long long)nsm * std::max(occ, 1));
-  k<<<(unsigned)grid, block, L.total, s>>>(pl->comp, pl->n_comp, pl->mem, pl->n_mem, pl->scaling, P, O,
-                                           PACK ? LF_MAP_CHUNK : g_member_chunk);
+  LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_map_ff, 256, L.total));
+  const long long tiles = (P.n + 255) / 256;
+  const long long grid = std::min<long long>(tiles, (long long)nsm * std::max(occ, 1));
+  k_map_ff<<<(unsigned)grid, 256, L.total, s>>>(pl->comp, pl->n_comp, pl->mem, pl->n_mem, pl->scaling, P, O);
   return LF_OK;
 }
 
@@ -536,7 +499,7 @@ static lf_status launch_map(const lf_plane* pl, const PosArgs& P, const OutArgs&
     if (P.pts) LF_TRY(launch_anchor<false>(pl, P, O, nsm, s));
     else LF_TRY(launch_anchor<true>(pl, P, O, nsm, s));
   } else if (precision == LF_FF) {
-    LF_TRY((launch_mixed<1, true, false>(pl, P, O, nsm, block, s)));
+    LF_TRY(launch_ff(pl, P, O, nsm, s));
   } else {
     PlaneLayout L = plane_layout<double>(pl->n_comp, pl->n_mem, 16);
     if (L.total > LF_SMEM_MAX) return fail(LF_EUNSUPPORTED, "plane too large for shared memory");

@@ -121,6 +121,111 @@ extern "C" lf_status lf_nfw_params(double H0, double Om, double z_l, double m200
   return LF_OK;
 }
 
+extern "C" lf_status lf_comp_from_physical(const lf_phys_comp* in, double H0, double Om, double z_l,
+                                           lf_comp* out) {
+  if (!in || !out) return fail(LF_EINVAL, "NULL argument");
+  auto given = [](double v) { return !std::isnan(v); };
+  lf_comp c;
+  memset(&c, 0, sizeof c);
+  c.kind = in->kind;
+  c.x = in->x;
+  c.y = in->y;
+  c.pa = in->pa_deg * (M_PI / 180.0);
+  switch (in->kind) {
+    case LF_SIE:
+    case LF_DPIE: {
+      if (!(in->eps >= 0.0 && in->eps < 1.0)) return fail(LF_EINVAL, "eps must be in [0, 1)");
+      const double q = (1.0 - in->eps) / (1.0 + in->eps);
+      if (given(in->vdisp)) {
+        c.b = lf_b_from_vdisp(in->vdisp);
+      } else if (given(in->theta_e) && given(in->z_ref)) {
+        // the area-equivalent Einstein radius at z_ref: theta_E = a_dis b sqrt(q)
+        const double a = lf_adis(H0, Om, z_l, in->z_ref);
+        if (!(a > 0.0)) return fail(LF_EINVAL, "z_ref must lie behind the lens");
+        c.b = in->theta_e / (std::sqrt(q) * a);
+      } else {
+        return fail(LF_EINVAL, "an isothermal component needs vdisp or (theta_e, z_ref)");
+      }
+      const double apk = lf_arcsec_per_kpc(H0, Om, z_l);
+      if (given(in->core_arcsec)) c.core = in->core_arcsec;
+      else if (given(in->core_kpc)) c.core = in->core_kpc * apk;
+      else return fail(LF_EINVAL, "an isothermal component needs a core radius");
+      c.cut = given(in->cut_kpc) ? in->cut_kpc * apk : 0.0;
+      c.eps = in->eps;
+      break;
+    }
+    case LF_NFW:
+    case LF_ENFW: {
+      if (given(in->kappa_s) && given(in->theta_s)) {
+        c.b = in->kappa_s;
+        c.core = in->theta_s;
+      } else {
+        LF_TRY(lf_nfw_params(H0, Om, z_l, in->m200, in->conc, &c.b, &c.core));
+      }
+      if (in->kind == LF_NFW) {
+        c.pa = 0.0;
+      } else {
+        if (!(in->eps >= 0.0 && in->eps < 1.0)) return fail(LF_EINVAL, "eps must be in [0, 1)");
+        c.eps = in->eps;
+      }
+      break;
+    }
+    case LF_SHEAR: {
+      // a shear quoted at source redshift z_ref carries that a_dis; the tables hold a_dis = 1
+      c.b = in->gamma;
+      if (given(in->z_ref)) {
+        const double a = lf_adis(H0, Om, z_l, in->z_ref);
+        if (!(a > 0.0)) return fail(LF_EINVAL, "z_ref must lie behind the lens");
+        c.b /= a;
+      }
+      break;
+    }
+    case LF_MULTIPOLE3:
+      c.b = in->amp;
+      break;
+    default:
+      return fail(LF_EINVAL, "unknown component kind %d", in->kind);
+  }
+  *out = c;
+  return LF_OK;
+}
+
+extern "C" lf_status lf_scaling_from_physical(double vstar_kms, double core_star_kpc, double cut_star_kpc,
+                                              double lam, double beta, double alpha, double H0, double Om,
+                                              double z_l, lf_scaling* out) {
+  if (!out) return fail(LF_EINVAL, "NULL output");
+  if (!(vstar_kms >= 0 && core_star_kpc >= 0 && cut_star_kpc > 0 && z_l > 0))
+    return fail(LF_EINVAL, "need v* >= 0, core* >= 0, cut* > 0 and z_l > 0");
+  const double apk = lf_arcsec_per_kpc(H0, Om, z_l);
+  out->b_star = lf_b_from_vdisp(vstar_kms);
+  out->core_star = core_star_kpc * apk;
+  out->cut_star = cut_star_kpc * apk;
+  out->lam = lam;
+  out->beta = beta;
+  out->alpha = alpha;
+  return LF_OK;
+}
+
+extern "C" lf_status lf_multiplane_ratios(double H0, double Om, const double* z_planes, int32_t n_planes,
+                                          double z_s, double* ratios) {
+  if (!z_planes || !ratios || n_planes < 1 || n_planes > LF_MAX_PLANES)
+    return fail(LF_EINVAL, "need 1..%d plane redshifts and an output table", LF_MAX_PLANES);
+  for (int j = 0; j < n_planes; ++j) {
+    if (!(z_planes[j] > 0.0) || (j > 0 && !(z_planes[j] > z_planes[j - 1])))
+      return fail(LF_EINVAL, "plane redshifts must be positive and increasing");
+  }
+  const int n = n_planes;
+  for (int j = 0; j < n; ++j) {
+    const double dj = lf_angular_distance(H0, Om, 0.0, z_planes[j]);
+    for (int i = 0; i < n; ++i)
+      ratios[i * n + j] = i < j ? lf_angular_distance(H0, Om, z_planes[i], z_planes[j]) / dj : 0.0;
+  }
+  const double ds = lf_angular_distance(H0, Om, 0.0, z_s);
+  for (int j = 0; j < n; ++j)
+    ratios[n * n + j] = z_s > z_planes[j] ? lf_angular_distance(H0, Om, z_planes[j], z_s) / ds : 0.0;
+  return LF_OK;
+}
+
 extern "C" lf_status lf_device_error(void* stream) {
   LF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   unsigned int v = 0, zero = 0;

@@ -45,9 +45,30 @@ __global__ void k_probe_dfma(double* out, double a, double b) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3;
 }
 
+// Failure-detection self-test: one thread arms an mbarrier for 16 bytes of bulk-copy
+// transactions and issues no copy, so the phase can never complete; the bounded wait gives
+// up after `polls` polls and records LF_DEVERR_TIMEOUT in the device error word, exactly as
+// a staging wait of the lens kernels does.  Nothing asynchronous is in flight when the block
+// exits.
+__global__ void k_selftest_wait_timeout(uint32_t polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, 16u);
+    if (!mbar_wait(&bar, 0u, polls)) lf_flag_error(LF_DEVERR_TIMEOUT);
+  }
+}
+
 }  // namespace lf
 
 using namespace lf;
+
+extern "C" lf_status lf_selftest_wait_timeout(uint32_t polls, void* stream) {
+  if (polls < 1 || polls > 65536) return fail(LF_EINVAL, "polls must be in 1..65536");
+  k_selftest_wait_timeout<<<1, 32, 0, (cudaStream_t)stream>>>(polls);
+  LF_CUDA(cudaGetLastError());
+  return LF_OK;
+}
 
 extern "C" lf_status lf_probe_alu(double* fp32_fma_per_s, double* mufu_rsqrt_per_s,
                                   double* fp64_fma_per_s, void* stream) {

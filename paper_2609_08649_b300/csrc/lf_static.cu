@@ -1,13 +1,19 @@
 // lf_chi2_batch_static: the batched source-plane chi^2 of one cluster without any device
 // allocation.
 //
-// Who needs it: callers that cannot call cudaMalloc.  Examples are a host whose GPU memory
-// is already reserved by another framework's caching allocator, a sampler step that must
-// not synchronise the device (cudaMalloc and cudaFree can), and plug-in environments that
-// forbid device allocation outright.  lf_plan_create allocates the plan's tables; this
-// entry point instead keeps every derived table (the cluster descriptor, the member
-// factors, the image arrays, the work counter) in one fixed array of device memory that
-// is part of the library image.  The caller still provides the inputs and the output.
+// Who needs it: callers that cannot call cudaMalloc.  Examples are a process whose GPU
+// memory is already reserved by another framework's caching allocator, and plug-in
+// environments that forbid device allocation outright.  lf_plan_create allocates the plan's
+// tables; this entry point instead keeps every derived table (the cluster descriptor, the
+// member factors, the image arrays, the work counter) in one fixed array of device memory
+// that is part of the library image.  The caller still provides the inputs and the output.
+//
+// The call uploads its host-side tables (the descriptor, the member-array pointers and the
+// image arrays, read from the caller's host memory and this function's stack) with
+// cudaMemcpyAsync from pageable memory.  Such a copy first waits for the stream's earlier
+// work, so the call returns to the host only once the stream has drained up to it.  It
+// cannot be captured into a CUDA graph either (the copies would record host addresses that
+// are gone at replay): a call on a capturing stream returns LF_EUNSUPPORTED before any work.
 //
 // The array is LF_STATIC_SCRATCH_BYTES (1 MiB) per device.  Every GPU that loads the library
 // holds it until the process exits.  Every call uses the same array and leaves its
@@ -104,6 +110,12 @@ extern "C" lf_status lf_chi2_batch_static(const lf_cluster* cl, const double* th
                                           int32_t precision, double* chi2, void* stream) {
   if (!cl || !theta || !chi2) return fail(LF_EINVAL, "cluster, theta and chi2 are required");
   if (S < 1) return fail(LF_EINVAL, "S must be >= 1");
+  {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    LF_CUDA(cudaStreamIsCapturing((cudaStream_t)stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(LF_EUNSUPPORTED, "lf_chi2_batch_static copies host tables and cannot be captured");
+  }
   if (precision < LF_FP64 || precision > LF_FF) return fail(LF_EINVAL, "unknown precision");
   if (cl->n_planes < 1 || cl->n_planes > LF_MAX_PLANES || !cl->planes || !cl->arcsec_per_kpc)
     return fail(LF_EINVAL, "cluster needs 1..8 planes and arcsec_per_kpc");

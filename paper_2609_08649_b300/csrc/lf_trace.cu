@@ -4,9 +4,9 @@
 // A_j = I - sum_{i<j} r_ij Psi_i(theta_i) A_i, then beta = theta_1 - sum_j rs_j alpha_j and
 // A = I - sum_j rs_j Psi_j A_j.  All planes are staged into shared memory once per
 // (persistent) block.  LF_MIXED evaluates each plane's components in FP32 on float-float
-// offsets from theta_j, carries theta_j, the deflections and beta in float-float and the 2x2
-// Jacobian product in FP32; LF_FF evaluates in float-float and keeps the recursion in FP64;
-// LF_FP64 does everything in FP64.
+// offsets from theta_j and carries theta_j, the deflections, beta and the 2x2 Jacobian
+// product in float-float (on the FP32 pipe); LF_FF evaluates in float-float and keeps the
+// recursion in FP64; LF_FP64 does everything in FP64.
 #include "lf_internal.h"
 #include "lf_eval.cuh"
 
@@ -88,8 +88,9 @@ __global__ void __launch_bounds__(256) k_trace(MultiPlaneArgs MP, RayIO io, int 
       t1y = io.y0 + (double)j * io.dy;
     }
     if constexpr (MODE == LF_MIXED) {
-      // The recursion with theta_j, the deflections and beta in float-float and the Jacobian
-      // product in FP32 (Psi is FP32-accurate in this tier), on the FP32 pipe.
+      // The recursion on the FP32 pipe: theta_j, the deflections and beta in float-float, and
+      // the Jacobian product Psi_j A_j and A_j in float-float as well (about 48 bits, the
+      // precision of the FP64 product to within the FP32 rounding of each Psi_j).
       ff t1xf, t1yf;
       {
         float h, l;
@@ -97,17 +98,17 @@ __global__ void __launch_bounds__(256) k_trace(MultiPlaneArgs MP, RayIO io, int 
         split_ff(t1y, h, l); t1yf = ff_make(h, l);
       }
       ff alx[LF_MAX_PLANES], aly[LF_MAX_PLANES];
-      float PAf[LF_MAX_PLANES][4];   // Psi_j A_j, row-major
+      ff PA[LF_MAX_PLANES][4];   // Psi_j A_j, row-major
       for (int j = 0; j < MP.np; ++j) {
         ff tx = t1xf, ty = t1yf;
-        float a00 = 1.f, a01 = 0.f, a10 = 0.f, a11 = 1.f;
+        ff a00 = ff_make(1.f, 0.f), a01 = ff_zero(), a10 = ff_zero(), a11 = ff_make(1.f, 0.f);
         for (int i = 0; i < j; ++i) {
           const float2 r = MP.rf[i][j];
           const ff rr = ff_make(r.x, r.y);
           tx = ff_sub(tx, ff_mul(rr, alx[i]));
           ty = ff_sub(ty, ff_mul(rr, aly[i]));
-          a00 = fmaf(-r.x, PAf[i][0], a00); a01 = fmaf(-r.x, PAf[i][1], a01);
-          a10 = fmaf(-r.x, PAf[i][2], a10); a11 = fmaf(-r.x, PAf[i][3], a11);
+          a00 = ff_sub(a00, ff_mul(rr, PA[i][0])); a01 = ff_sub(a01, ff_mul(rr, PA[i][1]));
+          a10 = ff_sub(a10, ff_mul(rr, PA[i][2])); a11 = ff_sub(a11, ff_mul(rr, PA[i][3]));
         }
         PlaneLayout L = plane_layout<T, Mem>(MP.nc[j], MP.nm[j], MP.base[j]);
         const CompT<T>* dc = reinterpret_cast<const CompT<T>*>(smem + L.dc);
@@ -119,30 +120,29 @@ __global__ void __launch_bounds__(256) k_trace(MultiPlaneArgs MP, RayIO io, int 
                             tab, acc);
         alx[j] = acc[0][0];
         aly[j] = acc[1][0];
-        const float pxx = acc[2][0].hi + acc[2][0].lo, pyy = acc[3][0].hi + acc[3][0].lo,
-                    pxy = acc[4][0].hi + acc[4][0].lo;
-        PAf[j][0] = fmaf(pxx, a00, pxy * a10);
-        PAf[j][1] = fmaf(pxx, a01, pxy * a11);
-        PAf[j][2] = fmaf(pxy, a00, pyy * a10);
-        PAf[j][3] = fmaf(pxy, a01, pyy * a11);
+        const ff pxx = acc[2][0], pyy = acc[3][0], pxy = acc[4][0];
+        PA[j][0] = ff_add(ff_mul(pxx, a00), ff_mul(pxy, a10));
+        PA[j][1] = ff_add(ff_mul(pxx, a01), ff_mul(pxy, a11));
+        PA[j][2] = ff_add(ff_mul(pxy, a00), ff_mul(pyy, a10));
+        PA[j][3] = ff_add(ff_mul(pxy, a01), ff_mul(pyy, a11));
       }
       ff bx = t1xf, by = t1yf;
-      float A00 = 1.f, A01 = 0.f, A10 = 0.f, A11 = 1.f;
+      ff A00 = ff_make(1.f, 0.f), A01 = ff_zero(), A10 = ff_zero(), A11 = ff_make(1.f, 0.f);
       for (int j = 0; j < MP.np; ++j) {
         const float2 r = MP.rsf[j];
         const ff rr = ff_make(r.x, r.y);
         bx = ff_sub(bx, ff_mul(rr, alx[j]));
         by = ff_sub(by, ff_mul(rr, aly[j]));
-        A00 = fmaf(-r.x, PAf[j][0], A00); A01 = fmaf(-r.x, PAf[j][1], A01);
-        A10 = fmaf(-r.x, PAf[j][2], A10); A11 = fmaf(-r.x, PAf[j][3], A11);
+        A00 = ff_sub(A00, ff_mul(rr, PA[j][0])); A01 = ff_sub(A01, ff_mul(rr, PA[j][1]));
+        A10 = ff_sub(A10, ff_mul(rr, PA[j][2])); A11 = ff_sub(A11, ff_mul(rr, PA[j][3]));
       }
       if (io.beta) {
         io.beta[2 * p] = ff_to_double(bx);
         io.beta[2 * p + 1] = ff_to_double(by);
       }
       if (io.A) {
-        io.A[4 * p] = A00; io.A[4 * p + 1] = A01;
-        io.A[4 * p + 2] = A10; io.A[4 * p + 3] = A11;
+        io.A[4 * p] = ff_to_double(A00); io.A[4 * p + 1] = ff_to_double(A01);
+        io.A[4 * p + 2] = ff_to_double(A10); io.A[4 * p + 3] = ff_to_double(A11);
       }
       continue;
     }

@@ -44,31 +44,21 @@ def nfw_params(cosmo, z_l, m200, conc):
     return ks.value, ts.value
 
 
+_PHYS_FIELDS = ("vdisp", "theta_e", "z_ref", "core_kpc", "core_arcsec", "cut_kpc", "m200", "conc",
+                "kappa_s", "theta_s", "gamma", "amp")
+
+
 def comp_record(c: W.PhysComp, z_l, cosmo):
-    """(x, y, b, eps, pa, core, cut, kind) in lensing units."""
-    pa = math.radians(c.pa_deg)
-    if c.kind in (W.SIE, W.DPIE):
-        q = (1 - c.eps) / (1 + c.eps)
-        if c.vdisp is not None:
-            b = b_from_vdisp(c.vdisp)
-        else:   # area-equivalent Einstein radius at z_ref: theta_E = a b sqrt(q)
-            b = c.theta_e / (math.sqrt(q) * adis(cosmo, z_l, c.z_ref))
-        apk = arcsec_per_kpc(cosmo, z_l)
-        core = c.core_arcsec if c.core_arcsec is not None else c.core_kpc * apk
-        cut = c.cut_kpc * apk if c.cut_kpc is not None else 0.0
-        return (c.x, c.y, b, c.eps, pa, core, cut, c.kind)
-    if c.kind == W.NFW:
-        ks, ts = nfw_params(cosmo, z_l, c.m200, c.conc)
-        return (c.x, c.y, ks, 0.0, 0.0, ts, 0.0, c.kind)
-    if c.kind == W.ENFW:   # spherical NFW normalisation, ellipticity applied to xi
-        ks, ts = (c.kappa_s, c.theta_s) if c.kappa_s is not None else nfw_params(cosmo, z_l, c.m200, c.conc)
-        return (c.x, c.y, ks, c.eps, pa, ts, 0.0, c.kind)
-    if c.kind == W.SHEAR:
-        g = c.gamma if c.z_ref is None else c.gamma / adis(cosmo, z_l, c.z_ref)
-        return (c.x, c.y, g, 0.0, pa, 0.0, 0.0, c.kind)
-    if c.kind == W.MPOLE3:
-        return (c.x, c.y, c.amp, 0.0, pa, 0.0, 0.0, c.kind)
-    raise ValueError(c.kind)
+    """(x, y, b, eps, pa, core, cut, kind) in lensing units, converted by the library's
+    lf_comp_from_physical (fields not given are passed as NaN)."""
+    p = L.lf_phys_comp()
+    p.kind, p.x, p.y, p.eps, p.pa_deg = c.kind, c.x, c.y, c.eps, c.pa_deg
+    for f in _PHYS_FIELDS:
+        v = getattr(c, f)
+        setattr(p, f, math.nan if v is None else float(v))
+    out = L.lf_comp()
+    L.check(L.lib.lf_comp_from_physical(C.byref(p), cosmo.H0, cosmo.Om, z_l, C.byref(out)))
+    return (out.x, out.y, out.b, out.eps, out.pa, out.core, out.cut, out.kind)
 
 
 @dataclass
@@ -107,9 +97,10 @@ def device_plane(pl: W.PhysPlane, cosmo, device="cuda") -> DevicePlane:
         m = pl.members
         mem = np.zeros(len(m.x), dtype=MEM_DTYPE)
         mem["x"], mem["y"], mem["log_l"] = m.x, m.y, m.log_l
-        apk = arcsec_per_kpc(cosmo, pl.z)
-        scaling = (b_from_vdisp(m.vstar), m.core_star_kpc * apk, m.cut_star_kpc * apk,
-                   m.lam, m.beta, m.alpha)
+        sc = L.lf_scaling()
+        L.check(L.lib.lf_scaling_from_physical(m.vstar, m.core_star_kpc, m.cut_star_kpc, m.lam, m.beta,
+                                               m.alpha, cosmo.H0, cosmo.Om, pl.z, C.byref(sc)))
+        scaling = (sc.b_star, sc.core_star, sc.cut_star, sc.lam, sc.beta, sc.alpha)
     else:
         mem = np.zeros(0, dtype=MEM_DTYPE)
         scaling = (0.0, 0.0, 1.0, 0.0, 0.0, 0.0)
@@ -125,17 +116,12 @@ def grid_struct(g: W.Grid) -> L.lf_grid:
 
 
 def multiplane_ratios(cosmo, zs_planes, z_s):
-    """(n+1) x n table: r[i][j] = D_ij/D_j for i < j, last row D_js/D_s."""
+    """(n+1) x n table (lf_multiplane_ratios): r[i][j] = D_ij/D_j for i < j, last row D_js/D_s."""
     n = len(zs_planes)
     r = np.zeros((n + 1, n))
-    for j in range(n):
-        dj = L.lib.lf_angular_distance(cosmo.H0, cosmo.Om, 0.0, zs_planes[j])
-        for i in range(j):
-            r[i, j] = L.lib.lf_angular_distance(cosmo.H0, cosmo.Om, zs_planes[i], zs_planes[j]) / dj
-    ds = L.lib.lf_angular_distance(cosmo.H0, cosmo.Om, 0.0, z_s)
-    for j in range(n):
-        r[n, j] = (L.lib.lf_angular_distance(cosmo.H0, cosmo.Om, zs_planes[j], z_s) / ds
-                   if z_s > zs_planes[j] else 0.0)
+    z = np.ascontiguousarray(zs_planes, dtype=np.float64)
+    L.check(L.lib.lf_multiplane_ratios(cosmo.H0, cosmo.Om, z.ctypes.data_as(C.c_void_p), n, float(z_s),
+                                       r.ctypes.data_as(C.c_void_p)))
     return r
 
 

@@ -126,3 +126,42 @@ def test_host_maps_binding_rejects_wrong_outputs():
     for out in bad:
         with pytest.raises(TypeError):
             api.jacobian_grid_host(None, grid, 0.5, "mixed", out=out)
+
+
+def test_host_unit_conversions_match_the_oracle():
+    """lf_comp_from_physical, lf_scaling_from_physical and lf_multiplane_ratios (host-only set-up
+    helpers) against the oracle's own conversions, on every component kind of the workloads."""
+    import numpy as np
+    from oracle import cosmology as cz
+    from oracle import lensing as OLL
+    from oracle import model as OM
+    from paper_2609_08649_b300 import _lib as L
+    from paper_2609_08649_b300 import model as PM
+    from paper_2609_08649_b300 import workloads as W
+    wls = [W.galaxy_c0(), W.cluster_c2(n_samples=1), W.multiplane_c3(n_grid=8, n_samples=1),
+           W.cluster_c5_enfw(n_samples=1), W.cluster_c2_mpole(n_samples=1)]
+    kinds = set()
+    for wl in wls:
+        for pl in wl.planes:
+            for c in pl.comps:
+                a = np.array(PM.comp_record(c, pl.z, wl.cosmo)[:7])
+                b = np.array(OM.comp_fields(c, pl.z, wl.cosmo))
+                assert np.all(np.abs(a - b) <= 1e-13 * np.maximum(1, np.abs(b))), (c.kind, a, b)
+                kinds.add(c.kind)
+            if pl.members is not None:
+                m = pl.members
+                sc = PM.device_plane(pl, wl.cosmo, device="cpu").scaling
+                apk = cz.arcsec_per_kpc(pl.z)
+                ref = (OLL.b_from_vdisp(m.vstar), m.core_star_kpc * apk, m.cut_star_kpc * apk, m.lam, m.beta, m.alpha)
+                assert np.allclose(sc, ref, rtol=1e-13, atol=0)
+    assert kinds >= {W.SIE, W.DPIE, W.NFW, W.SHEAR, W.MPOLE3, W.ENFW}
+    zs = [0.39, 0.9, 2.1]
+    r = PM.multiplane_ratios(W.Cosmo(), zs, 4.0)
+    r0, rs0 = cz.multiplane_ratios(zs, 4.0)
+    assert np.allclose(r[:3], np.array(r0), rtol=1e-13, atol=0) and np.allclose(r[3], rs0, rtol=1e-13, atol=0)
+    bad = L.lf_phys_comp()
+    bad.kind = W.SIE
+    for f in ("vdisp", "theta_e", "z_ref", "core_kpc", "core_arcsec", "cut_kpc"):
+        setattr(bad, f, float("nan"))
+    out = L.lf_comp()
+    assert L.lib.lf_comp_from_physical(C.byref(bad), 70.0, 0.3, 0.5, C.byref(out)) == L.LF_EINVAL

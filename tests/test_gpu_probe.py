@@ -18,3 +18,24 @@ def test_probe_rates_are_plausible():
     assert 0 < dfma < rsq < fma
     assert fma <= nsm * 128 * clock_max and rsq <= nsm * 32 * clock_max
     assert fma > 0.3 * nsm * 128 * 1.0e9
+
+
+def test_bounded_wait_runs_out_and_is_reported():
+    """The failure-detection path: a kernel whose mbarrier phase can never complete (16 bytes
+    of transactions expected, no copy issued) gives up after 64 polls, the device error word
+    reports LF_ETIMEOUT once, and the context stays usable."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import ctypes as C
+    from paper_2609_08649_b300 import _lib as L
+    from paper_2609_08649_b300 import api
+    api.device_error()                                   # start from a clean word
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L.check(L.lib.lf_selftest_wait_timeout(64, stream))
+    with pytest.raises(L.LFError) as e:
+        api.device_error()
+    assert e.value.status == L.LF_ETIMEOUT
+    api.device_error()                                   # the word was cleared
+    assert L.lib.lf_selftest_wait_timeout(0, stream) == L.LF_EINVAL
+    x = torch.arange(8.0, device="cuda")
+    assert float(x.sum()) == 28.0                        # the context still runs work

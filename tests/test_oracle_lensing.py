@@ -136,6 +136,86 @@ def test_cosmology_einstein_de_sitter_closed_form():
     assert cz.a_dis(0.5, 0.5) == 0.0 and 0 < cz.a_dis(0.5, 2.0) < cz.a_dis(0.5, 9.0) < 1
 
 
+def test_cosmology_flat_lcdm_against_independent_quadrature():
+    """Omega_m = 0.3: the oracle's adaptive quadrature against mpmath's tanh-sinh quadrature
+    of the same integral at 30 digits, for the redshift pairs of the workloads."""
+    import mpmath
+    mpmath.mp.dps = 30
+    c_h0 = mpmath.mpf(cz.C_KMS) / 70
+    E = lambda z: mpmath.sqrt(mpmath.mpf("0.3") * (1 + z) ** 3 + mpmath.mpf("0.7"))
+    for z1, z2 in [(0.0, 0.5), (0.0, 2.0), (0.5, 2.0), (0.39, 4.0), (0.9, 4.0), (2.1, 4.0), (0.5, 9.0)]:
+        ref = c_h0 / (1 + mpmath.mpf(z2)) * mpmath.quad(lambda z: 1 / E(z), [mpmath.mpf(z1), mpmath.mpf(z2)])
+        assert abs(cz.d_ang(z1, z2) / float(ref) - 1) < 1e-12, (z1, z2)
+    # a_dis and the kpc scale from the same distances
+    dd = c_h0 / mpmath.mpf("1.5") * mpmath.quad(lambda z: 1 / E(z), [0, mpmath.mpf("0.5")])
+    assert abs(cz.arcsec_per_kpc(0.5) / float(mpmath.mpf(cz.ARCSEC_PER_RAD) / (dd * 1000)) - 1) < 1e-12
+
+
+def _sheet_plane(k0):
+    t = lambda v: torch.tensor([[float(v)]])
+    return L.LPlane([L.SHEET], t(0), t(0), t(k0), t(0), t(0), t(0), t(0))
+
+
+def test_mass_sheet_closed_forms():
+    """A uniform sheet kappa_0: alpha = kappa_0 theta, gamma = 0, beta = (1 - a kappa_0) theta
+    and mu = 1 / (1 - a kappa_0)^2, through plane_sum, lens_map and jacobian_maps; added to
+    another lens it shifts kappa by kappa_0 and leaves gamma alone."""
+    k0, a = 0.37, 0.62
+    tx = torch.tensor([[1.5, -7.25, 12.0, 0.0]]); ty = torch.tensor([[2.0, 5.5, -9.0, 0.0]])
+    ax, ay, pxx, pyy, pxy = L.plane_sum(_sheet_plane(k0), tx, ty)
+    assert torch.equal(ax, k0 * tx) and torch.equal(ay, k0 * ty)
+    kappa, g1, g2, mu, det = L.jacobian_maps(ax, ay, pxx, pyy, pxy, a)
+    assert torch.allclose(kappa, torch.full_like(kappa, k0), rtol=0, atol=1e-15)
+    assert float(g1.abs().max()) == 0.0 and float(g2.abs().max()) == 0.0
+    assert torch.allclose(mu, torch.full_like(mu, 1 / (1 - a * k0) ** 2), rtol=1e-14, atol=0)
+    bx, by = L.lens_map(tx, ty, ax, ay, a)
+    assert torch.allclose(bx, (1 - a * k0) * tx, rtol=1e-15, atol=1e-15)
+    assert torch.allclose(by, (1 - a * k0) * ty, rtol=1e-15, atol=1e-15)
+    op = om.build_planes(small_cluster())[0]
+    both = L.LPlane(op.kind + [L.SHEET], *[torch.cat([getattr(op, f), getattr(_sheet_plane(k0), f)], 1)
+                                            for f in ("x", "y", "b", "eps", "pa", "core", "cut")],
+                    op.mx, op.my, op.log_l, op.b_star, op.core_star, op.cut_star, op.lam, op.beta, op.alpha)
+    k1, a1, b1, _, _ = L.jacobian_maps(*L.plane_sum(op, tx, ty), a)
+    k2, a2, b2, _, _ = L.jacobian_maps(*L.plane_sum(both, tx, ty), a)
+    assert torch.allclose(k2 - k1, torch.full_like(k1, k0), atol=1e-13)
+    assert torch.allclose(a1, a2, atol=1e-13) and torch.allclose(b1, b2, atol=1e-13)
+
+
+def test_mass_sheet_planes_multiplane_closed_form():
+    """Two sheet planes kappa_1, kappa_2: theta_2 = (1 - r_12 kappa_1) theta_1, so
+    beta = c theta_1 and A = c I with c = 1 - rs_1 kappa_1 - rs_2 kappa_2 (1 - r_12 kappa_1)."""
+    k1, k2 = 0.21, 0.34
+    r, rs = cz.multiplane_ratios([0.4, 1.0], 3.0)
+    tx = torch.tensor([[1.5, -7.25, 12.0]]); ty = torch.tensor([[2.0, 5.5, -9.0]])
+    beta, A = L.trace_multiplane([_sheet_plane(k1), _sheet_plane(k2)], r, rs, tx, ty)
+    c = 1 - rs[0] * k1 - rs[1] * k2 * (1 - r[0][1] * k1)
+    assert torch.allclose(beta[..., 0], c * tx, rtol=1e-14, atol=1e-14)
+    assert torch.allclose(beta[..., 1], c * ty, rtol=1e-14, atol=1e-14)
+    eye = torch.eye(2, dtype=torch.float64).expand_as(A)
+    assert torch.allclose(A, c * eye, rtol=0, atol=1e-15)
+
+
+def test_source_plane_chi2_is_invariant_under_a_mass_sheet():
+    """With a pure sheet lens, beta_i = (1 - a kappa_0) theta_i and mu_i = I / (1 - a kappa_0),
+    so M_i = S_i^-1 / (1 - a kappa_0)^2 and the factors cancel in Eq. chi2_src: the chi^2 is that
+    of the observed positions about their S^-1-weighted family mean, for every kappa_0."""
+    rng = np.random.default_rng(4)
+    fam_off = [0, 2, 5, 9]
+    th = torch.tensor(rng.uniform(-10, 10, (9, 2)))
+    sinv = torch.tensor(np.column_stack([rng.uniform(20, 200, 9), rng.uniform(-5, 5, 9), rng.uniform(20, 200, 9)]))
+    Sm = L.sinv_matrix(sinv)
+    ref = 0.0
+    for f in range(3):
+        i0, i1 = fam_off[f], fam_off[f + 1]
+        mean = torch.linalg.solve(Sm[i0:i1].sum(0), (Sm[i0:i1] @ th[i0:i1, :, None]).sum(0))[:, 0]
+        d = th[i0:i1] - mean
+        ref += float((d[:, None, :] @ Sm[i0:i1] @ d[:, :, None]).sum())
+    for k0 in (0.0, 0.3, -0.4):
+        beta, A = L.single_plane_source_terms(_sheet_plane(k0), th, fam_off, [0.7] * 3)
+        c = L.chi2_src(beta, A, sinv, fam_off)
+        assert abs(float(c.reshape(-1)[0]) - ref) <= 1e-12 * ref, k0
+
+
 def _chi2_model(theta_obs, fam_off, a, pl, sinv):
     beta, A = L.single_plane_source_terms(pl, theta_obs, fam_off, [a] * (len(fam_off) - 1))
     return beta, A, L.chi2_src(beta, A, sinv, fam_off)
