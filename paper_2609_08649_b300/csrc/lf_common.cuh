@@ -822,6 +822,33 @@ LF_INLINE void sie_alpha_ff(const ff& u, const ff& v, const ff& uu, const ff& vv
   av = ff_mul(qe, ff_atanh(z2, tab));
 }
 
+// alpha of a unit-strength dPIE (core s, cut a) in its (u, v) frame, float-float: the
+// difference of the two isothermal ellipsoids folded into one atan and one atanh by
+//   atan(z_s) - atan(z_a) = atan((z_s - z_a) / (1 + z_s z_a)),
+//   atanh(z_s) - atanh(z_a) = atanh((z_s - z_a) / (1 - z_s z_a)),
+// with z = e u / (psi~ + s) (resp. e v / (psi~ + q^2 s)) for each radius.  Writing X = psi_s + s,
+// Y = psi_a + a (X2, Y2 with q^2 s, q^2 a) and w = (a + s) / (psi_a + psi_s), the differences are
+// cancellation-free: Y - X = (a - s)(1 + q^2 w) and Y2 - X2 = q^2 (a - s)(1 + w), because
+// psi_a - psi_s = q^2 (a^2 - s^2) / (psi_a + psi_s).  So
+//   alpha_u = (q/e) atan(e u (Y - X) / (X Y + e^2 u^2)),
+//   alpha_v = (q/e) atanh(e v (Y2 - X2) / (X2 Y2 - e^2 v^2)).
+LF_INLINE void dpie_alpha_ff(const ff& u, const ff& v, const ff& uu, const ff& vv, const ff& q2,
+                             const ff& e, const ff& qe, const ff& s, const ff& ssq, const ff& q2s,
+                             const ff& a, const ff& asq, const ff& q2a, const float2* tab, ff& au,
+                             ff& av) {
+  const ff ps = ff_sqrt(ff_add(ff_mul(q2, ff_add(ssq, uu)), vv));
+  const ff pa = ff_sqrt(ff_add(ff_mul(q2, ff_add(asq, uu)), vv));
+  const ff amin = ff_sub(a, s);
+  const ff w = ff_div(ff_add(a, s), ff_add(pa, ps));
+  const ff eu = ff_mul(e, u), ev = ff_mul(e, v);
+  const ff num1 = ff_mul(ff_mul(eu, amin), ff_add_f(ff_mul(q2, w), 1.f));
+  const ff den1 = ff_add(ff_mul(ff_add(ps, s), ff_add(pa, a)), ff_sqr(eu));
+  const ff num2 = ff_mul(ff_mul(ff_mul(ev, q2), amin), ff_add_f(w, 1.f));
+  const ff den2 = ff_sub(ff_mul(ff_add(ps, q2s), ff_add(pa, q2a)), ff_sqr(ev));
+  au = ff_mul(qe, ff_atan(ff_div(num1, den1), tab));
+  av = ff_mul(qe, ff_atanh(ff_div(num2, den2), tab));
+}
+
 // alpha of the elliptical NFW's CSE sum (enfw_uv) with every operation in float-float: offsets
 // (u, v) in r_s units; returns the unit-kappa_s, r_s = 1 deflection in the (u, v) frame.
 __constant__ float2 c_cse_sff[LF_CSE_N] = {LF_CSE_S_FF_LIST};
@@ -908,16 +935,16 @@ LF_NOINLINE void eval_comp_mixed(const CompT<float>& c, float ph_x, float pl_x, 
   ff uu = ff_mul(u, u), vv = ff_mul(v, v);
   const ff q2 = ff_make(c.q2, c.lq2), e = ff_make(c.e, c.le), qe = ff_make(c.qe, c.lqe);
   ff au, av;
-  sie_alpha_ff(u, v, uu, vv, q2, e, qe, ff_make(c.s1, c.ls1), ff_make(c.s1sq, c.ls1sq),
-               ff_make(c.q2s1, c.lq2s1), tab, au, av);
+  if (c.kind == K_DPIE)
+    dpie_alpha_ff(u, v, uu, vv, q2, e, qe, ff_make(c.s1, c.ls1), ff_make(c.s1sq, c.ls1sq),
+                  ff_make(c.q2s1, c.lq2s1), ff_make(c.s2, c.ls2), ff_make(c.s2sq, c.ls2sq),
+                  ff_make(c.q2s2, c.lq2s2), tab, au, av);
+  else
+    sie_alpha_ff(u, v, uu, vv, q2, e, qe, ff_make(c.s1, c.ls1), ff_make(c.s1sq, c.ls1sq),
+                 ff_make(c.q2s1, c.lq2s1), tab, au, av);
   float puu, pvv, puv;
   sie_psi(u.hi, v.hi, c.q, c.q2, c.s1, c.s1sq, c.D01, puu, pvv, puv);
   if (c.kind == K_DPIE) {
-    ff bu, bv;
-    sie_alpha_ff(u, v, uu, vv, q2, e, qe, ff_make(c.s2, c.ls2), ff_make(c.s2sq, c.ls2sq),
-                 ff_make(c.q2s2, c.lq2s2), tab, bu, bv);
-    au = ff_sub(au, bu);
-    av = ff_sub(av, bv);
     float quu, qvv, quv;
     sie_psi(u.hi, v.hi, c.q, c.q2, c.s2, c.s2sq, c.D02, quu, qvv, quv);
     puu -= quu; pvv -= qvv; puv -= quv;

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_ff(const lf_comp* __re
 // mixed kernels.  T = LF_ANCHOR_T min(1, LF_ANCHOR_H0 / h): coarse tiles send more members to
 // the float-float path, so the precision does not depend on the pixel scale.
 #ifndef LF_ANCHOR_MINB
-#define LF_ANCHOR_MINB 4
+#define LF_ANCHOR_MINB 3   // 80 registers, 3 blocks of 256 per SM (no spills; 4 blocks at 64 registers measured 3 % slower)
 #endif
 #ifndef LF_ANCHOR_T
 #define LF_ANCHOR_T 0.3f

@@ -157,6 +157,8 @@ extern "C" lf_status lf_comp_from_physical(const lf_phys_comp* in, double H0, do
     case LF_NFW:
     case LF_ENFW: {
       if (given(in->kappa_s) && given(in->theta_s)) {
+        if (!(std::isfinite(in->kappa_s) && in->theta_s > 0.0 && std::isfinite(in->theta_s)))
+          return fail(LF_EINVAL, "need a finite kappa_s and theta_s > 0");
         c.b = in->kappa_s;
         c.core = in->theta_s;
       } else {

@@ -183,14 +183,24 @@ def test_invalid_enfw_components_are_refused(lib):
     grid = W.Grid(-10.0, -10.0, 1.0, 1.0, 21, 21)
     ref = api.jacobian_grid(PM.device_plane(W.PhysPlane(0.5, [good]), W.Cosmo()), grid, 0.5, "mixed")
     api.device_error()
-    for bad in (W.replace(good, theta_s=0.0), W.replace(good, theta_s=-3.0), W.replace(good, eps=1.0)):
-        dp = PM.device_plane(W.PhysPlane(0.5, [good, bad]), W.Cosmo())
+    for field, value in (("core", 0.0), ("core", -3.0), ("eps", 1.0)):
+        # the host converter refuses such a component, so write it into the table directly
+        dp = PM.device_plane(W.PhysPlane(0.5, [good, good]), W.Cosmo())
+        dp.comp_host[field][1] = value
+        dp.to("cuda")
         o = api.jacobian_grid(dp, grid, 0.5, "mixed")
         with pytest.raises(L.LFError):
             api.device_error()
         assert torch.equal(o["ax"], ref["ax"]) and torch.equal(o["mu"], ref["mu"])
-        wl = W.Workload("bad", W.Cosmo(), [W.PhysPlane(0.5, [good, bad])],
+        wl = W.Workload("bad", W.Cosmo(), [W.PhysPlane(0.5, [good, good])],
                         params=[W.ParamSpec(0, W.F_B, W.XF_IDENT, 0.3, 0.01, True)], n_samples=2)
         cat = W.load_catalogue("galaxy_sie_shear")
-        with pytest.raises(L.LFError):
-            api.Plan([PM.cluster_input(wl, cat)], 2, "mixed")
+        ci = PM.cluster_input(wl, cat)
+        ci.planes[0].comp_host[field][1] = value
+        ci.planes[0].to("cuda")
+        with pytest.raises(L.LFError) as e:
+            api.Plan([ci], 2, "mixed")
+        assert e.value.status == L.LF_EINVAL
+        bad = W.replace(good, **({"theta_s": value} if field == "core" else {"eps": value}))
+        with pytest.raises(L.LFError):      # the host converter refuses it too
+            PM.device_plane(W.PhysPlane(0.5, [bad]), W.Cosmo())

@@ -57,14 +57,16 @@ def _jac_bound(wl, x, y):
 
 
 def _check_mu(A, A0):
-    """mu = 1/det A where |det A| >= 1e-3, relative error bounded by the error of det A."""
+    """mu = 1/det A where |det A| >= 1e-3, relative error bounded by the error of det A: with
+    |dA_ij| <= e and |A_ij| <= m, |d det| <= 4 m e + 2 e^2 (four products of the 2x2
+    determinant), and |1/det - 1/det0| |det0| = |d det| / |det| <= |d det| / (|det0| - |d det|)."""
     det = A[:, 0, 0] * A[:, 1, 1] - A[:, 0, 1] * A[:, 1, 0]
     det0 = A0[:, 0, 0] * A0[:, 1, 1] - A0[:, 0, 1] * A0[:, 1, 0]
     m = np.abs(det0) >= 1e-3
     dA = np.abs(A - A0).max((1, 2))
-    ddet = 2 * np.abs(A0).max((1, 2)) * dA + 2 * dA * dA
+    ddet = 4 * np.abs(A0).max((1, 2)) * dA + 2 * dA * dA
     rel = np.abs(1 / det[m] - 1 / det0[m]) * np.abs(det0[m])
-    assert np.all(rel <= 1e-12 + 1.5 * ddet[m] / np.abs(det0[m])), rel.max()
+    assert np.all(rel <= 1e-12 + ddet[m] / (np.abs(det0[m]) - ddet[m])), rel.max()
 
 
 def _abs_scale(wl, x, y):
