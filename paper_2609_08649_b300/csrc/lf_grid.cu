@@ -114,8 +114,10 @@ __global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_ff(const lf_comp* __re
 // tile of half-diagonal h) instead of with |alpha_k|: on the cluster field at 0.04" pixels this
 // cuts the deflection error from ~1e-6" rms to ~2e-8".  Members whose change across the tile
 // is not small (3 kbar(theta0) h > T, or closer to theta0 than 2 h) are evaluated per position
-// in float-float instead, as are the explicit components.  psi_ij is FP32 as in the other
-// mixed kernels.  T = LF_ANCHOR_T min(1, LF_ANCHOR_H0 / h): coarse tiles send more members to
+// in float-float instead.  The elliptical isothermal components (SIE, dPIE) are anchored the
+// same way (sie_anchor_delta: their deflection at theta0 in float-float, its change by exact
+// differences of the atan / atanh arguments in FP32); every other explicit component is
+// evaluated in float-float at each position.  psi_ij is FP32 as in the other mixed kernels.  T = LF_ANCHOR_T min(1, LF_ANCHOR_H0 / h): coarse tiles send more members to
 // the float-float path, so the precision does not depend on the pixel scale.
 #ifndef LF_ANCHOR_MINB
 #define LF_ANCHOR_MINB 3   // 80 registers, 3 blocks of 256 per SM (no spills; 4 blocks at 64 registers measured 3 % slower)
@@ -125,6 +127,9 @@ __global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_ff(const lf_comp* __re
 #endif
 #ifndef LF_ANCHOR_H0
 #define LF_ANCHOR_H0 0.5
+#endif
+#ifndef LF_ANCHOR_HALO
+#define LF_ANCHOR_HALO 2.0f   // arcsec: bound on an anchored isothermal component's change across a tile
 #endif
 constexpr int LF_ATILE = 16;   // anchored grid tile: 16 x 16 pixels (one per thread of a 256-thread block)
 
@@ -182,9 +187,49 @@ __device__ __forceinline__ void anchor_pair_acc(const AnchorPair& m, float2 e2x,
   c[5] = fma2(tdy, dy, c[5]);
 }
 
+// An elliptical isothermal component (SIE or dPIE) at one tile's anchor: its frame offsets
+// u0, v0 and psi~ = sqrt(q^2 (r^2 + u^2) + v^2) there for the core and the cut radius, FP32;
+// anchored = 0 for the kinds evaluated in float-float at every position instead.
+struct __align__(16) AnchorComp {
+  float u0, v0, ps0, pa0;
+  int anchored, pad0, pad1, pad2;
+};
+
+// One isothermal ellipsoid of unit strength and radius r at (u, v) = (u0 + du, v0 + dv) in
+// its frame: the change of its deflection from the anchor (u0, v0), and its psi_ij, in FP32.
+// With dp2 = psi~^2 - psi0~^2 = q^2 du (2 u0 + du) + dv (2 v0 + dv) (cancellation-free) and
+// psi~ - psi0~ = dp2 / (psi~ + psi0~), the changes of z1 = e u / (psi~ + r) and
+// z2 = e v / (psi~ + q^2 r) enter through
+//   atan(z1) - atan(z10) = atan(e (du (psi0~ + r) - u0 (psi~ - psi0~)) / ((psi~ + r)(psi0~ + r) + e^2 u u0)),
+//   atanh(z2) - atanh(z20) = atanh(e (dv (psi0~ + q^2 r) - v0 (psi~ - psi0~))
+//                                   / ((psi~ + q^2 r)(psi0~ + q^2 r) - e^2 v v0)),
+// so the FP32 rounding scales with the change, not with the deflection.
+__device__ __forceinline__ void sie_anchor_delta(float u0, float v0, float du, float dv, float dp2, float ps0,
+                                                 float q, float q2, float e, float qe, float r, float r2,
+                                                 float q2r, float D0, float& dau, float& dav, float& puu,
+                                                 float& pvv, float& puv) {
+  const float ps2 = fmaf(ps0, ps0, dp2);
+  const float ips = rsqrtf(ps2), ps = ps2 * ips;
+  const float dps = dp2 * __fdividef(1.f, ps + ps0);
+  const float u = u0 + du, v = v0 + dv;
+  const float A = ps0 + r, B = ps0 + q2r, ee = e * e;
+  const float n1 = e * fmaf(du, A, -u0 * dps), d1 = fmaf(ps + r, A, ee * u * u0);
+  const float t2 = e * fmaf(dv, B, -v0 * dps) * __fdividef(1.f, fmaf(ps + q2r, B, -ee * v * v0));
+  // 1 + z1 z10 < 0 (|z1| > 1 on both sides of u = 0, possible for q^2 < 1/2): atan's branch
+  // moves by pi, with the sign of z1 - z10 (that of n1)
+  dau = qe * (atanf(n1 * __fdividef(1.f, d1)) + (d1 < 0.f ? copysignf(3.14159265358979f, n1) : 0.f));
+  dav = qe * atanhf(t2);     // |z2|, |z20| < 1: 1 - z2 z20 > 0
+  const float uu = u * u, vv = v * v;
+  const float f = q * ips * __fdividef(1.f, D0 + 2.f * ps * r + uu + vv);
+  const float sp = r * ps;
+  puu = f * (fmaf(q2, r2, vv) + sp);
+  pvv = f * (r2 + uu + sp);
+  puv = -f * u * v;
+}
+
 // Shared memory of the anchored kernel (host and device agree on it).
 struct AnchorLayout {
-  uint32_t rawc, rawm, dc, dm, ap, bits, red, total;
+  uint32_t rawc, rawm, dc, dm, ap, ac, bits, red, total;
 };
 __host__ __device__ inline AnchorLayout anchor_layout(int nc, int nm) {
   AnchorLayout L;
@@ -197,6 +242,8 @@ __host__ __device__ inline AnchorLayout anchor_layout(int nc, int nm) {
   L.dm = o; o += (uint32_t)nm * (uint32_t)sizeof(MemX);
   o = (o + 15u) & ~15u;
   L.ap = o; o += (uint32_t)((nm + 1) / 2) * (uint32_t)sizeof(AnchorPair);
+  o = (o + 15u) & ~15u;
+  L.ac = o; o += (uint32_t)nc * (uint32_t)sizeof(AnchorComp);
   o = (o + 15u) & ~15u;
   L.bits = o; o += (uint32_t)((nm + 31) / 32) * 4u;
   o = (o + 15u) & ~15u;
@@ -221,6 +268,7 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
   CompT<float>* dc = reinterpret_cast<CompT<float>*>(smem + L.dc);
   MemX* dm = reinterpret_cast<MemX*>(smem + L.dm);
   AnchorPair* ap = reinterpret_cast<AnchorPair*>(smem + L.ap);
+  AnchorComp* acp = reinterpret_cast<AnchorComp*>(smem + L.ac);
   uint32_t* bits = reinterpret_cast<uint32_t*>(smem + L.bits);
   double* red = reinterpret_cast<double*>(smem + L.red);
   float2* tab = reinterpret_cast<float2*>(smem + 16);
@@ -323,6 +371,35 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
       const int wi = (k0 >> 5) + warp;
       if (lane == 0 && wi < nw) bits[wi] = word;
     }
+    // elliptical isothermal components: frame offsets and psi~ at the anchor, and their
+    // float-float deflection there (on the threads with the fewest member records)
+    for (int c = 255 - tid; c >= 0 && c < nc; c += 256) {
+      const CompT<float>& C = dc[c];
+      AnchorComp rec;
+      const bool ell = (C.kind == K_SIE || C.kind == K_DPIE) && !C.round;
+      rec.pad0 = rec.pad1 = rec.pad2 = 0;
+      rec.u0 = rec.v0 = rec.ps0 = rec.pa0 = 0.f;
+      if (ell) {
+        const float dx0 = offset_ff(ahx, alx, C.xh, C.xl).hi, dy0 = offset_ff(ahy, aly, C.yh, C.yl).hi;
+        rec.u0 = fmaf(C.c, dx0, C.sn * dy0);
+        rec.v0 = fmaf(C.c, dy0, -C.sn * dx0);
+        const float uu = rec.u0 * rec.u0, vv = rec.v0 * rec.v0;
+        rec.ps0 = sqrtf(fmaf(C.q2, C.s1sq + uu, vv));
+        rec.pa0 = C.kind == K_DPIE ? sqrtf(fmaf(C.q2, C.s2sq + uu, vv)) : 0.f;
+      }
+      // anchored when its deflection changes little across the tile: |psi_ij| <~ b / psi~ with
+      // psi~ >= max(psi0~ - h, q s) over the tile, so the change is below b h / that
+      rec.anchored = ell && h <= LF_ANCHOR_H0 &&
+                     C.b * hf <= LF_ANCHOR_HALO * fmaxf(rec.ps0 - hf, C.q * C.s1);
+      if (rec.anchored) {
+        ff ax, ay;
+        Out5<float> o;
+        eval_comp_mixed(C, ahx, alx, ahy, aly, tab, ax, ay, o);
+        sax = ff_add(sax, ax);
+        say = ff_add(say, ay);
+      }
+      acp[c] = rec;
+    }
     for (int off = 16; off > 0; off >>= 1) {
       sax = ff_add(sax, ff_shfl_xor(sax, off));
       say = ff_add(say, ff_shfl_xor(say, off));
@@ -364,7 +441,28 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
       ff_acc(acc[3], kb + (c6[5].x + c6[5].y));
       ff_acc(acc[4], c6[4].x + c6[4].y);
     }
-    // the offset e was rounded to FP32: first-order correction with these members' psi
+    // the anchored explicit components: their change from the anchor and their psi_ij
+    for (int c = 0; c < nc; ++c) {
+      const AnchorComp R = acp[c];
+      if (!R.anchored) continue;
+      const CompT<float>& C = dc[c];
+      const float du = fmaf(C.c, ex, C.sn * ey), dv = fmaf(C.c, ey, -C.sn * ex);
+      const float dp2 = fmaf(C.q2 * du, fmaf(2.f, R.u0, du), dv * fmaf(2.f, R.v0, dv));
+      float dau, dav, puu, pvv, puv;
+      sie_anchor_delta(R.u0, R.v0, du, dv, dp2, R.ps0, C.q, C.q2, C.e, C.qe, C.s1, C.s1sq, C.q2s1, C.D01,
+                       dau, dav, puu, pvv, puv);
+      if (C.kind == K_DPIE) {
+        float bau, bav, quu, qvv, quv;
+        sie_anchor_delta(R.u0, R.v0, du, dv, dp2, R.pa0, C.q, C.q2, C.e, C.qe, C.s2, C.s2sq, C.q2s2, C.D02,
+                         bau, bav, quu, qvv, quv);
+        dau -= bau; dav -= bav; puu -= quu; pvv -= qvv; puv -= quv;
+      }
+      Out5<float> o;
+      rotate_back(C.c, C.sn, C.b * dau, C.b * dav, C.b * puu, C.b * pvv, C.b * puv, o);
+      ff_acc(acc[0], o.ax); ff_acc(acc[1], o.ay);
+      ff_acc(acc[2], o.pxx); ff_acc(acc[3], o.pyy); ff_acc(acc[4], o.pxy);
+    }
+    // the offset e was rounded to FP32: first-order correction with the anchored terms' psi
     ff_acc(acc[0], fmaf(acc[2].hi, exl, acc[4].hi * eyl));
     ff_acc(acc[1], fmaf(acc[4].hi, exl, acc[3].hi * eyl));
     acc[0] = ff_add(acc[0], sax);
@@ -374,7 +472,7 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
     split_ff(y, pyh, pyl);
     for (int c = 0; c < nc; ++c) {
       const CompT<float>& C = dc[c];
-      if (C.kind == 0) continue;
+      if (C.kind == 0 || acp[c].anchored) continue;
       ff ax, ay;
       Out5<float> o;
       eval_comp_ext(C, pxh, pxl, pyh, pyl, tab, ax, ay, o);
