@@ -117,8 +117,9 @@ __global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_ff(const lf_comp* __re
 // in float-float instead.  The elliptical isothermal components (SIE, dPIE) are anchored the
 // same way (sie_anchor_delta: their deflection at theta0 in float-float, its change by exact
 // differences of the atan / atanh arguments in FP32); every other explicit component is
-// evaluated in float-float at each position.  psi_ij is FP32 as in the other mixed kernels.  T = LF_ANCHOR_T min(1, LF_ANCHOR_H0 / h): coarse tiles send more members to
-// the float-float path, so the precision does not depend on the pixel scale.
+// evaluated in float-float at each position.  psi_ij is FP32 as in the other mixed kernels.
+// T = LF_ANCHOR_T min(1, LF_ANCHOR_H0 / h): coarse tiles send more members to the float-float
+// path, so the precision does not depend on the pixel scale.
 #ifndef LF_ANCHOR_MINB
 #define LF_ANCHOR_MINB 3   // 80 registers, 3 blocks of 256 per SM (no spills; 4 blocks at 64 registers measured 3 % slower)
 #endif
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_ff(const lf_comp* __re
 #define LF_ANCHOR_T 0.3f
 #endif
 #ifndef LF_ANCHOR_H0
-#define LF_ANCHOR_H0 0.5
+#define LF_ANCHOR_H0 0.5f
 #endif
 #ifndef LF_ANCHOR_HALO
 #define LF_ANCHOR_HALO 2.0f   // arcsec: bound on an anchored isothermal component's change across a tile
@@ -288,7 +289,8 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
   const long long n_tiles = GRID ? tiles_x * ((ny + LF_ATILE - 1) / LF_ATILE) : (P.n + 255) / 256;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     // this thread's position and the tile's anchor (FP64)
-    double x, y, cx, cy, h;
+    double x, y, cx, cy;
+    float hf;     // the tile's half-diagonal: thresholds only, so FP32 (the FP64 pipe is slow)
     long long pid;
     bool valid;
     if constexpr (GRID) {
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
       y = P.y0 + (double)j * P.dy;
       cx = P.x0 + ((double)(tx * LF_ATILE) + 0.5 * (LF_ATILE - 1)) * P.dx;
       cy = P.y0 + ((double)(ty * LF_ATILE) + 0.5 * (LF_ATILE - 1)) * P.dy;
-      h = 0.5 * (LF_ATILE - 1) * sqrt(P.dx * P.dx + P.dy * P.dy);
+      hf = 0.5f * (LF_ATILE - 1) * sqrtf((float)(P.dx * P.dx + P.dy * P.dy));
     } else {
       pid = tile * 256 + tid;
       valid = pid < P.n;
@@ -324,14 +326,13 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
       if (!(b4[2] <= -b4[3])) { b4[2] = 0.0; b4[3] = 0.0; }
       cx = 0.5 * (b4[0] - b4[1]);
       cy = 0.5 * (b4[2] - b4[3]);
-      h = 0.5 * sqrt((b4[0] + b4[1]) * (b4[0] + b4[1]) + (b4[2] + b4[3]) * (b4[2] + b4[3]));
+      hf = 0.5f * sqrtf((float)((b4[0] + b4[1]) * (b4[0] + b4[1]) + (b4[2] + b4[3]) * (b4[2] + b4[3])));
       if (!valid) { x = cx; y = cy; }
     }
     float ahx, alx, ahy, aly;
     split_ff(cx, ahx, alx);
     split_ff(cy, ahy, aly);
-    const float hf = (float)h;
-    const float thr = LF_ANCHOR_T * (float)fmin(1.0, LF_ANCHOR_H0 / fmax(h, 1e-300));
+    const float thr = LF_ANCHOR_T * fminf(1.f, LF_ANCHOR_H0 * __frcp_rn(fmaxf(hf, 1e-30f)));
 
     // ---- anchor pass: each member's record, its float-float deflection at theta0 (summed
     // over the block), and the members left to the per-position float-float path
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
           const float cs = S0 + m.sh, ca = R0 + m.ah;
           const float P0 = __fdividef(1.f, cs), Q0 = __fdividef(1.f, ca);
           const float kb0 = m.bdh * P0 * Q0 * fmaf(m.apch, __fdividef(1.f, R0 + S0), 1.f);
-          near = (3.f * kb0 * hf > thr) || ((double)u0 < 4.0 * h * h);
+          near = (3.f * kb0 * hf > thr) || (u0 < 4.f * hf * hf);
           if (!near) {
             ff ax, ay;
             member_alpha_ff(m, d0x, d0y, ax, ay);
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
       }
       // anchored when its deflection changes little across the tile: |psi_ij| <~ b / psi~ with
       // psi~ >= max(psi0~ - h, q s) over the tile, so the change is below b h / that
-      rec.anchored = ell && h <= LF_ANCHOR_H0 &&
+      rec.anchored = ell && hf <= LF_ANCHOR_H0 &&
                      C.b * hf <= LF_ANCHOR_HALO * fmaxf(rec.ps0 - hf, C.q * C.s1);
       if (rec.anchored) {
         ff ax, ay;
