@@ -71,6 +71,14 @@ LF_INLINE void ff_acc(ff& acc, float x) {
 
 LF_INLINE double ff_to_double(const ff& a) { return (double)a.hi + (double)a.lo; }
 
+// A float-float value from the lane `off` positions away (butterfly exchange; all lanes take part).
+LF_INLINE ff ff_shfl_xor(const ff& v, int off) {
+  ff r;
+  r.hi = __shfl_xor_sync(0xffffffffu, v.hi, off);
+  r.lo = __shfl_xor_sync(0xffffffffu, v.lo, off);
+  return r;
+}
+
 // Float-float arithmetic (Dekker 1971; Knuth TAOCP 4.2.2): each value is an unevaluated sum
 // hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits, built from FP32 operations and
 // the exact product error fmaf(a, b, -a b).

@@ -253,10 +253,6 @@ __host__ __device__ inline AnchorLayout anchor_layout(int nc, int nm) {
   return L;
 }
 
-__device__ __forceinline__ ff ff_shfl_xor(const ff& v, int off) {
-  return ff_make(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
-}
-
 template <bool GRID>
 __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_comp* __restrict__ comp, int nc,
                                                                   const lf_member* __restrict__ mem, int nm,
