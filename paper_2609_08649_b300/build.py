@@ -23,20 +23,25 @@ def up_to_date():
     return all(os.path.getmtime(s) <= t for s in sources())
 
 
-def build(force=False, verbose=False):
-    if not force and up_to_date():
+CHECK_LIB = os.path.join(HERE, "liblf_check.so")
+
+
+def build(force=False, verbose=False, check_bounds=False):
+    """Builds liblf.so, or with check_bounds the LF_CHECK_BOUNDS build liblf_check.so (device
+    index checks that record LF_DEVERR_BOUNDS; load it with LF_LIBRARY=<path>)."""
+    lib = CHECK_LIB if check_bounds else LIB
+    if not force and not check_bounds and up_to_date():
         return LIB
     cmd = [NVCC] + FLAGS + (["-Xptxas", "-v"] if verbose else []) + \
-        ["-o", LIB + ".tmp", os.path.join(CSRC, "lf.cu")]
+        (["-DLF_CHECK_BOUNDS=1"] if check_bounds else []) + ["-o", lib + ".tmp", os.path.join(CSRC, "lf.cu")]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
     if verbose:
         sys.stderr.write(r.stderr)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, check_bounds="--check-bounds" in sys.argv))

@@ -417,6 +417,20 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
     const int c = corder[w / spc];
     const int s = c * spc + (w % spc);
     const ClusterDesc& C = cds[c];
+#if LF_CHECK_BOUNDS
+    {
+      // the host's layout of this launch kind fits the block's window, and the image and
+      // family index arrays stay in range (a failed check skips the sample)
+      const uint32_t need = GRAD ? C.smem_grad : PASS == 1 ? C.smem_img : PASS == 2 ? C.smem_aux : C.smem;
+      bool okb = need <= lf_dyn_smem() && C.fam_off[0] == 0 && C.fam_off[C.n_fam] == C.n_img;
+      for (int f = tid; f < C.n_fam; f += blockDim.x) okb = okb && C.fam_off[f] < C.fam_off[f + 1];
+      for (int i = tid; i < C.n_img; i += blockDim.x) okb = okb && C.img_fam[i] >= 0 && C.img_fam[i] < C.n_fam;
+      if (!__syncthreads_and(LF_CHECK(okb) ? 1 : 0)) {
+        if (tid == 0) chi2[s] = NAN;
+        continue;
+      }
+    }
+#endif
     double* th = reinterpret_cast<double*>(smem + C.off_par);
     double* gacc = th + C.P;
     lf_comp* fraw = reinterpret_cast<lf_comp*>(smem + C.off_free);

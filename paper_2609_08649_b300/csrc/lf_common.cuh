@@ -1126,6 +1126,29 @@ LF_INLINE void lf_flag_error(unsigned int code) { atomicOr(&g_lf_err, code); }
 #define LF_DEVERR_TIMEOUT 1u
 #define LF_DEVERR_BADCOMP 2u
 #define LF_DEVERR_BADARG 4u    // an invalid per-item argument (e.g. a_dis outside (0, 1]) was skipped
+#define LF_DEVERR_BOUNDS 8u    // an index check of an LF_CHECK_BOUNDS build failed (the access was skipped)
+
+// Index checks of the LF_CHECK_BOUNDS build (off by default): LF_CHECK(cond) is true when the
+// condition holds; otherwise it records LF_DEVERR_BOUNDS and is false, so that the caller skips
+// the access.  In the default build it is the constant true and costs nothing.
+#ifndef LF_CHECK_BOUNDS
+#define LF_CHECK_BOUNDS 0
+#endif
+#if LF_CHECK_BOUNDS
+LF_INLINE bool lf_check(bool ok) {
+  if (!ok) lf_flag_error(LF_DEVERR_BOUNDS);
+  return ok;
+}
+#define LF_CHECK(...) lf_check((__VA_ARGS__))
+#else
+#define LF_CHECK(...) true
+#endif
+// Bytes of dynamic shared memory the running block was launched with.
+LF_INLINE uint32_t lf_dyn_smem() {
+  uint32_t v;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+  return v;
+}
 #define LF_WAIT_LIMIT (1u << 24)
 
 LF_INLINE uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }

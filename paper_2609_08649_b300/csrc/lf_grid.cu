@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_ff(const lf_comp* __re
   CompT<float>* dc = reinterpret_cast<CompT<float>*>(smem + L.dc);
   MemX* dm = reinterpret_cast<MemX*>(smem + L.dm);
   float2* tab = reinterpret_cast<float2*>(smem + 16);
+  if (!LF_CHECK(L.total <= lf_dyn_smem())) return;
   if (threadIdx.x == 0) mbar_init(bar, 1);
   init_ff_tables(tab);
   __syncthreads();
@@ -270,6 +271,7 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
   double* red = reinterpret_cast<double*>(smem + L.red);
   float2* tab = reinterpret_cast<float2*>(smem + 16);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (!LF_CHECK(L.total <= lf_dyn_smem() && blockDim.x == 256)) return;   // the host's layout
   if (tid == 0) mbar_init(bar, 1);
   init_ff_tables(tab);
   __syncthreads();
@@ -336,7 +338,7 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
     for (int k0 = 0; k0 < 2 * np; k0 += 256) {
       const int k = k0 + tid;
       bool near = false;
-      if (k < 2 * np) {
+      if (k < 2 * np && LF_CHECK((uint32_t)(k >> 1) < (uint32_t)np)) {
         AnchorPair& rec = ap[k >> 1];
         float* f = reinterpret_cast<float*>(&rec) + (k & 1);
         if (k < nm) {
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
       }
       const uint32_t word = __ballot_sync(0xffffffffu, near);
       const int wi = (k0 >> 5) + warp;
-      if (lane == 0 && wi < nw) bits[wi] = word;
+      if (lane == 0 && wi < nw && LF_CHECK(wi >= 0)) bits[wi] = word;
     }
     // elliptical isothermal components: frame offsets and psi~ at the anchor, and their
     // float-float deflection there (on the threads with the fewest member records)
@@ -482,6 +484,7 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
       while (word) {
         const int k = w * 32 + __ffs(word) - 1;
         word &= word - 1u;
+        if (!LF_CHECK(k < nm)) continue;
         ff ax, ay;
         Out5<float> o;
         eval_member_x(dm[k], pxh, pxl, pyh, pyl, ax, ay, o);
@@ -508,6 +511,7 @@ __global__ void __launch_bounds__(256) k_map_fp64(const lf_comp* __restrict__ co
   lf_member* rawm = reinterpret_cast<lf_member*>(smem + L.rawm);
   CompT<double>* dc = reinterpret_cast<CompT<double>*>(smem + L.dc);
   MemT<double>* dm = reinterpret_cast<MemT<double>*>(smem + L.dm);
+  if (!LF_CHECK(L.total <= lf_dyn_smem())) return;
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
   bool ok = stage_to_smem(rawc, comp, (uint32_t)nc * 64u, bar, 0);

@@ -236,6 +236,7 @@ extern "C" lf_status lf_device_error(void* stream) {
   if (v & LF_DEVERR_TIMEOUT) return fail(LF_ETIMEOUT, "a bounded device wait ran out");
   if (v & LF_DEVERR_BADCOMP) return fail(LF_EINVAL, "an invalid component was skipped on the device");
   if (v & LF_DEVERR_BADARG) return fail(LF_EINVAL, "an invalid per-source argument was skipped on the device");
+  if (v & LF_DEVERR_BOUNDS) return fail(LF_EINVAL, "an index check failed on the device (LF_CHECK_BOUNDS build)");
   return LF_OK;
 }
 

@@ -71,6 +71,8 @@ __global__ void __launch_bounds__(256) k_trace(MultiPlaneArgs MP, RayIO io, int 
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   float2* tab = reinterpret_cast<float2*>(smem + 16);
+  for (int j = 0; j < MP.np; ++j)
+    if (!LF_CHECK(plane_layout<T, Mem>(MP.nc[j], MP.nm[j], MP.base[j]).total <= lf_dyn_smem())) return;
   if (threadIdx.x == 0) mbar_init(bar, 1);
   init_ff_tables(tab);
   __syncthreads();
