@@ -28,13 +28,15 @@ from . import lensing as L
 from . import model as om
 
 
-def linearised(wl, theta, tobs, sinv, fam_off, fam_adis, td_scale):
+def linearised(wl, theta, tobs, sinv, fam_off, fam_adis, td_scale, create_graph=False):
     """Per image (S, N): mu at the observed image, the linearised mu_model, and the
-    linearised model arrival time T_model (days)."""
+    linearised model arrival time T_model (days).  With create_graph the results stay
+    differentiable in theta (grad mu by a second autograd pass), for the gradient of the
+    total chi^2; otherwise they are plain values."""
     theta = torch.as_tensor(theta, dtype=torch.float64)
     tobs = torch.as_tensor(tobs, dtype=torch.float64)
     S, N = theta.shape[0], tobs.shape[0]
-    with torch.no_grad():
+    with torch.set_grad_enabled(create_graph):
         pl = om.apply_params(wl, theta)[0]
         fa = om.family_adis(wl, theta, fam_adis)
     fam = torch.empty(N, dtype=torch.long)
@@ -43,13 +45,15 @@ def linearised(wl, theta, tobs, sinv, fam_off, fam_adis, td_scale):
     a = fa[:, fam]
     tx = tobs[:, 0].expand(S, N).clone().requires_grad_(True)
     ty = tobs[:, 1].expand(S, N).clone().requires_grad_(True)
-    ax, ay, pxx, pyy, pxy = L.plane_sum(pl, tx, ty)
-    det = (1.0 - a * pxx) * (1.0 - a * pyy) - (a * pxy) ** 2
-    mu = 1.0 / det
-    gx, gy = torch.autograd.grad(mu.sum(), (tx, ty))
-    with torch.no_grad():
-        tx, ty = tx.detach(), ty.detach()
-        ax, ay, pxx, pyy, pxy, mu = [v.detach() for v in (ax, ay, pxx, pyy, pxy, mu)]
+    with torch.enable_grad():
+        ax, ay, pxx, pyy, pxy = L.plane_sum(pl, tx, ty)
+        det = (1.0 - a * pxx) * (1.0 - a * pyy) - (a * pxy) ** 2
+        mu = 1.0 / det
+        gx, gy = torch.autograd.grad(mu.sum(), (tx, ty), create_graph=create_graph)
+    with torch.set_grad_enabled(create_graph):
+        if not create_graph:
+            ax, ay, pxx, pyy, pxy, mu = [v.detach() for v in (ax, ay, pxx, pyy, pxy, mu)]
+        tx, ty = tobs[:, 0].expand(S, N), tobs[:, 1].expand(S, N)
         bx, by = tx - a * ax, ty - a * ay
         beta = torch.stack([bx, by], -1)
         A = L.jac_matrix(pxx, pyy, pxy, a)
@@ -104,3 +108,18 @@ def chi2_aux(wl, theta, tobs, sinv, fam_off, fam_adis, td_scale, mag, mag_err, t
     """(chi2_flux, chi2_td) per sample."""
     _, mu_model, T = linearised(wl, theta, tobs, sinv, fam_off, fam_adis, td_scale)
     return chi2_flux(mu_model, mag, mag_err, fam_off), chi2_td(T, td, td_err, fam_off)
+
+
+def chi2_total_and_grad(wl, theta, tobs, sinv, fam_off, fam_adis, td_scale, mag, mag_err, td, td_err):
+    """The total chi^2 of Sec. 3 in its source-plane form, chi2_src + chi2_flux + chi2_td (S,),
+    and its gradient in the sampled parameters (S, P) by reverse-mode autograd through exactly
+    that FP64 computation (grad mu included, by a differentiable second pass)."""
+    th = torch.as_tensor(theta, dtype=torch.float64).clone().detach().requires_grad_(True)
+    tobs_t = torch.as_tensor(tobs, dtype=torch.float64)
+    pl = om.apply_params(wl, th)[0]
+    beta, A = L.single_plane_source_terms(pl, tobs_t, fam_off, om.family_adis(wl, th, fam_adis))
+    c_src = L.chi2_src(beta, A, sinv, fam_off)
+    _, mu_model, T = linearised(wl, th, tobs_t, sinv, fam_off, fam_adis, td_scale, create_graph=True)
+    total = c_src + chi2_flux(mu_model, mag, mag_err, fam_off) + chi2_td(T, td, td_err, fam_off)
+    (g,) = torch.autograd.grad(total.sum(), th)
+    return total.detach(), g
