@@ -266,8 +266,9 @@ typedef struct {
                                 multi-plane: [n_fam * n_planes] D_js/D_s per family  */
   /* Optional flux and time-delay measurements (Sec. 3.2-3.3; single-plane clusters; the
    * chi^2 of lf_chi2_batch then adds Eq. chi2_flux and Eq. chi2_td in their source-plane
-   * forms, with m_src and Delta t_0 per family solved analytically; no gradient).  An image
-   * takes part in a term when its value and its error are finite and the error is > 0.    */
+   * forms, with m_src and Delta t_0 per family solved analytically, and lf_chi2_grad_batch
+   * differentiates them).  An image takes part in a term when its value and its error are
+   * finite and the error is > 0.                                                            */
   const double* mag;         /* [n_img] observed magnitudes, or NULL (no flux term)          */
   const double* mag_err;     /* [n_img] magnitude errors                                      */
   const double* td;          /* [n_img] observed time delays in days (any zero point per
@@ -316,12 +317,16 @@ lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, int32_t n_cl
 lf_status lf_chi2_batch(lf_plan* plan, const double* theta, int32_t S, double* chi2,
                         void* stream);
 
-/* chi^2 and its gradient d chi^2 / d theta (device [S * P] FP64).  The source position is
- * held at its optimum (d chi^2 / d beta_model = 0), so only the explicit dependence is
- * differentiated.  Multi-plane plans run the adjoint of the recursion of Sec. 2.2 (reverse
- * sweep over the planes with the third derivatives of psi at every later plane's ray
- * positions); their per-image records must fit in shared memory next to the forward state
- * (LF_EUNSUPPORTED otherwise).  Plans with flux or time-delay terms: LF_EUNSUPPORTED. */
+/* chi^2 and its gradient d chi^2 / d theta (device [S * P] FP64).  For Eq. chi2_src the source
+ * position is held at its optimum (d chi^2 / d beta_model = 0), so only the explicit
+ * dependence is differentiated.  Multi-plane plans run the adjoint of the recursion of
+ * Sec. 2.2 (reverse sweep over the planes with the third derivatives of psi at every later
+ * plane's ray positions); their per-image records must fit in shared memory next to the
+ * forward state (LF_EUNSUPPORTED otherwise).  Plans with flux or time-delay terms add those
+ * terms to chi2 and their adjoint to grad: through the magnification (third derivatives of
+ * psi and their parameter derivatives), the arrival time (psi and its parameter derivatives)
+ * and beta_model, on which these terms do depend; such a plan whose parameters include a
+ * family's a_dis returns LF_EUNSUPPORTED. */
 lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int32_t S, double* chi2,
                              double* grad, void* stream);
 

@@ -89,6 +89,7 @@ struct ClusterDesc {
   const float4* sinv_f;            // [n_img] (xx, xy, yy, 0)
   int mpg_stride;                  // multi-plane adjoint: doubles per image record
   uint32_t off_img, off_imgd, off_fam, off_par, off_free, off_newton, off_fama, off_aux, off_mpg;
+  uint32_t off_auxg;               // adjoint of the flux / time-delay terms: per image records
   // shared memory of each launch kind: the common regions, then only the member records and
   // scratch that kind reads (source-plane chi^2; image-plane chi^2; flux / time delay; adjoint)
   uint32_t smem, smem_img, smem_aux, smem_grad;
@@ -167,36 +168,39 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
 
 // ------------------------------------------------------- dual component evaluation -
 // Unit-strength (alpha, Psi) of one explicit component and its derivatives with respect to
-// (x, y, eps, pa, core, cut) in tangent slots 0..5.
-template <class T>
-__device__ void comp_dual(const lf_comp& rc, double px, double py, Out5<Dual<T, 6>>& o) {
-  typedef Dual<T, 6> DT;
-  // offsets taken in FP64; d(dx)/dx_c = -1, d(dy)/dy_c = -1
-  DT dx = DT::cst((T)(px - rc.x)), dy = DT::cst((T)(py - rc.y));
-  dx.d[0] = (T)-1;
-  dy.d[1] = (T)-1;
-  DT pa = DT::var((T)rc.pa, 3);
+// (x, y, eps, pa, core, cut) in tangent slots 0..5, at the offset (dx0, dy0) from its centre.
+// S is the offset's scalar: T, or dual numbers over the offset itself (Dual<T, 2>), which
+// carry in addition the derivatives of Psi in position (the third derivatives of psi) and,
+// through the outer tangents, their derivatives in the fields.
+template <class T, class S>
+__device__ void comp_dual_g(const lf_comp& rc, S dx0, S dy0, Out5<Dual<S, 6>>& o) {
+  typedef Dual<S, 6> DT;
+  // d(dx)/dx_c = -1, d(dy)/dy_c = -1
+  DT dx = DT::cst(dx0), dy = DT::cst(dy0);
+  dx.d[0] = S(-1.0);
+  dy.d[1] = S(-1.0);
+  DT pa = DT::var(S(rc.pa), 3);
   if (rc.kind == LF_MULTIPOLE3) {
-    DT three = DT::cst((T)3);
+    DT three(3.0);
     multipole3(dx, dy, lf_cos(three * pa), lf_sin(three * pa), o);
     return;
   }
   if (rc.kind == LF_SHEAR) {
-    DT two = DT::cst((T)2);
+    DT two(2.0);
     DT c2 = lf_cos(two * pa), s2 = lf_sin(two * pa);
     o.ax = c2 * dx + s2 * dy;
     o.ay = s2 * dx - c2 * dy;
     o.pxx = c2; o.pyy = -c2; o.pxy = s2;
     return;
   }
-  DT core = DT::var((T)rc.core, 4);
+  DT core = DT::var(S(rc.core), 4);
   if (rc.kind == LF_NFW) {
-    nfw_sph(dx, dy, DT::cst((T)1), lf_rcp(core), o);
+    nfw_sph(dx, dy, DT(1.0), lf_rcp(core), o);
     return;
   }
   if (rc.kind == LF_ENFW) {   // unit kappa_s; tangents x, y, eps, pa and core (= r_s)
-    DT eps = DT::var((T)rc.eps, 2);
-    DT one = DT::cst((T)1), two = DT::cst((T)2);
+    DT eps = DT::var(S(rc.eps), 2);
+    DT one(1.0), two(2.0);
     DT q = (one - eps) / (one + eps);
     DT c = lf_cos(pa), sn = lf_sin(pa);
     DT irs = lf_rcp(core);
@@ -210,12 +214,12 @@ __device__ void comp_dual(const lf_comp& rc, double px, double py, Out5<Dual<T, 
   // eps = 0 is the round profile, as in the forward pass (sie_uv's q = 1 branch keeps the
   // exact first derivative in eps); else the elliptical closed form
   const bool round = rc.eps == 0.0;
-  DT eps = DT::var((T)rc.eps, 2);
-  DT one = DT::cst((T)1);
+  DT eps = DT::var(S(rc.eps), 2);
+  DT one(1.0);
   DT q = (one - eps) / (one + eps);
   DT q2 = q * q;
-  DT e = round ? DT::cst((T)0) : lf_sqrt((one - q) * (one + q));
-  DT qe = round ? DT::cst((T)0) : q / e;
+  DT e = round ? DT(0.0) : lf_sqrt((one - q) * (one + q));
+  DT qe = round ? DT(0.0) : q / e;
   DT c = lf_cos(pa), sn = lf_sin(pa);
   DT u = c * dx + sn * dy;
   DT v = c * dy - sn * dx;
@@ -223,13 +227,67 @@ __device__ void comp_dual(const lf_comp& rc, double px, double py, Out5<Dual<T, 
   DT s2 = core * core;
   sie_uv(u, v, q, q2, e, qe, core, s2, q2 * core, (one + q2) * s2, round, au, av, puu, pvv, puv);
   if (rc.kind == LF_DPIE) {
-    DT cut = DT::var((T)rc.cut, 5);
+    DT cut = DT::var(S(rc.cut), 5);
     DT c2 = cut * cut;
     DT bu, bv, quu, qvv, quv;
     sie_uv(u, v, q, q2, e, qe, cut, c2, q2 * cut, (one + q2) * c2, round, bu, bv, quu, qvv, quv);
     au = au - bu; av = av - bv; puu = puu - quu; pvv = pvv - qvv; puv = puv - quv;
   }
   rotate_back(c, sn, au, av, puu, pvv, puv, o);
+}
+
+// The same at the position (px, py), offsets taken in FP64.
+template <class T>
+__device__ void comp_dual(const lf_comp& rc, double px, double py, Out5<Dual<T, 6>>& o) {
+  comp_dual_g<T, T>(rc, (T)(px - rc.x), (T)(py - rc.y), o);
+}
+
+// The unit-strength lens potential of one explicit component (the closed forms of the forward
+// flux / time-delay pass, on raw fields) with its derivatives in the same six tangent slots.
+template <class T>
+__device__ Dual<T, 6> comp_potential_dual(const lf_comp& rc, T dx0, T dy0) {
+  typedef Dual<T, 6> DT;
+  DT dx = DT::cst(dx0), dy = DT::cst(dy0);
+  dx.d[0] = (T)-1;
+  dy.d[1] = (T)-1;
+  DT pa = DT::var((T)rc.pa, 3);
+  if (rc.kind == LF_MULTIPOLE3) {   // r^2 cos 3(phi - pa)
+    const DT r2 = dx * dx + dy * dy;
+    if (!(r2.v > (T)0)) return DT(0.0);
+    const DT ir = lf_rsqrt(r2), nx = dx * ir, ny = dy * ir;
+    const DT three(3.0);
+    const DT c3 = lf_cos(three * pa), s3 = lf_sin(three * pa);
+    return r2 * (c3 * nx * (nx * nx - three * ny * ny) + s3 * ny * (three * nx * nx - ny * ny));
+  }
+  if (rc.kind == LF_SHEAR) {
+    const DT two(2.0);
+    return DT(0.5) * lf_cos(two * pa) * (dx * dx - dy * dy) + lf_sin(two * pa) * dx * dy;
+  }
+  DT core = DT::var((T)rc.core, 4);
+  if (rc.kind == LF_NFW) return nfw_potential(dx, dy, DT(1.0), lf_rcp(core));
+  DT eps = DT::var((T)rc.eps, 2);
+  DT one(1.0);
+  DT q = (one - eps) / (one + eps);
+  DT c = lf_cos(pa), sn = lf_sin(pa);
+  if (rc.kind == LF_ENFW) {   // 2 r_s^2 psi_cse(u / r_s, v / r_s)
+    DT irs = lf_rcp(core);
+    DT u = (c * dx + sn * dy) * irs, v = (c * dy - sn * dx) * irs;
+    return DT(2.0) * core * core * enfw_potential_uv(u, v, q, q * q);
+  }
+  const bool round = rc.eps == 0.0;
+  DT q2 = q * q;
+  DT e = round ? DT(0.0) : lf_sqrt((one - q) * (one + q));
+  DT qe = round ? DT(0.0) : q / e;
+  DT u = c * dx + sn * dy;
+  DT v = c * dy - sn * dx;
+  DT s2 = core * core;
+  DT p = sie_potential_uv(u, v, q, q2, e, qe, core, s2, q2 * core, (one + q2) * s2, round);
+  if (rc.kind == LF_DPIE) {
+    DT cut = DT::var((T)rc.cut, 5);
+    DT c2 = cut * cut;
+    p = p - sie_potential_uv(u, v, q, q2, e, qe, cut, c2, q2 * cut, (one + q2) * c2, round);
+  }
+  return p;
 }
 
 template <class T, int N>
@@ -268,6 +326,12 @@ __global__ void k_chi2_prep(const ClusterDesc* __restrict__ cds, int spc, int S,
   raw[idx] = rc;
   digest_one_comp<T>(rc, reinterpret_cast<CompT<T>*>(dig)[idx]);
 }
+
+// Flux / time-delay records (doubles): per image psi, psi_xxx, psi_xxy, psi_xyy, psi_yyy, y_i,
+// d_i; per family m_src, Delta t_0 and lambda = G^-1 beta_model_bar (2); the adjoint's per-image
+// record psi_bar, T_bar (4), beta_bar (2), A_bar (00, 11, 01 + 10), (beta_model - beta)_bar (2),
+// M (00, 01, 11), one spare.
+constexpr uint32_t LF_AUXI = 7, LF_AUXF = 4, LF_AUXG = 16;
 
 // Record of one image in the mixed tiers (floats): [0..9] alpha, psi sums as float-float pairs
 // (then the five cotangents in [0..4]); [10..13] beta (x_hi, x_lo, y_hi, y_lo); [14..16] M;
@@ -879,7 +943,45 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         my += cf;
       }
     }
-    if constexpr (PASS == 2) {
+    // Per-image state of the flux / time-delay terms (one plane, FP64 from the sums): a_dis,
+    // theta, beta, beta_model, A, det A, mu, grad det A (from the third derivatives of psi at
+    // aux[LF_AUXI i + 1 ..]), beta_model - beta and A^-1 (beta_model - beta).
+    struct AuxImg {
+      double a, tx, ty, bx, by, A00, A11, A01, det, mu, gx, gy, db0, db1, dt0, dt1;
+    };
+    auto aux_image = [&](int i, const double* aux, AuxImg& q) {
+      const int f = C.img_fam[i], i0 = C.fam_off[f];
+      const double a = fa[f];
+      double sm[5], bmx, bmy;
+      if constexpr (MIXED) {
+        const float* r = imgf + i * ISF;
+        const float* r0 = imgf + i0 * ISF;
+        for (int k = 0; k < 5; ++k) sm[k] = (double)r[2 * k] + (double)r[2 * k + 1];
+        q.bx = ff_to_double(ff_make(r[10], r[11]));
+        q.by = ff_to_double(ff_make(r[12], r[13]));
+        bmx = ff_to_double(ff_make(r0[10], r0[11])) + fam[3 * f + 1];
+        bmy = ff_to_double(ff_make(r0[12], r0[13])) + fam[3 * f + 2];
+      } else {
+        const double* r = img + i * IS;
+        for (int k = 0; k < 5; ++k) sm[k] = r[k];
+        q.bx = r[8]; q.by = r[9];
+        bmx = img[i0 * IS + 8] + fam[3 * f + 1];
+        bmy = img[i0 * IS + 9] + fam[3 * f + 2];
+      }
+      q.a = a;
+      q.tx = C.theta[2 * i]; q.ty = C.theta[2 * i + 1];
+      q.A00 = 1.0 - a * sm[2]; q.A11 = 1.0 - a * sm[3]; q.A01 = -a * sm[4];
+      q.det = q.A00 * q.A11 - q.A01 * q.A01;
+      q.mu = 1.0 / q.det;
+      const double* d3 = aux + LF_AUXI * i + 1;
+      // grad det A from psi_xxx, psi_xxy, psi_xyy, psi_yyy; grad mu = -mu^2 grad det A
+      q.gx = -a * (d3[0] * q.A11 + d3[2] * q.A00) + 2.0 * a * q.A01 * d3[1];
+      q.gy = -a * (d3[1] * q.A11 + d3[3] * q.A00) + 2.0 * a * q.A01 * d3[2];
+      q.db0 = bmx - q.bx; q.db1 = bmy - q.by;
+      q.dt0 = (q.A11 * q.db0 - q.A01 * q.db1) / q.det;
+      q.dt1 = (q.A00 * q.db1 - q.A01 * q.db0) / q.det;
+    };
+    if constexpr (PASS == 2 || GRAD) {
       if (C.aux) {
         // ---- flux and time-delay terms in their source-plane forms (Sec. 3.2-3.3): psi and its
         // third derivatives at every observed image, the linearised magnification
@@ -887,6 +989,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         // K [(theta - beta_i)^2 / 2 - a psi] + K (beta_model - beta_i) . (beta_i - theta),
         // K = td_scale / a, then per family the nuisances m_src and Delta t_0
         double* aux = reinterpret_cast<double*>(smem + C.off_aux);
+        double* auxf = aux + LF_AUXI * n_img;
         __syncthreads();
         const PlaneDesc& P = C.pl[0];
         const CompT<T>* dc = reinterpret_cast<const CompT<T>*>(smem + P.off_dc);
@@ -913,74 +1016,52 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
 #pragma unroll
             for (int q = 0; q < 5; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
           if (act && k == 0)
-            for (int q = 0; q < 5; ++q) aux[6 * i + q] = v[q];
+            for (int q = 0; q < 5; ++q) aux[LF_AUXI * i + q] = v[q];
         }
         __syncthreads();
         for (int i = tid; i < n_img; i += blockDim.x) {
-          const int f = C.img_fam[i], i0 = C.fam_off[f];
-          const double a = fa[f];
-          double sm[5], bx, by, bmx, bmy;
-          if constexpr (MIXED) {
-            const float* r = imgf + i * ISF;
-            const float* r0 = imgf + i0 * ISF;
-            for (int q = 0; q < 5; ++q) sm[q] = (double)r[2 * q] + (double)r[2 * q + 1];
-            bx = ff_to_double(ff_make(r[10], r[11]));
-            by = ff_to_double(ff_make(r[12], r[13]));
-            bmx = ff_to_double(ff_make(r0[10], r0[11])) + fam[3 * f + 1];
-            bmy = ff_to_double(ff_make(r0[12], r0[13])) + fam[3 * f + 2];
-          } else {
-            const double* r = img + i * IS;
-            for (int q = 0; q < 5; ++q) sm[q] = r[q];
-            bx = r[8]; by = r[9];
-            bmx = img[i0 * IS + 8] + fam[3 * f + 1];
-            bmy = img[i0 * IS + 9] + fam[3 * f + 2];
-          }
-          const double tx = C.theta[2 * i], ty = C.theta[2 * i + 1];
-          const double A00 = 1.0 - a * sm[2], A11 = 1.0 - a * sm[3], A01 = -a * sm[4];
-          const double det = A00 * A11 - A01 * A01, mu = 1.0 / det;
-          const double* d3 = aux + 6 * i + 1;
-          // grad det A from psi_xxx, psi_xxy, psi_xyy, psi_yyy; grad mu = -mu^2 grad det A
-          const double gx = -a * (d3[0] * A11 + d3[2] * A00) + 2.0 * a * A01 * d3[1];
-          const double gy = -a * (d3[1] * A11 + d3[3] * A00) + 2.0 * a * A01 * d3[2];
-          const double db0 = bmx - bx, db1 = bmy - by;
-          const double dt0 = (A11 * db0 - A01 * db1) / det, dt1 = (A00 * db1 - A01 * db0) / det;
+          AuxImg q;
+          aux_image(i, aux, q);
           double y = 0.0, dd = 0.0;
           if (C.aux_wmag[i] > 0.0) {
-            const double mu_m = mu - mu * mu * (dt0 * gx + dt1 * gy);
+            const double mu_m = q.mu - q.mu * q.mu * (q.dt0 * q.gx + q.dt1 * q.gy);
             y = C.aux_mag[i] + 2.5 * log10(fabs(mu_m));
           }
           if (C.aux_wtd[i] > 0.0) {
-            const double Kf = C.td_scale / a;
-            const double geo = 0.5 * ((tx - bx) * (tx - bx) + (ty - by) * (ty - by));
-            const double Ti = Kf * (geo - a * aux[6 * i]) + Kf * (db0 * (bx - tx) + db1 * (by - ty));
+            const double Kf = C.td_scale / q.a;
+            const double ex = q.tx - q.bx, ey = q.ty - q.by;
+            const double geo = 0.5 * (ex * ex + ey * ey);
+            const double Ti = Kf * (geo - q.a * aux[LF_AUXI * i]) - Kf * (q.db0 * ex + q.db1 * ey);
             dd = C.aux_td[i] - Ti;
           }
-          aux[6 * i + 1] = y;
-          aux[6 * i + 2] = dd;
+          aux[LF_AUXI * i + 5] = y;
+          aux[LF_AUXI * i + 6] = dd;
         }
         __syncthreads();
         for (int f = tid; f < C.n_fam; f += blockDim.x) {
           const int i0 = C.fam_off[f], i1 = C.fam_off[f + 1];
           double wm = 0.0, ym = 0.0, wt = 0.0, yt = 0.0;
           for (int i = i0; i < i1; ++i) {
-            wm += C.aux_wmag[i]; ym += C.aux_wmag[i] * aux[6 * i + 1];
-            wt += C.aux_wtd[i]; yt += C.aux_wtd[i] * aux[6 * i + 2];
+            wm += C.aux_wmag[i]; ym += C.aux_wmag[i] * aux[LF_AUXI * i + 5];
+            wt += C.aux_wtd[i]; yt += C.aux_wtd[i] * aux[LF_AUXI * i + 6];
           }
-          double add = 0.0;
+          double add = 0.0, m_src = 0.0, t0 = 0.0;
           if (wm > 0.0) {
-            const double m_src = ym / wm;
+            m_src = ym / wm;
             for (int i = i0; i < i1; ++i) {
-              const double e = aux[6 * i + 1] - m_src;
+              const double e = aux[LF_AUXI * i + 5] - m_src;
               add += C.aux_wmag[i] * e * e;
             }
           }
           if (wt > 0.0) {
-            const double t0 = yt / wt;
+            t0 = yt / wt;
             for (int i = i0; i < i1; ++i) {
-              const double e = aux[6 * i + 2] - t0;
+              const double e = aux[LF_AUXI * i + 6] - t0;
               add += C.aux_wtd[i] * e * e;
             }
           }
+          auxf[LF_AUXF * f] = m_src;
+          auxf[LF_AUXF * f + 1] = t0;
           my += isfinite(add) ? add : INFINITY;
         }
       }
@@ -1096,6 +1177,87 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         }
         __syncthreads();
       }
+      // Adjoint of the flux / time-delay terms (one plane, FP64 from the sums).  With
+      // y_i = m_i + 2.5 log10|mu_model,i| and d_i = dt_i - T_model,i, the family nuisances are
+      // the weighted means, so y_bar = 2 w_m (y - m_src) and T_bar = -2 w_t (d - Delta t_0).
+      // Reverse sweep of mu_model = mu - mu^2 dtheta . grad det A, dtheta = A^-1 (beta_model -
+      // beta), T_model above: cotangents of psi, of its third derivatives, of beta_i, of A_i, and
+      // of beta_model, summed per family into lambda = G^-1 beta_model_bar (beta_model =
+      // G^-1 sum_j M_j beta_j, G = sum_j M_j).
+      double* auxg = reinterpret_cast<double*>(smem + C.off_auxg);
+      double* auxp = reinterpret_cast<double*>(smem + C.off_aux);
+      double* auxf = auxp + LF_AUXI * n_img;
+      if (C.np == 1 && C.aux) {
+        constexpr double LOG10E_25 = 2.5 * 0.43429448190325182765;   // 2.5 / ln 10
+        for (int i = tid; i < n_img; i += blockDim.x) {
+          const int f = C.img_fam[i];
+          AuxImg q;
+          aux_image(i, auxp, q);
+          const double* d3 = auxp + LF_AUXI * i + 1;
+          const double a = q.a;
+          const double ex = q.bx - q.tx, ey = q.by - q.ty;       // beta - theta
+          const double h = q.dt0 * q.gx + q.dt1 * q.gy;
+          const double mu_m = q.mu - q.mu * q.mu * h;
+          const double ybar = C.aux_wmag[i] > 0.0 ? 2.0 * C.aux_wmag[i] * (auxp[LF_AUXI * i + 5] - auxf[LF_AUXF * f]) : 0.0;
+          const double tbar = C.aux_wtd[i] > 0.0 ? -2.0 * C.aux_wtd[i] * (auxp[LF_AUXI * i + 6] - auxf[LF_AUXF * f + 1]) : 0.0;
+          const double mbar = ybar != 0.0 ? ybar * LOG10E_25 / mu_m : 0.0;
+          const double mubar = mbar * (1.0 - 2.0 * q.mu * h);
+          const double k = -mbar * q.mu * q.mu;
+          const double thb0 = k * q.gx, thb1 = k * q.gy;        // dtheta_bar
+          const double hb0 = k * q.dt0, hb1 = k * q.dt1;        // (grad det A)_bar
+          double* g = auxg + LF_AUXG * i;
+          // grad det A = -a (T0 A11 + T2 A00) + 2 a A01 T1, -a (T1 A11 + T3 A00) + 2 a A01 T2
+          double A00b = -a * (hb0 * d3[2] + hb1 * d3[3]);
+          double A11b = -a * (hb0 * d3[0] + hb1 * d3[1]);
+          double A01b = 2.0 * a * (hb0 * d3[1] + hb1 * d3[2]);
+          g[1] = -a * q.A11 * hb0;
+          g[2] = 2.0 * a * q.A01 * hb0 - a * q.A11 * hb1;
+          g[3] = -a * q.A00 * hb0 + 2.0 * a * q.A01 * hb1;
+          g[4] = -a * q.A00 * hb1;
+          // mu = 1 / det A
+          const double detb = -q.mu * q.mu * mubar;
+          A00b += detb * q.A11; A11b += detb * q.A00; A01b -= 2.0 * q.A01 * detb;
+          // dtheta = A^-1 db: db_bar = A^-1 dtheta_bar, A_bar -= (A^-1 dtheta_bar) dtheta^T
+          const double u00 = q.A11 * q.mu, u11 = q.A00 * q.mu, u01 = -q.A01 * q.mu;
+          const double l0 = u00 * thb0 + u01 * thb1, l1 = u01 * thb0 + u11 * thb1;
+          A00b -= l0 * q.dt0; A11b -= l1 * q.dt1; A01b -= l0 * q.dt1 + l1 * q.dt0;
+          // T_model = K [(theta - beta)^2 / 2 - a psi] + K db . (beta - theta), K = td_scale / a
+          const double K = C.td_scale / a;
+          const double dbb0 = l0 + tbar * K * ex, dbb1 = l1 + tbar * K * ey;
+          g[0] = -tbar * K * a;
+          g[5] = tbar * K * (ex + q.db0) - dbb0;                // beta_bar (db = beta_model - beta)
+          g[6] = tbar * K * (ey + q.db1) - dbb1;
+          g[7] = A00b; g[8] = A11b; g[9] = A01b;
+          g[10] = dbb0; g[11] = dbb1;
+          // M = A^-T S^-1 A^-1 in FP64
+          const double s0 = C.sinv[3 * i], s1 = C.sinv[3 * i + 1], s2 = C.sinv[3 * i + 2];
+          const double X00 = s0 * u00 + s1 * u01, X01 = s0 * u01 + s1 * u11;
+          const double X10 = s1 * u00 + s2 * u01, X11 = s1 * u01 + s2 * u11;
+          g[12] = u00 * X00 + u01 * X10;
+          g[13] = u00 * X01 + u01 * X11;
+          g[14] = u01 * X01 + u11 * X11;
+          g[15] = 0.0;
+        }
+        __syncthreads();
+        for (int f = tid; f < C.n_fam; f += blockDim.x) {
+          const int i0 = C.fam_off[f], i1 = C.fam_off[f + 1];
+          double b0 = 0.0, b1 = 0.0, G00 = 0.0, G01 = 0.0, G11 = 0.0;
+          for (int i = i0; i < i1; ++i) {
+            const double* g = auxg + LF_AUXG * i;
+            b0 += g[10]; b1 += g[11];
+            G00 += g[12]; G01 += g[13]; G11 += g[14];
+          }
+          if (i1 - i0 > 1) {      // lambda = G^-1 beta_model_bar; one image: beta_model = beta
+            const double idG = 1.0 / (G00 * G11 - G01 * G01);
+            auxf[LF_AUXF * f + 2] = (G11 * b0 - G01 * b1) * idG;
+            auxf[LF_AUXF * f + 3] = (G00 * b1 - G01 * b0) * idG;
+          } else {
+            auxf[LF_AUXF * f + 2] = b0;
+            auxf[LF_AUXF * f + 3] = b1;
+          }
+        }
+        __syncthreads();
+      }
       // cotangents of alpha and Psi at each image: with d = beta_i - beta_model, w = M d,
       // z = mu d: beta_bar = 2 w, A_bar = -2 w z^T; one plane: alpha_bar = -2 a w,
       // Psi_bar = 2 a sym(w z^T)
@@ -1166,6 +1328,33 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         const double a = fa[f];
         const double k2a = n_f > 1 ? 2.0 * a : 0.0;
         double cot[5] = {-k2a * w0, -k2a * w1, k2a * w0 * z0, k2a * w1 * z1, k2a * (w0 * z1 + w1 * z0)};
+        if (C.aux) {
+          // flux / time delay: beta_j_bar += M_j lambda and, through M_j = A_j^-T S^-1 A_j^-1,
+          // A_j_bar -= (M_j e_j)(A_j^-1 lambda)^T + (M_j lambda)(A_j^-1 e_j)^T, e_j = beta_j -
+          // beta_model; then alpha_bar = -a beta_bar, Psi_bar = -a A_bar
+          AuxImg q;
+          aux_image(i, auxp, q);
+          const double* g = auxg + LF_AUXG * i;
+          const double l0 = auxf[LF_AUXF * f + 2], l1 = auxf[LF_AUXF * f + 3];
+          double bb0 = g[5], bb1 = g[6], A00b = g[7], A11b = g[8], A01b = g[9];
+          if (n_f == 1) {
+            bb0 += l0; bb1 += l1;
+          } else {
+            const double M00_ = g[12], M01_ = g[13], M11_ = g[14];
+            const double u00 = q.A11 * q.mu, u11 = q.A00 * q.mu, u01 = -q.A01 * q.mu;
+            const double e0 = -q.db0, e1 = -q.db1;
+            const double Ml0 = M00_ * l0 + M01_ * l1, Ml1 = M01_ * l0 + M11_ * l1;
+            const double Me0 = M00_ * e0 + M01_ * e1, Me1 = M01_ * e0 + M11_ * e1;
+            const double ul0 = u00 * l0 + u01 * l1, ul1 = u01 * l0 + u11 * l1;
+            const double ue0 = u00 * e0 + u01 * e1, ue1 = u01 * e0 + u11 * e1;
+            bb0 += Ml0; bb1 += Ml1;
+            A00b -= Me0 * ul0 + Ml0 * ue0;
+            A11b -= Me1 * ul1 + Ml1 * ue1;
+            A01b -= Me0 * ul1 + Me1 * ul0 + Ml0 * ue1 + Ml1 * ue0;
+          }
+          cot[0] -= a * bb0; cot[1] -= a * bb1;
+          cot[2] -= a * A00b; cot[3] -= a * A11b; cot[4] -= a * A01b;
+        }
         if (fap[f] >= 0 && n_f > 1) {
           // a sampled a_dis: beta = theta - a alpha and A = I - a Psi give
           // d chi^2 / d a = (1/a) sum_i (alpha_bar . alpha_i + Psi_bar : Psi_i)
@@ -1211,7 +1400,13 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         const int k1 = act ? (int)((long long)K * (k + 1) / KS) : 0;
         const bool lead = (tid & 31) == 0;
         T cot[5];
+        T pb = (T)0, tb[4] = {(T)0, (T)0, (T)0, (T)0};   // flux / time delay: psi_bar, T_bar
         double px, py;
+        if (C.np == 1 && C.aux) {
+          const double* g = auxg + LF_AUXG * i;
+          pb = (T)g[0];
+          for (int q = 0; q < 4; ++q) tb[q] = (T)g[1 + q];
+        }
         if (C.np > 1) {
           const double* rj = mpg + i * MPS + 10 * j;
           for (int q = 0; q < 5; ++q) cot[q] = (T)rj[5 + q];
@@ -1233,7 +1428,27 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           // field order x, y, b, eps, pa, core, cut; tangent slots x0 y1 eps2 pa3 core4 cut5
           const int slot[7] = {0, 1, -1, 2, 3, 4, 5};
           T g[7] = {0, 0, 0, 0, 0, 0, 0};
-          if (mine) {
+          if (mine && C.aux) {
+            // with the flux / time-delay terms: also psi (its field derivatives) and the third
+            // derivatives of psi (dual numbers over the offset inside those over the fields)
+            typedef Dual<T, 2> S2;
+            const T ox = (T)(px - rc.x), oy = (T)(py - rc.y);
+            Out5<Dual<S2, 6>> o;
+            comp_dual_g<T, S2>(rc, S2::var(ox, 0), S2::var(oy, 1), o);
+            const Dual<T, 6> ps = comp_potential_dual<T>(rc, ox, oy);
+            const T b = (T)rc.b;
+            for (int fld = 0; fld < 7; ++fld) {
+              if (C.free_p[f][fld] < 0) continue;
+              const int sl = slot[fld];
+              const S2 ax = sl < 0 ? o.ax.v : o.ax.d[sl], ay = sl < 0 ? o.ay.v : o.ay.d[sl];
+              const S2 xx = sl < 0 ? o.pxx.v : o.pxx.d[sl], yy = sl < 0 ? o.pyy.v : o.pyy.d[sl];
+              const S2 xy = sl < 0 ? o.pxy.v : o.pxy.d[sl];
+              T v = cot[0] * ax.v + cot[1] * ay.v + cot[2] * xx.v + cot[3] * yy.v + cot[4] * xy.v;
+              v += pb * (sl < 0 ? ps.v : ps.d[sl]);
+              v += tb[0] * xx.d[0] + tb[1] * xx.d[1] + tb[2] * yy.d[0] + tb[3] * yy.d[1];
+              g[fld] = sl < 0 ? v : b * v;
+            }
+          } else if (mine) {
             Out5<Dual<T, 6>> o;
             comp_dual<T>(rc, px, py, o);
             const T b = (T)rc.b;
@@ -1284,9 +1499,31 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
             const T P2iS = Pq * Pq * iS, Q2iR = Qq * Qq * iR;
             const T U = ::lf_fma(cot[0], dx, ::lf_fma(cot[1], dy, cot[2] + cot[3]));
             const T V = ::lf_fma(cot[2], dxx, ::lf_fma(cot[3], dyy, cot[4] * dx * dy));
-            const T Gb = ::lf_fma(kb, U, (Q2iR - P2iS) * V);
-            const T Gs = M.b * ::lf_fma(-Pq * iS, U, P2iS * iS * ::lf_fma(Ms, iS, (T)2) * V);
-            const T Ga = M.b * ::lf_fma(Qq * iR, U, -Q2iR * iR * ::lf_fma(Ma, iR, (T)2) * V);
+            T Gb = ::lf_fma(kb, U, (Q2iR - P2iS) * V);
+            T Gs = M.b * ::lf_fma(-Pq * iS, U, P2iS * iS * ::lf_fma(Ms, iS, (T)2) * V);
+            T Ga = M.b * ::lf_fma(Qq * iR, U, -Q2iR * iR * ::lf_fma(Ma, iR, (T)2) * V);
+            if (C.aux) {
+              // flux / time delay.  psi per unit b is (S - R) - s ln(S + s) + a ln(R + a), with
+              // d/ds = -ln(S + s) and d/da = ln(R + a).  A round profile has d kbar / d(r^2) = t / 2,
+              // so psi_ijk = t (x_k delta_ij + x_j delta_ik + x_i delta_jk) + 2 t' x_i x_j x_k,
+              // t' = dt / d(r^2) = (P^2 / S^2)(P + 1 / (2S)) - (Q^2 / R^2)(Q + 1 / (2R)), and the
+              // contraction with T_bar is t W1 + 2 t' W3; t and t' on dual numbers over (s, a).
+              typedef Dual<T, 2> D2;
+              const D2 s_ = D2::var(Ms, 0), a_ = D2::var(Ma, 1);
+              const D2 Sd = lf_sqrt(s_ * s_ + D2::cst(r2));
+              const D2 Rd = lf_sqrt(a_ * a_ + D2::cst(r2));
+              const D2 iSd = lf_rcp(Sd), iRd = lf_rcp(Rd);
+              const D2 Pd = lf_rcp(Sd + s_), Qd = lf_rcp(Rd + a_);
+              const D2 P2d = Pd * Pd * iSd, Q2d = Qd * Qd * iRd;
+              const D2 td = Q2d - P2d;
+              const D2 tp = P2d * iSd * (Pd + D2(0.5) * iSd) - Q2d * iRd * (Qd + D2(0.5) * iRd);
+              const T W1 = (T)3 * (tb[0] * dx + tb[3] * dy) + tb[1] * dy + tb[2] * dx;
+              const T W3 = dxx * (tb[0] * dx + tb[1] * dy) + dyy * (tb[2] * dx + tb[3] * dy);
+              const T psi_u = (Ms - Ma) * (Ms + Ma) * ::lf_rcp(S + R) - Ms * ::lf_log(S + Ms) + Ma * ::lf_log(R + Ma);
+              Gb += pb * psi_u + td.v * W1 + (T)2 * tp.v * W3;
+              Gs += M.b * (-pb * ::lf_log(S + Ms) + td.d[0] * W1 + (T)2 * tp.d[0] * W3);
+              Ga += M.b * (pb * ::lf_log(R + Ma) + td.d[1] * W1 + (T)2 * tp.d[1] * W3);
+            }
             const T fa = Ma * inv_cut_star;
             gs[LF_S_BSTAR] += Gb * M.fb;
             gs[LF_S_LAM] += Gb * M.b * (T)2 * M.loglr;
@@ -1328,6 +1565,7 @@ struct lf_plan {
   NmWork nm;
   bool single_plane = true;
   bool has_aux = false;            // some cluster carries flux / time-delay measurements
+  bool aux_afree = false;          // ... and samples a family's a_dis (no gradient then)
   std::vector<ClusterDesc> desc;
   std::vector<double> cost;
   ClusterDesc* d_desc = nullptr;
@@ -1520,14 +1758,19 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
   C.off_newton = al(of);
   C.smem_img = al(C.off_newton + (uint32_t)C.n_img * 4u * 8u);
   // flux / time-delay pass: scalar members + per image psi, the third derivatives, y_i and d_i
+  // (LF_AUXI doubles), then per family m_src, Delta t_0 and the adjoint's lambda (LF_AUXF)
   C.off_aux = al(os);
-  C.smem_aux = al(C.off_aux + (C.aux ? (uint32_t)C.n_img * 6u * 8u : 0u));
+  const uint32_t aux_b = C.aux ? ((uint32_t)C.n_img * LF_AUXI + (uint32_t)C.n_fam * LF_AUXF) * 8u : 0u;
+  C.smem_aux = al(C.off_aux + aux_b);
   // adjoint: scalar members + (several planes) per image and plane the position theta_j (2),
   // Psi_j (3) and the cotangents of (alpha_j, Psi_j) (5); then the third derivatives of psi
-  // (4) at every plane after the first
+  // (4) at every plane after the first.  One plane with flux / time-delay terms: the forward
+  // pass's records above, then the adjoint's per-image records (LF_AUXG doubles).
   C.off_mpg = al(os);
   C.mpg_stride = C.np > 1 ? 10 * C.np + 4 * (C.np - 1) : 0;
   C.smem_grad = al(C.off_mpg + (uint32_t)C.n_img * (uint32_t)C.mpg_stride * 8u);
+  C.off_auxg = C.smem_aux;
+  if (C.aux) C.smem_grad = std::max(C.smem_grad, al(C.off_auxg + (uint32_t)C.n_img * LF_AUXG * 8u));
   int K = 0;
   for (int j = 0; j < C.np; ++j) K = std::max(K, C.pl[j].nc + C.pl[j].nm);
   C.ks = choose_ks(C.n_img, K, block, ks_cap, 2);
@@ -1932,6 +2175,7 @@ extern "C" lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, i
     else st = build_cluster(pl, clusters[c], pl->desc[c], pl->cost[c]);
     if (st == LF_OK && pl->desc[c].np > 1) pl->single_plane = false;
     if (st == LF_OK && pl->desc[c].aux) pl->has_aux = true;
+    if (st == LF_OK && pl->desc[c].aux && pl->desc[c].n_afree > 0) pl->aux_afree = true;
     if (st == LF_OK) pl->nfree_max = std::max(pl->nfree_max, pl->desc[c].n_free);
   }
   if (st == LF_OK) {
@@ -1985,7 +2229,8 @@ extern "C" lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int3
   if (plan->grad_ff) plan = plan->grad_ff;
   if (plan->smem_grad == 0)
     return fail(LF_EUNSUPPORTED, "the multi-plane adjoint's per-image records do not fit in shared memory");
-  if (plan->has_aux) return fail(LF_EUNSUPPORTED, "no gradient of the flux and time-delay terms");
+  if (plan->aux_afree)
+    return fail(LF_EUNSUPPORTED, "no gradient of the flux and time-delay terms with a sampled a_dis");
   return run(plan, theta, S, chi2, grad, stream);
 }
 

@@ -45,6 +45,10 @@ LF_INLINE float lf_acos(float x) { return acosf(x); }
 LF_INLINE double lf_acos(double x) { return acos(x); }
 LF_INLINE float lf_fma(float a, float b, float c) { return fmaf(a, b, c); }
 LF_INLINE double lf_fma(double a, double b, double c) { return fma(a, b, c); }
+LF_INLINE float lf_cos(float x) { return cosf(x); }
+LF_INLINE double lf_cos(double x) { return cos(x); }
+LF_INLINE float lf_sin(float x) { return sinf(x); }
+LF_INLINE double lf_sin(double x) { return sin(x); }
 
 template <class T> struct Out5 { T ax, ay, pxx, pyy, pxy; };
 
@@ -533,23 +537,24 @@ LF_INLINE void enfw_uv(U u, U v, U q, U q2, U& au, U& av, U& puu, U& pvv, U& puv
 // isothermal potential less its value at the centre,
 //   u alpha_u + v alpha_v + (q / (2 s)) ln(D / ((1 + q)^2 s^2))
 //     - q [s (q^2 u^2 + v^2) / P + u^2 + v^2] / (s D).
-template <class T>
-LF_INLINE T enfw_potential_uv(T u, T v, T q, T q2) {
-  const T uu = u * u, vv = v * v, r2 = uu + vv, opq2 = (T)1 + q2, opq = (T)1 + q;
-  const T w = lf_fma(q2, uu, vv);
-  T p = (T)0;
+template <class U, class T = typename scalar_of<U>::type>   // U: the arithmetic (T or dual numbers)
+LF_INLINE U enfw_potential_uv(U u, U v, U q, U q2) {
+  typedef U T_;
+  const U uu = u * u, vv = v * v, r2 = uu + vv, opq2 = (U)1 + q2, opq = (U)1 + q;
+  const U w = lf_fma(q2, uu, vv);
+  U p = (U)0;
   for (int i = 0; i < LF_CSE_N; ++i) {
-    const T s = cse_s<T>(i), s2 = s * s;
-    const T P2 = lf_fma(q2, s2 + uu, vv);
-    const T iP = lf_rsqrt(P2);
-    const T P = P2 * iP;
-    const T D = lf_fma(opq2, s2, lf_fma((T)2 * P, s, r2));
-    const T iD = lf_rcp(D);
-    const T qs = q * lf_rcp(s);
-    const T lin = qs * iP * iD * (u * u * lf_fma(q2, s, P) + vv * (P + s));   // u alpha_u + v alpha_v
-    const T lg = (T)0.5 * qs * lf_log(D * lf_rcp(opq * opq * s2));
-    const T cst = qs * iD * lf_fma(s * w, iP, r2);
-    p = lf_fma(cse_a<T>(i), lin + lg - cst, p);
+    const U s = U(cse_s<T>(i)), s2 = s * s;
+    const T_ P2 = lf_fma(q2, s2 + uu, vv);
+    const T_ iP = lf_rsqrt(P2);
+    const T_ P = P2 * iP;
+    const T_ D = lf_fma(opq2, s2, lf_fma((T_)2 * P, s, r2));
+    const T_ iD = lf_rcp(D);
+    const T_ qs = q * lf_rcp(s);
+    const T_ lin = qs * iP * iD * (u * u * lf_fma(q2, s, P) + vv * (P + s));   // u alpha_u + v alpha_v
+    const T_ lg = (T_)0.5 * qs * lf_log(D * lf_rcp(opq * opq * s2));
+    const T_ cst = qs * iD * lf_fma(s * w, iP, r2);
+    p = lf_fma(U(cse_a<T>(i)), lin + lg - cst, p);
   }
   return p;
 }
@@ -654,18 +659,11 @@ LF_INLINE void eval_member(const MemT<T>& m, T dx, T dy, Out5<T>& o) {
 //   shear: psi = (g1 (x^2 - y^2) + 2 g2 x y) / 2;  multipole: psi = A r^2 cos 3(phi - phi_3).
 template <class T>
 LF_INLINE T sie_potential_uv(T u, T v, T q, T q2, T e, T qe, T s, T s2, T q2s, T D0, bool round) {
+  // alpha from sie_uv (its round branch keeps the exact first derivative in q at q = 1, for
+  // dual numbers over eps) and psi~ in the elliptical form, equal to sqrt(s^2 + r^2) at q = 1
   T au, av, puu, pvv, puv;
-  T psit;
-  if (round) {
-    const T r2 = lf_fma(u, u, v * v);
-    psit = lf_sqrt(s2 + r2);
-    au = u * lf_rcp(psit + s);
-    av = v * lf_rcp(psit + s);
-  } else {
-    sie_uv(u, v, q, q2, e, qe, s, s2, q2s, D0, false, au, av, puu, pvv, puv);
-    psit = lf_sqrt(lf_fma(q2, s2 + u * u, v * v));
-  }
-  const T w = psit + s;
+  sie_uv(u, v, q, q2, e, qe, s, s2, q2s, D0, round, au, av, puu, pvv, puv);
+  const T w = lf_sqrt(lf_fma(q2, s2 + u * u, v * v)) + s;
   return u * au + v * av - (T)0.5 * q * s * lf_log(lf_fma(w, w, ((T)1 - q2) * u * u));
 }
 

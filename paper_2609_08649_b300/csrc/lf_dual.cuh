@@ -7,6 +7,20 @@
 
 namespace lf {
 
+// The scalar overloads, visible beside the dual ones below, so that the dual rules can call
+// the elementary functions of their value type whether it is a scalar or itself dual (dual
+// numbers nest: Dual<Dual<T, 2>, 6> carries mixed second derivatives).
+using ::lf_rcp;
+using ::lf_rsqrt;
+using ::lf_sqrt;
+using ::lf_atan;
+using ::lf_atanh;
+using ::lf_log;
+using ::lf_log1p;
+using ::lf_acos;
+using ::lf_cos;
+using ::lf_sin;
+
 template <class T, int N> struct Dual {
   T v;
   T d[N];
@@ -70,34 +84,34 @@ DUAL_T __device__ __forceinline__ bool operator>(const D& a, const D& b) { retur
 
 // Elementary functions: value from the scalar routine, derivative from the calculus rule.
 DUAL_T __device__ __forceinline__ D lf_rcp(const D& a) {
-  T r = ::lf_rcp(a.v);
+  T r = lf_rcp(a.v);
   return chain(a, r, -r * r);
 }
 DUAL_T __device__ __forceinline__ D operator/(const D& a, const D& b) { return a * lf_rcp(b); }
 DUAL_T __device__ __forceinline__ D lf_rsqrt(const D& a) {
-  T r = ::lf_rsqrt(a.v);
+  T r = lf_rsqrt(a.v);
   return chain(a, r, (T)-0.5 * r * r * r);
 }
 DUAL_T __device__ __forceinline__ D lf_sqrt(const D& a) {
-  T s = ::lf_sqrt(a.v);
-  return chain(a, s, (T)0.5 * ::lf_rcp(s));
+  T s = lf_sqrt(a.v);
+  return chain(a, s, (T)0.5 * lf_rcp(s));
 }
 DUAL_T __device__ __forceinline__ D lf_atan(const D& a) {
-  return chain(a, ::lf_atan(a.v), ::lf_rcp((T)1 + a.v * a.v));
+  return chain(a, lf_atan(a.v), lf_rcp((T)1 + a.v * a.v));
 }
 DUAL_T __device__ __forceinline__ D lf_atanh(const D& a) {
-  return chain(a, ::lf_atanh(a.v), ::lf_rcp(((T)1 - a.v) * ((T)1 + a.v)));
+  return chain(a, lf_atanh(a.v), lf_rcp(((T)1 - a.v) * ((T)1 + a.v)));
 }
-DUAL_T __device__ __forceinline__ D lf_log(const D& a) { return chain(a, ::lf_log(a.v), ::lf_rcp(a.v)); }
+DUAL_T __device__ __forceinline__ D lf_log(const D& a) { return chain(a, lf_log(a.v), lf_rcp(a.v)); }
 DUAL_T __device__ __forceinline__ D lf_log1p(const D& a) {
-  return chain(a, ::lf_log1p(a.v), ::lf_rcp((T)1 + a.v));
+  return chain(a, lf_log1p(a.v), lf_rcp((T)1 + a.v));
 }
 DUAL_T __device__ __forceinline__ D lf_acos(const D& a) {
-  return chain(a, ::lf_acos(a.v), -::lf_rsqrt(((T)1 - a.v) * ((T)1 + a.v)));
+  return chain(a, lf_acos(a.v), -lf_rsqrt(((T)1 - a.v) * ((T)1 + a.v)));
 }
 DUAL_T __device__ __forceinline__ D lf_fma(const D& a, const D& b, const D& c) { return a * b + c; }
-DUAL_T __device__ __forceinline__ D lf_cos(const D& a) { return chain(a, cos(a.v), -sin(a.v)); }
-DUAL_T __device__ __forceinline__ D lf_sin(const D& a) { return chain(a, sin(a.v), cos(a.v)); }
+DUAL_T __device__ __forceinline__ D lf_cos(const D& a) { return chain(a, lf_cos(a.v), -lf_sin(a.v)); }
+DUAL_T __device__ __forceinline__ D lf_sin(const D& a) { return chain(a, lf_sin(a.v), lf_cos(a.v)); }
 
 #undef D
 #undef DUAL_T
@@ -124,5 +138,5 @@ LF_INLINE void member_d3(T dx, T dy, T b, T s, T a, T (&d3)[4]) {
 
 }  // namespace lf
 
-template <class T, int N> struct scalar_of<lf::Dual<T, N>> { typedef T type; };
+template <class T, int N> struct scalar_of<lf::Dual<T, N>> { typedef typename scalar_of<T>::type type; };
 

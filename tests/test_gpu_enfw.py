@@ -174,6 +174,30 @@ def test_enfw_flux_and_delay_terms(lib, hera, prec):
     api.device_error()
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-7), ("ff", 1e-2)])
+def test_enfw_gradient_with_flux_and_delay_terms(lib, prec, tol):
+    """lf_chi2_grad_batch with the measurements on the eNFW + shear + m = 3 multipole model:
+    the potentials and third derivatives of every sampled component kind on dual numbers,
+    against the oracle's autograd of the total chi^2 (bounds as in test_gpu_auxterms.py)."""
+    api, PM = lib
+    wl = W.cluster_c5_enfw(n_samples=2)
+    th = W.sample_thetas(wl, wl.seed)[:2]
+    cat = W.load_catalogue("cluster_200")
+    aux = W.load_aux("cluster_200")
+    n = len(cat.theta_obs)
+    sinv = torch.tensor(np.tile([1 / wl.sigma_pos ** 2, 0, 1 / wl.sigma_pos ** 2], (n, 1)))
+    cref, gref = AX.chi2_total_and_grad(wl, th, torch.tensor(cat.theta_obs), sinv, list(cat.fam_off),
+                                        OM.single_plane_adis(wl, cat.fam_zs), cz.td_scale(wl.planes[0].z), *aux)
+    c, g = api.Plan([PM.cluster_input(wl, cat, aux=aux)], 2, prec).chi2_grad(torch.tensor(th, device="cuda"))
+    g, gref = g.cpu().numpy(), gref.numpy()
+    scale = np.maximum(np.abs(gref), 1e-2 * np.abs(gref).max(axis=1, keepdims=True))
+    e = (np.abs(g - gref) / scale).max()
+    print(f"eNFW total chi2 gradient ({prec}): error {e:.2e}")
+    assert np.all(np.abs(c.cpu().numpy() - cref.numpy()) <= {"fp64": 1e-9, "ff": 1e-3}[prec] * cref.numpy())
+    assert e < tol
+    api.device_error()
+
+
 def test_invalid_enfw_components_are_refused(lib):
     """A scale radius <= 0 or an ellipticity >= 1: a plan refuses the cluster before any launch;
     a map skips the component and raises the device error word."""
