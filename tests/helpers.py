@@ -176,3 +176,87 @@ def three_plane_images(n_src=12, seed=41, z_src=4.0, sigma=0.001):
     off = np.concatenate([[0], np.cumsum([len(f) for f in fams])]).astype(np.int32)
     obs = true + W.position_noise(seed + 1, len(true), sigma)
     return wl, W.Catalogue(obs, true, off, np.full(len(fams), z_src))
+
+
+def _abs_sums(pl, tx, ty):
+    """Per sample and position: sum_k |alpha_k| and sum_k max(|psi_xx|, |psi_yy|, |psi_xy|)_k
+    over a plane's components and members (oracle FP64).  tx, ty: (S, N)."""
+    sa = torch.zeros_like(tx)
+    sp = torch.zeros_like(tx)
+    for k, kind in enumerate(pl.kind):
+        col = lambda f: f[:, k:k + 1]
+        o = OL.component(kind, tx - col(pl.x), ty - col(pl.y), col(pl.b), col(pl.eps), col(pl.pa),
+                         col(pl.core), col(pl.cut))
+        sa += torch.hypot(o[0], o[1])
+        sp += torch.maximum(torch.maximum(o[2].abs(), o[3].abs()), o[4].abs())
+    if pl.n_members:
+        bm, cm, tm = OL.member_fields(pl)
+        for m in range(pl.n_members):
+            o = pr.pje_sph(tx - pl.mx[m], ty - pl.my[m], bm[:, m:m + 1], cm[:, m:m + 1], tm[:, m:m + 1])
+            sa += torch.hypot(o[0], o[1])
+            sp += torch.maximum(torch.maximum(o[2].abs(), o[3].abs()), o[4].abs())
+    return sa, sp
+
+
+def chi2_rounding_bound(wl, cat, theta, alpha_coef=0.0, psi_coef=4.0, alg_coef=4.0, sigma=None):
+    """First-order bound on |chi2_tier - chi2| per sample from the FP32 arithmetic of the mixed
+    tiers, single- or multi-plane, from the oracle's chi^2 differentiated (autograd) in each
+    image's beta_i and A_i:
+      |d chi2| <= sum_i |dchi2/dbeta_i| . e_i + |dchi2/dA_i| : E_i + alg_coef u sum_i |d_i|^T |M_i| |d_i|
+    with e_i = alpha_coef u sum_j rs_j sum_k |alpha_k(theta_j)| (FP32 deflections, the mixed
+    forward launch's members), E_i = psi_coef u [sum_j rs_j sum_k |psi_k(theta_j)| max|A_j| + |A_i|]
+    elementwise (psi_ij of every component in FP32; A rounded to FP32 before mu = A^-1 and
+    M = mu^T S^-1 mu, a backward error of order u |A|), and the last term the FP32 rounding of M
+    itself (d_i = beta_i - beta_model)."""
+    from oracle import gradient as OG
+    sig = wl.sigma_pos if sigma is None else sigma
+    th = torch.as_tensor(theta)
+    n = len(cat.theta_obs)
+    off = list(cat.fam_off)
+    tobs = torch.tensor(cat.theta_obs)
+    planes = OM.apply_params(wl, th)
+    zs = [p.z for p in wl.planes]
+    if len(planes) == 1:
+        a_f = OM.family_adis(wl, th, OM.single_plane_adis(wl, cat.fam_zs))
+        fam = np.concatenate([[f] * (off[f + 1] - off[f]) for f in range(len(off) - 1)])
+        rs = [a_f[:, fam]]                                     # (S, N)
+        r = [[0.0]]
+    else:
+        r, _ = cz.multiplane_ratios(zs, zs[-1] + 1.0, wl.cosmo.H0, wl.cosmo.Om)
+        fam_rs = [cz.multiplane_ratios(zs, z, wl.cosmo.H0, wl.cosmo.Om)[1] for z in cat.fam_zs]
+        rs = [v[None] for v in OL.image_ratios(fam_rs, off, len(planes))]
+    with torch.no_grad():
+        t1, alphas, psis, As = OL.multiplane_parts(planes, r, tobs[None, :, 0], tobs[None, :, 1])
+        ea = torch.zeros(th.shape[0], n, dtype=torch.float64)
+        EA = torch.zeros(th.shape[0], n, dtype=torch.float64)
+        for j, pl in enumerate(planes):
+            tj = t1.clone()
+            for i in range(j):
+                tj = tj - r[i][j] * alphas[i]
+            sa, sp = _abs_sums(pl, tj[..., 0], tj[..., 1])
+            ea += rs[j] * sa
+            EA += rs[j] * sp * As[j].abs().amax((-1, -2))
+    beta, A = OG._terms(wl, th, tobs, off, **({"fam_adis": OM.single_plane_adis(wl, cat.fam_zs)}
+                                               if len(planes) == 1 else {"fam_zs": list(cat.fam_zs)}))
+    beta = beta.detach().requires_grad_(True)
+    A = A.detach().requires_grad_(True)
+    sinv = torch.tensor(np.tile([1 / sig ** 2, 0, 1 / sig ** 2], (n, 1)))
+    c = OL.chi2_src(beta, A, sinv, off)
+    gb, gA = torch.autograd.grad(c.sum(), (beta, A))
+    with torch.no_grad():
+        Sm = OL.sinv_matrix(sinv)
+        mu = torch.linalg.inv(A)
+        M = mu.transpose(-1, -2) @ Sm[None] @ mu
+        alg = torch.zeros(th.shape[0], dtype=torch.float64)
+        for f in range(len(off) - 1):
+            i0, i1 = off[f], off[f + 1]
+            if i1 - i0 < 2:
+                continue
+            Mf, bf = M[:, i0:i1], beta[:, i0:i1]
+            bm = torch.linalg.solve(Mf.sum(1), (Mf @ bf[..., None]).sum(1))
+            d = (bf[..., None] - bm[:, None]).abs()
+            alg += (d.transpose(-1, -2) @ Mf.abs() @ d)[..., 0, 0].sum(1)
+        E = psi_coef * U32 * (EA[..., None, None] + A.abs())
+        bound = (gb.abs().sum(-1) * alpha_coef * U32 * ea).sum(1) + (gA.abs() * E).sum((-1, -2, -3)) \
+            + alg_coef * U32 * alg
+    return bound.numpy()

@@ -303,6 +303,44 @@ def test_multiplane_gradient_matches_oracle_autograd(lib, c2, prec):
     api.device_error()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "ff"])
+def test_multiplane_true_images(lib, prec):
+    """Three planes with a catalogue of true images of the model itself
+    (tests/helpers.three_plane_images: 44 images in 11 families at z = 4, every family kept,
+    magnified images with |det A| down to ~0.01 and cond A up to ~60 included), on the
+    unperturbed model (chi^2 ~ 4e-3, the catalogue's noise) and seven jittered samples.
+    FP64: the stated bounds.  Mixed tiers: near critical curves the FP32 psi_ij move chi^2 by
+    more than 1e-5 relative, so each sample is held to 1e-5 relative plus the first-order
+    rounding bound of tests/helpers.chi2_rounding_bound (FP32 psi_ij, FP32 A^-1 and M; the
+    mixed forward launch also FP32 member deflections); the float-float adjoint's gradient to
+    the stated 1e-4 per component (no image here reaches |det A| < 1e-3)."""
+    api, PM = lib
+    from tests.helpers import chi2_rounding_bound, three_plane_images
+    wl, cat = three_plane_images()
+    th = W.sample_thetas(wl, wl.seed)[:8]
+    plan = api.Plan([PM.cluster_input(wl, cat)], 8, prec)
+    t = torch.tensor(th, device="cuda")
+    c1 = plan.chi2(t).cpu().numpy()
+    c, g = plan.chi2_grad(t)
+    c = c.cpu().numpy()
+    cref, gref = oracle(wl, cat, th, grad=True)
+    cref, gref = cref.numpy(), gref.numpy()
+    r1, r = np.abs(c1 - cref) / cref, np.abs(c - cref) / cref
+    print(f"three planes, true images ({prec}): chi2 relative error per sample, forward {np.array2string(r1, precision=1)}, "
+          f"adjoint launch {np.array2string(r, precision=1)}")
+    if prec == "fp64":
+        assert r1.max() <= CHI2_TOL[prec] and r.max() <= CHI2_TOL[prec]
+    else:
+        b_ff = chi2_rounding_bound(wl, cat, th)
+        b_fwd = chi2_rounding_bound(wl, cat, th, alpha_coef=4.0) if prec == "mixed" else b_ff
+        print(f"  bounds / chi2: forward {np.array2string(b_fwd / cref, precision=1)}, "
+              f"float-float {np.array2string(b_ff / cref, precision=1)}")
+        assert np.all(np.abs(c1 - cref) <= CHI2_TOL[prec] * cref + b_fwd)
+        assert np.all(np.abs(c - cref) <= CHI2_TOL["ff"] * cref + b_ff)
+    assert grad_ok(g.cpu().numpy(), gref, prec)
+    api.device_error()
+
+
 def test_multiplane_gradient_matches_central_differences(lib, c2):
     """Float-float adjoint vs fourth-order central differences of the library's FP64 chi^2."""
     api, PM = lib
