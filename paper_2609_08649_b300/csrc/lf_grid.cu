@@ -121,8 +121,16 @@ __global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_ff(const lf_comp* __re
 // evaluated in float-float at each position.  psi_ij is FP32 as in the other mixed kernels.
 // T = LF_ANCHOR_T min(1, LF_ANCHOR_H0 / h): coarse tiles send more members to the float-float
 // path, so the precision does not depend on the pixel scale.
+// Each thread evaluates LF_AMAP_PPT positions of its tile (256 / LF_AMAP_PPT threads per
+// block): the positions share every member record load and run as independent chains.
+#ifndef LF_AMAP_PPT
+#define LF_AMAP_PPT 2
+#endif
+constexpr int LF_AMAP_THREADS = 256 / LF_AMAP_PPT;
+// Two positions: 128 registers, 4 blocks of 128 per SM (9.01 ms per 4096^2 cluster map, against
+// 9.34 ms at 5 blocks, 9.65 ms at 6, and 9.09 ms for one position per thread at 3 blocks of 256).
 #ifndef LF_ANCHOR_MINB
-#define LF_ANCHOR_MINB 3   // 80 registers, 3 blocks of 256 per SM (no spills; 4 blocks at 64 registers measured 3 % slower)
+#define LF_ANCHOR_MINB (LF_AMAP_PPT == 1 ? 3 : 4)
 #endif
 #ifndef LF_ANCHOR_T
 #define LF_ANCHOR_T 0.3f
@@ -255,9 +263,10 @@ __host__ __device__ inline AnchorLayout anchor_layout(int nc, int nm) {
 }
 
 template <bool GRID>
-__global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_comp* __restrict__ comp, int nc,
+__global__ void __launch_bounds__(LF_AMAP_THREADS, LF_ANCHOR_MINB) k_map_anchor(const lf_comp* __restrict__ comp, int nc,
                                                                   const lf_member* __restrict__ mem, int nm,
                                                                   lf_scaling sc, PosArgs P, OutArgs O, int chunk) {
+  constexpr int NT = LF_AMAP_THREADS, PPT = LF_AMAP_PPT, NWARP = NT / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   const AnchorLayout L = anchor_layout(nc, nm);
@@ -271,7 +280,7 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
   double* red = reinterpret_cast<double*>(smem + L.red);
   float2* tab = reinterpret_cast<float2*>(smem + 16);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (!LF_CHECK(L.total <= lf_dyn_smem() && blockDim.x == 256)) return;   // the host's layout
+  if (!LF_CHECK(L.total <= lf_dyn_smem() && blockDim.x == NT)) return;   // the host's layout
   if (tid == 0) mbar_init(bar, 1);
   init_ff_tables(tab);
   __syncthreads();
@@ -286,29 +295,41 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
   const long long ny = GRID ? P.n / P.nx : 0;
   const long long n_tiles = GRID ? tiles_x * ((ny + LF_ATILE - 1) / LF_ATILE) : (P.n + 255) / 256;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    // this thread's position and the tile's anchor (FP64)
-    double x, y, cx, cy;
+    // this thread's PPT positions (rows tid / 16 + 16 q / PPT of the tile, or points
+    // tile * 256 + tid + NT q) and the tile's anchor (FP64)
+    double x[PPT], y[PPT], cx, cy;
     float hf;     // the tile's half-diagonal: thresholds only, so FP32 (the FP64 pipe is slow)
-    long long pid;
-    bool valid;
+    long long pid[PPT];
+    bool valid[PPT];
     if constexpr (GRID) {
       const long long tx = tile % tiles_x, ty = tile / tiles_x;
-      const long long i = tx * LF_ATILE + (tid & (LF_ATILE - 1)), j = ty * LF_ATILE + tid / LF_ATILE;
-      valid = i < P.nx && j < ny;
-      pid = j * P.nx + i;
-      x = P.x0 + (double)i * P.dx;
-      y = P.y0 + (double)j * P.dy;
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        const int t = tid + NT * q;
+        const long long i = tx * LF_ATILE + (t & (LF_ATILE - 1)), j = ty * LF_ATILE + t / LF_ATILE;
+        valid[q] = i < P.nx && j < ny;
+        pid[q] = j * P.nx + i;
+        x[q] = P.x0 + (double)i * P.dx;
+        y[q] = P.y0 + (double)j * P.dy;
+      }
       cx = P.x0 + ((double)(tx * LF_ATILE) + 0.5 * (LF_ATILE - 1)) * P.dx;
       cy = P.y0 + ((double)(ty * LF_ATILE) + 0.5 * (LF_ATILE - 1)) * P.dy;
       hf = 0.5f * (LF_ATILE - 1) * sqrtf((float)(P.dx * P.dx + P.dy * P.dy));
     } else {
-      pid = tile * 256 + tid;
-      valid = pid < P.n;
-      x = valid ? P.pts[2 * pid] : 0.0;
-      y = valid ? P.pts[2 * pid + 1] : 0.0;
       // the tile's bounding box (non-finite positions ignored)
-      const bool fin = valid && isfinite(x) && isfinite(y);
-      double b4[4] = {fin ? x : INFINITY, fin ? -x : INFINITY, fin ? y : INFINITY, fin ? -y : INFINITY};
+      double b4[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        pid[q] = tile * 256 + tid + NT * q;
+        valid[q] = pid[q] < P.n;
+        x[q] = valid[q] ? P.pts[2 * pid[q]] : 0.0;
+        y[q] = valid[q] ? P.pts[2 * pid[q] + 1] : 0.0;
+        const bool fin = valid[q] && isfinite(x[q]) && isfinite(y[q]);
+        if (fin) {
+          b4[0] = fmin(b4[0], x[q]); b4[1] = fmin(b4[1], -x[q]);
+          b4[2] = fmin(b4[2], y[q]); b4[3] = fmin(b4[3], -y[q]);
+        }
+      }
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         for (int off = 16; off > 0; off >>= 1) b4[q] = fmin(b4[q], __shfl_xor_sync(0xffffffffu, b4[q], off));
@@ -317,7 +338,7 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
       __syncthreads();
       for (int q = 0; q < 4; ++q) {
         b4[q] = red[q];
-        for (int w = 1; w < 8; ++w) b4[q] = fmin(b4[q], red[w * 4 + q]);
+        for (int w = 1; w < NWARP; ++w) b4[q] = fmin(b4[q], red[w * 4 + q]);
       }
       __syncthreads();
       if (!(b4[0] <= -b4[1])) { b4[0] = 0.0; b4[1] = 0.0; }     // no finite position in the tile
@@ -325,7 +346,9 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
       cx = 0.5 * (b4[0] - b4[1]);
       cy = 0.5 * (b4[2] - b4[3]);
       hf = 0.5f * sqrtf((float)((b4[0] + b4[1]) * (b4[0] + b4[1]) + (b4[2] + b4[3]) * (b4[2] + b4[3])));
-      if (!valid) { x = cx; y = cy; }
+#pragma unroll
+      for (int q = 0; q < PPT; ++q)
+        if (!valid[q]) { x[q] = cx; y[q] = cy; }
     }
     float ahx, alx, ahy, aly;
     split_ff(cx, ahx, alx);
@@ -335,7 +358,7 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
     // ---- anchor pass: each member's record, its float-float deflection at theta0 (summed
     // over the block), and the members left to the per-position float-float path
     ff sax = ff_zero(), say = ff_zero();
-    for (int k0 = 0; k0 < 2 * np; k0 += 256) {
+    for (int k0 = 0; k0 < 2 * np; k0 += NT) {
       const int k = k0 + tid;
       bool near = false;
       if (k < 2 * np && LF_CHECK((uint32_t)(k >> 1) < (uint32_t)np)) {
@@ -372,7 +395,7 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
     }
     // elliptical isothermal components: frame offsets and psi~ at the anchor, and their
     // float-float deflection there (on the threads with the fewest member records)
-    for (int c = 255 - tid; c >= 0 && c < nc; c += 256) {
+    for (int c = NT - 1 - tid; c >= 0 && c < nc; c += NT) {
       const CompT<float>& C = dc[c];
       AnchorComp rec;
       const bool ell = (C.kind == K_SIE || C.kind == K_DPIE) && !C.round;
@@ -411,91 +434,115 @@ __global__ void __launch_bounds__(256, LF_ANCHOR_MINB) k_map_anchor(const lf_com
     __syncthreads();
     sax = ff_make(redf[0], redf[1]);
     say = ff_make(redf[2], redf[3]);
-    for (int w = 1; w < 8; ++w) {
+    for (int w = 1; w < NWARP; ++w) {
       sax = ff_add(sax, ff_make(redf[w * 4 + 0], redf[w * 4 + 1]));
       say = ff_add(say, ff_make(redf[w * 4 + 2], redf[w * 4 + 3]));
     }
 
-    // ---- per position: the anchored members' changes, then the float-float terms
-    const double exd = x - cx, eyd = y - cy;
-    const float ex = (float)exd, ey = (float)eyd;
-    const float exl = (float)(exd - (double)ex), eyl = (float)(eyd - (double)ey);
-    const float2 e2x = make_float2(2.f * ex, 2.f * ex), e2y = make_float2(2.f * ey, 2.f * ey);
-    const float2 ee = make_float2(fmaf(ex, ex, ey * ey), fmaf(ex, ex, ey * ey));
-    const float2 ex2 = make_float2(ex, ex), ey2 = make_float2(ey, ey);
-    ff acc[5];
+    // ---- per position: the anchored members' changes (the PPT positions share each record
+    // load and run as independent chains), then the float-float terms
+    float exl[PPT], eyl[PPT], exf[PPT], eyf[PPT];
+    float2 e2x[PPT], e2y[PPT], ee[PPT], ex2[PPT], ey2[PPT];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] = ff_zero();
+    for (int q = 0; q < PPT; ++q) {
+      const double exd = x[q] - cx, eyd = y[q] - cy;
+      const float ex = (float)exd, ey = (float)eyd;
+      exf[q] = ex; eyf[q] = ey;
+      exl[q] = (float)(exd - (double)ex); eyl[q] = (float)(eyd - (double)ey);
+      e2x[q] = make_float2(2.f * ex, 2.f * ex); e2y[q] = make_float2(2.f * ey, 2.f * ey);
+      ee[q] = make_float2(fmaf(ex, ex, ey * ey), fmaf(ex, ex, ey * ey));
+      ex2[q] = make_float2(ex, ex); ey2[q] = make_float2(ey, ey);
+    }
+    ff acc[PPT][5];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[q][v] = ff_zero();
     for (int j0 = 0; j0 < np; j0 += chunk) {
       const int j1 = min(j0 + chunk, np);
-      float2 c6[6];
+      float2 c6[PPT][6];
 #pragma unroll
-      for (int v = 0; v < 6; ++v) c6[v] = make_float2(0.f, 0.f);
+      for (int q = 0; q < PPT; ++q)
+#pragma unroll
+        for (int v = 0; v < 6; ++v) c6[q][v] = make_float2(0.f, 0.f);
+#if LF_AMAP_PPT == 1
 #pragma unroll 2
-      for (int j = j0; j < j1; ++j) anchor_pair_acc(ap[j], e2x, e2y, ee, ex2, ey2, c6);
-      const float kb = c6[2].x + c6[2].y;
-      ff_acc(acc[0], c6[0].x + c6[0].y);
-      ff_acc(acc[1], c6[1].x + c6[1].y);
-      ff_acc(acc[2], kb + (c6[3].x + c6[3].y));
-      ff_acc(acc[3], kb + (c6[5].x + c6[5].y));
-      ff_acc(acc[4], c6[4].x + c6[4].y);
-    }
-    // the anchored explicit components: their change from the anchor and their psi_ij
-    for (int c = 0; c < nc; ++c) {
-      const AnchorComp R = acp[c];
-      if (!R.anchored) continue;
-      const CompT<float>& C = dc[c];
-      const float du = fmaf(C.c, ex, C.sn * ey), dv = fmaf(C.c, ey, -C.sn * ex);
-      const float dp2 = fmaf(C.q2 * du, fmaf(2.f, R.u0, du), dv * fmaf(2.f, R.v0, dv));
-      float dau, dav, puu, pvv, puv;
-      sie_anchor_delta(R.u0, R.v0, du, dv, dp2, R.ps0, C.q, C.q2, C.e, C.qe, C.s1, C.s1sq, C.q2s1, C.D01,
-                       dau, dav, puu, pvv, puv);
-      if (C.kind == K_DPIE) {
-        float bau, bav, quu, qvv, quv;
-        sie_anchor_delta(R.u0, R.v0, du, dv, dp2, R.pa0, C.q, C.q2, C.e, C.qe, C.s2, C.s2sq, C.q2s2, C.D02,
-                         bau, bav, quu, qvv, quv);
-        dau -= bau; dav -= bav; puu -= quu; pvv -= qvv; puv -= quv;
+#endif
+      for (int j = j0; j < j1; ++j) {
+        const AnchorPair M = ap[j];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) anchor_pair_acc(M, e2x[q], e2y[q], ee[q], ex2[q], ey2[q], c6[q]);
       }
-      Out5<float> o;
-      rotate_back(C.c, C.sn, C.b * dau, C.b * dav, C.b * puu, C.b * pvv, C.b * puv, o);
-      ff_acc(acc[0], o.ax); ff_acc(acc[1], o.ay);
-      ff_acc(acc[2], o.pxx); ff_acc(acc[3], o.pyy); ff_acc(acc[4], o.pxy);
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        const float kb = c6[q][2].x + c6[q][2].y;
+        ff_acc(acc[q][0], c6[q][0].x + c6[q][0].y);
+        ff_acc(acc[q][1], c6[q][1].x + c6[q][1].y);
+        ff_acc(acc[q][2], kb + (c6[q][3].x + c6[q][3].y));
+        ff_acc(acc[q][3], kb + (c6[q][5].x + c6[q][5].y));
+        ff_acc(acc[q][4], c6[q][4].x + c6[q][4].y);
+      }
     }
-    // the offset e was rounded to FP32: first-order correction with the anchored terms' psi
-    ff_acc(acc[0], fmaf(acc[2].hi, exl, acc[4].hi * eyl));
-    ff_acc(acc[1], fmaf(acc[4].hi, exl, acc[3].hi * eyl));
-    acc[0] = ff_add(acc[0], sax);
-    acc[1] = ff_add(acc[1], say);
-    float pxh, pxl, pyh, pyl;
-    split_ff(x, pxh, pxl);
-    split_ff(y, pyh, pyl);
-    for (int c = 0; c < nc; ++c) {
-      const CompT<float>& C = dc[c];
-      if (C.kind == 0 || acp[c].anchored) continue;
-      ff ax, ay;
-      Out5<float> o;
-      eval_comp_ext(C, pxh, pxl, pyh, pyl, tab, ax, ay, o);
-      acc[0] = ff_add(acc[0], ax);
-      acc[1] = ff_add(acc[1], ay);
-      ff_acc(acc[2], o.pxx); ff_acc(acc[3], o.pyy); ff_acc(acc[4], o.pxy);
-    }
-    for (int w = 0; w < nw; ++w) {
-      uint32_t word = bits[w];
-      while (word) {
-        const int k = w * 32 + __ffs(word) - 1;
-        word &= word - 1u;
-        if (!LF_CHECK(k < nm)) continue;
+    for (int q = 0; q < PPT; ++q) {
+      const float ex = exf[q], ey = eyf[q];
+      ff* a5 = acc[q];
+      // the anchored explicit components: their change from the anchor and their psi_ij
+      for (int c = 0; c < nc; ++c) {
+        const AnchorComp R = acp[c];
+        if (!R.anchored) continue;
+        const CompT<float>& C = dc[c];
+        const float du = fmaf(C.c, ex, C.sn * ey), dv = fmaf(C.c, ey, -C.sn * ex);
+        const float dp2 = fmaf(C.q2 * du, fmaf(2.f, R.u0, du), dv * fmaf(2.f, R.v0, dv));
+        float dau, dav, puu, pvv, puv;
+        sie_anchor_delta(R.u0, R.v0, du, dv, dp2, R.ps0, C.q, C.q2, C.e, C.qe, C.s1, C.s1sq, C.q2s1, C.D01,
+                         dau, dav, puu, pvv, puv);
+        if (C.kind == K_DPIE) {
+          float bau, bav, quu, qvv, quv;
+          sie_anchor_delta(R.u0, R.v0, du, dv, dp2, R.pa0, C.q, C.q2, C.e, C.qe, C.s2, C.s2sq, C.q2s2, C.D02,
+                           bau, bav, quu, qvv, quv);
+          dau -= bau; dav -= bav; puu -= quu; pvv -= qvv; puv -= quv;
+        }
+        Out5<float> o;
+        rotate_back(C.c, C.sn, C.b * dau, C.b * dav, C.b * puu, C.b * pvv, C.b * puv, o);
+        ff_acc(a5[0], o.ax); ff_acc(a5[1], o.ay);
+        ff_acc(a5[2], o.pxx); ff_acc(a5[3], o.pyy); ff_acc(a5[4], o.pxy);
+      }
+      // the offset e was rounded to FP32: first-order correction with the anchored terms' psi
+      ff_acc(a5[0], fmaf(a5[2].hi, exl[q], a5[4].hi * eyl[q]));
+      ff_acc(a5[1], fmaf(a5[4].hi, exl[q], a5[3].hi * eyl[q]));
+      a5[0] = ff_add(a5[0], sax);
+      a5[1] = ff_add(a5[1], say);
+      float pxh, pxl, pyh, pyl;
+      split_ff(x[q], pxh, pxl);
+      split_ff(y[q], pyh, pyl);
+      for (int c = 0; c < nc; ++c) {
+        const CompT<float>& C = dc[c];
+        if (C.kind == 0 || acp[c].anchored) continue;
         ff ax, ay;
         Out5<float> o;
-        eval_member_x(dm[k], pxh, pxl, pyh, pyl, ax, ay, o);
-        acc[0] = ff_add(acc[0], ax);
-        acc[1] = ff_add(acc[1], ay);
-        ff_acc(acc[2], o.pxx); ff_acc(acc[3], o.pyy); ff_acc(acc[4], o.pxy);
+        eval_comp_ext(C, pxh, pxl, pyh, pyl, tab, ax, ay, o);
+        a5[0] = ff_add(a5[0], ax);
+        a5[1] = ff_add(a5[1], ay);
+        ff_acc(a5[2], o.pxx); ff_acc(a5[3], o.pyy); ff_acc(a5[4], o.pxy);
       }
+      for (int w = 0; w < nw; ++w) {
+        uint32_t word = bits[w];
+        while (word) {
+          const int k = w * 32 + __ffs(word) - 1;
+          word &= word - 1u;
+          if (!LF_CHECK(k < nm)) continue;
+          ff ax, ay;
+          Out5<float> o;
+          eval_member_x(dm[k], pxh, pxl, pyh, pyl, ax, ay, o);
+          a5[0] = ff_add(a5[0], ax);
+          a5[1] = ff_add(a5[1], ay);
+          ff_acc(a5[2], o.pxx); ff_acc(a5[3], o.pyy); ff_acc(a5[4], o.pxy);
+        }
+      }
+      if (valid[q])
+        write_out(O, pid[q], ff_to_double(a5[0]), ff_to_double(a5[1]), ff_to_double(a5[2]),
+                  ff_to_double(a5[3]), ff_to_double(a5[4]));
     }
-    if (valid)
-      write_out(O, pid, ff_to_double(acc[0]), ff_to_double(acc[1]), ff_to_double(acc[2]),
-                ff_to_double(acc[3]), ff_to_double(acc[4]));
     __syncthreads();     // the next tile rewrites the records, the bits and the sums
   }
 }
@@ -568,7 +615,7 @@ static lf_status launch_anchor(const lf_plane* pl, const PosArgs& P, const OutAr
   auto k = k_map_anchor<GRID>;
   LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
   int occ = 0;
-  LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 256, L.total));
+  LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, LF_AMAP_THREADS, L.total));
   long long tiles;
   if (GRID) {
     const long long ny = P.n / P.nx;
@@ -577,8 +624,8 @@ static lf_status launch_anchor(const lf_plane* pl, const PosArgs& P, const OutAr
     tiles = (P.n + 255) / 256;
   }
   const long long grid = std::min<long long>(tiles, (long long)nsm * std::max(occ, 1));
-  k<<<(unsigned)grid, 256, L.total, s>>>(pl->comp, pl->n_comp, pl->mem, pl->n_mem, pl->scaling, P, O,
-                                         LF_MAP_CHUNK);
+  k<<<(unsigned)grid, LF_AMAP_THREADS, L.total, s>>>(pl->comp, pl->n_comp, pl->mem, pl->n_mem, pl->scaling,
+                                                     P, O, LF_MAP_CHUNK);
   return LF_OK;
 }
 
