@@ -127,8 +127,9 @@ __global__ void __launch_bounds__(256, LF_MAP_MINB) k_map_ff(const lf_comp* __re
 #define LF_AMAP_PPT 2
 #endif
 constexpr int LF_AMAP_THREADS = 256 / LF_AMAP_PPT;
-// Two positions: 128 registers, 4 blocks of 128 per SM (9.01 ms per 4096^2 cluster map, against
-// 9.34 ms at 5 blocks, 9.65 ms at 6, and 9.09 ms for one position per thread at 3 blocks of 256).
+// Two positions: 128 registers, 4 blocks of 128 per SM (8.87 ms per 4096^2 cluster map with the
+// per-position tail unrolled; 9.34 ms at 5 blocks, 9.65 ms at 6, and 9.09 ms for one position per
+// thread at 3 blocks of 256).
 #ifndef LF_ANCHOR_MINB
 #define LF_ANCHOR_MINB (LF_AMAP_PPT == 1 ? 3 : 4)
 #endif
@@ -483,6 +484,7 @@ __global__ void __launch_bounds__(LF_AMAP_THREADS, LF_ANCHOR_MINB) k_map_anchor(
         ff_acc(acc[q][4], c6[q][4].x + c6[q][4].y);
       }
     }
+#pragma unroll
     for (int q = 0; q < PPT; ++q) {
       const float ex = exf[q], ey = eyf[q];
       ff* a5 = acc[q];
