@@ -71,6 +71,25 @@ def test_member_scaling_relation():
         assert abs(float(cm[0, k]) - m.core_star_kpc * apk * 10 ** (m.beta * m.log_l[k])) < 1e-12
 
 
+@pytest.mark.parametrize("lam,alpha", [(0.25, 0.5), (0.3, 0.8)])
+def test_member_mass_scales_as_luminosity_power(lam, alpha):
+    """A consequence of the scaling relations that the power laws do not restate: a core-less
+    pseudo-Jaffe member's deflection far outside its cut radius tends to b a / r (its total
+    lensing mass is proportional to b a), and b ~ v^2, so with v ~ L^lam and a ~ L^alpha the mass
+    grows as L^(2 lam + alpha), a constant mass-to-light ratio for the paper's lam = 1/4,
+    alpha = 1/2.  Measured from the full lens evaluation of one member at two luminosities."""
+    far = []
+    for log_l in (0.0, 1.0):
+        mem = W.PhysMembers(np.array([0.0]), np.array([0.0]), np.array([log_l]), vstar=220.0,
+                            core_star_kpc=0.0, cut_star_kpc=40.0, lam=lam, beta=0.5, alpha=alpha)
+        wl = W.Workload("one_member", W.Cosmo(), [W.PhysPlane(0.4, [], mem)], z_s=2.5)
+        pl = om.build_planes(wl)[0]
+        r = 1e6
+        ax = L.plane_sum(pl, torch.tensor([[r]]), torch.tensor([[0.0]]))[0]
+        far.append(float(ax[0, 0]) * r)
+    assert abs(far[1] / far[0] - 10.0 ** (2 * lam + alpha)) < 1e-4 * 10.0 ** (2 * lam + alpha)
+
+
 def test_isothermal_strength_from_velocity_dispersion():
     # b = 4 pi sigma^2 / c^2 in radians: sigma = 900 km/s -> 23.3603"
     assert abs(L.b_from_vdisp(900.0) - 23.3603) < 1e-4
