@@ -457,6 +457,9 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
   // the mixed tier's forward passes evaluate members two at a time (packed pair records, f32x2);
   // the adjoint and the flux / time-delay pass read the scalar records
   constexpr bool PACKM = (MODE == LF_MIXED) && !GRAD && PASS != 2;
+  // PASS 2: the flux / time-delay terms (the forward pass, or with GRAD their adjoint too); the
+  // other instantiations carry none of that code
+  constexpr bool AUX = PASS == 2;
   // images per evaluation task (independent chains per thread; with packed members, two
   // member evaluations per instruction and chain); the FP64 tier takes two
   constexpr int IPT = MIXED ? LF_CHI2_IPT : 2;
@@ -981,7 +984,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
       q.dt0 = (q.A11 * q.db0 - q.A01 * q.db1) / q.det;
       q.dt1 = (q.A00 * q.db1 - q.A01 * q.db0) / q.det;
     };
-    if constexpr (PASS == 2 || GRAD) {
+    if constexpr (AUX) {
       if (C.aux) {
         // ---- flux and time-delay terms in their source-plane forms (Sec. 3.2-3.3): psi and its
         // third derivatives at every observed image, the linearised magnification
@@ -1187,7 +1190,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
       double* auxg = reinterpret_cast<double*>(smem + C.off_auxg);
       double* auxp = reinterpret_cast<double*>(smem + C.off_aux);
       double* auxf = auxp + LF_AUXI * n_img;
-      if (C.np == 1 && C.aux) {
+      if (AUX && C.np == 1 && C.aux) {
         constexpr double LOG10E_25 = 2.5 * 0.43429448190325182765;   // 2.5 / ln 10
         for (int i = tid; i < n_img; i += blockDim.x) {
           const int f = C.img_fam[i];
@@ -1328,7 +1331,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         const double a = fa[f];
         const double k2a = n_f > 1 ? 2.0 * a : 0.0;
         double cot[5] = {-k2a * w0, -k2a * w1, k2a * w0 * z0, k2a * w1 * z1, k2a * (w0 * z1 + w1 * z0)};
-        if (C.aux) {
+        if (AUX && C.aux) {
           // flux / time delay: beta_j_bar += M_j lambda and, through M_j = A_j^-T S^-1 A_j^-1,
           // A_j_bar -= (M_j e_j)(A_j^-1 lambda)^T + (M_j lambda)(A_j^-1 e_j)^T, e_j = beta_j -
           // beta_model; then alpha_bar = -a beta_bar, Psi_bar = -a A_bar
@@ -1402,7 +1405,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         T cot[5];
         T pb = (T)0, tb[4] = {(T)0, (T)0, (T)0, (T)0};   // flux / time delay: psi_bar, T_bar
         double px, py;
-        if (C.np == 1 && C.aux) {
+        if (AUX && C.np == 1 && C.aux) {
           const double* g = auxg + LF_AUXG * i;
           pb = (T)g[0];
           for (int q = 0; q < 4; ++q) tb[q] = (T)g[1 + q];
@@ -1428,7 +1431,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           // field order x, y, b, eps, pa, core, cut; tangent slots x0 y1 eps2 pa3 core4 cut5
           const int slot[7] = {0, 1, -1, 2, 3, 4, 5};
           T g[7] = {0, 0, 0, 0, 0, 0, 0};
-          if (mine && C.aux) {
+          if (AUX && mine && C.aux) {
             // with the flux / time-delay terms: also psi (its field derivatives) and the third
             // derivatives of psi (dual numbers over the offset inside those over the fields)
             typedef Dual<T, 2> S2;
@@ -1502,7 +1505,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
             T Gb = ::lf_fma(kb, U, (Q2iR - P2iS) * V);
             T Gs = M.b * ::lf_fma(-Pq * iS, U, P2iS * iS * ::lf_fma(Ms, iS, (T)2) * V);
             T Ga = M.b * ::lf_fma(Qq * iR, U, -Q2iR * iR * ::lf_fma(Ma, iR, (T)2) * V);
-            if (C.aux) {
+            if (AUX && C.aux) {
               // flux / time delay.  psi per unit b is (S - R) - s ln(S + s) + a ln(R + a), with
               // d/ds = -ln(S + s) and d/da = ln(R + a).  A round profile has d kbar / d(r^2) = t / 2,
               // so psi_ijk = t (x_k delta_ij + x_j delta_ik + x_i delta_jk) + 2 t' x_i x_j x_k,
@@ -1586,7 +1589,7 @@ struct lf_plan {
   bool tuned = false;
   uint32_t smem = 0, smem_img = 0, smem_aux = 0;
   uint32_t smem_grad = 0;          // gradient launches (0: the plan has no gradient kernel)
-  int grid_chi2 = 0, grid_grad = 0, grid_aux = 0, grid_img = 0;
+  int grid_chi2 = 0, grid_grad = 0, grid_aux = 0, grid_img = 0;   // grid_grad: of the plan's gradient kernel
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -1803,9 +1806,13 @@ static lf_status relayout(lf_plan* pl) {
   const void* kc = pl->precision == LF_MIXED ? (const void*)k_chi2<LF_MIXED, false>
                    : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, false>
                                              : (const void*)k_chi2<LF_FP64, false>;
-  const void* kg = pl->precision == LF_MIXED ? nullptr     // gradient on the plan's LF_FF companion
-                   : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, true>
-                                             : (const void*)k_chi2<LF_FP64, true>;
+  // the gradient (with the flux / time-delay adjoint when the plan has measurements); a mixed
+  // plan's gradient runs on its LF_FF companion
+  const void* kg = pl->precision == LF_MIXED ? nullptr
+                   : pl->precision == LF_FF  ? (pl->has_aux ? (const void*)k_chi2<LF_FF, true, 2>
+                                                            : (const void*)k_chi2<LF_FF, true>)
+                                             : (pl->has_aux ? (const void*)k_chi2<LF_FP64, true, 2>
+                                                            : (const void*)k_chi2<LF_FP64, true>);
   const void* ki = pl->precision == LF_MIXED ? (const void*)k_chi2<LF_MIXED, false, 1>
                    : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, false, 1>
                                              : (const void*)k_chi2<LF_FP64, false, 1>;
@@ -1994,9 +2001,14 @@ static void launch_mode(lf_plan* pl, const double* theta, int S, double* chi2, d
   if (grad) {
     if constexpr (MODE != LF_MIXED) {   // a mixed plan's gradient runs on its LF_FF plan
       int g = std::min(pl->grid_grad, S);
-      k_chi2<MODE, true><<<g, pl->block, pl->smem_grad, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
-                                                         grad, pl->d_counter, g_member_chunk,
-                                                         pl->d_free_dig, pl->d_free_raw);
+      if (pl->has_aux)
+        k_chi2<MODE, true, 2><<<g, pl->block, pl->smem_grad, st>>>(pl->d_desc, pl->d_order, spc, S, theta,
+                                                              chi2, grad, pl->d_counter, g_member_chunk,
+                                                              pl->d_free_dig, pl->d_free_raw);
+      else
+        k_chi2<MODE, true><<<g, pl->block, pl->smem_grad, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
+                                                           grad, pl->d_counter, g_member_chunk,
+                                                           pl->d_free_dig, pl->d_free_raw);
     }
   } else if (pl->has_aux) {
     int g = std::min(pl->grid_aux, S);
