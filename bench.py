@@ -308,11 +308,13 @@ def main():
     fp32_ach = evals * FP32_INSTR_PER_EVAL / (ms * 1e-3) / 1e12
     xu_ach = evals * XU_INSTR_PER_EVAL / (ms * 1e-3) / 1e12
     traffic = map_kernel_traffic() if args.precision == "mixed" and args.grid == 4096 else None
-    fma_s, rsq_s, dfma_s = api.probe_alu()
+    fma_s, fma2_s, rsq_s, dfma_s = api.probe_alu2()
     roofline = {"bound": "alu", "achieved": fp32_ach, "peak": fp32_peak, "unit": "T FP32 lane-ops/s",
                 "frac": fp32_ach / fp32_peak, "traffic": traffic,
                 "xu": {"achieved": xu_ach, "peak": xu_peak, "frac": xu_ach / xu_peak},
-                "measured_rates": {"fp32_fma_T_per_s": fma_s / 1e12, "mufu_rsqrt_T_per_s": rsq_s / 1e12,
+                "measured_rates": {"fp32_fma_T_per_s": fma_s / 1e12,
+                                   "fp32_fma2_lane_T_per_s": fma2_s / 1e12,   # packed f32x2: same datapath
+                                   "mufu_rsqrt_T_per_s": rsq_s / 1e12,
                                    "fp64_fma_T_per_s": dfma_s / 1e12,
                                    "frac_of_measured_fp32": fp32_ach / (fma_s / 1e12),
                                    "frac_of_measured_xu": xu_ach / (rsq_s / 1e12)},

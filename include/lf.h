@@ -486,6 +486,12 @@ lf_status lf_selftest_wait_timeout(uint32_t polls, void* stream);
 lf_status lf_probe_alu(double* fp32_fma_per_s, double* mufu_rsqrt_per_s, double* fp64_fma_per_s,
                        void* stream);
 
+/* lf_probe_alu with one more rate: FP32 lane-operations per second of packed f32x2 FMA chains
+ * (two lanes' FMAs per instruction), or NULL to skip it.  Equal to the scalar FMA rate where the
+ * packed instructions share the FP32 datapath and save issue slots only. */
+lf_status lf_probe_alu2(double* fp32_fma_per_s, double* fp32_fma2_lanes_per_s,
+                        double* mufu_rsqrt_per_s, double* fp64_fma_per_s, void* stream);
+
 /* Reads and clears the device error word (waits for `stream`): LF_OK or LF_ETIMEOUT. */
 lf_status lf_device_error(void* stream);
 

@@ -92,6 +92,7 @@ def _load():
         "lf_mh_run": [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp],
         "lf_nm_run": [vp, vp, vp, i32, i32, vp, vp, vp, vp],
         "lf_probe_alu": [vp, vp, vp, vp],
+        "lf_probe_alu2": [vp, vp, vp, vp, vp],
         "lf_selftest_wait_timeout": [C.c_uint32, vp],
         "lf_chi2_batch_static": [vp, vp, i32, i32, vp, vp],
         "lf_plan_info": [vp, vp, vp, vp],
@@ -135,7 +136,7 @@ EXPORTS = ["lf_deflect_grid", "lf_jacobian_grid", "lf_jacobian_grid_host", "lf_j
            "lf_chi2_batch_static",
            "lf_plan_info", "lf_angular_distance", "lf_adis", "lf_arcsec_per_kpc",
            "lf_b_from_vdisp", "lf_td_scale", "lf_nfw_params", "lf_comp_from_physical", "lf_scaling_from_physical",
-           "lf_multiplane_ratios", "lf_device_error", "lf_selftest_wait_timeout", "lf_probe_alu", "lf_last_error", "lf_version"]
+           "lf_multiplane_ratios", "lf_device_error", "lf_selftest_wait_timeout", "lf_probe_alu", "lf_probe_alu2", "lf_last_error", "lf_version"]
 
 
 def check(status):

@@ -187,6 +187,13 @@ def probe_alu():
     return tuple(v.value for v in r)
 
 
+def probe_alu2():
+    """Measured (FP32 FMA, packed f32x2 FMA in lane-operations, MUFU rsqrt, FP64 FMA) per second."""
+    r = [C.c_double() for _ in range(4)]
+    L.check(L.lib.lf_probe_alu2(*[C.byref(v) for v in r], _stream()))
+    return tuple(v.value for v in r)
+
+
 def device_error():
     L.check(L.lib.lf_device_error(_stream()))
 

@@ -21,6 +21,26 @@ __global__ void k_probe_fma(float* out, float a, float b) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
+// The same FMA chains on packed f32x2 operands (fma.rn.f32x2): each instruction does two lanes'
+// work, so its lane-operation rate shows whether packing adds FP32 throughput or only saves
+// issue slots.
+__global__ void k_probe_fma2(float* out, float a, float b) {
+  const float2 A = make_float2(a, a), B = make_float2(b, b);
+  float2 x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = make_float2(threadIdx.x * 1e-3f + k, k + 0.5f);
+  for (int i = 0; i < LF_PROBE_ITERS / 2; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = __ffma2_rn(x[k], A, B);
+  }
+  float r = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) r += x[k].x + x[k].y;
+  out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
 __global__ void k_probe_rsqrt(float* out, float a) {
   float x0 = threadIdx.x * 1e-3f + 1.f, x1 = x0 + 1.f, x2 = x0 + 2.f, x3 = x0 + 3.f;
   float x4 = x0 + 4.f, x5 = x0 + 5.f, x6 = x0 + 6.f, x7 = x0 + 7.f;
@@ -72,6 +92,11 @@ extern "C" lf_status lf_selftest_wait_timeout(uint32_t polls, void* stream) {
 
 extern "C" lf_status lf_probe_alu(double* fp32_fma_per_s, double* mufu_rsqrt_per_s,
                                   double* fp64_fma_per_s, void* stream) {
+  return lf_probe_alu2(fp32_fma_per_s, nullptr, mufu_rsqrt_per_s, fp64_fma_per_s, stream);
+}
+
+extern "C" lf_status lf_probe_alu2(double* fp32_fma_per_s, double* fp32_fma2_lanes_per_s,
+                                   double* mufu_rsqrt_per_s, double* fp64_fma_per_s, void* stream) {
   if (!fp32_fma_per_s || !mufu_rsqrt_per_s || !fp64_fma_per_s) return fail(LF_EINVAL, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0, nsm = 0;
@@ -100,6 +125,9 @@ extern "C" lf_status lf_probe_alu(double* fp32_fma_per_s, double* mufu_rsqrt_per
   };
   timed([&] { k_probe_fma<<<blocks, threads, 0, st>>>((float*)buf, 0.999f, 0.001f); },
         (double)n * LF_PROBE_ITERS * 64, fp32_fma_per_s);
+  if (status == LF_OK && fp32_fma2_lanes_per_s)
+    timed([&] { k_probe_fma2<<<blocks, threads, 0, st>>>((float*)buf, 0.999f, 0.001f); },
+          (double)n * (LF_PROBE_ITERS / 2) * 128, fp32_fma2_lanes_per_s);
   if (status == LF_OK)
     timed([&] { k_probe_rsqrt<<<blocks, threads, 0, st>>>((float*)buf, 0.5f); },
           (double)n * (LF_PROBE_ITERS / 4) * 32, mufu_rsqrt_per_s);

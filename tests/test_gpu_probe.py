@@ -18,6 +18,10 @@ def test_probe_rates_are_plausible():
     assert 0 < dfma < rsq < fma
     assert fma <= nsm * 128 * clock_max and rsq <= nsm * 32 * clock_max
     assert fma > 0.3 * nsm * 128 * 1.0e9
+    # packed f32x2 FMA chains: lane-operations per second, on the same 128 FP32 lanes per SM
+    fma_b, fma2, rsq_b, dfma_b = api.probe_alu2()
+    print(f"probe: packed f32x2 FMA {fma2 / 1e12:.2f} T lane-ops/s (scalar {fma_b / 1e12:.2f})")
+    assert 0 < fma2 <= nsm * 128 * clock_max and 0 < fma_b <= nsm * 128 * clock_max
 
 
 def test_bounded_wait_runs_out_and_is_reported():
