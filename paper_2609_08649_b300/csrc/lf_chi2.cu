@@ -441,6 +441,173 @@ __device__ void d3_sum(const CompT<T>* dc, int nc, const Mem* dm, int nm, int k0
   for (int q = 0; q < 4; ++q) out[q] = (double)s3[q];
 }
 
+// M of a mixed-tier image record: FP32 words 14..16, or float-float words 14..19 when word 21
+// is set (images re-evaluated near a critical curve).
+__device__ __forceinline__ void image_M(const float* r, ff& M00, ff& M01, ff& M11) {
+  if (r[21] != 0.0f) {
+    M00 = ff_make(r[14], r[15]); M01 = ff_make(r[16], r[17]); M11 = ff_make(r[18], r[19]);
+  } else {
+    M00 = ff_make(r[14], 0.f); M01 = ff_make(r[15], 0.f); M11 = ff_make(r[16], 0.f);
+  }
+}
+
+// Near-critical refinement of the mixed tiers' source-plane chi^2: images whose |det A| (from
+// the tier's sums) is below refine_det get psi_ij with every component in float-float
+// (LF_MIXED: 3e-3, below which its FP32 member sums, not psi_ij, set the error; LF_FF: 1e-2)
+template <int MODE> __device__ __forceinline__ float refine_det() { return MODE == LF_MIXED ? 3e-3f : 1e-2f; }
+constexpr int LF_REFINE_MAX = 32;      // images per sample refined (more stay at the tier's precision)
+
+// psi_ij of a unit-strength softened isothermal ellipsoid in its (u, v) frame (the closed form of
+// sie_psi) with every operation in float-float.
+__device__ __forceinline__ void sie_psi_ff(const ff& u, const ff& v, const ff& q, const ff& q2, const ff& s,
+                                           const ff& s2, ff& puu, ff& pvv, ff& puv) {
+  const ff uu = ff_sqr(u), vv = ff_sqr(v);
+  const ff psi = ff_sqrt(ff_add(ff_mul(q2, ff_add(s2, uu)), vv));
+  const ff sp = ff_mul(s, psi);
+  const ff D = ff_add(ff_add(ff_mul(ff_add_f(q2, 1.f), s2), ff_mul_f(sp, 2.f)), ff_add(uu, vv));
+  const ff f = ff_div(q, ff_mul(psi, D));
+  puu = ff_mul(f, ff_add(ff_add(ff_mul(q2, s2), vv), sp));
+  pvv = ff_mul(f, ff_add(ff_add(s2, uu), sp));
+  puv = ff_neg(ff_mul(f, ff_mul(u, v)));
+}
+
+// psi_ij of a round pseudo-Jaffe member (kbar delta_ij + t x_i x_j, kbar = b (P - Q),
+// t = b (Q^2/R - P^2/S)) in float-float; the far-field differences lose log2(r / a) bits of
+// the 48, which leaves ~1e-12 relative.
+__device__ __forceinline__ void member_psi_ff(const ff& dx, const ff& dy, const ff& b, const ff& s,
+                                              const ff& a, ff& pxx, ff& pyy, ff& pxy) {
+  const ff r2 = ff_add(ff_sqr(dx), ff_sqr(dy));
+  const ff S = ff_sqrt(ff_add(ff_sqr(s), r2)), R = ff_sqrt(ff_add(ff_sqr(a), r2));
+  const ff P = ff_rcp(ff_add(S, s)), Q = ff_rcp(ff_add(R, a));
+  const ff kb = ff_mul(b, ff_sub(P, Q));
+  const ff t = ff_mul(b, ff_sub(ff_mul(ff_sqr(Q), ff_rcp(R)), ff_mul(ff_sqr(P), ff_rcp(S))));
+  const ff tdx = ff_mul(t, dx);
+  pxx = ff_add(kb, ff_mul(tdx, dx));
+  pyy = ff_add(kb, ff_mul(ff_mul(t, dy), dy));
+  pxy = ff_mul(tdx, dy);
+}
+
+// Member m's centre, strength, core and cut as float-float, for this sample's scaling relation.
+template <int MODE>
+__device__ __forceinline__ void member_ff(const PlaneDesc& P, int m, const lf_scaling& sc, bool lam_free,
+                                          bool beta_free, bool alpha_free, const ff& bs, const ff& cs,
+                                          const ff& as, ff& mx, ff& my, ff& b, ff& sv, ff& av) {
+  if constexpr (MODE == LF_MIXED) {
+    const MemPreF e = reinterpret_cast<const MemPreF*>(P.mpre)[m];
+    mx = ff_make(e.xh, e.xl);
+    my = ff_make(e.yh, e.yl);
+    ff fb = ff_make(e.fb, e.fbl), fs = ff_make(e.fs, e.fsl), fa = ff_make(e.fa, e.fal);
+    // a sampled exponent changes a factor by exp(d e ln L), applied as f (1 + expm1(.)): the FP32
+    // expm1 rounds only the small change
+    if (lam_free) fb = ff_add(fb, ff_mul_f(fb, expm1f((float)(2.0 * (sc.lam - P.sc.lam)) * e.lnl)));
+    if (beta_free) fs = ff_add(fs, ff_mul_f(fs, expm1f((float)(sc.beta - P.sc.beta) * e.lnl)));
+    if (alpha_free) fa = ff_add(fa, ff_mul_f(fa, expm1f((float)(sc.alpha - P.sc.alpha) * e.lnl)));
+    b = ff_mul(bs, fb); sv = ff_mul(cs, fs); av = ff_mul(as, fa);
+  } else {
+    const MemPreD e = reinterpret_cast<const MemPreD*>(P.mpre)[m];
+    mx = ff_from_double(e.x);
+    my = ff_from_double(e.y);
+    b = ff_from_double(sc.b_star * (lam_free ? exp(2.0 * sc.lam * e.lnl) : e.fb));
+    sv = ff_from_double(sc.core_star * (beta_free ? exp(sc.beta * e.lnl) : e.fs));
+    av = ff_from_double(sc.cut_star * (alpha_free ? exp(sc.alpha * e.lnl) : e.fa));
+  }
+}
+
+// This thread's share of psi_ij in float-float at image i of a single-plane cluster, for sample s.
+// The members (plan pre-table, this sample's scaling relation, Eq. scaling) go two per pass to
+// threads 0, 1, ...; the explicit components (the sample's digested table) go one ellipsoid each
+// to the last threads, which hold fewer members: an elliptical or round isothermal component or
+// either ellipsoid of a dPIE, and the shear, on the FP32 pipe; any other kind in FP64 from its
+// fields.
+template <int MODE>
+__device__ __noinline__ void refine_psi(const ClusterDesc& C, int s, const double* th, int i,
+                                        const unsigned char* smem, const lf_comp* fraw,
+                                        const lf_comp* free_raw, ff (&p)[3]) {
+  const PlaneDesc& P = C.pl[0];
+  const int nc = P.nc, nm = P.nm, B = blockDim.x, t = threadIdx.x;
+  const float4 tf = C.theta_ff[i];
+  ff a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero();
+  const CompT<float>* dc = reinterpret_cast<const CompT<float>*>(smem + P.off_dc);
+  for (int task = B - 1 - t; task < 2 * nc; task += B) {
+    const int c = task >> 1, part = task & 1;
+    const CompT<float>& cf = dc[c];
+    if (cf.kind == 0 || (part == 1 && cf.kind != K_DPIE)) continue;
+    ff pxx, pyy, pxy;
+    if (cf.kind == K_SIE || cf.kind == K_DPIE || cf.kind == K_SHEAR) {
+      const ff cc = ff_make(cf.c, cf.lc), sn = ff_make(cf.sn, cf.lsn), b = ff_make(cf.b, cf.lb);
+      if (cf.kind == K_SHEAR) {
+        pxx = ff_mul(b, cc);
+        pyy = ff_neg(pxx);
+        pxy = ff_mul(b, sn);
+      } else {
+        const ff dx = offset_ff(tf.x, tf.y, cf.xh, cf.xl), dy = offset_ff(tf.z, tf.w, cf.yh, cf.yl);
+        const ff u = ff_add(ff_mul(cc, dx), ff_mul(sn, dy)), v = ff_sub(ff_mul(cc, dy), ff_mul(sn, dx));
+        const ff q2 = ff_make(cf.q2, cf.lq2), q = ff_sqrt(q2);
+        ff puu, pvv, puv;
+        if (part == 0)
+          sie_psi_ff(u, v, q, q2, ff_make(cf.s1, cf.ls1), ff_make(cf.s1sq, cf.ls1sq), puu, pvv, puv);
+        else {            // the dPIE's cut ellipsoid, subtracted
+          sie_psi_ff(u, v, q, q2, ff_make(cf.s2, cf.ls2), ff_make(cf.s2sq, cf.ls2sq), puu, pvv, puv);
+          puu = ff_neg(puu); pvv = ff_neg(pvv); puv = ff_neg(puv);
+        }
+        const ff c2 = ff_sqr(cc), s2 = ff_sqr(sn), csn = ff_mul(cc, sn);
+        const ff cs2puv = ff_mul_f(ff_mul(csn, puv), 2.f);
+        pxx = ff_mul(b, ff_add(ff_sub(ff_mul(c2, puu), cs2puv), ff_mul(s2, pvv)));
+        pyy = ff_mul(b, ff_add(ff_add(ff_mul(s2, puu), cs2puv), ff_mul(c2, pvv)));
+        pxy = ff_mul(b, ff_add(ff_mul(csn, ff_sub(puu, pvv)), ff_mul(ff_sub(c2, s2), puv)));
+      }
+    } else {
+      const lf_comp* rawc = reinterpret_cast<const lf_comp*>(smem + P.off_rawc);
+      lf_comp rc = rawc[c];
+      for (int f = 0; f < C.n_free; ++f)
+        if (C.free_plane[f] == 0 && C.free_comp[f] == c)
+          rc = free_raw ? free_raw[(size_t)s * LF_MAX_FREE + f] : fraw[f];
+      CompT<double> cd;
+      digest_one_comp<double>(rc, cd);
+      Out5<double> o;
+      eval_comp(cd, ((double)tf.x + (double)tf.y) - cd.xh, ((double)tf.z + (double)tf.w) - cd.yh, o);
+      pxx = ff_from_double(o.pxx); pyy = ff_from_double(o.pyy); pxy = ff_from_double(o.pxy);
+    }
+    a0 = ff_add(a0, pxx); a1 = ff_add(a1, pyy); a2 = ff_add(a2, pxy);
+  }
+  if (nm > 0) {
+    lf_scaling sc = P.sc;
+    const bool sampled = (C.scal_plane == 0) && C.scal_free;
+    if (sampled) sample_scaling(C, th, sc);
+    const bool lf = sampled && C.scal_p[LF_S_LAM] >= 0, bf = sampled && C.scal_p[LF_S_BETA] >= 0;
+    const bool af = sampled && C.scal_p[LF_S_ALPHA] >= 0;
+    const ff bs = ff_from_double(sc.b_star), cs = ff_from_double(sc.core_star), as = ff_from_double(sc.cut_star);
+    for (int m = t; m < nm; m += 2 * B) {
+      const int m2 = min(m + B, nm - 1);           // the second member of the pass (a repeat is dropped)
+      ff mx, my, b, sv, av, nx, ny, nb, nsv, nav;
+      member_ff<MODE>(P, m, sc, lf, bf, af, bs, cs, as, mx, my, b, sv, av);
+      member_ff<MODE>(P, m2, sc, lf, bf, af, bs, cs, as, nx, ny, nb, nsv, nav);
+      ff pxx, pyy, pxy, qxx, qyy, qxy;
+      member_psi_ff(offset_ff(tf.x, tf.y, mx.hi, mx.lo), offset_ff(tf.z, tf.w, my.hi, my.lo), b, sv, av, pxx,
+                    pyy, pxy);
+      member_psi_ff(offset_ff(tf.x, tf.y, nx.hi, nx.lo), offset_ff(tf.z, tf.w, ny.hi, ny.lo), nb, nsv, nav,
+                    qxx, qyy, qxy);
+      a0 = ff_add(a0, pxx); a1 = ff_add(a1, pyy); a2 = ff_add(a2, pxy);
+      if (m + B < nm) { a0 = ff_add(a0, qxx); a1 = ff_add(a1, qyy); a2 = ff_add(a2, qxy); }
+    }
+  }
+  p[0] = a0; p[1] = a1; p[2] = a2;
+}
+
+// Float-float sum over the block (every thread takes part); the total is returned on thread 0.
+__device__ __forceinline__ ff block_sum_ff(ff v, ff* scratch) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = ff_add(v, ff_shfl_xor(v, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  ff r = ff_zero();
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = ff_add(r, scratch[w]);
+  return r;
+}
+
 template <int MODE, bool GRAD, int PASS = 0>   // MODE: LF_FP64, LF_MIXED or LF_FF
 __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD_THREADS : LF_CHI2_THREADS,
                                   LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD_MINB : LF_CHI2_MINB) k_chi2(const ClusterDesc* __restrict__ cds,
@@ -460,23 +627,35 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
   // PASS 2: the flux / time-delay terms (the forward pass, or with GRAD their adjoint too); the
   // other instantiations carry none of that code
   constexpr bool AUX = PASS == 2;
+  // the forward source-plane chi^2 of the mixed tiers re-evaluates near-critical images in FP64
+  constexpr bool REFINE = MIXED && PASS == 0 && !GRAD;
   // images per evaluation task (independent chains per thread; with packed members, two
   // member evaluations per instruction and chain); the FP64 tier takes two
   constexpr int IPT = MIXED ? LF_CHI2_IPT : 2;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   int* s_item = reinterpret_cast<int*>(smem + 8);
+  int* wctr = reinterpret_cast<int*>(smem + 288);           // warp-task counter (packed members)
+  int* s_nref = reinterpret_cast<int*>(smem + 292);         // near-critical images of the sample
+  int* s_ref = reinterpret_cast<int*>(smem + 296);          // ... their indices (LF_REFINE_MAX)
   double* scratch = reinterpret_cast<double*>(smem + 16);   // 32 doubles
   const int tid = threadIdx.x;
   float2* tab = reinterpret_cast<float2*>(smem + LF_TAB_OFF);
-  if (tid == 0) mbar_init(bar, 1);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    *wctr = 0;
+    *s_nref = 0;
+  }
   init_ff_tables(tab);
   __syncthreads();
   uint32_t phase = 0;
   int cur = -1;
 
   for (;;) {
-    if (tid == 0) *s_item = atomicAdd(counter, 1);
+    if (tid == 0) {
+      *s_item = atomicAdd(counter, 1);
+      *s_nref = 0;      // every thread read the previous sample's count before the barriers since
+    }
     __syncthreads();
     const int w = *s_item;
     __syncthreads();
@@ -654,6 +833,111 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
       const CompT<T>* dc = reinterpret_cast<const CompT<T>*>(smem + P.off_dc);
       const Mem* dm = reinterpret_cast<const Mem*>(smem + P.off_dm);
       const int K = P.nc + (PACKM ? (int)mem_records<MemPair>(P.nm) : P.nm);   // slices of these units
+      // position of image i on plane j as float-float (observed, given, or the recursion's theta_j)
+      auto image_pos = [&](int i, float& xh, float& xl, float& yh, float& yl) {
+        if (j == 0 && !pos) {
+          const float4 tf = C.theta_ff[i];
+          xh = tf.x; xl = tf.y; yh = tf.z; yl = tf.w;
+        } else if (j == 0) {
+          split_ff(pos[4 * i], xh, xl);
+          split_ff(pos[4 * i + 1], yh, yl);
+        } else {
+          split_ff(imgd[i * ISD + 0], xh, xl);
+          split_ff(imgd[i * ISD + 1], yh, yl);
+        }
+      };
+      if constexpr (PACKM) {
+        // Warp tasks taken from a block counter, most expensive first: groups of 32 member tasks
+        // (the main (image pair, slice) tasks, then the tail group), then groups of 32 images
+        // whose explicit components (float-float halos, shear, ...) one lane each evaluates.  The
+        // member warps do no explicit work, so the warps that finish their member groups early
+        // (the tail group's) take the explicit groups instead of waiting at the barrier.
+        const MemPair* dp = reinterpret_cast<const MemPair*>(smem + P.off_dmp);
+        const int K2 = (int)mem_records<MemPair>(P.nm);
+        const int lane = tid & 31;
+        const int n_mw = (ntask + 31) / 32;
+        const int n_wt = n_mw + (P.nc > 0 ? (n_img + 31) / 32 : 0);
+        for (;;) {
+          int wt = 0;
+          if (lane == 0) wt = atomicAdd(wctr, 1);
+          wt = __shfl_sync(0xffffffffu, wt, 0);
+          if (wt >= n_wt) break;
+          if (wt < n_mw) {
+            const int t = 32 * wt + lane;
+            const bool act = t < ntask;
+            const bool tail = t >= t_main;
+            const int ks = tail ? KST : KS;             // uniform over each group
+            const int tt = tail ? t - t_main : t;
+            const int pr = act ? (tail ? n_main + tt / KST : tt / KS) : 0;
+            const int k = act ? (tail ? tt - (pr - n_main) * KST : tt - pr * KS) : 0;
+            const int k0 = (int)((long long)K2 * k / ks), k1 = (int)((long long)K2 * (k + 1) / ks);
+            float xh[IPT], xl[IPT], yh[IPT], yl[IPT];
+            int ii[IPT];
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+              ii[q] = min(IPT * pr + q, n_img - 1);
+              image_pos(ii[q], xh[q], xl[q], yh[q], yl[q]);
+            }
+            ff acc[5][IPT];
+#pragma unroll
+            for (int c5 = 0; c5 < 5; ++c5)
+#pragma unroll
+              for (int q = 0; q < IPT; ++q) acc[c5][q] = ff_zero();
+            if (act) accumulate_packed<IPT>(dp, P.nm, k0, k1, chunk, xh, xl, yh, yl, acc);
+            for (int off = 1; off < ks; off <<= 1)
+#pragma unroll
+              for (int c5 = 0; c5 < 5; ++c5)
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) acc[c5][q] = ff_add(acc[c5][q], ff_shfl_xor(acc[c5][q], off));
+            if (act && k == 0) {
+#pragma unroll
+              for (int q = 0; q < IPT; ++q) {
+                if (q > 0 && ii[q] == ii[q - 1]) break;     // the clamped repeats of the last unit
+                for (int c5 = 0; c5 < 5; ++c5) {
+                  imgf[ii[q] * ISF + 2 * c5] = acc[c5][q].hi;
+                  imgf[ii[q] * ISF + 2 * c5 + 1] = acc[c5][q].lo;
+                }
+              }
+            }
+          } else {
+            const int i = 32 * (wt - n_mw) + lane;
+            if (i < n_img) {
+              float xh, xl, yh, yl;
+              image_pos(i, xh, xl, yh, yl);
+              ff e5[5];
+              for (int c5 = 0; c5 < 5; ++c5) e5[c5] = ff_zero();
+              for (int c = 0; c < P.nc; ++c) {
+                const CompT<float>& Cc = dc[c];
+                if (Cc.kind == 0) continue;
+                ff ax, ay;
+                Out5<float> o;
+                eval_comp_mixed(Cc, xh, xl, yh, yl, tab, ax, ay, o);
+                e5[0] = ff_add(e5[0], ax);
+                e5[1] = ff_add(e5[1], ay);
+                ff_acc(e5[2], o.pxx); ff_acc(e5[3], o.pyy); ff_acc(e5[4], o.pxy);
+              }
+              for (int c5 = 0; c5 < 5; ++c5) {
+                imgf[i * ISF + 10 + 2 * c5] = e5[c5].hi;
+                imgf[i * ISF + 11 + 2 * c5] = e5[c5].lo;
+              }
+            }
+          }
+        }
+        __syncthreads();
+        if (P.nc > 0) {
+          // explicit components' sums into the members' (record words 10..19 are free until the
+          // per-image algebra writes them)
+          for (int i = tid; i < n_img; i += blockDim.x) {
+            float* r = imgf + i * ISF;
+            for (int c5 = 0; c5 < 5; ++c5) {
+              const ff v = ff_add(ff_make(r[2 * c5], r[2 * c5 + 1]), ff_make(r[10 + 2 * c5], r[11 + 2 * c5]));
+              r[2 * c5] = v.hi;
+              r[2 * c5 + 1] = v.lo;
+            }
+          }
+        }
+        if (tid == 0) *wctr = 0;      // for the next plane (the barrier below orders it)
+      } else
       for (int base = 0; base < ntask; base += blockDim.x) {
         const int t = base + tid;
         const bool act = t < ntask;
@@ -691,11 +975,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
             if constexpr (MODE == LF_FF)
               accumulate_ext<IPT>(dc, P.nc, dm, P.nm, k0, k1, xh, xl, yh, yl, tab, acc);
             else
-              if constexpr (PACKM)
-                accumulate_packed<IPT>(dc, P.nc, reinterpret_cast<const MemPair*>(smem + P.off_dmp), P.nm,
-                                       k0, k1, chunk, xh, xl, yh, yl, tab, acc);
-              else
-                accumulate_mixed<IPT>(dc, P.nc, dm, P.nm, k0, k1, chunk, xh, xl, yh, yl, tab, acc);
+              accumulate_mixed<IPT>(dc, P.nc, dm, P.nm, k0, k1, chunk, xh, xl, yh, yl, tab, acc);
           }
           for (int off = 1; off < ks; off <<= 1)
 #pragma unroll
@@ -808,6 +1088,11 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           const ff A01 = ff_neg(ff_mul(a, ff_make(r[8], r[9])));
           det = ff_sub(ff_mul(A00, A11), ff_sqr(A01)).hi;
           a00 = A00.hi; a11 = A11.hi; a01 = a10 = A01.hi;
+          if constexpr (REFINE)
+            if (fabsf(det) < refine_det<MODE>()) {
+              const int q = atomicAdd(s_nref, 1);
+              if (q < LF_REFINE_MAX) s_ref[q] = i;
+            }
         } else {
           const double* st = imgd + i * ISD;
           double dbx = C.theta[2 * i], dby = C.theta[2 * i + 1];
@@ -833,8 +1118,59 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         r[15] = fmaf(m00, X01, m10 * X11);
         r[16] = fmaf(m01, X01, m11 * X11);
         r[17] = m00; r[18] = m01; r[19] = m10; r[20] = m11;
+        r[21] = 0.0f;                 // M in FP32 words 14..16
       }
       __syncthreads();
+      if constexpr (REFINE) {
+        // Images within |det A| < refine_det of a critical curve: psi_ij again with every
+        // component in float-float, and A, mu and M from them (beta is kept).  Near a critical
+        // curve M ~ mu^2 / sigma^2 is nearly of rank one, and its weak direction, which carries
+        // the family's chi^2, is lost with FP32 psi_ij (through det A) and FP32 words of M.  The
+        // FP32 rounding of beta moves chi^2 only by 2 (M d) . d beta, which stays small: the
+        // family's sum of M_i d_i is zero at beta_model.
+        const int nref = C.np == 1 ? min(*s_nref, LF_REFINE_MAX) : 0;
+        for (int q = 0; q < nref; ++q) {
+          const int i = s_ref[q];
+          ff p3[3];
+          refine_psi<MODE>(C, s, th, i, smem, fraw, free_dig ? free_raw : nullptr, p3);
+          ff* fsc = reinterpret_cast<ff*>(scratch);
+          ff tot[3];
+          for (int c3 = 0; c3 < 3; ++c3) tot[c3] = block_sum_ff(p3[c3], fsc);
+          if (tid == 0)
+            for (int c3 = 0; c3 < 3; ++c3) fsc[16 + c3] = tot[c3];
+          __syncthreads();
+          if (tid < 3) {
+            // M = adj(A) S^-1 adj(A) / det(A)^2 (A symmetric), one element per thread
+            float* r = imgf + i * ISF;
+            const float2 afa = faf[C.img_fam[i]];
+            const ff a = ff_make(afa.x, afa.y);
+            const ff A00 = ff_add_f(ff_neg(ff_mul(a, fsc[16])), 1.0f);
+            const ff A11 = ff_add_f(ff_neg(ff_mul(a, fsc[17])), 1.0f);
+            const ff A01 = ff_neg(ff_mul(a, fsc[18]));
+            const ff det = ff_sub(ff_mul(A00, A11), ff_sqr(A01));
+            const ff inv2 = ff_rcp(ff_sqr(det));
+            const float4 sv = C.sinv_f[i];
+            // T = S^-1 adj(A), adj(A) = [[A11, -A01], [-A01, A00]]
+            ff N;
+            if (tid == 0) {
+              const ff T00 = ff_sub(ff_mul_f(A11, sv.x), ff_mul_f(A01, sv.y));
+              const ff T10 = ff_sub(ff_mul_f(A11, sv.y), ff_mul_f(A01, sv.z));
+              N = ff_sub(ff_mul(A11, T00), ff_mul(A01, T10));
+              r[4] = fsc[16].hi; r[5] = fsc[16].lo; r[6] = fsc[17].hi; r[7] = fsc[17].lo;
+              r[8] = fsc[18].hi; r[9] = fsc[18].lo;
+              r[21] = 1.0f;     // M in float-float words 14..19 (the forward pass reads no mu)
+            } else {
+              const ff T01 = ff_sub(ff_mul_f(A00, sv.y), ff_mul_f(A01, sv.x));
+              const ff T11 = ff_sub(ff_mul_f(A00, sv.z), ff_mul_f(A01, sv.y));
+              N = tid == 1 ? ff_sub(ff_mul(A11, T01), ff_mul(A01, T11)) : ff_sub(ff_mul(A00, T11), ff_mul(A01, T01));
+            }
+            const ff M = ff_mul(N, inv2);
+            r[14 + 2 * tid] = M.hi;
+            r[15 + 2 * tid] = M.lo;
+          }
+        }
+        if (nref > 0) __syncthreads();
+      }
       // ---- A8 (mixed tiers): per family, offsets e_i = beta_i - beta_ref from the family's
       // first image, G = sum M_i, g = sum M_i e_i, the 2x2 solve and chi^2_f, all in
       // float-float on the FP32 pipe (the FP64 pipe is the slow one on this part).  The
@@ -848,9 +1184,11 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         for (int i = i0; i < i1; ++i) {
           const float* r = imgf + i * ISF;
           const ff e0 = ff_sub(ff_make(r[10], r[11]), br0), e1 = ff_sub(ff_make(r[12], r[13]), br1);
-          ff_acc(G00, r[14]); ff_acc(G01, r[15]); ff_acc(G11, r[16]);
-          g0 = ff_add(g0, ff_add(ff_mul_f(e0, r[14]), ff_mul_f(e1, r[15])));
-          g1 = ff_add(g1, ff_add(ff_mul_f(e0, r[15]), ff_mul_f(e1, r[16])));
+          ff M00, M01, M11;
+          image_M(r, M00, M01, M11);
+          G00 = ff_add(G00, M00); G01 = ff_add(G01, M01); G11 = ff_add(G11, M11);
+          g0 = ff_add(g0, ff_add(ff_mul(e0, M00), ff_mul(e1, M01)));
+          g1 = ff_add(g1, ff_add(ff_mul(e0, M01), ff_mul(e1, M11)));
         }
         double cf = 0.0, c0 = 0.0, c1 = 0.0;
         if (i1 - i0 == 1) {
@@ -865,8 +1203,10 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
             const float* r = imgf + i * ISF;
             const ff d0 = ff_sub(ff_sub(ff_make(r[10], r[11]), br0), cx);
             const ff d1 = ff_sub(ff_sub(ff_make(r[12], r[13]), br1), cy);
-            acc = ff_add(acc, ff_add(ff_mul_f(ff_sqr(d0), r[14]),
-                                     ff_add(ff_mul_f(ff_mul(d0, d1), 2.f * r[15]), ff_mul_f(ff_sqr(d1), r[16]))));
+            ff M00, M01, M11;
+            image_M(r, M00, M01, M11);
+            acc = ff_add(acc, ff_add(ff_mul(ff_sqr(d0), M00),
+                                     ff_add(ff_mul_f(ff_mul(ff_mul(d0, d1), M01), 2.f), ff_mul(ff_sqr(d1), M11))));
           }
           cf = ff_to_double(acc);
           c0 = ff_to_double(cx);
@@ -2019,7 +2359,7 @@ static void launch_mode(lf_plan* pl, const double* theta, int S, double* chi2, d
     int g = std::min(pl->grid_chi2, S);
     k_chi2<MODE, false><<<g, pl->block, pl->smem, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
                                                         nullptr, pl->d_counter, g_member_chunk,
-                                                        pl->d_free_dig, nullptr);
+                                                        pl->d_free_dig, pl->d_free_raw);
   }
 }
 

@@ -753,11 +753,12 @@ LF_INLINE float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c)
 //   c[0] += kbar dx, c[1] += kbar dy, c[2] += kbar, c[3] += t dx^2, c[4] += t dx dy,
 //   c[5] += t r^2;  then psi_xx = c2 + c3, psi_yy = c2 + c5 - c3, psi_xy = c4
 // (psi_ij = kbar delta_ij + t x_i x_j, so psi_yy = kbar + t (r^2 - dx^2)).
-// 33 FP32 lane-operations and 4 MUFU per member.
-LF_INLINE void member_pair_acc(const MemPair& m, float2 pxh, float2 pxl, float2 pyh, float2 pyl,
-                               float2 (&c)[6]) {
-  const float2 dx = add2(add2(pxh, m.nxh), add2(pxl, m.nxl));
-  const float2 dy = add2(add2(pyh, m.nyh), add2(pyl, m.nyl));
+// 31 FP32 lane-operations and 4 MUFU per member.
+// The position's low word is left out of the offsets here (dx = (x_h - c_h) - c_l): the caller
+// adds the first-order term Psi x_l of the members' sums instead (accumulate_packed).
+LF_INLINE void member_pair_acc(const MemPair& m, float2 pxh, float2 pyh, float2 (&c)[6]) {
+  const float2 dx = add2(add2(pxh, m.nxh), m.nxl);
+  const float2 dy = add2(add2(pyh, m.nyh), m.nyl);
   const float2 r2 = fma2(dx, dx, mul2(dy, dy));
   const float2 S2 = add2(m.s2, r2), R2 = add2(m.a2, r2);
   // Every consumer of a MUFU result is a scalar FP32 operation on one lane, writing its half

@@ -102,37 +102,29 @@ __device__ inline void digest_plane_pairs(const lf_comp* rawc, int nc, const lf_
   }
 }
 
-// LF_MIXED with packed member pairs: explicit components as in accumulate_mixed; members two
-// at a time (f32x2), `chunk` pairs per FP32 partial sum, each folded into the float-float
-// accumulators.  [k0, k1) counts explicit components first, then member pairs.
+// LF_MIXED members in packed pairs (f32x2), two members per instruction: [k0, k1) counts member
+// pairs, `chunk` pairs per FP32 partial sum, each folded into the float-float accumulators.  The
+// offsets leave out the position's low word x_l (member_pair_acc); its first-order effect on the
+// members' deflection, Psi x_l, is added at the end from the members' own psi sums (the second
+// order, x_l^2 / 2 times the derivative of psi, stays below 1e-11 arcsec at |x_l| <= 5e-6").
 template <int PPT>
-__device__ __forceinline__ void accumulate_packed(const CompT<float>* dc, int nc, const MemPair* dp,
-                                                  int nm, int k0, int k1, int chunk,
+__device__ __forceinline__ void accumulate_packed(const MemPair* dp, int nm, int k0, int k1, int chunk,
                                                   const float* pxh, const float* pxl,
                                                   const float* pyh, const float* pyl,
-                                                  const float2* tab, ff (&acc)[5][PPT]) {
-  const int c1 = min(k1, nc);
-  for (int c = k0; c < c1; ++c) {
-    const CompT<float>& C = dc[c];
-    if (C.kind == 0) continue;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      ff ax, ay;
-      Out5<float> o;
-      eval_comp_mixed(C, pxh[k], pxl[k], pyh[k], pyl[k], tab, ax, ay, o);
-      acc[0][k] = ff_add(acc[0][k], ax);
-      acc[1][k] = ff_add(acc[1][k], ay);
-      ff_acc(acc[2][k], o.pxx); ff_acc(acc[3][k], o.pyy); ff_acc(acc[4][k], o.pxy);
-    }
-  }
-  float2 qxh[PPT], qxl[PPT], qyh[PPT], qyl[PPT];
+                                                  ff (&acc)[5][PPT]) {
+  float2 qxh[PPT], qyh[PPT];
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    qxh[k] = make_float2(pxh[k], pxh[k]); qxl[k] = make_float2(pxl[k], pxl[k]);
-    qyh[k] = make_float2(pyh[k], pyh[k]); qyl[k] = make_float2(pyl[k], pyl[k]);
+    qxh[k] = make_float2(pxh[k], pxh[k]);
+    qyh[k] = make_float2(pyh[k], pyh[k]);
   }
+  ff m5[5][PPT];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) m5[v][k] = ff_zero();
   const int np = (int)mem_records<MemPair>(nm);
-  const int j_beg = max(k0, nc) - nc, j_end = min(k1, nc + np) - nc;
+  const int j_beg = k0, j_end = min(k1, np);
   for (int j0 = j_beg; j0 < j_end; j0 += chunk) {
     const int j1 = min(j0 + chunk, j_end);
     float2 cs[PPT][6];
@@ -146,18 +138,25 @@ __device__ __forceinline__ void accumulate_packed(const CompT<float>* dc, int nc
     for (int j = j0; j < j1; ++j) {
       const MemPair M = dp[j];
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) member_pair_acc(M, qxh[k], qxl[k], qyh[k], qyl[k], cs[k]);
+      for (int k = 0; k < PPT; ++k) member_pair_acc(M, qxh[k], qyh[k], cs[k]);
     }
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       const float kb = cs[k][2].x + cs[k][2].y, txx = cs[k][3].x + cs[k][3].y;
       const float trr = cs[k][5].x + cs[k][5].y;
-      ff_acc(acc[0][k], cs[k][0].x + cs[k][0].y);
-      ff_acc(acc[1][k], cs[k][1].x + cs[k][1].y);
-      ff_acc(acc[2][k], kb + txx);
-      ff_acc(acc[3][k], kb + (trr - txx));
-      ff_acc(acc[4][k], cs[k][4].x + cs[k][4].y);
+      ff_acc(m5[0][k], cs[k][0].x + cs[k][0].y);
+      ff_acc(m5[1][k], cs[k][1].x + cs[k][1].y);
+      ff_acc(m5[2][k], kb + txx);
+      ff_acc(m5[3][k], kb + (trr - txx));
+      ff_acc(m5[4][k], cs[k][4].x + cs[k][4].y);
     }
+  }
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    ff_acc(m5[0][k], fmaf(m5[2][k].hi, pxl[k], m5[4][k].hi * pyl[k]));
+    ff_acc(m5[1][k], fmaf(m5[4][k].hi, pxl[k], m5[3][k].hi * pyl[k]));
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v][k] = ff_add(acc[v][k], m5[v][k]);
   }
 }
 

@@ -103,6 +103,32 @@ def test_full_size_chi2_sampled(lib, c2):
     api.device_error()
 
 
+@pytest.mark.parametrize("prec", ["mixed", "ff"])
+def test_every_benchmark_sample_within_tolerance(lib, c2, prec):
+    """All 4096 samples of the benchmark launch (graph + tuner) within the stated 1e-5 of the
+    FP64 kernel, not a subset: about 3 % of them put an image within |det A| < 3e-3 of a
+    critical curve, where the tiers' FP32 psi_ij and alpha alone would miss it by up to 3e-3
+    (those images are re-evaluated in FP64).  The FP64 kernel is held to the oracle at 1e-10
+    by test_cluster_chi2_matches_oracle; the eight samples with the image nearest a critical
+    curve are also compared with the oracle directly."""
+    api, PM = lib
+    wl, cat, th = c2
+    t = torch.tensor(th, device="cuda")
+    ref = api.Plan([PM.cluster_input(wl, cat)], 4096, "fp64").chi2(t).cpu().numpy()
+    plan = api.Plan([PM.cluster_input(wl, cat)], 4096, prec, flags=api.FLAG_GRAPH | api.FLAG_AUTOTUNE)
+    got = plan.chi2(t).cpu().numpy()
+    rel = np.abs(got - ref) / np.abs(ref)
+    print(f"{prec}: max rel {rel.max():.3e}, median {np.median(rel):.3e}")
+    assert rel.max() <= 1e-5
+    kw = {"fam_adis": OM.single_plane_adis(wl, cat.fam_zs)}
+    with torch.no_grad():
+        _, A = OG._terms(wl, torch.as_tensor(th), torch.tensor(cat.theta_obs), list(cat.fam_off), **kw)
+    near = np.argsort(torch.linalg.det(A).abs().min(1).values.numpy())[:8]
+    o = oracle(wl, cat, th[near]).numpy()
+    assert np.all(np.abs(got[near] - o) <= 1e-5 * np.abs(o))
+    api.device_error()
+
+
 def test_graph_and_tuner_do_not_change_results(lib, c2):
     api, PM = lib
     wl, cat, th = c2
