@@ -911,7 +911,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
                 if (Cc.kind == 0) continue;
                 ff ax, ay;
                 Out5<float> o;
-                eval_comp_mixed(Cc, xh, xl, yh, yl, tab, ax, ay, o);
+                eval_comp_mixed_t<true>(Cc, xh, xl, yh, yl, tab, ax, ay, o);
                 e5[0] = ff_add(e5[0], ax);
                 e5[1] = ff_add(e5[1], ay);
                 ff_acc(e5[2], o.pxx); ff_acc(e5[3], o.pyy); ff_acc(e5[4], o.pxy);

@@ -875,10 +875,84 @@ LF_INLINE void enfw_alpha_ff(const ff& u, const ff& v, const ff& q, const ff& q2
   }
 }
 
+// Reduced-precision float-float atan / atanh of a ratio N / D (D > 0) for the chi^2 kernel's
+// mixed tier, ~1e-9 relative instead of ~1e-14: with c = k/64 the table point nearest |N|/D,
+//   atan(N/D) = atan(c) + atan(t),   t = (|N| - c D) / (D + c |N|),
+//   atanh(N/D) = atanh(c) + atanh(t), t = (|N| - c D) / (D - c |N|),
+// (|N| / D > 1 for atan: pi/2 - atan(D / |N|)).  The numerator of t is formed in float-float
+// (it cancels) and rounded once; t itself (|t| <= 1/128 for atan, < 0.05 for the atanh
+// arguments of ellipticities below 0.9) and its odd series are FP32, so t's rounding moves the
+// result by ~u |t|.  No float-float division is taken.
+LF_INLINE float series_t(float t, float sgn) {       // t -+ t^3/3 + t^5/5 -+ t^7/7 + t^9/9
+  const float t2 = t * t;
+  float p = fmaf(sgn * (1.0f / 9.0f), t2, 1.0f / 7.0f);
+  p = fmaf(p, t2 * sgn, 1.0f / 5.0f);
+  p = fmaf(p, t2 * sgn, 1.0f / 3.0f);
+  return fmaf(p * t2 * sgn, t, t);
+}
+LF_INLINE ff ff_atan_ratio_mx(const ff& N, const ff& D, const float2* tab) {
+  const bool neg = N.hi < 0.f;
+  const ff aN = neg ? ff_neg(N) : N;
+  const bool inv = aN.hi > D.hi;
+  const ff& U = inv ? D : aN;          // atan(U / V), U <= V
+  const ff& V = inv ? aN : D;
+  const int k = __float2int_rn(U.hi * __fdividef(64.f, V.hi));
+  const float c = (float)k * (1.0f / 64.0f);
+  const float num = ff_sub(U, ff_mul_f(V, c)).hi;
+  const float den = fmaf(c, U.hi, V.hi);
+  ff r = ff_add_f(ff_make(tab[k].x, tab[k].y), series_t(num * __fdividef(1.f, den), -1.f));
+  if (inv) r = ff_sub(ff_make(1.5707963705062866f, -4.371138828673793e-08f), r);
+  return neg ? ff_neg(r) : r;
+}
+LF_INLINE ff ff_atanh_ratio_mx(const ff& N, const ff& D, const float2* tab) {
+  const bool neg = N.hi < 0.f;
+  const ff aN = neg ? ff_neg(N) : N;
+  int k = __float2int_rn(aN.hi * __fdividef(64.f, D.hi));
+  k = k > 63 ? 63 : k;
+  const float c = (float)k * (1.0f / 64.0f);
+  const float num = ff_sub(aN, ff_mul_f(D, c)).hi;
+  const float den = ff_sub(D, ff_mul_f(aN, c)).hi;
+  const ff r = ff_add_f(ff_make(tab[LF_TAB_N + k].x, tab[LF_TAB_N + k].y), series_t(num * __fdividef(1.f, den), 1.f));
+  return neg ? ff_neg(r) : r;
+}
+// a / b with one correction of the FP32 quotient by the exact remainder (~44 bits).
+LF_INLINE ff ff_div1(const ff& a, const ff& b) {
+  const float r = __fdividef(1.0f, b.hi);
+  const float q1 = a.hi * r;
+  const ff rem = ff_sub(a, ff_mul_f(b, q1));
+  return fast_two_sum(q1, rem.hi * r);
+}
+// dpie_alpha_ff / sie_alpha_ff with the reduced-precision ratio forms above (chi^2 kernel,
+// LF_MIXED): the same cancellation-free arguments, one correction step for w.
+LF_INLINE void dpie_alpha_mx(const ff& u, const ff& v, const ff& uu, const ff& vv, const ff& q2,
+                             const ff& e, const ff& qe, const ff& s, const ff& ssq, const ff& q2s,
+                             const ff& a, const ff& asq, const ff& q2a, const float2* tab, ff& au,
+                             ff& av) {
+  const ff ps = ff_sqrt(ff_add(ff_mul(q2, ff_add(ssq, uu)), vv));
+  const ff pa = ff_sqrt(ff_add(ff_mul(q2, ff_add(asq, uu)), vv));
+  const ff amin = ff_sub(a, s);
+  const ff w = ff_div1(ff_add(a, s), ff_add(pa, ps));
+  const ff eu = ff_mul(e, u), ev = ff_mul(e, v);
+  const ff num1 = ff_mul(ff_mul(eu, amin), ff_add_f(ff_mul(q2, w), 1.f));
+  const ff den1 = ff_add(ff_mul(ff_add(ps, s), ff_add(pa, a)), ff_sqr(eu));
+  const ff num2 = ff_mul(ff_mul(ff_mul(ev, q2), amin), ff_add_f(w, 1.f));
+  const ff den2 = ff_sub(ff_mul(ff_add(ps, q2s), ff_add(pa, q2a)), ff_sqr(ev));
+  au = ff_mul(qe, ff_atan_ratio_mx(num1, den1, tab));
+  av = ff_mul(qe, ff_atanh_ratio_mx(num2, den2, tab));
+}
+LF_INLINE void sie_alpha_mx(const ff& u, const ff& v, const ff& uu, const ff& vv, const ff& q2,
+                            const ff& e, const ff& qe, const ff& s, const ff& ssq, const ff& q2s,
+                            const float2* tab, ff& au, ff& av) {
+  const ff psi = ff_sqrt(ff_add(ff_mul(q2, ff_add(ssq, uu)), vv));
+  au = ff_mul(qe, ff_atan_ratio_mx(ff_mul(e, u), ff_add(psi, s), tab));
+  av = ff_mul(qe, ff_atanh_ratio_mx(ff_mul(e, v), ff_add(psi, q2s), tab));
+}
+
 // One explicit component for the mixed path: alpha in float-float for elliptical
 // isothermal components (SIE, dPIE), the elliptical NFW and the shear, FP32 otherwise;
 // psi_ij in FP32.
-LF_NOINLINE void eval_comp_mixed(const CompT<float>& c, float ph_x, float pl_x, float ph_y,
+template <bool FAST>
+LF_NOINLINE void eval_comp_mixed_t(const CompT<float>& c, float ph_x, float pl_x, float ph_y,
                                float pl_y, const float2* tab, ff& ax, ff& ay, Out5<float>& o) {
   const bool ell = (c.kind == K_SIE || c.kind == K_DPIE) && !c.round;
   if (c.kind == K_MPOLE3) {
@@ -942,13 +1016,23 @@ LF_NOINLINE void eval_comp_mixed(const CompT<float>& c, float ph_x, float pl_x, 
   ff uu = ff_mul(u, u), vv = ff_mul(v, v);
   const ff q2 = ff_make(c.q2, c.lq2), e = ff_make(c.e, c.le), qe = ff_make(c.qe, c.lqe);
   ff au, av;
-  if (c.kind == K_DPIE)
-    dpie_alpha_ff(u, v, uu, vv, q2, e, qe, ff_make(c.s1, c.ls1), ff_make(c.s1sq, c.ls1sq),
-                  ff_make(c.q2s1, c.lq2s1), ff_make(c.s2, c.ls2), ff_make(c.s2sq, c.ls2sq),
-                  ff_make(c.q2s2, c.lq2s2), tab, au, av);
-  else
-    sie_alpha_ff(u, v, uu, vv, q2, e, qe, ff_make(c.s1, c.ls1), ff_make(c.s1sq, c.ls1sq),
-                 ff_make(c.q2s1, c.lq2s1), tab, au, av);
+  if (c.kind == K_DPIE) {
+    if constexpr (FAST)
+      dpie_alpha_mx(u, v, uu, vv, q2, e, qe, ff_make(c.s1, c.ls1), ff_make(c.s1sq, c.ls1sq),
+                    ff_make(c.q2s1, c.lq2s1), ff_make(c.s2, c.ls2), ff_make(c.s2sq, c.ls2sq),
+                    ff_make(c.q2s2, c.lq2s2), tab, au, av);
+    else
+      dpie_alpha_ff(u, v, uu, vv, q2, e, qe, ff_make(c.s1, c.ls1), ff_make(c.s1sq, c.ls1sq),
+                    ff_make(c.q2s1, c.lq2s1), ff_make(c.s2, c.ls2), ff_make(c.s2sq, c.ls2sq),
+                    ff_make(c.q2s2, c.lq2s2), tab, au, av);
+  } else {
+    if constexpr (FAST)
+      sie_alpha_mx(u, v, uu, vv, q2, e, qe, ff_make(c.s1, c.ls1), ff_make(c.s1sq, c.ls1sq),
+                   ff_make(c.q2s1, c.lq2s1), tab, au, av);
+    else
+      sie_alpha_ff(u, v, uu, vv, q2, e, qe, ff_make(c.s1, c.ls1), ff_make(c.s1sq, c.ls1sq),
+                   ff_make(c.q2s1, c.lq2s1), tab, au, av);
+  }
   float puu, pvv, puv;
   sie_psi(u.hi, v.hi, c.q, c.q2, c.s1, c.s1sq, c.D01, puu, pvv, puv);
   if (c.kind == K_DPIE) {
@@ -963,6 +1047,11 @@ LF_NOINLINE void eval_comp_mixed(const CompT<float>& c, float ph_x, float pl_x, 
   Out5<float> t;
   rotate_back(c.c, c.sn, 0.f, 0.f, c.b * puu, c.b * pvv, c.b * puv, t);
   o.pxx = t.pxx; o.pyy = t.pyy; o.pxy = t.pxy;
+}
+
+LF_INLINE void eval_comp_mixed(const CompT<float>& c, float ph_x, float pl_x, float ph_y, float pl_y,
+                               const float2* tab, ff& ax, ff& ay, Out5<float>& o) {
+  eval_comp_mixed_t<false>(c, ph_x, pl_x, ph_y, pl_y, tab, ax, ay, o);
 }
 
 // ln(y), y > 0, in float-float: y = m 2^e with m in [1/sqrt 2, sqrt 2) (exact scaling by a
