@@ -338,6 +338,10 @@ constexpr uint32_t LF_AUXI = 7, LF_AUXF = 4, LF_AUXG = 16;
 // [17..20] mu (00, 01, 10, 11).
 constexpr int IMGF = 22;
 
+// Member pairs per FP32 partial sum of the mixed tier's packed loop (64 members; each partial is
+// then folded into float-float).
+constexpr int LF_PAIR_CHUNK = 32;
+
 #ifndef LF_CHI2_THREADS
 #define LF_CHI2_THREADS 512
 #endif
@@ -647,18 +651,15 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
     *s_nref = 0;
   }
   init_ff_tables(tab);
+  if (tid == 0) *s_item = atomicAdd(counter, 1);     // the first work item
   __syncthreads();
   uint32_t phase = 0;
   int cur = -1;
 
   for (;;) {
-    if (tid == 0) {
-      *s_item = atomicAdd(counter, 1);
-      *s_nref = 0;      // every thread read the previous sample's count before the barriers since
-    }
-    __syncthreads();
+    // the item was taken during the previous item (its atomic's latency hidden behind that
+    // item's work) and published by the barriers since
     const int w = *s_item;
-    __syncthreads();
     if (w >= S) break;
     const int c = corder[w / spc];
     const int s = c * spc + (w % spc);
@@ -672,7 +673,11 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
       for (int f = tid; f < C.n_fam; f += blockDim.x) okb = okb && C.fam_off[f] < C.fam_off[f + 1];
       for (int i = tid; i < C.n_img; i += blockDim.x) okb = okb && C.img_fam[i] >= 0 && C.img_fam[i] < C.n_fam;
       if (!__syncthreads_and(LF_CHECK(okb) ? 1 : 0)) {
-        if (tid == 0) chi2[s] = NAN;
+        if (tid == 0) {
+          chi2[s] = NAN;
+          *s_item = atomicAdd(counter, 1);
+        }
+        __syncthreads();
         continue;
       }
     }
@@ -712,6 +717,11 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
       cur = c;
     }
     __syncthreads();
+    if (tid == 0) {
+      // every thread has read this item (and the previous item's count of near-critical images)
+      *s_item = atomicAdd(counter, 1);
+      *s_nref = 0;
+    }
 
     // ---- A1: this sample's parameters into the tables
     for (int f = tid; f < C.n_free; f += blockDim.x) {
@@ -883,7 +893,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
             for (int c5 = 0; c5 < 5; ++c5)
 #pragma unroll
               for (int q = 0; q < IPT; ++q) acc[c5][q] = ff_zero();
-            if (act) accumulate_packed<IPT>(dp, P.nm, k0, k1, chunk, xh, xl, yh, yl, acc);
+            if (act) accumulate_packed<IPT>(dp, P.nm, k0, k1, LF_PAIR_CHUNK, xh, xl, yh, yl, acc);
             for (int off = 1; off < ks; off <<= 1)
 #pragma unroll
               for (int c5 = 0; c5 < 5; ++c5)
