@@ -40,6 +40,26 @@ __device__ __forceinline__ void position_of(const PosArgs& P, long long p, doubl
   }
 }
 
+// write_out from float-float sums, with kappa, gamma, det A and mu = 1/det A in float-float on
+// the FP32 pipe (det A to ~1e-14 absolute) and only the FP64 stores' conversions on the FP64
+// pipe, which runs FP64 arithmetic at 1/64 of the FP32 rate on this part.
+__device__ __forceinline__ void write_out_ff(const OutArgs& O, const ff& a_dis, long long p, const ff& ax,
+                                            const ff& ay, const ff& pxx, const ff& pyy, const ff& pxy) {
+  if (O.ax) O.ax[p] = ff_to_double(ax);
+  if (O.ay) O.ay[p] = ff_to_double(ay);
+  // (the accumulators' low words may exceed half an ulp of the high ones: renormalise)
+  const ff kappa = ff_mul_f(ff_add(pxx, pyy), 0.5f), g1 = ff_mul_f(ff_sub(pxx, pyy), 0.5f);
+  const ff g2 = fast_two_sum(pxy.hi, pxy.lo);
+  if (O.kappa) O.kappa[p] = kappa.hi;
+  if (O.g1) O.g1[p] = g1.hi;
+  if (O.g2) O.g2[p] = g2.hi;
+  if (O.mu) {
+    const ff t = ff_add_f(ff_neg(ff_mul(a_dis, kappa)), 1.0f);
+    const ff det = ff_sub(ff_sqr(t), ff_mul(ff_sqr(a_dis), ff_add(ff_sqr(g1), ff_sqr(g2))));
+    O.mu[p] = ff_to_double(ff_div(ff_make(1.f, 0.f), det));
+  }
+}
+
 __device__ __forceinline__ void write_out(const OutArgs& O, long long p, double ax, double ay,
                                           double pxx, double pyy, double pxy) {
   if (O.ax) O.ax[p] = ax;
@@ -268,6 +288,7 @@ __global__ void __launch_bounds__(LF_AMAP_THREADS, LF_ANCHOR_MINB) k_map_anchor(
                                                                   const lf_member* __restrict__ mem, int nm,
                                                                   lf_scaling sc, PosArgs P, OutArgs O, int chunk) {
   constexpr int NT = LF_AMAP_THREADS, PPT = LF_AMAP_PPT, NWARP = NT / 32;
+  const ff a_ff = ff_from_double(O.a_dis);
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   const AnchorLayout L = anchor_layout(nc, nm);
@@ -541,9 +562,9 @@ __global__ void __launch_bounds__(LF_AMAP_THREADS, LF_ANCHOR_MINB) k_map_anchor(
           ff_acc(a5[2], o.pxx); ff_acc(a5[3], o.pyy); ff_acc(a5[4], o.pxy);
         }
       }
-      if (valid[q])
-        write_out(O, pid[q], ff_to_double(a5[0]), ff_to_double(a5[1]), ff_to_double(a5[2]),
-                  ff_to_double(a5[3]), ff_to_double(a5[4]));
+      if (valid[q]) {
+        write_out_ff(O, a_ff, pid[q], a5[0], a5[1], a5[2], a5[3], a5[4]);
+      }
     }
     __syncthreads();     // the next tile rewrites the records, the bits and the sums
   }
