@@ -633,6 +633,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
   constexpr bool AUX = PASS == 2;
   // the forward source-plane chi^2 of the mixed tiers re-evaluates near-critical images in FP64
   constexpr bool REFINE = MIXED && PASS == 0 && !GRAD;
+  constexpr bool FFSUM = PACKM && PASS == 0;
   // images per evaluation task (independent chains per thread; with packed members, two
   // member evaluations per instruction and chain); the FP64 tier takes two
   constexpr int IPT = MIXED ? LF_CHI2_IPT : 2;
@@ -770,6 +771,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
       const bool alpha_free = sampled && C.scal_p[LF_S_ALPHA] >= 0;
       const MemPre* mp = reinterpret_cast<const MemPre*>(P.mpre);   // plan table, L2-resident
       Mem* dm = reinterpret_cast<Mem*>(smem + P.off_dm);
+      const T bstar = (T)sc.b_star, cstar = (T)sc.core_star, astar = (T)sc.cut_star;
       const int n_lanes = PACKM ? 2 * (int)mem_records<MemPair>(P.nm) : P.nm;
       for (int i = tid; i < n_lanes; i += blockDim.x) {
         if constexpr (PACKM) {
@@ -800,9 +802,9 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
             fa = alpha_free ? exp(sc.alpha * m.lnl) : m.fa;
             d.xh = m.x; d.xl = 0; d.yh = m.y; d.yl = 0;
           }
-          d.b = (T)sc.b_star * fb;
-          d.s = (T)sc.core_star * fs;
-          d.a = (T)sc.cut_star * fa;
+          d.b = bstar * fb;
+          d.s = cstar * fs;
+          d.a = astar * fa;
           d.bd = d.b * (d.a - d.s);
           d.apc = d.a + d.s;
           d.fb = fb;
@@ -1079,6 +1081,10 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
     eval_planes(nullptr);
 
     double my = 0.0;
+    // the mixed tier's source-plane chi^2: the block's sum in float-float (FP32 pipe), with
+    // any non-finite family flagged apart
+    ff myf = ff_zero();
+    bool mybad = false;
     if constexpr (MIXED) {
       // ---- A5, A7 (mixed tiers): beta in float-float, det A in float-float, then
       // mu = A^-1 and M = mu^T S^-1 mu in FP32
@@ -1222,11 +1228,13 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           c0 = ff_to_double(cx);
           c1 = ff_to_double(cy);
           if (!isfinite(cf) || !(dG.hi > 0.f)) cf = INFINITY;
+          if constexpr (FFSUM) myf = ff_add(myf, acc);
         }
         fam[3 * f] = cf;
         fam[3 * f + 1] = c0;
         fam[3 * f + 2] = c1;
-        my += cf;
+        if constexpr (FFSUM) mybad = mybad || !isfinite(cf);
+        else my += cf;
       }
     } else {
       // ---- A5, A7 (FP64 tier): beta_i, A_i, mu_i, M_i
@@ -1494,7 +1502,14 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
       __syncthreads();
       continue;
     }
-    const double total = block_sum(my, scratch);
+    double total;
+    if constexpr (FFSUM) {
+      const bool bad = __syncthreads_or(mybad ? 1 : 0) != 0;
+      const ff t = block_sum_ff(myf, reinterpret_cast<ff*>(scratch));
+      total = bad ? INFINITY : ff_to_double(t);
+    } else {
+      total = block_sum(my, scratch);
+    }
     if (tid == 0) chi2[s] = total;
 
     if constexpr (GRAD) {
