@@ -491,6 +491,25 @@ __device__ __forceinline__ void member_psi_ff(const ff& dx, const ff& dy, const 
   pxy = ff_mul(tdx, dy);
 }
 
+// psi_ij of CSE term i of the elliptical NFW (unit kappa_s, r_s = 1: the closed form of enfw_uv)
+// in its (u, v) frame, float-float.
+__device__ __forceinline__ void enfw_term_psi_ff(const ff& u, const ff& v, const ff& q, const ff& q2, int i,
+                                                 ff& puu, ff& pvv, ff& puv) {
+  const float2 sv = c_cse_sff[i], cv = c_cse_cff[i];
+  const ff s = ff_make(sv.x, sv.y), s2 = ff_sqr(s);
+  const ff uu = ff_sqr(u), vv = ff_sqr(v);
+  const ff P = ff_sqrt(ff_add(ff_mul(q2, ff_add(s2, uu)), vv)), iP = ff_rcp(P);
+  const ff D = ff_add(ff_add(ff_mul(ff_add_f(q2, 1.f), s2), ff_mul_f(ff_mul(P, s), 2.f)), ff_add(uu, vv));
+  const ff iD = ff_rcp(D);
+  const ff A = ff_add(ff_mul(q2, s), P), B = ff_add(P, s);
+  const ff f = ff_mul(ff_mul(ff_make(cv.x, cv.y), q), ff_mul(iP, iD));
+  const ff iP2 = ff_sqr(iP), g = ff_mul_f(ff_mul(iP, iD), 2.f);
+  const ff q2s = ff_mul(q2, s);
+  puu = ff_mul(f, ff_sub(ff_sub(A, ff_mul(ff_mul(ff_mul(q2s, q2), uu), iP2)), ff_mul(ff_mul(g, uu), ff_sqr(A))));
+  pvv = ff_mul(f, ff_sub(ff_sub(B, ff_mul(ff_mul(s, vv), iP2)), ff_mul(ff_mul(g, vv), ff_sqr(B))));
+  puv = ff_neg(ff_mul(ff_mul(f, ff_mul(u, v)), ff_add(ff_mul(q2s, iP2), ff_mul(g, ff_mul(A, B)))));
+}
+
 // Member m's centre, strength, core and cut as float-float, for this sample's scaling relation.
 template <int MODE>
 __device__ __forceinline__ void member_ff(const PlaneDesc& P, int m, const lf_scaling& sc, bool lam_free,
@@ -532,12 +551,30 @@ __device__ __noinline__ void refine_psi(const ClusterDesc& C, int s, const doubl
   const float4 tf = C.theta_ff[i];
   ff a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero();
   const CompT<float>* dc = reinterpret_cast<const CompT<float>*>(smem + P.off_dc);
-  for (int task = B - 1 - t; task < 2 * nc; task += B) {
-    const int c = task >> 1, part = task & 1;
+  // tasks (component, part): an ellipsoid of an isothermal component or dPIE, a CSE term of an
+  // elliptical NFW, or the whole component
+  constexpr int NPART = LF_CSE_N > 2 ? LF_CSE_N : 2;
+  for (int task = B - 1 - t; task < NPART * nc; task += B) {
+    const int c = task / NPART, part = task - c * NPART;
     const CompT<float>& cf = dc[c];
-    if (cf.kind == 0 || (part == 1 && cf.kind != K_DPIE)) continue;
+    if (cf.kind == 0 || (part >= (cf.kind == K_DPIE ? 2 : cf.kind == K_ENFW ? LF_CSE_N : 1))) continue;
     ff pxx, pyy, pxy;
-    if (cf.kind == K_SIE || cf.kind == K_DPIE || cf.kind == K_SHEAR) {
+    if (cf.kind == K_ENFW) {
+      // term `part` of the CSE sum: Psi = 2 kappa_s Psi_cse at (u, v) / r_s, rotated back
+      const ff cc = ff_make(cf.c, cf.lc), sn = ff_make(cf.sn, cf.lsn), b2 = ff_mul_f(ff_make(cf.b, cf.lb), 2.f);
+      const ff dx = offset_ff(tf.x, tf.y, cf.xh, cf.xl), dy = offset_ff(tf.z, tf.w, cf.yh, cf.yl);
+      const ff irs = ff_rcp(ff_make(cf.s1, cf.ls1));
+      const ff u = ff_mul(ff_add(ff_mul(cc, dx), ff_mul(sn, dy)), irs);
+      const ff v = ff_mul(ff_sub(ff_mul(cc, dy), ff_mul(sn, dx)), irs);
+      const ff q2 = ff_make(cf.q2, cf.lq2), q = ff_sqrt(q2);
+      ff puu, pvv, puv;
+      enfw_term_psi_ff(u, v, q, q2, part, puu, pvv, puv);
+      const ff c2 = ff_sqr(cc), s2 = ff_sqr(sn), csn = ff_mul(cc, sn);
+      const ff cs2puv = ff_mul_f(ff_mul(csn, puv), 2.f);
+      pxx = ff_mul(b2, ff_add(ff_sub(ff_mul(c2, puu), cs2puv), ff_mul(s2, pvv)));
+      pyy = ff_mul(b2, ff_add(ff_add(ff_mul(s2, puu), cs2puv), ff_mul(c2, pvv)));
+      pxy = ff_mul(b2, ff_add(ff_mul(csn, ff_sub(puu, pvv)), ff_mul(ff_sub(c2, s2), puv)));
+    } else if (cf.kind == K_SIE || cf.kind == K_DPIE || cf.kind == K_SHEAR) {
       const ff cc = ff_make(cf.c, cf.lc), sn = ff_make(cf.sn, cf.lsn), b = ff_make(cf.b, cf.lb);
       if (cf.kind == K_SHEAR) {
         pxx = ff_mul(b, cc);
