@@ -90,6 +90,7 @@ struct ClusterDesc {
   int mpg_stride;                  // multi-plane adjoint: doubles per image record
   uint32_t off_img, off_imgd, off_fam, off_par, off_free, off_newton, off_fama, off_aux, off_mpg;
   uint32_t off_auxg;               // adjoint of the flux / time-delay terms: per image records
+  uint32_t off_rscr;               // near-critical refinement: 12 float-float sums per warp + 12
   // shared memory of each launch kind: the common regions, then only the member records and
   // scratch that kind reads (source-plane chi^2; image-plane chi^2; flux / time delay; adjoint)
   uint32_t smem, smem_img, smem_aux, smem_grad;
@@ -536,103 +537,151 @@ __device__ __forceinline__ void member_ff(const PlaneDesc& P, int m, const lf_sc
   }
 }
 
-// This thread's share of psi_ij in float-float at image i of a single-plane cluster, for sample s.
-// The members (plan pre-table, this sample's scaling relation, Eq. scaling) go two per pass to
-// threads 0, 1, ...; the explicit components (the sample's digested table) go one ellipsoid each
-// to the last threads, which hold fewer members: an elliptical or round isothermal component or
-// either ellipsoid of a dPIE, and the shear, on the FP32 pipe; any other kind in FP64 from its
-// fields.
+// Near-critical images refined per pass (each thread's member records are loaded once per pass
+// and evaluated at all of them, as independent chains).
+constexpr int LF_REFINE_BATCH = 4;
+
+// psi_ij (float-float) of one explicit component's part at position (x, y) (float-float words of
+// tf): an ellipsoid of an isothermal component or dPIE, a CSE term of an elliptical NFW, the
+// shear, the multipole; any other kind (the spherical NFW) whole, in FP64 from its fields.
+// Returns false for an empty part.
+__device__ __forceinline__ bool comp_part_psi_ff(const CompT<float>& cf, int part, const float4& tf,
+                                                 const ClusterDesc& C, int s, int c, const unsigned char* smem,
+                                                 const lf_comp* fraw, const lf_comp* free_raw, ff& pxx,
+                                                 ff& pyy, ff& pxy) {
+  if (cf.kind == 0 || (part >= (cf.kind == K_DPIE ? 2 : cf.kind == K_ENFW ? LF_CSE_N : 1))) return false;
+  if (cf.kind == K_ENFW || cf.kind == K_SIE || cf.kind == K_DPIE) {
+    const ff cc = ff_make(cf.c, cf.lc), sn = ff_make(cf.sn, cf.lsn), b = ff_make(cf.b, cf.lb);
+    const ff dx = offset_ff(tf.x, tf.y, cf.xh, cf.xl), dy = offset_ff(tf.z, tf.w, cf.yh, cf.yl);
+    ff u = ff_add(ff_mul(cc, dx), ff_mul(sn, dy)), v = ff_sub(ff_mul(cc, dy), ff_mul(sn, dx));
+    const ff q2 = ff_make(cf.q2, cf.lq2), q = ff_sqrt(q2);
+    ff puu, pvv, puv, k;
+    if (cf.kind == K_ENFW) {
+      // term `part` of the CSE sum: Psi = 2 kappa_s Psi_cse at (u, v) / r_s
+      const ff irs = ff_rcp(ff_make(cf.s1, cf.ls1));
+      u = ff_mul(u, irs);
+      v = ff_mul(v, irs);
+      enfw_term_psi_ff(u, v, q, q2, part, puu, pvv, puv);
+      k = ff_mul_f(b, 2.f);
+    } else if (part == 0) {
+      sie_psi_ff(u, v, q, q2, ff_make(cf.s1, cf.ls1), ff_make(cf.s1sq, cf.ls1sq), puu, pvv, puv);
+      k = b;
+    } else {             // the dPIE's cut ellipsoid, subtracted
+      sie_psi_ff(u, v, q, q2, ff_make(cf.s2, cf.ls2), ff_make(cf.s2sq, cf.ls2sq), puu, pvv, puv);
+      k = ff_neg(b);
+    }
+    const ff c2 = ff_sqr(cc), s2 = ff_sqr(sn), csn = ff_mul(cc, sn);
+    const ff cs2puv = ff_mul_f(ff_mul(csn, puv), 2.f);
+    pxx = ff_mul(k, ff_add(ff_sub(ff_mul(c2, puu), cs2puv), ff_mul(s2, pvv)));
+    pyy = ff_mul(k, ff_add(ff_add(ff_mul(s2, puu), cs2puv), ff_mul(c2, pvv)));
+    pxy = ff_mul(k, ff_add(ff_mul(csn, ff_sub(puu, pvv)), ff_mul(ff_sub(c2, s2), puv)));
+  } else if (cf.kind == K_SHEAR) {
+    const ff b = ff_make(cf.b, cf.lb);
+    pxx = ff_mul(b, ff_make(cf.c, cf.lc));
+    pyy = ff_neg(pxx);
+    pxy = ff_mul(b, ff_make(cf.sn, cf.lsn));
+  } else if (cf.kind == K_MPOLE3) {
+    // psi_ij of the third-order multipole (the form of multipole3), a function of n = x / r
+    const ff dx = offset_ff(tf.x, tf.y, cf.xh, cf.xl), dy = offset_ff(tf.z, tf.w, cf.yh, cf.yl);
+    const ff r2 = ff_add(ff_sqr(dx), ff_sqr(dy));
+    if (!(r2.hi > 0.f)) {
+      pxx = pyy = pxy = ff_zero();
+      return true;
+    }
+    const ff ir = ff_rcp(ff_sqrt(r2)), nx = ff_mul(dx, ir), ny = ff_mul(dy, ir);
+    const ff c3 = ff_make(cf.c, cf.lc), s3 = ff_make(cf.sn, cf.lsn), b = ff_make(cf.b, cf.lb);
+    const ff xx = ff_sqr(nx), yy = ff_sqr(ny), xy = ff_mul(nx, ny), d = ff_sub(xx, yy);
+    const ff G = ff_add(ff_mul(ff_mul(c3, nx), ff_sub(xx, ff_mul_f(yy, 3.f))),
+                        ff_mul(ff_mul(s3, ny), ff_sub(ff_mul_f(xx, 3.f), yy)));
+    const ff Hx = ff_mul_f(ff_add(ff_mul(c3, d), ff_mul_f(ff_mul(s3, xy), 2.f)), 3.f);
+    const ff Hy = ff_mul_f(ff_sub(ff_mul(s3, d), ff_mul_f(ff_mul(c3, xy), 2.f)), 3.f);
+    const ff L = ff_mul_f(ff_add(ff_mul(c3, nx), ff_mul(s3, ny)), 6.f);
+    const ff G3 = ff_mul_f(G, 3.f);
+    pxx = ff_mul(b, ff_add(ff_sub(ff_sub(L, ff_mul_f(ff_mul(nx, Hx), 2.f)), G), ff_mul(G3, xx)));
+    pyy = ff_mul(b, ff_add(ff_sub(ff_sub(ff_neg(L), ff_mul_f(ff_mul(ny, Hy), 2.f)), G), ff_mul(G3, yy)));
+    pxy = ff_mul(b, ff_add(ff_sub(ff_sub(ff_mul_f(ff_sub(ff_mul(s3, nx), ff_mul(c3, ny)), 6.f), ff_mul(ny, Hx)),
+                                  ff_mul(nx, Hy)), ff_mul(G3, xy)));
+  } else {
+    const PlaneDesc& P = C.pl[0];
+    lf_comp rc = reinterpret_cast<const lf_comp*>(smem + P.off_rawc)[c];
+    for (int f = 0; f < C.n_free; ++f)
+      if (C.free_plane[f] == 0 && C.free_comp[f] == c)
+        rc = free_raw ? free_raw[(size_t)s * LF_MAX_FREE + f] : fraw[f];
+    CompT<double> cd;
+    digest_one_comp<double>(rc, cd);
+    Out5<double> o;
+    eval_comp(cd, ((double)tf.x + (double)tf.y) - cd.xh, ((double)tf.z + (double)tf.w) - cd.yh, o);
+    pxx = ff_from_double(o.pxx); pyy = ff_from_double(o.pyy); pxy = ff_from_double(o.pxy);
+  }
+  return true;
+}
+
+// This thread's share of psi_ij in float-float at nb (<= LF_REFINE_BATCH) images img[] of a
+// single-plane cluster, for sample s.  The members (plan pre-table, this sample's scaling
+// relation, Eq. scaling) go two per pass to threads 0, 1, ..., each evaluated at every image;
+// the explicit components' parts (comp_part_psi_ff) go one (image, component, part) each to
+// the last threads, which hold fewer members.
 template <int MODE>
-__device__ __noinline__ void refine_psi(const ClusterDesc& C, int s, const double* th, int i,
-                                        const unsigned char* smem, const lf_comp* fraw,
-                                        const lf_comp* free_raw, ff (&p)[3]) {
+__device__ __noinline__ void refine_psi(const ClusterDesc& C, int s, const double* th, const int* img,
+                                        int nb, const unsigned char* smem, const lf_comp* fraw,
+                                        const lf_comp* free_raw, ff (&p)[LF_REFINE_BATCH][3]) {
   const PlaneDesc& P = C.pl[0];
   const int nc = P.nc, nm = P.nm, B = blockDim.x, t = threadIdx.x;
-  const float4 tf = C.theta_ff[i];
-  ff a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero();
-  const CompT<float>* dc = reinterpret_cast<const CompT<float>*>(smem + P.off_dc);
-  // tasks (component, part): an ellipsoid of an isothermal component or dPIE, a CSE term of an
-  // elliptical NFW, or the whole component
+  float4 tf[LF_REFINE_BATCH];
+#pragma unroll
+  for (int k = 0; k < LF_REFINE_BATCH; ++k) {
+    tf[k] = C.theta_ff[img[min(k, nb - 1)]];
+    p[k][0] = ff_zero(); p[k][1] = ff_zero(); p[k][2] = ff_zero();
+  }
   constexpr int NPART = LF_CSE_N > 2 ? LF_CSE_N : 2;
-  for (int task = B - 1 - t; task < NPART * nc; task += B) {
-    const int c = task / NPART, part = task - c * NPART;
-    const CompT<float>& cf = dc[c];
-    if (cf.kind == 0 || (part >= (cf.kind == K_DPIE ? 2 : cf.kind == K_ENFW ? LF_CSE_N : 1))) continue;
+  const CompT<float>* dc = reinterpret_cast<const CompT<float>*>(smem + P.off_dc);
+  for (int task = B - 1 - t; task < NPART * nc * nb; task += B) {
+    const int k = task / (NPART * nc), rest = task - k * NPART * nc;
+    const int c = rest / NPART, part = rest - c * NPART;
     ff pxx, pyy, pxy;
-    if (cf.kind == K_ENFW) {
-      // term `part` of the CSE sum: Psi = 2 kappa_s Psi_cse at (u, v) / r_s, rotated back
-      const ff cc = ff_make(cf.c, cf.lc), sn = ff_make(cf.sn, cf.lsn), b2 = ff_mul_f(ff_make(cf.b, cf.lb), 2.f);
-      const ff dx = offset_ff(tf.x, tf.y, cf.xh, cf.xl), dy = offset_ff(tf.z, tf.w, cf.yh, cf.yl);
-      const ff irs = ff_rcp(ff_make(cf.s1, cf.ls1));
-      const ff u = ff_mul(ff_add(ff_mul(cc, dx), ff_mul(sn, dy)), irs);
-      const ff v = ff_mul(ff_sub(ff_mul(cc, dy), ff_mul(sn, dx)), irs);
-      const ff q2 = ff_make(cf.q2, cf.lq2), q = ff_sqrt(q2);
-      ff puu, pvv, puv;
-      enfw_term_psi_ff(u, v, q, q2, part, puu, pvv, puv);
-      const ff c2 = ff_sqr(cc), s2 = ff_sqr(sn), csn = ff_mul(cc, sn);
-      const ff cs2puv = ff_mul_f(ff_mul(csn, puv), 2.f);
-      pxx = ff_mul(b2, ff_add(ff_sub(ff_mul(c2, puu), cs2puv), ff_mul(s2, pvv)));
-      pyy = ff_mul(b2, ff_add(ff_add(ff_mul(s2, puu), cs2puv), ff_mul(c2, pvv)));
-      pxy = ff_mul(b2, ff_add(ff_mul(csn, ff_sub(puu, pvv)), ff_mul(ff_sub(c2, s2), puv)));
-    } else if (cf.kind == K_SIE || cf.kind == K_DPIE || cf.kind == K_SHEAR) {
-      const ff cc = ff_make(cf.c, cf.lc), sn = ff_make(cf.sn, cf.lsn), b = ff_make(cf.b, cf.lb);
-      if (cf.kind == K_SHEAR) {
-        pxx = ff_mul(b, cc);
-        pyy = ff_neg(pxx);
-        pxy = ff_mul(b, sn);
-      } else {
-        const ff dx = offset_ff(tf.x, tf.y, cf.xh, cf.xl), dy = offset_ff(tf.z, tf.w, cf.yh, cf.yl);
-        const ff u = ff_add(ff_mul(cc, dx), ff_mul(sn, dy)), v = ff_sub(ff_mul(cc, dy), ff_mul(sn, dx));
-        const ff q2 = ff_make(cf.q2, cf.lq2), q = ff_sqrt(q2);
-        ff puu, pvv, puv;
-        if (part == 0)
-          sie_psi_ff(u, v, q, q2, ff_make(cf.s1, cf.ls1), ff_make(cf.s1sq, cf.ls1sq), puu, pvv, puv);
-        else {            // the dPIE's cut ellipsoid, subtracted
-          sie_psi_ff(u, v, q, q2, ff_make(cf.s2, cf.ls2), ff_make(cf.s2sq, cf.ls2sq), puu, pvv, puv);
-          puu = ff_neg(puu); pvv = ff_neg(pvv); puv = ff_neg(puv);
-        }
-        const ff c2 = ff_sqr(cc), s2 = ff_sqr(sn), csn = ff_mul(cc, sn);
-        const ff cs2puv = ff_mul_f(ff_mul(csn, puv), 2.f);
-        pxx = ff_mul(b, ff_add(ff_sub(ff_mul(c2, puu), cs2puv), ff_mul(s2, pvv)));
-        pyy = ff_mul(b, ff_add(ff_add(ff_mul(s2, puu), cs2puv), ff_mul(c2, pvv)));
-        pxy = ff_mul(b, ff_add(ff_mul(csn, ff_sub(puu, pvv)), ff_mul(ff_sub(c2, s2), puv)));
-      }
-    } else {
-      const lf_comp* rawc = reinterpret_cast<const lf_comp*>(smem + P.off_rawc);
-      lf_comp rc = rawc[c];
-      for (int f = 0; f < C.n_free; ++f)
-        if (C.free_plane[f] == 0 && C.free_comp[f] == c)
-          rc = free_raw ? free_raw[(size_t)s * LF_MAX_FREE + f] : fraw[f];
-      CompT<double> cd;
-      digest_one_comp<double>(rc, cd);
-      Out5<double> o;
-      eval_comp(cd, ((double)tf.x + (double)tf.y) - cd.xh, ((double)tf.z + (double)tf.w) - cd.yh, o);
-      pxx = ff_from_double(o.pxx); pyy = ff_from_double(o.pyy); pxy = ff_from_double(o.pxy);
-    }
-    a0 = ff_add(a0, pxx); a1 = ff_add(a1, pyy); a2 = ff_add(a2, pxy);
+    if (!comp_part_psi_ff(dc[c], part, tf[k], C, s, c, smem, fraw, free_raw, pxx, pyy, pxy)) continue;
+#pragma unroll
+    for (int kk = 0; kk < LF_REFINE_BATCH; ++kk)
+      if (kk == k) { p[kk][0] = ff_add(p[kk][0], pxx); p[kk][1] = ff_add(p[kk][1], pyy); p[kk][2] = ff_add(p[kk][2], pxy); }
   }
-  if (nm > 0) {
-    lf_scaling sc = P.sc;
-    const bool sampled = (C.scal_plane == 0) && C.scal_free;
-    if (sampled) sample_scaling(C, th, sc);
-    const bool lf = sampled && C.scal_p[LF_S_LAM] >= 0, bf = sampled && C.scal_p[LF_S_BETA] >= 0;
-    const bool af = sampled && C.scal_p[LF_S_ALPHA] >= 0;
-    const ff bs = ff_from_double(sc.b_star), cs = ff_from_double(sc.core_star), as = ff_from_double(sc.cut_star);
-    for (int m = t; m < nm; m += 2 * B) {
-      const int m2 = min(m + B, nm - 1);           // the second member of the pass (a repeat is dropped)
-      ff mx, my, b, sv, av, nx, ny, nb, nsv, nav;
-      member_ff<MODE>(P, m, sc, lf, bf, af, bs, cs, as, mx, my, b, sv, av);
-      member_ff<MODE>(P, m2, sc, lf, bf, af, bs, cs, as, nx, ny, nb, nsv, nav);
-      ff pxx, pyy, pxy, qxx, qyy, qxy;
-      member_psi_ff(offset_ff(tf.x, tf.y, mx.hi, mx.lo), offset_ff(tf.z, tf.w, my.hi, my.lo), b, sv, av, pxx,
-                    pyy, pxy);
-      member_psi_ff(offset_ff(tf.x, tf.y, nx.hi, nx.lo), offset_ff(tf.z, tf.w, ny.hi, ny.lo), nb, nsv, nav,
-                    qxx, qyy, qxy);
-      a0 = ff_add(a0, pxx); a1 = ff_add(a1, pyy); a2 = ff_add(a2, pxy);
-      if (m + B < nm) { a0 = ff_add(a0, qxx); a1 = ff_add(a1, qyy); a2 = ff_add(a2, qxy); }
+  if (nm == 0) return;
+  lf_scaling sc = P.sc;
+  const bool sampled = (C.scal_plane == 0) && C.scal_free;
+  if (sampled) sample_scaling(C, th, sc);
+  const bool lf = sampled && C.scal_p[LF_S_LAM] >= 0, bf = sampled && C.scal_p[LF_S_BETA] >= 0;
+  const bool af = sampled && C.scal_p[LF_S_ALPHA] >= 0;
+  const ff bs = ff_from_double(sc.b_star), cs = ff_from_double(sc.core_star), as = ff_from_double(sc.cut_star);
+  for (int m = t; m < nm; m += B) {
+    ff mx, my, b, sv, av;
+    member_ff<MODE>(P, m, sc, lf, bf, af, bs, cs, as, mx, my, b, sv, av);
+#pragma unroll
+    for (int k = 0; k < LF_REFINE_BATCH; ++k) {
+      if (k >= nb) break;
+      ff pxx, pyy, pxy;
+      member_psi_ff(offset_ff(tf[k].x, tf[k].y, mx.hi, mx.lo), offset_ff(tf[k].z, tf[k].w, my.hi, my.lo), b, sv,
+                    av, pxx, pyy, pxy);
+      p[k][0] = ff_add(p[k][0], pxx); p[k][1] = ff_add(p[k][1], pyy); p[k][2] = ff_add(p[k][2], pxy);
     }
   }
-  p[0] = a0; p[1] = a1; p[2] = a2;
+}
+
+// Float-float sums over the block of n (<= 12) values per thread; the totals land in out[0..n)
+// (shared memory), visible to every thread on return.  red holds 12 float-float values per warp.
+__device__ __forceinline__ void block_sums_ff(const ff* v, int n, ff* red, ff* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = 0; j < n; ++j) {
+    ff x = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = ff_add(x, ff_shfl_xor(x, o));
+    if (lane == 0) red[warp * 12 + j] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    ff r = ff_zero();
+    for (int w = 0; w < nw; ++w) r = ff_add(r, red[w * 12 + threadIdx.x]);
+    out[threadIdx.x] = r;
+  }
+  __syncthreads();
 }
 
 // Float-float sum over the block (every thread takes part); the total is returned on thread 0.
@@ -1182,44 +1231,44 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         // FP32 rounding of beta moves chi^2 only by 2 (M d) . d beta, which stays small: the
         // family's sum of M_i d_i is zero at beta_model.
         const int nref = C.np == 1 ? min(*s_nref, LF_REFINE_MAX) : 0;
-        for (int q = 0; q < nref; ++q) {
-          const int i = s_ref[q];
-          ff p3[3];
-          refine_psi<MODE>(C, s, th, i, smem, fraw, free_dig ? free_raw : nullptr, p3);
-          ff* fsc = reinterpret_cast<ff*>(scratch);
-          ff tot[3];
-          for (int c3 = 0; c3 < 3; ++c3) tot[c3] = block_sum_ff(p3[c3], fsc);
-          if (tid == 0)
-            for (int c3 = 0; c3 < 3; ++c3) fsc[16 + c3] = tot[c3];
-          __syncthreads();
-          if (tid < 3) {
+        for (int q0 = 0; q0 < nref; q0 += LF_REFINE_BATCH) {
+          const int nb = min(LF_REFINE_BATCH, nref - q0);
+          ff p3[LF_REFINE_BATCH][3];
+          refine_psi<MODE>(C, s, th, s_ref + q0, nb, smem, fraw, free_dig ? free_raw : nullptr, p3);
+          // the sums of every image of the pass: warp partials, then the totals
+          ff* red = reinterpret_cast<ff*>(smem + C.off_rscr);
+          ff* tot = red + 12 * (blockDim.x >> 5);
+          block_sums_ff(&p3[0][0], 3 * nb, red, tot);
+          if (tid < 3 * nb) {
             // M = adj(A) S^-1 adj(A) / det(A)^2 (A symmetric), one element per thread
+            const int k = tid / 3, el = tid - 3 * k, i = s_ref[q0 + k];
+            const ff* ps = tot + 3 * k;
             float* r = imgf + i * ISF;
             const float2 afa = faf[C.img_fam[i]];
             const ff a = ff_make(afa.x, afa.y);
-            const ff A00 = ff_add_f(ff_neg(ff_mul(a, fsc[16])), 1.0f);
-            const ff A11 = ff_add_f(ff_neg(ff_mul(a, fsc[17])), 1.0f);
-            const ff A01 = ff_neg(ff_mul(a, fsc[18]));
+            const ff A00 = ff_add_f(ff_neg(ff_mul(a, ps[0])), 1.0f);
+            const ff A11 = ff_add_f(ff_neg(ff_mul(a, ps[1])), 1.0f);
+            const ff A01 = ff_neg(ff_mul(a, ps[2]));
             const ff det = ff_sub(ff_mul(A00, A11), ff_sqr(A01));
             const ff inv2 = ff_rcp(ff_sqr(det));
             const float4 sv = C.sinv_f[i];
             // T = S^-1 adj(A), adj(A) = [[A11, -A01], [-A01, A00]]
             ff N;
-            if (tid == 0) {
+            if (el == 0) {
               const ff T00 = ff_sub(ff_mul_f(A11, sv.x), ff_mul_f(A01, sv.y));
               const ff T10 = ff_sub(ff_mul_f(A11, sv.y), ff_mul_f(A01, sv.z));
               N = ff_sub(ff_mul(A11, T00), ff_mul(A01, T10));
-              r[4] = fsc[16].hi; r[5] = fsc[16].lo; r[6] = fsc[17].hi; r[7] = fsc[17].lo;
-              r[8] = fsc[18].hi; r[9] = fsc[18].lo;
+              r[4] = ps[0].hi; r[5] = ps[0].lo; r[6] = ps[1].hi; r[7] = ps[1].lo;
+              r[8] = ps[2].hi; r[9] = ps[2].lo;
               r[21] = 1.0f;     // M in float-float words 14..19 (the forward pass reads no mu)
             } else {
               const ff T01 = ff_sub(ff_mul_f(A00, sv.y), ff_mul_f(A01, sv.x));
               const ff T11 = ff_sub(ff_mul_f(A00, sv.z), ff_mul_f(A01, sv.y));
-              N = tid == 1 ? ff_sub(ff_mul(A11, T01), ff_mul(A01, T11)) : ff_sub(ff_mul(A00, T11), ff_mul(A01, T01));
+              N = el == 1 ? ff_sub(ff_mul(A11, T01), ff_mul(A01, T11)) : ff_sub(ff_mul(A00, T11), ff_mul(A01, T01));
             }
             const ff M = ff_mul(N, inv2);
-            r[14 + 2 * tid] = M.hi;
-            r[15 + 2 * tid] = M.lo;
+            r[14 + 2 * el] = M.hi;
+            r[15 + 2 * el] = M.lo;
           }
         }
         if (nref > 0) __syncthreads();
@@ -2145,6 +2194,9 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
   o = al(o); C.off_free = o; o += (uint32_t)C.n_free * 64u;
   // per sample: a_dis of each family (double, float-float) and the parameter setting it
   o = al(o); C.off_fama = o; o += (uint32_t)C.n_fam * (8u + 8u + 4u);
+  // the near-critical refinement's reduction scratch (mixed tiers)
+  o = al(o); C.off_rscr = o;
+  if (mixed) o += ((uint32_t)block / 32u + 1u) * 12u * 8u;
   const uint32_t var = al(o);
   // forward passes: the members as packed pairs (mixed tier) or scalar records
   uint32_t of = var, os = var;
