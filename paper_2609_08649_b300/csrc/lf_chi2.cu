@@ -53,6 +53,7 @@ struct PlaneDesc {
   uint32_t off_rawc, off_mpre, off_dc;
   uint32_t off_dm;                 // scalar member records (adjoint, flux / time-delay pass)
   uint32_t off_dmp;                // the mixed tier's packed pairs (forward passes); = off_dm else
+  uint32_t off_mfac;               // the mixed tier's members' base factors (fb, fs, fa), FP32
 };
 
 struct ClusterDesc {
@@ -865,6 +866,17 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           if (i >= P.nm) {      // zero-strength pad of an odd member count
             pair_lane(dp[i >> 1], i & 1, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 2.f);
             continue;
+          }
+          if (!fresh && !lam_free && !beta_free && !alpha_free) {
+            // only the scaling relation's amplitudes are sampled: the centres stay, and the base
+            // factors are in shared memory (no reload of the plan's table)
+            const float3 f3 = reinterpret_cast<const float3*>(smem + P.off_mfac)[i];
+            pair_lane_scale(dp[i >> 1], i & 1, bstar * f3.x, cstar * f3.y, astar * f3.z);
+            continue;
+          }
+          if (fresh) {
+            const MemPreF& mb = reinterpret_cast<const MemPreF*>(P.mpre)[i];
+            reinterpret_cast<float3*>(smem + P.off_mfac)[i] = make_float3(mb.fb, mb.fs, mb.fa);
           }
         }
         const MemPre& m = mp[i];
@@ -2205,6 +2217,8 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
     P.off_dmp = al(of);
     of = P.off_dmp + (precision == LF_MIXED ? mem_records<MemPair>(P.nm) * (uint32_t)sizeof(MemPair)
                                             : (uint32_t)P.nm * mem_sz);
+    P.off_mfac = al(of);
+    if (precision == LF_MIXED) of = P.off_mfac + (uint32_t)P.nm * 12u;
     P.off_dm = al(os);
     os = P.off_dm + (uint32_t)P.nm * mem_sz;
   }

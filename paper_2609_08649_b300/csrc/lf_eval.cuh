@@ -170,6 +170,14 @@ __device__ __forceinline__ void pair_lane(MemPair& p, int lane, float xh, float 
   f[16] = a + s; f[18] = b * (a - s); f[20] = b; f[22] = 0.f;
 }
 
+// Rewrites lane `lane`'s strength, core and cut fields (with the derived constants) of a packed
+// pair record, keeping its centre.
+__device__ __forceinline__ void pair_lane_scale(MemPair& p, int lane, float b, float s, float a) {
+  float* f = reinterpret_cast<float*>(&p) + lane;
+  f[8] = s * s; f[10] = a * a; f[12] = s; f[14] = a;
+  f[16] = a + s; f[18] = b * (a - s); f[20] = b;
+}
+
 // Float-float tier: every deflection in float-float, accumulated in float-float.
 template <int PPT>
 __device__ __forceinline__ void accumulate_ext(const CompT<float>* dc, int nc, const MemX* dm,
