@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(LF_AMAP_THREADS, LF_ANCHOR_MINB) k_map_anchor(
                                                                   lf_scaling sc, PosArgs P, OutArgs O, int chunk) {
   constexpr int NT = LF_AMAP_THREADS, PPT = LF_AMAP_PPT, NWARP = NT / 32;
   const ff a_ff = ff_from_double(O.a_dis);
+  const ff dxf = ff_from_double(P.dx), dyf = ff_from_double(P.dy);
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   const AnchorLayout L = anchor_layout(nc, nm);
@@ -467,10 +468,21 @@ __global__ void __launch_bounds__(LF_AMAP_THREADS, LF_ANCHOR_MINB) k_map_anchor(
     float2 e2x[PPT], e2y[PPT], ee[PPT], ex2[PPT], ey2[PPT];
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-      const double exd = x[q] - cx, eyd = y[q] - cy;
-      const float ex = (float)exd, ey = (float)eyd;
+      float ex, ey;
+      if constexpr (GRID) {
+        // the offset from the anchor is (l - 7.5) times the pixel size for the l-th pixel of the
+        // tile's row (column): one float-float product on the FP32 pipe
+        const int t = tid + NT * q;
+        const ff gx = ff_mul_f(dxf, (float)(t & (LF_ATILE - 1)) - 0.5f * (LF_ATILE - 1));
+        const ff gy = ff_mul_f(dyf, (float)(t / LF_ATILE) - 0.5f * (LF_ATILE - 1));
+        ex = gx.hi; ey = gy.hi;
+        exl[q] = gx.lo; eyl[q] = gy.lo;
+      } else {
+        const double exd = x[q] - cx, eyd = y[q] - cy;
+        ex = (float)exd; ey = (float)eyd;
+        exl[q] = (float)(exd - (double)ex); eyl[q] = (float)(eyd - (double)ey);
+      }
       exf[q] = ex; eyf[q] = ey;
-      exl[q] = (float)(exd - (double)ex); eyl[q] = (float)(eyd - (double)ey);
       e2x[q] = make_float2(2.f * ex, 2.f * ex); e2y[q] = make_float2(2.f * ey, 2.f * ey);
       ee[q] = make_float2(fmaf(ex, ex, ey * ey), fmaf(ex, ex, ey * ey));
       ex2[q] = make_float2(ex, ex); ey2[q] = make_float2(ey, ey);
