@@ -1191,6 +1191,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         const int f = C.img_fam[i];
         ff bx, by;
         float a00, a01, a10, a11, det;
+        ff fA00 = ff_zero(), fA11 = ff_zero(), fA01 = ff_zero();
         if (C.np == 1) {
           const float2 af = faf[f];
           const ff a = ff_make(af.x, af.y);
@@ -1202,6 +1203,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           const ff A01 = ff_neg(ff_mul(a, ff_make(r[8], r[9])));
           det = ff_sub(ff_mul(A00, A11), ff_sqr(A01)).hi;
           a00 = A00.hi; a11 = A11.hi; a01 = a10 = A01.hi;
+          fA00 = A00; fA11 = A11; fA01 = A01;
           if constexpr (REFINE)
             if (fabsf(det) < refine_det<MODE>()) {
               const int q = atomicAdd(s_nref, 1);
@@ -1233,6 +1235,23 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         r[16] = fmaf(m01, X01, m11 * X11);
         r[17] = m00; r[18] = m01; r[19] = m10; r[20] = m11;
         r[21] = 0.0f;                 // M in FP32 words 14..16
+        if constexpr (REFINE && MODE == LF_FF) {
+          if (C.np == 1) {
+            // the float-float tier's forward chi^2 keeps M of every image in float-float words
+            // (M = adj(A) S^-1 adj(A) / det A^2 from the float-float A): FP32 words of M lose its
+            // weak direction already at moderate magnification (|det A| ~ 0.02)
+            const ff inv2 = ff_rcp(ff_sqr(ff_sub(ff_mul(fA00, fA11), ff_sqr(fA01))));
+            const ff T00 = ff_sub(ff_mul_f(fA11, sv.x), ff_mul_f(fA01, sv.y));
+            const ff T10 = ff_sub(ff_mul_f(fA11, sv.y), ff_mul_f(fA01, sv.z));
+            const ff T01 = ff_sub(ff_mul_f(fA00, sv.y), ff_mul_f(fA01, sv.x));
+            const ff T11 = ff_sub(ff_mul_f(fA00, sv.z), ff_mul_f(fA01, sv.y));
+            const ff M00 = ff_mul(ff_sub(ff_mul(fA11, T00), ff_mul(fA01, T10)), inv2);
+            const ff M01 = ff_mul(ff_sub(ff_mul(fA11, T01), ff_mul(fA01, T11)), inv2);
+            const ff M11 = ff_mul(ff_sub(ff_mul(fA00, T11), ff_mul(fA01, T01)), inv2);
+            r[14] = M00.hi; r[15] = M00.lo; r[16] = M01.hi; r[17] = M01.lo; r[18] = M11.hi; r[19] = M11.lo;
+            r[21] = 1.0f;
+          }
+        }
       }
       __syncthreads();
       if constexpr (REFINE) {

@@ -222,6 +222,27 @@ def test_multicluster_gradient_one_launch(lib, c4, prec):
         assert grad_ok(g[sl], gref.numpy(), prec)
 
 
+def test_multicluster_forward_every_sample_ff(lib):
+    """The float-float tier's forward chi^2 on all 16 synthetic clusters x 64 samples in one
+    launch, every sample within the stated 1e-5 of the FP64 kernel.  Its M is kept in
+    float-float words: with FP32 words, whose weak direction is lost already at |det A| ~ 0.02,
+    one sample missed by 1.0e-5 (the mixed tier's forward launch misses on 13 samples, 3.3e-4
+    worst, from its FP32 member sums; see the design notes)."""
+    api, PM = lib
+    wls = W.multicluster_c4()
+    cats = [W.load_catalogue(f"multicluster_{c:02d}") for c in range(len(wls))]
+    spc = 64
+    th = torch.tensor(np.concatenate([W.sample_thetas(W.replace(w, n_samples=spc), w.seed) for w in wls]),
+                      device="cuda")
+    ins = [PM.cluster_input(w, c) for w, c in zip(wls, cats)]
+    ref = api.Plan(ins, spc * len(wls), "fp64").chi2(th).cpu().numpy()
+    got = api.Plan(ins, spc * len(wls), "ff", flags=api.FLAG_GRAPH | api.FLAG_AUTOTUNE).chi2(th).cpu().numpy()
+    rel = np.abs(got - ref) / np.abs(ref)
+    print(f"ff, 16 clusters: max rel {rel.max():.3e}")
+    assert rel.max() <= 1e-5
+    api.device_error()
+
+
 def multiplane_case(n_samples=6):
     """Three planes; besides the main plane's halos and scaling relation, the sampled
     parameters include components of both later planes (an NFW's position, a dPIE's
