@@ -91,7 +91,6 @@ struct ClusterDesc {
   int mpg_stride;                  // multi-plane adjoint: doubles per image record
   uint32_t off_img, off_imgd, off_fam, off_par, off_free, off_newton, off_fama, off_aux, off_mpg;
   uint32_t off_auxg;               // adjoint of the flux / time-delay terms: per image records
-  uint32_t off_rscr;               // near-critical refinement: 12 float-float sums per warp + 12
   // shared memory of each launch kind: the common regions, then only the member records and
   // scratch that kind reads (source-plane chi^2; image-plane chi^2; flux / time delay; adjoint)
   uint32_t smem, smem_img, smem_aux, smem_grad;
@@ -448,241 +447,13 @@ __device__ void d3_sum(const CompT<T>* dc, int nc, const Mem* dm, int nm, int k0
 }
 
 // M of a mixed-tier image record: FP32 words 14..16, or float-float words 14..19 when word 21
-// is set (images re-evaluated near a critical curve).
+// is set (the forward source-plane chi^2).
 __device__ __forceinline__ void image_M(const float* r, ff& M00, ff& M01, ff& M11) {
   if (r[21] != 0.0f) {
     M00 = ff_make(r[14], r[15]); M01 = ff_make(r[16], r[17]); M11 = ff_make(r[18], r[19]);
   } else {
     M00 = ff_make(r[14], 0.f); M01 = ff_make(r[15], 0.f); M11 = ff_make(r[16], 0.f);
   }
-}
-
-// Near-critical refinement of the mixed tiers' source-plane chi^2: images whose |det A| (from
-// the tier's sums) is below refine_det get psi_ij with every component in float-float
-// (LF_MIXED: 3e-3, below which its FP32 member sums, not psi_ij, set the error; LF_FF: 1e-2)
-template <int MODE> __device__ __forceinline__ float refine_det() { return MODE == LF_MIXED ? 3e-3f : 1e-2f; }
-constexpr int LF_REFINE_MAX = 32;      // images per sample refined (more stay at the tier's precision)
-
-// psi_ij of a unit-strength softened isothermal ellipsoid in its (u, v) frame (the closed form of
-// sie_psi) with every operation in float-float.
-__device__ __forceinline__ void sie_psi_ff(const ff& u, const ff& v, const ff& q, const ff& q2, const ff& s,
-                                           const ff& s2, ff& puu, ff& pvv, ff& puv) {
-  const ff uu = ff_sqr(u), vv = ff_sqr(v);
-  const ff psi = ff_sqrt(ff_add(ff_mul(q2, ff_add(s2, uu)), vv));
-  const ff sp = ff_mul(s, psi);
-  const ff D = ff_add(ff_add(ff_mul(ff_add_f(q2, 1.f), s2), ff_mul_f(sp, 2.f)), ff_add(uu, vv));
-  const ff f = ff_div(q, ff_mul(psi, D));
-  puu = ff_mul(f, ff_add(ff_add(ff_mul(q2, s2), vv), sp));
-  pvv = ff_mul(f, ff_add(ff_add(s2, uu), sp));
-  puv = ff_neg(ff_mul(f, ff_mul(u, v)));
-}
-
-// psi_ij of a round pseudo-Jaffe member (kbar delta_ij + t x_i x_j, kbar = b (P - Q),
-// t = b (Q^2/R - P^2/S)) in float-float; the far-field differences lose log2(r / a) bits of
-// the 48, which leaves ~1e-12 relative.
-__device__ __forceinline__ void member_psi_ff(const ff& dx, const ff& dy, const ff& b, const ff& s,
-                                              const ff& a, ff& pxx, ff& pyy, ff& pxy) {
-  const ff r2 = ff_add(ff_sqr(dx), ff_sqr(dy));
-  const ff S = ff_sqrt(ff_add(ff_sqr(s), r2)), R = ff_sqrt(ff_add(ff_sqr(a), r2));
-  const ff P = ff_rcp(ff_add(S, s)), Q = ff_rcp(ff_add(R, a));
-  const ff kb = ff_mul(b, ff_sub(P, Q));
-  const ff t = ff_mul(b, ff_sub(ff_mul(ff_sqr(Q), ff_rcp(R)), ff_mul(ff_sqr(P), ff_rcp(S))));
-  const ff tdx = ff_mul(t, dx);
-  pxx = ff_add(kb, ff_mul(tdx, dx));
-  pyy = ff_add(kb, ff_mul(ff_mul(t, dy), dy));
-  pxy = ff_mul(tdx, dy);
-}
-
-// psi_ij of CSE term i of the elliptical NFW (unit kappa_s, r_s = 1: the closed form of enfw_uv)
-// in its (u, v) frame, float-float.
-__device__ __forceinline__ void enfw_term_psi_ff(const ff& u, const ff& v, const ff& q, const ff& q2, int i,
-                                                 ff& puu, ff& pvv, ff& puv) {
-  const float2 sv = c_cse_sff[i], cv = c_cse_cff[i];
-  const ff s = ff_make(sv.x, sv.y), s2 = ff_sqr(s);
-  const ff uu = ff_sqr(u), vv = ff_sqr(v);
-  const ff P = ff_sqrt(ff_add(ff_mul(q2, ff_add(s2, uu)), vv)), iP = ff_rcp(P);
-  const ff D = ff_add(ff_add(ff_mul(ff_add_f(q2, 1.f), s2), ff_mul_f(ff_mul(P, s), 2.f)), ff_add(uu, vv));
-  const ff iD = ff_rcp(D);
-  const ff A = ff_add(ff_mul(q2, s), P), B = ff_add(P, s);
-  const ff f = ff_mul(ff_mul(ff_make(cv.x, cv.y), q), ff_mul(iP, iD));
-  const ff iP2 = ff_sqr(iP), g = ff_mul_f(ff_mul(iP, iD), 2.f);
-  const ff q2s = ff_mul(q2, s);
-  puu = ff_mul(f, ff_sub(ff_sub(A, ff_mul(ff_mul(ff_mul(q2s, q2), uu), iP2)), ff_mul(ff_mul(g, uu), ff_sqr(A))));
-  pvv = ff_mul(f, ff_sub(ff_sub(B, ff_mul(ff_mul(s, vv), iP2)), ff_mul(ff_mul(g, vv), ff_sqr(B))));
-  puv = ff_neg(ff_mul(ff_mul(f, ff_mul(u, v)), ff_add(ff_mul(q2s, iP2), ff_mul(g, ff_mul(A, B)))));
-}
-
-// Member m's centre, strength, core and cut as float-float, for this sample's scaling relation.
-template <int MODE>
-__device__ __forceinline__ void member_ff(const PlaneDesc& P, int m, const lf_scaling& sc, bool lam_free,
-                                          bool beta_free, bool alpha_free, const ff& bs, const ff& cs,
-                                          const ff& as, ff& mx, ff& my, ff& b, ff& sv, ff& av) {
-  if constexpr (MODE == LF_MIXED) {
-    const MemPreF e = reinterpret_cast<const MemPreF*>(P.mpre)[m];
-    mx = ff_make(e.xh, e.xl);
-    my = ff_make(e.yh, e.yl);
-    ff fb = ff_make(e.fb, e.fbl), fs = ff_make(e.fs, e.fsl), fa = ff_make(e.fa, e.fal);
-    // a sampled exponent changes a factor by exp(d e ln L), applied as f (1 + expm1(.)): the FP32
-    // expm1 rounds only the small change
-    if (lam_free) fb = ff_add(fb, ff_mul_f(fb, expm1f((float)(2.0 * (sc.lam - P.sc.lam)) * e.lnl)));
-    if (beta_free) fs = ff_add(fs, ff_mul_f(fs, expm1f((float)(sc.beta - P.sc.beta) * e.lnl)));
-    if (alpha_free) fa = ff_add(fa, ff_mul_f(fa, expm1f((float)(sc.alpha - P.sc.alpha) * e.lnl)));
-    b = ff_mul(bs, fb); sv = ff_mul(cs, fs); av = ff_mul(as, fa);
-  } else {
-    const MemPreD e = reinterpret_cast<const MemPreD*>(P.mpre)[m];
-    mx = ff_from_double(e.x);
-    my = ff_from_double(e.y);
-    b = ff_from_double(sc.b_star * (lam_free ? exp(2.0 * sc.lam * e.lnl) : e.fb));
-    sv = ff_from_double(sc.core_star * (beta_free ? exp(sc.beta * e.lnl) : e.fs));
-    av = ff_from_double(sc.cut_star * (alpha_free ? exp(sc.alpha * e.lnl) : e.fa));
-  }
-}
-
-// Near-critical images refined per pass (each thread's member records are loaded once per pass
-// and evaluated at all of them, as independent chains).
-constexpr int LF_REFINE_BATCH = 4;
-
-// psi_ij (float-float) of one explicit component's part at position (x, y) (float-float words of
-// tf): an ellipsoid of an isothermal component or dPIE, a CSE term of an elliptical NFW, the
-// shear, the multipole; any other kind (the spherical NFW) whole, in FP64 from its fields.
-// Returns false for an empty part.
-__device__ __forceinline__ bool comp_part_psi_ff(const CompT<float>& cf, int part, const float4& tf,
-                                                 const ClusterDesc& C, int s, int c, const unsigned char* smem,
-                                                 const lf_comp* fraw, const lf_comp* free_raw, ff& pxx,
-                                                 ff& pyy, ff& pxy) {
-  if (cf.kind == 0 || (part >= (cf.kind == K_DPIE ? 2 : cf.kind == K_ENFW ? LF_CSE_N : 1))) return false;
-  if (cf.kind == K_ENFW || cf.kind == K_SIE || cf.kind == K_DPIE) {
-    const ff cc = ff_make(cf.c, cf.lc), sn = ff_make(cf.sn, cf.lsn), b = ff_make(cf.b, cf.lb);
-    const ff dx = offset_ff(tf.x, tf.y, cf.xh, cf.xl), dy = offset_ff(tf.z, tf.w, cf.yh, cf.yl);
-    ff u = ff_add(ff_mul(cc, dx), ff_mul(sn, dy)), v = ff_sub(ff_mul(cc, dy), ff_mul(sn, dx));
-    const ff q2 = ff_make(cf.q2, cf.lq2), q = ff_sqrt(q2);
-    ff puu, pvv, puv, k;
-    if (cf.kind == K_ENFW) {
-      // term `part` of the CSE sum: Psi = 2 kappa_s Psi_cse at (u, v) / r_s
-      const ff irs = ff_rcp(ff_make(cf.s1, cf.ls1));
-      u = ff_mul(u, irs);
-      v = ff_mul(v, irs);
-      enfw_term_psi_ff(u, v, q, q2, part, puu, pvv, puv);
-      k = ff_mul_f(b, 2.f);
-    } else if (part == 0) {
-      sie_psi_ff(u, v, q, q2, ff_make(cf.s1, cf.ls1), ff_make(cf.s1sq, cf.ls1sq), puu, pvv, puv);
-      k = b;
-    } else {             // the dPIE's cut ellipsoid, subtracted
-      sie_psi_ff(u, v, q, q2, ff_make(cf.s2, cf.ls2), ff_make(cf.s2sq, cf.ls2sq), puu, pvv, puv);
-      k = ff_neg(b);
-    }
-    const ff c2 = ff_sqr(cc), s2 = ff_sqr(sn), csn = ff_mul(cc, sn);
-    const ff cs2puv = ff_mul_f(ff_mul(csn, puv), 2.f);
-    pxx = ff_mul(k, ff_add(ff_sub(ff_mul(c2, puu), cs2puv), ff_mul(s2, pvv)));
-    pyy = ff_mul(k, ff_add(ff_add(ff_mul(s2, puu), cs2puv), ff_mul(c2, pvv)));
-    pxy = ff_mul(k, ff_add(ff_mul(csn, ff_sub(puu, pvv)), ff_mul(ff_sub(c2, s2), puv)));
-  } else if (cf.kind == K_SHEAR) {
-    const ff b = ff_make(cf.b, cf.lb);
-    pxx = ff_mul(b, ff_make(cf.c, cf.lc));
-    pyy = ff_neg(pxx);
-    pxy = ff_mul(b, ff_make(cf.sn, cf.lsn));
-  } else if (cf.kind == K_MPOLE3) {
-    // psi_ij of the third-order multipole (the form of multipole3), a function of n = x / r
-    const ff dx = offset_ff(tf.x, tf.y, cf.xh, cf.xl), dy = offset_ff(tf.z, tf.w, cf.yh, cf.yl);
-    const ff r2 = ff_add(ff_sqr(dx), ff_sqr(dy));
-    if (!(r2.hi > 0.f)) {
-      pxx = pyy = pxy = ff_zero();
-      return true;
-    }
-    const ff ir = ff_rcp(ff_sqrt(r2)), nx = ff_mul(dx, ir), ny = ff_mul(dy, ir);
-    const ff c3 = ff_make(cf.c, cf.lc), s3 = ff_make(cf.sn, cf.lsn), b = ff_make(cf.b, cf.lb);
-    const ff xx = ff_sqr(nx), yy = ff_sqr(ny), xy = ff_mul(nx, ny), d = ff_sub(xx, yy);
-    const ff G = ff_add(ff_mul(ff_mul(c3, nx), ff_sub(xx, ff_mul_f(yy, 3.f))),
-                        ff_mul(ff_mul(s3, ny), ff_sub(ff_mul_f(xx, 3.f), yy)));
-    const ff Hx = ff_mul_f(ff_add(ff_mul(c3, d), ff_mul_f(ff_mul(s3, xy), 2.f)), 3.f);
-    const ff Hy = ff_mul_f(ff_sub(ff_mul(s3, d), ff_mul_f(ff_mul(c3, xy), 2.f)), 3.f);
-    const ff L = ff_mul_f(ff_add(ff_mul(c3, nx), ff_mul(s3, ny)), 6.f);
-    const ff G3 = ff_mul_f(G, 3.f);
-    pxx = ff_mul(b, ff_add(ff_sub(ff_sub(L, ff_mul_f(ff_mul(nx, Hx), 2.f)), G), ff_mul(G3, xx)));
-    pyy = ff_mul(b, ff_add(ff_sub(ff_sub(ff_neg(L), ff_mul_f(ff_mul(ny, Hy), 2.f)), G), ff_mul(G3, yy)));
-    pxy = ff_mul(b, ff_add(ff_sub(ff_sub(ff_mul_f(ff_sub(ff_mul(s3, nx), ff_mul(c3, ny)), 6.f), ff_mul(ny, Hx)),
-                                  ff_mul(nx, Hy)), ff_mul(G3, xy)));
-  } else {
-    const PlaneDesc& P = C.pl[0];
-    lf_comp rc = reinterpret_cast<const lf_comp*>(smem + P.off_rawc)[c];
-    for (int f = 0; f < C.n_free; ++f)
-      if (C.free_plane[f] == 0 && C.free_comp[f] == c)
-        rc = free_raw ? free_raw[(size_t)s * LF_MAX_FREE + f] : fraw[f];
-    CompT<double> cd;
-    digest_one_comp<double>(rc, cd);
-    Out5<double> o;
-    eval_comp(cd, ((double)tf.x + (double)tf.y) - cd.xh, ((double)tf.z + (double)tf.w) - cd.yh, o);
-    pxx = ff_from_double(o.pxx); pyy = ff_from_double(o.pyy); pxy = ff_from_double(o.pxy);
-  }
-  return true;
-}
-
-// This thread's share of psi_ij in float-float at nb (<= LF_REFINE_BATCH) images img[] of a
-// single-plane cluster, for sample s.  The members (plan pre-table, this sample's scaling
-// relation, Eq. scaling) go two per pass to threads 0, 1, ..., each evaluated at every image;
-// the explicit components' parts (comp_part_psi_ff) go one (image, component, part) each to
-// the last threads, which hold fewer members.
-template <int MODE>
-__device__ __noinline__ void refine_psi(const ClusterDesc& C, int s, const double* th, const int* img,
-                                        int nb, const unsigned char* smem, const lf_comp* fraw,
-                                        const lf_comp* free_raw, ff (&p)[LF_REFINE_BATCH][3]) {
-  const PlaneDesc& P = C.pl[0];
-  const int nc = P.nc, nm = P.nm, B = blockDim.x, t = threadIdx.x;
-  float4 tf[LF_REFINE_BATCH];
-#pragma unroll
-  for (int k = 0; k < LF_REFINE_BATCH; ++k) {
-    tf[k] = C.theta_ff[img[min(k, nb - 1)]];
-    p[k][0] = ff_zero(); p[k][1] = ff_zero(); p[k][2] = ff_zero();
-  }
-  constexpr int NPART = LF_CSE_N > 2 ? LF_CSE_N : 2;
-  const CompT<float>* dc = reinterpret_cast<const CompT<float>*>(smem + P.off_dc);
-  for (int task = B - 1 - t; task < NPART * nc * nb; task += B) {
-    const int k = task / (NPART * nc), rest = task - k * NPART * nc;
-    const int c = rest / NPART, part = rest - c * NPART;
-    ff pxx, pyy, pxy;
-    if (!comp_part_psi_ff(dc[c], part, tf[k], C, s, c, smem, fraw, free_raw, pxx, pyy, pxy)) continue;
-#pragma unroll
-    for (int kk = 0; kk < LF_REFINE_BATCH; ++kk)
-      if (kk == k) { p[kk][0] = ff_add(p[kk][0], pxx); p[kk][1] = ff_add(p[kk][1], pyy); p[kk][2] = ff_add(p[kk][2], pxy); }
-  }
-  if (nm == 0) return;
-  lf_scaling sc = P.sc;
-  const bool sampled = (C.scal_plane == 0) && C.scal_free;
-  if (sampled) sample_scaling(C, th, sc);
-  const bool lf = sampled && C.scal_p[LF_S_LAM] >= 0, bf = sampled && C.scal_p[LF_S_BETA] >= 0;
-  const bool af = sampled && C.scal_p[LF_S_ALPHA] >= 0;
-  const ff bs = ff_from_double(sc.b_star), cs = ff_from_double(sc.core_star), as = ff_from_double(sc.cut_star);
-  for (int m = t; m < nm; m += B) {
-    ff mx, my, b, sv, av;
-    member_ff<MODE>(P, m, sc, lf, bf, af, bs, cs, as, mx, my, b, sv, av);
-#pragma unroll
-    for (int k = 0; k < LF_REFINE_BATCH; ++k) {
-      if (k >= nb) break;
-      ff pxx, pyy, pxy;
-      member_psi_ff(offset_ff(tf[k].x, tf[k].y, mx.hi, mx.lo), offset_ff(tf[k].z, tf[k].w, my.hi, my.lo), b, sv,
-                    av, pxx, pyy, pxy);
-      p[k][0] = ff_add(p[k][0], pxx); p[k][1] = ff_add(p[k][1], pyy); p[k][2] = ff_add(p[k][2], pxy);
-    }
-  }
-}
-
-// Float-float sums over the block of n (<= 12) values per thread; the totals land in out[0..n)
-// (shared memory), visible to every thread on return.  red holds 12 float-float values per warp.
-__device__ __forceinline__ void block_sums_ff(const ff* v, int n, ff* red, ff* out) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int j = 0; j < n; ++j) {
-    ff x = v[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x = ff_add(x, ff_shfl_xor(x, o));
-    if (lane == 0) red[warp * 12 + j] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < n) {
-    ff r = ff_zero();
-    for (int w = 0; w < nw; ++w) r = ff_add(r, red[w * 12 + threadIdx.x]);
-    out[threadIdx.x] = r;
-  }
-  __syncthreads();
 }
 
 // Float-float sum over the block (every thread takes part); the total is returned on thread 0.
@@ -718,8 +489,8 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
   // PASS 2: the flux / time-delay terms (the forward pass, or with GRAD their adjoint too); the
   // other instantiations carry none of that code
   constexpr bool AUX = PASS == 2;
-  // the forward source-plane chi^2 of the mixed tiers re-evaluates near-critical images in FP64
-  constexpr bool REFINE = MIXED && PASS == 0 && !GRAD;
+  // the forward source-plane chi^2 of the mixed tiers keeps every image's M in float-float words
+  constexpr bool FFM = MIXED && PASS == 0 && !GRAD;
   constexpr bool FFSUM = PACKM && PASS == 0;
   // images per evaluation task (independent chains per thread; with packed members, two
   // member evaluations per instruction and chain); the FP64 tier takes two
@@ -728,15 +499,12 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   int* s_item = reinterpret_cast<int*>(smem + 8);
   int* wctr = reinterpret_cast<int*>(smem + 288);           // warp-task counter (packed members)
-  int* s_nref = reinterpret_cast<int*>(smem + 292);         // near-critical images of the sample
-  int* s_ref = reinterpret_cast<int*>(smem + 296);          // ... their indices (LF_REFINE_MAX)
   double* scratch = reinterpret_cast<double*>(smem + 16);   // 32 doubles
   const int tid = threadIdx.x;
   float2* tab = reinterpret_cast<float2*>(smem + LF_TAB_OFF);
   if (tid == 0) {
     mbar_init(bar, 1);
     *wctr = 0;
-    *s_nref = 0;
   }
   init_ff_tables(tab);
   if (tid == 0) *s_item = atomicAdd(counter, 1);     // the first work item
@@ -805,11 +573,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
       cur = c;
     }
     __syncthreads();
-    if (tid == 0) {
-      // every thread has read this item (and the previous item's count of near-critical images)
-      *s_item = atomicAdd(counter, 1);
-      *s_nref = 0;
-    }
+    if (tid == 0) *s_item = atomicAdd(counter, 1);    // every thread has read this item
 
     // ---- A1: this sample's parameters into the tables
     for (int f = tid; f < C.n_free; f += blockDim.x) {
@@ -1192,6 +956,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         ff bx, by;
         float a00, a01, a10, a11, det;
         ff fA00 = ff_zero(), fA11 = ff_zero(), fA01 = ff_zero();
+        double dM[3] = {0.0, 0.0, 0.0};     // several planes: M from the FP64 A (forward chi^2)
         if (C.np == 1) {
           const float2 af = faf[f];
           const ff a = ff_make(af.x, af.y);
@@ -1204,11 +969,6 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           det = ff_sub(ff_mul(A00, A11), ff_sqr(A01)).hi;
           a00 = A00.hi; a11 = A11.hi; a01 = a10 = A01.hi;
           fA00 = A00; fA11 = A11; fA01 = A01;
-          if constexpr (REFINE)
-            if (fabsf(det) < refine_det<MODE>()) {
-              const int q = atomicAdd(s_nref, 1);
-              if (q < LF_REFINE_MAX) s_ref[q] = i;
-            }
         } else {
           const double* st = imgd + i * ISD;
           double dbx = C.theta[2 * i], dby = C.theta[2 * i + 1];
@@ -1223,6 +983,17 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           by = ff_from_double(dby);
           det = (float)(A00 * A11 - A01 * A10);
           a00 = (float)A00; a01 = (float)A01; a10 = (float)A10; a11 = (float)A11;
+          if constexpr (FFM) {
+            // M = mu^T S^-1 mu with mu = A^-1 (A not symmetric), from the FP64 A
+            const double id = 1.0 / (A00 * A11 - A01 * A10);
+            const double u00 = A11 * id, u01 = -A01 * id, u10 = -A10 * id, u11 = A00 * id;
+            const double s0 = C.sinv[3 * i], s1 = C.sinv[3 * i + 1], s2 = C.sinv[3 * i + 2];
+            const double X00 = s0 * u00 + s1 * u10, X01 = s0 * u01 + s1 * u11;
+            const double X10 = s1 * u00 + s2 * u10, X11 = s1 * u01 + s2 * u11;
+            dM[0] = u00 * X00 + u10 * X10;
+            dM[1] = u00 * X01 + u10 * X11;
+            dM[2] = u01 * X01 + u11 * X11;
+          }
         }
         const float id = 1.0f / det;
         const float m00 = a11 * id, m01 = -a01 * id, m10 = -a10 * id, m11 = a00 * id;
@@ -1235,11 +1006,18 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         r[16] = fmaf(m01, X01, m11 * X11);
         r[17] = m00; r[18] = m01; r[19] = m10; r[20] = m11;
         r[21] = 0.0f;                 // M in FP32 words 14..16
-        if constexpr (REFINE && MODE == LF_FF) {
-          if (C.np == 1) {
-            // the float-float tier's forward chi^2 keeps M of every image in float-float words
-            // (M = adj(A) S^-1 adj(A) / det A^2 from the float-float A): FP32 words of M lose its
-            // weak direction already at moderate magnification (|det A| ~ 0.02)
+        if constexpr (FFM) {
+          // M in float-float words (14..19; the forward pass reads no mu).  Near a critical curve
+          // M ~ mu^2 / sigma^2 is nearly of rank one, and its weak direction, which carries the
+          // family's chi^2, is lost in FP32 words of M already at moderate magnification
+          // (|det A| ~ 0.02): several planes from the FP64 A, one plane as
+          // M = adj(A) S^-1 adj(A) / det A^2 from the float-float A
+          if (C.np > 1) {
+            split_ff(dM[0], r[14], r[15]);
+            split_ff(dM[1], r[16], r[17]);
+            split_ff(dM[2], r[18], r[19]);
+            r[21] = 1.0f;
+          } else {
             const ff inv2 = ff_rcp(ff_sqr(ff_sub(ff_mul(fA00, fA11), ff_sqr(fA01))));
             const ff T00 = ff_sub(ff_mul_f(fA11, sv.x), ff_mul_f(fA01, sv.y));
             const ff T10 = ff_sub(ff_mul_f(fA11, sv.y), ff_mul_f(fA01, sv.z));
@@ -1254,56 +1032,6 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
         }
       }
       __syncthreads();
-      if constexpr (REFINE) {
-        // Images within |det A| < refine_det of a critical curve: psi_ij again with every
-        // component in float-float, and A, mu and M from them (beta is kept).  Near a critical
-        // curve M ~ mu^2 / sigma^2 is nearly of rank one, and its weak direction, which carries
-        // the family's chi^2, is lost with FP32 psi_ij (through det A) and FP32 words of M.  The
-        // FP32 rounding of beta moves chi^2 only by 2 (M d) . d beta, which stays small: the
-        // family's sum of M_i d_i is zero at beta_model.
-        const int nref = C.np == 1 ? min(*s_nref, LF_REFINE_MAX) : 0;
-        for (int q0 = 0; q0 < nref; q0 += LF_REFINE_BATCH) {
-          const int nb = min(LF_REFINE_BATCH, nref - q0);
-          ff p3[LF_REFINE_BATCH][3];
-          refine_psi<MODE>(C, s, th, s_ref + q0, nb, smem, fraw, free_dig ? free_raw : nullptr, p3);
-          // the sums of every image of the pass: warp partials, then the totals
-          ff* red = reinterpret_cast<ff*>(smem + C.off_rscr);
-          ff* tot = red + 12 * (blockDim.x >> 5);
-          block_sums_ff(&p3[0][0], 3 * nb, red, tot);
-          if (tid < 3 * nb) {
-            // M = adj(A) S^-1 adj(A) / det(A)^2 (A symmetric), one element per thread
-            const int k = tid / 3, el = tid - 3 * k, i = s_ref[q0 + k];
-            const ff* ps = tot + 3 * k;
-            float* r = imgf + i * ISF;
-            const float2 afa = faf[C.img_fam[i]];
-            const ff a = ff_make(afa.x, afa.y);
-            const ff A00 = ff_add_f(ff_neg(ff_mul(a, ps[0])), 1.0f);
-            const ff A11 = ff_add_f(ff_neg(ff_mul(a, ps[1])), 1.0f);
-            const ff A01 = ff_neg(ff_mul(a, ps[2]));
-            const ff det = ff_sub(ff_mul(A00, A11), ff_sqr(A01));
-            const ff inv2 = ff_rcp(ff_sqr(det));
-            const float4 sv = C.sinv_f[i];
-            // T = S^-1 adj(A), adj(A) = [[A11, -A01], [-A01, A00]]
-            ff N;
-            if (el == 0) {
-              const ff T00 = ff_sub(ff_mul_f(A11, sv.x), ff_mul_f(A01, sv.y));
-              const ff T10 = ff_sub(ff_mul_f(A11, sv.y), ff_mul_f(A01, sv.z));
-              N = ff_sub(ff_mul(A11, T00), ff_mul(A01, T10));
-              r[4] = ps[0].hi; r[5] = ps[0].lo; r[6] = ps[1].hi; r[7] = ps[1].lo;
-              r[8] = ps[2].hi; r[9] = ps[2].lo;
-              r[21] = 1.0f;     // M in float-float words 14..19 (the forward pass reads no mu)
-            } else {
-              const ff T01 = ff_sub(ff_mul_f(A00, sv.y), ff_mul_f(A01, sv.x));
-              const ff T11 = ff_sub(ff_mul_f(A00, sv.z), ff_mul_f(A01, sv.y));
-              N = el == 1 ? ff_sub(ff_mul(A11, T01), ff_mul(A01, T11)) : ff_sub(ff_mul(A00, T11), ff_mul(A01, T01));
-            }
-            const ff M = ff_mul(N, inv2);
-            r[14 + 2 * el] = M.hi;
-            r[15 + 2 * el] = M.lo;
-          }
-        }
-        if (nref > 0) __syncthreads();
-      }
       // ---- A8 (mixed tiers): per family, offsets e_i = beta_i - beta_ref from the family's
       // first image, G = sum M_i, g = sum M_i e_i, the 2x2 solve and chi^2_f, all in
       // float-float on the FP32 pipe (the FP64 pipe is the slow one on this part).  The
@@ -2225,9 +1953,6 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
   o = al(o); C.off_free = o; o += (uint32_t)C.n_free * 64u;
   // per sample: a_dis of each family (double, float-float) and the parameter setting it
   o = al(o); C.off_fama = o; o += (uint32_t)C.n_fam * (8u + 8u + 4u);
-  // the near-critical refinement's reduction scratch (mixed tiers)
-  o = al(o); C.off_rscr = o;
-  if (mixed) o += ((uint32_t)block / 32u + 1u) * 12u * 8u;
   const uint32_t var = al(o);
   // forward passes: the members as packed pairs (mixed tier) or scalar records
   uint32_t of = var, os = var;
