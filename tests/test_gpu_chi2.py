@@ -8,10 +8,11 @@ component (relative to the larger of |g_p| and 1e-2 max_p |g_p| of the sample). 
 tier's lf_chi2_grad_batch runs the float-float adjoint (its member deflections in float-float:
 the cotangents are weighted by d_i = beta_i - beta_model ~ sigma_pos, so FP32 deflections would
 put ~1e-4 relative errors on them), so its chi^2 and gradient share the float-float bounds.
-Near critical curves both mixed tiers form A from FP32 psi_ij, so chi^2 moves by ~u/|det A|
-and the gradient by ~u/|det A|^3: a sample with an image at |det A| < 1e-3 is held to the
-near-critical bounds (norm 1e-3, 1e-2 per component) and the first-order chi^2 bound of
-tests/helpers.chi2_mixed_bound."""
+The forward chi^2 (lf_chi2_batch) of the mixed tiers keeps M in float-float words and is held
+to 1e-5 on every sample, near critical curves included.  The adjoint launch forms A from FP32
+psi_ij and keeps M in FP32, so its gradient moves by ~u/|det A|^3 near a critical curve: a
+sample with an image at |det A| < 1e-3 is held to the near-critical bounds (norm 1e-3, 1e-2
+per component)."""
 import numpy as np
 import pytest
 import torch
@@ -107,10 +108,10 @@ def test_full_size_chi2_sampled(lib, c2):
 def test_every_benchmark_sample_within_tolerance(lib, c2, prec):
     """All 4096 samples of the benchmark launch (graph + tuner) within the stated 1e-5 of the
     FP64 kernel, not a subset: about 3 % of them put an image within |det A| < 3e-3 of a
-    critical curve, where the tiers' FP32 psi_ij and alpha alone would miss it by up to 3e-3
-    (those images are re-evaluated in FP64).  The FP64 kernel is held to the oracle at 1e-10
-    by test_cluster_chi2_matches_oracle; the eight samples with the image nearest a critical
-    curve are also compared with the oracle directly."""
+    critical curve, where M kept in FP32 words would miss it by up to 3e-3 (its weak
+    direction is lost; the tiers keep M in float-float words).  The FP64 kernel is held to the
+    oracle at 1e-10 by test_cluster_chi2_matches_oracle; the eight samples with the image
+    nearest a critical curve are also compared with the oracle directly."""
     api, PM = lib
     wl, cat, th = c2
     t = torch.tensor(th, device="cuda")
@@ -309,16 +310,16 @@ def test_full_size_gradient_sampled(lib, prec):
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5), ("ff", 1e-5)])
 def test_multiplane_chi2(lib, c2, prec, tol):
-    """Three planes, families at z = 4.  The catalogue's images are not images of this
-    synthetic model; the families kept are those with |det A| >= 0.02 at every image (near a
-    critical curve the mixed tier's FP32 magnification tensors set the chi^2 error)."""
+    """Three planes, families at z = 4, every family of the 200-image catalogue kept.  Its
+    images are not images of this synthetic model and many sit near its critical curves; the
+    forward chi^2 holds the stated bound there because the mixed tiers keep M in float-float
+    words (with FP32 words, 94 of 1024 samples of the benchmark's three-plane launch missed
+    1e-5, up to 4.3e-3)."""
     api, PM = lib
     _, cat, _ = c2
     wl = W.multiplane_c3(n_grid=8, n_samples=6)
     th = W.sample_thetas(wl, wl.seed)
-    cat3 = families_off_critical(wl, W.Catalogue(cat.theta_obs, cat.theta_true, cat.fam_off,
-                                                 np.full(len(cat.fam_zs), 4.0)), th, 0.02)
-    assert len(cat3.theta_obs) >= 60
+    cat3 = W.Catalogue(cat.theta_obs, cat.theta_true, cat.fam_off, np.full(len(cat.fam_zs), 4.0))
     plan = api.Plan([PM.cluster_input(wl, cat3)], 6, prec)
     c = plan.chi2(torch.tensor(th, device="cuda")).cpu().numpy()
     ref = oracle(wl, cat3, th).numpy()
@@ -356,11 +357,14 @@ def test_multiplane_true_images(lib, prec):
     (tests/helpers.three_plane_images: 44 images in 11 families at z = 4, every family kept,
     magnified images with |det A| down to ~0.01 and cond A up to ~60 included), on the
     unperturbed model (chi^2 ~ 4e-3, the catalogue's noise) and seven jittered samples.
-    FP64: the stated bounds.  Mixed tiers: near critical curves the FP32 psi_ij move chi^2 by
-    more than 1e-5 relative, so each sample is held to 1e-5 relative plus the first-order
-    rounding bound of tests/helpers.chi2_rounding_bound (FP32 psi_ij, FP32 A^-1 and M; the
-    mixed forward launch also FP32 member deflections); the float-float adjoint's gradient to
-    the stated 1e-4 per component (no image here reaches |det A| < 1e-3)."""
+    FP64: the stated bounds.  Float-float tier: the forward chi^2 (M in float-float words) to the
+    stated 1e-5.  Mixed tier's forward chi^2: at the unperturbed model chi^2 is the
+    catalogue's noise (~4e-3), and the FP32 member deflections' rounding (~1e-6") moves it by
+    more than 1e-5 of that, so it is held to 1e-5 relative plus the first-order rounding bound
+    of tests/helpers.chi2_rounding_bound with FP32 deflections.  The adjoint launch's chi^2,
+    whose M is FP32, to 1e-5 relative plus that bound without the deflection term; the
+    float-float adjoint's gradient to the stated 1e-4 per component (no image here reaches
+    |det A| < 1e-3)."""
     api, PM = lib
     from tests.helpers import chi2_rounding_bound, three_plane_images
     wl, cat = three_plane_images()
@@ -379,10 +383,12 @@ def test_multiplane_true_images(lib, prec):
         assert r1.max() <= CHI2_TOL[prec] and r.max() <= CHI2_TOL[prec]
     else:
         b_ff = chi2_rounding_bound(wl, cat, th)
-        b_fwd = chi2_rounding_bound(wl, cat, th, alpha_coef=4.0) if prec == "mixed" else b_ff
-        print(f"  bounds / chi2: forward {np.array2string(b_fwd / cref, precision=1)}, "
-              f"float-float {np.array2string(b_ff / cref, precision=1)}")
-        assert np.all(np.abs(c1 - cref) <= CHI2_TOL[prec] * cref + b_fwd)
+        print(f"  bound / chi2 (adjoint launch): {np.array2string(b_ff / cref, precision=1)}")
+        if prec == "ff":
+            assert r1.max() <= CHI2_TOL[prec]
+        else:
+            b_fwd = chi2_rounding_bound(wl, cat, th, alpha_coef=4.0)
+            assert np.all(np.abs(c1 - cref) <= CHI2_TOL[prec] * cref + b_fwd)
         assert np.all(np.abs(c - cref) <= CHI2_TOL["ff"] * cref + b_ff)
     assert grad_ok(g.cpu().numpy(), gref, prec)
     api.device_error()
