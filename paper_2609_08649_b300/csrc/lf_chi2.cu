@@ -54,6 +54,7 @@ struct PlaneDesc {
   uint32_t off_dm;                 // scalar member records (adjoint, flux / time-delay pass)
   uint32_t off_dmp;                // the mixed tier's packed pairs (forward passes); = off_dm else
   uint32_t off_mfac;               // the mixed tier's members' base factors (fb, fs, fa), FP32
+  uint32_t off_dma;                // the mixed tier's gradient: each member's change (MemA)
 };
 
 struct ClusterDesc {
@@ -88,6 +89,9 @@ struct ClusterDesc {
   const float4* theta_ff;          // [n_img] (x_hi, x_lo, y_hi, y_lo)
   const float2* ratio_ff;          // [n_fam * np]
   const float4* sinv_f;            // [n_img] (xx, xy, yy, 0)
+  // the mixed tier's gradient (one plane): every image's member deflection sum at the plan's
+  // base fields, FP64 rounded to float-float (x_hi, x_lo, y_hi, y_lo); null: not anchored
+  const float4* mbase;
   int mpg_stride;                  // multi-plane adjoint: doubles per image record
   uint32_t off_img, off_imgd, off_fam, off_par, off_free, off_newton, off_fama, off_aux, off_mpg;
   uint32_t off_auxg;               // adjoint of the flux / time-delay terms: per image records
@@ -489,8 +493,9 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
   // PASS 2: the flux / time-delay terms (the forward pass, or with GRAD their adjoint too); the
   // other instantiations carry none of that code
   constexpr bool AUX = PASS == 2;
-  // the forward source-plane chi^2 of the mixed tiers keeps every image's M in float-float words
-  constexpr bool FFM = MIXED && PASS == 0 && !GRAD;
+  // the source-plane chi^2 of the mixed tiers (and its adjoint) keeps every image's M in
+  // float-float words
+  constexpr bool FFM = MIXED && PASS == 0;
   constexpr bool FFSUM = PACKM && PASS == 0;
   // images per evaluation task (independent chains per thread; with packed members, two
   // member evaluations per instruction and chain); the FP64 tier takes two
@@ -623,6 +628,10 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
       const MemPre* mp = reinterpret_cast<const MemPre*>(P.mpre);   // plan table, L2-resident
       Mem* dm = reinterpret_cast<Mem*>(smem + P.off_dm);
       const T bstar = (T)sc.b_star, cstar = (T)sc.core_star, astar = (T)sc.cut_star;
+      // the gradient's anchored member sum: the plan's base scaling and the sample's change
+      const float bstar0 = (float)P.sc.b_star, cstar0 = (float)P.sc.core_star, astar0 = (float)P.sc.cut_star;
+      const float dbstar = (float)(sc.b_star - P.sc.b_star), dcstar = (float)(sc.core_star - P.sc.core_star),
+                  dastar = (float)(sc.cut_star - P.sc.cut_star);
       const int n_lanes = PACKM ? 2 * (int)mem_records<MemPair>(P.nm) : P.nm;
       for (int i = tid; i < n_lanes; i += blockDim.x) {
         if constexpr (PACKM) {
@@ -654,10 +663,27 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           T fb, fs, fa;
           MemT<T> d;
           if constexpr (MODE == LF_MIXED) {
-            fb = lam_free ? m.fb + fmaf(m.fb, expm1f((float)(2.0 * (sc.lam - P.sc.lam)) * m.lnl), m.fbl) : m.fb;
-            fs = beta_free ? m.fs + fmaf(m.fs, expm1f((float)(sc.beta - P.sc.beta) * m.lnl), m.fsl) : m.fs;
-            fa = alpha_free ? m.fa + fmaf(m.fa, expm1f((float)(sc.alpha - P.sc.alpha) * m.lnl), m.fal) : m.fa;
+            const float eb = lam_free ? expm1f((float)(2.0 * (sc.lam - P.sc.lam)) * m.lnl) : 0.f;
+            const float es = beta_free ? expm1f((float)(sc.beta - P.sc.beta) * m.lnl) : 0.f;
+            const float ea = alpha_free ? expm1f((float)(sc.alpha - P.sc.alpha) * m.lnl) : 0.f;
+            fb = lam_free ? m.fb + fmaf(m.fb, eb, m.fbl) : m.fb;
+            fs = beta_free ? m.fs + fmaf(m.fs, es, m.fsl) : m.fs;
+            fa = alpha_free ? m.fa + fmaf(m.fa, ea, m.fal) : m.fa;
             d.xh = m.xh; d.xl = m.xl; d.yh = m.yh; d.yl = m.yl;
+            if (GRAD && C.mbase) {
+              // b - b0 = (b* - b0*) f_b + b0* f_b0 expm1(2 dlam ln L), and alike for the core and
+              // the cut: FP32 rounds the change, not the field
+              MemA& q = reinterpret_cast<MemA*>(smem + P.off_dma)[i];
+              const float s0 = cstar0 * m.fs, a0 = astar0 * m.fa;
+              q.db = fmaf(dbstar, fb, bstar0 * m.fb * eb);
+              q.ds = fmaf(dcstar, fs, s0 * es);
+              q.da = fmaf(dastar, fa, a0 * ea);
+              q.s0 = s0;
+              q.a0 = a0;
+              q.s02 = s0 * s0;
+              q.a02 = a0 * a0;
+              q.pad = 0.f;
+            }
           } else {
             fb = lam_free ? exp(2.0 * sc.lam * m.lnl) : m.fb;
             fs = beta_free ? exp(sc.beta * m.lnl) : m.fs;
@@ -848,6 +874,9 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           if (act) {
             if constexpr (MODE == LF_FF)
               accumulate_ext<IPT>(dc, P.nc, dm, P.nm, k0, k1, xh, xl, yh, yl, tab, acc);
+            else if (GRAD && C.mbase)
+              accumulate_anchored<IPT>(dc, P.nc, dm, reinterpret_cast<const MemA*>(smem + P.off_dma), P.nm,
+                                       k0, k1, chunk, xh, xl, yh, yl, tab, acc);
             else
               accumulate_mixed<IPT>(dc, P.nc, dm, P.nm, k0, k1, chunk, xh, xl, yh, yl, tab, acc);
           }
@@ -865,6 +894,11 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
               if (q > 0 && ii[q] == ii[q - 1]) break;     // the clamped repeats of the last unit
+              if (MODE == LF_MIXED && GRAD && C.mbase) {  // the members' base sum
+                const float4 b4 = C.mbase[ii[q]];
+                acc[0][q] = ff_add(acc[0][q], ff_make(b4.x, b4.y));
+                acc[1][q] = ff_add(acc[1][q], ff_make(b4.z, b4.w));
+              }
               for (int c5 = 0; c5 < 5; ++c5) {
                 imgf[ii[q] * ISF + 2 * c5] = acc[c5][q].hi;
                 imgf[ii[q] * ISF + 2 * c5 + 1] = acc[c5][q].lo;
@@ -1484,8 +1518,27 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           const float* r0 = imgf + i0 * ISF;
           d0 = ff_to_double(ff_sub(ff_make(r[10], r[11]), ff_make(r0[10], r0[11]))) - fam[3 * f + 1];
           d1 = ff_to_double(ff_sub(ff_make(r[12], r[13]), ff_make(r0[12], r0[13]))) - fam[3 * f + 2];
-          M00 = r[14]; M01 = r[15]; M11 = r[16];
-          u00 = r[17]; u01 = r[18]; u10 = r[19]; u11 = r[20];
+          ff m00, m01, m11;
+          image_M(r, m00, m01, m11);
+          M00 = ff_to_double(m00); M01 = ff_to_double(m01); M11 = ff_to_double(m11);
+          // mu = A^-1 again in FP64 (words 17..20 hold M's low words): one plane from the
+          // float-float psi sums, several from the recursion's FP64 A
+          double A00 = 1.0, A01 = 0.0, A10 = 0.0, A11 = 1.0;
+          if (C.np == 1) {
+            const double a = fa[f];
+            A00 -= a * ((double)r[4] + (double)r[5]);
+            A11 -= a * ((double)r[6] + (double)r[7]);
+            A01 = A10 = -a * ((double)r[8] + (double)r[9]);
+          } else {
+            const double* st = imgd + i * ISD;
+            for (int l = 0; l < C.np; ++l) {
+              const double rs = C.fam_ratio[f * C.np + l];
+              const double* pl = st + 2 + 6 * l;
+              A00 -= rs * pl[2]; A01 -= rs * pl[3]; A10 -= rs * pl[4]; A11 -= rs * pl[5];
+            }
+          }
+          const double id = 1.0 / (A00 * A11 - A01 * A10);
+          u00 = A11 * id; u01 = -A01 * id; u10 = -A10 * id; u11 = A00 * id;
         } else {
           const double* r = img + i * IS;
           d0 = (r[8] - img[i0 * IS + 8]) - fam[3 * f + 1];
@@ -1761,6 +1814,34 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
   }
 }
 
+// The anchor of the mixed tier's gradient: every image's member deflection sum at the plan's
+// base fields (Eq. scaling, from the plan's float-float factor table), in FP64, rounded to
+// float-float words.  One thread per image; run once per plan.
+__global__ void k_member_base(const double* __restrict__ theta, int n_img, const MemPreF* __restrict__ mp,
+                              int nm, lf_scaling sc, float4* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_img) return;
+  const double x = theta[2 * i], y = theta[2 * i + 1];
+  double ax = 0.0, ay = 0.0;
+  for (int k = 0; k < nm; ++k) {
+    const MemPreF m = mp[k];
+    const double dx = x - ((double)m.xh + (double)m.xl), dy = y - ((double)m.yh + (double)m.yl);
+    const double b = sc.b_star * ((double)m.fb + (double)m.fbl);
+    const double s = sc.core_star * ((double)m.fs + (double)m.fsl);
+    const double a = sc.cut_star * ((double)m.fa + (double)m.fal);
+    const double r2 = dx * dx + dy * dy;
+    const double S = sqrt(s * s + r2), R = sqrt(a * a + r2);
+    // b (1/(S + s) - 1/(R + a)) without its far-field cancellation
+    const double kb = b * (a - s) / ((S + s) * (R + a)) * (1.0 + (a + s) / (R + S));
+    ax += kb * dx;
+    ay += kb * dy;
+  }
+  float xh, xl, yh, yl;
+  split_ff(ax, xh, xl);
+  split_ff(ay, yh, yl);
+  out[i] = make_float4(xh, xl, yh, yl);
+}
+
 }  // namespace lf
 
 // ======================================================================= host =======
@@ -1802,14 +1883,19 @@ struct lf_plan {
   int grid_chi2 = 0, grid_grad = 0, grid_aux = 0, grid_img = 0;   // grid_grad: of the plan's gradient kernel
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  const void* g_theta = nullptr;
-  void* g_out = nullptr;
-  int g_S = -1;
-  // LF_MIXED plans: the LF_FF plan over the same clusters that serves lf_chi2_grad_batch.
-  // The cotangents of the adjoint are weighted by the offsets d_i = beta_i - beta_model,
-  // which are only ~sigma_pos: FP32 member deflections (a few 1e-6 arcsec) would put ~1e-4
-  // relative errors on them, so the gradient evaluates the deflections in float-float.
+  // CUDA graphs of the chi^2 launch (slot 0) and the gradient launch (slot 1), each with the
+  // buffers and S it was captured for
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  const void* g_theta[2] = {nullptr, nullptr};
+  void* g_out[2] = {nullptr, nullptr};
+  int g_S[2] = {-1, -1};
+  // The cotangents of the adjoint are weighted by the offsets d_i = beta_i - beta_model, which
+  // are only ~sigma_pos: FP32 member deflections (a few 1e-6 arcsec) would put ~1e-4 relative
+  // errors on them.  A single-plane LF_MIXED plan without flux / time-delay terms therefore
+  // anchors its gradient's member sums at the plan's base fields (grad_anchor: the base sums
+  // per image in FP64, the sample's change in FP32); any other LF_MIXED plan runs its gradient
+  // on grad_ff, the LF_FF plan over the same clusters.
+  bool grad_anchor = false;
   lf_plan* grad_ff = nullptr;
 };
 
@@ -1965,6 +2051,8 @@ static void layout_cluster(ClusterDesc& C, int precision, int block, int ks_cap)
     if (precision == LF_MIXED) of = P.off_mfac + (uint32_t)P.nm * 12u;
     P.off_dm = al(os);
     os = P.off_dm + (uint32_t)P.nm * mem_sz;
+    P.off_dma = al(os);
+    if (precision == LF_MIXED && C.mbase) os = P.off_dma + (uint32_t)P.nm * (uint32_t)sizeof(MemA);
   }
   if (precision != LF_MIXED)
     for (int j = 0; j < C.np; ++j) C.pl[j].off_dmp = C.pl[j].off_dm;
@@ -2019,8 +2107,9 @@ static lf_status relayout(lf_plan* pl) {
                    : pl->precision == LF_FF  ? (const void*)k_chi2<LF_FF, false>
                                              : (const void*)k_chi2<LF_FP64, false>;
   // the gradient (with the flux / time-delay adjoint when the plan has measurements); a mixed
-  // plan's gradient runs on its LF_FF companion
-  const void* kg = pl->precision == LF_MIXED ? nullptr
+  // plan's gradient is anchored (one plane, no flux / time-delay terms) or runs on its LF_FF
+  // companion
+  const void* kg = pl->precision == LF_MIXED ? (pl->grad_anchor ? (const void*)k_chi2<LF_MIXED, true> : nullptr)
                    : pl->precision == LF_FF  ? (pl->has_aux ? (const void*)k_chi2<LF_FF, true, 2>
                                                             : (const void*)k_chi2<LF_FF, true>)
                                              : (pl->has_aux ? (const void*)k_chi2<LF_FP64, true, 2>
@@ -2051,10 +2140,11 @@ static lf_status relayout(lf_plan* pl) {
     LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kg, pl->block, pl->smem_grad));
     pl->grid_grad = nsm * std::max(occ, 1);
   }
-  if (pl->gexec) {
-    cudaGraphExecDestroy(pl->gexec);
-    pl->gexec = nullptr;
-  }
+  for (int g = 0; g < 2; ++g)
+    if (pl->gexec[g]) {
+      cudaGraphExecDestroy(pl->gexec[g]);
+      pl->gexec[g] = nullptr;
+    }
   return LF_OK;
 }
 
@@ -2211,8 +2301,12 @@ static void launch_mode(lf_plan* pl, const double* theta, int S, double* chi2, d
     k_chi2_prep<MODE><<<(nprep + 63) / 64, 64, 0, st>>>(pl->d_desc, spc, S, pl->nfree_max, theta,
                                                         pl->d_free_dig, pl->d_free_raw);
   if (grad) {
-    if constexpr (MODE != LF_MIXED) {   // a mixed plan's gradient runs on its LF_FF plan
-      int g = std::min(pl->grid_grad, S);
+    int g = std::min(pl->grid_grad, S);
+    if constexpr (MODE == LF_MIXED) {   // anchored plans only (the others use their LF_FF plan)
+      k_chi2<MODE, true><<<g, pl->block, pl->smem_grad, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
+                                                         grad, pl->d_counter, g_member_chunk,
+                                                         pl->d_free_dig, pl->d_free_raw);
+    } else {
       if (pl->has_aux)
         k_chi2<MODE, true, 2><<<g, pl->block, pl->smem_grad, st>>>(pl->d_desc, pl->d_order, spc, S, theta,
                                                               chi2, grad, pl->d_counter, g_member_chunk,
@@ -2340,22 +2434,23 @@ static lf_status run(lf_plan* pl, const double* theta, int S, double* chi2, doub
   // CUDA graph: the counter reset and the persistent launch, replayed while the buffers and
   // S are unchanged, on the plan's stream ordered after / before the caller's stream.
   void* out_key = grad ? (void*)grad : (void*)chi2;
-  if (!pl->gexec || pl->g_theta != theta || pl->g_out != out_key || pl->g_S != S) {
-    if (pl->gexec) { cudaGraphExecDestroy(pl->gexec); pl->gexec = nullptr; }
+  const int gs = grad ? 1 : 0;
+  if (!pl->gexec[gs] || pl->g_theta[gs] != theta || pl->g_out[gs] != out_key || pl->g_S[gs] != S) {
+    if (pl->gexec[gs]) { cudaGraphExecDestroy(pl->gexec[gs]); pl->gexec[gs] = nullptr; }
     cudaGraph_t g = nullptr;
     LF_CUDA(cudaStreamBeginCapture(pl->gstream, cudaStreamCaptureModeThreadLocal));
     lf_status ls = launch_chi2(pl, theta, S, chi2, grad, pl->gstream);
     cudaError_t ce = cudaStreamEndCapture(pl->gstream, &g);
     if (ls != LF_OK) { if (g) cudaGraphDestroy(g); return ls; }
     if (ce != cudaSuccess) return fail(LF_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
-    ce = cudaGraphInstantiate(&pl->gexec, g, 0);
+    ce = cudaGraphInstantiate(&pl->gexec[gs], g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) return fail(LF_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
-    pl->g_theta = theta; pl->g_out = out_key; pl->g_S = S;
+    pl->g_theta[gs] = theta; pl->g_out[gs] = out_key; pl->g_S[gs] = S;
   }
   LF_CUDA(cudaEventRecord(pl->ev_in, st));
   LF_CUDA(cudaStreamWaitEvent(pl->gstream, pl->ev_in, 0));
-  LF_CUDA(cudaGraphLaunch(pl->gexec, pl->gstream));
+  LF_CUDA(cudaGraphLaunch(pl->gexec[gs], pl->gstream));
   LF_CUDA(cudaEventRecord(pl->ev_out, pl->gstream));
   LF_CUDA(cudaStreamWaitEvent(st, pl->ev_out, 0));
   return LF_OK;
@@ -2366,7 +2461,8 @@ static lf_status run(lf_plan* pl, const double* theta, int S, double* chi2, doub
 extern "C" lf_status lf_plan_destroy(lf_plan* pl) {
   if (!pl) return LF_OK;
   if (pl->grad_ff) lf_plan_destroy(pl->grad_ff);
-  if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+  for (int g = 0; g < 2; ++g)
+    if (pl->gexec[g]) cudaGraphExecDestroy(pl->gexec[g]);
   if (pl->ev_in) cudaEventDestroy(pl->ev_in);
   if (pl->ev_out) cudaEventDestroy(pl->ev_out);
   if (pl->gstream) cudaStreamDestroy(pl->gstream);
@@ -2423,6 +2519,22 @@ extern "C" lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, i
     if (st == LF_OK) pl->d_free_raw = (lf_comp*)p;
     if (st == LF_OK) st = plan_alloc(pl, &p, n_clusters * sizeof(ClusterDesc));
     if (st == LF_OK) pl->d_desc = (ClusterDesc*)p;
+    if (st == LF_OK && precision == LF_MIXED && pl->single_plane && !pl->has_aux) {
+      // the anchored gradient: the members' base sums at every image
+      for (int c = 0; c < n_clusters && st == LF_OK; ++c) {
+        ClusterDesc& C = pl->desc[c];
+        st = plan_alloc(pl, &p, (size_t)std::max(C.n_img, 1) * sizeof(float4));
+        if (st != LF_OK) break;
+        const PlaneDesc& P0 = C.pl[0];
+        if (C.n_img > 0)
+          k_member_base<<<(C.n_img + 127) / 128, 128>>>(C.theta, C.n_img, (const MemPreF*)P0.mpre, P0.nm,
+                                                        P0.sc, (float4*)p);
+        C.mbase = (const float4*)p;
+      }
+      if (st == LF_OK && (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess))
+        st = fail(LF_ECUDA, "the members' base sums failed");
+      pl->grad_anchor = st == LF_OK;
+    }
     if (st == LF_OK) st = relayout(pl);
     if (st == LF_OK && (flags & 1)) {
       if (cudaStreamCreateWithFlags(&pl->gstream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -2431,7 +2543,7 @@ extern "C" lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, i
         st = fail(LF_ECUDA, "stream / event creation failed");
     }
   }
-  if (st == LF_OK && precision == LF_MIXED)
+  if (st == LF_OK && precision == LF_MIXED && !pl->grad_anchor)
     st = lf_plan_create(&pl->grad_ff, clusters, n_clusters, max_samples, LF_FF, flags);
   if (st != LF_OK) {
     lf_plan_destroy(pl);
@@ -2451,6 +2563,8 @@ extern "C" lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int3
   if (!plan) return fail(LF_EINVAL, "plan is NULL");
   if (!grad) return fail(LF_EINVAL, "grad is NULL");
   if (plan->grad_ff) plan = plan->grad_ff;
+  if (plan->precision == LF_MIXED && !plan->grad_anchor)
+    return fail(LF_EUNSUPPORTED, "no gradient plan");
   if (plan->smem_grad == 0)
     return fail(LF_EUNSUPPORTED, "the multi-plane adjoint's per-image records do not fit in shared memory");
   if (plan->aux_afree)

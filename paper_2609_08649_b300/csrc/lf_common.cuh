@@ -397,6 +397,15 @@ template <class T> struct MemT {
   T fs, loglr, pad0, pad1;  // fs = (L/L*)^beta = s / core*, loglr = ln(L/L*)
 };
 
+// A member's change from the plan's base fields to the sample's, for the anchored member sum
+// of the gradient's forward pass: ds = s - s0, da = a - a0, db = b - b0 (each from the sampled
+// factors' small perturbations, so that FP32 rounds the change, not the field), and the base
+// core and cut with their squares.
+struct MemA {
+  float ds, da, db, s0;
+  float a0, s02, a02, pad;
+};
+
 // Builds the evaluation constants of one explicit component from its fields.
 template <class T>
 __host__ __device__ inline void digest_comp(int kind, double x, double y, double b, double eps,
@@ -643,6 +652,43 @@ LF_INLINE void eval_member(const MemT<T>& m, T dx, T dy, Out5<T>& o) {
   o.ay = kbar * dy;
   o.pxx = lf_fma(t * dx, dx, kbar);
   o.pyy = lf_fma(t * dy, dy, kbar);
+  o.pxy = t * dx * dy;
+}
+
+// The change of a pseudo-Jaffe member's deflection from its base fields (b0, s0, a0) to the
+// sample's (b, s, a) at a fixed offset, and the sample's psi_ij.  With P = 1/(S + s),
+// Q = 1/(R + a), S = sqrt(s^2 + r^2), R = sqrt(a^2 + r^2) and kbar = P - Q:
+//   P - P0 = -ds (P + P0) / (S + S0),   Q - Q0 = -da (Q + Q0) / (R + R0),
+//   b kbar - b0 kbar0 = db kbar + b0 (kbar - kbar0),
+// with kbar in its cancellation-free form (a - s) P Q (1 + (a + s) / (R + S)).  Every FP32
+// rounding falls on a term proportional to (ds, da, db), so the change carries a relative
+// error of a few u of itself instead of u of the member's whole deflection.  o.ax, o.ay: the
+// change; o.pxx, o.pyy, o.pxy: the sample's psi_ij.  Three reciprocals share two MUFU rcp.
+LF_INLINE void eval_member_anchored(const MemT<float>& m, const MemA& d, float dx, float dy,
+                                    Out5<float>& o) {
+  const float r2 = fmaf(dx, dx, dy * dy);
+  const float S2 = m.s2 + r2, R2 = m.a2 + r2, S02 = d.s02 + r2, R02 = d.a02 + r2;
+  const float iS = lf_rsqrt(S2), iR = lf_rsqrt(R2), iS0 = lf_rsqrt(S02), iR0 = lf_rsqrt(R02);
+  const float S = S2 * iS, R = R2 * iR, S0 = S02 * iS0, R0 = R02 * iR0;
+  const float Ss = S + m.s, Ra = R + m.a, Ss0 = S0 + d.s0, Ra0 = R0 + d.a0;
+  const float X = Ss * Ra, X0 = Ss0 * Ra0;
+  const float inv = lf_rcp(X * X0);
+  const float PQ = inv * X0, P0Q0 = inv * X;
+  const float P = PQ * Ra, Q = PQ * Ss, P0 = P0Q0 * Ra0, Q0 = P0Q0 * Ss0;
+  const float Y1 = S + S0, Y2 = R + R0, Y3 = R + S;
+  const float Y12 = Y1 * Y2;
+  const float inv2 = lf_rcp(Y12 * Y3);
+  const float iY3 = inv2 * Y12, iY12 = inv2 * Y3;
+  const float dP = -d.ds * (P + P0) * (iY12 * Y2);
+  const float dQ = -d.da * (Q + Q0) * (iY12 * Y1);
+  const float kk = (m.a - m.s) * PQ * fmaf(m.apc, iY3, 1.0f);   // kbar of the sample
+  const float dK = fmaf(d.db, kk, (m.b - d.db) * (dP - dQ));
+  const float K = m.b * kk;
+  const float t = m.b * (Q * Q * iR - P * P * iS);
+  o.ax = dK * dx;
+  o.ay = dK * dy;
+  o.pxx = fmaf(t * dx, dx, K);
+  o.pyy = fmaf(t * dy, dy, K);
   o.pxy = t * dx * dy;
 }
 

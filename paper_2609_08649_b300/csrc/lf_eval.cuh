@@ -289,6 +289,57 @@ __device__ __forceinline__ void accumulate_mixed(const CompT<float>* dc, int nc,
   }
 }
 
+// The gradient's forward sums of the mixed tier: as accumulate_mixed, but each member adds
+// its change from the plan's base fields (eval_member_anchored) to alpha; the caller adds the
+// base sum of every image's members, taken once per plan in FP64.  psi_ij is the sample's.
+template <int PPT>
+__device__ __forceinline__ void accumulate_anchored(const CompT<float>* dc, int nc,
+                                                    const MemT<float>* dm, const MemA* da, int nm,
+                                                    int k0, int k1, int chunk, const float* pxh,
+                                                    const float* pxl, const float* pyh,
+                                                    const float* pyl, const float2* tab,
+                                                    ff (&acc)[5][PPT]) {
+  const int c1 = min(k1, nc);
+  for (int c = k0; c < c1; ++c) {
+    const CompT<float>& C = dc[c];
+    if (C.kind == 0) continue;
+    for (int k = 0; k < PPT; ++k) {
+      ff ax, ay;
+      Out5<float> o;
+      eval_comp_mixed(C, pxh[k], pxl[k], pyh[k], pyl[k], tab, ax, ay, o);
+      acc[0][k] = ff_add(acc[0][k], ax);
+      acc[1][k] = ff_add(acc[1][k], ay);
+      ff_acc(acc[2][k], o.pxx); ff_acc(acc[3][k], o.pyy); ff_acc(acc[4][k], o.pxy);
+    }
+  }
+  const int m_beg = max(k0, nc) - nc, m_end = min(k1, nc + nm) - nc;
+  for (int m0 = m_beg; m0 < m_end; m0 += chunk) {
+    const int m1 = min(m0 + chunk, m_end);
+    float cs[5][PPT];
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) cs[v][k] = 0.f;
+    for (int m = m0; m < m1; ++m) {
+      const MemT<float> M = dm[m];
+      const MemA D = da[m];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const float dx = offset_of(pxh[k], pxl[k], M.xh, M.xl);
+        const float dy = offset_of(pyh[k], pyl[k], M.yh, M.yl);
+        Out5<float> o;
+        eval_member_anchored(M, D, dx, dy, o);
+        cs[0][k] += o.ax; cs[1][k] += o.ay;
+        cs[2][k] += o.pxx; cs[3][k] += o.pyy; cs[4][k] += o.pxy;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) ff_acc(acc[v][k], cs[v][k]);
+  }
+}
+
 // FP64 version for one position: plain sum.
 __device__ __forceinline__ void accumulate_fp64(const CompT<double>* dc, int nc,
                                                 const MemT<double>* dm, int nm, int k0, int k1,
