@@ -371,6 +371,11 @@ constexpr int LF_PAIR_CHUNK = 32;
 #endif
 #define LF_CHI2_CAPPED(MODE, GRAD, PASS) ((MODE) == LF_MIXED && !(GRAD) && (PASS) != 2)
 // largest block a plan of this tier may use
+// Threads per block of the mixed tier's gradient launch: at its 128 registers per thread and
+// ~50 KB of shared memory per block, 4 blocks of 128 fill the SM's registers (16 warps)
+#ifndef LF_CHI2_GRAD_BLOCK
+#define LF_CHI2_GRAD_BLOCK 128
+#endif
 static inline int chi2_max_block(int precision) {
   return precision == LF_MIXED ? std::min(LF_CHI2_THREADS, LF_CHI2_FWD_THREADS) : LF_CHI2_THREADS;
 }
@@ -1658,6 +1663,141 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
       // Every lane of a warp runs each round (inactive ones with zero terms), so that each
       // parameter's terms are summed over the warp by shuffles and added to the block's
       // accumulator by one lane: one shared-memory atomic per warp, not one per lane.
+      if constexpr (!AUX) {
+        // The sampled explicit components: one task per (component, image), the images padded
+        // to whole warps so that a warp's lanes share the component and its terms are summed
+        // by shuffles (a cluster with few images still fills the block).
+        const int n_imgp = (n_img + 31) & ~31;
+        const int ntask_e = C.n_free * n_imgp;
+        for (int base = 0; base < ntask_e; base += blockDim.x) {
+          const int t = base + tid;
+          const int f = min(t / n_imgp, C.n_free - 1);
+          const int i = t - (t / n_imgp) * n_imgp;
+          const lf_comp& rc = fraw[f];
+          if (t >= ntask_e || C.free_plane[f] != j || rc.kind < 1 || rc.kind > 6) continue;   // whole warps
+          T g[7] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0, (T)0};
+          if (i < n_img) {
+            T cot[5];
+            double px, py;
+            if (C.np > 1) {
+              const double* rj = mpg + i * MPS + 10 * j;
+              for (int q = 0; q < 5; ++q) cot[q] = (T)rj[5 + q];
+              px = rj[0]; py = rj[1];
+            } else {
+              if constexpr (MIXED) {
+                for (int q = 0; q < 5; ++q) cot[q] = imgf[i * ISF + q];
+              } else {
+                for (int q = 0; q < 5; ++q) cot[q] = img[i * IS + q];
+              }
+              px = C.theta[2 * i]; py = C.theta[2 * i + 1];
+            }
+            Out5<Dual<T, 6>> o;
+            comp_dual<T>(rc, px, py, o);
+            // field order x, y, b, eps, pa, core, cut; tangent slots x0 y1 eps2 pa3 core4 cut5
+            const int slot[7] = {0, 1, -1, 2, 3, 4, 5};
+            const T b = (T)rc.b;
+            for (int q = 0; q < 7; ++q) g[q] = q == LF_F_B ? contract(o, cot, -1) : b * contract(o, cot, slot[q]);
+          }
+          for (int q = 0; q < 7; ++q) {
+            const int p = C.free_p[f][q];
+            if (p < 0) continue;
+            const double gw = warp_sum((double)g[q]);
+            if ((tid & 31) == 0) atomicAdd(&gacc[p], gw * xform_deriv(C.p_xform[p], th[p], P.apk));
+          }
+        }
+      }
+      if constexpr (!AUX) {
+        if (mem_grad) {
+          // The members: one task per (image pair, component slice), two independent chains
+          // per lane and one shared-memory read of each member record for both images.  Each
+          // member's (alpha, Psi) per unit strength is kbar (dx, dy) and Psi_ij = kbar delta_ij +
+          // t x_i x_j; its derivative in a parameter contracts with the cotangents as
+          // kbar' U + t' V, with U and V below.  Closed forms, P = 1/(S + s), Q = 1/(R + a):
+          // dkbar/ds = -P/S, dkbar/da = Q/R, dt/ds = (P^2/S^2)(2 + s/S), dt/da =
+          // -(Q^2/R^2)(2 + a/R); kbar = P - Q is taken in its cancellation-free form.
+          const int ntask_m = ((n_img + 1) / 2) * KS;
+          for (int base = 0; base < ntask_m; base += blockDim.x) {
+            const int t = base + tid;
+            const bool act = t < ntask_m;
+            const int pr = act ? t / KS : 0, k = act ? t - pr * KS : 0;
+            const int k0 = act ? (int)((long long)K * k / KS) : 0;
+            const int k1 = act ? (int)((long long)K * (k + 1) / KS) : 0;
+            const int m0 = act ? max(k0, P.nc) - P.nc : 0, m1 = act ? min(k1, K) - P.nc : 0;
+            T cot[2][5], qxh[2], qxl[2], qyh[2], qyl[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int i = min(2 * pr + h, n_img - 1);
+              double px, py;
+              if (C.np > 1) {
+                const double* rj = mpg + i * MPS + 10 * j;
+                for (int q = 0; q < 5; ++q) cot[h][q] = (T)rj[5 + q];
+                px = rj[0]; py = rj[1];
+              } else {
+                if constexpr (MIXED) {
+                  for (int q = 0; q < 5; ++q) cot[h][q] = imgf[i * ISF + q];
+                } else {
+                  for (int q = 0; q < 5; ++q) cot[h][q] = img[i * IS + q];
+                }
+                px = C.theta[2 * i]; py = C.theta[2 * i + 1];
+              }
+              if (2 * pr + h >= n_img)      // the odd image count's empty slot
+                for (int q = 0; q < 5; ++q) cot[h][q] = (T)0;
+              if constexpr (MIXED) {
+                float a_, b_, c_, d_;
+                split_ff(px, a_, b_);
+                split_ff(py, c_, d_);
+                qxh[h] = a_; qxl[h] = b_; qyh[h] = c_; qyl[h] = d_;
+              } else {
+                qxh[h] = (T)px; qxl[h] = (T)0; qyh[h] = (T)py; qyl[h] = (T)0;
+              }
+            }
+            T gs[6] = {0, 0, 0, 0, 0, 0};
+            for (int m = m0; m < m1; ++m) {
+              const Mem& M = dm[m];
+              const T Ms = mem_s(M), Ma = mem_a(M);
+              T Gb = (T)0, Gs = (T)0, Ga = (T)0;
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                T dx, dy;
+                if constexpr (MIXED) {
+                  dx = offset_of(qxh[h], qxl[h], M.xh, M.xl);
+                  dy = offset_of(qyh[h], qyl[h], M.yh, M.yl);
+                } else {
+                  dx = qxh[h] - M.xh;
+                  dy = qyh[h] - M.yh;
+                }
+                const T* c = cot[h];
+                const T dxx = dx * dx, dyy = dy * dy, r2 = dxx + dyy;
+                const T iS = ::lf_rsqrt(::lf_fma(Ms, Ms, r2)), iR = ::lf_rsqrt(::lf_fma(Ma, Ma, r2));
+                const T S = ::lf_fma(Ms, Ms, r2) * iS, R = ::lf_fma(Ma, Ma, r2) * iR;
+                const T Pq = ::lf_rcp(S + Ms), Qq = ::lf_rcp(R + Ma);
+                const T kb = (Ma - Ms) * Pq * Qq * ::lf_fma(Ma + Ms, ::lf_rcp(R + S), (T)1);
+                const T P2iS = Pq * Pq * iS, Q2iR = Qq * Qq * iR;
+                const T U = ::lf_fma(c[0], dx, ::lf_fma(c[1], dy, c[2] + c[3]));
+                const T V = ::lf_fma(c[2], dxx, ::lf_fma(c[3], dyy, c[4] * dx * dy));
+                Gb += ::lf_fma(kb, U, (Q2iR - P2iS) * V);
+                Gs += ::lf_fma(-Pq * iS, U, P2iS * iS * ::lf_fma(Ms, iS, (T)2) * V);
+                Ga += ::lf_fma(Qq * iR, U, -Q2iR * iR * ::lf_fma(Ma, iR, (T)2) * V);
+              }
+              Gs *= M.b;
+              Ga *= M.b;
+              const T fa = Ma * inv_cut_star;
+              gs[LF_S_BSTAR] += Gb * M.fb;
+              gs[LF_S_LAM] += Gb * M.b * (T)2 * M.loglr;
+              gs[LF_S_CORESTAR] += Gs * M.fs;
+              gs[LF_S_BETA] += Gs * Ms * M.loglr;
+              gs[LF_S_CUTSTAR] += Ga * fa;
+              gs[LF_S_ALPHA] += Ga * Ma * M.loglr;
+            }
+            for (int q = 0; q < 6; ++q) {
+              const int p = C.scal_p[q];
+              if (p < 0) continue;
+              const double gw = warp_sum((double)gs[q]);
+              if ((tid & 31) == 0) atomicAdd(&gacc[p], gw * xform_deriv(C.p_xform[p], th[p], P.apk));
+            }
+          }
+        }
+      } else
       for (int base = 0; base < ntask_img; base += blockDim.x) {
         const int t = base + tid;
         const bool act = t < ntask_img;
@@ -1685,6 +1825,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           }
           px = C.theta[2 * i]; py = C.theta[2 * i + 1];
         }
+        if constexpr (AUX)
         for (int f = 0; f < C.n_free; ++f) {
           const int kc = C.free_comp[f];
           if (C.free_plane[f] != j) continue;
@@ -1876,6 +2017,7 @@ struct lf_plan {
   lf_comp* d_free_raw = nullptr;   // [max_samples * LF_MAX_FREE] their fields (adjoint)
   std::vector<void*> allocs;
   int block = LF_CHI2_BLOCK;
+  int block_grad = LF_CHI2_BLOCK;  // threads per block of the gradient launch
   int ks_cap = 32;
   bool tuned = false;
   uint32_t smem = 0, smem_img = 0, smem_aux = 0;
@@ -2135,9 +2277,10 @@ static lf_status relayout(lf_plan* pl) {
   LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kc, pl->block, pl->smem));
   pl->grid_chi2 = nsm * std::max(occ, 1);
   pl->grid_grad = 0;
+  pl->block_grad = pl->grad_anchor ? LF_CHI2_GRAD_BLOCK : pl->block;
   if (pl->smem_grad > 0 && kg) {
     LF_TRY(kset(kg, pl->smem_grad));
-    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kg, pl->block, pl->smem_grad));
+    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kg, pl->block_grad, pl->smem_grad));
     pl->grid_grad = nsm * std::max(occ, 1);
   }
   for (int g = 0; g < 2; ++g)
@@ -2303,9 +2446,9 @@ static void launch_mode(lf_plan* pl, const double* theta, int S, double* chi2, d
   if (grad) {
     int g = std::min(pl->grid_grad, S);
     if constexpr (MODE == LF_MIXED) {   // anchored plans only (the others use their LF_FF plan)
-      k_chi2<MODE, true><<<g, pl->block, pl->smem_grad, st>>>(pl->d_desc, pl->d_order, spc, S, theta, chi2,
-                                                         grad, pl->d_counter, g_member_chunk,
-                                                         pl->d_free_dig, pl->d_free_raw);
+      k_chi2<MODE, true><<<g, pl->block_grad, pl->smem_grad, st>>>(pl->d_desc, pl->d_order, spc, S, theta,
+                                                              chi2, grad, pl->d_counter, g_member_chunk,
+                                                              pl->d_free_dig, pl->d_free_raw);
     } else {
       if (pl->has_aux)
         k_chi2<MODE, true, 2><<<g, pl->block, pl->smem_grad, st>>>(pl->d_desc, pl->d_order, spc, S, theta,
