@@ -326,7 +326,15 @@ lf_status lf_chi2_batch(lf_plan* plan, const double* theta, int32_t S, double* c
  * terms to chi2 and their adjoint to grad: through the magnification (third derivatives of
  * psi and their parameter derivatives), the arrival time (psi and its parameter derivatives)
  * and beta_model, on which these terms do depend; such a plan whose parameters include a
- * family's a_dis returns LF_EUNSUPPORTED. */
+ * family's a_dis returns LF_EUNSUPPORTED.
+ * Precision: the cotangents are weighted by the offsets beta_i - beta_model (~ the position
+ * errors), so the member deflections need more than FP32.  An LF_MIXED plan with one plane per
+ * cluster and no flux / time-delay terms anchors them at the plan's own fields: every image's
+ * member sum at the fields given to lf_plan_create, once, in FP64; per sample the change of
+ * each member from those fields in FP32, in a form whose rounding is relative to the change.
+ * Its precision is best for samples near the plan's fields (the usual case of a sampler or
+ * optimizer around a mode).  Any other LF_MIXED plan runs its gradient on an LF_FF plan over
+ * the same clusters, built with it. */
 lf_status lf_chi2_grad_batch(lf_plan* plan, const double* theta, int32_t S, double* chi2,
                              double* grad, void* stream);
 

@@ -4,13 +4,16 @@ differences), plus the plan's edge cases.
 
 Tolerances: FP64 path 1e-10 relative on chi^2 and 1e-8 on the gradient; the mixed and
 float-float tiers the stated targets, 1e-5 relative on chi^2 and 1e-4 on every gradient
-component (relative to the larger of |g_p| and 1e-2 max_p |g_p| of the sample).  The mixed
-tier's lf_chi2_grad_batch runs the float-float adjoint (its member deflections in float-float:
-the cotangents are weighted by d_i = beta_i - beta_model ~ sigma_pos, so FP32 deflections would
-put ~1e-4 relative errors on them), so its chi^2 and gradient share the float-float bounds.
+component (relative to the larger of |g_p| and 1e-2 max_p |g_p| of the sample).  The cotangents
+of the adjoint are weighted by d_i = beta_i - beta_model ~ sigma_pos, so FP32 member deflections
+would put ~1e-4 relative errors on them: the mixed tier's lf_chi2_grad_batch anchors its member
+sums at the plan's fields (FP64 sums per image once, the sample's change per member in FP32,
+rounded relative to the change) on single-plane plans, and runs the float-float adjoint on the
+others, so its chi^2 and gradient share the float-float bounds.
 The forward chi^2 (lf_chi2_batch) of the mixed tiers keeps M in float-float words and is held
 to 1e-5 on every sample, near critical curves included.  The adjoint launch forms A from FP32
-psi_ij and keeps M in FP32, so its gradient moves by ~u/|det A|^3 near a critical curve: a
+psi_ij (M in float-float words as well), so its gradient moves by ~u/|det A|^3 near a
+critical curve: a
 sample with an image at |det A| < 1e-3 is held to the near-critical bounds (norm 1e-3, 1e-2
 per component)."""
 import numpy as np
@@ -193,6 +196,60 @@ def test_gradient_matches_central_differences(lib, c2, prec):
     fd = np.array([(8 * (f[p, 0] - f[p, 1]) - (f[p, 2] - f[p, 3])) /
                    (12 * 1e-4 * max(abs(float(t0[0, p])), 1.0)) for p in range(P)])
     assert grad_ok(g.cpu().numpy(), fd[None], prec)
+
+
+@pytest.mark.parametrize("move", [0.1, 0.3])
+def test_mixed_gradient_far_from_plan_fields(lib, c2, move):
+    """The mixed tier anchors its gradient's member sums at the plan's fields: each image's sum
+    at the fields given to the plan in FP64, each member's change to the sample's fields in
+    FP32, rounded relative to the change.  Samples whose scaling amplitudes (v*, cut*) sit 10 %
+    and 30 % from the plan's still meet the stated chi^2 and gradient bounds (measured 4.3e-6
+    per component with the amplitudes 30 % rms away)."""
+    api, PM = lib
+    wl, cat, th = c2
+    base = np.array([p.base for p in wl.params])
+    ks = [i for i, p in enumerate(wl.params) if p.comp == -1]
+    t = th[1:4].copy()
+    signs = np.array([[1.0, -1.0], [-1.0, 1.0], [1.0, 1.0]])
+    for col, k in enumerate(ks):
+        t[:, k] = base[k] * (1.0 + move * signs[:, col])
+    plan = api.Plan([PM.cluster_input(wl, cat)], 8, "mixed")
+    c, g = plan.chi2_grad(torch.tensor(t, device="cuda"))
+    cref, gref = oracle(wl, cat, t, grad=True)
+    rel = np.abs(c.cpu().numpy() - cref.numpy()) / np.abs(cref.numpy())
+    print(f"amplitudes {move:.0%} from the plan's: chi2 rel {rel.max():.2e}")
+    assert np.all(rel <= CHI2_TOL["mixed"])
+    assert grad_ok(g.cpu().numpy(), gref.numpy(), "mixed")
+
+
+def test_mixed_gradient_sampled_exponents_far_from_plan(lib, c4):
+    """All six scaling slots sampled (one cluster of the 16-cluster workload), the exponents
+    lambda, beta, alpha moved by +-0.05 and the amplitudes by +-10 % from the plan's fields: the
+    anchored member changes (expm1 of the exponent change times ln L) against the oracle."""
+    api, PM = lib
+    wls, cats = c4
+    w, cat = wls[0], cats[0]
+    base = np.array([p.base for p in w.params])
+    t = np.tile(base, (3, 1))
+    sl = {p.field: i for i, p in enumerate(w.params) if p.comp == -1}
+    sg = np.array([1.0, -1.0, 1.0])
+    for f in (0, 1, 2):
+        t[:, sl[f]] = base[sl[f]] * (1.0 + 0.1 * sg * (1 if f != 1 else -1))
+    for f in (3, 4, 5):
+        t[:, sl[f]] = base[sl[f]] + 0.05 * sg * (1 if f != 4 else -1)
+    plan = api.Plan([PM.cluster_input(w, cat)], 4, "mixed")
+    c, g = plan.chi2_grad(torch.tensor(t, device="cuda"))
+    cref, gref = oracle(w, cat, t, grad=True)
+    rel = np.abs(c.cpu().numpy() - cref.numpy()) / np.abs(cref.numpy())
+    with torch.no_grad():
+        _, A = OG._terms(w, torch.tensor(t), torch.tensor(cat.theta_obs), list(cat.fam_off),
+                         fam_adis=OM.single_plane_adis(w, cat.fam_zs))
+    det = torch.linalg.det(A).abs().min(1).values.numpy()
+    print(f"exponents moved: chi2 rel {rel.max():.2e}, min |det A| per sample {det}")
+    for s_ in range(3):
+        assert rel[s_] <= max(CHI2_TOL["mixed"], chi2_mixed_bound(w, cat, t[s_:s_ + 1])[0] / abs(float(cref[s_])))
+        assert grad_ok(g[s_:s_ + 1].cpu().numpy(), gref[s_:s_ + 1].numpy(),
+                       "mixed" if det[s_] >= 1e-3 else "near_critical")
 
 
 @pytest.fixture(scope="module")
