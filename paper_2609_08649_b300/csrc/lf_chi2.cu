@@ -1752,10 +1752,55 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
               }
             }
             T gs[6] = {0, 0, 0, 0, 0, 0};
+            // FP32 tiers: the two images are the two lanes of packed f32x2 instructions (the
+            // MUFU results are consumed by scalar operations, as in member_pair_acc)
+            float2 px2, pxl2, py2, pyl2, c0, c1, c23, c2, c3, c4;
+            if constexpr (MIXED) {
+              px2 = make_float2(qxh[0], qxh[1]); pxl2 = make_float2(qxl[0], qxl[1]);
+              py2 = make_float2(qyh[0], qyh[1]); pyl2 = make_float2(qyl[0], qyl[1]);
+              c0 = make_float2(cot[0][0], cot[1][0]); c1 = make_float2(cot[0][1], cot[1][1]);
+              c2 = make_float2(cot[0][2], cot[1][2]); c3 = make_float2(cot[0][3], cot[1][3]);
+              c4 = make_float2(cot[0][4], cot[1][4]);
+              c23 = add2(c2, c3);
+            }
             for (int m = m0; m < m1; ++m) {
               const Mem& M = dm[m];
               const T Ms = mem_s(M), Ma = mem_a(M);
               T Gb = (T)0, Gs = (T)0, Ga = (T)0;
+              if constexpr (MIXED) {
+                const float2 dx = add2(add2(px2, make_float2(-M.xh, -M.xh)), add2(pxl2, make_float2(-M.xl, -M.xl)));
+                const float2 dy = add2(add2(py2, make_float2(-M.yh, -M.yh)), add2(pyl2, make_float2(-M.yl, -M.yl)));
+                const float2 Ms2 = make_float2(Ms, Ms), Ma2 = make_float2(Ma, Ma);
+                const float2 dxx = mul2(dx, dx), dyy = mul2(dy, dy), r2 = add2(dxx, dyy);
+                const float2 S2 = fma2(Ms2, Ms2, r2), R2 = fma2(Ma2, Ma2, r2);
+                float2 iS, iR, S, R, Pq, Qq, iRS, w, pq, nP2iS, Q2iR, gsU, gsV, gaU, gaV;
+                iS.x = rsqrtf(S2.x); iS.y = rsqrtf(S2.y);
+                iR.x = rsqrtf(R2.x); iR.y = rsqrtf(R2.y);
+                S.x = S2.x * iS.x; S.y = S2.y * iS.y;
+                R.x = R2.x * iR.x; R.y = R2.y * iR.y;
+                const float2 Ss = add2(S, Ms2), Ra = add2(R, Ma2), RS = add2(R, S);
+                Pq.x = __fdividef(1.f, Ss.x); Pq.y = __fdividef(1.f, Ss.y);
+                Qq.x = __fdividef(1.f, Ra.x); Qq.y = __fdividef(1.f, Ra.y);
+                iRS.x = __fdividef(1.f, RS.x); iRS.y = __fdividef(1.f, RS.y);
+                const float amp = Ma + Ms, ams = Ma - Ms;
+                w.x = fmaf(amp, iRS.x, 1.f); w.y = fmaf(amp, iRS.y, 1.f);
+                pq.x = Pq.x * Qq.x; pq.y = Pq.y * Qq.y;
+                nP2iS.x = -(Pq.x * Pq.x) * iS.x; nP2iS.y = -(Pq.y * Pq.y) * iS.y;
+                Q2iR.x = Qq.x * Qq.x * iR.x; Q2iR.y = Qq.y * Qq.y * iR.y;
+                gsU.x = -Pq.x * iS.x; gsU.y = -Pq.y * iS.y;
+                gsV.x = -nP2iS.x * iS.x * fmaf(Ms, iS.x, 2.f); gsV.y = -nP2iS.y * iS.y * fmaf(Ms, iS.y, 2.f);
+                gaU.x = Qq.x * iR.x; gaU.y = Qq.y * iR.y;
+                gaV.x = -Q2iR.x * iR.x * fmaf(Ma, iR.x, 2.f); gaV.y = -Q2iR.y * iR.y * fmaf(Ma, iR.y, 2.f);
+                const float2 kb = mul2(mul2(make_float2(ams, ams), pq), w);
+                const float2 U = fma2(c0, dx, fma2(c1, dy, c23));
+                const float2 V = fma2(c2, dxx, fma2(c3, dyy, mul2(c4, mul2(dx, dy))));
+                const float2 gb = fma2(kb, U, mul2(add2(Q2iR, nP2iS), V));
+                const float2 gss = fma2(gsU, U, mul2(gsV, V));
+                const float2 gaa = fma2(gaU, U, mul2(gaV, V));
+                Gb = gb.x + gb.y;
+                Gs = gss.x + gss.y;
+                Ga = gaa.x + gaa.y;
+              } else {
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
                 T dx, dy;
@@ -1778,6 +1823,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
                 Gb += ::lf_fma(kb, U, (Q2iR - P2iS) * V);
                 Gs += ::lf_fma(-Pq * iS, U, P2iS * iS * ::lf_fma(Ms, iS, (T)2) * V);
                 Ga += ::lf_fma(Qq * iR, U, -Q2iR * iR * ::lf_fma(Ma, iR, (T)2) * V);
+              }
               }
               Gs *= M.b;
               Ga *= M.b;
