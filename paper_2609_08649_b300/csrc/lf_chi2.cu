@@ -879,7 +879,7 @@ __global__ void __launch_bounds__(LF_CHI2_CAPPED(MODE, GRAD, PASS) ? LF_CHI2_FWD
           if (act) {
             if constexpr (MODE == LF_FF)
               accumulate_ext<IPT>(dc, P.nc, dm, P.nm, k0, k1, xh, xl, yh, yl, tab, acc);
-            else if (GRAD && C.mbase && j == 0)
+            else if (GRAD && C.mbase)   // anchored plans: one plane
               accumulate_anchored<IPT>(dc, P.nc, dm, reinterpret_cast<const MemA*>(smem + P.off_dma), P.nm,
                                        k0, k1, chunk, xh, xl, yh, yl, tab, acc);
             else
@@ -2708,11 +2708,10 @@ extern "C" lf_status lf_plan_create(lf_plan** out, const lf_cluster* clusters, i
     if (st == LF_OK) pl->d_free_raw = (lf_comp*)p;
     if (st == LF_OK) st = plan_alloc(pl, &p, n_clusters * sizeof(ClusterDesc));
     if (st == LF_OK) pl->d_desc = (ClusterDesc*)p;
-    // the anchored gradient: one plane (its member positions and the images are fixed). With
-    // members on the first of several planes only, anchoring measured 1.98 against 2.93 ms for
-    // the float-float companion, but the later planes' FP32 NFW sums then set the chi^2 of
-    // true images at the noise level (1.1e-6 against a 1e-7 bound), so such plans keep the
-    // companion.
+    // the anchored gradient: one plane, whose member positions and images are fixed.  (With
+    // members on the first of several planes only, the later planes' explicit components in
+    // float-float set the time: 3.00 ms against 2.92 ms for the float-float companion on the
+    // three-plane workload, so such plans keep the companion.)
     if (st == LF_OK && precision == LF_MIXED && pl->single_plane && !pl->has_aux) {
       // the anchored gradient: the members' base sums at every image
       for (int c = 0; c < n_clusters && st == LF_OK; ++c) {

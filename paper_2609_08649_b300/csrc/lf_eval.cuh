@@ -289,9 +289,12 @@ __device__ __forceinline__ void accumulate_mixed(const CompT<float>* dc, int nc,
   }
 }
 
-// The gradient's forward sums of the mixed tier: as accumulate_mixed, but each member adds
-// its change from the plan's base fields (eval_member_anchored) to alpha; the caller adds the
-// base sum of every image's members, taken once per plan in FP64.  psi_ij is the sample's.
+// The gradient's forward sums of the mixed tier: each member adds its change from the plan's
+// base fields (eval_member_anchored) to alpha, and the caller adds the base sum of every
+// image's members, taken once per plan in FP64; psi_ij is the sample's.  The explicit
+// components take the float-float tier's forms (eval_comp_ext: float-float deflections for
+// the round profiles and the spherical NFW as well), since the adjoint's cotangents need
+// every deflection beyond FP32.
 template <int PPT>
 __device__ __forceinline__ void accumulate_anchored(const CompT<float>* dc, int nc,
                                                     const MemT<float>* dm, const MemA* da, int nm,
@@ -306,7 +309,7 @@ __device__ __forceinline__ void accumulate_anchored(const CompT<float>* dc, int 
     for (int k = 0; k < PPT; ++k) {
       ff ax, ay;
       Out5<float> o;
-      eval_comp_mixed(C, pxh[k], pxl[k], pyh[k], pyl[k], tab, ax, ay, o);
+      eval_comp_ext(C, pxh[k], pxl[k], pyh[k], pyl[k], tab, ax, ay, o);
       acc[0][k] = ff_add(acc[0][k], ax);
       acc[1][k] = ff_add(acc[1][k], ay);
       ff_acc(acc[2][k], o.pxx); ff_acc(acc[3][k], o.pyy); ff_acc(acc[4][k], o.pxy);
