@@ -180,10 +180,11 @@ def test_gradient_matches_oracle_autograd(lib, c2, prec):
     assert np.all(np.abs(c.cpu().numpy() - cref.numpy()) <= CHI2_TOL[prec] * np.abs(cref.numpy()))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "ff"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "ff"])
 def test_gradient_at_round_halo(lib, c2, prec):
     """A sampled ellipticity at exactly eps = 0 (the round profile in the forward pass): the
-    adjoint takes the round branch with its exact derivative in eps there."""
+    adjoint takes the round branch with its exact derivative in eps there.  The mixed tier's
+    anchored launch evaluates that round halo in the float-float tier's form."""
     api, PM = lib
     wl, cat, th = c2
     t = th[:3].copy()
